@@ -1,0 +1,200 @@
+"""FP64 CPU oracle for NTVS (arXiv 1803.01112) -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline / reference arm of
+``bench.py`` may import this package.  The product library never uses it and shares
+no code with it.  The arithmetic is in ``ntvs_oracle.c`` (plain single-threaded C,
+double precision); this module is argument marshalling.
+
+Pins (what fixes each function independently of itself) live in ``tests/test_oracle_*.py``:
+  * orc_splitmix64 / orc_rand_ell : published SplitMix64 outputs, an independent
+    Python SplitMix64, and the N=1 no-check identity ell_k = k (Sec. II-B).
+  * orc_tv       : phi(const) = 0, closed form of a step edge, homogeneity and shift
+    invariance, the 1D total variation.
+  * orc_tv_grad  : central finite differences of phi_eps, and a hand-expanded 2x2x1 case.
+  * orc_drop_block / orc_drop_sweep : exact hyperplane projection of one-row blocks,
+    the one-row closed form, fixed points of consistent systems, convergence to the
+    numpy least-squares solution, a hand-computed 3-voxel 4-row block.
+  * orc_drop_block_at : equals orc_drop_block on every voxel of small cases.
+  * orc_ntvs     : N = 0 is plain DROP; the check variant without rejections equals
+    the variant without the check; accepted steps never raise phi; ell_k >= k.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ntvs_oracle.c")
+_SO = os.path.join(_HERE, "libntvs_oracle.so")
+
+
+def build_command(out: str = _SO):
+    return ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", out, _SRC, "-lm"]
+
+
+def build(force: bool = False) -> str:
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        subprocess.run(build_command(), check=True)
+    return _SO
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("alpha", ctypes.c_double), ("beta0", ctypes.c_double),
+                ("eps_tv", ctypes.c_double), ("N", ctypes.c_int32), ("tv_check", ctypes.c_int32),
+                ("max_retries", ctypes.c_int32), ("pad", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class _Trace(ctypes.Structure):
+    _fields_ = [("ell_k", ctypes.c_void_p), ("ell_step", ctypes.c_void_p), ("tries", ctypes.c_void_p),
+                ("accepted", ctypes.c_void_p), ("tv", ctypes.c_void_p), ("resid_ss", ctypes.c_void_p)]
+
+
+_L = None
+
+
+def _lib():
+    global _L
+    if _L is None:
+        build()
+        L = ctypes.CDLL(_SO)
+        vp, i64, u64, d, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_int32
+        L.orc_splitmix64.argtypes = [u64, u64]; L.orc_splitmix64.restype = u64
+        L.orc_rand_ell.argtypes = [u64, i64, i64]; L.orc_rand_ell.restype = i64
+        L.orc_tv.argtypes = [vp, i32, i32, i32, d]; L.orc_tv.restype = d
+        L.orc_tv_grad.argtypes = [vp, i32, i32, i32, d, vp]; L.orc_tv_grad.restype = None
+        L.orc_drop_block.argtypes = [vp, vp, vp, vp, i64, i64, i64, d, vp, vp]; L.orc_drop_block.restype = None
+        L.orc_drop_sweep.argtypes = [vp, vp, vp, vp, vp, i32, i64, d, vp, vp]; L.orc_drop_sweep.restype = None
+        L.orc_drop_block_at.argtypes = [vp, vp, vp, vp, i64, i64, i64, d, vp, i64, vp, vp]
+        L.orc_drop_block_at.restype = None
+        L.orc_ntvs.argtypes = [vp, vp, vp, vp, vp, i32, i32, i32, i32, ctypes.POINTER(_Params),
+                               i32, i32, ctypes.POINTER(i64), vp, vp, ctypes.POINTER(_Trace)]
+        L.orc_ntvs.restype = i32
+        _L = L
+    return _L
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+# ------------------------------------------------------------------ RNG / schedule
+def splitmix64(seed: int, n: int) -> int:
+    return int(_lib().orc_splitmix64(seed, n))
+
+
+def rand_ell(seed: int, k: int, ell_prev: int) -> int:
+    return int(_lib().orc_rand_ell(seed, k, ell_prev))
+
+
+# ------------------------------------------------------------------ TV
+def tv(x, shape, eps: float = 0.0) -> float:
+    nx, ny, nz = shape
+    x = _f64(x).reshape(-1)
+    assert x.size == nx * ny * nz
+    return float(_lib().orc_tv(x.ctypes.data, nx, ny, nz, eps))
+
+
+def tv_grad(x, shape, eps: float) -> np.ndarray:
+    nx, ny, nz = shape
+    x = _f64(x).reshape(-1)
+    g = np.empty_like(x)
+    _lib().orc_tv_grad(x.ctypes.data, nx, ny, nz, eps, g.ctypes.data)
+    return g
+
+
+# ------------------------------------------------------------------ DROP
+def _csr(row_ptr, col, val, b):
+    return (np.ascontiguousarray(row_ptr, np.int64), np.ascontiguousarray(col, np.int32),
+            _f64(val), _f64(b))
+
+
+def drop_block(row_ptr, col, val, b, r0: int, r1: int, x, lam: float):
+    rp, c, v, bb = _csr(row_ptr, col, val, b)
+    x = _f64(x).copy()
+    ss = ctypes.c_double(0.0)
+    _lib().orc_drop_block(rp.ctypes.data, c.ctypes.data, v.ctypes.data, bb.ctypes.data, r0, r1, x.size,
+                          lam, x.ctypes.data, ctypes.byref(ss))
+    return x, ss.value
+
+
+def drop_sweep(row_ptr, col, val, b, block_ptr, x, lam: float):
+    rp, c, v, bb = _csr(row_ptr, col, val, b)
+    bp = np.ascontiguousarray(block_ptr, np.int64)
+    B = bp.size - 1
+    x = _f64(x).copy()
+    ss = np.zeros(max(B, 1), np.float64)
+    _lib().orc_drop_sweep(rp.ctypes.data, c.ctypes.data, v.ctypes.data, bb.ctypes.data, bp.ctypes.data, B,
+                          x.size, lam, x.ctypes.data, ss.ctypes.data)
+    return x, ss[:B]
+
+
+def drop_block_at(row_ptr, col, val, b, r0: int, r1: int, x, lam: float, vox) -> np.ndarray:
+    rp, c, v, bb = _csr(row_ptr, col, val, b)
+    x = _f64(x)
+    vox = np.ascontiguousarray(vox, np.int64)
+    out = np.empty(vox.size, np.float64)
+    _lib().orc_drop_block_at(rp.ctypes.data, c.ctypes.data, v.ctypes.data, bb.ctypes.data, r0, r1, x.size,
+                             lam, x.ctypes.data, vox.size, vox.ctypes.data, out.ctypes.data)
+    return out
+
+
+# ------------------------------------------------------------------ NTVS
+@dataclass
+class Params:
+    lam: float
+    N: int
+    alpha: float
+    beta0: float = 1.0
+    tv_check: bool = False
+    seed: int = 0
+    eps_tv: float = 1e-8
+    max_retries: int = 64
+
+
+@dataclass
+class Result:
+    x: np.ndarray
+    ell_k: np.ndarray
+    ell_step: np.ndarray
+    tries: np.ndarray
+    accepted: np.ndarray
+    tv: np.ndarray
+    resid_ss: np.ndarray
+    ell_prev: int
+
+
+def ntvs(row_ptr, col, val, b, block_ptr, shape, params: Params, K: int, x0,
+         k0: int = 0, ell_prev: int = 0, ell_override: Optional[np.ndarray] = None) -> Result:
+    """K cycles of NTVS from x0 (Appendix C); returns the image and the traces."""
+    nx, ny, nz = shape
+    rp, c, v, bb = _csr(row_ptr, col, val, b)
+    bp = np.ascontiguousarray(block_ptr, np.int64)
+    B = bp.size - 1
+    x = _f64(x0).reshape(-1).copy()
+    N = params.N
+    ell_k = np.zeros(max(K, 1), np.int64)
+    ell_step = np.zeros(max(K * N, 1), np.int64)
+    tries = np.zeros(max(K * N, 1), np.int32)
+    accepted = np.zeros(max(K * N, 1), np.int32)
+    tvs = np.zeros(max(K, 1), np.float64)
+    rss = np.zeros(max(K * B, 1), np.float64)
+    tr = _Trace(ell_k.ctypes.data, ell_step.ctypes.data, tries.ctypes.data, accepted.ctypes.data,
+                tvs.ctypes.data, rss.ctypes.data)
+    p = _Params(params.lam, params.alpha, params.beta0, params.eps_tv, N, int(params.tv_check),
+                params.max_retries, 0, params.seed)
+    ep = ctypes.c_int64(ell_prev)
+    ov = None if ell_override is None else np.ascontiguousarray(ell_override, np.int64)
+    _lib().orc_ntvs(rp.ctypes.data, c.ctypes.data, v.ctypes.data, bb.ctypes.data, bp.ctypes.data, B,
+                    nx, ny, nz, ctypes.byref(p), K, k0, ctypes.byref(ep), _ptr(ov), x.ctypes.data,
+                    ctypes.byref(tr))
+    return Result(x, ell_k[:K], ell_step[:K * N].reshape(K, N), tries[:K * N].reshape(K, N),
+                  accepted[:K * N].reshape(K, N), tvs[:K], rss[:K * B].reshape(K, B), int(ep.value))
