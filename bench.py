@@ -1,0 +1,386 @@
+#!/usr/bin/env python3
+"""Benchmark of the NTVS hot path: histories/s per DROP+TVS iteration.
+
+Workload (default): CTP404-like phantom on a 200x200x16 grid of 1x1x2.5 mm voxels,
+10M bent proton histories over 360 angles (CSR, int32 columns, FP32 lengths, ~260
+entries per row), 20 DROP blocks, N=3 TV steps, alpha=0.75, lambda=2e-4, no TV check.
+One step = one NTVS cycle: N TV perturbation steps, a DROP sweep over all 20 blocks and
+the FP64 TV of the result.  value = histories / second of one cycle, whole job.
+
+The system (~21 GB) is far larger than L2 (129 MB), so every timed cycle streams it from
+HBM; no L2 flush is needed.  Device timing: CUDA events on the stream the library
+launches on.  `e2e` times the public C-ABI path from pinned host buffers: load the
+system, set the image, run 12 cycles, read the image back.
+
+--impl reference times the FP64 CPU oracle (plain C, one thread) on a bounded sample of
+the same workload (its first rows), per step one cycle.
+
+Multi-GPU (torchrun): every rank runs an independent replica of the reconstruction
+(reconstructions share nothing); value = all ranks' histories / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "histories/s per DROP+TVS iteration"
+UNIT = "histories/s"
+PARAMS = dict(lam=2e-4, N=3, alpha=0.75, seed=2)
+E2E_CYCLES = 12
+L2_NOTE = "inputs larger than L2: the system streamed every cycle is ~21 GB vs 129 MB L2"
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ntvs", "reference"], default="ntvs")
+    ap.add_argument("--workload", choices=["ctp404_full", "slice2d"], default="ctp404_full")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-rows", type=int, default=3_000_000, help="oracle sample: first rows of the workload")
+    ap.add_argument("--ref-rows", type=int, default=1_000_000, help="reference arm: rows per step")
+    ap.add_argument("--rows", type=int, default=0,
+                    help="profiling case: only the first ROWS histories, in blocks of the full workload's size")
+    return ap.parse_args(argv)
+
+
+def workload_spec(name):
+    import synth
+    if name == "slice2d":
+        return synth.spec_slice_2d(), np.float64
+    return synth.spec_ctp404_3d(), np.float32
+
+
+# ------------------------------------------------------------------ distributed helpers
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """MAX of a float over ranks (identity when world == 1)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int, device=None):
+    if world > 1:
+        import torch.distributed as dist
+        if device is not None and dist.get_backend() == "nccl":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, local_rank: int):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [v for v in vis.split(",") if v.strip()]
+        self.index = ids[local_rank] if local_rank < len(ids) and ids[local_rank].strip().isdigit() else str(local_rank)
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{local_rank}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.index, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        for ln in open(self.path):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                               parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ roofline inputs
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def drop_kernel_hash():
+    h = hashlib.sha256()
+    for f in ("kernels_drop.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1803_01112_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def ncu_traffic_per_launch():
+    """dram bytes per DROP launch from the committed ncu summary, if it was taken on the
+    current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "drop_block_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_src_sha256") != drop_kernel_hash():
+        return None
+    return d.get("dram_bytes_per_full_launch")
+
+
+def algorithmic_drop_bytes(s, val_itemsize, b_itemsize):
+    """HBM bytes a DROP block launch must move, per block: each entry's value and column
+    once, plus row_ptr (8 B), b and 1/||a||^2 per row.  x and delta stay in L2."""
+    bp = s.block_ptr()
+    out = []
+    for t in range(len(bp) - 1):
+        r0, r1 = int(bp[t]), int(bp[t + 1])
+        nnz = int(s.row_ptr[r1] - s.row_ptr[r0])
+        out.append(nnz * (val_itemsize + 4) + (r1 - r0) * (8 + 2 * b_itemsize))
+    return out
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+def time_oracle(spec, vdt, rows, K=1):
+    """Oracle cycles on the first `rows` histories of the workload (blocks of the same
+    size as the workload's).  Returns (seconds per cycle, rows, blocks)."""
+    import oracle
+    import synth
+    rows = min(rows, spec.n_hist)
+    s = synth.generate(spec, vdt, rows=(0, rows))
+    per = -(-spec.n_hist // spec.n_blocks)
+    B = max(1, -(-rows // per))
+    bp = np.minimum(np.arange(B + 1, dtype=np.int64) * per, rows)
+    val = s.val.astype(np.float64)
+    b = s.b.astype(vdt).astype(np.float64)
+    shape = (spec.nx, spec.ny, spec.nz)
+    prm = oracle.Params(lam=PARAMS["lam"], N=PARAMS["N"], alpha=PARAMS["alpha"], seed=PARAMS["seed"])
+    t0 = time.perf_counter()
+    oracle.ntvs(s.row_ptr, s.col, val, b, bp, shape, prm, K, s.xbar)
+    return (time.perf_counter() - t0) / K, rows, B
+
+
+# ------------------------------------------------------------------ arms
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    spec, vdt = workload_spec(args.workload)
+    rows = min(args.ref_rows, spec.n_hist)
+    import oracle
+    import synth
+    s = synth.generate(spec, vdt, rows=(0, rows))
+    per = -(-spec.n_hist // spec.n_blocks)
+    B = max(1, -(-rows // per))
+    bp = np.minimum(np.arange(B + 1, dtype=np.int64) * per, rows)
+    val = s.val.astype(np.float64)
+    b = s.b.astype(vdt).astype(np.float64)
+    shape = (spec.nx, spec.ny, spec.nz)
+    prm = oracle.Params(lam=PARAMS["lam"], N=PARAMS["N"], alpha=PARAMS["alpha"], seed=PARAMS["seed"])
+    x = s.xbar.copy()
+    ell = 0
+    for k in range(args.warmup):
+        res = oracle.ntvs(s.row_ptr, s.col, val, b, bp, shape, prm, 1, x, k0=k, ell_prev=ell)
+        x, ell = res.x, res.ell_prev
+    t0 = time.perf_counter()
+    for k in range(args.warmup, args.warmup + args.steps):
+        res = oracle.ntvs(s.row_ptr, s.col, val, b, bp, shape, prm, 1, x, k0=k, ell_prev=ell)
+        x, ell = res.x, res.ell_prev
+    dt = (time.perf_counter() - t0) / args.steps
+    value = rows / dt
+    sample = (f"first {rows} of {spec.n_hist} histories ({B} blocks of {per} rows), one NTVS cycle per step, "
+              "FP64 oracle in plain C")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": spec.name, "n_blocks": spec.n_blocks, **PARAMS, "tv_check": False},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ntvs(args):
+    import torch
+
+    import synth
+    import paper_1803_01112_gb300 as ntvs
+
+    rank, world, local = dist_env()
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+    ntvs.lib()
+    spec, vdt = workload_spec(args.workload)
+
+    def pinned(shape, dt):
+        t = torch.empty(int(np.prod(shape)), dtype=getattr(torch, np.dtype(dt).name), pin_memory=True)
+        return t.numpy()
+
+    n_blocks = spec.n_blocks
+    if args.rows:
+        per = -(-spec.n_hist // spec.n_blocks)
+        s = synth.generate(spec, vdt, alloc=pinned, rows=(0, min(args.rows, spec.n_hist)))
+        n_blocks = max(1, -(-s.M // per))
+        spec = spec.replace(n_hist=s.M, n_blocks=n_blocks, name=f"{spec.name}_first{s.M}rows")
+        s.spec = spec
+    else:
+        s = synth.generate(spec, vdt, alloc=pinned)
+    b = pinned((s.M,), vdt)
+    b[:] = s.b.astype(vdt)
+    x0 = pinned((spec.V,), vdt)
+    x0[:] = s.xbar.astype(vdt)
+    shape = (spec.nx, spec.ny, spec.nz)
+    stream = torch.cuda.current_stream(device)
+
+    r = ntvs.Reconstructor(local, stream.cuda_stream)
+    r.load(shape, s.row_ptr, s.col, s.val, b, n_blocks=spec.n_blocks)
+    r.set_params(**PARAMS)
+    r.set_image(x0)
+    r.run(args.warmup)
+    r.sync()
+    torch.cuda.synchronize(device)
+
+    # ---- timed region: K cycles, events on the launching stream
+    clocks = ClockSampler(local)
+    barrier(world, device)
+    torch.cuda.synchronize(device)
+    r.set_profiling(True)
+    launches0 = r.stats()["n_launches"]
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        r.run(1)
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    ms_local = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    barrier(world, device)
+    launches = r.stats()["n_launches"] - launches0
+    prof = r.profile()
+    r.set_profiling(False)
+    ms = max_over_ranks(ms_local, world, device)
+    ms_step = ms / args.steps
+    value = world * spec.n_hist * args.steps / (ms / 1e3)
+
+    # ---- roofline of the dominant kernel (DROP gather + scatter)
+    vsz = np.dtype(vdt).itemsize
+    blk_bytes = algorithmic_drop_bytes(s, vsz, vsz)
+    avg_bytes = float(np.mean(blk_bytes))
+    avg_ms = prof["drop_block_ms"] / max(prof["drop_block_launches"], 1)
+    achieved = avg_bytes / (avg_ms / 1e3) / 1e9
+    peak, peak_kind = measured_peaks()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": ncu_traffic_per_launch(), "kernel": "drop_block_kernel",
+                "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": avg_bytes,
+                "avg_launch_ms": avg_ms}
+    kernel_ms = {k: prof[k] / args.steps for k in ("drop_block_ms", "drop_apply_ms", "tv_ms")}
+
+    # ---- end to end through the C ABI from pinned host buffers
+    e2e = None
+    if not args.no_e2e and args.e2e_steps > 0:
+        h2d = s.row_ptr.nbytes + s.col.nbytes + s.val.nbytes + b.nbytes + x0.nbytes
+        out = pinned((spec.V,), vdt)
+        times = []
+        for _ in range(args.e2e_steps):
+            barrier(world, device)
+            torch.cuda.synchronize(device)
+            t0 = time.perf_counter()
+            re = ntvs.Reconstructor(local, stream.cuda_stream)
+            re.load(shape, s.row_ptr, s.col, s.val, b, n_blocks=spec.n_blocks)
+            re.set_params(**PARAMS)
+            re.set_image(x0)
+            re.run(E2E_CYCLES)
+            ntvs.ntvs_get_image(re.handle, out)
+            t1 = time.perf_counter()
+            re.close()
+            times.append(max_over_ranks(t1 - t0, world, device))
+        t_e2e = statistics.mean(times)
+        e2e = {"value": world * spec.n_hist * E2E_CYCLES / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(out.nbytes), "cycles_per_step": E2E_CYCLES,
+               "seconds_per_step": t_e2e}
+
+    # ---- CPU oracle baseline (rank 0, one GPU only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sec, rows, B = time_oracle(spec, vdt, args.cpu_rows)
+        cpu = {"value": rows / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {rows} of {spec.n_hist} histories ({B} blocks), one NTVS cycle, FP64 plain C"}
+
+    r.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32" if vdt == np.float32 else "f64", "data": "synthetic",
+                "config": {"workload": spec.name, "grid": [spec.nx, spec.ny, spec.nz], "histories": spec.n_hist,
+                           "nnz": s.nnz, "n_blocks": spec.n_blocks, **PARAMS, "tv_check": False,
+                           "storage": "csr32", "l2": L2_NOTE,
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "kernel_ms_per_step": kernel_ms, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ntvs(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

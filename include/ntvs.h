@@ -1,0 +1,221 @@
+/*
+ * ntvs.h - C ABI of the GB300 (sm_103a) NTVS reconstruction library.
+ *
+ * NTVS = total variation superiorization with N normalized TV perturbation steps of
+ * size beta0*alpha^ell between feasibility-seeking sweeps, with or without the TV
+ * reduction check (arXiv 1803.01112, Sec. II-B, Appendix C).  The feasibility-seeking
+ * operator P_T is one sweep of block-DROP over the blocks of proton histories
+ * (Sec. II-D, DROP of ref. CEHN08):
+ *
+ *     for each block t, with every row i of the block seeing the same x:
+ *       r_i  = (b_i - <a_i, x>) / ||a_i||^2            (0 when ||a_i|| = 0)
+ *       x_j += lambda * (1/s_j^t) * sum_{i in t} a_ij r_i   (only where s_j^t > 0)
+ *     s_j^t = number of stored entries (i, j) of block t with a_ij != 0.
+ *
+ * phi = TV = sum over voxels of the Euclidean length of the forward-difference
+ * vector (Sec. IV, ref. CCCNP10), index spacing, difference past the last index = 0.
+ * The perturbation direction is v = -grad phi_eps / ||grad phi_eps|| (Appendix A),
+ * phi_eps(x) = sum_p sqrt(eps + |forward differences at p|^2); v = 0 if the gradient is 0.
+ *
+ * Conventions for every entry point:
+ *   - returns NTVS_OK (0) or a negative NTVS_ERR_* code; ntvs_last_error() gives the
+ *     calling thread's last message.  No C++ exception crosses the ABI.
+ *   - images are dense [nz][ny][nx] (x fastest), voxel index (iz*ny + iy)*nx + ix.
+ *   - NTVS_MEM_HOST pointers are copied during the call (the caller keeps ownership).
+ *     NTVS_MEM_DEVICE pointers must be device memory of the context's GPU; system
+ *     arrays passed that way are borrowed and must outlive the context (or the next
+ *     ntvs_load_system).  Output buffers are allocated by the caller.
+ *   - work is queued on the context's CUDA stream; device-memory outputs are ready
+ *     when that stream reaches them, host outputs when the call returns.
+ *   - a context is not thread safe: one thread at a time per context.
+ */
+#ifndef NTVS_H
+#define NTVS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NTVS_OK 0
+#define NTVS_ERR_ARG (-1)      /* bad argument, size or pointer                       */
+#define NTVS_ERR_CSR (-2)      /* malformed system (row_ptr, col range, non-finite)   */
+#define NTVS_ERR_OOM (-3)      /* device allocation failed                            */
+#define NTVS_ERR_CUDA (-4)     /* a CUDA runtime call or kernel launch failed         */
+#define NTVS_ERR_TIMEOUT (-5)  /* a bounded device-side wait ran out                  */
+#define NTVS_ERR_STATE (-6)    /* call made in the wrong state (e.g. no system yet)   */
+
+/* element types */
+#define NTVS_F64 0
+#define NTVS_F32 1
+#define NTVS_F16 2
+#define NTVS_BF16 3
+
+/* memory kinds */
+#define NTVS_MEM_HOST 0
+#define NTVS_MEM_DEVICE 1
+
+/* index storage of the system on the device */
+#define NTVS_CSR32 0     /* int32 column per entry                                      */
+#define NTVS_DELTA16 1   /* uint16 column deltas along each row, packed at load time    */
+
+typedef struct ntvs_ctx ntvs_ctx;
+
+/* The linear system of one reconstruction: row i is proton history i, a_ij its
+ * intersection length with voxel j, b_i its WEPL (Sec. I, Sec. II-D). */
+typedef struct {
+    int32_t nx, ny, nz;          /* image grid, V = nx*ny*nz                                */
+    int32_t n_blocks;            /* B; used when block_ptr is NULL: contiguous blocks of
+                                    ceil(M/B) rows in stored order                           */
+    int64_t n_rows;              /* M >= 0                                                    */
+    const int64_t* row_ptr;      /* [M+1], row_ptr[0] = 0, non-decreasing (mem_kind)          */
+    const int32_t* col;          /* [nnz] voxel index in [0, V) (mem_kind)                    */
+    const void* val;             /* [nnz] a_ij, type val_dtype (mem_kind)                     */
+    const void* b;               /* [M] WEPL, double if val_dtype == NTVS_F64 else float      */
+    const int64_t* block_ptr;    /* NULL or [B+1] HOST array, block t = rows [bp[t], bp[t+1]) */
+    int32_t val_dtype;           /* NTVS_F64 (FP64 path) | NTVS_F32 (FP32 path) |
+                                    NTVS_F16 / NTVS_BF16 (FP32 arithmetic on half storage)   */
+    int32_t mem_kind;            /* NTVS_MEM_HOST | NTVS_MEM_DEVICE (row_ptr, col, val, b)    */
+    int32_t storage;             /* NTVS_CSR32 | NTVS_DELTA16                                 */
+    int32_t reserved;            /* 0                                                         */
+} ntvs_system;
+
+/* Parameters of NTVS (Sec. II-E, Appendix A/C). */
+typedef struct {
+    double lambda;       /* DROP relaxation lambda                                        */
+    double alpha;        /* perturbation kernel, 0 < alpha < 1                             */
+    double beta0;        /* beta_{k,n} = beta0 * alpha^ell; the paper's value is 1         */
+    double eps_tv;       /* epsilon of phi_eps in the gradient (>= 0; default 1e-8)        */
+    int32_t N;           /* TV perturbation steps per cycle, >= 0                          */
+    int32_t tv_check;    /* 0: NTVS; 1: NTVS with the TV reduction requirement             */
+    int32_t max_retries; /* tries per step in check mode before the step is skipped (>=1) */
+    int32_t reserved;    /* 0                                                              */
+    uint64_t seed;       /* stream of the ell draws (SplitMix64, output k for cycle k)     */
+} ntvs_params;
+
+typedef struct {
+    int64_t k;             /* cycles completed                                           */
+    int64_t ell_prev;      /* ell_{k-1}, the exponent carried into the next cycle        */
+    int64_t n_steps;       /* perturbation steps taken (N per cycle)                     */
+    int64_t n_accepted;    /* steps that changed x                                       */
+    int64_t n_tries;       /* tries (check mode: >= n_steps)                             */
+    int64_t nnz;           /* stored entries of the loaded system                        */
+    int64_t n_rows;        /* M                                                          */
+    int32_t n_blocks;      /* B                                                          */
+    int32_t compute_dtype; /* NTVS_F64 or NTVS_F32                                       */
+    double last_tv;        /* phi(x) after the last completed cycle (FP64)               */
+    int64_t n_launches;    /* kernels this context has launched (all entry points)       */
+} ntvs_stats;
+
+/* Device time of the context's kernels, measured with CUDA events recorded on the
+ * context's stream around every launch while profiling is on. */
+typedef struct {
+    double drop_block_ms;     /* DROP gather + scatter kernels (step a5)                 */
+    int64_t drop_block_launches;
+    double drop_apply_ms;     /* x += delta / s kernels (step a6)                         */
+    int64_t drop_apply_launches;
+    double tv_ms;             /* TV gradient, value and perturbation kernels              */
+    int64_t tv_launches;
+} ntvs_profile;
+
+/* Library version string. */
+const char* ntvs_version(void);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char* ntvs_last_error(void);
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t to queue
+ * work on (e.g. torch.cuda.current_stream().cuda_stream), or NULL for a stream the
+ * context creates and owns.  *out is NULL on failure. */
+int ntvs_create(ntvs_ctx** out, int device, void* cuda_stream);
+
+/* Destroy a context (synchronizes its stream, frees its device memory).  NULL is a no-op. */
+int ntvs_destroy(ntvs_ctx* ctx);
+
+/* Load (replace) the system.  Validates it on the device (row_ptr non-decreasing from 0,
+ * col in [0,V), finite val and b), computes ||a_i||^2 in FP64 from the stored values,
+ * the block partition and the per-block hit counts s_j^t, and packs DELTA16 storage.
+ * Resets the image to 0, the cycle counter k and ell_{k-1} to 0 and the traces.
+ * Errors: NTVS_ERR_ARG (sizes, dtypes, V > 2^31-1), NTVS_ERR_CSR (validation),
+ * NTVS_ERR_OOM, NTVS_ERR_CUDA.  Synchronous. */
+int ntvs_load_system(ntvs_ctx* ctx, const ntvs_system* sys);
+
+/* Set the NTVS parameters (Appendix C).  Validated: N >= 0, 0 < alpha < 1, beta0 >= 0,
+ * eps_tv >= 0, lambda finite, max_retries >= 1 when tv_check.  Default before the first
+ * call: lambda 1e-4, alpha 0.75, beta0 1, eps_tv 1e-8, N 0, no check, 64 retries, seed 0. */
+int ntvs_set_params(ntvs_ctx* ctx, const ntvs_params* p);
+
+/* Set the current image x (the initial iterate x-bar of Appendix A) from V values of
+ * `dtype` (NTVS_F64 or NTVS_F32) in host or device memory. */
+int ntvs_set_image(ntvs_ctx* ctx, const void* x, int dtype, int mem_kind);
+
+/* Copy the current image into V values of `dtype` (NTVS_F64 or NTVS_F32). */
+int ntvs_get_image(ntvs_ctx* ctx, void* out, int dtype, int mem_kind);
+
+/* Run k_iters cycles of NTVS from the current state (Appendix C): per cycle
+ * ell_k = rand(k, ell_{k-1}); N perturbation steps x <- x + beta0*alpha^ell v, ell++
+ * (with the check: retry with ell++ until phi(z) <= phi(x), at most max_retries tries,
+ * beta recomputed after every try); then x <- P_T(x); then phi(x) in FP64.
+ * Without the check the call only queues work; with it the host waits for each
+ * check decision. */
+int ntvs_run(ntvs_ctx* ctx, int k_iters);
+
+/* Wait for the context's stream. */
+int ntvs_sync(ntvs_ctx* ctx);
+
+/* phi(x) of the current image, FP64 reduction on the device (synchronous). */
+int ntvs_get_tv(ntvs_ctx* ctx, double* tv);
+
+/* Counters of the run so far (synchronous). */
+int ntvs_get_stats(ntvs_ctx* ctx, ntvs_stats* st);
+
+/* Per-block residual sums of squares sum_i (b_i - <a_i,x>)^2 (FP64, x before the block's
+ * update) of the last DROP sweep; out has room for `cap` >= n_blocks doubles. */
+int ntvs_get_block_resid(ntvs_ctx* ctx, double* out, int cap);
+
+/* Traces of the run so far: ell_k per cycle ([k] entries), and per perturbation step
+ * the tries and whether x changed ([k*N] entries).  *n receives the number written;
+ * any output pointer may be NULL. */
+int ntvs_get_trace(ntvs_ctx* ctx, int64_t* ell_k, int32_t* tries, int32_t* accepted,
+                   int64_t cap, int64_t* n_cycles);
+
+/* Checkpoint state besides the image: cycle counter k and ell_{k-1}.  Restoring
+ * (k, ell_prev) and the image resumes a run exactly where it stopped. */
+int ntvs_get_state(ntvs_ctx* ctx, int64_t* k, int64_t* ell_prev);
+int ntvs_set_state(ntvs_ctx* ctx, int64_t k, int64_t ell_prev);
+
+/* Turn per-launch event timing on (1) or off (0); turning it on clears the totals. */
+int ntvs_set_profiling(ntvs_ctx* ctx, int on);
+
+/* Totals of the launches timed since profiling was turned on (synchronizes the stream). */
+int ntvs_get_profile(ntvs_ctx* ctx, ntvs_profile* out);
+
+/* Test hook: replay ell_k for the next n cycles instead of drawing it (NULL clears). */
+int ntvs_set_ell_override(ntvs_ctx* ctx, const int64_t* ell_k, int64_t n);
+
+/* ---- single steps of the hot path (same kernels as ntvs_run) ---------------------- */
+
+/* g = grad phi_eps(x) of the current image into V values of `dtype` (NTVS_F64/F32);
+ * *gnorm (may be NULL) receives ||g||_2 from the FP64 device reduction.  Synchronous. */
+int ntvs_tv_gradient(ntvs_ctx* ctx, void* g_out, int dtype, int mem_kind, double* gnorm);
+
+/* One perturbation step without the check: x <- x - beta * g/||g|| (Appendix C). */
+int ntvs_perturb(ntvs_ctx* ctx, double beta);
+
+/* One try with the check: z = x - beta g/||g||; if phi(z) <= phi(x) then x <- z.
+ * *accepted receives 1 or 0; *phi_x / *phi_z (may be NULL) the FP64 values.  Synchronous. */
+int ntvs_perturb_checked(ntvs_ctx* ctx, double beta, int* accepted, double* phi_x, double* phi_z);
+
+/* One DROP block t in [0, B) on the current image (queued); its residual sum of squares
+ * is readable afterwards with ntvs_get_block_resid. */
+int ntvs_drop_block(ntvs_ctx* ctx, int t);
+
+/* One full DROP sweep P_T (blocks 0..B-1 in order). */
+int ntvs_drop_sweep(ntvs_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NTVS_H */

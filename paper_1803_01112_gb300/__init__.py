@@ -1,0 +1,343 @@
+"""NTVS proton-CT reconstruction on GB300 (sm_103a): Python binding of the C ABI.
+
+Total variation superiorization with N normalized TV perturbation steps of size
+beta0*alpha^ell interleaved with block-DROP feasibility-seeking sweeps, with or without
+the TV reduction check (arXiv 1803.01112, Sec. II-B, Appendix C).
+
+Every step of the computation runs in the CUDA kernels of ``libntvs.so``; this module
+only marshals arguments (numpy arrays = host memory, CUDA torch tensors = device
+memory).  The module-level ``ntvs_*`` functions carry the C names of include/ntvs.h;
+``Reconstructor`` is a small object wrapper over them.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+from . import _ffi
+from ._ffi import (NTVS_BF16, NTVS_CSR32, NTVS_DELTA16, NTVS_F16, NTVS_F32, NTVS_F64, NTVS_MEM_DEVICE,
+                   NTVS_MEM_HOST, NtvsError, check, lib)
+
+__all__ = ["Reconstructor", "NtvsError", "build", "lib", "NTVS_F64", "NTVS_F32", "NTVS_F16", "NTVS_BF16",
+           "NTVS_CSR32", "NTVS_DELTA16"]
+
+_NP_DT = {np.dtype(np.float64): NTVS_F64, np.dtype(np.float32): NTVS_F32, np.dtype(np.float16): NTVS_F16}
+
+
+def build(force: bool = False) -> str:
+    from . import _build
+    return _build.build(force=force)
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _dtype_code(a) -> int:
+    if _is_torch(a):
+        import torch
+        m = {torch.float64: NTVS_F64, torch.float32: NTVS_F32, torch.float16: NTVS_F16, torch.bfloat16: NTVS_BF16}
+        return m[a.dtype]
+    return _NP_DT[np.dtype(a.dtype)]
+
+
+def _ptr_kind(a, dtype=None):
+    """(pointer, mem_kind) of a contiguous numpy array (host) or CUDA torch tensor (device)."""
+    if a is None:
+        return None, NTVS_MEM_HOST
+    if _is_torch(a):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if dtype is not None and a.dtype != dtype[1]:
+            raise TypeError(f"expected {dtype[1]}, got {a.dtype}")
+        return a.data_ptr(), (NTVS_MEM_DEVICE if a.is_cuda else NTVS_MEM_HOST)
+    if not (a.flags["C_CONTIGUOUS"]):
+        raise ValueError("array must be C-contiguous")
+    if dtype is not None and np.dtype(a.dtype) != np.dtype(dtype[0]):
+        raise TypeError(f"expected {np.dtype(dtype[0])}, got {a.dtype}")
+    return a.ctypes.data, NTVS_MEM_HOST
+
+
+# ----------------------------------------------------------------- C-named functions
+def ntvs_version() -> str:
+    return lib().ntvs_version().decode()
+
+
+def ntvs_last_error() -> str:
+    return lib().ntvs_last_error().decode()
+
+
+def ntvs_create(device: int = 0, stream: Optional[int] = None) -> int:
+    h = ctypes.c_void_p()
+    check(lib().ntvs_create(ctypes.byref(h), device, stream), "ntvs_create")
+    return h.value
+
+
+def ntvs_destroy(ctx: int) -> None:
+    check(lib().ntvs_destroy(ctx), "ntvs_destroy")
+
+
+def ntvs_load_system(ctx: int, nx: int, ny: int, nz: int, row_ptr, col, val, b, n_blocks: int = 1,
+                     block_ptr=None, storage: int = NTVS_CSR32) -> None:
+    """Arrays are all numpy (host, copied) or all CUDA torch tensors (device, borrowed:
+    they must stay alive while the context uses them)."""
+    import_torch = _is_torch(row_ptr)
+    rp, kind = _ptr_kind(row_ptr)
+    cp, kc = _ptr_kind(col)
+    vptr, kv = _ptr_kind(val)
+    bptr, kb = _ptr_kind(b)
+    if len({kind, kc, kv, kb}) != 1:
+        raise ValueError("row_ptr, col, val and b must all be host arrays or all device tensors")
+    vdt = _dtype_code(val)
+    want_b = np.float64 if vdt == NTVS_F64 else np.float32
+    if import_torch:
+        import torch
+        for a, t, nm in ((row_ptr, torch.int64, "row_ptr"), (col, torch.int32, "col"),
+                         (b, torch.float64 if vdt == NTVS_F64 else torch.float32, "b")):
+            if a.dtype != t:
+                raise TypeError(f"{nm} must be {t}")
+    else:
+        for a, t, nm in ((row_ptr, np.int64, "row_ptr"), (col, np.int32, "col"), (b, want_b, "b")):
+            if np.dtype(a.dtype) != np.dtype(t):
+                raise TypeError(f"{nm} must be {np.dtype(t)}")
+    bp = None
+    if block_ptr is not None:
+        bp = np.ascontiguousarray(block_ptr, dtype=np.int64)
+        n_blocks = bp.size - 1
+    s = _ffi.ntvs_system(nx, ny, nz, n_blocks, (row_ptr.numel() if import_torch else row_ptr.size) - 1,
+                         rp, cp, vptr, bptr, None if bp is None else bp.ctypes.data, vdt, kind, storage, 0)
+    check(lib().ntvs_load_system(ctx, ctypes.byref(s)), "ntvs_load_system")
+
+
+def ntvs_set_params(ctx: int, lam: float, N: int, alpha: float, beta0: float = 1.0, tv_check: bool = False,
+                    seed: int = 0, eps_tv: float = 1e-8, max_retries: int = 64) -> None:
+    p = _ffi.ntvs_params(lam, alpha, beta0, eps_tv, N, int(bool(tv_check)), max_retries, 0, seed)
+    check(lib().ntvs_set_params(ctx, ctypes.byref(p)), "ntvs_set_params")
+
+
+def ntvs_set_image(ctx: int, x) -> None:
+    ptr, kind = _ptr_kind(x)
+    check(lib().ntvs_set_image(ctx, ptr, _dtype_code(x), kind), "ntvs_set_image")
+
+
+def ntvs_get_image(ctx: int, out) -> None:
+    ptr, kind = _ptr_kind(out)
+    check(lib().ntvs_get_image(ctx, ptr, _dtype_code(out), kind), "ntvs_get_image")
+
+
+def ntvs_run(ctx: int, k_iters: int) -> None:
+    check(lib().ntvs_run(ctx, k_iters), "ntvs_run")
+
+
+def ntvs_sync(ctx: int) -> None:
+    check(lib().ntvs_sync(ctx), "ntvs_sync")
+
+
+def ntvs_get_tv(ctx: int) -> float:
+    v = ctypes.c_double()
+    check(lib().ntvs_get_tv(ctx, ctypes.byref(v)), "ntvs_get_tv")
+    return v.value
+
+
+def ntvs_get_stats(ctx: int) -> dict:
+    st = _ffi.ntvs_stats()
+    check(lib().ntvs_get_stats(ctx, ctypes.byref(st)), "ntvs_get_stats")
+    return {f: getattr(st, f) for f, _ in _ffi.ntvs_stats._fields_}
+
+
+def ntvs_get_block_resid(ctx: int, n_blocks: int) -> np.ndarray:
+    out = np.zeros(max(n_blocks, 1), np.float64)
+    check(lib().ntvs_get_block_resid(ctx, out.ctypes.data, out.size), "ntvs_get_block_resid")
+    return out[:n_blocks]
+
+
+def ntvs_get_trace(ctx: int, cap: int = 1 << 16):
+    ell = np.zeros(cap, np.int64)
+    tries = np.zeros(cap, np.int32)
+    acc = np.zeros(cap, np.int32)
+    n = ctypes.c_int64()
+    check(lib().ntvs_get_trace(ctx, ell.ctypes.data, tries.ctypes.data, acc.ctypes.data, cap, ctypes.byref(n)),
+          "ntvs_get_trace")
+    return ell, tries, acc, n.value
+
+
+def ntvs_get_state(ctx: int):
+    k, e = ctypes.c_int64(), ctypes.c_int64()
+    check(lib().ntvs_get_state(ctx, ctypes.byref(k), ctypes.byref(e)), "ntvs_get_state")
+    return k.value, e.value
+
+
+def ntvs_set_state(ctx: int, k: int, ell_prev: int) -> None:
+    check(lib().ntvs_set_state(ctx, k, ell_prev), "ntvs_set_state")
+
+
+def ntvs_set_profiling(ctx: int, on: bool) -> None:
+    check(lib().ntvs_set_profiling(ctx, int(bool(on))), "ntvs_set_profiling")
+
+
+def ntvs_get_profile(ctx: int) -> dict:
+    pr = _ffi.ntvs_profile()
+    check(lib().ntvs_get_profile(ctx, ctypes.byref(pr)), "ntvs_get_profile")
+    return {f: getattr(pr, f) for f, _ in _ffi.ntvs_profile._fields_}
+
+
+def ntvs_set_ell_override(ctx: int, ell) -> None:
+    if ell is None:
+        check(lib().ntvs_set_ell_override(ctx, None, 0), "ntvs_set_ell_override")
+        return
+    a = np.ascontiguousarray(ell, np.int64)
+    check(lib().ntvs_set_ell_override(ctx, a.ctypes.data, a.size), "ntvs_set_ell_override")
+
+
+def ntvs_tv_gradient(ctx: int, out=None):
+    gn = ctypes.c_double()
+    if out is None:
+        check(lib().ntvs_tv_gradient(ctx, None, NTVS_F64, NTVS_MEM_HOST, ctypes.byref(gn)), "ntvs_tv_gradient")
+    else:
+        ptr, kind = _ptr_kind(out)
+        check(lib().ntvs_tv_gradient(ctx, ptr, _dtype_code(out), kind, ctypes.byref(gn)), "ntvs_tv_gradient")
+    return gn.value
+
+
+def ntvs_perturb(ctx: int, beta: float) -> None:
+    check(lib().ntvs_perturb(ctx, beta), "ntvs_perturb")
+
+
+def ntvs_perturb_checked(ctx: int, beta: float):
+    a, px, pz = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+    check(lib().ntvs_perturb_checked(ctx, beta, ctypes.byref(a), ctypes.byref(px), ctypes.byref(pz)),
+          "ntvs_perturb_checked")
+    return bool(a.value), px.value, pz.value
+
+
+def ntvs_drop_block(ctx: int, t: int) -> None:
+    check(lib().ntvs_drop_block(ctx, t), "ntvs_drop_block")
+
+
+def ntvs_drop_sweep(ctx: int) -> None:
+    check(lib().ntvs_drop_sweep(ctx), "ntvs_drop_sweep")
+
+
+# ----------------------------------------------------------------- object wrapper
+@dataclass
+class Params:
+    lam: float = 1e-4
+    N: int = 0
+    alpha: float = 0.75
+    beta0: float = 1.0
+    tv_check: bool = False
+    seed: int = 0
+    eps_tv: float = 1e-8
+    max_retries: int = 64
+
+
+class Reconstructor:
+    """One reconstruction context on one GPU (see include/ntvs.h for the semantics)."""
+
+    def __init__(self, device: int = 0, stream: Optional[int] = None):
+        self._ctx = ntvs_create(device, stream)
+        self._keep = ()
+        self.shape = None
+        self.n_blocks = 0
+
+    @property
+    def handle(self) -> int:
+        return self._ctx
+
+    def close(self) -> None:
+        if self._ctx:
+            ntvs_destroy(self._ctx)
+            self._ctx = None
+            self._keep = ()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, shape, row_ptr, col, val, b, n_blocks: int = 1, block_ptr=None, storage: int = NTVS_CSR32):
+        nx, ny, nz = shape
+        ntvs_load_system(self._ctx, nx, ny, nz, row_ptr, col, val, b, n_blocks, block_ptr, storage)
+        self._keep = (row_ptr, col, val, b) if _is_torch(row_ptr) and row_ptr.is_cuda else ()
+        self.shape = (nx, ny, nz)
+        self.n_blocks = (len(block_ptr) - 1) if block_ptr is not None else n_blocks
+        return self
+
+    def set_params(self, p: Params = None, **kw):
+        p = p or Params(**kw)
+        ntvs_set_params(self._ctx, p.lam, p.N, p.alpha, p.beta0, p.tv_check, p.seed, p.eps_tv, p.max_retries)
+        return self
+
+    def set_image(self, x):
+        ntvs_set_image(self._ctx, x)
+        return self
+
+    def get_image(self, dtype=np.float64) -> np.ndarray:
+        out = np.empty(int(np.prod(self.shape)), dtype)
+        ntvs_get_image(self._ctx, out)
+        return out
+
+    def run(self, k: int):
+        ntvs_run(self._ctx, k)
+        return self
+
+    def sync(self):
+        ntvs_sync(self._ctx)
+        return self
+
+    def tv(self) -> float:
+        return ntvs_get_tv(self._ctx)
+
+    def stats(self) -> dict:
+        return ntvs_get_stats(self._ctx)
+
+    def block_resid(self) -> np.ndarray:
+        return ntvs_get_block_resid(self._ctx, self.n_blocks)
+
+    def trace(self):
+        ell, tries, acc, n = ntvs_get_trace(self._ctx)
+        st = self.stats()
+        ns = st["n_steps"]
+        return ell[:n].copy(), tries[:ns].copy(), acc[:ns].copy()
+
+    def state(self):
+        return ntvs_get_state(self._ctx)
+
+    def set_state(self, k: int, ell_prev: int):
+        ntvs_set_state(self._ctx, k, ell_prev)
+        return self
+
+    def set_profiling(self, on: bool = True):
+        ntvs_set_profiling(self._ctx, on)
+        return self
+
+    def profile(self) -> dict:
+        return ntvs_get_profile(self._ctx)
+
+    def set_ell_override(self, ell):
+        ntvs_set_ell_override(self._ctx, ell)
+        return self
+
+    def tv_gradient(self, dtype=np.float64):
+        out = np.empty(int(np.prod(self.shape)), dtype)
+        gn = ntvs_tv_gradient(self._ctx, out)
+        return out, gn
+
+    def perturb(self, beta: float):
+        ntvs_perturb(self._ctx, beta)
+        return self
+
+    def perturb_checked(self, beta: float):
+        return ntvs_perturb_checked(self._ctx, beta)
+
+    def drop_block(self, t: int):
+        ntvs_drop_block(self._ctx, t)
+        return self
+
+    def drop_sweep(self):
+        ntvs_drop_sweep(self._ctx)
+        return self

@@ -1,0 +1,119 @@
+"""ctypes declarations of the C ABI in include/ntvs.h (argument marshalling only).
+
+Every function of the header is bound here under its C name.  The library is the
+in-tree ``libntvs.so`` built by ``paper_1803_01112_gb300._build``; importing this module
+fails loudly when it is missing -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libntvs.so")
+
+NTVS_OK = 0
+NTVS_ERR_ARG = -1
+NTVS_ERR_CSR = -2
+NTVS_ERR_OOM = -3
+NTVS_ERR_CUDA = -4
+NTVS_ERR_TIMEOUT = -5
+NTVS_ERR_STATE = -6
+
+NTVS_F64, NTVS_F32, NTVS_F16, NTVS_BF16 = 0, 1, 2, 3
+NTVS_MEM_HOST, NTVS_MEM_DEVICE = 0, 1
+NTVS_CSR32, NTVS_DELTA16 = 0, 1
+
+ERROR_NAMES = {NTVS_ERR_ARG: "NTVS_ERR_ARG", NTVS_ERR_CSR: "NTVS_ERR_CSR", NTVS_ERR_OOM: "NTVS_ERR_OOM",
+               NTVS_ERR_CUDA: "NTVS_ERR_CUDA", NTVS_ERR_TIMEOUT: "NTVS_ERR_TIMEOUT",
+               NTVS_ERR_STATE: "NTVS_ERR_STATE"}
+
+
+class ntvs_system(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("n_blocks", ctypes.c_int32), ("n_rows", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p),
+                ("b", ctypes.c_void_p), ("block_ptr", ctypes.c_void_p),
+                ("val_dtype", ctypes.c_int32), ("mem_kind", ctypes.c_int32),
+                ("storage", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class ntvs_params(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("alpha", ctypes.c_double), ("beta0", ctypes.c_double),
+                ("eps_tv", ctypes.c_double), ("N", ctypes.c_int32), ("tv_check", ctypes.c_int32),
+                ("max_retries", ctypes.c_int32), ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class ntvs_stats(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int64), ("ell_prev", ctypes.c_int64), ("n_steps", ctypes.c_int64),
+                ("n_accepted", ctypes.c_int64), ("n_tries", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("n_rows", ctypes.c_int64), ("n_blocks", ctypes.c_int32), ("compute_dtype", ctypes.c_int32),
+                ("last_tv", ctypes.c_double), ("n_launches", ctypes.c_int64)]
+
+
+class ntvs_profile(ctypes.Structure):
+    _fields_ = [("drop_block_ms", ctypes.c_double), ("drop_block_launches", ctypes.c_int64),
+                ("drop_apply_ms", ctypes.c_double), ("drop_apply_launches", ctypes.c_int64),
+                ("tv_ms", ctypes.c_double), ("tv_launches", ctypes.c_int64)]
+
+
+vp, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+P = ctypes.POINTER
+
+# name -> (restype, argtypes); the list is the whole header
+SIGNATURES = {
+    "ntvs_version": (ctypes.c_char_p, []),
+    "ntvs_last_error": (ctypes.c_char_p, []),
+    "ntvs_create": (ctypes.c_int, [P(vp), ctypes.c_int, vp]),
+    "ntvs_destroy": (ctypes.c_int, [vp]),
+    "ntvs_load_system": (ctypes.c_int, [vp, P(ntvs_system)]),
+    "ntvs_set_params": (ctypes.c_int, [vp, P(ntvs_params)]),
+    "ntvs_set_image": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int]),
+    "ntvs_get_image": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int]),
+    "ntvs_run": (ctypes.c_int, [vp, ctypes.c_int]),
+    "ntvs_sync": (ctypes.c_int, [vp]),
+    "ntvs_get_tv": (ctypes.c_int, [vp, P(d)]),
+    "ntvs_get_stats": (ctypes.c_int, [vp, P(ntvs_stats)]),
+    "ntvs_get_block_resid": (ctypes.c_int, [vp, vp, ctypes.c_int]),
+    "ntvs_get_trace": (ctypes.c_int, [vp, vp, vp, vp, i64, P(i64)]),
+    "ntvs_get_state": (ctypes.c_int, [vp, P(i64), P(i64)]),
+    "ntvs_set_state": (ctypes.c_int, [vp, i64, i64]),
+    "ntvs_set_ell_override": (ctypes.c_int, [vp, vp, i64]),
+    "ntvs_set_profiling": (ctypes.c_int, [vp, ctypes.c_int]),
+    "ntvs_get_profile": (ctypes.c_int, [vp, P(ntvs_profile)]),
+    "ntvs_tv_gradient": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P(d)]),
+    "ntvs_perturb": (ctypes.c_int, [vp, d]),
+    "ntvs_perturb_checked": (ctypes.c_int, [vp, d, P(ctypes.c_int), P(d), P(d)]),
+    "ntvs_drop_block": (ctypes.c_int, [vp, ctypes.c_int]),
+    "ntvs_drop_sweep": (ctypes.c_int, [vp]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'` (no CPU fallback exists)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class NtvsError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = lib().ntvs_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def check(code: int, where: str) -> None:
+    if code != NTVS_OK:
+        raise NtvsError(code, where)

@@ -1,0 +1,81 @@
+// Device helpers shared by the kernel translation units.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ntvs_internal.h"
+
+namespace ntvs {
+
+template <typename T> struct StorageOf;
+__device__ __forceinline__ float to_compute(float v) { return v; }
+__device__ __forceinline__ double to_compute(double v) { return v; }
+__device__ __forceinline__ float to_compute(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_compute(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// fused x - s*g, spelled out so every kernel that forms a perturbed voxel rounds alike
+__device__ __forceinline__ float perturbed(float x, float s, float g) { return __fmaf_rn(-s, g, x); }
+__device__ __forceinline__ double perturbed(double x, double s, double g) { return __fma_rn(-s, g, x); }
+
+template <typename T>
+__device__ __forceinline__ T step_scale(double beta, const double* gnorm2) {
+    double n2 = *gnorm2;
+    return (n2 > 0.0) ? (T)(beta / sqrt(n2)) : (T)0;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum of v over the CTA (blockDim.x multiple of 32, <= 1024); result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* sh /* >= 32 */) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        r = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+        r = warp_sum(r);
+    }
+    return r;
+}
+
+// Deterministic grid reduction of NV values per CTA: CTA b writes partials[q*grid + b];
+// the last CTA to finish sums each q in a fixed order into out[q] and resets the ticket.
+// Returns true in the last CTA (all threads), after out[] is written.
+template <int NV>
+__device__ __forceinline__ bool grid_reduce(const double (&v)[NV], double* partials, unsigned* ticket,
+                                            double* const (&out)[NV]) {
+    __shared__ double sh[32];
+    __shared__ bool last;
+    double tot[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) tot[q] = block_sum(v[q], sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) partials[q * gridDim.x + blockIdx.x] = tot[q];
+        __threadfence();
+        unsigned t = atomicAdd(ticket, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double a = 0.0;
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) a += __ldcg(&partials[q * gridDim.x + i]);
+        a = block_sum(a, sh);
+        if (threadIdx.x == 0 && out[q]) *out[q] = a;
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
+    return true;
+}
+
+}  // namespace ntvs

@@ -1,0 +1,152 @@
+// Load-time preparation of the system (runs once per ntvs_load_system, outside the
+// iteration): validation, FP64 row norms ||a_i||^2 of the stored values, and the
+// per-block hit counts s_j^t of the block-DROP weights (Sec. II-D, DROP of ref. CEHN08).
+#include "common.cuh"
+
+namespace ntvs {
+
+template <typename V> __device__ __forceinline__ double as_f64(V v) { return (double)to_compute(v); }
+
+__global__ void validate_rows_kernel(const int64_t* __restrict__ row_ptr, int64_t M, int* flags) {
+    int f = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x)
+        if (row_ptr[i] > row_ptr[i + 1]) f |= 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && row_ptr[0] != 0) f |= 2;
+    if (f) atomicOr(flags, f);
+}
+
+template <typename V>
+__global__ void validate_entries_kernel(const int32_t* __restrict__ col, const V* __restrict__ val, int64_t nnz,
+                                        int64_t nvox, int* flags) {
+    int f = 0;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = col[p];
+        if (c < 0 || (int64_t)c >= nvox) f |= 4;
+        if (!isfinite(as_f64(val[p]))) f |= 8;
+    }
+    if (f) atomicOr(flags, f);
+}
+
+template <typename B>
+__global__ void validate_rhs_kernel(const B* __restrict__ b, int64_t M, int* flags) {
+    int f = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite((double)b[i])) f |= 16;
+    if (f) atomicOr(flags, f);
+}
+
+// warp per row: inv_norm2[i] = 1 / sum a^2 (FP64), 0 for a zero row
+template <typename V, typename T>
+__global__ void row_inv_norm2_kernel(const int64_t* __restrict__ row_ptr, const V* __restrict__ val, int64_t M,
+                                     T* __restrict__ inv_norm2) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w0; i < M; i += nw) {
+        double s = 0.0;
+        for (int64_t p = row_ptr[i] + lane; p < row_ptr[i + 1]; p += 32) {
+            const double a = as_f64(val[p]);
+            s += a * a;
+        }
+        s = warp_sum(s);
+        if (lane == 0) inv_norm2[i] = (s > 0.0) ? (T)(1.0 / s) : (T)0;
+    }
+}
+
+template <typename V>
+__global__ void hit_counts_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                  const V* __restrict__ val, int64_t r0, int64_t r1, int32_t* __restrict__ cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = r0 + w0; i < r1; i += nw)
+        for (int64_t p = row_ptr[i] + lane; p < row_ptr[i + 1]; p += 32)
+            if (as_f64(val[p]) != 0.0) atomicAdd(cnt + col[p], 1);
+}
+
+template <typename T>
+__global__ void inv_counts_kernel(const int32_t* __restrict__ cnt, T* __restrict__ inv_s, int64_t n) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = cnt[j];
+        inv_s[j] = c > 0 ? (T)(1.0 / (double)c) : (T)0;
+    }
+}
+
+static int prep_grid() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return (sms > 0 ? sms : 1) * 8;
+}
+
+cudaError_t k_validate_rows(const int64_t* row_ptr, int64_t M, int* flags, cudaStream_t s) {
+    validate_rows_kernel<<<prep_grid(), 256, 0, s>>>(row_ptr, M, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t k_validate_entries(const int32_t* col, const void* val, int vdt, int64_t nnz, int64_t V, int* flags,
+                               cudaStream_t s) {
+    if (nnz <= 0) return cudaSuccess;
+    const int g = prep_grid();
+    switch (vdt) {
+        case F64: validate_entries_kernel<double><<<g, 256, 0, s>>>(col, (const double*)val, nnz, V, flags); break;
+        case F32: validate_entries_kernel<float><<<g, 256, 0, s>>>(col, (const float*)val, nnz, V, flags); break;
+        case F16: validate_entries_kernel<__half><<<g, 256, 0, s>>>(col, (const __half*)val, nnz, V, flags); break;
+        case BF16:
+            validate_entries_kernel<__nv_bfloat16><<<g, 256, 0, s>>>(col, (const __nv_bfloat16*)val, nnz, V, flags);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t k_validate_rhs(const void* b, int bdt, int64_t M, int* flags, cudaStream_t s) {
+    if (M <= 0) return cudaSuccess;
+    if (bdt == F64) validate_rhs_kernel<double><<<prep_grid(), 256, 0, s>>>((const double*)b, M, flags);
+    else validate_rhs_kernel<float><<<prep_grid(), 256, 0, s>>>((const float*)b, M, flags);
+    return cudaGetLastError();
+}
+
+template <typename V>
+static void launch_norm(const int64_t* rp, const V* val, int64_t M, void* out, int cdt, cudaStream_t s) {
+    if (cdt == F64) row_inv_norm2_kernel<V, double><<<prep_grid(), 256, 0, s>>>(rp, val, M, (double*)out);
+    else row_inv_norm2_kernel<V, float><<<prep_grid(), 256, 0, s>>>(rp, val, M, (float*)out);
+}
+
+cudaError_t k_row_inv_norm2(const int64_t* row_ptr, const void* val, int vdt, int64_t M, void* inv_norm2, int cdt,
+                            cudaStream_t s) {
+    if (M <= 0) return cudaSuccess;
+    switch (vdt) {
+        case F64: launch_norm(row_ptr, (const double*)val, M, inv_norm2, cdt, s); break;
+        case F32: launch_norm(row_ptr, (const float*)val, M, inv_norm2, cdt, s); break;
+        case F16: launch_norm(row_ptr, (const __half*)val, M, inv_norm2, cdt, s); break;
+        case BF16: launch_norm(row_ptr, (const __nv_bfloat16*)val, M, inv_norm2, cdt, s); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t k_hit_counts(const int64_t* row_ptr, const int32_t* col, const void* val, int vdt, int64_t r0, int64_t r1,
+                         int32_t* cnt, cudaStream_t s) {
+    if (r1 <= r0) return cudaSuccess;
+    const int g = prep_grid();
+    switch (vdt) {
+        case F64: hit_counts_kernel<double><<<g, 256, 0, s>>>(row_ptr, col, (const double*)val, r0, r1, cnt); break;
+        case F32: hit_counts_kernel<float><<<g, 256, 0, s>>>(row_ptr, col, (const float*)val, r0, r1, cnt); break;
+        case F16: hit_counts_kernel<__half><<<g, 256, 0, s>>>(row_ptr, col, (const __half*)val, r0, r1, cnt); break;
+        case BF16:
+            hit_counts_kernel<__nv_bfloat16><<<g, 256, 0, s>>>(row_ptr, col, (const __nv_bfloat16*)val, r0, r1, cnt);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t k_inv_counts(const int32_t* cnt, void* inv_s, int cdt, int64_t n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (cdt == F64) inv_counts_kernel<double><<<prep_grid(), 256, 0, s>>>(cnt, (double*)inv_s, n);
+    else inv_counts_kernel<float><<<prep_grid(), 256, 0, s>>>(cnt, (float*)inv_s, n);
+    return cudaGetLastError();
+}
+
+}  // namespace ntvs

@@ -1,0 +1,796 @@
+// Host runtime and C ABI of the NTVS library (declared in include/ntvs.h).
+//
+// The outer loop of NTVS (arXiv 1803.01112, Appendix C) runs here on the host: it
+// draws ell_k = rand(k, ell_{k-1}) (Sec. II-B item 4), forms beta = beta0 * alpha^ell
+// (Appendix A) and queues the kernels of one cycle on the context's stream: N TV
+// perturbation steps, then one block-DROP sweep P_T (Sec. II-D), then phi(x) in FP64.
+// Without the TV check nothing waits on the device; with it the host reads each
+// accept decision (one small device-to-host copy per try).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ntvs.h"
+#include "ntvs_internal.h"
+
+using namespace ntvs;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+std::string cuda_msg(const char* what, cudaError_t e) { return std::string(what) + ": " + cudaGetErrorString(e); }
+
+#define CUDA_TRY(expr)                                                                                      \
+    do {                                                                                                    \
+        cudaError_t e_ = (expr);                                                                            \
+        if (e_ != cudaSuccess)                                                                              \
+            return fail(e_ == cudaErrorMemoryAllocation ? NTVS_ERR_OOM : NTVS_ERR_CUDA, cuda_msg(#expr, e_)); \
+    } while (0)
+
+#define TRY(expr)                   \
+    do {                            \
+        int r_ = (expr);            \
+        if (r_ != NTVS_OK) return r_; \
+    } while (0)
+
+// SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) in counter form: output n of stream seed.
+uint64_t splitmix64_at(uint64_t seed, uint64_t n) {
+    uint64_t z = seed + (n + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// ell_k = rand(k, ell_{k-1}): uniform integer between the two (inclusive), draw k of the stream.
+int64_t draw_ell(uint64_t seed, int64_t k, int64_t ell_prev) {
+    const int64_t lo = k < ell_prev ? k : ell_prev, hi = k < ell_prev ? ell_prev : k;
+    const uint64_t span = (uint64_t)(hi - lo) + 1u;
+    return lo + (int64_t)(splitmix64_at(seed, (uint64_t)k) % span);
+}
+
+template <typename T>
+int dev_alloc(T** p, size_t bytes, const char* what) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? NTVS_ERR_OOM : NTVS_ERR_CUDA,
+                    std::string("device allocation of ") + what + " (" + std::to_string(bytes) + " bytes): " +
+                        cudaGetErrorString(e));
+    }
+    return NTVS_OK;
+}
+
+template <typename T>
+void dev_free(T*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+}  // namespace
+
+struct ntvs_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int sms = 1;
+
+    // system
+    bool loaded = false;
+    int nx = 0, ny = 0, nz = 0;
+    int64_t V = 0, M = 0, nnz = 0;
+    int B = 0;
+    int vdt = F32, cdt = F32, storage = NTVS_CSR32;
+    std::vector<int64_t> block_ptr;
+    int64_t* row_ptr = nullptr;
+    int32_t* col = nullptr;
+    void* val = nullptr;
+    void* b = nullptr;
+    bool own_row_ptr = false, own_col = false, own_val = false, own_b = false;
+    void* inv_norm2 = nullptr;
+    void* inv_s = nullptr;
+    int lpr = 32;
+    int drop_grid = 1;
+
+    // image and scratch
+    void* x = nullptr;
+    void* delta = nullptr;
+    void* g = nullptr;
+    RedScratch red{nullptr, nullptr, 1};
+    double* dscal = nullptr;   // [0] ||g||^2, [1] phi(x), [2] phi(z), [3] phi for ntvs_get_tv
+    int* daccept = nullptr;
+    int* dflags = nullptr;
+    double* resid = nullptr;   // [B]
+    double* tvhist = nullptr;  // [tvcap]
+    int64_t tvcap = 0;
+    double* hscal = nullptr;   // pinned [8]
+    int* hint = nullptr;       // pinned [4]
+
+    // parameters and state
+    ntvs_params p{};
+    int64_t k = 0, ell_prev = 0;
+    std::vector<int64_t> ell_trace;
+    std::vector<int32_t> tries_trace, acc_trace;
+    std::vector<int64_t> override_ell;
+    size_t override_pos = 0;
+    int64_t n_steps = 0, n_accepted = 0, n_tries = 0;
+    int64_t n_launches = 0;
+
+    // per-launch event timing (profiling on): pairs recorded around each launch
+    bool profiling = false;
+    struct Timed { int kind; cudaEvent_t a, b; };
+    std::vector<Timed> timed;
+    std::vector<cudaEvent_t> event_pool;
+    double prof_ms[3] = {0, 0, 0};
+    int64_t prof_n[3] = {0, 0, 0};
+
+    size_t csz() const { return dt_size(cdt); }
+
+    void free_system() {
+        if (own_row_ptr) dev_free(row_ptr);
+        if (own_col) dev_free(col);
+        if (own_val) dev_free(val);
+        if (own_b) dev_free(b);
+        row_ptr = nullptr; col = nullptr; val = nullptr; b = nullptr;
+        own_row_ptr = own_col = own_val = own_b = false;
+        dev_free(inv_norm2);
+        dev_free(inv_s);
+        dev_free(x);
+        dev_free(delta);
+        dev_free(g);
+        dev_free(resid);
+        loaded = false;
+    }
+};
+
+namespace {
+
+int use_device(ntvs_ctx* c) {
+    if (!c) return fail(NTVS_ERR_ARG, "null context");
+    CUDA_TRY(cudaSetDevice(c->device));
+    return NTVS_OK;
+}
+
+int need_system(ntvs_ctx* c) {
+    if (!c->loaded) return fail(NTVS_ERR_STATE, "no system loaded");
+    return NTVS_OK;
+}
+
+enum { KIND_DROP = 0, KIND_APPLY = 1, KIND_TV = 2 };
+
+cudaEvent_t take_event(ntvs_ctx* c) {
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Folds finished timings into the totals (after a stream sync).
+void harvest_timing(ntvs_ctx* c) {
+    for (auto& t : c->timed) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+            c->prof_ms[t.kind] += ms;
+            c->prof_n[t.kind] += 1;
+        }
+        c->event_pool.push_back(t.a);
+        c->event_pool.push_back(t.b);
+    }
+    c->timed.clear();
+}
+
+// Runs launch() on the context's stream, counted and (when profiling) bracketed by events.
+template <typename F>
+cudaError_t timed_launch(ntvs_ctx* c, int kind, F launch) {
+    c->n_launches += 1;
+    if (!c->profiling) return launch();
+    if (c->timed.size() > 4096) {   // bound the outstanding events
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return e;
+        harvest_timing(c);
+    }
+    cudaEvent_t a = take_event(c), b = take_event(c);
+    cudaEventRecord(a, c->stream);
+    cudaError_t e = launch();
+    cudaEventRecord(b, c->stream);
+    c->timed.push_back({kind, a, b});
+    return e;
+}
+
+int copy_in(void** dst, bool* own, const void* src, size_t bytes, int mem_kind, cudaStream_t s, const char* what) {
+    if (mem_kind == NTVS_MEM_DEVICE) {
+        *dst = const_cast<void*>(src);
+        *own = false;
+        return NTVS_OK;
+    }
+    TRY(dev_alloc(dst, bytes, what));
+    *own = true;
+    if (bytes) CUDA_TRY(cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, s));
+    return NTVS_OK;
+}
+
+int ensure_tvhist(ntvs_ctx* c, int64_t need) {
+    if (need <= c->tvcap) return NTVS_OK;
+    int64_t cap = c->tvcap ? c->tvcap : 1024;
+    while (cap < need) cap *= 2;
+    double* nb = nullptr;
+    TRY(dev_alloc(&nb, (size_t)cap * sizeof(double), "tv history"));
+    if (c->tvhist) {
+        CUDA_TRY(cudaMemcpyAsync(nb, c->tvhist, (size_t)c->tvcap * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        dev_free(c->tvhist);
+    }
+    c->tvhist = nb;
+    c->tvcap = cap;
+    return NTVS_OK;
+}
+
+// ---- one TV perturbation step (Appendix C inner loop) --------------------------------
+int launch_grad(ntvs_ctx* c, bool with_phi) {
+    CUDA_TRY(timed_launch(c, KIND_TV, [&] {
+        return k_tv_grad(c->cdt, c->x, c->g, c->nx, c->ny, c->nz, c->p.eps_tv, c->red, c->dscal + 0,
+                         with_phi ? c->dscal + 1 : nullptr, c->stream);
+    }));
+    return NTVS_OK;
+}
+
+// one check-mode try with step beta: returns accept in *acc (host), x updated when accepted
+int checked_try(ntvs_ctx* c, double beta, int* acc) {
+    CUDA_TRY(timed_launch(c, KIND_TV, [&] {
+        return k_tv_value(c->cdt, c->x, c->g, c->dscal + 0, beta, c->nx, c->ny, c->nz, c->red, c->dscal + 2,
+                          c->dscal + 1, c->daccept, c->stream);
+    }));
+    CUDA_TRY(timed_launch(c, KIND_TV, [&] {
+        return k_tv_apply(c->cdt, c->x, c->g, c->dscal + 0, beta, c->daccept, c->V, c->stream);
+    }));
+    CUDA_TRY(cudaMemcpyAsync(c->hint, c->daccept, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    *acc = c->hint[0];
+    return NTVS_OK;
+}
+
+int perturb_steps(ntvs_ctx* c, int64_t* ell_io) {
+    int64_t ell = *ell_io;
+    const int N = c->p.N;
+    for (int n = 0; n < N; ++n) {
+        double beta = c->p.beta0 * std::pow(c->p.alpha, (double)ell);
+        int tries = 0, acc = 0;
+        if (!c->p.tv_check) {
+            TRY(launch_grad(c, false));
+            CUDA_TRY(timed_launch(c, KIND_TV, [&] {
+                return k_tv_apply(c->cdt, c->x, c->g, c->dscal + 0, beta, nullptr, c->V, c->stream);
+            }));
+            ell += 1;
+            tries = 1;
+            acc = 1;
+        } else {
+            TRY(launch_grad(c, true));
+            for (;;) {
+                int a = 0;
+                TRY(checked_try(c, beta, &a));
+                ell += 1;
+                tries += 1;
+                if (a) { acc = 1; break; }
+                if (tries >= c->p.max_retries) break;
+                beta = c->p.beta0 * std::pow(c->p.alpha, (double)ell);
+            }
+        }
+        c->tries_trace.push_back(tries);
+        c->acc_trace.push_back(acc);
+        c->n_steps += 1;
+        c->n_tries += tries;
+        c->n_accepted += acc;
+    }
+    *ell_io = ell;
+    return NTVS_OK;
+}
+
+// ---- block-DROP ------------------------------------------------------------------------
+int drop_block(ntvs_ctx* c, int t) {
+    const int64_t r0 = c->block_ptr[t], r1 = c->block_ptr[t + 1];
+    CUDA_TRY(cudaMemsetAsync(c->resid + t, 0, sizeof(double), c->stream));
+    if (r1 <= r0) return NTVS_OK;
+    DropArgs a;
+    a.row_ptr = c->row_ptr;
+    a.col = c->col;
+    a.val = c->val;
+    a.b = c->b;
+    a.inv_norm2 = c->inv_norm2;
+    a.r0 = r0;
+    a.r1 = r1;
+    a.x = c->x;
+    a.delta = c->delta;
+    a.lambda = c->p.lambda;
+    a.resid_ss = c->resid + t;
+    a.vdt = c->vdt;
+    a.cdt = c->cdt;
+    a.lanes_per_row = c->lpr;
+    a.grid = c->drop_grid;
+    CUDA_TRY(timed_launch(c, KIND_DROP, [&] { return k_drop_block(a, c->stream); }));
+    CUDA_TRY(timed_launch(c, KIND_APPLY, [&] {
+        return k_drop_apply(c->cdt, c->x, c->delta, (const char*)c->inv_s + (size_t)t * c->V * c->csz(), c->V,
+                            c->stream);
+    }));
+    return NTVS_OK;
+}
+
+int drop_sweep(ntvs_ctx* c) {
+    for (int t = 0; t < c->B; ++t) TRY(drop_block(c, t));
+    return NTVS_OK;
+}
+
+int copy_image_out(ntvs_ctx* c, const void* src, void* out, int dtype, int mem_kind) {
+    if (dtype != NTVS_F64 && dtype != NTVS_F32) return fail(NTVS_ERR_ARG, "image dtype must be NTVS_F64 or NTVS_F32");
+    if (!out && c->V) return fail(NTVS_ERR_ARG, "null output");
+    if (mem_kind == NTVS_MEM_DEVICE) {
+        CUDA_TRY(k_convert(src, c->cdt, out, dtype, c->V, c->stream));
+        return NTVS_OK;
+    }
+    if (mem_kind != NTVS_MEM_HOST) return fail(NTVS_ERR_ARG, "bad mem_kind");
+    if (dtype == c->cdt) {
+        CUDA_TRY(cudaMemcpyAsync(out, src, (size_t)c->V * c->csz(), cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        return NTVS_OK;
+    }
+    std::vector<unsigned char> tmp((size_t)c->V * c->csz());
+    CUDA_TRY(cudaMemcpyAsync(tmp.data(), src, tmp.size(), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (c->cdt == NTVS_F64) {
+        const double* s = (const double*)tmp.data();
+        float* d = (float*)out;
+        for (int64_t j = 0; j < c->V; ++j) d[j] = (float)s[j];
+    } else {
+        const float* s = (const float*)tmp.data();
+        double* d = (double*)out;
+        for (int64_t j = 0; j < c->V; ++j) d[j] = (double)s[j];
+    }
+    return NTVS_OK;
+}
+
+}  // namespace
+
+// =========================================================================== C ABI
+extern "C" {
+
+const char* ntvs_version(void) { return "ntvs-gb300 0.1 (sm_103a)"; }
+
+const char* ntvs_last_error(void) { return g_err.c_str(); }
+
+int ntvs_create(ntvs_ctx** out, int device, void* cuda_stream) {
+    if (!out) return fail(NTVS_ERR_ARG, "null output pointer");
+    *out = nullptr;
+    int ndev = 0;
+    CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(NTVS_ERR_ARG, "device index out of range");
+    CUDA_TRY(cudaSetDevice(device));
+    ntvs_ctx* c = new ntvs_ctx();
+    c->device = device;
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+    if (c->sms < 1) c->sms = 1;
+    int rc = NTVS_OK;
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete c; return fail(NTVS_ERR_CUDA, cuda_msg("cudaStreamCreate", e)); }
+        c->own_stream = true;
+    }
+    const int maxgrid = c->sms * 8;
+    c->red.grid = 1;
+    if ((rc = dev_alloc(&c->red.partials, sizeof(double) * 2 * (size_t)maxgrid, "reduction partials")) ||
+        (rc = dev_alloc(&c->red.ticket, sizeof(unsigned), "reduction ticket")) ||
+        (rc = dev_alloc(&c->dscal, sizeof(double) * 8, "scalars")) ||
+        (rc = dev_alloc(&c->daccept, sizeof(int) * 4, "accept flag")) ||
+        (rc = dev_alloc(&c->dflags, sizeof(int) * 4, "flags"))) {
+        ntvs_destroy(c);
+        return rc;
+    }
+    cudaError_t e1 = cudaMemsetAsync(c->red.ticket, 0, sizeof(unsigned), c->stream);
+    cudaError_t e2 = cudaMemsetAsync(c->dscal, 0, sizeof(double) * 8, c->stream);
+    cudaError_t e3 = cudaHostAlloc((void**)&c->hscal, sizeof(double) * 8, cudaHostAllocDefault);
+    cudaError_t e4 = cudaHostAlloc((void**)&c->hint, sizeof(int) * 4, cudaHostAllocDefault);
+    cudaError_t e5 = cudaStreamSynchronize(c->stream);
+    if (e1 || e2 || e3 || e4 || e5) {
+        ntvs_destroy(c);
+        return fail(NTVS_ERR_CUDA, "context set-up failed");
+    }
+    c->p.lambda = 1e-4;
+    c->p.alpha = 0.75;
+    c->p.beta0 = 1.0;
+    c->p.eps_tv = 1e-8;
+    c->p.N = 0;
+    c->p.tv_check = 0;
+    c->p.max_retries = 64;
+    c->p.seed = 0;
+    *out = c;
+    return NTVS_OK;
+}
+
+int ntvs_destroy(ntvs_ctx* c) {
+    if (!c) return NTVS_OK;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    c->free_system();
+    dev_free(c->red.partials);
+    dev_free(c->red.ticket);
+    dev_free(c->dscal);
+    dev_free(c->daccept);
+    dev_free(c->dflags);
+    dev_free(c->tvhist);
+    for (auto& t : c->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
+    for (auto e : c->event_pool) cudaEventDestroy(e);
+    if (c->hscal) cudaFreeHost(c->hscal);
+    if (c->hint) cudaFreeHost(c->hint);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return NTVS_OK;
+}
+
+int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
+    TRY(use_device(c));
+    if (!s) return fail(NTVS_ERR_ARG, "null system");
+    if (s->nx < 1 || s->ny < 1 || s->nz < 1) return fail(NTVS_ERR_ARG, "grid sizes must be >= 1");
+    const int64_t V = (int64_t)s->nx * s->ny * s->nz;
+    if (V > 0x7fffffffLL) return fail(NTVS_ERR_ARG, "V exceeds the int32 column range");
+    if (s->n_rows < 0) return fail(NTVS_ERR_ARG, "n_rows < 0");
+    if (s->val_dtype < NTVS_F64 || s->val_dtype > NTVS_BF16) return fail(NTVS_ERR_ARG, "bad val_dtype");
+    if (s->mem_kind != NTVS_MEM_HOST && s->mem_kind != NTVS_MEM_DEVICE) return fail(NTVS_ERR_ARG, "bad mem_kind");
+    if (s->storage != NTVS_CSR32) return fail(NTVS_ERR_ARG, "storage: only NTVS_CSR32 is supported");
+    if (!s->row_ptr) return fail(NTVS_ERR_ARG, "null row_ptr");
+    const int64_t M = s->n_rows;
+    if (M > 0 && (!s->b)) return fail(NTVS_ERR_ARG, "null b");
+    // block partition (host)
+    std::vector<int64_t> bp;
+    if (s->block_ptr) {
+        if (s->n_blocks < 1) return fail(NTVS_ERR_ARG, "n_blocks must be >= 1 with block_ptr");
+        bp.assign(s->block_ptr, s->block_ptr + s->n_blocks + 1);
+        if (bp.front() != 0 || bp.back() != M) return fail(NTVS_ERR_ARG, "block_ptr must run from 0 to n_rows");
+        for (int t = 0; t < s->n_blocks; ++t)
+            if (bp[t] > bp[t + 1]) return fail(NTVS_ERR_ARG, "block_ptr decreases");
+    } else {
+        if (s->n_blocks < 1) return fail(NTVS_ERR_ARG, "n_blocks must be >= 1");
+        const int64_t per = (M + s->n_blocks - 1) / s->n_blocks;
+        bp.resize((size_t)s->n_blocks + 1);
+        for (int t = 0; t <= s->n_blocks; ++t) bp[t] = std::min<int64_t>((int64_t)t * per, M);
+    }
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->free_system();
+    c->nx = s->nx; c->ny = s->ny; c->nz = s->nz;
+    c->V = V;
+    c->M = M;
+    c->B = (int)bp.size() - 1;
+    c->block_ptr = bp;
+    c->vdt = s->val_dtype;
+    c->cdt = (s->val_dtype == NTVS_F64) ? F64 : F32;
+    c->storage = s->storage;
+    cudaStream_t st = c->stream;
+
+    // row_ptr and nnz
+    int64_t nnz = 0;
+    if (s->mem_kind == NTVS_MEM_HOST) {
+        nnz = s->row_ptr[M];
+    } else {
+        CUDA_TRY(cudaMemcpyAsync(c->hscal, s->row_ptr + M, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        std::memcpy(&nnz, c->hscal, sizeof(int64_t));
+    }
+    if (nnz < 0) return fail(NTVS_ERR_CSR, "row_ptr[n_rows] < 0");
+    if (nnz > 0 && (!s->col || !s->val)) return fail(NTVS_ERR_ARG, "null col or val");
+    c->nnz = nnz;
+    const size_t vsz = dt_size(c->vdt), csz = c->csz();
+    TRY(copy_in((void**)&c->row_ptr, &c->own_row_ptr, s->row_ptr, sizeof(int64_t) * (size_t)(M + 1), s->mem_kind, st,
+                "row_ptr"));
+    TRY(copy_in((void**)&c->col, &c->own_col, s->col, sizeof(int32_t) * (size_t)nnz, s->mem_kind, st, "col"));
+    TRY(copy_in(&c->val, &c->own_val, s->val, vsz * (size_t)nnz, s->mem_kind, st, "val"));
+    TRY(copy_in(&c->b, &c->own_b, s->b, csz * (size_t)M, s->mem_kind, st, "b"));
+
+    // validation
+    CUDA_TRY(cudaMemsetAsync(c->dflags, 0, sizeof(int), st));
+    CUDA_TRY(k_validate_rows(c->row_ptr, M, c->dflags, st));
+    CUDA_TRY(cudaMemcpyAsync(c->hint, c->dflags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (c->hint[0]) {
+        c->free_system();
+        return fail(NTVS_ERR_CSR, (c->hint[0] & 2) ? "row_ptr[0] != 0" : "row_ptr decreases");
+    }
+    CUDA_TRY(k_validate_entries(c->col, c->val, c->vdt, nnz, V, c->dflags, st));
+    CUDA_TRY(k_validate_rhs(c->b, c->cdt, M, c->dflags, st));
+    CUDA_TRY(cudaMemcpyAsync(c->hint, c->dflags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (c->hint[0]) {
+        const int f = c->hint[0];
+        c->free_system();
+        return fail(NTVS_ERR_CSR, (f & 4) ? "column index outside [0, V)" : (f & 8) ? "non-finite matrix value"
+                                                                                    : "non-finite right-hand side");
+    }
+
+    // row norms and per-block hit counts
+    TRY(dev_alloc(&c->inv_norm2, csz * (size_t)M, "inv_norm2"));
+    CUDA_TRY(k_row_inv_norm2(c->row_ptr, c->val, c->vdt, M, c->inv_norm2, c->cdt, st));
+    int32_t* cnt = nullptr;
+    TRY(dev_alloc(&cnt, sizeof(int32_t) * (size_t)c->B * V, "hit counts"));
+    CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)c->B * V, st));
+    for (int t = 0; t < c->B; ++t)
+        CUDA_TRY(k_hit_counts(c->row_ptr, c->col, c->val, c->vdt, bp[t], bp[t + 1], cnt + (size_t)t * V, st));
+    TRY(dev_alloc(&c->inv_s, csz * (size_t)c->B * V, "inverse hit counts"));
+    CUDA_TRY(k_inv_counts(cnt, c->inv_s, c->cdt, (int64_t)c->B * V, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    dev_free(cnt);
+
+    // image state
+    TRY(dev_alloc(&c->x, csz * (size_t)V, "x"));
+    TRY(dev_alloc(&c->delta, csz * (size_t)V, "delta"));
+    TRY(dev_alloc(&c->g, csz * (size_t)V, "g"));
+    TRY(dev_alloc(&c->resid, sizeof(double) * (size_t)c->B, "residuals"));
+    CUDA_TRY(cudaMemsetAsync(c->x, 0, csz * (size_t)V, st));
+    CUDA_TRY(cudaMemsetAsync(c->delta, 0, csz * (size_t)V, st));
+    CUDA_TRY(cudaMemsetAsync(c->g, 0, csz * (size_t)V, st));
+    CUDA_TRY(cudaMemsetAsync(c->resid, 0, sizeof(double) * (size_t)c->B, st));
+
+    // launch shapes: lanes per row from the mean row length
+    const double mean = M ? (double)nnz / (double)M : 0.0;
+    c->lpr = mean <= 12.0 ? 4 : mean <= 40.0 ? 8 : mean <= 120.0 ? 16 : 32;
+    c->drop_grid = c->sms * 8;
+    c->red.grid = red_grid(V, c->sms);
+
+    c->k = 0;
+    c->ell_prev = 0;
+    c->ell_trace.clear();
+    c->tries_trace.clear();
+    c->acc_trace.clear();
+    c->n_steps = c->n_accepted = c->n_tries = 0;
+    CUDA_TRY(cudaStreamSynchronize(st));
+    c->loaded = true;
+    return NTVS_OK;
+}
+
+int ntvs_set_params(ntvs_ctx* c, const ntvs_params* p) {
+    if (!c || !p) return fail(NTVS_ERR_ARG, "null argument");
+    if (p->N < 0) return fail(NTVS_ERR_ARG, "N must be >= 0");
+    if (!(p->alpha > 0.0 && p->alpha < 1.0)) return fail(NTVS_ERR_ARG, "alpha must lie in (0, 1)");
+    if (!(p->beta0 >= 0.0) || !std::isfinite(p->beta0)) return fail(NTVS_ERR_ARG, "beta0 must be finite and >= 0");
+    if (!(p->eps_tv >= 0.0) || !std::isfinite(p->eps_tv)) return fail(NTVS_ERR_ARG, "eps_tv must be finite and >= 0");
+    if (!std::isfinite(p->lambda)) return fail(NTVS_ERR_ARG, "lambda must be finite");
+    if (p->tv_check && p->max_retries < 1) return fail(NTVS_ERR_ARG, "max_retries must be >= 1");
+    c->p = *p;
+    return NTVS_OK;
+}
+
+int ntvs_set_image(ntvs_ctx* c, const void* x, int dtype, int mem_kind) {
+    TRY(use_device(c));
+    TRY(need_system(c));
+    if (dtype != NTVS_F64 && dtype != NTVS_F32) return fail(NTVS_ERR_ARG, "image dtype must be NTVS_F64 or NTVS_F32");
+    if (!x) return fail(NTVS_ERR_ARG, "null image");
+    if (mem_kind == NTVS_MEM_DEVICE) {
+        CUDA_TRY(k_convert(x, dtype, c->x, c->cdt, c->V, c->stream));
+        return NTVS_OK;
+    }
+    if (mem_kind != NTVS_MEM_HOST) return fail(NTVS_ERR_ARG, "bad mem_kind");
+    if (dtype == c->cdt) {
+        CUDA_TRY(cudaMemcpyAsync(c->x, x, (size_t)c->V * c->csz(), cudaMemcpyHostToDevice, c->stream));
+    } else {
+        std::vector<unsigned char> tmp((size_t)c->V * c->csz());
+        if (c->cdt == NTVS_F64) {
+            const float* s = (const float*)x;
+            double* d = (double*)tmp.data();
+            for (int64_t j = 0; j < c->V; ++j) d[j] = s[j];
+        } else {
+            const double* s = (const double*)x;
+            float* d = (float*)tmp.data();
+            for (int64_t j = 0; j < c->V; ++j) d[j] = (float)s[j];
+        }
+        CUDA_TRY(cudaMemcpyAsync(c->x, tmp.data(), tmp.size(), cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+    }
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return NTVS_OK;
+}
+
+int ntvs_get_image(ntvs_ctx* c, void* out, int dtype, int mem_kind) {
+    TRY(use_device(c));
+    TRY(need_system(c));
+    return copy_image_out(c, c->x, out, dtype, mem_kind);
+}
+
+int ntvs_run(ntvs_ctx* c, int k_iters) {
+    TRY(use_device(c));
+    TRY(need_system(c));
+    if (k_iters < 0) return fail(NTVS_ERR_ARG, "k_iters < 0");
+    TRY(ensure_tvhist(c, c->k + k_iters));
+    for (int kk = 0; kk < k_iters; ++kk) {
+        int64_t ell;
+        if (c->override_pos < c->override_ell.size()) ell = c->override_ell[c->override_pos++];
+        else ell = draw_ell(c->p.seed, c->k, c->ell_prev);
+        c->ell_trace.push_back(ell);
+        TRY(perturb_steps(c, &ell));
+        c->ell_prev = ell;
+        TRY(drop_sweep(c));
+        CUDA_TRY(timed_launch(c, KIND_TV, [&] {
+            return k_tv_value(c->cdt, c->x, nullptr, c->dscal, 0.0, c->nx, c->ny, c->nz, c->red, c->tvhist + c->k,
+                              nullptr, nullptr, c->stream);
+        }));
+        c->k += 1;
+    }
+    return NTVS_OK;
+}
+
+int ntvs_sync(ntvs_ctx* c) {
+    TRY(use_device(c));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return NTVS_OK;
+}
+
+int ntvs_get_tv(ntvs_ctx* c, double* tv) {
+    TRY(use_device(c));
+    TRY(need_system(c));
+    if (!tv) return fail(NTVS_ERR_ARG, "null output");
+    CUDA_TRY(timed_launch(c, KIND_TV, [&] {
+        return k_tv_value(c->cdt, c->x, nullptr, c->dscal, 0.0, c->nx, c->ny, c->nz, c->red, c->dscal + 3, nullptr,
+                          nullptr, c->stream);
+    }));
+    CUDA_TRY(cudaMemcpyAsync(c->hscal, c->dscal + 3, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    *tv = c->hscal[0];
+    return NTVS_OK;
+}
+
+int ntvs_get_stats(ntvs_ctx* c, ntvs_stats* st) {
+    TRY(use_device(c));
+    if (!st) return fail(NTVS_ERR_ARG, "null output");
+    std::memset(st, 0, sizeof(*st));
+    st->k = c->k;
+    st->ell_prev = c->ell_prev;
+    st->n_steps = c->n_steps;
+    st->n_accepted = c->n_accepted;
+    st->n_tries = c->n_tries;
+    st->nnz = c->nnz;
+    st->n_rows = c->M;
+    st->n_blocks = c->B;
+    st->compute_dtype = c->cdt;
+    st->last_tv = NAN;
+    st->n_launches = c->n_launches;
+    if (c->k > 0 && c->tvhist) {
+        CUDA_TRY(cudaMemcpyAsync(c->hscal, c->tvhist + (c->k - 1), sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        st->last_tv = c->hscal[0];
+    } else {
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+    }
+    return NTVS_OK;
+}
+
+int ntvs_get_block_resid(ntvs_ctx* c, double* out, int cap) {
+    TRY(use_device(c));
+    TRY(need_system(c));
+    if (!out || cap < c->B) return fail(NTVS_ERR_ARG, "output too small");
+    CUDA_TRY(cudaMemcpyAsync(out, c->resid, sizeof(double) * (size_t)c->B, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return NTVS_OK;
+}
+
+int ntvs_get_trace(ntvs_ctx* c, int64_t* ell_k, int32_t* tries, int32_t* accepted, int64_t cap, int64_t* n_cycles) {
+    if (!c) return fail(NTVS_ERR_ARG, "null context");
+    const int64_t nk = (int64_t)c->ell_trace.size();
+    const int64_t ns = (int64_t)c->tries_trace.size();
+    if (ell_k) for (int64_t i = 0; i < nk && i < cap; ++i) ell_k[i] = c->ell_trace[i];
+    if (tries) for (int64_t i = 0; i < ns && i < cap; ++i) tries[i] = c->tries_trace[i];
+    if (accepted) for (int64_t i = 0; i < ns && i < cap; ++i) accepted[i] = c->acc_trace[i];
+    if (n_cycles) *n_cycles = nk;
+    return NTVS_OK;
+}
+
+int ntvs_get_state(ntvs_ctx* c, int64_t* k, int64_t* ell_prev) {
+    if (!c) return fail(NTVS_ERR_ARG, "null context");
+    if (k) *k = c->k;
+    if (ell_prev) *ell_prev = c->ell_prev;
+    return NTVS_OK;
+}
+
+int ntvs_set_state(ntvs_ctx* c, int64_t k, int64_t ell_prev) {
+    if (!c) return fail(NTVS_ERR_ARG, "null context");
+    if (k < 0 || ell_prev < 0) return fail(NTVS_ERR_ARG, "k and ell_prev must be >= 0");
+    c->k = k;
+    c->ell_prev = ell_prev;
+    return NTVS_OK;
+}
+
+int ntvs_set_profiling(ntvs_ctx* c, int on) {
+    TRY(use_device(c));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    harvest_timing(c);
+    c->profiling = on != 0;
+    if (c->profiling) {
+        for (int q = 0; q < 3; ++q) { c->prof_ms[q] = 0.0; c->prof_n[q] = 0; }
+    }
+    return NTVS_OK;
+}
+
+int ntvs_get_profile(ntvs_ctx* c, ntvs_profile* out) {
+    TRY(use_device(c));
+    if (!out) return fail(NTVS_ERR_ARG, "null output");
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    harvest_timing(c);
+    out->drop_block_ms = c->prof_ms[KIND_DROP];
+    out->drop_block_launches = c->prof_n[KIND_DROP];
+    out->drop_apply_ms = c->prof_ms[KIND_APPLY];
+    out->drop_apply_launches = c->prof_n[KIND_APPLY];
+    out->tv_ms = c->prof_ms[KIND_TV];
+    out->tv_launches = c->prof_n[KIND_TV];
+    return NTVS_OK;
+}
+
+int ntvs_set_ell_override(ntvs_ctx* c, const int64_t* ell_k, int64_t n) {
+    if (!c) return fail(NTVS_ERR_ARG, "null context");
+    c->override_ell.clear();
+    c->override_pos = 0;
+    if (ell_k && n > 0) c->override_ell.assign(ell_k, ell_k + n);
+    return NTVS_OK;
+}
+
+int ntvs_tv_gradient(ntvs_ctx* c, void* g_out, int dtype, int mem_kind, double* gnorm) {
+    TRY(use_device(c));
+    TRY(need_system(c));
+    TRY(launch_grad(c, false));
+    if (g_out) TRY(copy_image_out(c, c->g, g_out, dtype, mem_kind));
+    if (gnorm) {
+        CUDA_TRY(cudaMemcpyAsync(c->hscal, c->dscal, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        *gnorm = std::sqrt(c->hscal[0]);
+    }
+    return NTVS_OK;
+}
+
+int ntvs_perturb(ntvs_ctx* c, double beta) {
+    TRY(use_device(c));
+    TRY(need_system(c));
+    TRY(launch_grad(c, false));
+    CUDA_TRY(timed_launch(c, KIND_TV, [&] {
+        return k_tv_apply(c->cdt, c->x, c->g, c->dscal + 0, beta, nullptr, c->V, c->stream);
+    }));
+    return NTVS_OK;
+}
+
+int ntvs_perturb_checked(ntvs_ctx* c, double beta, int* accepted, double* phi_x, double* phi_z) {
+    TRY(use_device(c));
+    TRY(need_system(c));
+    TRY(launch_grad(c, true));
+    int a = 0;
+    TRY(checked_try(c, beta, &a));
+    if (accepted) *accepted = a;
+    if (phi_x || phi_z) {
+        CUDA_TRY(cudaMemcpyAsync(c->hscal, c->dscal, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        if (phi_x) *phi_x = c->hscal[1];
+        if (phi_z) *phi_z = c->hscal[2];
+    }
+    return NTVS_OK;
+}
+
+int ntvs_drop_block(ntvs_ctx* c, int t) {
+    TRY(use_device(c));
+    TRY(need_system(c));
+    if (t < 0 || t >= c->B) return fail(NTVS_ERR_ARG, "block index out of range");
+    return drop_block(c, t);
+}
+
+int ntvs_drop_sweep(ntvs_ctx* c) {
+    TRY(use_device(c));
+    TRY(need_system(c));
+    return drop_sweep(c);
+}
+
+}  // extern "C"

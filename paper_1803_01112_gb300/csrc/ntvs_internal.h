@@ -1,0 +1,80 @@
+// Internal launch interface between the host runtime (ntvs_api.cu) and the kernel
+// translation units.  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ntvs {
+
+// compute / storage element types (same numbering as the public NTVS_F64 ...)
+enum Dt { F64 = 0, F32 = 1, F16 = 2, BF16 = 3 };
+
+inline size_t dt_size(int dt) { return dt == F64 ? 8 : dt == F32 ? 4 : 2; }
+
+// Grid used by every deterministic reduction: a fixed CTA count so the order of the
+// final sum over CTA partials never changes.
+constexpr int kRedThreads = 256;
+int red_grid(int64_t n, int sm_count);
+
+// ------------------------------------------------------------------ load-time prep
+// flags |= 1 if row_ptr decreases, 2 if row_ptr[0] != 0
+cudaError_t k_validate_rows(const int64_t* row_ptr, int64_t M, int* flags, cudaStream_t s);
+// flags |= 4 if a column is outside [0, V), 8 if a value is not finite
+cudaError_t k_validate_entries(const int32_t* col, const void* val, int vdt, int64_t nnz, int64_t V,
+                               int* flags, cudaStream_t s);
+// flags |= 16 if a right-hand side is not finite
+cudaError_t k_validate_rhs(const void* b, int bdt, int64_t M, int* flags, cudaStream_t s);
+// inv_norm2[i] = 1 / sum_j a_ij^2 (FP64 sum of the stored values), 0 for a zero row
+cudaError_t k_row_inv_norm2(const int64_t* row_ptr, const void* val, int vdt, int64_t M, void* inv_norm2,
+                            int cdt, cudaStream_t s);
+// cnt[j] += 1 for every entry of rows [r0, r1) with a_ij != 0
+cudaError_t k_hit_counts(const int64_t* row_ptr, const int32_t* col, const void* val, int vdt, int64_t r0,
+                         int64_t r1, int32_t* cnt, cudaStream_t s);
+// inv_s[j] = cnt[j] ? 1/cnt[j] : 0
+cudaError_t k_inv_counts(const int32_t* cnt, void* inv_s, int cdt, int64_t n, cudaStream_t s);
+
+// ------------------------------------------------------------------ TV
+// Scratch of the deterministic reductions: partials[2*grid] doubles and a ticket word
+// that the last CTA resets to 0.
+struct RedScratch {
+    double* partials;
+    unsigned* ticket;
+    int grid;
+};
+
+// g = grad phi_eps(x); *gnorm2 = ||g||^2 (FP64); if phi != nullptr also *phi = phi_0(x).
+cudaError_t k_tv_grad(int cdt, const void* x, void* g, int nx, int ny, int nz, double eps, RedScratch r,
+                      double* gnorm2, double* phi, cudaStream_t s);
+// *phi = phi_0(z), z = x - sc*g with sc = beta/sqrt(*gnorm2) (z = x when g == nullptr or
+// gnorm2 == 0).  If phi_ref != nullptr, *accept = (*phi <= *phi_ref).
+cudaError_t k_tv_value(int cdt, const void* x, const void* g, const double* gnorm2, double beta, int nx, int ny,
+                       int nz, RedScratch r, double* phi, const double* phi_ref, int* accept, cudaStream_t s);
+// x <- x - sc*g (sc as in k_tv_value); skipped when accept != nullptr and *accept == 0.
+cudaError_t k_tv_apply(int cdt, void* x, const void* g, const double* gnorm2, double beta, const int* accept,
+                       int64_t V, cudaStream_t s);
+
+// ------------------------------------------------------------------ DROP
+struct DropArgs {
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const void* val;       // storage type vdt
+    const void* b;         // compute type
+    const void* inv_norm2; // compute type
+    int64_t r0, r1;
+    const void* x;         // compute type
+    void* delta;           // compute type, accumulates lambda * sum_i a_ij r_i
+    double lambda;
+    double* resid_ss;      // += sum_i (b_i - <a_i,x>)^2
+    int vdt, cdt;
+    int lanes_per_row;     // 4, 8, 16 or 32
+    int grid;
+};
+cudaError_t k_drop_block(const DropArgs& a, cudaStream_t s);
+// x_j += delta_j * inv_s_j ; delta_j = 0
+cudaError_t k_drop_apply(int cdt, void* x, void* delta, const void* inv_s, int64_t V, cudaStream_t s);
+
+// ------------------------------------------------------------------ misc
+// convert between the image's compute type and F64/F32 buffers (device to device)
+cudaError_t k_convert(const void* src, int sdt, void* dst, int ddt, int64_t n, cudaStream_t s);
+
+}  // namespace ntvs

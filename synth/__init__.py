@@ -69,8 +69,9 @@ def _lib():
         vp = ctypes.c_void_p
         L.syn_phantom.argtypes = [ctypes.POINTER(_Cfg), vp, vp, vp]
         L.syn_plan.argtypes = [ctypes.POINTER(_Cfg), vp, vp, vp, vp]
-        L.syn_count.argtypes = [ctypes.POINTER(_Cfg), vp, vp, vp, vp, vp]
-        L.syn_fill.argtypes = [ctypes.POINTER(_Cfg), vp, vp, vp, vp, vp, vp, vp, ctypes.c_int32, vp, vp]
+        L.syn_count.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int64, vp, vp, vp, vp, vp]
+        L.syn_fill.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int64, vp, vp, vp, vp, vp, vp, vp, ctypes.c_int32,
+                               vp, vp]
         L.syn_splitmix64_at.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
         L.syn_splitmix64_at.restype = ctypes.c_uint64
         for f in ("syn_phantom", "syn_plan", "syn_count", "syn_fill"):
@@ -217,9 +218,11 @@ def phantom(spec: Spec):
 
 
 def generate(spec: Spec, val_dtype=np.float64,
-             alloc: Callable[[Sequence[int], np.dtype], np.ndarray] = None) -> System:
-    """Generate the system.  ``alloc(shape, dtype)`` provides the col / val buffers
-    (e.g. views of pinned host memory); default ``np.empty``."""
+             alloc: Callable[[Sequence[int], np.dtype], np.ndarray] = None,
+             rows: Optional[Tuple[int, int]] = None) -> System:
+    """Generate the system, or only its rows [r0, r1) when ``rows`` is given (the same rows
+    the whole system has there).  ``alloc(shape, dtype)`` provides the col / val / b
+    buffers (e.g. views of pinned host memory); default ``np.empty``."""
     val_dtype = np.dtype(val_dtype)
     if val_dtype not in (np.dtype(np.float64), np.dtype(np.float32)):
         raise ValueError("val_dtype must be float64 or float32")
@@ -234,8 +237,12 @@ def generate(spec: Spec, val_dtype=np.float64,
     key = np.empty(M, np.uint64)
     angle = np.empty(M, np.int32)
     L.syn_plan(ctypes.byref(c), t.ctypes.data, z.ctypes.data, key.ctypes.data, angle.ctypes.data)
+    if rows is not None:
+        r0, r1 = rows
+        t, z, key, angle = (np.ascontiguousarray(a[r0:r1]) for a in (t, z, key, angle))
+        M = r1 - r0
     nnz_row = np.empty(M, np.int64)
-    L.syn_count(ctypes.byref(c), t.ctypes.data, z.ctypes.data, key.ctypes.data, angle.ctypes.data,
+    L.syn_count(ctypes.byref(c), M, t.ctypes.data, z.ctypes.data, key.ctypes.data, angle.ctypes.data,
                 nnz_row.ctypes.data)
     row_ptr = np.zeros(M + 1, np.int64)
     np.cumsum(nnz_row, out=row_ptr[1:])
@@ -243,7 +250,7 @@ def generate(spec: Spec, val_dtype=np.float64,
     col = alloc((nnz,), np.dtype(np.int32))
     val = alloc((nnz,), val_dtype)
     b = np.empty(M, np.float64)
-    L.syn_fill(ctypes.byref(c), t.ctypes.data, z.ctypes.data, key.ctypes.data, angle.ctypes.data,
+    L.syn_fill(ctypes.byref(c), M, t.ctypes.data, z.ctypes.data, key.ctypes.data, angle.ctypes.data,
                row_ptr.ctypes.data, col.ctypes.data, val.ctypes.data,
                0 if val_dtype == np.float64 else 1, b.ctypes.data, xstar.ctypes.data)
     return System(spec, row_ptr, col, val, b, xstar, xbar, label, angle, t, z)

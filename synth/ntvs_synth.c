@@ -339,15 +339,15 @@ static void trace_row(const syn_cfg* c, double t, double z, uint64_t key, int a,
 }
 
 
-/* pass 1: nonzeros per row */
-void syn_count(const syn_cfg* c, const double* t, const double* z, const uint64_t* key,
+/* pass 1: nonzeros of rows 0..n-1 of the plan arrays passed */
+void syn_count(const syn_cfg* c, int64_t n, const double* t, const double* z, const uint64_t* key,
                const int32_t* angle, int64_t* row_nnz) {
     #pragma omp parallel
     {
         rowbuf rb; rb_init(&rb);
         double* sbuf = (double*)malloc(sizeof(double) * (size_t)seg_scratch(c));
         #pragma omp for schedule(dynamic, 1024)
-        for (int64_t r = 0; r < c->n_hist; ++r) {
+        for (int64_t r = 0; r < n; ++r) {
             trace_row(c, t[r], z[r], key[r], angle[r], &rb, sbuf);
             row_nnz[r] = rb.n;
         }
@@ -355,9 +355,10 @@ void syn_count(const syn_cfg* c, const double* t, const double* z, const uint64_
     }
 }
 
-/* pass 2: write col / val (val_dtype 0 = f64, 1 = f32) and b.
- * b_r = (sum_j len_rj * xstar_j) * (1 + noise_sigma * N(0,1)), from the f64 lengths. */
-void syn_fill(const syn_cfg* c, const double* t, const double* z, const uint64_t* key,
+/* pass 2: write col / val (val_dtype 0 = f64, 1 = f32) and b of rows 0..n-1 of the plan
+ * arrays passed.  b_r = (sum_j len_rj * xstar_j) * (1 + noise_sigma * N(0,1)), from the
+ * f64 lengths. */
+void syn_fill(const syn_cfg* c, int64_t n, const double* t, const double* z, const uint64_t* key,
               const int32_t* angle, const int64_t* row_ptr, int32_t* col, void* val, int32_t val_dtype,
               double* b, const double* xstar) {
     #pragma omp parallel
@@ -365,7 +366,7 @@ void syn_fill(const syn_cfg* c, const double* t, const double* z, const uint64_t
         rowbuf rb; rb_init(&rb);
         double* sbuf = (double*)malloc(sizeof(double) * (size_t)seg_scratch(c));
         #pragma omp for schedule(dynamic, 1024)
-        for (int64_t r = 0; r < c->n_hist; ++r) {
+        for (int64_t r = 0; r < n; ++r) {
             trace_row(c, t[r], z[r], key[r], angle[r], &rb, sbuf);
             int64_t p = row_ptr[r];
             double wepl = 0.0;

@@ -1,0 +1,265 @@
+"""GPU parity of the single steps of the hot path against the FP64 oracle (through the C ABI).
+
+Tolerances: the FP64 path differs from the oracle only in summation order (1e-12
+relative); the FP32 path computes each voxel of the TV gradient with ~10 float
+operations of O(1) terms (absolute error ~1e-6) and each DROP update with ~300-term
+float dot products (relative 1e-6); the bounds below leave a factor of ~10.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from _gpu_util import empty_system, load, ntvs_module, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(1, 1, 1), (7, 1, 1), (1, 9, 1), (33, 17, 1), (40, 37, 5), (64, 48, 3), (200, 200, 16)]
+
+
+def _image(shape, seed, kind):
+    V = int(np.prod(shape))
+    rng = np.random.default_rng(seed)
+    if kind == "random":
+        return rng.uniform(0.0, 2.0, size=V)
+    xs, _, _ = synth.phantom(synth.spec_scaled_3d(nx=shape[0], ny=shape[1], nz=shape[2]))
+    return xs + 0.01 * rng.normal(size=V)   # piecewise constant + noise
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("kind", ["random", "phantom"])
+def test_tv_gradient_and_value(dtype, shape, kind):
+    ntvs = ntvs_module()
+    if kind == "phantom" and shape[0] != shape[1]:
+        pytest.skip("phantom needs a square slice")
+    x = _image(shape, 11, kind).astype(dtype)
+    x64 = x.astype(np.float64)
+    eps = 1e-8
+    r = empty_system(ntvs, shape) if dtype == np.float64 else _empty32(ntvs, shape)
+    try:
+        r.set_params(lam=1.0, N=1, alpha=0.5, eps_tv=eps)
+        r.set_image(x)
+        g, gn = r.tv_gradient(np.float64)
+        tv = r.tv()
+    finally:
+        r.close()
+    g_ref = oracle.tv_grad(x64, shape, eps)
+    scale = max(np.abs(g_ref).max(), 1.0)
+    if dtype == np.float64:
+        np.testing.assert_allclose(g, g_ref, rtol=1e-11, atol=1e-11 * scale)
+        assert gn == pytest.approx(np.linalg.norm(g_ref), rel=1e-12)
+    else:
+        np.testing.assert_allclose(g, g_ref, rtol=1e-4, atol=2e-5 * scale)
+        assert gn == pytest.approx(np.linalg.norm(g_ref), rel=1e-5)
+    assert tv == pytest.approx(oracle.tv(x64, shape), rel=1e-12, abs=1e-12)
+
+
+def _empty32(ntvs, shape):
+    r = ntvs.Reconstructor(0)
+    r.load(shape, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.float32), np.zeros(0, np.float32))
+    return r
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_perturb_step_closed_form(dtype):
+    ntvs = ntvs_module()
+    shape = (31, 29, 3)
+    x = _image(shape, 3, "random").astype(dtype)
+    r = empty_system(ntvs, shape) if dtype == np.float64 else _empty32(ntvs, shape)
+    try:
+        r.set_params(lam=1.0, N=1, alpha=0.5, eps_tv=1e-8)
+        r.set_image(x)
+        r.perturb(0.37)
+        got = r.get_image()
+    finally:
+        r.close()
+    x64 = x.astype(np.float64)
+    g = oracle.tv_grad(x64, shape, 1e-8)
+    want = x64 - 0.37 * g / np.linalg.norm(g)
+    tol = 1e-13 if dtype == np.float64 else 2e-7
+    np.testing.assert_allclose(got, want, rtol=0, atol=tol * max(1.0, np.abs(want).max()))
+
+
+def test_perturb_checked_decisions():
+    ntvs = ntvs_module()
+    shape = (5, 5, 1)
+    x = np.zeros(25)
+    x[12] = 0.05
+    r = empty_system(ntvs, shape)
+    try:
+        r.set_params(lam=1.0, N=1, alpha=0.5, eps_tv=1e-8)
+        r.set_image(x)
+        acc, px, pz = r.perturb_checked(1.0)     # overshoots the spike: rejected
+        assert not acc and pz > px
+        np.testing.assert_array_equal(r.get_image(), x)
+        acc2, px2, pz2 = r.perturb_checked(1e-3)   # small step lowers TV: accepted
+        assert acc2 and pz2 <= px2
+        g = oracle.tv_grad(x, shape, 1e-8)
+        np.testing.assert_allclose(r.get_image(), x - 1e-3 * g / np.linalg.norm(g), atol=1e-15)
+        assert px == pytest.approx(oracle.tv(x, shape), rel=1e-14)
+    finally:
+        r.close()
+
+
+def _small_system(curved=True, n_hist=6000, nx=24, nz=3, blocks=3, seed=5):
+    return synth.generate(synth.spec_scaled_3d(nx=nx, ny=nx, nz=nz, n_hist=n_hist, n_angles=30, n_blocks=blocks,
+                                               seed=seed, curved=curved))
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("curved", [False, True])
+def test_drop_block_and_sweep(dtype, curved):
+    ntvs = ntvs_module()
+    s = _small_system(curved)
+    r, val64, b64 = load(ntvs, s, dtype)
+    bp = s.block_ptr()
+    x0 = s.xbar.astype(dtype).astype(np.float64)
+    try:
+        r.set_params(lam=0.9, N=0, alpha=0.5)
+        r.set_image(x0.astype(dtype))
+        r.drop_block(1)
+        got1 = r.get_image()
+        res1 = r.block_resid()[1]
+        r.set_image(x0.astype(dtype))
+        r.drop_sweep()
+        got = r.get_image()
+        res = r.block_resid()
+    finally:
+        r.close()
+    want1, ss1 = oracle.drop_block(s.row_ptr, s.col, val64, b64, bp[1], bp[2], x0, 0.9)
+    want, ss = oracle.drop_sweep(s.row_ptr, s.col, val64, b64, bp, x0, 0.9)
+    tol = 1e-12 if dtype == np.float64 else 1e-6
+    assert rel_l2(got1, want1) < tol
+    assert rel_l2(got, want) < tol
+    assert res1 == pytest.approx(ss1, rel=1e-10 if dtype == np.float64 else 1e-4)
+    np.testing.assert_allclose(res, ss, rtol=1e-10 if dtype == np.float64 else 1e-4)
+
+
+@pytest.mark.parametrize("lanes_case", ["short", "medium", "long"])
+def test_drop_row_lengths_cover_every_lane_shape(lanes_case):
+    # mean row length selects 4/8/16/32 lanes per row; rows beyond the register-held
+    # chunks take the re-read tail path
+    ntvs = ntvs_module()
+    rng = np.random.default_rng(9)
+    V = 5000
+    per = {"short": (1, 20), "medium": (30, 110), "long": (200, 700)}[lanes_case]
+    M = 3000
+    lens = rng.integers(per[0], per[1], size=M)
+    lens[::97] = 0                      # some empty rows
+    rows = [np.sort(rng.choice(V, size=n, replace=False)) for n in lens]
+    rp = np.zeros(M + 1, np.int64)
+    rp[1:] = np.cumsum(lens)
+    col = np.concatenate(rows).astype(np.int32)
+    val = rng.uniform(0.1, 1.2, size=col.size)
+    val[::13] = 0.0                     # stored zeros do not count in s_j
+    b = rng.uniform(5, 50, size=M)
+    x0 = rng.uniform(0.5, 1.5, size=V)
+    bp = np.array([0, 1000, 1001, 2500, 3000], np.int64)
+    r = ntvs.Reconstructor(0)
+    try:
+        r.load((50, 100, 1), rp, col, val, b, block_ptr=bp)
+        r.set_params(lam=1.3, N=0, alpha=0.5)
+        r.set_image(x0)
+        r.drop_sweep()
+        got = r.get_image()
+    finally:
+        r.close()
+    want, _ = oracle.drop_sweep(rp, col, val, b, bp, x0, 1.3)
+    assert rel_l2(got, want) < 1e-12
+
+
+def test_degenerate_systems():
+    ntvs = ntvs_module()
+    # more blocks than rows (empty blocks), a zero-norm row, a voxel hit by nothing, V = 1 grid
+    rp = np.array([0, 1, 1, 3], np.int64)
+    col = np.array([0, 1, 2], np.int32)
+    val = np.array([1.0, 0.0, 2.0])
+    b = np.array([3.0, 1.0, 4.0])
+    x0 = np.array([0.0, 5.0, 0.0, -1.0])
+    r = ntvs.Reconstructor(0)
+    try:
+        r.load((4, 1, 1), rp, col, val, b, n_blocks=7)
+        r.set_params(lam=1.0, N=0, alpha=0.5)
+        r.set_image(x0)
+        r.drop_sweep()
+        got = r.get_image()
+    finally:
+        r.close()
+    want, _ = oracle.drop_sweep(rp, col, val, b, synth.block_partition(3, 7), x0, 1.0)
+    np.testing.assert_allclose(got, want, atol=1e-15)
+    r = ntvs.Reconstructor(0)
+    try:
+        r.load((1, 1, 1), np.array([0, 1], np.int64), np.array([0], np.int32), np.array([2.0]), np.array([3.0]))
+        r.set_params(lam=1.0, N=2, alpha=0.5)
+        r.set_image(np.array([0.25]))
+        r.run(3)
+        assert r.get_image()[0] == pytest.approx(1.5, abs=1e-15)   # exact projection, TV steps are zero
+        assert r.tv() == 0.0
+    finally:
+        r.close()
+
+
+def test_validation_errors():
+    ntvs = ntvs_module()
+    from paper_1803_01112_gb300._ffi import NTVS_ERR_ARG, NTVS_ERR_CSR, NTVS_ERR_STATE
+    r = ntvs.Reconstructor(0)
+    try:
+        with pytest.raises(ntvs.NtvsError) as e:
+            r.run(1)
+        assert e.value.code == NTVS_ERR_STATE
+        good = dict(row_ptr=np.array([0, 2, 3], np.int64), col=np.array([0, 1, 3], np.int32),
+                    val=np.array([1.0, 1.0, 1.0]), b=np.array([1.0, 2.0]))
+        bad_cases = [dict(row_ptr=np.array([0, 2, 1], np.int64), col=np.array([0, 1], np.int32),
+                          val=np.array([1.0, 1.0]), b=np.array([1.0, 2.0])),
+                     dict(good, col=np.array([0, 1, 4], np.int32)),
+                     dict(good, col=np.array([0, -1, 3], np.int32)),
+                     dict(good, val=np.array([1.0, np.nan, 1.0])),
+                     dict(good, b=np.array([1.0, np.inf]))]
+        for case in bad_cases:
+            with pytest.raises(ntvs.NtvsError) as e:
+                r.load((2, 2, 1), case["row_ptr"], case["col"], case["val"], case["b"])
+            assert e.value.code == NTVS_ERR_CSR
+        r.load((2, 2, 1), **good)
+        for kw in (dict(alpha=1.0), dict(alpha=0.0), dict(N=-1), dict(beta0=-1.0), dict(tv_check=True, max_retries=0)):
+            with pytest.raises(ntvs.NtvsError) as e:
+                r.set_params(**dict(dict(lam=1.0, N=1, alpha=0.5), **kw))
+            assert e.value.code == NTVS_ERR_ARG
+        with pytest.raises(ntvs.NtvsError) as e:
+            r.drop_block(5)
+        assert e.value.code == NTVS_ERR_ARG
+        with pytest.raises(ntvs.NtvsError) as e:
+            r.load((2, 2, 1), **good, block_ptr=np.array([0, 3, 2], np.int64))
+        assert e.value.code == NTVS_ERR_ARG
+    finally:
+        r.close()
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_device_pointers_match_host(dtype):
+    ntvs = ntvs_module()
+    import torch
+    s = _small_system(n_hist=3000)
+    r_host, val64, b64 = load(ntvs, s, dtype)
+    tdt = torch.float64 if dtype == np.float64 else torch.float32
+    dev = dict(row_ptr=torch.from_numpy(s.row_ptr).cuda(), col=torch.from_numpy(s.col).cuda(),
+               val=torch.from_numpy(s.val.astype(dtype)).cuda(), b=torch.from_numpy(s.b.astype(dtype)).cuda())
+    r_dev = ntvs.Reconstructor(0, torch.cuda.current_stream().cuda_stream)
+    try:
+        r_dev.load((s.spec.nx, s.spec.ny, s.spec.nz), dev["row_ptr"], dev["col"], dev["val"], dev["b"],
+                   n_blocks=s.spec.n_blocks)
+        outs = []
+        for r in (r_host, r_dev):
+            r.set_params(lam=0.7, N=2, alpha=0.75, seed=3)
+            r.set_image(torch.from_numpy(s.xbar.astype(dtype)).cuda() if r is r_dev else s.xbar.astype(dtype))
+            r.run(2)
+            out = torch.empty(s.spec.V, dtype=tdt, device="cuda")
+            ntvs.ntvs_get_image(r.handle, out)
+            r.sync()
+            outs.append(out.cpu().numpy())
+        # scatter atomics make the summation order (not the result class) run dependent
+        tol = 1e-12 if dtype == np.float64 else 1e-6
+        np.testing.assert_allclose(outs[0], outs[1], rtol=tol, atol=tol)
+    finally:
+        r_host.close()
+        r_dev.close()

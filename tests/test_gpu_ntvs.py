@@ -1,0 +1,190 @@
+"""GPU parity of whole NTVS runs (Appendix C: N TV steps + a DROP sweep per cycle) with the
+FP64 oracle, through the C ABI.
+
+Bars: FP64 path relative L2 <= 1e-10 (summation order only); FP32 path relative L2
+<= 1e-5 after k cycles (the FP32 bar of the method's specification); ell traces and
+check-mode decision traces identical.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from _gpu_util import load, ntvs_module, oracle_run, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _run_gpu(r, prm, K, x0, dtype):
+    r.set_params(lam=prm.lam, N=prm.N, alpha=prm.alpha, beta0=prm.beta0, tv_check=prm.tv_check, seed=prm.seed,
+                 eps_tv=prm.eps_tv, max_retries=prm.max_retries)
+    r.set_image(x0.astype(dtype))
+    r.run(K)
+    x = r.get_image()
+    ell, tries, acc = r.trace()
+    return x, ell, tries, acc, r.stats(), r.block_resid()
+
+
+@pytest.mark.parametrize("lam", [1e-3, 0.5])
+def test_slice_2d_fp64_matches_oracle(lam):
+    """2D 32x32 slice, 20k straight histories, 10 blocks, k=4, N=3, alpha=0.75 (FP64)."""
+    ntvs = ntvs_module()
+    s = synth.generate(synth.spec_slice_2d())
+    r, val64, b64 = load(ntvs, s, np.float64)
+    prm = oracle.Params(lam=lam, N=3, alpha=0.75, seed=1)
+    try:
+        x, ell, tries, acc, st, res = _run_gpu(r, prm, 4, s.xbar, np.float64)
+    finally:
+        r.close()
+    ref = oracle_run(s, val64, b64, prm, 4, s.xbar)
+    assert rel_l2(x, ref.x) <= 1e-10
+    np.testing.assert_array_equal(ell, ref.ell_k)
+    assert st["k"] == 4 and st["ell_prev"] == ref.ell_prev
+    assert st["last_tv"] == pytest.approx(ref.tv[-1], rel=1e-10)
+    np.testing.assert_allclose(res, ref.resid_ss[-1], rtol=1e-9)
+
+
+@pytest.mark.parametrize("lam,N,K", [(2e-4, 3, 12), (2e-4, 6, 6), (0.3, 3, 6)])
+def test_scaled_3d_fp32_matches_oracle(lam, N, K):
+    """CTP404-like 3D problem at reduced size, bent paths, FP32 storage and arithmetic."""
+    ntvs = ntvs_module()
+    s = synth.generate(synth.spec_scaled_3d(nx=48, ny=48, nz=4, n_hist=60_000, n_angles=60, n_blocks=5))
+    r, val64, b64 = load(ntvs, s, np.float32)
+    prm = oracle.Params(lam=lam, N=N, alpha=0.75, seed=2)
+    try:
+        x, ell, *_ = _run_gpu(r, prm, K, s.xbar, np.float32)
+    finally:
+        r.close()
+    ref = oracle_run(s, val64, b64, prm, K, s.xbar)
+    err = rel_l2(x, ref.x)
+    assert err <= 1e-5, f"relative L2 {err:.3e}"
+    np.testing.assert_array_equal(ell, ref.ell_k)
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_check_mode_matches_oracle(dtype):
+    ntvs = ntvs_module()
+    s = synth.generate(synth.spec_scaled_3d(nx=32, ny=32, nz=3, n_hist=20_000, n_angles=40, n_blocks=4))
+    r, val64, b64 = load(ntvs, s, dtype)
+    prm = oracle.Params(lam=0.3, N=4, alpha=0.75, seed=5, tv_check=True)
+    K = 5
+    try:
+        x, ell, tries, acc, st, _ = _run_gpu(r, prm, K, s.xbar, dtype)
+    finally:
+        r.close()
+    ref = oracle_run(s, val64, b64, prm, K, s.xbar)
+    # the decision traces must agree (no near-ties in this case); rejections do occur
+    np.testing.assert_array_equal(tries, ref.tries.reshape(-1))
+    np.testing.assert_array_equal(acc, ref.accepted.reshape(-1))
+    np.testing.assert_array_equal(ell, ref.ell_k)
+    assert ref.tries.max() > 1
+    assert rel_l2(x, ref.x) <= (1e-10 if dtype == np.float64 else 1e-5)
+    assert st["n_tries"] == ref.tries.sum() and st["n_accepted"] == ref.accepted.sum()
+
+
+def test_N0_is_plain_drop_on_gpu():
+    ntvs = ntvs_module()
+    s = synth.generate(synth.spec_slice_2d().replace(n_hist=5000, n_blocks=5))
+    r, val64, b64 = load(ntvs, s, np.float64)
+    try:
+        x, *_ = _run_gpu(r, oracle.Params(lam=0.8, N=0, alpha=0.75), 3, s.xbar, np.float64)
+        r.set_image(s.xbar)
+        for _ in range(3):
+            r.drop_sweep()
+        x2 = r.get_image()
+    finally:
+        r.close()
+    xr = s.xbar.copy()
+    for _ in range(3):
+        xr, _ = oracle.drop_sweep(s.row_ptr, s.col, val64, b64, s.block_ptr(), xr, 0.8)
+    assert rel_l2(x, xr) < 1e-12 and rel_l2(x2, xr) < 1e-12
+
+
+@pytest.mark.parametrize("check", [False, True])
+def test_checkpoint_resume_equals_one_run(check):
+    ntvs = ntvs_module()
+    s = synth.generate(synth.spec_slice_2d().replace(n_hist=6000, n_blocks=3))
+    prm = oracle.Params(lam=0.4, N=3, alpha=0.75, seed=17, tv_check=check)
+    r, val64, b64 = load(ntvs, s, np.float64)
+    try:
+        whole, ell_whole, *_ = _run_gpu(r, prm, 4, s.xbar, np.float64)
+    finally:
+        r.close()
+    r1, *_ = load(ntvs, s, np.float64)
+    try:
+        x_half, *_ = _run_gpu(r1, prm, 2, s.xbar, np.float64)
+        k, ell_prev = r1.state()
+    finally:
+        r1.close()
+    r2, *_ = load(ntvs, s, np.float64)
+    try:
+        r2.set_params(lam=prm.lam, N=prm.N, alpha=prm.alpha, seed=prm.seed, tv_check=check)
+        r2.set_image(x_half)
+        r2.set_state(k, ell_prev)
+        r2.run(2)
+        resumed = r2.get_image()
+        ell2, *_ = r2.trace()
+    finally:
+        r2.close()
+    assert rel_l2(resumed, whole) < 1e-12
+    np.testing.assert_array_equal(np.concatenate([ell_whole[:2], ell2]), ell_whole)
+
+
+def test_ell_override_replays_oracle_schedule():
+    ntvs = ntvs_module()
+    s = synth.generate(synth.spec_slice_2d().replace(n_hist=4000, n_blocks=2))
+    r, val64, b64 = load(ntvs, s, np.float64)
+    forced = np.array([0, 3, 3, 9])
+    prm = oracle.Params(lam=0.5, N=2, alpha=0.6, seed=1)
+    try:
+        r.set_ell_override(forced)
+        x, ell, *_ = _run_gpu(r, prm, 4, s.xbar, np.float64)
+    finally:
+        r.close()
+    ref = oracle_run(s, val64, b64, prm, 4, s.xbar, ell_override=forced)
+    np.testing.assert_array_equal(ell, forced)
+    assert rel_l2(x, ref.x) < 1e-10
+
+
+def test_full_size_sampled_parity():
+    """200x200x16 grid, 10M bent histories, 20 blocks, FP32 - the benchmarked workload in the
+    benchmarked launch configuration.  The oracle evaluates sampled voxels of one DROP block
+    and the whole TV gradient; one full cycle is checked by invariants."""
+    ntvs = ntvs_module()
+    spec = synth.spec_ctp404_3d()
+    s = synth.generate(spec, np.float32)
+    shape = (spec.nx, spec.ny, spec.nz)
+    bp = s.block_ptr()
+    r = ntvs.Reconstructor(0)
+    rng = np.random.default_rng(0)
+    try:
+        r.load(shape, s.row_ptr, s.col, s.val, s.b.astype(np.float32), n_blocks=spec.n_blocks)
+        x0 = s.xbar.astype(np.float32)
+        r.set_params(lam=2e-4, N=3, alpha=0.75, seed=2)
+        # one DROP block at full size (block 7: a middle block), sampled voxels
+        r.set_image(x0)
+        r.drop_block(7)
+        got = r.get_image()
+        vox = np.concatenate([rng.choice(spec.V, 400, replace=False), np.nonzero(s.label >= 0)[0][::1601]])
+        r0, r1 = int(bp[7]), int(bp[8])
+        p0, p1 = int(s.row_ptr[r0]), int(s.row_ptr[r1])
+        want = oracle.drop_block_at(s.row_ptr[r0:r1 + 1] - p0, s.col[p0:p1], s.val[p0:p1],
+                                    s.b[r0:r1].astype(np.float32), 0, r1 - r0, x0.astype(np.float64), 2e-4, vox)
+        upd_g, upd_w = got[vox] - x0[vox], want - x0[vox]
+        np.testing.assert_allclose(upd_g, upd_w, rtol=1e-4, atol=1e-6 * np.abs(upd_w).max())
+        # the TV gradient of the whole full-size image
+        r.set_image(s.xstar.astype(np.float32))
+        g, gn = r.tv_gradient()
+        g_ref = oracle.tv_grad(s.xstar.astype(np.float32).astype(np.float64), shape, 1e-8)
+        np.testing.assert_allclose(g, g_ref, rtol=1e-4, atol=2e-5 * np.abs(g_ref).max())
+        # one full cycle: finite, and phi reported equals the oracle's phi of the returned image
+        r.set_image(x0)
+        r.run(1)
+        x1 = r.get_image()
+        assert np.all(np.isfinite(x1))
+        st = r.stats()
+        assert st["last_tv"] == pytest.approx(oracle.tv(x1, shape), rel=1e-12)
+        res = r.block_resid()
+        assert np.all(np.isfinite(res)) and np.all(res > 0)
+    finally:
+        r.close()

@@ -100,3 +100,14 @@ def test_phantom_values_and_labels():
         j = np.argmin((xc - ins.cx) ** 2 + (yc - ins.cy) ** 2)
         assert lab[j] == i
         assert xs[j] == pytest.approx(ins.rsp, abs=1e-12)
+
+
+def test_row_range_equals_slice_of_whole_system():
+    sp = synth.spec_scaled_3d(n_hist=5000)
+    whole = synth.generate(sp)
+    part = synth.generate(sp, rows=(1200, 3100))
+    p0, p1 = whole.row_ptr[1200], whole.row_ptr[3100]
+    np.testing.assert_array_equal(part.row_ptr, whole.row_ptr[1200:3101] - p0)
+    np.testing.assert_array_equal(part.col, whole.col[p0:p1])
+    np.testing.assert_array_equal(part.val, whole.val[p0:p1])
+    np.testing.assert_array_equal(part.b, whole.b[1200:3100])
