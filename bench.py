@@ -280,7 +280,7 @@ def run_ntvs(args):
     x0 = pinned((spec.V,), vdt)
     x0[:] = s.xbar.astype(vdt)
     shape = (spec.nx, spec.ny, spec.nz)
-    stream = torch.cuda.current_stream(device)
+    stream = torch.cuda.Stream(device)   # the library launches on this stream; events are recorded on it
 
     r = ntvs.Reconstructor(local, stream.cuda_stream)
     r.load(shape, s.row_ptr, s.col, s.val, b, n_blocks=spec.n_blocks)

@@ -126,8 +126,9 @@ const char* ntvs_version(void);
 const char* ntvs_last_error(void);
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t to queue
- * work on (e.g. torch.cuda.current_stream().cuda_stream), or NULL for a stream the
- * context creates and owns.  *out is NULL on failure. */
+ * work on (e.g. a torch.cuda.Stream's cuda_stream), or NULL for a non-blocking stream the
+ * context creates and owns; pass cudaStreamLegacy ((void*)0x1) to queue on the legacy
+ * default stream.  *out is NULL on failure. */
 int ntvs_create(ntvs_ctx** out, int device, void* cuda_stream);
 
 /* Destroy a context (synchronizes its stream, frees its device memory).  NULL is a no-op. */

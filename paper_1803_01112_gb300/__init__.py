@@ -71,7 +71,12 @@ def ntvs_last_error() -> str:
 
 
 def ntvs_create(device: int = 0, stream: Optional[int] = None) -> int:
+    """stream: None -> the context owns a stream; a cudaStream_t handle otherwise.  The
+    handle 0 (torch's default stream) is passed as cudaStreamLegacy, since NULL means
+    "own stream" in the C ABI."""
     h = ctypes.c_void_p()
+    if stream is not None and int(stream) == 0:
+        stream = 1   # cudaStreamLegacy
     check(lib().ntvs_create(ctypes.byref(h), device, stream), "ntvs_create")
     return h.value
 

@@ -15,14 +15,14 @@ __device__ __forceinline__ double to_compute(double v) { return v; }
 __device__ __forceinline__ float to_compute(__half v) { return __half2float(v); }
 __device__ __forceinline__ float to_compute(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-// fused x - s*g, spelled out so every kernel that forms a perturbed voxel rounds alike
-__device__ __forceinline__ float perturbed(float x, float s, float g) { return __fmaf_rn(-s, g, x); }
+// fused x - s*g on the FP64 master image, spelled out so every kernel that forms a
+// perturbed voxel rounds alike
 __device__ __forceinline__ double perturbed(double x, double s, double g) { return __fma_rn(-s, g, x); }
 
-template <typename T>
-__device__ __forceinline__ T step_scale(double beta, const double* gnorm2) {
-    double n2 = *gnorm2;
-    return (n2 > 0.0) ? (T)(beta / sqrt(n2)) : (T)0;
+// s = beta / ||g|| (0 when g = 0, i.e. v = 0)
+__device__ __forceinline__ double step_scale(double beta, const double* gnorm2) {
+    const double n2 = *gnorm2;
+    return (n2 > 0.0) ? beta / sqrt(n2) : 0.0;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {

@@ -65,10 +65,12 @@ drop_block_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict
 }
 
 template <typename T>
-__global__ void drop_apply_kernel(T* __restrict__ x, T* __restrict__ delta, const T* __restrict__ inv_s, int64_t V) {
+__global__ void drop_apply_kernel(double* __restrict__ x, float* __restrict__ x32, T* __restrict__ delta,
+                                  const T* __restrict__ inv_s, int64_t V) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < V; j += (int64_t)gridDim.x * blockDim.x) {
-        const T d = delta[j];
-        x[j] += d * __ldg(inv_s + j);
+        const double v = x[j] + (double)delta[j] * (double)__ldg(inv_s + j);
+        x[j] = v;
+        if (x32) x32[j] = (float)v;
         delta[j] = (T)0;
     }
 }
@@ -106,15 +108,10 @@ cudaError_t k_drop_block(const DropArgs& a, cudaStream_t s) {
     }
 }
 
-cudaError_t k_drop_apply(int cdt, void* x, void* delta, const void* inv_s, int64_t V, cudaStream_t s) {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int64_t need = (V + 255) / 256;
-    int grid = (int)(need < (int64_t)sms * 8 ? need : (int64_t)sms * 8);
-    if (grid < 1) grid = 1;
-    if (cdt == F64) drop_apply_kernel<double><<<grid, 256, 0, s>>>((double*)x, (double*)delta, (const double*)inv_s, V);
-    else drop_apply_kernel<float><<<grid, 256, 0, s>>>((float*)x, (float*)delta, (const float*)inv_s, V);
+cudaError_t k_drop_apply(int cdt, double* x, float* x32, void* delta, const void* inv_s, int64_t V, int grid,
+                         cudaStream_t s) {
+    if (cdt == F64) drop_apply_kernel<double><<<grid, 256, 0, s>>>(x, x32, (double*)delta, (const double*)inv_s, V);
+    else drop_apply_kernel<float><<<grid, 256, 0, s>>>(x, x32, (float*)delta, (const float*)inv_s, V);
     return cudaGetLastError();
 }
 

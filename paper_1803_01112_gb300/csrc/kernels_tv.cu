@@ -17,9 +17,11 @@ int red_grid(int64_t n, int sm_count) {
 // One voxel of grad phi_eps:
 //   g_q = -sum_a d_a(q) / D_q + sum_{a: q-e_a inside} d_a(q-e_a) / D_{q-e_a}
 // with d_a(c) = x_{c+e_a} - x_c (0 past the last index) and D_c = sqrt(eps + |d(c)|^2).
+// The image is the FP64 master copy; differences are formed in FP64 (so nearly equal
+// neighbours keep their difference) and the rest of the arithmetic runs in T.
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
-tv_grad_kernel(const T* __restrict__ x, T* __restrict__ g, int nx, int ny, int nz, T eps,
+tv_grad_kernel(const double* __restrict__ x, T* __restrict__ g, int nx, int ny, int nz, T eps,
                double* partials, unsigned* ticket, double* gnorm2, double* phi) {
     const int64_t sxy = (int64_t)nx * ny, V = sxy * nz;
     double acc[2] = {0.0, 0.0};
@@ -28,65 +30,64 @@ tv_grad_kernel(const T* __restrict__ x, T* __restrict__ g, int nx, int ny, int n
         const int64_t t = p / nx;
         const int iy = (int)(t % ny), iz = (int)(t / ny);
         const bool hx = ix + 1 < nx, hy = iy + 1 < ny, hz = iz + 1 < nz;
-        const T xc = __ldg(x + p);
-        const T xpx = hx ? __ldg(x + p + 1) : xc;
-        const T xpy = hy ? __ldg(x + p + nx) : xc;
-        const T xpz = hz ? __ldg(x + p + sxy) : xc;
-        const T dx = xpx - xc, dy = xpy - xc, dz = xpz - xc;
+        const double xc = __ldg(x + p);
+        const double ex = hx ? __ldg(x + p + 1) - xc : 0.0;
+        const double ey = hy ? __ldg(x + p + nx) - xc : 0.0;
+        const double ez = hz ? __ldg(x + p + sxy) - xc : 0.0;
+        const T dx = (T)ex, dy = (T)ey, dz = (T)ez;
         const T D = sqrt(eps + (dx * dx + dy * dy + dz * dz));
         T gq = (D > (T)0) ? -(dx + dy + dz) / D : (T)0;
         if (ix > 0) {
-            const T xm = __ldg(x + p - 1);
-            const T a = xc - xm;
-            const T b = hy ? __ldg(x + p - 1 + nx) - xm : (T)0;
-            const T c = hz ? __ldg(x + p - 1 + sxy) - xm : (T)0;
+            const double xm = __ldg(x + p - 1);
+            const T a = (T)(xc - xm);
+            const T b = hy ? (T)(__ldg(x + p - 1 + nx) - xm) : (T)0;
+            const T c = hz ? (T)(__ldg(x + p - 1 + sxy) - xm) : (T)0;
             const T Dm = sqrt(eps + (a * a + b * b + c * c));
             if (Dm > (T)0) gq += a / Dm;
         }
         if (iy > 0) {
-            const T xm = __ldg(x + p - nx);
-            const T a = xc - xm;
-            const T b = hx ? __ldg(x + p - nx + 1) - xm : (T)0;
-            const T c = hz ? __ldg(x + p - nx + sxy) - xm : (T)0;
+            const double xm = __ldg(x + p - nx);
+            const T a = (T)(xc - xm);
+            const T b = hx ? (T)(__ldg(x + p - nx + 1) - xm) : (T)0;
+            const T c = hz ? (T)(__ldg(x + p - nx + sxy) - xm) : (T)0;
             const T Dm = sqrt(eps + (a * a + b * b + c * c));
             if (Dm > (T)0) gq += a / Dm;
         }
         if (iz > 0) {
-            const T xm = __ldg(x + p - sxy);
-            const T a = xc - xm;
-            const T b = hx ? __ldg(x + p - sxy + 1) - xm : (T)0;
-            const T c = hy ? __ldg(x + p - sxy + nx) - xm : (T)0;
+            const double xm = __ldg(x + p - sxy);
+            const T a = (T)(xc - xm);
+            const T b = hx ? (T)(__ldg(x + p - sxy + 1) - xm) : (T)0;
+            const T c = hy ? (T)(__ldg(x + p - sxy + nx) - xm) : (T)0;
             const T Dm = sqrt(eps + (a * a + b * b + c * c));
             if (Dm > (T)0) gq += a / Dm;
         }
         g[p] = gq;
         acc[0] += (double)gq * (double)gq;
-        if (phi) {
-            const double ex = (double)xpx - (double)xc, ey = (double)xpy - (double)xc, ez = (double)xpz - (double)xc;
-            acc[1] += sqrt(ex * ex + ey * ey + ez * ez);
-        }
+        if (phi) acc[1] += sqrt(ex * ex + ey * ey + ez * ez);
     }
     double* const outs[2] = {gnorm2, phi};
     grid_reduce<2>(acc, partials, ticket, outs);
 }
 
-// phi_0(z), z = x - sc*g (z = x if g is null), FP64 per-voxel terms from the T values.
+// phi_0(z), z = x - sc*g (z = x if g is null), FP64 from the master image.
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
-tv_value_kernel(const T* __restrict__ x, const T* __restrict__ g, const double* gnorm2, double beta, int nx, int ny,
-                int nz, double* partials, unsigned* ticket, double* phi, const double* phi_ref, int* accept) {
+tv_value_kernel(const double* __restrict__ x, const T* __restrict__ g, const double* gnorm2, double beta, int nx,
+                int ny, int nz, double* partials, unsigned* ticket, double* phi, const double* phi_ref, int* accept) {
     const int64_t sxy = (int64_t)nx * ny, V = sxy * nz;
-    const T sc = g ? step_scale<T>(beta, gnorm2) : (T)0;
+    const double sc = g ? step_scale(beta, gnorm2) : 0.0;
     double acc[1] = {0.0};
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < V; p += (int64_t)gridDim.x * blockDim.x) {
         const int ix = (int)(p % nx);
         const int64_t t = p / nx;
         const int iy = (int)(t % ny), iz = (int)(t / ny);
-        auto zat = [&](int64_t q) -> T { return g ? perturbed(__ldg(x + q), sc, __ldg(g + q)) : __ldg(x + q); };
-        const T zc = zat(p);
-        const double ex = (ix + 1 < nx) ? (double)zat(p + 1) - (double)zc : 0.0;
-        const double ey = (iy + 1 < ny) ? (double)zat(p + nx) - (double)zc : 0.0;
-        const double ez = (iz + 1 < nz) ? (double)zat(p + sxy) - (double)zc : 0.0;
+        auto zat = [&](int64_t q) -> double {
+            return g ? perturbed(__ldg(x + q), sc, (double)__ldg(g + q)) : __ldg(x + q);
+        };
+        const double zc = zat(p);
+        const double ex = (ix + 1 < nx) ? zat(p + 1) - zc : 0.0;
+        const double ey = (iy + 1 < ny) ? zat(p + nx) - zc : 0.0;
+        const double ez = (iz + 1 < nz) ? zat(p + sxy) - zc : 0.0;
         acc[0] += sqrt(ex * ex + ey * ey + ez * ez);
     }
     double* const outs[1] = {phi};
@@ -98,13 +99,17 @@ tv_value_kernel(const T* __restrict__ x, const T* __restrict__ g, const double* 
     }
 }
 
+// x <- x - sc*g on the master image (and its FP32 gather copy when present)
 template <typename T>
-__global__ void tv_apply_kernel(T* __restrict__ x, const T* __restrict__ g, const double* gnorm2, double beta,
-                                const int* accept, int64_t V) {
+__global__ void tv_apply_kernel(double* __restrict__ x, float* __restrict__ x32, const T* __restrict__ g,
+                                const double* gnorm2, double beta, const int* accept, int64_t V) {
     if (accept && *accept == 0) return;
-    const T sc = step_scale<T>(beta, gnorm2);
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < V; p += (int64_t)gridDim.x * blockDim.x)
-        x[p] = perturbed(x[p], sc, g[p]);
+    const double sc = step_scale(beta, gnorm2);
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < V; p += (int64_t)gridDim.x * blockDim.x) {
+        const double z = perturbed(x[p], sc, (double)g[p]);
+        x[p] = z;
+        if (x32) x32[p] = (float)z;
+    }
 }
 
 static int g_sm_count = 0;
@@ -118,35 +123,35 @@ static int sm_count() {
     return g_sm_count;
 }
 
-cudaError_t k_tv_grad(int cdt, const void* x, void* g, int nx, int ny, int nz, double eps, RedScratch r,
+cudaError_t k_tv_grad(int cdt, const double* x, void* g, int nx, int ny, int nz, double eps, RedScratch r,
                       double* gnorm2, double* phi, cudaStream_t s) {
     if (cdt == F64)
-        tv_grad_kernel<double><<<r.grid, kRedThreads, 0, s>>>((const double*)x, (double*)g, nx, ny, nz, eps,
-                                                              r.partials, r.ticket, gnorm2, phi);
+        tv_grad_kernel<double><<<r.grid, kRedThreads, 0, s>>>(x, (double*)g, nx, ny, nz, eps, r.partials, r.ticket,
+                                                              gnorm2, phi);
     else
-        tv_grad_kernel<float><<<r.grid, kRedThreads, 0, s>>>((const float*)x, (float*)g, nx, ny, nz, (float)eps,
-                                                             r.partials, r.ticket, gnorm2, phi);
+        tv_grad_kernel<float><<<r.grid, kRedThreads, 0, s>>>(x, (float*)g, nx, ny, nz, (float)eps, r.partials,
+                                                             r.ticket, gnorm2, phi);
     return cudaGetLastError();
 }
 
-cudaError_t k_tv_value(int cdt, const void* x, const void* g, const double* gnorm2, double beta, int nx, int ny,
+cudaError_t k_tv_value(int cdt, const double* x, const void* g, const double* gnorm2, double beta, int nx, int ny,
                        int nz, RedScratch r, double* phi, const double* phi_ref, int* accept, cudaStream_t s) {
     if (cdt == F64)
-        tv_value_kernel<double><<<r.grid, kRedThreads, 0, s>>>((const double*)x, (const double*)g, gnorm2, beta, nx,
-                                                               ny, nz, r.partials, r.ticket, phi, phi_ref, accept);
+        tv_value_kernel<double><<<r.grid, kRedThreads, 0, s>>>(x, (const double*)g, gnorm2, beta, nx, ny, nz,
+                                                               r.partials, r.ticket, phi, phi_ref, accept);
     else
-        tv_value_kernel<float><<<r.grid, kRedThreads, 0, s>>>((const float*)x, (const float*)g, gnorm2, beta, nx, ny,
-                                                              nz, r.partials, r.ticket, phi, phi_ref, accept);
+        tv_value_kernel<float><<<r.grid, kRedThreads, 0, s>>>(x, (const float*)g, gnorm2, beta, nx, ny, nz,
+                                                              r.partials, r.ticket, phi, phi_ref, accept);
     return cudaGetLastError();
 }
 
-cudaError_t k_tv_apply(int cdt, void* x, const void* g, const double* gnorm2, double beta, const int* accept,
-                       int64_t V, cudaStream_t s) {
+cudaError_t k_tv_apply(int cdt, double* x, float* x32, const void* g, const double* gnorm2, double beta,
+                       const int* accept, int64_t V, cudaStream_t s) {
     const int grid = red_grid(V, sm_count());
     if (cdt == F64)
-        tv_apply_kernel<double><<<grid, kRedThreads, 0, s>>>((double*)x, (const double*)g, gnorm2, beta, accept, V);
+        tv_apply_kernel<double><<<grid, kRedThreads, 0, s>>>(x, x32, (const double*)g, gnorm2, beta, accept, V);
     else
-        tv_apply_kernel<float><<<grid, kRedThreads, 0, s>>>((float*)x, (const float*)g, gnorm2, beta, accept, V);
+        tv_apply_kernel<float><<<grid, kRedThreads, 0, s>>>(x, x32, (const float*)g, gnorm2, beta, accept, V);
     return cudaGetLastError();
 }
 

@@ -101,9 +101,12 @@ struct ntvs_ctx {
     void* inv_s = nullptr;
     int lpr = 32;
     int drop_grid = 1;
+    int apply_grid = 1;
 
-    // image and scratch
-    void* x = nullptr;
+    // image and scratch: x is the FP64 master image; x32 its FP32 copy gathered by the
+    // FP32-path DROP kernels (null on the FP64 path)
+    double* x = nullptr;
+    float* x32 = nullptr;
     void* delta = nullptr;
     void* g = nullptr;
     RedScratch red{nullptr, nullptr, 1};
@@ -146,6 +149,7 @@ struct ntvs_ctx {
         dev_free(inv_norm2);
         dev_free(inv_s);
         dev_free(x);
+        dev_free(x32);
         dev_free(delta);
         dev_free(g);
         dev_free(resid);
@@ -255,7 +259,7 @@ int checked_try(ntvs_ctx* c, double beta, int* acc) {
                           c->dscal + 1, c->daccept, c->stream);
     }));
     CUDA_TRY(timed_launch(c, KIND_TV, [&] {
-        return k_tv_apply(c->cdt, c->x, c->g, c->dscal + 0, beta, c->daccept, c->V, c->stream);
+        return k_tv_apply(c->cdt, c->x, c->x32, c->g, c->dscal + 0, beta, c->daccept, c->V, c->stream);
     }));
     CUDA_TRY(cudaMemcpyAsync(c->hint, c->daccept, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -272,7 +276,7 @@ int perturb_steps(ntvs_ctx* c, int64_t* ell_io) {
         if (!c->p.tv_check) {
             TRY(launch_grad(c, false));
             CUDA_TRY(timed_launch(c, KIND_TV, [&] {
-                return k_tv_apply(c->cdt, c->x, c->g, c->dscal + 0, beta, nullptr, c->V, c->stream);
+                return k_tv_apply(c->cdt, c->x, c->x32, c->g, c->dscal + 0, beta, nullptr, c->V, c->stream);
             }));
             ell += 1;
             tries = 1;
@@ -312,7 +316,7 @@ int drop_block(ntvs_ctx* c, int t) {
     a.inv_norm2 = c->inv_norm2;
     a.r0 = r0;
     a.r1 = r1;
-    a.x = c->x;
+    a.x = (c->cdt == F64) ? (const void*)c->x : (const void*)c->x32;
     a.delta = c->delta;
     a.lambda = c->p.lambda;
     a.resid_ss = c->resid + t;
@@ -322,8 +326,8 @@ int drop_block(ntvs_ctx* c, int t) {
     a.grid = c->drop_grid;
     CUDA_TRY(timed_launch(c, KIND_DROP, [&] { return k_drop_block(a, c->stream); }));
     CUDA_TRY(timed_launch(c, KIND_APPLY, [&] {
-        return k_drop_apply(c->cdt, c->x, c->delta, (const char*)c->inv_s + (size_t)t * c->V * c->csz(), c->V,
-                            c->stream);
+        return k_drop_apply(c->cdt, c->x, c->x32, c->delta, (const char*)c->inv_s + (size_t)t * c->V * c->csz(),
+                            c->V, c->apply_grid, c->stream);
     }));
     return NTVS_OK;
 }
@@ -333,23 +337,24 @@ int drop_sweep(ntvs_ctx* c) {
     return NTVS_OK;
 }
 
-int copy_image_out(ntvs_ctx* c, const void* src, void* out, int dtype, int mem_kind) {
+// copy V values of device type sdt into `out` (dtype F64/F32, host or device)
+int copy_image_out(ntvs_ctx* c, const void* src, int sdt, void* out, int dtype, int mem_kind) {
     if (dtype != NTVS_F64 && dtype != NTVS_F32) return fail(NTVS_ERR_ARG, "image dtype must be NTVS_F64 or NTVS_F32");
     if (!out && c->V) return fail(NTVS_ERR_ARG, "null output");
     if (mem_kind == NTVS_MEM_DEVICE) {
-        CUDA_TRY(k_convert(src, c->cdt, out, dtype, c->V, c->stream));
+        CUDA_TRY(k_convert(src, sdt, out, dtype, c->V, c->stream));
         return NTVS_OK;
     }
     if (mem_kind != NTVS_MEM_HOST) return fail(NTVS_ERR_ARG, "bad mem_kind");
-    if (dtype == c->cdt) {
-        CUDA_TRY(cudaMemcpyAsync(out, src, (size_t)c->V * c->csz(), cudaMemcpyDeviceToHost, c->stream));
+    if (dtype == sdt) {
+        CUDA_TRY(cudaMemcpyAsync(out, src, (size_t)c->V * dt_size(sdt), cudaMemcpyDeviceToHost, c->stream));
         CUDA_TRY(cudaStreamSynchronize(c->stream));
         return NTVS_OK;
     }
-    std::vector<unsigned char> tmp((size_t)c->V * c->csz());
+    std::vector<unsigned char> tmp((size_t)c->V * dt_size(sdt));
     CUDA_TRY(cudaMemcpyAsync(tmp.data(), src, tmp.size(), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
-    if (c->cdt == NTVS_F64) {
+    if (sdt == NTVS_F64) {
         const double* s = (const double*)tmp.data();
         float* d = (float*)out;
         for (int64_t j = 0; j < c->V; ++j) d[j] = (float)s[j];
@@ -532,11 +537,13 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
     dev_free(cnt);
 
     // image state
-    TRY(dev_alloc(&c->x, csz * (size_t)V, "x"));
+    TRY(dev_alloc(&c->x, sizeof(double) * (size_t)V, "x"));
+    if (c->cdt == F32) TRY(dev_alloc(&c->x32, sizeof(float) * (size_t)V, "x32"));
     TRY(dev_alloc(&c->delta, csz * (size_t)V, "delta"));
     TRY(dev_alloc(&c->g, csz * (size_t)V, "g"));
     TRY(dev_alloc(&c->resid, sizeof(double) * (size_t)c->B, "residuals"));
-    CUDA_TRY(cudaMemsetAsync(c->x, 0, csz * (size_t)V, st));
+    CUDA_TRY(cudaMemsetAsync(c->x, 0, sizeof(double) * (size_t)V, st));
+    if (c->x32) CUDA_TRY(cudaMemsetAsync(c->x32, 0, sizeof(float) * (size_t)V, st));
     CUDA_TRY(cudaMemsetAsync(c->delta, 0, csz * (size_t)V, st));
     CUDA_TRY(cudaMemsetAsync(c->g, 0, csz * (size_t)V, st));
     CUDA_TRY(cudaMemsetAsync(c->resid, 0, sizeof(double) * (size_t)c->B, st));
@@ -545,6 +552,10 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
     const double mean = M ? (double)nnz / (double)M : 0.0;
     c->lpr = mean <= 12.0 ? 4 : mean <= 40.0 ? 8 : mean <= 120.0 ? 16 : 32;
     c->drop_grid = c->sms * 8;
+    {
+        const int64_t need = (V + 255) / 256;
+        c->apply_grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)c->sms * 8));
+    }
     c->red.grid = red_grid(V, c->sms);
 
     c->k = 0;
@@ -576,34 +587,27 @@ int ntvs_set_image(ntvs_ctx* c, const void* x, int dtype, int mem_kind) {
     if (dtype != NTVS_F64 && dtype != NTVS_F32) return fail(NTVS_ERR_ARG, "image dtype must be NTVS_F64 or NTVS_F32");
     if (!x) return fail(NTVS_ERR_ARG, "null image");
     if (mem_kind == NTVS_MEM_DEVICE) {
-        CUDA_TRY(k_convert(x, dtype, c->x, c->cdt, c->V, c->stream));
-        return NTVS_OK;
-    }
-    if (mem_kind != NTVS_MEM_HOST) return fail(NTVS_ERR_ARG, "bad mem_kind");
-    if (dtype == c->cdt) {
-        CUDA_TRY(cudaMemcpyAsync(c->x, x, (size_t)c->V * c->csz(), cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(k_convert(x, dtype, c->x, NTVS_F64, c->V, c->stream));
+    } else if (mem_kind != NTVS_MEM_HOST) {
+        return fail(NTVS_ERR_ARG, "bad mem_kind");
+    } else if (dtype == NTVS_F64) {
+        CUDA_TRY(cudaMemcpyAsync(c->x, x, (size_t)c->V * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
     } else {
-        std::vector<unsigned char> tmp((size_t)c->V * c->csz());
-        if (c->cdt == NTVS_F64) {
-            const float* s = (const float*)x;
-            double* d = (double*)tmp.data();
-            for (int64_t j = 0; j < c->V; ++j) d[j] = s[j];
-        } else {
-            const double* s = (const double*)x;
-            float* d = (float*)tmp.data();
-            for (int64_t j = 0; j < c->V; ++j) d[j] = (float)s[j];
-        }
-        CUDA_TRY(cudaMemcpyAsync(c->x, tmp.data(), tmp.size(), cudaMemcpyHostToDevice, c->stream));
+        std::vector<double> tmp((size_t)c->V);
+        const float* s = (const float*)x;
+        for (int64_t j = 0; j < c->V; ++j) tmp[j] = s[j];
+        CUDA_TRY(cudaMemcpyAsync(c->x, tmp.data(), tmp.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
         CUDA_TRY(cudaStreamSynchronize(c->stream));
     }
-    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (c->x32) CUDA_TRY(k_convert(c->x, NTVS_F64, c->x32, NTVS_F32, c->V, c->stream));
     return NTVS_OK;
 }
 
 int ntvs_get_image(ntvs_ctx* c, void* out, int dtype, int mem_kind) {
     TRY(use_device(c));
     TRY(need_system(c));
-    return copy_image_out(c, c->x, out, dtype, mem_kind);
+    return copy_image_out(c, c->x, NTVS_F64, out, dtype, mem_kind);
 }
 
 int ntvs_run(ntvs_ctx* c, int k_iters) {
@@ -745,7 +749,7 @@ int ntvs_tv_gradient(ntvs_ctx* c, void* g_out, int dtype, int mem_kind, double* 
     TRY(use_device(c));
     TRY(need_system(c));
     TRY(launch_grad(c, false));
-    if (g_out) TRY(copy_image_out(c, c->g, g_out, dtype, mem_kind));
+    if (g_out) TRY(copy_image_out(c, c->g, c->cdt, g_out, dtype, mem_kind));
     if (gnorm) {
         CUDA_TRY(cudaMemcpyAsync(c->hscal, c->dscal, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -759,7 +763,7 @@ int ntvs_perturb(ntvs_ctx* c, double beta) {
     TRY(need_system(c));
     TRY(launch_grad(c, false));
     CUDA_TRY(timed_launch(c, KIND_TV, [&] {
-        return k_tv_apply(c->cdt, c->x, c->g, c->dscal + 0, beta, nullptr, c->V, c->stream);
+        return k_tv_apply(c->cdt, c->x, c->x32, c->g, c->dscal + 0, beta, nullptr, c->V, c->stream);
     }));
     return NTVS_OK;
 }

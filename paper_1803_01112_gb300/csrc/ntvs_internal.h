@@ -42,16 +42,18 @@ struct RedScratch {
     int grid;
 };
 
+// The image x is always the FP64 master copy; g and the stencil arithmetic use cdt.
 // g = grad phi_eps(x); *gnorm2 = ||g||^2 (FP64); if phi != nullptr also *phi = phi_0(x).
-cudaError_t k_tv_grad(int cdt, const void* x, void* g, int nx, int ny, int nz, double eps, RedScratch r,
+cudaError_t k_tv_grad(int cdt, const double* x, void* g, int nx, int ny, int nz, double eps, RedScratch r,
                       double* gnorm2, double* phi, cudaStream_t s);
 // *phi = phi_0(z), z = x - sc*g with sc = beta/sqrt(*gnorm2) (z = x when g == nullptr or
 // gnorm2 == 0).  If phi_ref != nullptr, *accept = (*phi <= *phi_ref).
-cudaError_t k_tv_value(int cdt, const void* x, const void* g, const double* gnorm2, double beta, int nx, int ny,
+cudaError_t k_tv_value(int cdt, const double* x, const void* g, const double* gnorm2, double beta, int nx, int ny,
                        int nz, RedScratch r, double* phi, const double* phi_ref, int* accept, cudaStream_t s);
-// x <- x - sc*g (sc as in k_tv_value); skipped when accept != nullptr and *accept == 0.
-cudaError_t k_tv_apply(int cdt, void* x, const void* g, const double* gnorm2, double beta, const int* accept,
-                       int64_t V, cudaStream_t s);
+// x <- x - sc*g (sc as in k_tv_value), x32 (may be null) <- (float)x; skipped when
+// accept != nullptr and *accept == 0.
+cudaError_t k_tv_apply(int cdt, double* x, float* x32, const void* g, const double* gnorm2, double beta,
+                       const int* accept, int64_t V, cudaStream_t s);
 
 // ------------------------------------------------------------------ DROP
 struct DropArgs {
@@ -61,7 +63,7 @@ struct DropArgs {
     const void* b;         // compute type
     const void* inv_norm2; // compute type
     int64_t r0, r1;
-    const void* x;         // compute type
+    const void* x;         // gather image: FP64 master (F64 path) or its FP32 copy (F32 path)
     void* delta;           // compute type, accumulates lambda * sum_i a_ij r_i
     double lambda;
     double* resid_ss;      // += sum_i (b_i - <a_i,x>)^2
@@ -70,8 +72,9 @@ struct DropArgs {
     int grid;
 };
 cudaError_t k_drop_block(const DropArgs& a, cudaStream_t s);
-// x_j += delta_j * inv_s_j ; delta_j = 0
-cudaError_t k_drop_apply(int cdt, void* x, void* delta, const void* inv_s, int64_t V, cudaStream_t s);
+// x_j += delta_j * inv_s_j on the FP64 master (x32_j <- (float)x_j when x32 != null); delta_j = 0
+cudaError_t k_drop_apply(int cdt, double* x, float* x32, void* delta, const void* inv_s, int64_t V, int grid,
+                         cudaStream_t s);
 
 // ------------------------------------------------------------------ misc
 // convert between the image's compute type and F64/F32 buffers (device to device)
