@@ -215,6 +215,27 @@ int ntvs_drop_block(ntvs_ctx* ctx, int t);
 /* One full DROP sweep P_T (blocks 0..B-1 in order). */
 int ntvs_drop_sweep(ntvs_ctx* ctx);
 
+/* ---- allocation-free entry point --------------------------------------------------- */
+
+/* phi(x) of a caller-owned image, for callers that cannot allocate device memory: code
+ * that runs inside a host callback or a framework hook where allocating is not allowed,
+ * under an allocator that must own every device allocation of the process, or with a
+ * device-memory budget fixed in advance.  The paper has no counterpart; it computes the
+ * same FP64 value as ntvs_get_tv, without a context.
+ *   x       : device pointer, V = nx*ny*nz values of `dtype` (NTVS_F64 or NTVS_F32),
+ *             layout [nz][ny][nx]; on the current CUDA device.
+ *   tv_out  : device pointer to one double, written when the stream reaches the kernel.
+ *   cuda_stream : cudaStream_t to queue on (NULL = the default stream).
+ * Nothing is allocated: the reduction scratch (4096 FP64 partials and a ticket word) is a
+ * static device array that every GPU loading the library holds until the process exits.
+ * Limit: V <= 16,777,216 voxels (4096 CTAs x 256 threads x 16 voxels); larger images
+ * return NTVS_ERR_ARG.  The first call on a device looks up the scratch's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any
+ * stream capture.  All calls share the one scratch array, which keeps the last call's
+ * contents: calls that overlap on the GPU (other streams, other threads) race and give
+ * wrong results, so order them on one stream.  Errors: NTVS_ERR_ARG, NTVS_ERR_CUDA. */
+int ntvs_tv_value_static(const void* x, int dtype, int nx, int ny, int nz, double* tv_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

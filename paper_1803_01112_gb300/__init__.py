@@ -226,6 +226,17 @@ def ntvs_drop_sweep(ctx: int) -> None:
     check(lib().ntvs_drop_sweep(ctx), "ntvs_drop_sweep")
 
 
+def ntvs_tv_value_static(x, shape, out, stream: Optional[int] = None) -> None:
+    """phi(x) into out[0] without any allocation (see include/ntvs.h): x and out are CUDA
+    tensors owned by the caller (x float64/float32 of nx*ny*nz values, out one float64)."""
+    nx, ny, nz = shape
+    ptr, kind = _ptr_kind(x)
+    optr, okind = _ptr_kind(out)
+    if kind != NTVS_MEM_DEVICE or okind != NTVS_MEM_DEVICE:
+        raise ValueError("x and out must be CUDA tensors")
+    check(lib().ntvs_tv_value_static(ptr, _dtype_code(x), nx, ny, nz, optr, stream), "ntvs_tv_value_static")
+
+
 # ----------------------------------------------------------------- object wrapper
 @dataclass
 class Params:

@@ -86,6 +86,7 @@ SIGNATURES = {
     "ntvs_perturb_checked": (ctypes.c_int, [vp, d, P(ctypes.c_int), P(d), P(d)]),
     "ntvs_drop_block": (ctypes.c_int, [vp, ctypes.c_int]),
     "ntvs_drop_sweep": (ctypes.c_int, [vp]),
+    "ntvs_tv_value_static": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]),
 }
 
 _lib = None

@@ -79,6 +79,8 @@ void dev_free(T*& p) {
 
 }  // namespace
 
+void ntvs::set_last_error(const std::string& msg) { g_err = msg; }
+
 struct ntvs_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace ntvs {
 
 // compute / storage element types (same numbering as the public NTVS_F64 ...)
@@ -77,6 +79,9 @@ cudaError_t k_drop_apply(int cdt, double* x, float* x32, void* delta, const void
                          cudaStream_t s);
 
 // ------------------------------------------------------------------ misc
+// sets the calling thread's ntvs_last_error() text
+void set_last_error(const std::string& msg);
+
 // convert between the image's compute type and F64/F32 buffers (device to device)
 cudaError_t k_convert(const void* src, int sdt, void* dst, int ddt, int64_t n, cudaStream_t s);
 
