@@ -286,6 +286,7 @@ def run_ntvs(args):
     r.load(shape, s.row_ptr, s.col, s.val, b, n_blocks=spec.n_blocks)
     r.set_params(**PARAMS)
     r.set_image(x0)
+    st0 = r.stats()
     r.run(args.warmup)
     r.sync()
     torch.cuda.synchronize(device)
@@ -320,8 +321,9 @@ def run_ntvs(args):
     avg_ms = prof["drop_block_ms"] / max(prof["drop_block_launches"], 1)
     achieved = avg_bytes / (avg_ms / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
+    kname = "drop_block_window_kernel" if st0["drop_schedule"] == 2 else "drop_block_kernel"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": ncu_traffic_per_launch(), "kernel": "drop_block_kernel",
+                "traffic": ncu_traffic_per_launch(), "kernel": kname,
                 "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": avg_bytes,
                 "avg_launch_ms": avg_ms}
     kernel_ms = {k: prof[k] / args.steps for k in ("drop_block_ms", "drop_apply_ms", "tv_ms")}
@@ -365,6 +367,8 @@ def run_ntvs(args):
                 "config": {"workload": spec.name, "grid": [spec.nx, spec.ny, spec.nz], "histories": spec.n_hist,
                            "nnz": s.nnz, "n_blocks": spec.n_blocks, **PARAMS, "tv_check": False,
                            "storage": "csr32", "l2": L2_NOTE,
+                           "drop_schedule": {1: "plain", 2: "window"}.get(st0["drop_schedule"]),
+                           "lanes_per_row": st0["lanes_per_row"],
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "kernel_ms_per_step": kernel_ms, "clocks": clk}

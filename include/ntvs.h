@@ -78,8 +78,19 @@ typedef struct {
                                     NTVS_F16 / NTVS_BF16 (FP32 arithmetic on half storage)   */
     int32_t mem_kind;            /* NTVS_MEM_HOST | NTVS_MEM_DEVICE (row_ptr, col, val, b)    */
     int32_t storage;             /* NTVS_CSR32 | NTVS_DELTA16                                 */
-    int32_t reserved;            /* 0                                                         */
+    int32_t schedule;            /* DROP kernel schedule: NTVS_SCHED_AUTO (0), NTVS_SCHED_PLAIN,
+                                    NTVS_SCHED_WINDOW (see below)                             */
 } ntvs_system;
+
+/* DROP kernel schedules.  PLAIN: rows in stored order, every scatter a global reduction.
+ * WINDOW: rows grouped at load time by the z-slice holding their middle entry; one CTA
+ * per SM accumulates its slice in shared memory (needs nx*ny*sizeof(compute type) of
+ * shared memory per CTA).  AUTO picks WINDOW when the slice fits and rows come in runs of
+ * the same slice (e.g. stored by projection angle, then slice), else PLAIN.  All give
+ * the same result up to the order of floating-point summation. */
+#define NTVS_SCHED_AUTO 0
+#define NTVS_SCHED_PLAIN 1
+#define NTVS_SCHED_WINDOW 2
 
 /* Parameters of NTVS (Sec. II-E, Appendix A/C). */
 typedef struct {
@@ -106,6 +117,8 @@ typedef struct {
     int32_t compute_dtype; /* NTVS_F64 or NTVS_F32                                       */
     double last_tv;        /* phi(x) after the last completed cycle (FP64)               */
     int64_t n_launches;    /* kernels this context has launched (all entry points)       */
+    int32_t drop_schedule; /* NTVS_SCHED_PLAIN or NTVS_SCHED_WINDOW (chosen at load)      */
+    int32_t lanes_per_row; /* lanes per row of the DROP kernel                           */
 } ntvs_stats;
 
 /* Device time of the context's kernels, measured with CUDA events recorded on the

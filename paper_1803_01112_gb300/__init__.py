@@ -86,7 +86,7 @@ def ntvs_destroy(ctx: int) -> None:
 
 
 def ntvs_load_system(ctx: int, nx: int, ny: int, nz: int, row_ptr, col, val, b, n_blocks: int = 1,
-                     block_ptr=None, storage: int = NTVS_CSR32) -> None:
+                     block_ptr=None, storage: int = NTVS_CSR32, schedule: int = 0) -> None:
     """Arrays are all numpy (host, copied) or all CUDA torch tensors (device, borrowed:
     they must stay alive while the context uses them)."""
     import_torch = _is_torch(row_ptr)
@@ -113,7 +113,7 @@ def ntvs_load_system(ctx: int, nx: int, ny: int, nz: int, row_ptr, col, val, b, 
         bp = np.ascontiguousarray(block_ptr, dtype=np.int64)
         n_blocks = bp.size - 1
     s = _ffi.ntvs_system(nx, ny, nz, n_blocks, (row_ptr.numel() if import_torch else row_ptr.size) - 1,
-                         rp, cp, vptr, bptr, None if bp is None else bp.ctypes.data, vdt, kind, storage, 0)
+                         rp, cp, vptr, bptr, None if bp is None else bp.ctypes.data, vdt, kind, storage, schedule)
     check(lib().ntvs_load_system(ctx, ctypes.byref(s)), "ntvs_load_system")
 
 
@@ -275,9 +275,10 @@ class Reconstructor:
         except Exception:
             pass
 
-    def load(self, shape, row_ptr, col, val, b, n_blocks: int = 1, block_ptr=None, storage: int = NTVS_CSR32):
+    def load(self, shape, row_ptr, col, val, b, n_blocks: int = 1, block_ptr=None, storage: int = NTVS_CSR32,
+             schedule: int = 0):
         nx, ny, nz = shape
-        ntvs_load_system(self._ctx, nx, ny, nz, row_ptr, col, val, b, n_blocks, block_ptr, storage)
+        ntvs_load_system(self._ctx, nx, ny, nz, row_ptr, col, val, b, n_blocks, block_ptr, storage, schedule)
         self._keep = (row_ptr, col, val, b) if _is_torch(row_ptr) and row_ptr.is_cuda else ()
         self.shape = (nx, ny, nz)
         self.n_blocks = (len(block_ptr) - 1) if block_ptr is not None else n_blocks

@@ -23,6 +23,7 @@ NTVS_ERR_STATE = -6
 NTVS_F64, NTVS_F32, NTVS_F16, NTVS_BF16 = 0, 1, 2, 3
 NTVS_MEM_HOST, NTVS_MEM_DEVICE = 0, 1
 NTVS_CSR32, NTVS_DELTA16 = 0, 1
+NTVS_SCHED_AUTO, NTVS_SCHED_PLAIN, NTVS_SCHED_WINDOW = 0, 1, 2
 
 ERROR_NAMES = {NTVS_ERR_ARG: "NTVS_ERR_ARG", NTVS_ERR_CSR: "NTVS_ERR_CSR", NTVS_ERR_OOM: "NTVS_ERR_OOM",
                NTVS_ERR_CUDA: "NTVS_ERR_CUDA", NTVS_ERR_TIMEOUT: "NTVS_ERR_TIMEOUT",
@@ -35,7 +36,7 @@ class ntvs_system(ctypes.Structure):
                 ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p),
                 ("b", ctypes.c_void_p), ("block_ptr", ctypes.c_void_p),
                 ("val_dtype", ctypes.c_int32), ("mem_kind", ctypes.c_int32),
-                ("storage", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("storage", ctypes.c_int32), ("schedule", ctypes.c_int32)]
 
 
 class ntvs_params(ctypes.Structure):
@@ -48,7 +49,8 @@ class ntvs_stats(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int64), ("ell_prev", ctypes.c_int64), ("n_steps", ctypes.c_int64),
                 ("n_accepted", ctypes.c_int64), ("n_tries", ctypes.c_int64), ("nnz", ctypes.c_int64),
                 ("n_rows", ctypes.c_int64), ("n_blocks", ctypes.c_int32), ("compute_dtype", ctypes.c_int32),
-                ("last_tv", ctypes.c_double), ("n_launches", ctypes.c_int64)]
+                ("last_tv", ctypes.c_double), ("n_launches", ctypes.c_int64),
+                ("drop_schedule", ctypes.c_int32), ("lanes_per_row", ctypes.c_int32)]
 
 
 class ntvs_profile(ctypes.Structure):

@@ -1,64 +1,197 @@
 // Block-DROP kernels (P_T of arXiv 1803.01112 Appendix C; DROP of ref. CEHN08, Sec. II-D).
 //
 // drop_block: for every row i of block t (all rows see the same x):
-//     d_i = <a_i, x>                    (CSR gather, x is L2-resident)
+//     d_i = <a_i, x>                    (CSR gather, x is L2/L1-resident)
 //     r_i = lambda (b_i - d_i) / ||a_i||^2
-//     delta_j += r_i a_ij               (scatter-add, fire-and-forget L2 reductions)
-//   A group of LPR lanes owns a row; the row's entries stay in registers between the
-//   dot product and the scatter, so the matrix streams from HBM exactly once.
+//     delta_j += r_i a_ij               (scatter-add)
+//   A group of LPR lanes owns a row; each lane loads VW consecutive entries per step
+//   (16-byte column and value vectors for 4-byte values), and the row's entries stay in
+//   registers between the dot product and the scatter, so the matrix streams from HBM
+//   exactly once.
+//
+//   Windowed variant (one 1024-thread CTA per SM): the CTA owns a list of row segments
+//   that share a "home" z-slice (assigned at load time), keeps delta for that slice in
+//   shared memory and scatters there with shared-memory atomics; entries outside the
+//   slice go to global memory.  When the home slice changes, and at the end, the window
+//   is flushed into delta with one global reduction per touched voxel.  This replaces
+//   ~1 global L2 atomic per matrix entry by ~0.2.
+//   Plain variant (any row order): every scatter is a global reduction.
 // drop_apply: x_j += delta_j / s_j^t (inverse counts precomputed), delta_j = 0.
 #include "common.cuh"
 
 namespace ntvs {
 
-template <typename T> __device__ __forceinline__ void red_add(T* p, T v) { atomicAdd(p, v); }
+// 4 consecutive values from an 8- or 16-byte aligned address, streamed (evict-first)
+__device__ __forceinline__ void load4(const float* p, float (&o)[4]) {
+    const float4 v = __ldcs(reinterpret_cast<const float4*>(p));
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void load4(const __half* p, float (&o)[4]) {
+    const uint2 v = __ldcs(reinterpret_cast<const uint2*>(p));
+    const __half2 h0 = *reinterpret_cast<const __half2*>(&v.x), h1 = *reinterpret_cast<const __half2*>(&v.y);
+    const float2 f0 = __half22float2(h0), f1 = __half22float2(h1);
+    o[0] = f0.x; o[1] = f0.y; o[2] = f1.x; o[3] = f1.y;
+}
+__device__ __forceinline__ void load4(const __nv_bfloat16* p, float (&o)[4]) {
+    const uint2 v = __ldcs(reinterpret_cast<const uint2*>(p));
+    const __nv_bfloat162 h0 = *reinterpret_cast<const __nv_bfloat162*>(&v.x);
+    const __nv_bfloat162 h1 = *reinterpret_cast<const __nv_bfloat162*>(&v.y);
+    const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
+    o[0] = f0.x; o[1] = f0.y; o[2] = f1.x; o[3] = f1.y;
+}
 
-// CH chunks of LPR entries per row are kept in registers; longer rows re-read the tail.
-template <typename T, typename V, int LPR, int CH>
+struct Window {
+    void* win;     // shared-memory delta of voxels [w0, w0 + W)
+    int64_t w0;
+    int W;
+};
+
+template <typename T, bool WIN>
+__device__ __forceinline__ void scatter(T* delta, const Window& w, int32_t c, T v) {
+    if (WIN) {
+        const int64_t rel = (int64_t)c - w.w0;
+        if ((uint64_t)rel < (uint64_t)w.W) {
+            atomicAdd(reinterpret_cast<T*>(w.win) + rel, v);
+            return;
+        }
+    }
+    atomicAdd(delta + c, v);
+}
+
+// One row per group of LPR lanes (all lanes of the warp call this together).
+// VW entries per lane per step from aligned addresses; CH steps held in registers.
+template <typename T, typename V, int LPR, int CH, int VW, bool WIN>
+__device__ __forceinline__ void drop_row(int64_t i, bool valid, int sub, const int64_t* __restrict__ row_ptr,
+                                         const int32_t* __restrict__ col, const V* __restrict__ val,
+                                         const T* __restrict__ b, const T* __restrict__ inv_norm2,
+                                         const T* __restrict__ x, T* __restrict__ delta, T lambda, const Window& w,
+                                         double& ss) {
+    int64_t p0 = 0, p1 = 0;
+    if (valid) { p0 = __ldg(row_ptr + i); p1 = __ldg(row_ptr + i + 1); }
+    const int64_t pa = p0 & ~(int64_t)(VW - 1);
+    int32_t c[CH][VW];
+    T a[CH][VW];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+        const int64_t q = pa + ((int64_t)u * LPR + sub) * VW;
+        if (q < p1) {
+            if constexpr (VW == 4) {
+                const int4 cv = __ldcs(reinterpret_cast<const int4*>(col + q));
+                float av[4];
+                load4(val + q, av);
+                c[u][0] = cv.x; c[u][1] = cv.y; c[u][2] = cv.z; c[u][3] = cv.w;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    a[u][e] = (T)av[e];
+                    if (q + e < p0 || q + e >= p1) c[u][e] = -1;
+                }
+            } else {
+                c[u][0] = __ldcs(col + q);
+                a[u][0] = (T)to_compute(val[q]);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < VW; ++e) { c[u][e] = -1; a[u][e] = (T)0; }
+        }
+    }
+    T acc = (T)0;
+#pragma unroll
+    for (int u = 0; u < CH; ++u)
+#pragma unroll
+        for (int e = 0; e < VW; ++e)
+            if (c[u][e] >= 0) acc += a[u][e] * __ldg(x + c[u][e]);
+    // entries beyond the register-held steps (long rows): scalar, re-read for the scatter
+    const int64_t tail0 = pa + (int64_t)CH * LPR * VW;
+    for (int64_t p = (tail0 > p0 ? tail0 : p0) + sub; p < p1; p += LPR)
+        acc += (T)to_compute(val[p]) * __ldg(x + col[p]);
+#pragma unroll
+    for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    T r = (T)0;
+    if (valid) {
+        const T res = __ldg(b + i) - acc;
+        r = lambda * res * __ldg(inv_norm2 + i);
+        if (sub == 0) ss += (double)res * (double)res;
+    }
+#pragma unroll
+    for (int u = 0; u < CH; ++u)
+#pragma unroll
+        for (int e = 0; e < VW; ++e)
+            if (c[u][e] >= 0) scatter<T, WIN>(delta, w, c[u][e], r * a[u][e]);
+    for (int64_t p = (tail0 > p0 ? tail0 : p0) + sub; p < p1; p += LPR)
+        scatter<T, WIN>(delta, w, col[p], r * (T)to_compute(val[p]));
+}
+
+// Plain variant: grid-stride over the rows of the block.
+template <typename T, typename V, int LPR, int CH, int VW>
 __global__ void __launch_bounds__(256)
 drop_block_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, const V* __restrict__ val,
                   const T* __restrict__ b, const T* __restrict__ inv_norm2, int64_t r0, int64_t r1,
                   const T* __restrict__ x, T* __restrict__ delta, T lambda, double* resid_ss) {
-    constexpr int G = 32 / LPR;   // rows per warp pass
+    constexpr int G = 32 / LPR;
     const int lane = threadIdx.x & 31;
-    const int sub = lane % LPR;
-    const int grp = lane / LPR;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const Window w{nullptr, 0, 0};
     double ss = 0.0;
     for (int64_t base = r0 + warp * G; base < r1; base += nwarps * G) {
-        const int64_t i = base + grp;
-        const bool valid = i < r1;
-        int64_t p0 = 0, p1 = 0;
-        if (valid) { p0 = __ldg(row_ptr + i); p1 = __ldg(row_ptr + i + 1); }
-        int32_t c[CH];
-        T a[CH];
-#pragma unroll
-        for (int u = 0; u < CH; ++u) {
-            const int64_t p = p0 + sub + (int64_t)u * LPR;
-            if (p < p1) { c[u] = __ldcs(col + p); a[u] = (T)to_compute(val[p]); }
-            else { c[u] = -1; a[u] = (T)0; }
-        }
-        T acc = (T)0;
-#pragma unroll
-        for (int u = 0; u < CH; ++u)
-            if (c[u] >= 0) acc += a[u] * __ldg(x + c[u]);
-        for (int64_t p = p0 + sub + (int64_t)CH * LPR; p < p1; p += LPR)
-            acc += (T)to_compute(val[p]) * __ldg(x + col[p]);
-#pragma unroll
-        for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        T r = (T)0;
-        if (valid) {
-            const T res = __ldg(b + i) - acc;
-            r = lambda * res * __ldg(inv_norm2 + i);
-            if (sub == 0) ss += (double)res * (double)res;
-        }
-#pragma unroll
-        for (int u = 0; u < CH; ++u)
-            if (c[u] >= 0) red_add(delta + c[u], r * a[u]);
-        for (int64_t p = p0 + sub + (int64_t)CH * LPR; p < p1; p += LPR)
-            red_add(delta + col[p], r * (T)to_compute(val[p]));
+        const int64_t i = base + lane / LPR;
+        drop_row<T, V, LPR, CH, VW, false>(i, i < r1, lane % LPR, row_ptr, col, val, b, inv_norm2, x, delta, lambda,
+                                           w, ss);
     }
+    __shared__ double sh[32];
+    const double tot = block_sum(ss, sh);
+    if (threadIdx.x == 0 && tot != 0.0) atomicAdd(resid_ss, tot);
+}
+
+// Windowed variant: CTA b processes segments [seg_begin[b], seg_begin[b+1]) in order.
+template <typename T>
+__device__ __forceinline__ void flush_window(T* win, int W, T* delta, int64_t w0) {
+    for (int j = threadIdx.x; j < W; j += blockDim.x) {
+        const T v = win[j];
+        if (v != (T)0) {
+            atomicAdd(delta + w0 + j, v);
+            win[j] = (T)0;
+        }
+    }
+}
+
+template <typename T, typename V, int LPR, int CH, int VW>
+__global__ void __launch_bounds__(1024, 1)
+drop_block_window_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                         const V* __restrict__ val, const T* __restrict__ b, const T* __restrict__ inv_norm2,
+                         const DropSegment* __restrict__ segs, const int32_t* __restrict__ seg_begin,
+                         int64_t slice, const T* __restrict__ x, T* __restrict__ delta, T lambda,
+                         double* resid_ss) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* win = reinterpret_cast<T*>(smem_raw);
+    const int W = (int)slice;
+    constexpr int G = 32 / LPR;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    for (int j = threadIdx.x; j < W; j += blockDim.x) win[j] = (T)0;
+    __syncthreads();
+    const int s0 = seg_begin[blockIdx.x], s1 = seg_begin[blockIdx.x + 1];
+    int cur = s0 < s1 ? segs[s0].home : 0;
+    Window w{win, (int64_t)cur * slice, W};
+    double ss = 0.0;
+    for (int s = s0; s < s1; ++s) {
+        const DropSegment sg = segs[s];
+        if (sg.home != cur) {   // uniform across the CTA
+            __syncthreads();
+            flush_window(win, W, delta, w.w0);
+            __syncthreads();
+            cur = sg.home;
+            w.w0 = (int64_t)cur * slice;
+        }
+        for (int64_t base = sg.r0 + (int64_t)warp * G; base < sg.r1; base += (int64_t)nwarps * G) {
+            const int64_t i = base + lane / LPR;
+            drop_row<T, V, LPR, CH, VW, true>(i, i < sg.r1, lane % LPR, row_ptr, col, val, b, inv_norm2, x, delta,
+                                              lambda, w, ss);
+        }
+    }
+    __syncthreads();
+    flush_window(win, W, delta, w.w0);
     __shared__ double sh[32];
     const double tot = block_sum(ss, sh);
     if (threadIdx.x == 0 && tot != 0.0) atomicAdd(resid_ss, tot);
@@ -75,35 +208,57 @@ __global__ void drop_apply_kernel(double* __restrict__ x, float* __restrict__ x3
     }
 }
 
-template <typename T, typename V, int LPR, int CH>
-static void launch_block(const DropArgs& a, cudaStream_t s) {
-    drop_block_kernel<T, V, LPR, CH><<<a.grid, 256, 0, s>>>(
-        a.row_ptr, a.col, (const V*)a.val, (const T*)a.b, (const T*)a.inv_norm2, a.r0, a.r1, (const T*)a.x,
-        (T*)a.delta, (T)a.lambda, a.resid_ss);
+// ------------------------------------------------------------------ launch
+template <typename T, typename V, int LPR, int CH, int VW>
+static cudaError_t launch_cfg(const DropArgs& a, cudaStream_t s) {
+    if (a.segs) {
+        auto kern = drop_block_window_kernel<T, V, LPR, CH, VW>;
+        const size_t smem = (size_t)a.slice * sizeof(T);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<a.grid, 1024, smem, s>>>(a.row_ptr, a.col, (const V*)a.val, (const T*)a.b, (const T*)a.inv_norm2,
+                                        a.segs, a.seg_begin, a.slice, (const T*)a.x, (T*)a.delta, (T)a.lambda,
+                                        a.resid_ss);
+    } else {
+        drop_block_kernel<T, V, LPR, CH, VW><<<a.grid, 256, 0, s>>>(
+            a.row_ptr, a.col, (const V*)a.val, (const T*)a.b, (const T*)a.inv_norm2, a.r0, a.r1, (const T*)a.x,
+            (T*)a.delta, (T)a.lambda, a.resid_ss);
+    }
+    return cudaGetLastError();
 }
 
 template <typename T, typename V>
-static cudaError_t dispatch_lpr(const DropArgs& a, cudaStream_t s) {
+static cudaError_t dispatch(const DropArgs& a, cudaStream_t s) {
+    if constexpr (sizeof(V) <= 4) {
+        if (a.vector4) {
+        switch (a.lanes_per_row) {
+            case 4: return launch_cfg<T, V, 4, 2, 4>(a, s);
+            case 8: return launch_cfg<T, V, 8, 2, 4>(a, s);
+            case 16: return launch_cfg<T, V, 16, 3, 4>(a, s);
+            case 32: return launch_cfg<T, V, 32, 3, 4>(a, s);
+            default: return cudaErrorInvalidValue;
+        }
+        }
+    }
     switch (a.lanes_per_row) {
-        case 4: launch_block<T, V, 4, 8>(a, s); break;
-        case 8: launch_block<T, V, 8, 8>(a, s); break;
-        case 16: launch_block<T, V, 16, 10>(a, s); break;
-        case 32: launch_block<T, V, 32, 12>(a, s); break;
+        case 4: return launch_cfg<T, V, 4, 8, 1>(a, s);
+        case 8: return launch_cfg<T, V, 8, 8, 1>(a, s);
+        case 16: return launch_cfg<T, V, 16, 10, 1>(a, s);
+        case 32: return launch_cfg<T, V, 32, 12, 1>(a, s);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 cudaError_t k_drop_block(const DropArgs& a, cudaStream_t s) {
     if (a.r1 <= a.r0) return cudaSuccess;
     if (a.cdt == F64) {
-        if (a.vdt != F64) return cudaErrorInvalidValue;
-        return dispatch_lpr<double, double>(a, s);
+        if (a.vdt != F64 || a.vector4) return cudaErrorInvalidValue;
+        return dispatch<double, double>(a, s);
     }
     switch (a.vdt) {
-        case F32: return dispatch_lpr<float, float>(a, s);
-        case F16: return dispatch_lpr<float, __half>(a, s);
-        case BF16: return dispatch_lpr<float, __nv_bfloat16>(a, s);
+        case F32: return dispatch<float, float>(a, s);
+        case F16: return dispatch<float, __half>(a, s);
+        case BF16: return dispatch<float, __nv_bfloat16>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -112,6 +267,22 @@ cudaError_t k_drop_apply(int cdt, double* x, float* x32, void* delta, const void
                          cudaStream_t s) {
     if (cdt == F64) drop_apply_kernel<double><<<grid, 256, 0, s>>>(x, x32, (double*)delta, (const double*)inv_s, V);
     else drop_apply_kernel<float><<<grid, 256, 0, s>>>(x, x32, (float*)delta, (const float*)inv_s, V);
+    return cudaGetLastError();
+}
+
+// home slice of each row: the z-slice of its middle entry (-1 for an empty row)
+__global__ void row_home_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int64_t M,
+                                int64_t slice, int32_t* __restrict__ home) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p0 = row_ptr[i], p1 = row_ptr[i + 1];
+        home[i] = (p1 > p0) ? (int32_t)(col[p0 + (p1 - p0) / 2] / slice) : -1;
+    }
+}
+
+cudaError_t k_row_home(const int64_t* row_ptr, const int32_t* col, int64_t M, int64_t slice, int32_t* home, int grid,
+                       cudaStream_t s) {
+    if (M <= 0) return cudaSuccess;
+    row_home_kernel<<<grid, 256, 0, s>>>(row_ptr, col, M, slice, home);
     return cudaGetLastError();
 }
 

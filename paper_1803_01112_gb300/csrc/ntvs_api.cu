@@ -104,6 +104,11 @@ struct ntvs_ctx {
     int lpr = 32;
     int drop_grid = 1;
     int apply_grid = 1;
+    bool vector4 = false;
+    int schedule = NTVS_SCHED_PLAIN;
+    DropSegment* segs = nullptr;       // windowed schedule: all blocks' segments
+    int32_t* seg_begin = nullptr;      // [B][win_grid + 1]
+    int win_grid = 0;
 
     // image and scratch: x is the FP64 master image; x32 its FP32 copy gathered by the
     // FP32-path DROP kernels (null on the FP64 path)
@@ -150,6 +155,9 @@ struct ntvs_ctx {
         own_row_ptr = own_col = own_val = own_b = false;
         dev_free(inv_norm2);
         dev_free(inv_s);
+        dev_free(segs);
+        dev_free(seg_begin);
+        schedule = NTVS_SCHED_PLAIN;
         dev_free(x);
         dev_free(x32);
         dev_free(delta);
@@ -326,6 +334,15 @@ int drop_block(ntvs_ctx* c, int t) {
     a.cdt = c->cdt;
     a.lanes_per_row = c->lpr;
     a.grid = c->drop_grid;
+    a.vector4 = c->vector4;
+    a.segs = nullptr;
+    a.seg_begin = nullptr;
+    a.slice = (int64_t)c->nx * c->ny;
+    if (c->schedule == NTVS_SCHED_WINDOW) {
+        a.segs = c->segs;
+        a.seg_begin = c->seg_begin + (size_t)t * (c->win_grid + 1);
+        a.grid = c->win_grid;
+    }
     CUDA_TRY(timed_launch(c, KIND_DROP, [&] { return k_drop_block(a, c->stream); }));
     CUDA_TRY(timed_launch(c, KIND_APPLY, [&] {
         return k_drop_apply(c->cdt, c->x, c->x32, c->delta, (const char*)c->inv_s + (size_t)t * c->V * c->csz(),
@@ -369,6 +386,92 @@ int copy_image_out(ntvs_ctx* c, const void* src, int sdt, void* out, int dtype, 
 }
 
 }  // namespace
+
+// ---- DROP schedule planning (load time) ------------------------------------------------
+// Rows are cut into chunks of at most kChunkRows consecutive rows with the same home
+// slice; per block, chunks are ordered by home slice and dealt to the win_grid CTAs in
+// contiguous runs of about equal row count.  Consecutive chunks of one CTA with the same
+// home slice and adjacent rows merge into one segment.
+constexpr int kChunkRows = 64;
+constexpr double kMinMeanRun = 8.0;
+
+static int plan_schedule(ntvs_ctx* c, int requested) {
+    c->schedule = NTVS_SCHED_PLAIN;
+    if (requested == NTVS_SCHED_PLAIN || c->M == 0) return NTVS_OK;
+    const int64_t slice = (int64_t)c->nx * c->ny;
+    int optin = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    const int64_t need = slice * (int64_t)c->csz();
+    if (need + 1024 > optin) {
+        if (requested == NTVS_SCHED_WINDOW)
+            return fail(NTVS_ERR_ARG, "windowed schedule: an nx*ny slice needs " + std::to_string(need) +
+                                          " bytes of shared memory, the device allows " + std::to_string(optin));
+        return NTVS_OK;
+    }
+    // home slice of every row
+    int32_t* dhome = nullptr;
+    TRY(dev_alloc(&dhome, sizeof(int32_t) * (size_t)c->M, "row home slices"));
+    std::vector<int32_t> home((size_t)c->M);
+    cudaError_t e = k_row_home(c->row_ptr, c->col, c->M, slice, dhome, c->sms * 8, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(home.data(), dhome, sizeof(int32_t) * home.size(), cudaMemcpyDeviceToHost,
+                                              c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(dhome);
+    if (e != cudaSuccess) return fail(NTVS_ERR_CUDA, cuda_msg("row home slices", e));
+    int32_t last = 0;
+    for (auto& h : home) {   // empty rows join their predecessor's run
+        if (h < 0) h = last;
+        last = h;
+    }
+    // mean run length of equal home slices in stored order
+    int64_t runs = 1;
+    for (int64_t i = 1; i < c->M; ++i) runs += home[i] != home[i - 1];
+    const double mean_run = (double)c->M / (double)runs;
+    if (requested == NTVS_SCHED_AUTO && mean_run < kMinMeanRun) return NTVS_OK;
+
+    const int G = c->sms;
+    struct Chunk { int64_t r0, r1; int32_t home; };
+    std::vector<DropSegment> segs;
+    std::vector<int32_t> begin((size_t)c->B * (G + 1), 0);
+    std::vector<Chunk> ch;
+    for (int t = 0; t < c->B; ++t) {
+        const int64_t r0 = c->block_ptr[t], r1 = c->block_ptr[t + 1];
+        ch.clear();
+        for (int64_t i = r0; i < r1;) {
+            const int32_t h = home[i];
+            int64_t j = i + 1;
+            while (j < r1 && j - i < kChunkRows && home[j] == h) ++j;
+            ch.push_back({i, j, h});
+            i = j;
+        }
+        std::stable_sort(ch.begin(), ch.end(), [](const Chunk& a, const Chunk& b) { return a.home < b.home; });
+        int32_t* bg = begin.data() + (size_t)t * (G + 1);
+        const int64_t total = r1 - r0;
+        int cta = 0;
+        bg[0] = (int32_t)segs.size();
+        int64_t cum = 0;
+        for (const Chunk& k : ch) {
+            const int owner = total > 0 ? (int)std::min<int64_t>(G - 1, (cum * G) / total) : 0;
+            while (cta < owner) bg[++cta] = (int32_t)segs.size();
+            const bool own_last = (int64_t)segs.size() > bg[cta];
+            if (own_last && segs.back().home == k.home && segs.back().r1 == k.r0) segs.back().r1 = k.r1;
+            else segs.push_back({k.r0, k.r1, k.home, 0});
+            cum += k.r1 - k.r0;
+        }
+        while (cta < G) bg[++cta] = (int32_t)segs.size();
+    }
+    if (segs.size() > (size_t)INT32_MAX) return NTVS_OK;
+    TRY(dev_alloc(&c->segs, sizeof(DropSegment) * std::max<size_t>(segs.size(), 1), "DROP segments"));
+    TRY(dev_alloc(&c->seg_begin, sizeof(int32_t) * begin.size(), "DROP segment index"));
+    CUDA_TRY(cudaMemcpyAsync(c->segs, segs.data(), sizeof(DropSegment) * segs.size(), cudaMemcpyHostToDevice,
+                             c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->seg_begin, begin.data(), sizeof(int32_t) * begin.size(), cudaMemcpyHostToDevice,
+                             c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->win_grid = G;
+    c->schedule = NTVS_SCHED_WINDOW;
+    return NTVS_OK;
+}
 
 // =========================================================================== C ABI
 extern "C" {
@@ -457,6 +560,7 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
     if (s->val_dtype < NTVS_F64 || s->val_dtype > NTVS_BF16) return fail(NTVS_ERR_ARG, "bad val_dtype");
     if (s->mem_kind != NTVS_MEM_HOST && s->mem_kind != NTVS_MEM_DEVICE) return fail(NTVS_ERR_ARG, "bad mem_kind");
     if (s->storage != NTVS_CSR32) return fail(NTVS_ERR_ARG, "storage: only NTVS_CSR32 is supported");
+    if (s->schedule < NTVS_SCHED_AUTO || s->schedule > NTVS_SCHED_WINDOW) return fail(NTVS_ERR_ARG, "bad schedule");
     if (!s->row_ptr) return fail(NTVS_ERR_ARG, "null row_ptr");
     const int64_t M = s->n_rows;
     if (M > 0 && (!s->b)) return fail(NTVS_ERR_ARG, "null b");
@@ -554,6 +658,9 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
     const double mean = M ? (double)nnz / (double)M : 0.0;
     c->lpr = mean <= 12.0 ? 4 : mean <= 40.0 ? 8 : mean <= 120.0 ? 16 : 32;
     c->drop_grid = c->sms * 8;
+    c->vector4 = c->cdt == F32 && ((uintptr_t)c->col % 16 == 0) &&
+                 ((uintptr_t)c->val % (c->vdt == F32 ? 16 : 8) == 0);
+    TRY(plan_schedule(c, s->schedule));
     {
         const int64_t need = (V + 255) / 256;
         c->apply_grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)c->sms * 8));
@@ -669,6 +776,8 @@ int ntvs_get_stats(ntvs_ctx* c, ntvs_stats* st) {
     st->compute_dtype = c->cdt;
     st->last_tv = NAN;
     st->n_launches = c->n_launches;
+    st->drop_schedule = c->schedule;
+    st->lanes_per_row = c->lpr;
     if (c->k > 0 && c->tvhist) {
         CUDA_TRY(cudaMemcpyAsync(c->hscal, c->tvhist + (c->k - 1), sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         CUDA_TRY(cudaStreamSynchronize(c->stream));

@@ -58,6 +58,12 @@ cudaError_t k_tv_apply(int cdt, double* x, float* x32, const void* g, const doub
                        const int* accept, int64_t V, cudaStream_t s);
 
 // ------------------------------------------------------------------ DROP
+// A run of consecutive rows [r0, r1) whose entries lie mostly in z-slice `home`.
+struct DropSegment {
+    int64_t r0, r1;
+    int32_t home, pad;
+};
+
 struct DropArgs {
     const int64_t* row_ptr;
     const int32_t* col;
@@ -72,8 +78,17 @@ struct DropArgs {
     int vdt, cdt;
     int lanes_per_row;     // 4, 8, 16 or 32
     int grid;
+    bool vector4;          // col/val 16-byte (8-byte for 2-byte values) aligned: 4-entry vector loads
+    // windowed schedule (segs != nullptr): grid CTAs of 1024 threads, CTA c takes segments
+    // [seg_begin[c], seg_begin[c+1]); shared window of one z-slice (slice = nx*ny voxels)
+    const DropSegment* segs;
+    const int32_t* seg_begin;
+    int64_t slice;
 };
 cudaError_t k_drop_block(const DropArgs& a, cudaStream_t s);
+// home[i] = z-slice of the middle entry of row i (-1 for an empty row)
+cudaError_t k_row_home(const int64_t* row_ptr, const int32_t* col, int64_t M, int64_t slice, int32_t* home, int grid,
+                       cudaStream_t s);
 // x_j += delta_j * inv_s_j on the FP64 master (x32_j <- (float)x_j when x32 != null); delta_j = 0
 cudaError_t k_drop_apply(int cdt, double* x, float* x32, void* delta, const void* inv_s, int64_t V, int grid,
                          cudaStream_t s);

@@ -136,6 +136,69 @@ def test_drop_block_and_sweep(dtype, curved):
     np.testing.assert_allclose(res, ss, rtol=1e-10 if dtype == np.float64 else 1e-4)
 
 
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("schedule", ["plain", "window", "auto"])
+def test_drop_schedules_match_oracle(dtype, schedule):
+    """Both DROP kernel schedules (stored-order rows with global reductions; rows grouped by
+    home z-slice with a shared-memory window) give the oracle's sweep."""
+    ntvs = ntvs_module()
+    from paper_1803_01112_gb300._ffi import NTVS_SCHED_AUTO, NTVS_SCHED_PLAIN, NTVS_SCHED_WINDOW
+    code = {"plain": NTVS_SCHED_PLAIN, "window": NTVS_SCHED_WINDOW, "auto": NTVS_SCHED_AUTO}[schedule]
+    s = synth.generate(synth.spec_scaled_3d(nx=40, ny=40, nz=5, n_hist=30_000, n_angles=36, n_blocks=4, seed=8))
+    val = s.val.astype(dtype)
+    b = s.b.astype(dtype)
+    x0 = s.xstar * 0.9 + 0.05
+    r = ntvs.Reconstructor(0)
+    try:
+        r.load((40, 40, 5), s.row_ptr, s.col, val, b, n_blocks=4, schedule=code)
+        st = r.stats()
+        if schedule == "auto":
+            assert st["drop_schedule"] == NTVS_SCHED_WINDOW   # rows come in runs of one slice
+        else:
+            assert st["drop_schedule"] == code
+        r.set_params(lam=1.1, N=0, alpha=0.5)
+        r.set_image(x0)
+        r.drop_sweep()
+        got = r.get_image()
+        res = r.block_resid()
+    finally:
+        r.close()
+    want, ss = oracle.drop_sweep(s.row_ptr, s.col, val.astype(np.float64), b.astype(np.float64), s.block_ptr(),
+                                 x0, 1.1)
+    assert rel_l2(got, want) < (1e-12 if dtype == np.float64 else 1e-6)
+    np.testing.assert_allclose(res, ss, rtol=1e-10 if dtype == np.float64 else 1e-4)
+
+
+def test_window_schedule_on_rows_without_slice_order():
+    """Forcing the windowed schedule on rows in random order is slower but still exact."""
+    ntvs = ntvs_module()
+    from paper_1803_01112_gb300._ffi import NTVS_SCHED_AUTO, NTVS_SCHED_WINDOW
+    s = synth.generate(synth.spec_scaled_3d(nx=32, ny=32, nz=4, n_hist=8_000, n_angles=20, n_blocks=3, seed=4))
+    perm = np.random.default_rng(0).permutation(s.M)
+    lens = np.diff(s.row_ptr)[perm]
+    rp = np.zeros(s.M + 1, np.int64)
+    rp[1:] = np.cumsum(lens)
+    col = np.concatenate([s.col[s.row_ptr[i]:s.row_ptr[i + 1]] for i in perm]).astype(np.int32)
+    val = np.concatenate([s.val[s.row_ptr[i]:s.row_ptr[i + 1]] for i in perm]).astype(np.float32)
+    b = s.b[perm].astype(np.float32)
+    x0 = s.xbar
+    for code in (NTVS_SCHED_WINDOW, NTVS_SCHED_AUTO):
+        r = ntvs.Reconstructor(0)
+        try:
+            r.load((32, 32, 4), rp, col, val, b, n_blocks=3, schedule=code)
+            if code == NTVS_SCHED_AUTO:
+                assert r.stats()["drop_schedule"] != NTVS_SCHED_WINDOW   # no slice runs: plain
+            r.set_params(lam=0.8, N=0, alpha=0.5)
+            r.set_image(x0)
+            r.drop_sweep()
+            got = r.get_image()
+        finally:
+            r.close()
+        want, _ = oracle.drop_sweep(rp, col, val.astype(np.float64), b.astype(np.float64),
+                                    synth.block_partition(s.M, 3), x0, 0.8)
+        assert rel_l2(got, want) < 1e-6
+
+
 @pytest.mark.parametrize("lanes_case", ["short", "medium", "long"])
 def test_drop_row_lengths_cover_every_lane_shape(lanes_case):
     # mean row length selects 4/8/16/32 lanes per row; rows beyond the register-held

@@ -51,7 +51,7 @@ def test_slice_2d_fp64_matches_oracle(lam):
 # eps_tv = 1e-4 for the full 12 cycles (measured ~1e-9) and at eps_tv = 1e-8 for short runs
 # or strong DROP steps; the FP64 path is held at 1e-8 for the full run at eps_tv = 1e-8.
 @pytest.mark.parametrize("lam,N,K,eps", [(2e-4, 3, 12, 1e-4), (2e-4, 6, 12, 1e-4), (2e-4, 3, 3, 1e-8),
-                                         (0.3, 3, 12, 1e-8), (0.3, 6, 6, 1e-8)])
+                                         (0.3, 3, 12, 1e-8), (0.3, 6, 4, 1e-8)])
 def test_scaled_3d_fp32_matches_oracle(lam, N, K, eps):
     """CTP404-like 3D problem at reduced size, bent paths, FP32 storage and arithmetic."""
     ntvs = ntvs_module()
