@@ -270,12 +270,17 @@ cudaError_t k_drop_apply(int cdt, double* x, float* x32, void* delta, const void
     return cudaGetLastError();
 }
 
-// home slice of each row: the z-slice of its middle entry (-1 for an empty row)
+// home slice of each row: the median of the z-slices of its first, middle and last
+// entries (-1 for an empty row); a path that bends out of its slice and back keeps the
+// slice it enters and leaves by
 __global__ void row_home_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int64_t M,
                                 int64_t slice, int32_t* __restrict__ home) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t p0 = row_ptr[i], p1 = row_ptr[i + 1];
-        home[i] = (p1 > p0) ? (int32_t)(col[p0 + (p1 - p0) / 2] / slice) : -1;
+        if (p1 <= p0) { home[i] = -1; continue; }
+        const int32_t a = (int32_t)(col[p0] / slice), m = (int32_t)(col[p0 + (p1 - p0) / 2] / slice),
+                      c = (int32_t)(col[p1 - 1] / slice);
+        home[i] = max(min(a, m), min(max(a, m), c));
     }
 }
 

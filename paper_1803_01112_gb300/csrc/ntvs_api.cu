@@ -658,8 +658,9 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
     const double mean = M ? (double)nnz / (double)M : 0.0;
     c->lpr = mean <= 12.0 ? 4 : mean <= 40.0 ? 8 : mean <= 120.0 ? 16 : 32;
     c->drop_grid = c->sms * 8;
-    c->vector4 = c->cdt == F32 && ((uintptr_t)c->col % 16 == 0) &&
-                 ((uintptr_t)c->val % (c->vdt == F32 ? 16 : 8) == 0);
+    // 4-entry vector loads put entries 4 apart along a path into one scatter instruction,
+    // which measured slower than one coalesced entry per lane; kept off
+    c->vector4 = false;
     TRY(plan_schedule(c, s->schedule));
     {
         const int64_t need = (V + 255) / 256;

@@ -86,7 +86,7 @@ struct DropArgs {
     int64_t slice;
 };
 cudaError_t k_drop_block(const DropArgs& a, cudaStream_t s);
-// home[i] = z-slice of the middle entry of row i (-1 for an empty row)
+// home[i] = median z-slice of the first, middle and last entries of row i (-1: empty row)
 cudaError_t k_row_home(const int64_t* row_ptr, const int32_t* col, int64_t M, int64_t slice, int32_t* home, int grid,
                        cudaStream_t s);
 // x_j += delta_j * inv_s_j on the FP64 master (x32_j <- (float)x_j when x32 != null); delta_j = 0
