@@ -54,6 +54,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=3_000_000, help="oracle sample: first rows of the workload")
     ap.add_argument("--ref-rows", type=int, default=1_000_000, help="reference arm: rows per step")
+    ap.add_argument("--schedule", choices=["auto", "plain", "window"], default="auto",
+                    help="DROP kernel schedule (auto picks the windowed one for slice-ordered rows)")
     ap.add_argument("--rows", type=int, default=0,
                     help="profiling case: only the first ROWS histories, in blocks of the full workload's size")
     return ap.parse_args(argv)
@@ -283,7 +285,8 @@ def run_ntvs(args):
     stream = torch.cuda.Stream(device)   # the library launches on this stream; events are recorded on it
 
     r = ntvs.Reconstructor(local, stream.cuda_stream)
-    r.load(shape, s.row_ptr, s.col, s.val, b, n_blocks=spec.n_blocks)
+    sched = {"auto": 0, "plain": 1, "window": 2}[args.schedule]
+    r.load(shape, s.row_ptr, s.col, s.val, b, n_blocks=spec.n_blocks, schedule=sched)
     r.set_params(**PARAMS)
     r.set_image(x0)
     st0 = r.stats()
@@ -339,7 +342,7 @@ def run_ntvs(args):
             torch.cuda.synchronize(device)
             t0 = time.perf_counter()
             re = ntvs.Reconstructor(local, stream.cuda_stream)
-            re.load(shape, s.row_ptr, s.col, s.val, b, n_blocks=spec.n_blocks)
+            re.load(shape, s.row_ptr, s.col, s.val, b, n_blocks=spec.n_blocks, schedule=sched)
             re.set_params(**PARAMS)
             re.set_image(x0)
             re.run(E2E_CYCLES)

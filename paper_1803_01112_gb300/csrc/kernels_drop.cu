@@ -46,12 +46,17 @@ struct Window {
     int W;
 };
 
+// Shared-memory slot of window offset j: the low 5 bits are XORed with the next 5, a
+// bijection inside each group of 32 slots.  Paths along y step the offset by nx (200: 8
+// mod 32), which without the swizzle puts a warp's 32 updates into 4 banks.
+__device__ __forceinline__ int swz(int j) { return j ^ ((j >> 5) & 31); }
+
 template <typename T, bool WIN>
 __device__ __forceinline__ void scatter(T* delta, const Window& w, int32_t c, T v) {
     if (WIN) {
         const int64_t rel = (int64_t)c - w.w0;
         if ((uint64_t)rel < (uint64_t)w.W) {
-            atomicAdd(reinterpret_cast<T*>(w.win) + rel, v);
+            atomicAdd(reinterpret_cast<T*>(w.win) + swz((int)rel), v);
             return;
         }
     }
@@ -144,13 +149,14 @@ drop_block_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict
 }
 
 // Windowed variant: CTA b processes segments [seg_begin[b], seg_begin[b+1]) in order.
+// The window holds Wp = W rounded up to 32 slots (swizzled); slots past W stay 0.
 template <typename T>
-__device__ __forceinline__ void flush_window(T* win, int W, T* delta, int64_t w0) {
-    for (int j = threadIdx.x; j < W; j += blockDim.x) {
-        const T v = win[j];
+__device__ __forceinline__ void flush_window(T* win, int Wp, T* delta, int64_t w0) {
+    for (int jj = threadIdx.x; jj < Wp; jj += blockDim.x) {
+        const T v = win[jj];
         if (v != (T)0) {
-            atomicAdd(delta + w0 + j, v);
-            win[j] = (T)0;
+            atomicAdd(delta + w0 + swz(jj), v);
+            win[jj] = (T)0;
         }
     }
 }
@@ -165,11 +171,12 @@ drop_block_window_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __r
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* win = reinterpret_cast<T*>(smem_raw);
     const int W = (int)slice;
+    const int Wp = (W + 31) & ~31;
     constexpr int G = 32 / LPR;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
-    for (int j = threadIdx.x; j < W; j += blockDim.x) win[j] = (T)0;
+    for (int j = threadIdx.x; j < Wp; j += blockDim.x) win[j] = (T)0;
     __syncthreads();
     const int s0 = seg_begin[blockIdx.x], s1 = seg_begin[blockIdx.x + 1];
     int cur = s0 < s1 ? segs[s0].home : 0;
@@ -179,7 +186,7 @@ drop_block_window_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __r
         const DropSegment sg = segs[s];
         if (sg.home != cur) {   // uniform across the CTA
             __syncthreads();
-            flush_window(win, W, delta, w.w0);
+            flush_window(win, Wp, delta, w.w0);
             __syncthreads();
             cur = sg.home;
             w.w0 = (int64_t)cur * slice;
@@ -191,7 +198,7 @@ drop_block_window_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __r
         }
     }
     __syncthreads();
-    flush_window(win, W, delta, w.w0);
+    flush_window(win, Wp, delta, w.w0);
     __shared__ double sh[32];
     const double tot = block_sum(ss, sh);
     if (threadIdx.x == 0 && tot != 0.0) atomicAdd(resid_ss, tot);
@@ -213,7 +220,7 @@ template <typename T, typename V, int LPR, int CH, int VW>
 static cudaError_t launch_cfg(const DropArgs& a, cudaStream_t s) {
     if (a.segs) {
         auto kern = drop_block_window_kernel<T, V, LPR, CH, VW>;
-        const size_t smem = (size_t)a.slice * sizeof(T);
+        const size_t smem = (size_t)((a.slice + 31) & ~31LL) * sizeof(T);
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         kern<<<a.grid, 1024, smem, s>>>(a.row_ptr, a.col, (const V*)a.val, (const T*)a.b, (const T*)a.inv_norm2,

@@ -388,10 +388,11 @@ int copy_image_out(ntvs_ctx* c, const void* src, int sdt, void* out, int dtype, 
 }  // namespace
 
 // ---- DROP schedule planning (load time) ------------------------------------------------
-// Rows are cut into chunks of at most kChunkRows consecutive rows with the same home
-// slice; per block, chunks are ordered by home slice and dealt to the win_grid CTAs in
-// contiguous runs of about equal row count.  Consecutive chunks of one CTA with the same
-// home slice and adjacent rows merge into one segment.
+// Each block's rows are cut into chunks of kChunkRows consecutive rows; a chunk's home
+// slice is the median of its rows' home slices (so a few rows that bend out of their
+// slice do not break a run).  Per block, chunks are ordered by home slice and dealt to the
+// win_grid CTAs in contiguous runs of about equal row count; consecutive chunks of one
+// CTA with the same home slice and adjacent rows merge into one segment.
 constexpr int kChunkRows = 64;
 constexpr double kMinMeanRun = 8.0;
 
@@ -401,7 +402,7 @@ static int plan_schedule(ntvs_ctx* c, int requested) {
     const int64_t slice = (int64_t)c->nx * c->ny;
     int optin = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
-    const int64_t need = slice * (int64_t)c->csz();
+    const int64_t need = ((slice + 31) & ~31LL) * (int64_t)c->csz();
     if (need + 1024 > optin) {
         if (requested == NTVS_SCHED_WINDOW)
             return fail(NTVS_ERR_ARG, "windowed schedule: an nx*ny slice needs " + std::to_string(need) +
@@ -437,12 +438,12 @@ static int plan_schedule(ntvs_ctx* c, int requested) {
     for (int t = 0; t < c->B; ++t) {
         const int64_t r0 = c->block_ptr[t], r1 = c->block_ptr[t + 1];
         ch.clear();
-        for (int64_t i = r0; i < r1;) {
-            const int32_t h = home[i];
-            int64_t j = i + 1;
-            while (j < r1 && j - i < kChunkRows && home[j] == h) ++j;
-            ch.push_back({i, j, h});
-            i = j;
+        std::vector<int32_t> hh;
+        for (int64_t i = r0; i < r1; i += kChunkRows) {
+            const int64_t j = std::min<int64_t>(r1, i + kChunkRows);
+            hh.assign(home.begin() + i, home.begin() + j);
+            std::nth_element(hh.begin(), hh.begin() + hh.size() / 2, hh.end());
+            ch.push_back({i, j, hh[hh.size() / 2]});
         }
         std::stable_sort(ch.begin(), ch.end(), [](const Chunk& a, const Chunk& b) { return a.home < b.home; });
         int32_t* bg = begin.data() + (size_t)t * (G + 1);
