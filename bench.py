@@ -54,7 +54,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=3_000_000, help="oracle sample: first rows of the workload")
     ap.add_argument("--ref-rows", type=int, default=1_000_000, help="reference arm: rows per step")
-    ap.add_argument("--schedule", choices=["auto", "plain", "window"], default="auto",
+    ap.add_argument("--schedule", choices=["auto", "plain", "window", "pipeline"], default="auto",
                     help="DROP kernel schedule (auto picks the windowed one for slice-ordered rows)")
     ap.add_argument("--rows", type=int, default=0,
                     help="profiling case: only the first ROWS histories, in blocks of the full workload's size")
@@ -160,7 +160,7 @@ def measured_peaks():
 
 def drop_kernel_hash():
     h = hashlib.sha256()
-    for f in ("kernels_drop.cu", "common.cuh"):
+    for f in ("kernels_drop.cu", "kernels_drop_tma.cu", "common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1803_01112_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 
@@ -285,7 +285,7 @@ def run_ntvs(args):
     stream = torch.cuda.Stream(device)   # the library launches on this stream; events are recorded on it
 
     r = ntvs.Reconstructor(local, stream.cuda_stream)
-    sched = {"auto": 0, "plain": 1, "window": 2}[args.schedule]
+    sched = {"auto": 0, "plain": 1, "window": 2, "pipeline": 3}[args.schedule]
     r.load(shape, s.row_ptr, s.col, s.val, b, n_blocks=spec.n_blocks, schedule=sched)
     r.set_params(**PARAMS)
     r.set_image(x0)
@@ -324,7 +324,7 @@ def run_ntvs(args):
     avg_ms = prof["drop_block_ms"] / max(prof["drop_block_launches"], 1)
     achieved = avg_bytes / (avg_ms / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
-    kname = "drop_block_window_kernel" if st0["drop_schedule"] == 2 else "drop_block_kernel"
+    kname = {2: "drop_block_window_kernel", 3: "drop_pipe_kernel"}.get(st0["drop_schedule"], "drop_block_kernel")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": ncu_traffic_per_launch(), "kernel": kname,
                 "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": avg_bytes,
@@ -370,7 +370,7 @@ def run_ntvs(args):
                 "config": {"workload": spec.name, "grid": [spec.nx, spec.ny, spec.nz], "histories": spec.n_hist,
                            "nnz": s.nnz, "n_blocks": spec.n_blocks, **PARAMS, "tv_check": False,
                            "storage": "csr32", "l2": L2_NOTE,
-                           "drop_schedule": {1: "plain", 2: "window"}.get(st0["drop_schedule"]),
+                           "drop_schedule": {1: "plain", 2: "window", 3: "pipeline"}.get(st0["drop_schedule"]),
                            "lanes_per_row": st0["lanes_per_row"],
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

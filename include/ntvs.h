@@ -83,14 +83,18 @@ typedef struct {
 } ntvs_system;
 
 /* DROP kernel schedules.  PLAIN: rows in stored order, every scatter a global reduction.
- * WINDOW: rows grouped at load time by the z-slice holding their middle entry; one CTA
- * per SM accumulates its slice in shared memory (needs nx*ny*sizeof(compute type) of
- * shared memory per CTA).  AUTO picks WINDOW when the slice fits and rows come in runs of
- * the same slice (e.g. stored by projection angle, then slice), else PLAIN.  All give
- * the same result up to the order of floating-point summation. */
+ * WINDOW: rows grouped at load time by their home z-slice (median slice of the rows of
+ * each 64-row chunk); one CTA per SM accumulates its slice in shared memory (needs
+ * nx*ny*sizeof(compute type) of shared memory per CTA).  PIPELINE: WINDOW's grouping
+ * with the matrix streamed into shared memory by the TMA engine (cp.async.bulk) ahead of
+ * the consumer warps; needs 16-byte aligned col/val and 64 KB more shared memory.  AUTO
+ * picks PIPELINE, else WINDOW, when the slice fits and rows come in runs of the same slice
+ * (e.g. stored by projection angle, then slice), else PLAIN.  All give the same result up
+ * to the order of floating-point summation. */
 #define NTVS_SCHED_AUTO 0
 #define NTVS_SCHED_PLAIN 1
 #define NTVS_SCHED_WINDOW 2
+#define NTVS_SCHED_PIPELINE 3
 
 /* Parameters of NTVS (Sec. II-E, Appendix A/C). */
 typedef struct {
@@ -117,7 +121,7 @@ typedef struct {
     int32_t compute_dtype; /* NTVS_F64 or NTVS_F32                                       */
     double last_tv;        /* phi(x) after the last completed cycle (FP64)               */
     int64_t n_launches;    /* kernels this context has launched (all entry points)       */
-    int32_t drop_schedule; /* NTVS_SCHED_PLAIN or NTVS_SCHED_WINDOW (chosen at load)      */
+    int32_t drop_schedule; /* NTVS_SCHED_PLAIN, _WINDOW or _PIPELINE (chosen at load)      */
     int32_t lanes_per_row; /* lanes per row of the DROP kernel                           */
 } ntvs_stats;
 

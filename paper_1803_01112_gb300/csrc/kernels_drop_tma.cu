@@ -1,0 +1,270 @@
+// Block-DROP with a TMA-fed pipeline (P_T of arXiv 1803.01112 Appendix C; DROP of ref.
+// CEHN08, Sec. II-D): the same update as drop_block_window_kernel,
+//     r_i = lambda (b_i - <a_i, x>) / ||a_i||^2,   delta_j += r_i a_ij,
+// with the matrix stream decoupled from the dependent gather -> dot -> scatter chain.
+//
+// One CTA per SM.  Warp 0 is the producer: one thread walks the CTA's stage list
+// (planned at load time: runs of whole rows of one home z-slice, at most kStageRows rows
+// and S entries, start aligned to 16 bytes) and copies each stage's columns and values
+// into a ring of kStages shared-memory slots with cp.async.bulk, completing on the
+// slot's "full" mbarrier.  Warps 1..31 are consumers: they walk the same stages in order,
+// each taking every 31st row, compute the row's dot product from shared memory (x
+// gathered from L1/L2), and scatter r_i a_ij into a shared-memory window of the home
+// slice (XOR-swizzled slots) or, outside the slice, into delta with global reductions.
+// A consumer releases a slot by arriving on its "empty" mbarrier.  When the home slice
+// changes the consumers meet on a third mbarrier and flush the window.
+//
+// Every wait is bounded by a %globaltimer deadline: on expiry the thread records an
+// error code (read by the host as NTVS_ERR_TIMEOUT) and leaves, and the producer waits
+// (again bounded) for its own copies in flight before it exits.
+#include "common.cuh"
+
+namespace ntvs {
+
+namespace {
+
+constexpr int kStages = 4;                      // ring slots
+constexpr int kThreads = 1024;
+constexpr int kConsumers = kThreads / 32 - 1;   // 31 consumer warps
+constexpr uint64_t kWaitNs = 2000000000ull;     // 2 s per wait
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t now_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("{ .reg .b64 st; mbarrier.arrive.shared::cta.b64 st, [%0]; }" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("{ .reg .b64 st; mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1; }" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase with the given parity; false (and *err set) on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = now_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (now_ns() - t0 > kWaitNs) {
+            atomicExch(err, code);
+            return false;
+        }
+    }
+    return true;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ int swz(int j) { return j ^ ((j >> 5) & 31); }
+
+template <typename T>
+__device__ __forceinline__ void scatter_w(T* win, int W, int64_t w0, T* delta, int32_t c, T v) {
+    const int64_t rel = (int64_t)c - w0;
+    if ((uint64_t)rel < (uint64_t)W) atomicAdd(win + swz((int)rel), v);
+    else atomicAdd(delta + c, v);
+}
+
+// one row of a stage: entries [o0, o1) of the stage buffers (or of global memory)
+template <typename T, typename V>
+__device__ __forceinline__ void pipe_row(const int32_t* cs, const V* vs, int o0, int o1, int64_t i, const T* b,
+                                         const T* inv_norm2, const T* x, T* win, int W, int64_t w0, T* delta, T lambda,
+                                         double& ss) {
+    const int lane = threadIdx.x & 31;
+    const T bi = __ldg(b + i), ni = __ldg(inv_norm2 + i);
+    T acc = (T)0;
+#pragma unroll 4
+    for (int q = o0 + lane; q < o1; q += 32) acc += (T)to_compute(vs[q]) * __ldg(x + cs[q]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    const T res = bi - acc;
+    const T r = lambda * res * ni;
+    if (lane == 0) ss += (double)res * (double)res;
+#pragma unroll 4
+    for (int q = o0 + lane; q < o1; q += 32) scatter_w(win, W, w0, delta, cs[q], r * (T)to_compute(vs[q]));
+}
+
+template <typename T>
+__device__ __forceinline__ void flush_w(T* win, int Wp, T* delta, int64_t w0, int tid, int nthreads) {
+    for (int jj = tid; jj < Wp; jj += nthreads) {
+        const T v = win[jj];
+        if (v != (T)0) {
+            atomicAdd(delta + w0 + swz(jj), v);
+            win[jj] = (T)0;
+        }
+    }
+}
+
+template <typename T, typename V>
+__global__ void __launch_bounds__(kThreads, 1)
+drop_pipe_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, const V* __restrict__ val,
+                 const T* __restrict__ b, const T* __restrict__ inv_norm2, const DropStage* __restrict__ stages,
+                 const int32_t* __restrict__ stage_begin, int64_t slice, int S, const T* __restrict__ x,
+                 T* __restrict__ delta, T lambda, double* resid_ss, int* err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int W = (int)slice;
+    const int Wp = (W + 31) & ~31;
+    T* win = reinterpret_cast<T*>(smem_raw);
+    int32_t* ring_c = reinterpret_cast<int32_t*>(smem_raw + (size_t)Wp * sizeof(T));
+    V* ring_v = reinterpret_cast<V*>(reinterpret_cast<unsigned char*>(ring_c) + (size_t)kStages * S * sizeof(int32_t));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(ring_v) +
+                                                 (size_t)kStages * S * sizeof(V));
+    uint64_t* full = bars;
+    uint64_t* empty = bars + kStages;
+    uint64_t* cbar = bars + 2 * kStages;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int j = 0; j < kStages; ++j) {
+            mbar_init(full + j, 1);
+            mbar_init(empty + j, kConsumers);
+        }
+        mbar_init(cbar, kConsumers);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int j = tid; j < Wp; j += kThreads) win[j] = (T)0;
+    __syncthreads();
+
+    const int s0 = stage_begin[blockIdx.x], s1 = stage_begin[blockIdx.x + 1];
+    const int n = s1 - s0;
+
+    if (warp == 0) {
+        // ---------------------------------------------------------------- producer
+        if (lane == 0) {
+            int k = 0;
+            for (; k < n; ++k) {
+                const int slot = k % kStages;
+                if (k >= kStages && !mbar_wait(empty + slot, ((k / kStages) - 1) & 1, err, 1)) break;
+                const DropStage st = stages[s0 + k];
+                if (st.nent > 0) {
+                    const uint32_t bc = (uint32_t)st.nent * (uint32_t)sizeof(int32_t);
+                    const uint32_t bv = (uint32_t)st.nent * (uint32_t)sizeof(V);
+                    mbar_arrive_expect_tx(full + slot, bc + bv);
+                    bulk_g2s(ring_c + (size_t)slot * S, col + st.e0, bc, full + slot);
+                    bulk_g2s(ring_v + (size_t)slot * S, val + st.e0, bv, full + slot);
+                } else {
+                    mbar_arrive(full + slot);   // rows read straight from global memory
+                }
+            }
+            // the last issued stages may still be landing: wait for them before leaving
+            for (int j = (k > kStages ? k - kStages : 0); j < k; ++j)
+                if (!mbar_wait(full + (j % kStages), (j / kStages) & 1, err, 2)) break;
+        }
+        return;
+    }
+
+    // -------------------------------------------------------------------- consumers
+    const int cw = warp - 1;
+    const int ctid = tid - 32;
+    const int cthreads = kThreads - 32;
+    double ss = 0.0;
+    int64_t next = cw;      // index (in this CTA's row sequence) of this warp's next row
+    int64_t base = 0;       // row-sequence index of the current stage's first row
+    int cur = n > 0 ? stages[s0].home : 0;
+    uint32_t cphase = 0;
+    bool ok = true;
+    for (int k = 0; k < n && ok; ++k) {
+        const DropStage st = stages[s0 + k];
+        if (st.home != cur) {   // flush the window of the previous slice (all consumers)
+            __syncwarp();
+            if (lane == 0) mbar_arrive(cbar);
+            ok = mbar_wait(cbar, cphase & 1, err, 3);
+            cphase++;
+            if (!ok) break;
+            flush_w(win, Wp, delta, (int64_t)cur * slice, ctid, cthreads);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(cbar);
+            ok = mbar_wait(cbar, cphase & 1, err, 3);
+            cphase++;
+            if (!ok) break;
+            cur = st.home;
+        }
+        const int slot = k % kStages;
+        ok = mbar_wait(full + slot, (k / kStages) & 1, err, 4);
+        if (!ok) break;
+        const int64_t w0 = (int64_t)cur * slice;
+        while (next < base + st.nrows) {
+            const int j = (int)(next - base);
+            const int64_t i = st.r0 + j;
+            if (st.nent > 0) {
+                pipe_row<T, V>(ring_c + (size_t)slot * S, ring_v + (size_t)slot * S, st.off[j], st.off[j + 1], i, b,
+                               inv_norm2, x, win, W, w0, delta, lambda, ss);
+            } else {
+                const int64_t p0 = row_ptr[i], p1 = row_ptr[i + 1];
+                pipe_row<T, V>(col + p0, val + p0, 0, (int)(p1 - p0), i, b, inv_norm2, x, win, W, w0, delta, lambda,
+                               ss);
+            }
+            next += kConsumers;
+        }
+        base += st.nrows;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty + slot);
+    }
+    if (ok) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(cbar);
+        if (mbar_wait(cbar, cphase & 1, err, 5)) flush_w(win, Wp, delta, (int64_t)cur * slice, ctid, cthreads);
+    }
+    if (lane == 0 && ss != 0.0) atomicAdd(resid_ss, ss);
+}
+
+}  // namespace
+
+int pipe_stage_entries(int vdt) {
+    // ring of kStages slots, 64 KB in total, slot length a multiple of 8 entries
+    const int per = 4 + (int)dt_size(vdt);
+    return ((65536 / (kStages * per)) / 8) * 8;
+}
+
+size_t pipe_smem_bytes(int cdt, int vdt, int64_t slice) {
+    const size_t Wp = (size_t)((slice + 31) & ~31LL);
+    const size_t S = (size_t)pipe_stage_entries(vdt);
+    return Wp * dt_size(cdt) + kStages * S * (4 + dt_size(vdt)) + (2 * kStages + 1) * sizeof(uint64_t);
+}
+
+template <typename T, typename V>
+static cudaError_t launch_pipe(const DropPipeArgs& a, cudaStream_t s) {
+    auto kern = drop_pipe_kernel<T, V>;
+    const size_t smem = pipe_smem_bytes(a.cdt, a.vdt, a.slice);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<a.grid, kThreads, smem, s>>>(a.row_ptr, a.col, (const V*)a.val, (const T*)a.b, (const T*)a.inv_norm2,
+                                         a.stages, a.stage_begin, a.slice, pipe_stage_entries(a.vdt), (const T*)a.x,
+                                         (T*)a.delta, (T)a.lambda, a.resid_ss, a.err);
+    return cudaGetLastError();
+}
+
+cudaError_t k_drop_pipe(const DropPipeArgs& a, cudaStream_t s) {
+    if (a.cdt == F64) {
+        if (a.vdt != F64) return cudaErrorInvalidValue;
+        return launch_pipe<double, double>(a, s);
+    }
+    switch (a.vdt) {
+        case F32: return launch_pipe<float, float>(a, s);
+        case F16: return launch_pipe<float, __half>(a, s);
+        case BF16: return launch_pipe<float, __nv_bfloat16>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace ntvs

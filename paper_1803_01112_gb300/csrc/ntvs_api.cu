@@ -108,7 +108,10 @@ struct ntvs_ctx {
     int schedule = NTVS_SCHED_PLAIN;
     DropSegment* segs = nullptr;       // windowed schedule: all blocks' segments
     int32_t* seg_begin = nullptr;      // [B][win_grid + 1]
+    DropStage* stages = nullptr;       // pipelined schedule: all blocks' stages
+    int32_t* stage_begin = nullptr;    // [B][win_grid + 1]
     int win_grid = 0;
+    int* derr = nullptr;               // device error word (bounded waits that ran out)
 
     // image and scratch: x is the FP64 master image; x32 its FP32 copy gathered by the
     // FP32-path DROP kernels (null on the FP64 path)
@@ -157,6 +160,8 @@ struct ntvs_ctx {
         dev_free(inv_s);
         dev_free(segs);
         dev_free(seg_begin);
+        dev_free(stages);
+        dev_free(stage_begin);
         schedule = NTVS_SCHED_PLAIN;
         dev_free(x);
         dev_free(x32);
@@ -223,6 +228,21 @@ cudaError_t timed_launch(ntvs_ctx* c, int kind, F launch) {
     cudaEventRecord(b, c->stream);
     c->timed.push_back({kind, a, b});
     return e;
+}
+
+// Reads (and clears) the device error word after the stream has drained: a bounded
+// device-side wait that ran out leaves a nonzero code there.
+int check_device_error(ntvs_ctx* c) {
+    CUDA_TRY(cudaMemcpyAsync(c->hint + 1, c->derr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    const int code = c->hint[1];
+    if (code) {
+        CUDA_TRY(cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        return fail(NTVS_ERR_TIMEOUT, "a bounded wait in the pipelined DROP kernel ran out (code " +
+                                          std::to_string(code) + "); the image of this run is invalid");
+    }
+    return NTVS_OK;
 }
 
 int copy_in(void** dst, bool* own, const void* src, size_t bytes, int mem_kind, cudaStream_t s, const char* what) {
@@ -343,7 +363,28 @@ int drop_block(ntvs_ctx* c, int t) {
         a.seg_begin = c->seg_begin + (size_t)t * (c->win_grid + 1);
         a.grid = c->win_grid;
     }
-    CUDA_TRY(timed_launch(c, KIND_DROP, [&] { return k_drop_block(a, c->stream); }));
+    if (c->schedule == NTVS_SCHED_PIPELINE) {
+        DropPipeArgs pa;
+        pa.row_ptr = c->row_ptr;
+        pa.col = c->col;
+        pa.val = c->val;
+        pa.b = c->b;
+        pa.inv_norm2 = c->inv_norm2;
+        pa.stages = c->stages;
+        pa.stage_begin = c->stage_begin + (size_t)t * (c->win_grid + 1);
+        pa.slice = (int64_t)c->nx * c->ny;
+        pa.x = a.x;
+        pa.delta = c->delta;
+        pa.lambda = c->p.lambda;
+        pa.resid_ss = c->resid + t;
+        pa.err = c->derr;
+        pa.vdt = c->vdt;
+        pa.cdt = c->cdt;
+        pa.grid = c->win_grid;
+        CUDA_TRY(timed_launch(c, KIND_DROP, [&] { return k_drop_pipe(pa, c->stream); }));
+    } else {
+        CUDA_TRY(timed_launch(c, KIND_DROP, [&] { return k_drop_block(a, c->stream); }));
+    }
     CUDA_TRY(timed_launch(c, KIND_APPLY, [&] {
         return k_drop_apply(c->cdt, c->x, c->x32, c->delta, (const char*)c->inv_s + (size_t)t * c->V * c->csz(),
                             c->V, c->apply_grid, c->stream);
@@ -404,7 +445,7 @@ static int plan_schedule(ntvs_ctx* c, int requested) {
     CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     const int64_t need = ((slice + 31) & ~31LL) * (int64_t)c->csz();
     if (need + 1024 > optin) {
-        if (requested == NTVS_SCHED_WINDOW)
+        if (requested == NTVS_SCHED_WINDOW || requested == NTVS_SCHED_PIPELINE)
             return fail(NTVS_ERR_ARG, "windowed schedule: an nx*ny slice needs " + std::to_string(need) +
                                           " bytes of shared memory, the device allows " + std::to_string(optin));
         return NTVS_OK;
@@ -462,6 +503,73 @@ static int plan_schedule(ntvs_ctx* c, int requested) {
         while (cta < G) bg[++cta] = (int32_t)segs.size();
     }
     if (segs.size() > (size_t)INT32_MAX) return NTVS_OK;
+    c->win_grid = G;
+
+    // pipelined schedule: cut every segment into ring-slot stages of whole rows
+    const bool aligned = ((uintptr_t)c->col % 16 == 0) && ((uintptr_t)c->val % 16 == 0);
+    const bool pipe_fits = (int64_t)pipe_smem_bytes(c->cdt, c->vdt, slice) + 1024 <= optin;
+    const bool want_pipe = requested == NTVS_SCHED_PIPELINE || (requested == NTVS_SCHED_AUTO && aligned && pipe_fits);
+    if (want_pipe) {
+        if (c->nz > 32767) return fail(NTVS_ERR_ARG, "pipelined schedule: nz > 32767");
+        if (!aligned || !pipe_fits) {
+            return fail(NTVS_ERR_ARG, !aligned ? "pipelined schedule: col and val must be 16-byte aligned"
+                                               : "pipelined schedule: slice window + ring exceed shared memory");
+        }
+        std::vector<int64_t> rp((size_t)c->M + 1);
+        CUDA_TRY(cudaMemcpyAsync(rp.data(), c->row_ptr, sizeof(int64_t) * rp.size(), cudaMemcpyDeviceToHost,
+                                 c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        const int64_t S = pipe_stage_entries(c->vdt);
+        const int64_t A = dt_size(c->vdt) == 2 ? 8 : 4;   // entries per 16 bytes of both col and val
+        auto down = [&](int64_t e) { return (e / A) * A; };
+        auto up = [&](int64_t e) { return ((e + A - 1) / A) * A; };
+        std::vector<DropStage> stages;
+        std::vector<int32_t> sbeg((size_t)c->B * (G + 1), 0);
+        for (int t = 0; t < c->B; ++t) {
+            const int32_t* bg = begin.data() + (size_t)t * (G + 1);
+            int32_t* sb = sbeg.data() + (size_t)t * (G + 1);
+            for (int cta = 0; cta < G; ++cta) {
+                sb[cta] = (int32_t)stages.size();
+                for (int32_t q = bg[cta]; q < bg[cta + 1]; ++q) {
+                    const DropSegment& sg = segs[q];
+                    for (int64_t i = sg.r0; i < sg.r1;) {
+                        DropStage st;
+                        std::memset(&st, 0, sizeof(st));
+                        st.r0 = i;
+                        st.home = (int16_t)sg.home;
+                        const int64_t e0 = down(rp[i]);
+                        int64_t j = i;
+                        while (j < sg.r1 && j - i < kStageRows && up(rp[j + 1]) - e0 <= S) ++j;
+                        if (j == i) {   // one row longer than a slot: consumers read it from global memory
+                            st.e0 = rp[i];
+                            st.nent = 0;
+                            st.nrows = 1;
+                            i += 1;
+                        } else {
+                            st.e0 = e0;
+                            st.nent = (int32_t)(up(rp[j]) - e0);
+                            st.nrows = (int16_t)(j - i);
+                            for (int64_t k = 0; k <= j - i; ++k) st.off[k] = (uint16_t)(rp[i + k] - e0);
+                            i = j;
+                        }
+                        stages.push_back(st);
+                    }
+                }
+            }
+            sb[G] = (int32_t)stages.size();
+        }
+        if (stages.size() > (size_t)INT32_MAX) return fail(NTVS_ERR_ARG, "too many pipeline stages");
+        TRY(dev_alloc(&c->stages, sizeof(DropStage) * std::max<size_t>(stages.size(), 1), "DROP stages"));
+        TRY(dev_alloc(&c->stage_begin, sizeof(int32_t) * sbeg.size(), "DROP stage index"));
+        CUDA_TRY(cudaMemcpyAsync(c->stages, stages.data(), sizeof(DropStage) * stages.size(), cudaMemcpyHostToDevice,
+                                 c->stream));
+        CUDA_TRY(cudaMemcpyAsync(c->stage_begin, sbeg.data(), sizeof(int32_t) * sbeg.size(), cudaMemcpyHostToDevice,
+                                 c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        c->schedule = NTVS_SCHED_PIPELINE;
+        return NTVS_OK;
+    }
+
     TRY(dev_alloc(&c->segs, sizeof(DropSegment) * std::max<size_t>(segs.size(), 1), "DROP segments"));
     TRY(dev_alloc(&c->seg_begin, sizeof(int32_t) * begin.size(), "DROP segment index"));
     CUDA_TRY(cudaMemcpyAsync(c->segs, segs.data(), sizeof(DropSegment) * segs.size(), cudaMemcpyHostToDevice,
@@ -469,7 +577,6 @@ static int plan_schedule(ntvs_ctx* c, int requested) {
     CUDA_TRY(cudaMemcpyAsync(c->seg_begin, begin.data(), sizeof(int32_t) * begin.size(), cudaMemcpyHostToDevice,
                              c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
-    c->win_grid = G;
     c->schedule = NTVS_SCHED_WINDOW;
     return NTVS_OK;
 }
@@ -506,12 +613,14 @@ int ntvs_create(ntvs_ctx** out, int device, void* cuda_stream) {
         (rc = dev_alloc(&c->red.ticket, sizeof(unsigned), "reduction ticket")) ||
         (rc = dev_alloc(&c->dscal, sizeof(double) * 8, "scalars")) ||
         (rc = dev_alloc(&c->daccept, sizeof(int) * 4, "accept flag")) ||
-        (rc = dev_alloc(&c->dflags, sizeof(int) * 4, "flags"))) {
+        (rc = dev_alloc(&c->dflags, sizeof(int) * 4, "flags")) ||
+        (rc = dev_alloc(&c->derr, sizeof(int), "error word"))) {
         ntvs_destroy(c);
         return rc;
     }
     cudaError_t e1 = cudaMemsetAsync(c->red.ticket, 0, sizeof(unsigned), c->stream);
     cudaError_t e2 = cudaMemsetAsync(c->dscal, 0, sizeof(double) * 8, c->stream);
+    if (e2 == cudaSuccess) e2 = cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream);
     cudaError_t e3 = cudaHostAlloc((void**)&c->hscal, sizeof(double) * 8, cudaHostAllocDefault);
     cudaError_t e4 = cudaHostAlloc((void**)&c->hint, sizeof(int) * 4, cudaHostAllocDefault);
     cudaError_t e5 = cudaStreamSynchronize(c->stream);
@@ -541,6 +650,7 @@ int ntvs_destroy(ntvs_ctx* c) {
     dev_free(c->dscal);
     dev_free(c->daccept);
     dev_free(c->dflags);
+    dev_free(c->derr);
     dev_free(c->tvhist);
     for (auto& t : c->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
     for (auto e : c->event_pool) cudaEventDestroy(e);
@@ -561,7 +671,7 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
     if (s->val_dtype < NTVS_F64 || s->val_dtype > NTVS_BF16) return fail(NTVS_ERR_ARG, "bad val_dtype");
     if (s->mem_kind != NTVS_MEM_HOST && s->mem_kind != NTVS_MEM_DEVICE) return fail(NTVS_ERR_ARG, "bad mem_kind");
     if (s->storage != NTVS_CSR32) return fail(NTVS_ERR_ARG, "storage: only NTVS_CSR32 is supported");
-    if (s->schedule < NTVS_SCHED_AUTO || s->schedule > NTVS_SCHED_WINDOW) return fail(NTVS_ERR_ARG, "bad schedule");
+    if (s->schedule < NTVS_SCHED_AUTO || s->schedule > NTVS_SCHED_PIPELINE) return fail(NTVS_ERR_ARG, "bad schedule");
     if (!s->row_ptr) return fail(NTVS_ERR_ARG, "null row_ptr");
     const int64_t M = s->n_rows;
     if (M > 0 && (!s->b)) return fail(NTVS_ERR_ARG, "null b");
@@ -718,6 +828,7 @@ int ntvs_set_image(ntvs_ctx* c, const void* x, int dtype, int mem_kind) {
 int ntvs_get_image(ntvs_ctx* c, void* out, int dtype, int mem_kind) {
     TRY(use_device(c));
     TRY(need_system(c));
+    TRY(check_device_error(c));
     return copy_image_out(c, c->x, NTVS_F64, out, dtype, mem_kind);
 }
 
@@ -746,7 +857,7 @@ int ntvs_run(ntvs_ctx* c, int k_iters) {
 int ntvs_sync(ntvs_ctx* c) {
     TRY(use_device(c));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
-    return NTVS_OK;
+    return check_device_error(c);
 }
 
 int ntvs_get_tv(ntvs_ctx* c, double* tv) {
@@ -760,7 +871,7 @@ int ntvs_get_tv(ntvs_ctx* c, double* tv) {
     CUDA_TRY(cudaMemcpyAsync(c->hscal, c->dscal + 3, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     *tv = c->hscal[0];
-    return NTVS_OK;
+    return check_device_error(c);
 }
 
 int ntvs_get_stats(ntvs_ctx* c, ntvs_stats* st) {
@@ -796,7 +907,7 @@ int ntvs_get_block_resid(ntvs_ctx* c, double* out, int cap) {
     if (!out || cap < c->B) return fail(NTVS_ERR_ARG, "output too small");
     CUDA_TRY(cudaMemcpyAsync(out, c->resid, sizeof(double) * (size_t)c->B, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
-    return NTVS_OK;
+    return check_device_error(c);
 }
 
 int ntvs_get_trace(ntvs_ctx* c, int64_t* ell_k, int32_t* tries, int32_t* accepted, int64_t cap, int64_t* n_cycles) {

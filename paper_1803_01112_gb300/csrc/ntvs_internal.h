@@ -93,6 +93,41 @@ cudaError_t k_row_home(const int64_t* row_ptr, const int32_t* col, int64_t M, in
 cudaError_t k_drop_apply(int cdt, double* x, float* x32, void* delta, const void* inv_s, int64_t V, int grid,
                          cudaStream_t s);
 
+// TMA-fed pipeline (drop_pipe_kernel): a stage is a run of at most kStageRows whole rows
+// of one home slice whose entries [e0, e0 + nent) fit one ring slot (e0 and nent aligned
+// to 16 bytes of both col and val); off[k] = row_ptr[r0 + k] - e0.  nent == 0 marks a
+// single row too long for a slot, read from global memory.
+constexpr int kStageRows = 15;
+struct DropStage {
+    int64_t e0;
+    int64_t r0;
+    int32_t nent;
+    int16_t nrows;
+    int16_t home;
+    uint16_t off[kStageRows + 1];
+    int64_t pad;
+};
+struct DropPipeArgs {
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const void* val;
+    const void* b;
+    const void* inv_norm2;
+    const DropStage* stages;
+    const int32_t* stage_begin;   // [grid + 1] for this block
+    int64_t slice;
+    const void* x;
+    void* delta;
+    double lambda;
+    double* resid_ss;
+    int* err;                     // set (nonzero) when a bounded wait runs out
+    int vdt, cdt;
+    int grid;
+};
+cudaError_t k_drop_pipe(const DropPipeArgs& a, cudaStream_t s);
+int pipe_stage_entries(int vdt);                              // entries per ring slot
+size_t pipe_smem_bytes(int cdt, int vdt, int64_t slice);      // dynamic shared memory
+
 // ------------------------------------------------------------------ misc
 // sets the calling thread's ntvs_last_error() text
 void set_last_error(const std::string& msg);

@@ -137,13 +137,16 @@ def test_drop_block_and_sweep(dtype, curved):
 
 
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
-@pytest.mark.parametrize("schedule", ["plain", "window", "auto"])
+@pytest.mark.parametrize("schedule", ["plain", "window", "pipeline", "auto"])
 def test_drop_schedules_match_oracle(dtype, schedule):
-    """Both DROP kernel schedules (stored-order rows with global reductions; rows grouped by
-    home z-slice with a shared-memory window) give the oracle's sweep."""
+    """Every DROP kernel schedule (stored-order rows with global reductions; rows grouped by
+    home z-slice with a shared-memory window; the same fed by TMA bulk copies) gives the
+    oracle's sweep."""
     ntvs = ntvs_module()
-    from paper_1803_01112_gb300._ffi import NTVS_SCHED_AUTO, NTVS_SCHED_PLAIN, NTVS_SCHED_WINDOW
-    code = {"plain": NTVS_SCHED_PLAIN, "window": NTVS_SCHED_WINDOW, "auto": NTVS_SCHED_AUTO}[schedule]
+    from paper_1803_01112_gb300._ffi import (NTVS_SCHED_AUTO, NTVS_SCHED_PIPELINE, NTVS_SCHED_PLAIN,
+                                             NTVS_SCHED_WINDOW)
+    code = {"plain": NTVS_SCHED_PLAIN, "window": NTVS_SCHED_WINDOW, "pipeline": NTVS_SCHED_PIPELINE,
+            "auto": NTVS_SCHED_AUTO}[schedule]
     s = synth.generate(synth.spec_scaled_3d(nx=40, ny=40, nz=5, n_hist=30_000, n_angles=36, n_blocks=4, seed=8))
     val = s.val.astype(dtype)
     b = s.b.astype(dtype)
@@ -153,7 +156,7 @@ def test_drop_schedules_match_oracle(dtype, schedule):
         r.load((40, 40, 5), s.row_ptr, s.col, val, b, n_blocks=4, schedule=code)
         st = r.stats()
         if schedule == "auto":
-            assert st["drop_schedule"] == NTVS_SCHED_WINDOW   # rows come in runs of one slice
+            assert st["drop_schedule"] == NTVS_SCHED_PIPELINE   # rows come in runs of one slice
         else:
             assert st["drop_schedule"] == code
         r.set_params(lam=1.1, N=0, alpha=0.5)
@@ -172,7 +175,7 @@ def test_drop_schedules_match_oracle(dtype, schedule):
 def test_window_schedule_on_rows_without_slice_order():
     """Forcing the windowed schedule on rows in random order is slower but still exact."""
     ntvs = ntvs_module()
-    from paper_1803_01112_gb300._ffi import NTVS_SCHED_AUTO, NTVS_SCHED_WINDOW
+    from paper_1803_01112_gb300._ffi import NTVS_SCHED_AUTO, NTVS_SCHED_PIPELINE, NTVS_SCHED_WINDOW
     s = synth.generate(synth.spec_scaled_3d(nx=32, ny=32, nz=4, n_hist=8_000, n_angles=20, n_blocks=3, seed=4))
     perm = np.random.default_rng(0).permutation(s.M)
     lens = np.diff(s.row_ptr)[perm]
@@ -182,12 +185,12 @@ def test_window_schedule_on_rows_without_slice_order():
     val = np.concatenate([s.val[s.row_ptr[i]:s.row_ptr[i + 1]] for i in perm]).astype(np.float32)
     b = s.b[perm].astype(np.float32)
     x0 = s.xbar
-    for code in (NTVS_SCHED_WINDOW, NTVS_SCHED_AUTO):
+    for code in (NTVS_SCHED_WINDOW, NTVS_SCHED_PIPELINE, NTVS_SCHED_AUTO):
         r = ntvs.Reconstructor(0)
         try:
             r.load((32, 32, 4), rp, col, val, b, n_blocks=3, schedule=code)
             if code == NTVS_SCHED_AUTO:
-                assert r.stats()["drop_schedule"] != NTVS_SCHED_WINDOW   # no slice runs: plain
+                assert r.stats()["drop_schedule"] not in (NTVS_SCHED_WINDOW, NTVS_SCHED_PIPELINE)   # plain
             r.set_params(lam=0.8, N=0, alpha=0.5)
             r.set_image(x0)
             r.drop_sweep()
@@ -197,6 +200,45 @@ def test_window_schedule_on_rows_without_slice_order():
         want, _ = oracle.drop_sweep(rp, col, val.astype(np.float64), b.astype(np.float64),
                                     synth.block_partition(s.M, 3), x0, 0.8)
         assert rel_l2(got, want) < 1e-6
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_pipeline_rows_longer_than_a_ring_slot(dtype):
+    """Rows with more entries than a shared-memory ring slot are read from global memory;
+    short and long rows, empty rows and stored zeros mixed, several home slices."""
+    ntvs = ntvs_module()
+    from paper_1803_01112_gb300._ffi import NTVS_SCHED_PIPELINE
+    rng = np.random.default_rng(21)
+    nx, ny, nz = 64, 64, 3
+    V = nx * ny * nz
+    M = 3000
+    lens = rng.integers(20, 300, size=M)
+    lens[::50] = rng.integers(2100, 3900, size=lens[::50].size)   # longer than a slot
+    lens[7::97] = 0
+    rows = []
+    for k, n in enumerate(lens):
+        z = (k * 3) // M                                              # rows come slice by slice
+        pool = np.arange(z * nx * ny, (z + 1) * nx * ny)
+        rows.append(np.sort(rng.choice(pool, size=n, replace=False)))
+    rp = np.zeros(M + 1, np.int64)
+    rp[1:] = np.cumsum(lens)
+    col = np.concatenate(rows).astype(np.int32)
+    val = rng.uniform(0.1, 1.2, size=col.size).astype(dtype)
+    val[::31] = 0
+    b = rng.uniform(5, 80, size=M).astype(dtype)
+    x0 = rng.uniform(0.5, 1.5, size=V)
+    r = ntvs.Reconstructor(0)
+    try:
+        r.load((nx, ny, nz), rp, col, val, b, n_blocks=4, schedule=NTVS_SCHED_PIPELINE)
+        r.set_params(lam=0.9, N=0, alpha=0.5)
+        r.set_image(x0)
+        r.drop_sweep()
+        got = r.get_image()
+    finally:
+        r.close()
+    want, _ = oracle.drop_sweep(rp, col, val.astype(np.float64), b.astype(np.float64),
+                                synth.block_partition(M, 4), x0, 0.9)
+    assert rel_l2(got, want) < (1e-12 if dtype == np.float64 else 1e-6)
 
 
 @pytest.mark.parametrize("lanes_case", ["short", "medium", "long"])
