@@ -24,6 +24,7 @@ namespace ntvs {
 namespace {
 
 constexpr int kStages = 4;                      // ring slots
+constexpr int kDescBatch = 32;                  // stage descriptors fetched per bulk copy
 constexpr int kThreads = 1024;
 constexpr int kConsumers = kThreads / 32 - 1;   // 31 consumer warps
 constexpr uint64_t kWaitNs = 2000000000ull;     // 2 s per wait
@@ -124,14 +125,17 @@ drop_pipe_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict_
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int W = (int)slice;
     const int Wp = (W + 31) & ~31;
+    // layout: window | ring of columns | ring of values | 2 x kDescBatch descriptors | mbarriers
     T* win = reinterpret_cast<T*>(smem_raw);
     int32_t* ring_c = reinterpret_cast<int32_t*>(smem_raw + (size_t)Wp * sizeof(T));
     V* ring_v = reinterpret_cast<V*>(reinterpret_cast<unsigned char*>(ring_c) + (size_t)kStages * S * sizeof(int32_t));
-    uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(ring_v) +
-                                                 (size_t)kStages * S * sizeof(V));
+    DropStage* desc = reinterpret_cast<DropStage*>(reinterpret_cast<unsigned char*>(ring_v) +
+                                                   (size_t)kStages * S * sizeof(V));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(desc + 2 * kDescBatch);
     uint64_t* full = bars;
     uint64_t* empty = bars + kStages;
     uint64_t* cbar = bars + 2 * kStages;
+    uint64_t* dbar = bars + 2 * kStages + 1;   // [2]: descriptor batches
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
@@ -140,6 +144,8 @@ drop_pipe_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict_
             mbar_init(empty + j, kConsumers);
         }
         mbar_init(cbar, kConsumers);
+        mbar_init(dbar, 1);
+        mbar_init(dbar + 1, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (int j = tid; j < Wp; j += kThreads) win[j] = (T)0;
@@ -147,15 +153,34 @@ drop_pipe_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict_
 
     const int s0 = stage_begin[blockIdx.x], s1 = stage_begin[blockIdx.x + 1];
     const int n = s1 - s0;
+    const int nb = (n + kDescBatch - 1) / kDescBatch;
 
     if (warp == 0) {
         // ---------------------------------------------------------------- producer
         if (lane == 0) {
+            auto load_batch = [&](int m) {
+                const int cnt = min(kDescBatch, n - m * kDescBatch);
+                const uint32_t bytes = (uint32_t)cnt * (uint32_t)sizeof(DropStage);
+                mbar_arrive_expect_tx(dbar + (m & 1), bytes);
+                bulk_g2s(desc + (m & 1) * kDescBatch, stages + s0 + (size_t)m * kDescBatch, bytes, dbar + (m & 1));
+            };
+            int issued_b = 0, waited_b = 0;   // descriptor batches issued / waited for
+            if (nb > 0) { load_batch(0); issued_b = 1; }
+            if (nb > 1) { load_batch(1); issued_b = 2; }
             int k = 0;
+            bool ok = true;
             for (; k < n; ++k) {
+                const int m = k / kDescBatch;
+                if (k % kDescBatch == 0) {
+                    ok = mbar_wait(dbar + (m & 1), (m >> 1) & 1, err, 6);
+                    if (!ok) break;
+                    waited_b = m + 1;
+                }
                 const int slot = k % kStages;
-                if (k >= kStages && !mbar_wait(empty + slot, ((k / kStages) - 1) & 1, err, 1)) break;
-                const DropStage st = stages[s0 + k];
+                if (k >= kStages && !(ok = mbar_wait(empty + slot, ((k / kStages) - 1) & 1, err, 1))) break;
+                // every consumer is past stage 32m - 1: batch m - 1's buffer may take batch m + 1
+                if (k % kDescBatch == kStages - 1 && m >= 1 && m + 1 < nb) { load_batch(m + 1); issued_b = m + 2; }
+                const DropStage& st = desc[(m & 1) * kDescBatch + (k % kDescBatch)];
                 if (st.nent > 0) {
                     const uint32_t bc = (uint32_t)st.nent * (uint32_t)sizeof(int32_t);
                     const uint32_t bv = (uint32_t)st.nent * (uint32_t)sizeof(V);
@@ -166,9 +191,12 @@ drop_pipe_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict_
                     mbar_arrive(full + slot);   // rows read straight from global memory
                 }
             }
-            // the last issued stages may still be landing: wait for them before leaving
+            // copies possibly still landing: the last issued stages and unconsumed batches
             for (int j = (k > kStages ? k - kStages : 0); j < k; ++j)
                 if (!mbar_wait(full + (j % kStages), (j / kStages) & 1, err, 2)) break;
+            for (int m = waited_b; m < issued_b; ++m)
+                if (!mbar_wait(dbar + (m & 1), (m >> 1) & 1, err, 7)) break;
+            (void)ok;
         }
         return;
     }
@@ -180,33 +208,37 @@ drop_pipe_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict_
     double ss = 0.0;
     int64_t next = cw;      // index (in this CTA's row sequence) of this warp's next row
     int64_t base = 0;       // row-sequence index of the current stage's first row
-    int cur = n > 0 ? stages[s0].home : 0;
+    int cur = -1;
     uint32_t cphase = 0;
     bool ok = true;
     for (int k = 0; k < n && ok; ++k) {
-        const DropStage st = stages[s0 + k];
-        if (st.home != cur) {   // flush the window of the previous slice (all consumers)
-            __syncwarp();
-            if (lane == 0) mbar_arrive(cbar);
-            ok = mbar_wait(cbar, cphase & 1, err, 3);
-            cphase++;
-            if (!ok) break;
-            flush_w(win, Wp, delta, (int64_t)cur * slice, ctid, cthreads);
-            __syncwarp();
-            if (lane == 0) mbar_arrive(cbar);
-            ok = mbar_wait(cbar, cphase & 1, err, 3);
-            cphase++;
-            if (!ok) break;
-            cur = st.home;
-        }
         const int slot = k % kStages;
         ok = mbar_wait(full + slot, (k / kStages) & 1, err, 4);
         if (!ok) break;
+        const DropStage& st = desc[((k / kDescBatch) & 1) * kDescBatch + (k % kDescBatch)];
+        const int home = st.home, nrows = st.nrows, nent = st.nent;
+        const int64_t r0 = st.r0;
+        if (home != cur) {
+            if (cur >= 0) {   // flush the window of the previous slice (all consumers)
+                __syncwarp();
+                if (lane == 0) mbar_arrive(cbar);
+                ok = mbar_wait(cbar, cphase & 1, err, 3);
+                cphase++;
+                if (!ok) break;
+                flush_w(win, Wp, delta, (int64_t)cur * slice, ctid, cthreads);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(cbar);
+                ok = mbar_wait(cbar, cphase & 1, err, 3);
+                cphase++;
+                if (!ok) break;
+            }
+            cur = home;
+        }
         const int64_t w0 = (int64_t)cur * slice;
-        while (next < base + st.nrows) {
+        while (next < base + nrows) {
             const int j = (int)(next - base);
-            const int64_t i = st.r0 + j;
-            if (st.nent > 0) {
+            const int64_t i = r0 + j;
+            if (nent > 0) {
                 pipe_row<T, V>(ring_c + (size_t)slot * S, ring_v + (size_t)slot * S, st.off[j], st.off[j + 1], i, b,
                                inv_norm2, x, win, W, w0, delta, lambda, ss);
             } else {
@@ -216,11 +248,11 @@ drop_pipe_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict_
             }
             next += kConsumers;
         }
-        base += st.nrows;
+        base += nrows;
         __syncwarp();
         if (lane == 0) mbar_arrive(empty + slot);
     }
-    if (ok) {
+    if (ok && cur >= 0) {
         __syncwarp();
         if (lane == 0) mbar_arrive(cbar);
         if (mbar_wait(cbar, cphase & 1, err, 5)) flush_w(win, Wp, delta, (int64_t)cur * slice, ctid, cthreads);
@@ -239,7 +271,8 @@ int pipe_stage_entries(int vdt) {
 size_t pipe_smem_bytes(int cdt, int vdt, int64_t slice) {
     const size_t Wp = (size_t)((slice + 31) & ~31LL);
     const size_t S = (size_t)pipe_stage_entries(vdt);
-    return Wp * dt_size(cdt) + kStages * S * (4 + dt_size(vdt)) + (2 * kStages + 1) * sizeof(uint64_t);
+    return Wp * dt_size(cdt) + kStages * S * (4 + dt_size(vdt)) + 2 * kDescBatch * sizeof(DropStage) +
+           (2 * kStages + 3) * sizeof(uint64_t);
 }
 
 template <typename T, typename V>
