@@ -204,6 +204,48 @@ drop_block_window_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __r
     if (threadIdx.x == 0 && tot != 0.0) atomicAdd(resid_ss, tot);
 }
 
+// Plain variant on DELTA16 index storage: a warp per row; columns are decoded chunk by
+// chunk with a warp prefix sum, once for the dot product and once for the scatter.
+template <typename T, typename V>
+__global__ void __launch_bounds__(256)
+drop_block_d16_kernel(const int64_t* __restrict__ row_ptr, Delta16 d16, const V* __restrict__ val,
+                      const T* __restrict__ b, const T* __restrict__ inv_norm2, int64_t r0, int64_t r1,
+                      const T* __restrict__ x, T* __restrict__ delta, T lambda, double* resid_ss) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double ss = 0.0;
+    for (int64_t i = r0 + warp; i < r1; i += nwarps) {
+        const int64_t p0 = __ldg(row_ptr + i), p1 = __ldg(row_ptr + i + 1);
+        const int32_t base = __ldg(d16.base + i);
+        const int e0 = __ldg(d16.exc_off + i), ne = __ldg(d16.exc_off + i + 1) - e0;
+        const int2* ex = d16.exc + e0;
+        T acc = (T)0;
+        int carry = base;
+        for (int64_t pb = p0; pb < p1; pb += 32) {
+            const int64_t p = pb + lane;
+            const bool valid = p < p1;
+            const int c = decode_delta16(valid ? (int)__ldcs(d16.col16 + p) : 0, valid, (int)(p - p0), ex, ne, carry);
+            if (valid) acc += (T)to_compute(val[p]) * __ldg(x + c);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        const T res = __ldg(b + i) - acc;
+        const T r = lambda * res * __ldg(inv_norm2 + i);
+        if (lane == 0) ss += (double)res * (double)res;
+        carry = base;
+        for (int64_t pb = p0; pb < p1; pb += 32) {
+            const int64_t p = pb + lane;
+            const bool valid = p < p1;
+            const int c = decode_delta16(valid ? (int)d16.col16[p] : 0, valid, (int)(p - p0), ex, ne, carry);
+            if (valid) atomicAdd(delta + c, r * (T)to_compute(val[p]));
+        }
+    }
+    __shared__ double sh[32];
+    const double tot = block_sum(ss, sh);
+    if (threadIdx.x == 0 && tot != 0.0) atomicAdd(resid_ss, tot);
+}
+
 template <typename T>
 __global__ void drop_apply_kernel(double* __restrict__ x, float* __restrict__ x32, T* __restrict__ delta,
                                   const T* __restrict__ inv_s, int64_t V) {
@@ -256,8 +298,26 @@ static cudaError_t dispatch(const DropArgs& a, cudaStream_t s) {
     }
 }
 
+template <typename T, typename V>
+static cudaError_t launch_d16(const DropArgs& a, cudaStream_t s) {
+    drop_block_d16_kernel<T, V><<<a.grid, 256, 0, s>>>(a.row_ptr, a.d16, (const V*)a.val, (const T*)a.b,
+                                                        (const T*)a.inv_norm2, a.r0, a.r1, (const T*)a.x, (T*)a.delta,
+                                                        (T)a.lambda, a.resid_ss);
+    return cudaGetLastError();
+}
+
 cudaError_t k_drop_block(const DropArgs& a, cudaStream_t s) {
     if (a.r1 <= a.r0) return cudaSuccess;
+    if (a.use_d16) {
+        if (a.segs) return cudaErrorInvalidValue;   // the windowed schedule reads int32 columns
+        if (a.cdt == F64) return a.vdt == F64 ? launch_d16<double, double>(a, s) : cudaErrorInvalidValue;
+        switch (a.vdt) {
+            case F32: return launch_d16<float, float>(a, s);
+            case F16: return launch_d16<float, __half>(a, s);
+            case BF16: return launch_d16<float, __nv_bfloat16>(a, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     if (a.cdt == F64) {
         if (a.vdt != F64 || a.vector4) return cudaErrorInvalidValue;
         return dispatch<double, double>(a, s);

@@ -105,6 +105,38 @@ __device__ __forceinline__ void pipe_row(const int32_t* cs, const V* vs, int o0,
     for (int q = o0 + lane; q < o1; q += 32) scatter_w(win, W, w0, delta, cs[q], r * (T)to_compute(vs[q]));
 }
 
+// the same on DELTA16 storage: cs holds the row's int16 column differences
+template <typename T, typename V>
+__device__ __forceinline__ void pipe_row_d16(const int16_t* cs, const V* vs, int o0, int o1, int64_t i,
+                                             const Delta16& d16, const T* b, const T* inv_norm2, const T* x, T* win,
+                                             int W, int64_t w0, T* delta, T lambda, double& ss) {
+    const int lane = threadIdx.x & 31;
+    const T bi = __ldg(b + i), ni = __ldg(inv_norm2 + i);
+    const int32_t base = __ldg(d16.base + i);
+    const int e0 = __ldg(d16.exc_off + i), ne = __ldg(d16.exc_off + i + 1) - e0;
+    const int2* ex = d16.exc + e0;
+    T acc = (T)0;
+    int carry = base;
+    for (int qb = o0; qb < o1; qb += 32) {
+        const int q = qb + lane;
+        const bool valid = q < o1;
+        const int c = decode_delta16(valid ? (int)cs[q] : 0, valid, q - o0, ex, ne, carry);
+        if (valid) acc += (T)to_compute(vs[q]) * __ldg(x + c);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    const T res = bi - acc;
+    const T r = lambda * res * ni;
+    if (lane == 0) ss += (double)res * (double)res;
+    carry = base;
+    for (int qb = o0; qb < o1; qb += 32) {
+        const int q = qb + lane;
+        const bool valid = q < o1;
+        const int c = decode_delta16(valid ? (int)cs[q] : 0, valid, q - o0, ex, ne, carry);
+        if (valid) scatter_w(win, W, w0, delta, c, r * (T)to_compute(vs[q]));
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void flush_w(T* win, int Wp, T* delta, int64_t w0, int tid, int nthreads) {
     for (int jj = tid; jj < Wp; jj += nthreads) {
@@ -116,19 +148,20 @@ __device__ __forceinline__ void flush_w(T* win, int Wp, T* delta, int64_t w0, in
     }
 }
 
-template <typename T, typename V>
+template <typename T, typename V, typename IdxT>
 __global__ void __launch_bounds__(kThreads, 1)
-drop_pipe_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, const V* __restrict__ val,
+drop_pipe_kernel(const int64_t* __restrict__ row_ptr, const IdxT* __restrict__ col, const V* __restrict__ val,
                  const T* __restrict__ b, const T* __restrict__ inv_norm2, const DropStage* __restrict__ stages,
                  const int32_t* __restrict__ stage_begin, int64_t slice, int S, const T* __restrict__ x,
-                 T* __restrict__ delta, T lambda, double* resid_ss, int* err) {
+                 T* __restrict__ delta, T lambda, double* resid_ss, int* err, Delta16 d16) {
+    constexpr bool kD16 = sizeof(IdxT) == 2;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int W = (int)slice;
     const int Wp = (W + 31) & ~31;
     // layout: window | ring of columns | ring of values | 2 x kDescBatch descriptors | mbarriers
     T* win = reinterpret_cast<T*>(smem_raw);
-    int32_t* ring_c = reinterpret_cast<int32_t*>(smem_raw + (size_t)Wp * sizeof(T));
-    V* ring_v = reinterpret_cast<V*>(reinterpret_cast<unsigned char*>(ring_c) + (size_t)kStages * S * sizeof(int32_t));
+    IdxT* ring_c = reinterpret_cast<IdxT*>(smem_raw + (size_t)Wp * sizeof(T));
+    V* ring_v = reinterpret_cast<V*>(reinterpret_cast<unsigned char*>(ring_c) + (size_t)kStages * S * sizeof(IdxT));
     DropStage* desc = reinterpret_cast<DropStage*>(reinterpret_cast<unsigned char*>(ring_v) +
                                                    (size_t)kStages * S * sizeof(V));
     uint64_t* bars = reinterpret_cast<uint64_t*>(desc + 2 * kDescBatch);
@@ -182,7 +215,7 @@ drop_pipe_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict_
                 if (k % kDescBatch == kStages - 1 && m >= 1 && m + 1 < nb) { load_batch(m + 1); issued_b = m + 2; }
                 const DropStage& st = desc[(m & 1) * kDescBatch + (k % kDescBatch)];
                 if (st.nent > 0) {
-                    const uint32_t bc = (uint32_t)st.nent * (uint32_t)sizeof(int32_t);
+                    const uint32_t bc = (uint32_t)st.nent * (uint32_t)sizeof(IdxT);
                     const uint32_t bv = (uint32_t)st.nent * (uint32_t)sizeof(V);
                     mbar_arrive_expect_tx(full + slot, bc + bv);
                     bulk_g2s(ring_c + (size_t)slot * S, col + st.e0, bc, full + slot);
@@ -238,13 +271,24 @@ drop_pipe_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict_
         while (next < base + nrows) {
             const int j = (int)(next - base);
             const int64_t i = r0 + j;
-            if (nent > 0) {
-                pipe_row<T, V>(ring_c + (size_t)slot * S, ring_v + (size_t)slot * S, st.off[j], st.off[j + 1], i, b,
-                               inv_norm2, x, win, W, w0, delta, lambda, ss);
+            if constexpr (kD16) {
+                if (nent > 0) {
+                    pipe_row_d16<T, V>(ring_c + (size_t)slot * S, ring_v + (size_t)slot * S, st.off[j], st.off[j + 1],
+                                       i, d16, b, inv_norm2, x, win, W, w0, delta, lambda, ss);
+                } else {
+                    const int64_t p0 = row_ptr[i], p1 = row_ptr[i + 1];
+                    pipe_row_d16<T, V>(col + p0, val + p0, 0, (int)(p1 - p0), i, d16, b, inv_norm2, x, win, W, w0,
+                                       delta, lambda, ss);
+                }
             } else {
-                const int64_t p0 = row_ptr[i], p1 = row_ptr[i + 1];
-                pipe_row<T, V>(col + p0, val + p0, 0, (int)(p1 - p0), i, b, inv_norm2, x, win, W, w0, delta, lambda,
-                               ss);
+                if (nent > 0) {
+                    pipe_row<T, V>(ring_c + (size_t)slot * S, ring_v + (size_t)slot * S, st.off[j], st.off[j + 1], i,
+                                   b, inv_norm2, x, win, W, w0, delta, lambda, ss);
+                } else {
+                    const int64_t p0 = row_ptr[i], p1 = row_ptr[i + 1];
+                    pipe_row<T, V>(col + p0, val + p0, 0, (int)(p1 - p0), i, b, inv_norm2, x, win, W, w0, delta,
+                                   lambda, ss);
+                }
             }
             next += kConsumers;
         }
@@ -262,29 +306,35 @@ drop_pipe_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict_
 
 }  // namespace
 
-int pipe_stage_entries(int vdt) {
+int pipe_stage_entries(int vdt, int idx_bytes) {
     // ring of kStages slots, 64 KB in total, slot length a multiple of 8 entries
-    const int per = 4 + (int)dt_size(vdt);
+    const int per = idx_bytes + (int)dt_size(vdt);
     return ((65536 / (kStages * per)) / 8) * 8;
 }
 
-size_t pipe_smem_bytes(int cdt, int vdt, int64_t slice) {
+size_t pipe_smem_bytes(int cdt, int vdt, int idx_bytes, int64_t slice) {
     const size_t Wp = (size_t)((slice + 31) & ~31LL);
-    const size_t S = (size_t)pipe_stage_entries(vdt);
-    return Wp * dt_size(cdt) + kStages * S * (4 + dt_size(vdt)) + 2 * kDescBatch * sizeof(DropStage) +
+    const size_t S = (size_t)pipe_stage_entries(vdt, idx_bytes);
+    return Wp * dt_size(cdt) + kStages * S * (idx_bytes + dt_size(vdt)) + 2 * kDescBatch * sizeof(DropStage) +
            (2 * kStages + 3) * sizeof(uint64_t);
+}
+
+template <typename T, typename V, typename IdxT>
+static cudaError_t launch_pipe_idx(const DropPipeArgs& a, const IdxT* col, cudaStream_t s) {
+    auto kern = drop_pipe_kernel<T, V, IdxT>;
+    const size_t smem = pipe_smem_bytes(a.cdt, a.vdt, (int)sizeof(IdxT), a.slice);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<a.grid, kThreads, smem, s>>>(a.row_ptr, col, (const V*)a.val, (const T*)a.b, (const T*)a.inv_norm2,
+                                         a.stages, a.stage_begin, a.slice, pipe_stage_entries(a.vdt, sizeof(IdxT)),
+                                         (const T*)a.x, (T*)a.delta, (T)a.lambda, a.resid_ss, a.err, a.d16);
+    return cudaGetLastError();
 }
 
 template <typename T, typename V>
 static cudaError_t launch_pipe(const DropPipeArgs& a, cudaStream_t s) {
-    auto kern = drop_pipe_kernel<T, V>;
-    const size_t smem = pipe_smem_bytes(a.cdt, a.vdt, a.slice);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<a.grid, kThreads, smem, s>>>(a.row_ptr, a.col, (const V*)a.val, (const T*)a.b, (const T*)a.inv_norm2,
-                                         a.stages, a.stage_begin, a.slice, pipe_stage_entries(a.vdt), (const T*)a.x,
-                                         (T*)a.delta, (T)a.lambda, a.resid_ss, a.err);
-    return cudaGetLastError();
+    if (a.use_d16) return launch_pipe_idx<T, V, int16_t>(a, a.d16.col16, s);
+    return launch_pipe_idx<T, V, int32_t>(a, a.col, s);
 }
 
 cudaError_t k_drop_pipe(const DropPipeArgs& a, cudaStream_t s) {

@@ -150,3 +150,73 @@ cudaError_t k_inv_counts(const int32_t* cnt, void* inv_s, int cdt, int64_t n, cu
 }
 
 }  // namespace ntvs
+
+namespace ntvs {
+
+// ------------------------------------------------------------------ DELTA16 packing
+// Row i stores base[i] = col[p0] and, for every entry k of the row, the int16 difference
+// d_k = col[p0+k] - col[p0+k-1] (d_0 = 0).  A difference outside [-32767, 32767] is stored
+// as kDeltaEscape and its value goes to the row's exception list (entry index, delta).
+
+// exceptions per row
+__global__ void delta16_count_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int64_t M,
+                                     int32_t* __restrict__ cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w0; i < M; i += nw) {
+        const int64_t p0 = row_ptr[i], p1 = row_ptr[i + 1];
+        int n = 0;
+        for (int64_t p = p0 + 1 + lane; p < p1; p += 32) {
+            const int64_t d = (int64_t)col[p] - (int64_t)col[p - 1];
+            n += (d < -32767 || d > 32767) ? 1 : 0;
+        }
+        for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+        if (lane == 0) cnt[i] = n;
+    }
+}
+
+__global__ void delta16_fill_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int64_t M,
+                                    const int32_t* __restrict__ exc_off, int16_t* __restrict__ col16,
+                                    int32_t* __restrict__ base, int2* __restrict__ exc) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w0; i < M; i += nw) {
+        const int64_t p0 = row_ptr[i], p1 = row_ptr[i + 1];
+        if (lane == 0) base[i] = (p1 > p0) ? col[p0] : 0;
+        int written = 0;   // exceptions of this row written so far (warp-uniform)
+        for (int64_t pb = p0; pb < p1; pb += 32) {
+            const int64_t p = pb + lane;
+            bool esc = false;
+            int32_t d = 0;
+            if (p < p1 && p > p0) {
+                const int64_t dd = (int64_t)col[p] - (int64_t)col[p - 1];
+                esc = dd < -32767 || dd > 32767;
+                d = (int32_t)dd;
+            }
+            if (p < p1) col16[p] = esc ? (int16_t)kDeltaEscape : (int16_t)d;
+            const unsigned m = __ballot_sync(0xffffffffu, esc);
+            if (esc) {
+                const int rank = __popc(m & ((1u << lane) - 1));
+                exc[exc_off[i] + written + rank] = make_int2((int)(p - p0), d);
+            }
+            written += __popc(m);
+        }
+    }
+}
+
+cudaError_t k_delta16_count(const int64_t* row_ptr, const int32_t* col, int64_t M, int32_t* cnt, cudaStream_t s) {
+    if (M <= 0) return cudaSuccess;
+    delta16_count_kernel<<<prep_grid(), 256, 0, s>>>(row_ptr, col, M, cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t k_delta16_fill(const int64_t* row_ptr, const int32_t* col, int64_t M, const int32_t* exc_off,
+                           int16_t* col16, int32_t* base, int2* exc, cudaStream_t s) {
+    if (M <= 0) return cudaSuccess;
+    delta16_fill_kernel<<<prep_grid(), 256, 0, s>>>(row_ptr, col, M, exc_off, col16, base, exc);
+    return cudaGetLastError();
+}
+
+}  // namespace ntvs

@@ -112,6 +112,12 @@ struct ntvs_ctx {
     int32_t* stage_begin = nullptr;    // [B][win_grid + 1]
     int win_grid = 0;
     int* derr = nullptr;               // device error word (bounded waits that ran out)
+    // DELTA16 index storage (packed at load from the int32 columns)
+    int16_t* col16 = nullptr;
+    int32_t* rbase = nullptr;
+    int32_t* exc_off = nullptr;
+    int2* exc = nullptr;
+    Delta16 d16() const { return Delta16{col16, rbase, exc_off, exc}; }
 
     // image and scratch: x is the FP64 master image; x32 its FP32 copy gathered by the
     // FP32-path DROP kernels (null on the FP64 path)
@@ -162,6 +168,10 @@ struct ntvs_ctx {
         dev_free(seg_begin);
         dev_free(stages);
         dev_free(stage_begin);
+        dev_free(col16);
+        dev_free(rbase);
+        dev_free(exc_off);
+        dev_free(exc);
         schedule = NTVS_SCHED_PLAIN;
         dev_free(x);
         dev_free(x32);
@@ -355,6 +365,8 @@ int drop_block(ntvs_ctx* c, int t) {
     a.lanes_per_row = c->lpr;
     a.grid = c->drop_grid;
     a.vector4 = c->vector4;
+    a.use_d16 = c->storage == NTVS_DELTA16;
+    a.d16 = c->d16();
     a.segs = nullptr;
     a.seg_begin = nullptr;
     a.slice = (int64_t)c->nx * c->ny;
@@ -381,6 +393,8 @@ int drop_block(ntvs_ctx* c, int t) {
         pa.vdt = c->vdt;
         pa.cdt = c->cdt;
         pa.grid = c->win_grid;
+        pa.use_d16 = c->storage == NTVS_DELTA16;
+        pa.d16 = c->d16();
         CUDA_TRY(timed_launch(c, KIND_DROP, [&] { return k_drop_pipe(pa, c->stream); }));
     } else {
         CUDA_TRY(timed_launch(c, KIND_DROP, [&] { return k_drop_block(a, c->stream); }));
@@ -427,6 +441,42 @@ int copy_image_out(ntvs_ctx* c, const void* src, int sdt, void* out, int dtype, 
 }
 
 }  // namespace
+
+// ---- DELTA16 packing (load time) -----------------------------------------------------------
+// Exceptions are counted per row on the device, offsets are summed on the host, then the
+// int16 differences, row bases and exception lists are written; int32 columns that the
+// context owns are released afterwards.
+static int pack_delta16(ntvs_ctx* c) {
+    const int64_t M = c->M;
+    int32_t* cnt = nullptr;
+    TRY(dev_alloc(&cnt, sizeof(int32_t) * (size_t)std::max<int64_t>(M, 1), "DELTA16 exception counts"));
+    std::vector<int32_t> h((size_t)M + 1, 0);
+    cudaError_t e = k_delta16_count(c->row_ptr, c->col, M, cnt, c->stream);
+    if (e == cudaSuccess && M > 0)
+        e = cudaMemcpyAsync(h.data() + 1, cnt, sizeof(int32_t) * (size_t)M, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(cnt);
+    if (e != cudaSuccess) return fail(NTVS_ERR_CUDA, cuda_msg("DELTA16 exception count", e));
+    int64_t total = 0;
+    for (int64_t i = 0; i < M; ++i) {   // h[i+1] holds row i's count; turn into offsets
+        total += h[(size_t)i + 1];
+        if (total > INT32_MAX) return fail(NTVS_ERR_ARG, "DELTA16: too many escaped differences");
+        h[(size_t)i + 1] = (int32_t)total;
+    }
+    TRY(dev_alloc(&c->col16, sizeof(int16_t) * (size_t)std::max<int64_t>(c->nnz, 8), "DELTA16 columns"));
+    TRY(dev_alloc(&c->rbase, sizeof(int32_t) * (size_t)std::max<int64_t>(M, 1), "DELTA16 row bases"));
+    TRY(dev_alloc(&c->exc_off, sizeof(int32_t) * h.size(), "DELTA16 exception offsets"));
+    TRY(dev_alloc(&c->exc, sizeof(int2) * (size_t)std::max<int64_t>(total, 1), "DELTA16 exceptions"));
+    CUDA_TRY(cudaMemcpyAsync(c->exc_off, h.data(), sizeof(int32_t) * h.size(), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(k_delta16_fill(c->row_ptr, c->col, M, c->exc_off, c->col16, c->rbase, c->exc, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (c->own_col) {
+        dev_free(c->col);
+        c->own_col = false;
+    }
+    c->col = nullptr;
+    return NTVS_OK;
+}
 
 // ---- DROP schedule planning (load time) ------------------------------------------------
 // Each block's rows are cut into chunks of kChunkRows consecutive rows; a chunk's home
@@ -506,8 +556,11 @@ static int plan_schedule(ntvs_ctx* c, int requested) {
     c->win_grid = G;
 
     // pipelined schedule: cut every segment into ring-slot stages of whole rows
-    const bool aligned = ((uintptr_t)c->col % 16 == 0) && ((uintptr_t)c->val % 16 == 0);
-    const bool pipe_fits = (int64_t)pipe_smem_bytes(c->cdt, c->vdt, slice) + 1024 <= optin;
+    const bool d16 = c->storage == NTVS_DELTA16;
+    const int idx_bytes = d16 ? 2 : 4;
+    // DELTA16 columns are packed into a buffer of our own (aligned); the int32 ones may be borrowed
+    const bool aligned = (d16 || (uintptr_t)c->col % 16 == 0) && ((uintptr_t)c->val % 16 == 0);
+    const bool pipe_fits = (int64_t)pipe_smem_bytes(c->cdt, c->vdt, idx_bytes, slice) + 1024 <= optin;
     const bool want_pipe = requested == NTVS_SCHED_PIPELINE || (requested == NTVS_SCHED_AUTO && aligned && pipe_fits);
     if (want_pipe) {
         if (c->nz > 32767) return fail(NTVS_ERR_ARG, "pipelined schedule: nz > 32767");
@@ -519,8 +572,9 @@ static int plan_schedule(ntvs_ctx* c, int requested) {
         CUDA_TRY(cudaMemcpyAsync(rp.data(), c->row_ptr, sizeof(int64_t) * rp.size(), cudaMemcpyDeviceToHost,
                                  c->stream));
         CUDA_TRY(cudaStreamSynchronize(c->stream));
-        const int64_t S = pipe_stage_entries(c->vdt);
-        const int64_t A = dt_size(c->vdt) == 2 ? 8 : 4;   // entries per 16 bytes of both col and val
+        const int64_t S = pipe_stage_entries(c->vdt, idx_bytes);
+        // entries per 16 bytes of both the column and the value arrays
+        const int64_t A = 16 / std::min<int64_t>(idx_bytes, (int64_t)dt_size(c->vdt));
         auto down = [&](int64_t e) { return (e / A) * A; };
         auto up = [&](int64_t e) { return ((e + A - 1) / A) * A; };
         std::vector<DropStage> stages;
@@ -570,6 +624,12 @@ static int plan_schedule(ntvs_ctx* c, int requested) {
         return NTVS_OK;
     }
 
+    if (d16) {
+        if (requested == NTVS_SCHED_WINDOW)
+            return fail(NTVS_ERR_ARG, "windowed schedule reads int32 columns: use PIPELINE or PLAIN with DELTA16");
+        c->schedule = NTVS_SCHED_PLAIN;
+        return NTVS_OK;
+    }
     TRY(dev_alloc(&c->segs, sizeof(DropSegment) * std::max<size_t>(segs.size(), 1), "DROP segments"));
     TRY(dev_alloc(&c->seg_begin, sizeof(int32_t) * begin.size(), "DROP segment index"));
     CUDA_TRY(cudaMemcpyAsync(c->segs, segs.data(), sizeof(DropSegment) * segs.size(), cudaMemcpyHostToDevice,
@@ -670,7 +730,7 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
     if (s->n_rows < 0) return fail(NTVS_ERR_ARG, "n_rows < 0");
     if (s->val_dtype < NTVS_F64 || s->val_dtype > NTVS_BF16) return fail(NTVS_ERR_ARG, "bad val_dtype");
     if (s->mem_kind != NTVS_MEM_HOST && s->mem_kind != NTVS_MEM_DEVICE) return fail(NTVS_ERR_ARG, "bad mem_kind");
-    if (s->storage != NTVS_CSR32) return fail(NTVS_ERR_ARG, "storage: only NTVS_CSR32 is supported");
+    if (s->storage != NTVS_CSR32 && s->storage != NTVS_DELTA16) return fail(NTVS_ERR_ARG, "bad storage");
     if (s->schedule < NTVS_SCHED_AUTO || s->schedule > NTVS_SCHED_PIPELINE) return fail(NTVS_ERR_ARG, "bad schedule");
     if (!s->row_ptr) return fail(NTVS_ERR_ARG, "null row_ptr");
     const int64_t M = s->n_rows;
@@ -773,6 +833,7 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
     // which measured slower than one coalesced entry per lane; kept off
     c->vector4 = false;
     TRY(plan_schedule(c, s->schedule));
+    if (c->storage == NTVS_DELTA16) TRY(pack_delta16(c));
     {
         const int64_t need = (V + 255) / 256;
         c->apply_grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)c->sms * 8));

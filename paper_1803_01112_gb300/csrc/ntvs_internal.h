@@ -35,6 +35,21 @@ cudaError_t k_hit_counts(const int64_t* row_ptr, const int32_t* col, const void*
 // inv_s[j] = cnt[j] ? 1/cnt[j] : 0
 cudaError_t k_inv_counts(const int32_t* cnt, void* inv_s, int cdt, int64_t n, cudaStream_t s);
 
+// DELTA16 index storage: base[i] = first column of row i; col16[p] = column difference to
+// the previous entry of the row (0 for the first), or kDeltaEscape when it does not fit
+// in [-32767, 32767]; the row's escaped differences are (entry index, difference) pairs
+// exc[exc_off[i] .. exc_off[i+1]).
+constexpr int kDeltaEscape = -32768;
+struct Delta16 {
+    const int16_t* col16;
+    const int32_t* base;
+    const int32_t* exc_off;   // [M + 1]
+    const int2* exc;
+};
+cudaError_t k_delta16_count(const int64_t* row_ptr, const int32_t* col, int64_t M, int32_t* cnt, cudaStream_t s);
+cudaError_t k_delta16_fill(const int64_t* row_ptr, const int32_t* col, int64_t M, const int32_t* exc_off,
+                           int16_t* col16, int32_t* base, int2* exc, cudaStream_t s);
+
 // ------------------------------------------------------------------ TV
 // Scratch of the deterministic reductions: partials[2*grid] doubles and a ticket word
 // that the last CTA resets to 0.
@@ -79,6 +94,8 @@ struct DropArgs {
     int lanes_per_row;     // 4, 8, 16 or 32
     int grid;
     bool vector4;          // col/val 16-byte (8-byte for 2-byte values) aligned: 4-entry vector loads
+    bool use_d16;          // DELTA16 index storage (d16 below) instead of col
+    Delta16 d16;
     // windowed schedule (segs != nullptr): grid CTAs of 1024 threads, CTA c takes segments
     // [seg_begin[c], seg_begin[c+1]); shared window of one z-slice (slice = nx*ny voxels)
     const DropSegment* segs;
@@ -123,10 +140,12 @@ struct DropPipeArgs {
     int* err;                     // set (nonzero) when a bounded wait runs out
     int vdt, cdt;
     int grid;
+    bool use_d16;                 // DELTA16 index storage (d16) instead of col
+    Delta16 d16;
 };
 cudaError_t k_drop_pipe(const DropPipeArgs& a, cudaStream_t s);
-int pipe_stage_entries(int vdt);                              // entries per ring slot
-size_t pipe_smem_bytes(int cdt, int vdt, int64_t slice);      // dynamic shared memory
+int pipe_stage_entries(int vdt, int idx_bytes);                             // entries per ring slot
+size_t pipe_smem_bytes(int cdt, int vdt, int idx_bytes, int64_t slice);     // dynamic shared memory
 
 // ------------------------------------------------------------------ misc
 // sets the calling thread's ntvs_last_error() text

@@ -55,3 +55,34 @@ def oracle_run(s, val64, b64, prm: oracle.Params, K, x0, block_ptr=None, **kw):
     shape = (s.spec.nx, s.spec.ny, s.spec.nz)
     bp = s.block_ptr() if block_ptr is None else block_ptr
     return oracle.ntvs(s.row_ptr, s.col, val64, b64, bp, shape, prm, K, x0, **kw)
+
+
+def quantize(val, kind):
+    """Values as stored in half precision, returned as (array to hand to the library,
+    float64 copy of the stored values for the oracle)."""
+    import torch
+    if kind == "fp16":
+        q = np.asarray(val, np.float16)
+        return q, q.astype(np.float64)
+    if kind == "bf16":
+        t = torch.from_numpy(np.asarray(val, np.float32)).to(torch.bfloat16)
+        return t, t.to(torch.float64).numpy()
+    raise ValueError(kind)
+
+
+def roi_means(x, spec, frac=0.75):
+    """Mean of x over a circle of radius frac * (insert radius) around every insert centre,
+    in every slice, plus the background ring midway between the inserts and the cylinder."""
+    nx, ny, nz = spec.nx, spec.ny, spec.nz
+    iy, ix = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    xc = (-0.5 * nx + ix + 0.5) * spec.dx
+    yc = (-0.5 * ny + iy + 0.5) * spec.dy
+    img = np.asarray(x, np.float64).reshape(nz, ny, nx)
+    out = []
+    for ins in spec.inserts:
+        m = (xc - ins.cx) ** 2 + (yc - ins.cy) ** 2 <= (frac * ins.r) ** 2
+        out.append(img[:, m].mean())
+    rr = np.hypot(xc, yc)
+    ring = np.abs(rr - 0.3 * spec.cyl_r) <= 0.1 * spec.cyl_r
+    out.append(img[:, ring].mean())
+    return np.array(out)
