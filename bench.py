@@ -52,6 +52,7 @@ def parse_args(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mixed", type=int, default=1, help="also time BF16 lengths + DELTA16 columns (0: skip)")
     ap.add_argument("--cpu-rows", type=int, default=3_000_000, help="oracle sample: first rows of the workload")
     ap.add_argument("--ref-rows", type=int, default=1_000_000, help="reference arm: rows per step")
     ap.add_argument("--schedule", choices=["auto", "plain", "window", "pipeline"], default="auto",
@@ -177,15 +178,16 @@ def ncu_traffic_per_launch():
     return d.get("dram_bytes_per_full_launch")
 
 
-def algorithmic_drop_bytes(s, val_itemsize, b_itemsize):
+def algorithmic_drop_bytes(s, val_itemsize, b_itemsize, index_bytes=4, extra_row_bytes=0):
     """HBM bytes a DROP block launch must move, per block: each entry's value and column
-    once, plus row_ptr (8 B), b and 1/||a||^2 per row.  x and delta stay in L2."""
+    once, plus row_ptr (8 B), b and 1/||a||^2 per row (and, for DELTA16, the row's base
+    column and exception offset).  x and delta stay in L2."""
     bp = s.block_ptr()
     out = []
     for t in range(len(bp) - 1):
         r0, r1 = int(bp[t]), int(bp[t + 1])
         nnz = int(s.row_ptr[r1] - s.row_ptr[r0])
-        out.append(nnz * (val_itemsize + 4) + (r1 - r0) * (8 + 2 * b_itemsize))
+        out.append(nnz * (val_itemsize + index_bytes) + (r1 - r0) * (8 + 2 * b_itemsize + extra_row_bytes))
     return out
 
 
@@ -331,6 +333,41 @@ def run_ntvs(args):
                 "avg_launch_ms": avg_ms}
     kernel_ms = {k: prof[k] / args.steps for k in ("drop_block_ms", "drop_apply_ms", "tv_ms")}
 
+    # ---- mixed precision on the same workload: BF16 lengths + DELTA16 columns (FP32 math)
+    variants = []
+    if args.mixed and vdt == np.float32:
+        import torch as _t
+        vb = _t.from_numpy(s.val).to(_t.bfloat16)
+        rm = ntvs.Reconstructor(local, stream.cuda_stream)
+        rm.load(shape, s.row_ptr, s.col, vb, b, n_blocks=spec.n_blocks, storage=ntvs.NTVS_DELTA16, schedule=sched)
+        rm.set_params(**PARAMS)
+        rm.set_image(x0)
+        stm = rm.stats()
+        rm.run(args.warmup)
+        rm.sync()
+        barrier(world, device)
+        torch.cuda.synchronize(device)
+        rm.set_profiling(True)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            rm.run(1)
+        f1.record(stream)
+        torch.cuda.synchronize(device)
+        msm = max_over_ranks(f0.elapsed_time(f1), world, device)
+        pm = rm.profile()
+        rm.close()
+        del vb
+        bytes_m = float(np.mean(algorithmic_drop_bytes(s, 2, 4, index_bytes=2, extra_row_bytes=8))) + \
+            8.0 * stm["n_escaped"] / spec.n_blocks
+        avg_m = pm["drop_block_ms"] / max(pm["drop_block_launches"], 1)
+        variants.append({"name": "bf16 lengths + delta16 columns", "value": world * spec.n_hist * args.steps / (msm / 1e3),
+                         "unit": UNIT, "ms_per_step": msm / args.steps, "vs_fp32": ms / msm,
+                         "drop_schedule": {1: "plain", 2: "window", 3: "pipeline"}.get(stm["drop_schedule"]),
+                         "roofline": {"bound": "hbm", "achieved": bytes_m / (avg_m / 1e3) / 1e9, "peak": peak,
+                                      "unit": "GB/s", "frac": bytes_m / (avg_m / 1e3) / 1e9 / peak,
+                                      "algorithmic_bytes_per_launch": bytes_m, "avg_launch_ms": avg_m}})
+
     # ---- end to end through the C ABI from pinned host buffers
     e2e = None
     if not args.no_e2e and args.e2e_steps > 0:
@@ -374,7 +411,7 @@ def run_ntvs(args):
                            "lanes_per_row": st0["lanes_per_row"],
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "kernel_ms_per_step": kernel_ms, "clocks": clk}
+                "kernel_ms_per_step": kernel_ms, "clocks": clk, "variants": variants}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -87,10 +87,11 @@ typedef struct {
  * each 64-row chunk); one CTA per SM accumulates its slice in shared memory (needs
  * nx*ny*sizeof(compute type) of shared memory per CTA).  PIPELINE: WINDOW's grouping
  * with the matrix streamed into shared memory by the TMA engine (cp.async.bulk) ahead of
- * the consumer warps; needs 16-byte aligned col/val and 64 KB more shared memory.  AUTO
- * picks PIPELINE, else WINDOW, when the slice fits and rows come in runs of the same slice
- * (e.g. stored by projection angle, then slice), else PLAIN.  All give the same result up
- * to the order of floating-point summation. */
+ * the consumer warps; needs 16-byte aligned col/val and 64 KB more shared memory.  When
+ * the slice fits and rows come in runs of the same slice (e.g. stored by projection angle,
+ * then slice), AUTO picks WINDOW for NTVS_CSR32 storage and PIPELINE for NTVS_DELTA16
+ * (WINDOW reads int32 columns only); otherwise PLAIN.  All give the same result up to the
+ * order of floating-point summation. */
 #define NTVS_SCHED_AUTO 0
 #define NTVS_SCHED_PLAIN 1
 #define NTVS_SCHED_WINDOW 2
@@ -123,6 +124,7 @@ typedef struct {
     int64_t n_launches;    /* kernels this context has launched (all entry points)       */
     int32_t drop_schedule; /* NTVS_SCHED_PLAIN, _WINDOW or _PIPELINE (chosen at load)      */
     int32_t lanes_per_row; /* lanes per row of the DROP kernel                           */
+    int64_t n_escaped;     /* DELTA16: column differences kept in the exception lists    */
 } ntvs_stats;
 
 /* Device time of the context's kernels, measured with CUDA events recorded on the

@@ -50,7 +50,8 @@ class ntvs_stats(ctypes.Structure):
                 ("n_accepted", ctypes.c_int64), ("n_tries", ctypes.c_int64), ("nnz", ctypes.c_int64),
                 ("n_rows", ctypes.c_int64), ("n_blocks", ctypes.c_int32), ("compute_dtype", ctypes.c_int32),
                 ("last_tv", ctypes.c_double), ("n_launches", ctypes.c_int64),
-                ("drop_schedule", ctypes.c_int32), ("lanes_per_row", ctypes.c_int32)]
+                ("drop_schedule", ctypes.c_int32), ("lanes_per_row", ctypes.c_int32),
+                ("n_escaped", ctypes.c_int64)]
 
 
 class ntvs_profile(ctypes.Structure):

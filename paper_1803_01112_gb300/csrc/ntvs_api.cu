@@ -117,6 +117,7 @@ struct ntvs_ctx {
     int32_t* rbase = nullptr;
     int32_t* exc_off = nullptr;
     int2* exc = nullptr;
+    int64_t n_escaped = 0;
     Delta16 d16() const { return Delta16{col16, rbase, exc_off, exc}; }
 
     // image and scratch: x is the FP64 master image; x32 its FP32 copy gathered by the
@@ -172,6 +173,7 @@ struct ntvs_ctx {
         dev_free(rbase);
         dev_free(exc_off);
         dev_free(exc);
+        n_escaped = 0;
         schedule = NTVS_SCHED_PLAIN;
         dev_free(x);
         dev_free(x32);
@@ -467,6 +469,7 @@ static int pack_delta16(ntvs_ctx* c) {
     TRY(dev_alloc(&c->rbase, sizeof(int32_t) * (size_t)std::max<int64_t>(M, 1), "DELTA16 row bases"));
     TRY(dev_alloc(&c->exc_off, sizeof(int32_t) * h.size(), "DELTA16 exception offsets"));
     TRY(dev_alloc(&c->exc, sizeof(int2) * (size_t)std::max<int64_t>(total, 1), "DELTA16 exceptions"));
+    c->n_escaped = total;
     CUDA_TRY(cudaMemcpyAsync(c->exc_off, h.data(), sizeof(int32_t) * h.size(), cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(k_delta16_fill(c->row_ptr, c->col, M, c->exc_off, c->col16, c->rbase, c->exc, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -561,7 +564,11 @@ static int plan_schedule(ntvs_ctx* c, int requested) {
     // DELTA16 columns are packed into a buffer of our own (aligned); the int32 ones may be borrowed
     const bool aligned = (d16 || (uintptr_t)c->col % 16 == 0) && ((uintptr_t)c->val % 16 == 0);
     const bool pipe_fits = (int64_t)pipe_smem_bytes(c->cdt, c->vdt, idx_bytes, slice) + 1024 <= optin;
-    const bool want_pipe = requested == NTVS_SCHED_PIPELINE || (requested == NTVS_SCHED_AUTO && aligned && pipe_fits);
+    // AUTO: int32 columns take the windowed kernel (measured faster than the pipelined one
+    // on the 200x200x16 workload); DELTA16 columns, which the windowed kernel does not
+    // read, take the pipelined one when it fits
+    const bool want_pipe = requested == NTVS_SCHED_PIPELINE ||
+                           (requested == NTVS_SCHED_AUTO && d16 && aligned && pipe_fits);
     if (want_pipe) {
         if (c->nz > 32767) return fail(NTVS_ERR_ARG, "pipelined schedule: nz > 32767");
         if (!aligned || !pipe_fits) {
@@ -952,6 +959,7 @@ int ntvs_get_stats(ntvs_ctx* c, ntvs_stats* st) {
     st->n_launches = c->n_launches;
     st->drop_schedule = c->schedule;
     st->lanes_per_row = c->lpr;
+    st->n_escaped = c->n_escaped;
     if (c->k > 0 && c->tvhist) {
         CUDA_TRY(cudaMemcpyAsync(c->hscal, c->tvhist + (c->k - 1), sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         CUDA_TRY(cudaStreamSynchronize(c->stream));

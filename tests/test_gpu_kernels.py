@@ -156,7 +156,7 @@ def test_drop_schedules_match_oracle(dtype, schedule):
         r.load((40, 40, 5), s.row_ptr, s.col, val, b, n_blocks=4, schedule=code)
         st = r.stats()
         if schedule == "auto":
-            assert st["drop_schedule"] == NTVS_SCHED_PIPELINE   # rows come in runs of one slice
+            assert st["drop_schedule"] == NTVS_SCHED_WINDOW   # rows come in runs of one slice
         else:
             assert st["drop_schedule"] == code
         r.set_params(lam=1.1, N=0, alpha=0.5)
