@@ -333,40 +333,45 @@ def run_ntvs(args):
                 "avg_launch_ms": avg_ms}
     kernel_ms = {k: prof[k] / args.steps for k in ("drop_block_ms", "drop_apply_ms", "tv_ms")}
 
-    # ---- mixed precision on the same workload: BF16 lengths + DELTA16 columns (FP32 math)
+    # ---- mixed precision on the same workload (FP32 arithmetic): BF16 lengths with int32
+    # or DELTA16 columns
     variants = []
     if args.mixed and vdt == np.float32:
         import torch as _t
         vb = _t.from_numpy(s.val).to(_t.bfloat16)
-        rm = ntvs.Reconstructor(local, stream.cuda_stream)
-        rm.load(shape, s.row_ptr, s.col, vb, b, n_blocks=spec.n_blocks, storage=ntvs.NTVS_DELTA16, schedule=sched)
-        rm.set_params(**PARAMS)
-        rm.set_image(x0)
-        stm = rm.stats()
-        rm.run(args.warmup)
-        rm.sync()
-        barrier(world, device)
-        torch.cuda.synchronize(device)
-        rm.set_profiling(True)
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        for _ in range(args.steps):
-            rm.run(1)
-        f1.record(stream)
-        torch.cuda.synchronize(device)
-        msm = max_over_ranks(f0.elapsed_time(f1), world, device)
-        pm = rm.profile()
-        rm.close()
+        for name, storage, ib in (("bf16 lengths + int32 columns", ntvs.NTVS_CSR32, 4),
+                                  ("bf16 lengths + delta16 columns", ntvs.NTVS_DELTA16, 2)):
+            rm = ntvs.Reconstructor(local, stream.cuda_stream)
+            rm.load(shape, s.row_ptr, s.col, vb, b, n_blocks=spec.n_blocks, storage=storage, schedule=sched)
+            rm.set_params(**PARAMS)
+            rm.set_image(x0)
+            stm = rm.stats()
+            rm.run(args.warmup)
+            rm.sync()
+            barrier(world, device)
+            torch.cuda.synchronize(device)
+            rm.set_profiling(True)
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for _ in range(args.steps):
+                rm.run(1)
+            f1.record(stream)
+            torch.cuda.synchronize(device)
+            msm = max_over_ranks(f0.elapsed_time(f1), world, device)
+            pm = rm.profile()
+            rm.close()
+            extra = 8 if storage == ntvs.NTVS_DELTA16 else 0
+            bytes_m = float(np.mean(algorithmic_drop_bytes(s, 2, 4, index_bytes=ib, extra_row_bytes=extra))) + \
+                8.0 * stm["n_escaped"] / spec.n_blocks
+            avg_m = pm["drop_block_ms"] / max(pm["drop_block_launches"], 1)
+            ach = bytes_m / (avg_m / 1e3) / 1e9
+            variants.append({"name": name, "value": world * spec.n_hist * args.steps / (msm / 1e3), "unit": UNIT,
+                             "ms_per_step": msm / args.steps, "vs_fp32": ms / msm,
+                             "drop_schedule": {1: "plain", 2: "window", 3: "pipeline"}.get(stm["drop_schedule"]),
+                             "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                                          "frac": ach / peak, "algorithmic_bytes_per_launch": bytes_m,
+                                          "avg_launch_ms": avg_m}})
         del vb
-        bytes_m = float(np.mean(algorithmic_drop_bytes(s, 2, 4, index_bytes=2, extra_row_bytes=8))) + \
-            8.0 * stm["n_escaped"] / spec.n_blocks
-        avg_m = pm["drop_block_ms"] / max(pm["drop_block_launches"], 1)
-        variants.append({"name": "bf16 lengths + delta16 columns", "value": world * spec.n_hist * args.steps / (msm / 1e3),
-                         "unit": UNIT, "ms_per_step": msm / args.steps, "vs_fp32": ms / msm,
-                         "drop_schedule": {1: "plain", 2: "window", 3: "pipeline"}.get(stm["drop_schedule"]),
-                         "roofline": {"bound": "hbm", "achieved": bytes_m / (avg_m / 1e3) / 1e9, "peak": peak,
-                                      "unit": "GB/s", "frac": bytes_m / (avg_m / 1e3) / 1e9 / peak,
-                                      "algorithmic_bytes_per_launch": bytes_m, "avg_launch_ms": avg_m}})
 
     # ---- end to end through the C ABI from pinned host buffers
     e2e = None

@@ -89,9 +89,9 @@ typedef struct {
  * with the matrix streamed into shared memory by the TMA engine (cp.async.bulk) ahead of
  * the consumer warps; needs 16-byte aligned col/val and 64 KB more shared memory.  When
  * the slice fits and rows come in runs of the same slice (e.g. stored by projection angle,
- * then slice), AUTO picks WINDOW for NTVS_CSR32 storage and PIPELINE for NTVS_DELTA16
- * (WINDOW reads int32 columns only); otherwise PLAIN.  All give the same result up to the
- * order of floating-point summation. */
+ * then slice), AUTO picks WINDOW (measured fastest); otherwise PLAIN.  Every schedule reads
+ * both index storages.  All give the same result up to the order of floating-point
+ * summation. */
 #define NTVS_SCHED_AUTO 0
 #define NTVS_SCHED_PLAIN 1
 #define NTVS_SCHED_WINDOW 2

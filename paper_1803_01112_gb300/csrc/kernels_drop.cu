@@ -126,6 +126,71 @@ __device__ __forceinline__ void drop_row(int64_t i, bool valid, int sub, const i
         scatter<T, WIN>(delta, w, col[p], r * (T)to_compute(val[p]));
 }
 
+// drop_row on DELTA16 storage, a warp per row: each 32-entry chunk is decoded once (warp
+// prefix sum of the int16 differences, escapes from the row's exception list) into the
+// same registers the CSR32 path loads; long-row tails decode on the fly.
+template <typename T, typename V, int CH, bool WIN>
+__device__ __forceinline__ void drop_row_d16(int64_t i, bool valid, const int64_t* __restrict__ row_ptr,
+                                             const Delta16& d16, const V* __restrict__ val, const T* __restrict__ b,
+                                             const T* __restrict__ inv_norm2, const T* __restrict__ x,
+                                             T* __restrict__ delta, T lambda, const Window& w, double& ss) {
+    const int lane = threadIdx.x & 31;
+    int64_t p0 = 0, p1 = 0;
+    int32_t base = 0;
+    int e0 = 0, ne = 0;
+    if (valid) {
+        p0 = __ldg(row_ptr + i);
+        p1 = __ldg(row_ptr + i + 1);
+        base = __ldg(d16.base + i);
+        e0 = __ldg(d16.exc_off + i);
+        ne = __ldg(d16.exc_off + i + 1) - e0;
+    }
+    const int2* ex = d16.exc + e0;
+    int32_t c[CH];
+    T a[CH];
+    int carry = base;
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+        const int64_t p = p0 + lane + (int64_t)u * 32;
+        const bool ok = p < p1;
+        int dd = 0;
+        if (ok) { dd = __ldcs(d16.col16 + p); a[u] = (T)to_compute(val[p]); } else { a[u] = (T)0; }
+        const int cc = decode_delta16(dd, ok, (int)(p - p0), ex, ne, carry);
+        c[u] = ok ? cc : -1;
+    }
+    const int tail_carry = carry;
+    const int64_t tail0 = p0 + (int64_t)CH * 32;
+    T acc = (T)0;
+#pragma unroll
+    for (int u = 0; u < CH; ++u)
+        if (c[u] >= 0) acc += a[u] * __ldg(x + c[u]);
+    carry = tail_carry;
+    for (int64_t pb = tail0; pb < p1; pb += 32) {
+        const int64_t p = pb + lane;
+        const bool ok = p < p1;
+        const int cc = decode_delta16(ok ? (int)d16.col16[p] : 0, ok, (int)(p - p0), ex, ne, carry);
+        if (ok) acc += (T)to_compute(val[p]) * __ldg(x + cc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    T r = (T)0;
+    if (valid) {
+        const T res = __ldg(b + i) - acc;
+        r = lambda * res * __ldg(inv_norm2 + i);
+        if (lane == 0) ss += (double)res * (double)res;
+    }
+#pragma unroll
+    for (int u = 0; u < CH; ++u)
+        if (c[u] >= 0) scatter<T, WIN>(delta, w, c[u], r * a[u]);
+    carry = tail_carry;
+    for (int64_t pb = tail0; pb < p1; pb += 32) {
+        const int64_t p = pb + lane;
+        const bool ok = p < p1;
+        const int cc = decode_delta16(ok ? (int)d16.col16[p] : 0, ok, (int)(p - p0), ex, ne, carry);
+        if (ok) scatter<T, WIN>(delta, w, cc, r * (T)to_compute(val[p]));
+    }
+}
+
 // Plain variant: grid-stride over the rows of the block.
 template <typename T, typename V, int LPR, int CH, int VW>
 __global__ void __launch_bounds__(256)
@@ -161,13 +226,13 @@ __device__ __forceinline__ void flush_window(T* win, int Wp, T* delta, int64_t w
     }
 }
 
-template <typename T, typename V, int LPR, int CH, int VW>
+template <typename T, typename V, int LPR, int CH, int VW, bool D16>
 __global__ void __launch_bounds__(1024, 1)
 drop_block_window_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                          const V* __restrict__ val, const T* __restrict__ b, const T* __restrict__ inv_norm2,
                          const DropSegment* __restrict__ segs, const int32_t* __restrict__ seg_begin,
                          int64_t slice, const T* __restrict__ x, T* __restrict__ delta, T lambda,
-                         double* resid_ss) {
+                         double* resid_ss, Delta16 d16) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* win = reinterpret_cast<T*>(smem_raw);
     const int W = (int)slice;
@@ -193,8 +258,12 @@ drop_block_window_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __r
         }
         for (int64_t base = sg.r0 + (int64_t)warp * G; base < sg.r1; base += (int64_t)nwarps * G) {
             const int64_t i = base + lane / LPR;
-            drop_row<T, V, LPR, CH, VW, true>(i, i < sg.r1, lane % LPR, row_ptr, col, val, b, inv_norm2, x, delta,
-                                              lambda, w, ss);
+            if constexpr (D16) {
+                drop_row_d16<T, V, CH, true>(i, i < sg.r1, row_ptr, d16, val, b, inv_norm2, x, delta, lambda, w, ss);
+            } else {
+                drop_row<T, V, LPR, CH, VW, true>(i, i < sg.r1, lane % LPR, row_ptr, col, val, b, inv_norm2, x, delta,
+                                                  lambda, w, ss);
+            }
         }
     }
     __syncthreads();
@@ -258,16 +327,21 @@ __global__ void drop_apply_kernel(double* __restrict__ x, float* __restrict__ x3
 }
 
 // ------------------------------------------------------------------ launch
+template <typename T, typename V, int LPR, int CH, int VW, bool D16>
+static cudaError_t launch_window(const DropArgs& a, cudaStream_t s) {
+    auto kern = drop_block_window_kernel<T, V, LPR, CH, VW, D16>;
+    const size_t smem = (size_t)((a.slice + 31) & ~31LL) * sizeof(T);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<a.grid, 1024, smem, s>>>(a.row_ptr, a.col, (const V*)a.val, (const T*)a.b, (const T*)a.inv_norm2, a.segs,
+                                    a.seg_begin, a.slice, (const T*)a.x, (T*)a.delta, (T)a.lambda, a.resid_ss, a.d16);
+    return cudaGetLastError();
+}
+
 template <typename T, typename V, int LPR, int CH, int VW>
 static cudaError_t launch_cfg(const DropArgs& a, cudaStream_t s) {
     if (a.segs) {
-        auto kern = drop_block_window_kernel<T, V, LPR, CH, VW>;
-        const size_t smem = (size_t)((a.slice + 31) & ~31LL) * sizeof(T);
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        kern<<<a.grid, 1024, smem, s>>>(a.row_ptr, a.col, (const V*)a.val, (const T*)a.b, (const T*)a.inv_norm2,
-                                        a.segs, a.seg_begin, a.slice, (const T*)a.x, (T*)a.delta, (T)a.lambda,
-                                        a.resid_ss);
+        return launch_window<T, V, LPR, CH, VW, false>(a, s);
     } else {
         drop_block_kernel<T, V, LPR, CH, VW><<<a.grid, 256, 0, s>>>(
             a.row_ptr, a.col, (const V*)a.val, (const T*)a.b, (const T*)a.inv_norm2, a.r0, a.r1, (const T*)a.x,
@@ -309,7 +383,16 @@ static cudaError_t launch_d16(const DropArgs& a, cudaStream_t s) {
 cudaError_t k_drop_block(const DropArgs& a, cudaStream_t s) {
     if (a.r1 <= a.r0) return cudaSuccess;
     if (a.use_d16) {
-        if (a.segs) return cudaErrorInvalidValue;   // the windowed schedule reads int32 columns
+        if (a.segs) {   // windowed: a warp per row, 12 register chunks
+            if (a.cdt == F64) return a.vdt == F64 ? launch_window<double, double, 32, 12, 1, true>(a, s)
+                                                  : cudaErrorInvalidValue;
+            switch (a.vdt) {
+                case F32: return launch_window<float, float, 32, 12, 1, true>(a, s);
+                case F16: return launch_window<float, __half, 32, 12, 1, true>(a, s);
+                case BF16: return launch_window<float, __nv_bfloat16, 32, 12, 1, true>(a, s);
+                default: return cudaErrorInvalidValue;
+            }
+        }
         if (a.cdt == F64) return a.vdt == F64 ? launch_d16<double, double>(a, s) : cudaErrorInvalidValue;
         switch (a.vdt) {
             case F32: return launch_d16<float, float>(a, s);

@@ -564,11 +564,9 @@ static int plan_schedule(ntvs_ctx* c, int requested) {
     // DELTA16 columns are packed into a buffer of our own (aligned); the int32 ones may be borrowed
     const bool aligned = (d16 || (uintptr_t)c->col % 16 == 0) && ((uintptr_t)c->val % 16 == 0);
     const bool pipe_fits = (int64_t)pipe_smem_bytes(c->cdt, c->vdt, idx_bytes, slice) + 1024 <= optin;
-    // AUTO: int32 columns take the windowed kernel (measured faster than the pipelined one
-    // on the 200x200x16 workload); DELTA16 columns, which the windowed kernel does not
-    // read, take the pipelined one when it fits
-    const bool want_pipe = requested == NTVS_SCHED_PIPELINE ||
-                           (requested == NTVS_SCHED_AUTO && d16 && aligned && pipe_fits);
+    // AUTO takes the windowed kernel (measured faster than the pipelined one on the
+    // 200x200x16 workload); the pipelined one only on request
+    const bool want_pipe = requested == NTVS_SCHED_PIPELINE;
     if (want_pipe) {
         if (c->nz > 32767) return fail(NTVS_ERR_ARG, "pipelined schedule: nz > 32767");
         if (!aligned || !pipe_fits) {
@@ -631,12 +629,6 @@ static int plan_schedule(ntvs_ctx* c, int requested) {
         return NTVS_OK;
     }
 
-    if (d16) {
-        if (requested == NTVS_SCHED_WINDOW)
-            return fail(NTVS_ERR_ARG, "windowed schedule reads int32 columns: use PIPELINE or PLAIN with DELTA16");
-        c->schedule = NTVS_SCHED_PLAIN;
-        return NTVS_OK;
-    }
     TRY(dev_alloc(&c->segs, sizeof(DropSegment) * std::max<size_t>(segs.size(), 1), "DROP segments"));
     TRY(dev_alloc(&c->seg_begin, sizeof(int32_t) * begin.size(), "DROP segment index"));
     CUDA_TRY(cudaMemcpyAsync(c->segs, segs.data(), sizeof(DropSegment) * segs.size(), cudaMemcpyHostToDevice,

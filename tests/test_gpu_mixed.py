@@ -30,12 +30,12 @@ def _sweep(ntvs, shape, rp, col, val, b, nb, x0, lam, storage, schedule):
         r.close()
 
 
-@pytest.mark.parametrize("schedule", ["plain", "pipeline"])
+@pytest.mark.parametrize("schedule", ["plain", "window", "pipeline"])
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
 def test_delta16_is_lossless(schedule, dtype):
     ntvs = ntvs_module()
-    from paper_1803_01112_gb300._ffi import NTVS_DELTA16, NTVS_SCHED_PIPELINE, NTVS_SCHED_PLAIN
-    sched = {"plain": NTVS_SCHED_PLAIN, "pipeline": NTVS_SCHED_PIPELINE}[schedule]
+    from paper_1803_01112_gb300._ffi import NTVS_DELTA16, NTVS_SCHED_PIPELINE, NTVS_SCHED_PLAIN, NTVS_SCHED_WINDOW
+    sched = {"plain": NTVS_SCHED_PLAIN, "window": NTVS_SCHED_WINDOW, "pipeline": NTVS_SCHED_PIPELINE}[schedule]
     s = synth.generate(synth.spec_scaled_3d(nx=40, ny=40, nz=6, n_hist=30_000, n_angles=36, n_blocks=4, seed=12))
     val, b = s.val.astype(dtype), s.b.astype(dtype)
     x0 = s.xstar * 0.9 + 0.05
