@@ -234,6 +234,42 @@ int ntvs_drop_block(ntvs_ctx* ctx, int t);
 /* One full DROP sweep P_T (blocks 0..B-1 in order). */
 int ntvs_drop_sweep(ntvs_ctx* ctx);
 
+/* ---- batched reconstructions ----------------------------------------------------------
+ * Many independent NTVS reconstructions (Appendix C, without the TV check) advanced
+ * together on one GPU: every member has its own grid, system, blocks and parameters, and
+ * one cycle of all members costs one kernel launch per step type (2*N_max TV launches,
+ * 3 per DROP block step, 2 more), replayed from a CUDA graph; only the members' step sizes
+ * beta_{k,n} (host-drawn ell schedules, as in ntvs_run) are copied in per cycle.  Members
+ * take FP32 values in CSR32 storage (host or device arrays, copied at ntvs_batch_add).
+ * The DROP kernel's lanes per row are chosen at finalize by timing block step 0. */
+typedef struct ntvs_batch ntvs_batch;
+
+typedef struct {
+    int32_t members;            /* reconstructions in the batch                          */
+    int32_t lanes_per_row;      /* DROP lanes per row picked by the finalize-time tuning  */
+    int64_t cycles;             /* cycles run                                             */
+    int64_t n_launches;         /* kernels launched by ntvs_batch_run                     */
+    int64_t kernels_per_cycle;  /* kernels in one cycle's graph                           */
+    int64_t total_rows, total_nnz, total_voxels;
+} ntvs_batch_stats;
+
+int ntvs_batch_create(ntvs_batch** out, int device, void* cuda_stream);
+int ntvs_batch_destroy(ntvs_batch* bt);
+/* Add a member: system (val_dtype NTVS_F32, storage NTVS_CSR32, validated on the host),
+ * parameters (tv_check must be 0) and initial image x0 (V values, F64 or F32, host or
+ * device).  *index (may be NULL) receives the member's index.  Before finalize only. */
+int ntvs_batch_add(ntvs_batch* bt, const ntvs_system* sys, const ntvs_params* p, const void* x0, int x0_dtype,
+                   int x0_mem, int* index);
+/* Build the work lists, tune the DROP kernel and capture the cycle graph; max_cycles
+ * bounds the cycles that may be run (per-member phi history). */
+int ntvs_batch_finalize(ntvs_batch* bt, int max_cycles);
+/* Run k_iters cycles of every member (queued on the batch's stream). */
+int ntvs_batch_run(ntvs_batch* bt, int k_iters);
+/* Member `index`'s image (synchronous); phi after its last cycle (FP64). */
+int ntvs_batch_get_image(ntvs_batch* bt, int index, void* out, int dtype, int mem_kind);
+int ntvs_batch_get_tv(ntvs_batch* bt, int index, double* tv);
+int ntvs_batch_get_stats(ntvs_batch* bt, ntvs_batch_stats* st);
+
 /* ---- allocation-free entry point --------------------------------------------------- */
 
 /* phi(x) of a caller-owned image, for callers that cannot allocate device memory: code

@@ -226,6 +226,70 @@ def ntvs_drop_sweep(ctx: int) -> None:
     check(lib().ntvs_drop_sweep(ctx), "ntvs_drop_sweep")
 
 
+def _system_struct(nx, ny, nz, row_ptr, col, val, b, n_blocks=1, block_ptr=None, storage=NTVS_CSR32, schedule=0):
+    rp, kind = _ptr_kind(row_ptr)
+    cp, _ = _ptr_kind(col)
+    vptr, _ = _ptr_kind(val)
+    bptr, _ = _ptr_kind(b)
+    bp = None
+    if block_ptr is not None:
+        bp = np.ascontiguousarray(block_ptr, dtype=np.int64)
+        n_blocks = bp.size - 1
+    nrows = (row_ptr.numel() if _is_torch(row_ptr) else row_ptr.size) - 1
+    st = _ffi.ntvs_system(nx, ny, nz, n_blocks, nrows, rp, cp, vptr, bptr, None if bp is None else bp.ctypes.data,
+                          _dtype_code(val), kind, storage, schedule)
+    return st, bp
+
+
+def ntvs_batch_create(device: int = 0, stream: Optional[int] = None) -> int:
+    h = ctypes.c_void_p()
+    if stream is not None and int(stream) == 0:
+        stream = 1   # cudaStreamLegacy
+    check(lib().ntvs_batch_create(ctypes.byref(h), device, stream), "ntvs_batch_create")
+    return h.value
+
+
+def ntvs_batch_destroy(bt: int) -> None:
+    check(lib().ntvs_batch_destroy(bt), "ntvs_batch_destroy")
+
+
+def ntvs_batch_add(bt: int, shape, row_ptr, col, val, b, n_blocks: int, params: "Params", x0, block_ptr=None) -> int:
+    nx, ny, nz = shape
+    st, _keep = _system_struct(nx, ny, nz, row_ptr, col, val, b, n_blocks, block_ptr)
+    p = _ffi.ntvs_params(params.lam, params.alpha, params.beta0, params.eps_tv, params.N, int(bool(params.tv_check)),
+                         params.max_retries, 0, params.seed)
+    xp, xk = _ptr_kind(x0)
+    idx = ctypes.c_int()
+    check(lib().ntvs_batch_add(bt, ctypes.byref(st), ctypes.byref(p), xp, _dtype_code(x0), xk, ctypes.byref(idx)),
+          "ntvs_batch_add")
+    return idx.value
+
+
+def ntvs_batch_finalize(bt: int, max_cycles: int) -> None:
+    check(lib().ntvs_batch_finalize(bt, max_cycles), "ntvs_batch_finalize")
+
+
+def ntvs_batch_run(bt: int, k_iters: int) -> None:
+    check(lib().ntvs_batch_run(bt, k_iters), "ntvs_batch_run")
+
+
+def ntvs_batch_get_image(bt: int, index: int, out) -> None:
+    ptr, kind = _ptr_kind(out)
+    check(lib().ntvs_batch_get_image(bt, index, ptr, _dtype_code(out), kind), "ntvs_batch_get_image")
+
+
+def ntvs_batch_get_tv(bt: int, index: int) -> float:
+    v = ctypes.c_double()
+    check(lib().ntvs_batch_get_tv(bt, index, ctypes.byref(v)), "ntvs_batch_get_tv")
+    return v.value
+
+
+def ntvs_batch_get_stats(bt: int) -> dict:
+    st = _ffi.ntvs_batch_stats()
+    check(lib().ntvs_batch_get_stats(bt, ctypes.byref(st)), "ntvs_batch_get_stats")
+    return {f: getattr(st, f) for f, _ in _ffi.ntvs_batch_stats._fields_}
+
+
 def ntvs_tv_value_static(x, shape, out, stream: Optional[int] = None) -> None:
     """phi(x) into out[0] without any allocation (see include/ntvs.h): x and out are CUDA
     tensors owned by the caller (x float64/float32 of nx*ny*nz values, out one float64)."""
@@ -248,6 +312,49 @@ class Params:
     seed: int = 0
     eps_tv: float = 1e-8
     max_retries: int = 64
+
+
+class Batch:
+    """Independent reconstructions advanced together (see ntvs_batch_* in include/ntvs.h)."""
+
+    def __init__(self, device: int = 0, stream: Optional[int] = None):
+        self._bt = ntvs_batch_create(device, stream)
+        self.shapes = []
+
+    def add(self, shape, row_ptr, col, val, b, n_blocks: int, params: "Params", x0, block_ptr=None) -> int:
+        i = ntvs_batch_add(self._bt, shape, row_ptr, col, val, b, n_blocks, params, x0, block_ptr)
+        self.shapes.append(tuple(shape))
+        return i
+
+    def finalize(self, max_cycles: int = 1024):
+        ntvs_batch_finalize(self._bt, max_cycles)
+        return self
+
+    def run(self, k: int):
+        ntvs_batch_run(self._bt, k)
+        return self
+
+    def get_image(self, index: int, dtype=np.float64) -> np.ndarray:
+        out = np.empty(int(np.prod(self.shapes[index])), dtype)
+        ntvs_batch_get_image(self._bt, index, out)
+        return out
+
+    def tv(self, index: int) -> float:
+        return ntvs_batch_get_tv(self._bt, index)
+
+    def stats(self) -> dict:
+        return ntvs_batch_get_stats(self._bt)
+
+    def close(self):
+        if self._bt:
+            ntvs_batch_destroy(self._bt)
+            self._bt = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Reconstructor:

@@ -60,6 +60,12 @@ class ntvs_profile(ctypes.Structure):
                 ("tv_ms", ctypes.c_double), ("tv_launches", ctypes.c_int64)]
 
 
+class ntvs_batch_stats(ctypes.Structure):
+    _fields_ = [("members", ctypes.c_int32), ("lanes_per_row", ctypes.c_int32), ("cycles", ctypes.c_int64),
+                ("n_launches", ctypes.c_int64), ("kernels_per_cycle", ctypes.c_int64), ("total_rows", ctypes.c_int64),
+                ("total_nnz", ctypes.c_int64), ("total_voxels", ctypes.c_int64)]
+
+
 vp, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
 P = ctypes.POINTER
 
@@ -89,6 +95,15 @@ SIGNATURES = {
     "ntvs_perturb_checked": (ctypes.c_int, [vp, d, P(ctypes.c_int), P(d), P(d)]),
     "ntvs_drop_block": (ctypes.c_int, [vp, ctypes.c_int]),
     "ntvs_drop_sweep": (ctypes.c_int, [vp]),
+    "ntvs_batch_create": (ctypes.c_int, [P(vp), ctypes.c_int, vp]),
+    "ntvs_batch_destroy": (ctypes.c_int, [vp]),
+    "ntvs_batch_add": (ctypes.c_int, [vp, P(ntvs_system), P(ntvs_params), vp, ctypes.c_int, ctypes.c_int,
+                                      P(ctypes.c_int)]),
+    "ntvs_batch_finalize": (ctypes.c_int, [vp, ctypes.c_int]),
+    "ntvs_batch_run": (ctypes.c_int, [vp, ctypes.c_int]),
+    "ntvs_batch_get_image": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int]),
+    "ntvs_batch_get_tv": (ctypes.c_int, [vp, ctypes.c_int, P(d)]),
+    "ntvs_batch_get_stats": (ctypes.c_int, [vp, P(ntvs_batch_stats)]),
     "ntvs_tv_value_static": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]),
 }
 
