@@ -53,6 +53,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mixed", type=int, default=1, help="also time BF16 lengths + DELTA16 columns (0: skip)")
+    ap.add_argument("--batched", type=int, default=1, help="also time the batched parameter sweep (0: skip)")
+    ap.add_argument("--batch-members", type=int, default=64)
+    ap.add_argument("--batch-scale", type=float, default=1.0)
     ap.add_argument("--cpu-rows", type=int, default=3_000_000, help="oracle sample: first rows of the workload")
     ap.add_argument("--ref-rows", type=int, default=1_000_000, help="reference arm: rows per step")
     ap.add_argument("--schedule", choices=["auto", "plain", "window", "pipeline"], default="auto",
@@ -251,6 +254,76 @@ def run_reference(args):
     return 0
 
 
+def batch_members(n_members, seed=4, scale=1.0):
+    """Members of the batched sweep: grids nx = ny in {64..128} (step 8), nz in {8..16},
+    histories U(0.05, 0.4) * 1e6 * scale, and (N, alpha, lambda) drawn from
+    {1..6} x {0.5, 0.6, 0.75, 0.9} x {1e-4, 2e-4, 5e-4} without repetition."""
+    import synth
+    rng = np.random.default_rng(seed)
+    combos = [(N, a, l) for N in range(1, 7) for a in (0.5, 0.6, 0.75, 0.9) for l in (1e-4, 2e-4, 5e-4)]
+    pick = rng.choice(len(combos), size=n_members, replace=n_members > len(combos))
+    out = []
+    for k in range(n_members):
+        n = int(rng.integers(8, 17)) * 8
+        nz = int(rng.integers(8, 17))
+        m = int(rng.uniform(0.05, 0.4) * 1e6 * scale)
+        N, a, l = combos[pick[k]]
+        out.append((synth.spec_batch_member(1000 + k, n, n, nz, m), dict(lam=l, N=N, alpha=a, seed=2000 + k)))
+    return out
+
+
+def run_batched_variant(args, ntvs, local, stream, world, device):
+    import torch
+
+    import synth
+    members = batch_members(args.batch_members, scale=args.batch_scale)
+    systems = [(synth.generate(sp, np.float32), prm) for sp, prm in members]
+    total_rows = sum(s.M for s, _ in systems)
+    bt = ntvs.Batch(local, stream.cuda_stream)
+    for s, prm in systems:
+        sp = s.spec
+        bt.add((sp.nx, sp.ny, sp.nz), s.row_ptr, s.col, s.val, s.b.astype(np.float32), sp.n_blocks,
+               ntvs.Params(**prm), s.xbar)
+    bt.finalize(max_cycles=args.warmup + args.steps + 1)
+    bt.run(args.warmup)
+    torch.cuda.synchronize(device)
+    barrier(world, device)
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    bt.run(args.steps)
+    g1.record(stream)
+    torch.cuda.synchronize(device)
+    ms_b = max_over_ranks(g0.elapsed_time(g1), world, device)
+    bst = bt.stats()
+    bt.close()
+    # the same members one after another through single contexts (FP32, default schedule)
+    seq_ms = 0.0
+    for s, prm in systems:
+        sp = s.spec
+        r = ntvs.Reconstructor(local, stream.cuda_stream)
+        r.load((sp.nx, sp.ny, sp.nz), s.row_ptr, s.col, s.val, s.b.astype(np.float32), n_blocks=sp.n_blocks)
+        r.set_params(**prm)
+        r.set_image(s.xbar)
+        r.run(1)
+        r.sync()
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        r.run(args.steps)
+        h1.record(stream)
+        torch.cuda.synchronize(device)
+        seq_ms += h0.elapsed_time(h1)
+        r.close()
+    seq_ms = max_over_ranks(seq_ms, world, device)
+    return {"name": f"batched sweep of {len(systems)} members", "value": world * total_rows * args.steps / (ms_b / 1e3),
+            "unit": UNIT, "ms_per_step": ms_b / args.steps,
+            "sequential_value": world * total_rows * args.steps / (seq_ms / 1e3),
+            "vs_sequential": seq_ms / ms_b, "members": len(systems), "total_histories": int(total_rows),
+            "total_nnz": int(bst["total_nnz"]), "kernels_per_cycle": int(bst["kernels_per_cycle"]),
+            "lanes_per_row": int(bst["lanes_per_row"]),
+            "recipe": "nx=ny in {64..128}, nz in {8..16}, 0.05-0.4M bent histories each (scaled by batch_scale), "
+                      "4-8 random inserts, 20 blocks, (N, alpha, lambda) from the 72-combination sweep, no TV check"}
+
+
 def run_ntvs(args):
     import torch
 
@@ -372,6 +445,10 @@ def run_ntvs(args):
                                           "frac": ach / peak, "algorithmic_bytes_per_launch": bytes_m,
                                           "avg_launch_ms": avg_m}})
         del vb
+
+    # ---- batched reconstructions: a parameter sweep over members of uneven size
+    if args.batched:
+        variants.append(run_batched_variant(args, ntvs, local, stream, world, device))
 
     # ---- end to end through the C ABI from pinned host buffers
     e2e = None

@@ -162,6 +162,26 @@ def spec_scaled_3d(nx=40, ny=40, nz=4, n_hist=40_000, n_angles=60, n_blocks=5, s
                 dev_max=min(2.0, 2.0 * s * 2))
 
 
+def spec_batch_member(seed: int, nx: int, ny: int, nz: int, n_hist: int, n_blocks: int = 20) -> Spec:
+    """One member of a batched parameter sweep: a cylinder filling the grid with 4-8 random,
+    non-overlapping cylindrical inserts of RSP U[0, 1.8]; bent paths over 90 angles."""
+    rng = np.random.default_rng(seed)
+    R = 0.45 * min(nx, ny)
+    ins = []
+    for _ in range(200):
+        if len(ins) >= int(rng.integers(4, 9)):
+            break
+        r = float(rng.uniform(0.06, 0.12) * R)
+        rho = float(rng.uniform(0.0, 0.75 * R))
+        phi = float(rng.uniform(0.0, 2.0 * math.pi))
+        cx, cy = rho * math.cos(phi), rho * math.sin(phi)
+        if all((cx - i.cx) ** 2 + (cy - i.cy) ** 2 > (r + i.r + 1.0) ** 2 for i in ins) and rho + r < R - 1.0:
+            ins.append(Insert(cx, cy, r, float(rng.uniform(0.0, 1.8))))
+    return Spec(name=f"member{seed}_{nx}x{ny}x{nz}_{n_hist}", nx=nx, ny=ny, nz=nz, dx=1.0, dy=1.0, dz=2.5,
+                cyl_r=R, cyl_rsp=1.0, inserts=tuple(ins), n_hist=n_hist, n_angles=90, curved=True,
+                n_blocks=n_blocks, seed=seed)
+
+
 @dataclasses.dataclass
 class System:
     spec: Spec
