@@ -96,6 +96,7 @@ typedef struct {
 #define NTVS_SCHED_PLAIN 1
 #define NTVS_SCHED_WINDOW 2
 #define NTVS_SCHED_PIPELINE 3
+#define NTVS_SCHED_ONTHEFLY 4   /* reported for systems loaded with ntvs_load_paths */
 
 /* Parameters of NTVS (Sec. II-E, Appendix A/C). */
 typedef struct {
@@ -160,6 +161,36 @@ int ntvs_destroy(ntvs_ctx* ctx);
  * Errors: NTVS_ERR_ARG (sizes, dtypes, V > 2^31-1), NTVS_ERR_CSR (validation),
  * NTVS_ERR_OOM, NTVS_ERR_CUDA.  Synchronous. */
 int ntvs_load_system(ntvs_ctx* ctx, const ntvs_system* sys);
+
+/* A system given as proton paths instead of a stored matrix: row i of A is traced from
+ * history i's path every DROP sweep (Sec. I: rows are the intersection lengths of each
+ * tracked proton with the voxels).  Path record i (10 floats, mm): chord start P_in (x,y,z),
+ * chord end P_out (x,y,z), offsets (A_lat, B_lat, A_z, B_z); the path is
+ *   P(s) = P_in + s (P_out - P_in) + (A_lat h10(s) + B_lat h11(s)) n + (A_z h10(s) + B_z h11(s)) e_z
+ * for s in [0,1], h10 = s^3 - 2 s^2 + s, h11 = s^3 - s^2, n = (-u_y, u_x, 0) the in-plane unit
+ * normal of the chord, cut into n_seg straight segments.  Each segment is cut at the voxel
+ * planes it crosses and each piece (FP32 geometry) is credited to the voxel holding its
+ * midpoint; pieces shorter than min_len are dropped.  Voxels are dx x dy x dz with the grid
+ * origin at (-nx dx/2, -ny dy/2, 0). */
+typedef struct {
+    int32_t nx, ny, nz;
+    int32_t n_blocks;            /* contiguous blocks of ceil(M/B) rows when block_ptr is NULL */
+    double dx, dy, dz;           /* voxel size (mm)                                            */
+    int64_t n_rows;              /* M                                                          */
+    const float* paths;          /* [M][10] path records (mem_kind)                            */
+    const float* b;              /* [M] WEPL (mem_kind)                                        */
+    const int64_t* block_ptr;    /* NULL or [B+1] HOST array                                   */
+    int32_t n_seg;               /* straight segments per path, 1..64                          */
+    int32_t mem_kind;            /* NTVS_MEM_HOST (copied) | NTVS_MEM_DEVICE (borrowed)        */
+    double min_len;              /* pieces shorter than this are dropped (mm), >= 0            */
+} ntvs_paths;
+
+/* Load (replace) the system as paths (FP32 arithmetic).  At load one thread per row
+ * traces the path, merges the pieces of one voxel at segment joins and computes ||a_i||^2
+ * (FP64) and the hit counts s_j^t; every DROP sweep traces the paths again.  Resets the
+ * image and the run state like ntvs_load_system.  Errors: NTVS_ERR_ARG, NTVS_ERR_CSR
+ * (non-finite path or b), NTVS_ERR_OOM, NTVS_ERR_CUDA. */
+int ntvs_load_paths(ntvs_ctx* ctx, const ntvs_paths* p);
 
 /* Set the NTVS parameters (Appendix C).  Validated: N >= 0, 0 < alpha < 1, beta0 >= 0,
  * eps_tv >= 0, lambda finite, max_retries >= 1 when tv_check.  Default before the first

@@ -117,6 +117,24 @@ def ntvs_load_system(ctx: int, nx: int, ny: int, nz: int, row_ptr, col, val, b, 
     check(lib().ntvs_load_system(ctx, ctypes.byref(s)), "ntvs_load_system")
 
 
+def ntvs_load_paths(ctx: int, nx: int, ny: int, nz: int, voxel, paths, b, n_blocks: int = 1, block_ptr=None,
+                    n_seg: int = 16, min_len: float = 1e-4) -> None:
+    """paths: float32 [M, 10] records, b: float32 [M]; numpy (host) or CUDA tensors (device)."""
+    pp, kind = _ptr_kind(paths)
+    bp_, kb = _ptr_kind(b)
+    if kind != kb:
+        raise ValueError("paths and b must both be host arrays or both device tensors")
+    nrows = (paths.shape[0])
+    bp = None
+    if block_ptr is not None:
+        bp = np.ascontiguousarray(block_ptr, dtype=np.int64)
+        n_blocks = bp.size - 1
+    dx, dy, dz = voxel
+    st = _ffi.ntvs_paths(nx, ny, nz, n_blocks, dx, dy, dz, nrows, pp, bp_, None if bp is None else bp.ctypes.data,
+                         n_seg, kind, min_len)
+    check(lib().ntvs_load_paths(ctx, ctypes.byref(st)), "ntvs_load_paths")
+
+
 def ntvs_set_params(ctx: int, lam: float, N: int, alpha: float, beta0: float = 1.0, tv_check: bool = False,
                     seed: int = 0, eps_tv: float = 1e-8, max_retries: int = 64) -> None:
     p = _ffi.ntvs_params(lam, alpha, beta0, eps_tv, N, int(bool(tv_check)), max_retries, 0, seed)
@@ -387,6 +405,15 @@ class Reconstructor:
         nx, ny, nz = shape
         ntvs_load_system(self._ctx, nx, ny, nz, row_ptr, col, val, b, n_blocks, block_ptr, storage, schedule)
         self._keep = (row_ptr, col, val, b) if _is_torch(row_ptr) and row_ptr.is_cuda else ()
+        self.shape = (nx, ny, nz)
+        self.n_blocks = (len(block_ptr) - 1) if block_ptr is not None else n_blocks
+        return self
+
+    def load_paths(self, shape, voxel, paths, b, n_blocks: int = 1, block_ptr=None, n_seg: int = 16,
+                   min_len: float = 1e-4):
+        nx, ny, nz = shape
+        ntvs_load_paths(self._ctx, nx, ny, nz, voxel, paths, b, n_blocks, block_ptr, n_seg, min_len)
+        self._keep = (paths, b) if _is_torch(paths) and paths.is_cuda else ()
         self.shape = (nx, ny, nz)
         self.n_blocks = (len(block_ptr) - 1) if block_ptr is not None else n_blocks
         return self

@@ -23,7 +23,7 @@ NTVS_ERR_STATE = -6
 NTVS_F64, NTVS_F32, NTVS_F16, NTVS_BF16 = 0, 1, 2, 3
 NTVS_MEM_HOST, NTVS_MEM_DEVICE = 0, 1
 NTVS_CSR32, NTVS_DELTA16 = 0, 1
-NTVS_SCHED_AUTO, NTVS_SCHED_PLAIN, NTVS_SCHED_WINDOW, NTVS_SCHED_PIPELINE = 0, 1, 2, 3
+NTVS_SCHED_AUTO, NTVS_SCHED_PLAIN, NTVS_SCHED_WINDOW, NTVS_SCHED_PIPELINE, NTVS_SCHED_ONTHEFLY = 0, 1, 2, 3, 4
 
 ERROR_NAMES = {NTVS_ERR_ARG: "NTVS_ERR_ARG", NTVS_ERR_CSR: "NTVS_ERR_CSR", NTVS_ERR_OOM: "NTVS_ERR_OOM",
                NTVS_ERR_CUDA: "NTVS_ERR_CUDA", NTVS_ERR_TIMEOUT: "NTVS_ERR_TIMEOUT",
@@ -37,6 +37,14 @@ class ntvs_system(ctypes.Structure):
                 ("b", ctypes.c_void_p), ("block_ptr", ctypes.c_void_p),
                 ("val_dtype", ctypes.c_int32), ("mem_kind", ctypes.c_int32),
                 ("storage", ctypes.c_int32), ("schedule", ctypes.c_int32)]
+
+
+class ntvs_paths(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("n_blocks", ctypes.c_int32),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("n_rows", ctypes.c_int64), ("paths", ctypes.c_void_p), ("b", ctypes.c_void_p),
+                ("block_ptr", ctypes.c_void_p), ("n_seg", ctypes.c_int32), ("mem_kind", ctypes.c_int32),
+                ("min_len", ctypes.c_double)]
 
 
 class ntvs_params(ctypes.Structure):
@@ -77,6 +85,7 @@ SIGNATURES = {
     "ntvs_destroy": (ctypes.c_int, [vp]),
     "ntvs_load_system": (ctypes.c_int, [vp, P(ntvs_system)]),
     "ntvs_set_params": (ctypes.c_int, [vp, P(ntvs_params)]),
+    "ntvs_load_paths": (ctypes.c_int, [vp, P(ntvs_paths)]),
     "ntvs_set_image": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int]),
     "ntvs_get_image": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int]),
     "ntvs_run": (ctypes.c_int, [vp, ctypes.c_int]),

@@ -118,6 +118,11 @@ struct ntvs_ctx {
     int32_t* exc_off = nullptr;
     int2* exc = nullptr;
     int64_t n_escaped = 0;
+    // on-the-fly rows (ntvs_load_paths): path records and b, traced every sweep
+    bool paths_mode = false;
+    float* paths = nullptr;
+    bool own_paths = false;
+    OtfArgs otf{};
     Delta16 d16() const { return Delta16{col16, rbase, exc_off, exc}; }
 
     // image and scratch: x is the FP64 master image; x32 its FP32 copy gathered by the
@@ -174,6 +179,10 @@ struct ntvs_ctx {
         dev_free(exc_off);
         dev_free(exc);
         n_escaped = 0;
+        if (own_paths) dev_free(paths);
+        paths = nullptr;
+        own_paths = false;
+        paths_mode = false;
         schedule = NTVS_SCHED_PLAIN;
         dev_free(x);
         dev_free(x32);
@@ -350,6 +359,17 @@ int drop_block(ntvs_ctx* c, int t) {
     const int64_t r0 = c->block_ptr[t], r1 = c->block_ptr[t + 1];
     CUDA_TRY(cudaMemsetAsync(c->resid + t, 0, sizeof(double), c->stream));
     if (r1 <= r0) return NTVS_OK;
+    if (c->paths_mode) {
+        CUDA_TRY(timed_launch(c, KIND_DROP, [&] {
+            return k_otf_drop(c->otf, r0, r1, (const float*)c->inv_norm2, c->x32, (float*)c->delta, c->p.lambda,
+                              c->resid + t, c->stream);
+        }));
+        CUDA_TRY(timed_launch(c, KIND_APPLY, [&] {
+            return k_drop_apply(c->cdt, c->x, c->x32, c->delta, (const char*)c->inv_s + (size_t)t * c->V * c->csz(),
+                                c->V, c->apply_grid, c->stream);
+        }));
+        return NTVS_OK;
+    }
     DropArgs a;
     a.row_ptr = c->row_ptr;
     a.col = c->col;
@@ -839,6 +859,101 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
     }
     c->red.grid = red_grid(V, c->sms);
 
+    c->k = 0;
+    c->ell_prev = 0;
+    c->ell_trace.clear();
+    c->tries_trace.clear();
+    c->acc_trace.clear();
+    c->n_steps = c->n_accepted = c->n_tries = 0;
+    CUDA_TRY(cudaStreamSynchronize(st));
+    c->loaded = true;
+    return NTVS_OK;
+}
+
+int ntvs_load_paths(ntvs_ctx* c, const ntvs_paths* s) {
+    TRY(use_device(c));
+    if (!s) return fail(NTVS_ERR_ARG, "null paths");
+    if (s->nx < 1 || s->ny < 1 || s->nz < 1) return fail(NTVS_ERR_ARG, "grid sizes must be >= 1");
+    const int64_t V = (int64_t)s->nx * s->ny * s->nz;
+    if (V > 0x7fffffffLL) return fail(NTVS_ERR_ARG, "V exceeds the int32 voxel range");
+    if (!(s->dx > 0 && s->dy > 0 && s->dz > 0)) return fail(NTVS_ERR_ARG, "voxel sizes must be > 0");
+    if (s->n_seg < 1 || s->n_seg > 64) return fail(NTVS_ERR_ARG, "n_seg must be in [1, 64]");
+    if (!(s->min_len >= 0)) return fail(NTVS_ERR_ARG, "min_len must be >= 0");
+    if (s->n_rows < 0) return fail(NTVS_ERR_ARG, "n_rows < 0");
+    if (s->mem_kind != NTVS_MEM_HOST && s->mem_kind != NTVS_MEM_DEVICE) return fail(NTVS_ERR_ARG, "bad mem_kind");
+    const int64_t M = s->n_rows;
+    if (M > 0 && (!s->paths || !s->b)) return fail(NTVS_ERR_ARG, "null paths or b");
+    std::vector<int64_t> bp;
+    if (s->block_ptr) {
+        if (s->n_blocks < 1) return fail(NTVS_ERR_ARG, "n_blocks must be >= 1 with block_ptr");
+        bp.assign(s->block_ptr, s->block_ptr + s->n_blocks + 1);
+        if (bp.front() != 0 || bp.back() != M) return fail(NTVS_ERR_ARG, "block_ptr must run from 0 to n_rows");
+        for (int t = 0; t < s->n_blocks; ++t)
+            if (bp[t] > bp[t + 1]) return fail(NTVS_ERR_ARG, "block_ptr decreases");
+    } else {
+        if (s->n_blocks < 1) return fail(NTVS_ERR_ARG, "n_blocks must be >= 1");
+        const int64_t per = (M + s->n_blocks - 1) / s->n_blocks;
+        for (int t = 0; t <= s->n_blocks; ++t) bp.push_back(std::min<int64_t>((int64_t)t * per, M));
+    }
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->free_system();
+    cudaStream_t st = c->stream;
+    c->nx = s->nx; c->ny = s->ny; c->nz = s->nz;
+    c->V = V;
+    c->M = M;
+    c->B = (int)bp.size() - 1;
+    c->block_ptr = bp;
+    c->vdt = F32;
+    c->cdt = F32;
+    c->storage = NTVS_CSR32;
+    c->nnz = 0;
+    TRY(copy_in((void**)&c->paths, &c->own_paths, s->paths, sizeof(float) * 10 * (size_t)M, s->mem_kind, st, "paths"));
+    TRY(copy_in(&c->b, &c->own_b, s->b, sizeof(float) * (size_t)M, s->mem_kind, st, "b"));
+    c->paths_mode = true;
+    OtfArgs& o = c->otf;
+    o.paths = c->paths;
+    o.b = (const float*)c->b;
+    o.M = M;
+    o.nx = s->nx; o.ny = s->ny; o.nz = s->nz;
+    o.dx = s->dx; o.dy = s->dy; o.dz = s->dz;
+    o.n_seg = s->n_seg;
+    o.min_len = (float)s->min_len;
+    o.grid = c->sms * 8;
+    CUDA_TRY(cudaMemsetAsync(c->dflags, 0, sizeof(int), st));
+    CUDA_TRY(k_otf_validate(o, c->dflags, st));
+    CUDA_TRY(cudaMemcpyAsync(c->hint, c->dflags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (c->hint[0]) {
+        const int f = c->hint[0];
+        c->free_system();
+        return fail(NTVS_ERR_CSR, (f & 32) ? "non-finite path record" : "non-finite right-hand side");
+    }
+    TRY(dev_alloc(&c->inv_norm2, sizeof(float) * (size_t)std::max<int64_t>(M, 1), "inv_norm2"));
+    int32_t* cnt = nullptr;
+    TRY(dev_alloc(&cnt, sizeof(int32_t) * (size_t)c->B * V, "hit counts"));
+    CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)c->B * V, st));
+    for (int t = 0; t < c->B; ++t)
+        CUDA_TRY(k_otf_prep(o, bp[t], bp[t + 1], (float*)c->inv_norm2, cnt + (size_t)t * V, st));
+    TRY(dev_alloc(&c->inv_s, sizeof(float) * (size_t)c->B * V, "inverse hit counts"));
+    CUDA_TRY(k_inv_counts(cnt, c->inv_s, F32, (int64_t)c->B * V, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    dev_free(cnt);
+    TRY(dev_alloc(&c->x, sizeof(double) * (size_t)V, "x"));
+    TRY(dev_alloc(&c->x32, sizeof(float) * (size_t)V, "x32"));
+    TRY(dev_alloc(&c->delta, sizeof(float) * (size_t)V, "delta"));
+    TRY(dev_alloc(&c->g, sizeof(float) * (size_t)V, "g"));
+    TRY(dev_alloc(&c->resid, sizeof(double) * (size_t)c->B, "residuals"));
+    CUDA_TRY(cudaMemsetAsync(c->x, 0, sizeof(double) * (size_t)V, st));
+    CUDA_TRY(cudaMemsetAsync(c->x32, 0, sizeof(float) * (size_t)V, st));
+    CUDA_TRY(cudaMemsetAsync(c->delta, 0, sizeof(float) * (size_t)V, st));
+    CUDA_TRY(cudaMemsetAsync(c->resid, 0, sizeof(double) * (size_t)c->B, st));
+    c->lpr = 16;
+    c->schedule = NTVS_SCHED_ONTHEFLY;
+    {
+        const int64_t need = (V + 255) / 256;
+        c->apply_grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)c->sms * 8));
+    }
+    c->red.grid = red_grid(V, c->sms);
     c->k = 0;
     c->ell_prev = 0;
     c->ell_trace.clear();

@@ -147,6 +147,23 @@ cudaError_t k_drop_pipe(const DropPipeArgs& a, cudaStream_t s);
 int pipe_stage_entries(int vdt, int idx_bytes);                             // entries per ring slot
 size_t pipe_smem_bytes(int cdt, int vdt, int idx_bytes, int64_t slice);     // dynamic shared memory
 
+// ------------------------------------------------------------------ on-the-fly rows
+struct OtfArgs {
+    const float* paths;   // [M][10]
+    const float* b;       // [M]
+    int64_t M;
+    int nx, ny, nz;
+    double dx, dy, dz;
+    int n_seg;
+    float min_len;
+    int grid;
+};
+cudaError_t k_otf_validate(const OtfArgs& a, int* flags, cudaStream_t s);
+// inv_norm2 of rows [r0, r1) and the block's hit counts cnt (+= 1 per distinct voxel)
+cudaError_t k_otf_prep(const OtfArgs& a, int64_t r0, int64_t r1, float* inv_norm2, int32_t* cnt, cudaStream_t s);
+cudaError_t k_otf_drop(const OtfArgs& a, int64_t r0, int64_t r1, const float* inv_norm2, const float* x, float* delta,
+                       double lambda, double* resid_ss, cudaStream_t s);
+
 // ------------------------------------------------------------------ misc
 // sets the calling thread's ntvs_last_error() text
 void set_last_error(const std::string& msg);

@@ -72,6 +72,10 @@ def _lib():
         L.syn_count.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int64, vp, vp, vp, vp, vp]
         L.syn_fill.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int64, vp, vp, vp, vp, vp, vp, vp, ctypes.c_int32,
                                vp, vp]
+        L.syn_paths.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int64, vp, vp, vp, vp, vp]
+        L.syn_rhs.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int64, vp, vp, vp, vp, vp, vp]
+        L.syn_paths.restype = None
+        L.syn_rhs.restype = None
         L.syn_splitmix64_at.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
         L.syn_splitmix64_at.restype = ctypes.c_uint64
         for f in ("syn_phantom", "syn_plan", "syn_count", "syn_fill"):
@@ -274,6 +278,58 @@ def generate(spec: Spec, val_dtype=np.float64,
                row_ptr.ctypes.data, col.ctypes.data, val.ctypes.data,
                0 if val_dtype == np.float64 else 1, b.ctypes.data, xstar.ctypes.data)
     return System(spec, row_ptr, col, val, b, xstar, xbar, label, angle, t, z)
+
+
+@dataclasses.dataclass
+class Paths:
+    """Histories as path records (float32 [M, 10]: P_in xyz, P_out xyz, A_lat, B_lat, A_z,
+    B_z; see ntvs_synth.c) with their WEPL b, the phantom and the initial iterate."""
+    spec: Spec
+    paths: np.ndarray
+    b: np.ndarray
+    xstar: np.ndarray
+    xbar: np.ndarray
+    label: np.ndarray
+
+    @property
+    def M(self) -> int:
+        return int(self.paths.shape[0])
+
+
+def generate_paths(spec: Spec, rows: Optional[Tuple[int, int]] = None, with_rhs: bool = True) -> Paths:
+    """The same histories as ``generate`` (same rows, same b) as path records, without the
+    matrix; b is traced row by row without being stored."""
+    keep = []
+    c = _cfg(spec, keep)
+    L = _lib()
+    M = spec.n_hist
+    xstar, xbar, label = phantom(spec)
+    t = np.empty(M, np.float64)
+    z = np.empty(M, np.float64)
+    key = np.empty(M, np.uint64)
+    angle = np.empty(M, np.int32)
+    L.syn_plan(ctypes.byref(c), t.ctypes.data, z.ctypes.data, key.ctypes.data, angle.ctypes.data)
+    if rows is not None:
+        r0, r1 = rows
+        t, z, key, angle = (np.ascontiguousarray(a[r0:r1]) for a in (t, z, key, angle))
+        M = r1 - r0
+    paths = np.empty((M, 10), np.float32)
+    L.syn_paths(ctypes.byref(c), M, t.ctypes.data, z.ctypes.data, key.ctypes.data, angle.ctypes.data,
+                paths.ctypes.data)
+    b = np.zeros(M, np.float64)
+    if with_rhs:
+        L.syn_rhs(ctypes.byref(c), M, t.ctypes.data, z.ctypes.data, key.ctypes.data, angle.ctypes.data,
+                  b.ctypes.data, xstar.ctypes.data)
+    return Paths(spec, paths, b, xstar, xbar, label)
+
+
+def spec_large_onthefly(seed: int = 5, n_hist: int = 60_000_000) -> Spec:
+    """256x256x64 voxels of 0.8x0.8x1.25 mm, 720 angles, bent paths, 40 blocks (the grid is
+    scaled from the CTP404 layout)."""
+    s = 256 * 0.8 / 200.0
+    return Spec(name=f"ctp404_256x256x64_onthefly_{n_hist}", nx=256, ny=256, nz=64, dx=0.8, dy=0.8, dz=1.25,
+                cyl_r=75.0 * s, cyl_rsp=1.0, inserts=_ring(8, 60.0 * s, 6.1 * s, CTP404_SIM_RSP),
+                n_hist=n_hist, n_angles=720, curved=True, n_blocks=40, seed=seed)
 
 
 def splitmix64_at(seed: int, n: int) -> int:

@@ -387,3 +387,73 @@ void syn_fill(const syn_cfg* c, int64_t n, const double* t, const double* z, con
 
 /* raw SplitMix64 stream value, exported for tests of the generator itself */
 uint64_t syn_splitmix64_at(uint64_t seed, uint64_t n) { return sm64_at(seed, n); }
+
+/* ------------------------------------------------------------ path records */
+/* The path of row r as 10 floats: chord start P_in (x, y, z), chord end P_out (x, y, z),
+ * and the cubic-Hermite offset coefficients (A_lat, B_lat, A_z, B_z): the path is
+ *   P(s) = P_in + s (P_out - P_in) + (A_lat h10(s) + B_lat h11(s)) n + (A_z h10(s) + B_z h11(s)) e_z,
+ * s in [0, 1], n the in-plane unit normal (-u_y, u_x) of the chord direction u, split into
+ * n_seg straight segments at s = q / n_seg.  Rows whose line misses the grid get
+ * P_in = P_out (an empty row). */
+void syn_paths(const syn_cfg* c, int64_t n, const double* t, const double* z, const uint64_t* key,
+               const int32_t* angle, float* out) {
+    #pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < n; ++r) {
+        float* o = out + 10 * r;
+        double th = (c->angle_span_deg * angle[r] / c->n_angles) * (M_PI / 180.0);
+        double ux = cos(th), uy = sin(th), nxv = -sin(th), nyv = cos(th);
+        double hx = 0.5 * c->nx * c->dx, hy = 0.5 * c->ny * c->dy;
+        double lo = -1e300, hi = 1e300;
+        double px = t[r] * nxv, py = t[r] * nyv;
+        int miss = 0;
+        if (ux != 0.0) {
+            double s0 = (-hx - px) / ux, s1 = (hx - px) / ux;
+            if (s0 > s1) { double q = s0; s0 = s1; s1 = q; }
+            if (s0 > lo) lo = s0;
+            if (s1 < hi) hi = s1;
+        } else if (px < -hx || px > hx) miss = 1;
+        if (uy != 0.0) {
+            double s0 = (-hy - py) / uy, s1 = (hy - py) / uy;
+            if (s0 > s1) { double q = s0; s0 = s1; s1 = q; }
+            if (s0 > lo) lo = s0;
+            if (s1 < hi) hi = s1;
+        } else if (py < -hy || py > hy) miss = 1;
+        if (miss || !(hi > lo)) {
+            for (int k = 0; k < 10; ++k) o[k] = 0.0f;
+            continue;
+        }
+        lo -= 1.0; hi += 1.0;
+        o[0] = (float)(px + lo * ux); o[1] = (float)(py + lo * uy); o[2] = (float)z[r];
+        o[3] = (float)(px + hi * ux); o[4] = (float)(py + hi * uy); o[5] = (float)z[r];
+        if (c->curved) {
+            double k = (27.0 / 8.0) * c->dev_max;
+            o[6] = (float)((2.0 * u01(c->seed, key[r] * DRAWS_PER_HIST + 2) - 1.0) * k);
+            o[7] = (float)((2.0 * u01(c->seed, key[r] * DRAWS_PER_HIST + 3) - 1.0) * k);
+            o[8] = (float)((2.0 * u01(c->seed, key[r] * DRAWS_PER_HIST + 4) - 1.0) * k);
+            o[9] = (float)((2.0 * u01(c->seed, key[r] * DRAWS_PER_HIST + 5) - 1.0) * k);
+        } else {
+            o[6] = o[7] = o[8] = o[9] = 0.0f;
+        }
+    }
+}
+
+/* b of rows 0..n-1 without storing them: the same trace and noise as syn_fill. */
+void syn_rhs(const syn_cfg* c, int64_t n, const double* t, const double* z, const uint64_t* key,
+             const int32_t* angle, double* b, const double* xstar) {
+    #pragma omp parallel
+    {
+        rowbuf rb; rb_init(&rb);
+        double* sbuf = (double*)malloc(sizeof(double) * (size_t)seg_scratch(c));
+        #pragma omp for schedule(dynamic, 1024)
+        for (int64_t r = 0; r < n; ++r) {
+            trace_row(c, t[r], z[r], key[r], angle[r], &rb, sbuf);
+            double wepl = 0.0;
+            for (int i = 0; i < rb.n; ++i) wepl += rb.len[i] * xstar[rb.col[i]];
+            double u1 = 1.0 - u01(c->seed, key[r] * DRAWS_PER_HIST + 6);
+            double u2 = u01(c->seed, key[r] * DRAWS_PER_HIST + 7);
+            double gauss = sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+            b[r] = wepl * (1.0 + c->noise_sigma * gauss);
+        }
+        free(sbuf); rb_free(&rb);
+    }
+}

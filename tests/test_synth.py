@@ -111,3 +111,37 @@ def test_row_range_equals_slice_of_whole_system():
     np.testing.assert_array_equal(part.col, whole.col[p0:p1])
     np.testing.assert_array_equal(part.val, whole.val[p0:p1])
     np.testing.assert_array_equal(part.b, whole.b[1200:3100])
+
+
+def test_path_records_match_the_traced_rows():
+    """A path record re-traced on the CPU (a plain polyline walk) gives the generator's row."""
+    sp = synth.spec_scaled_3d(nx=30, ny=26, nz=4, n_hist=400)
+    s = synth.generate(sp)
+    pr = synth.generate_paths(sp)
+    np.testing.assert_allclose(pr.b, s.b, rtol=1e-12)
+    o = np.array([-0.5 * sp.nx * sp.dx, -0.5 * sp.ny * sp.dy, 0.0])
+    h = np.array([sp.dx, sp.dy, sp.dz])
+    n = np.array([sp.nx, sp.ny, sp.nz])
+    for r in range(0, s.M, 23):
+        p = pr.paths[r].astype(np.float64)
+        P, Q, A = p[0:3], p[3:6], p[6:10]
+        u = (Q[:2] - P[:2]) / np.linalg.norm(Q[:2] - P[:2])
+        nv = np.array([-u[1], u[0], 0.0])
+        sg = np.linspace(0.0, 1.0, sp.n_seg + 1)
+        h10, h11 = sg ** 3 - 2 * sg ** 2 + sg, sg ** 3 - sg ** 2
+        pts = P[None] + sg[:, None] * (Q - P)[None] + (A[0] * h10 + A[1] * h11)[:, None] * nv[None]
+        pts[:, 2] += A[2] * h10 + A[3] * h11
+        acc = {}
+        for a, bq in zip(pts[:-1], pts[1:]):   # fine sampling of each segment
+            ts = np.linspace(0.0, 1.0, 4001)
+            mid = a[None] + ((ts[:-1] + ts[1:]) / 2)[:, None] * (bq - a)[None]
+            idx = np.floor((mid - o) / h).astype(int)
+            ok = np.all((idx >= 0) & (idx < n), axis=1)
+            seg_len = np.linalg.norm(bq - a) / 4000
+            for j in ((idx[ok, 2] * sp.ny + idx[ok, 1]) * sp.nx + idx[ok, 0]):
+                acc[j] = acc.get(j, 0.0) + seg_len
+        cols = s.col[s.row_ptr[r]:s.row_ptr[r + 1]]
+        vals = s.val[s.row_ptr[r]:s.row_ptr[r + 1]]
+        assert np.sum(vals) == pytest.approx(sum(acc.values()), rel=2e-3, abs=2e-3)
+        big = {j for j, v in acc.items() if v > 0.05}
+        assert big <= set(cols.tolist())
