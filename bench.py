@@ -56,6 +56,8 @@ def parse_args(argv=None):
     ap.add_argument("--batched", type=int, default=1, help="also time the batched parameter sweep (0: skip)")
     ap.add_argument("--batch-members", type=int, default=64)
     ap.add_argument("--batch-scale", type=float, default=1.0)
+    ap.add_argument("--onthefly", type=int, default=1, help="also time on-the-fly rows on the 256x256x64 grid")
+    ap.add_argument("--otf-histories", type=int, default=6_000_000)
     ap.add_argument("--cpu-rows", type=int, default=3_000_000, help="oracle sample: first rows of the workload")
     ap.add_argument("--ref-rows", type=int, default=1_000_000, help="reference arm: rows per step")
     ap.add_argument("--schedule", choices=["auto", "plain", "window", "pipeline"], default="auto",
@@ -324,6 +326,43 @@ def run_batched_variant(args, ntvs, local, stream, world, device):
                       "4-8 random inserts, 20 blocks, (N, alpha, lambda) from the 72-combination sweep, no TV check"}
 
 
+def run_onthefly_variant(args, ntvs, local, stream, world, device):
+    """256x256x64 grid (0.8x0.8x1.25 mm), bent paths over 720 angles, 40 blocks, N = 4,
+    rows traced in every sweep from 44-byte history records (10 path floats + b)."""
+    import torch
+
+    import synth
+    spec = synth.spec_large_onthefly(n_hist=args.otf_histories)
+    pr = synth.generate_paths(spec)
+    r = ntvs.Reconstructor(local, stream.cuda_stream)
+    r.load_paths((spec.nx, spec.ny, spec.nz), (spec.dx, spec.dy, spec.dz), pr.paths, pr.b.astype(np.float32),
+                 n_blocks=spec.n_blocks, n_seg=spec.n_seg, min_len=spec.min_len)
+    r.set_params(lam=2e-4, N=4, alpha=0.75, seed=5)
+    r.set_image(pr.xbar)
+    r.run(1)
+    r.sync()
+    steps = max(1, min(args.steps, 5))
+    barrier(world, device)
+    torch.cuda.synchronize(device)
+    r.set_profiling(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r.run(steps)
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    ms = max_over_ranks(e0.elapsed_time(e1), world, device)
+    prof = r.profile()
+    r.close()
+    avg = prof["drop_block_ms"] / max(prof["drop_block_launches"], 1)
+    hbm_bytes = 44.0 * spec.n_hist / spec.n_blocks + 16.0 * spec.n_hist / spec.n_blocks   # records + 1/||a||^2 etc.
+    return {"name": "on-the-fly rows, 256x256x64, 720 angles, 40 blocks, N=4",
+            "value": world * spec.n_hist * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+            "histories": spec.n_hist, "drop_launch_ms": avg,
+            "hbm_gb_s_per_drop_launch": hbm_bytes / (avg / 1e3) / 1e9,
+            "bound": "alu + L2 atomics (path tracing; 60 B of HBM per history and launch)",
+            "note": "6M histories (the 60M-history layout with 1/10 of the histories); b traced on the host"}
+
+
 def run_ntvs(args):
     import torch
 
@@ -449,6 +488,10 @@ def run_ntvs(args):
     # ---- batched reconstructions: a parameter sweep over members of uneven size
     if args.batched:
         variants.append(run_batched_variant(args, ntvs, local, stream, world, device))
+
+    # ---- on-the-fly rows on the large grid
+    if args.onthefly:
+        variants.append(run_onthefly_variant(args, ntvs, local, stream, world, device))
 
     # ---- end to end through the C ABI from pinned host buffers
     e2e = None
