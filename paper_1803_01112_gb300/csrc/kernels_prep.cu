@@ -15,55 +15,6 @@ __global__ void validate_rows_kernel(const int64_t* __restrict__ row_ptr, int64_
     if (f) atomicOr(flags, f);
 }
 
-template <typename V>
-__global__ void validate_entries_kernel(const int32_t* __restrict__ col, const V* __restrict__ val, int64_t nnz,
-                                        int64_t nvox, int* flags) {
-    int f = 0;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t c = col[p];
-        if (c < 0 || (int64_t)c >= nvox) f |= 4;
-        if (!isfinite(as_f64(val[p]))) f |= 8;
-    }
-    if (f) atomicOr(flags, f);
-}
-
-template <typename B>
-__global__ void validate_rhs_kernel(const B* __restrict__ b, int64_t M, int* flags) {
-    int f = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x)
-        if (!isfinite((double)b[i])) f |= 16;
-    if (f) atomicOr(flags, f);
-}
-
-// warp per row: inv_norm2[i] = 1 / sum a^2 (FP64), 0 for a zero row
-template <typename V, typename T>
-__global__ void row_inv_norm2_kernel(const int64_t* __restrict__ row_ptr, const V* __restrict__ val, int64_t M,
-                                     T* __restrict__ inv_norm2) {
-    const int lane = threadIdx.x & 31;
-    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = w0; i < M; i += nw) {
-        double s = 0.0;
-        for (int64_t p = row_ptr[i] + lane; p < row_ptr[i + 1]; p += 32) {
-            const double a = as_f64(val[p]);
-            s += a * a;
-        }
-        s = warp_sum(s);
-        if (lane == 0) inv_norm2[i] = (s > 0.0) ? (T)(1.0 / s) : (T)0;
-    }
-}
-
-template <typename V>
-__global__ void hit_counts_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                                  const V* __restrict__ val, int64_t r0, int64_t r1, int32_t* __restrict__ cnt) {
-    const int lane = threadIdx.x & 31;
-    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = r0 + w0; i < r1; i += nw)
-        for (int64_t p = row_ptr[i] + lane; p < row_ptr[i + 1]; p += 32)
-            if (as_f64(val[p]) != 0.0) atomicAdd(cnt + col[p], 1);
-}
-
 template <typename T>
 __global__ void inv_counts_kernel(const int32_t* __restrict__ cnt, T* __restrict__ inv_s, int64_t n) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
@@ -84,64 +35,6 @@ cudaError_t k_validate_rows(const int64_t* row_ptr, int64_t M, int* flags, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t k_validate_entries(const int32_t* col, const void* val, int vdt, int64_t nnz, int64_t V, int* flags,
-                               cudaStream_t s) {
-    if (nnz <= 0) return cudaSuccess;
-    const int g = prep_grid();
-    switch (vdt) {
-        case F64: validate_entries_kernel<double><<<g, 256, 0, s>>>(col, (const double*)val, nnz, V, flags); break;
-        case F32: validate_entries_kernel<float><<<g, 256, 0, s>>>(col, (const float*)val, nnz, V, flags); break;
-        case F16: validate_entries_kernel<__half><<<g, 256, 0, s>>>(col, (const __half*)val, nnz, V, flags); break;
-        case BF16:
-            validate_entries_kernel<__nv_bfloat16><<<g, 256, 0, s>>>(col, (const __nv_bfloat16*)val, nnz, V, flags);
-            break;
-        default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t k_validate_rhs(const void* b, int bdt, int64_t M, int* flags, cudaStream_t s) {
-    if (M <= 0) return cudaSuccess;
-    if (bdt == F64) validate_rhs_kernel<double><<<prep_grid(), 256, 0, s>>>((const double*)b, M, flags);
-    else validate_rhs_kernel<float><<<prep_grid(), 256, 0, s>>>((const float*)b, M, flags);
-    return cudaGetLastError();
-}
-
-template <typename V>
-static void launch_norm(const int64_t* rp, const V* val, int64_t M, void* out, int cdt, cudaStream_t s) {
-    if (cdt == F64) row_inv_norm2_kernel<V, double><<<prep_grid(), 256, 0, s>>>(rp, val, M, (double*)out);
-    else row_inv_norm2_kernel<V, float><<<prep_grid(), 256, 0, s>>>(rp, val, M, (float*)out);
-}
-
-cudaError_t k_row_inv_norm2(const int64_t* row_ptr, const void* val, int vdt, int64_t M, void* inv_norm2, int cdt,
-                            cudaStream_t s) {
-    if (M <= 0) return cudaSuccess;
-    switch (vdt) {
-        case F64: launch_norm(row_ptr, (const double*)val, M, inv_norm2, cdt, s); break;
-        case F32: launch_norm(row_ptr, (const float*)val, M, inv_norm2, cdt, s); break;
-        case F16: launch_norm(row_ptr, (const __half*)val, M, inv_norm2, cdt, s); break;
-        case BF16: launch_norm(row_ptr, (const __nv_bfloat16*)val, M, inv_norm2, cdt, s); break;
-        default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t k_hit_counts(const int64_t* row_ptr, const int32_t* col, const void* val, int vdt, int64_t r0, int64_t r1,
-                         int32_t* cnt, cudaStream_t s) {
-    if (r1 <= r0) return cudaSuccess;
-    const int g = prep_grid();
-    switch (vdt) {
-        case F64: hit_counts_kernel<double><<<g, 256, 0, s>>>(row_ptr, col, (const double*)val, r0, r1, cnt); break;
-        case F32: hit_counts_kernel<float><<<g, 256, 0, s>>>(row_ptr, col, (const float*)val, r0, r1, cnt); break;
-        case F16: hit_counts_kernel<__half><<<g, 256, 0, s>>>(row_ptr, col, (const __half*)val, r0, r1, cnt); break;
-        case BF16:
-            hit_counts_kernel<__nv_bfloat16><<<g, 256, 0, s>>>(row_ptr, col, (const __nv_bfloat16*)val, r0, r1, cnt);
-            break;
-        default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-}
-
 cudaError_t k_inv_counts(const int32_t* cnt, void* inv_s, int cdt, int64_t n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     if (cdt == F64) inv_counts_kernel<double><<<prep_grid(), 256, 0, s>>>(cnt, (double*)inv_s, n);
@@ -152,6 +45,68 @@ cudaError_t k_inv_counts(const int32_t* cnt, void* inv_s, int cdt, int64_t n, cu
 }  // namespace ntvs
 
 namespace ntvs {
+
+// ------------------------------------------------------------------ fused block pass
+// One pass over the rows [r0, r1) of a block, a warp per row: flags |= 4 for a column
+// outside [0, V) (the entry is then skipped), 8 for a non-finite value, 16 for a
+// non-finite b; inv_norm2[i] = 1 / sum a^2 (FP64 sum of the stored values, 0 for a zero
+// row); cnt[j] += 1 for every entry with a != 0.  Requires a validated row_ptr.
+template <typename V, typename T>
+__global__ void __launch_bounds__(256) prep_block_kernel(const int64_t* __restrict__ row_ptr,
+                                                         const int32_t* __restrict__ col, const V* __restrict__ val,
+                                                         const T* __restrict__ b, int64_t r0, int64_t r1, int64_t nvox,
+                                                         T* __restrict__ inv_norm2, int32_t* __restrict__ cnt,
+                                                         int* flags) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int f = 0;
+    for (int64_t i = r0 + w0; i < r1; i += nw) {
+        const int64_t p0 = __ldg(row_ptr + i), p1 = __ldg(row_ptr + i + 1);
+        double sq = 0.0;
+#pragma unroll 4
+        for (int64_t p = p0 + lane; p < p1; p += 32) {
+            const int32_t c = __ldcs(col + p);
+            const double a = as_f64(val[p]);
+            if (!isfinite(a)) f |= 8;
+            sq += a * a;
+            if (c < 0 || (int64_t)c >= nvox) f |= 4;
+            else if (a != 0.0) atomicAdd(cnt + c, 1);
+        }
+        sq = warp_sum(sq);
+        if (lane == 0) {
+            inv_norm2[i] = (sq > 0.0 && isfinite(sq)) ? (T)(1.0 / sq) : (T)0;
+            if (!isfinite((double)b[i])) f |= 16;
+        }
+    }
+    if (f) atomicOr(flags, f);
+}
+
+template <typename V>
+static cudaError_t launch_prep(const int64_t* rp, const int32_t* col, const V* val, const void* b, int64_t r0,
+                               int64_t r1, int64_t nvox, void* inn, int cdt, int32_t* cnt, int* flags, cudaStream_t s) {
+    if (cdt == F64)
+        prep_block_kernel<V, double><<<prep_grid(), 256, 0, s>>>(rp, col, val, (const double*)b, r0, r1, nvox,
+                                                                 (double*)inn, cnt, flags);
+    else
+        prep_block_kernel<V, float><<<prep_grid(), 256, 0, s>>>(rp, col, val, (const float*)b, r0, r1, nvox,
+                                                                (float*)inn, cnt, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t k_prep_block(const int64_t* row_ptr, const int32_t* col, const void* val, int vdt, const void* b,
+                         int64_t r0, int64_t r1, int64_t nvox, void* inv_norm2, int cdt, int32_t* cnt, int* flags,
+                         cudaStream_t s) {
+    if (r1 <= r0) return cudaSuccess;
+    switch (vdt) {
+        case F64: return launch_prep(row_ptr, col, (const double*)val, b, r0, r1, nvox, inv_norm2, cdt, cnt, flags, s);
+        case F32: return launch_prep(row_ptr, col, (const float*)val, b, r0, r1, nvox, inv_norm2, cdt, cnt, flags, s);
+        case F16: return launch_prep(row_ptr, col, (const __half*)val, b, r0, r1, nvox, inv_norm2, cdt, cnt, flags, s);
+        case BF16:
+            return launch_prep(row_ptr, col, (const __nv_bfloat16*)val, b, r0, r1, nvox, inv_norm2, cdt, cnt, flags, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 // ------------------------------------------------------------------ DELTA16 packing
 // Row i stores base[i] = col[p0] and, for every entry k of the row, the int16 difference

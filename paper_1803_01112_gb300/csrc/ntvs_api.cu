@@ -808,25 +808,23 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
         c->free_system();
         return fail(NTVS_ERR_CSR, (c->hint[0] & 2) ? "row_ptr[0] != 0" : "row_ptr decreases");
     }
-    CUDA_TRY(k_validate_entries(c->col, c->val, c->vdt, nnz, V, c->dflags, st));
-    CUDA_TRY(k_validate_rhs(c->b, c->cdt, M, c->dflags, st));
-    CUDA_TRY(cudaMemcpyAsync(c->hint, c->dflags, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaStreamSynchronize(st));
-    if (c->hint[0]) {
-        const int f = c->hint[0];
-        c->free_system();
-        return fail(NTVS_ERR_CSR, (f & 4) ? "column index outside [0, V)" : (f & 8) ? "non-finite matrix value"
-                                                                                    : "non-finite right-hand side");
-    }
-
-    // row norms and per-block hit counts
+    // one pass per block: entry / rhs validation, FP64 row norms, per-block hit counts
     TRY(dev_alloc(&c->inv_norm2, csz * (size_t)M, "inv_norm2"));
-    CUDA_TRY(k_row_inv_norm2(c->row_ptr, c->val, c->vdt, M, c->inv_norm2, c->cdt, st));
     int32_t* cnt = nullptr;
     TRY(dev_alloc(&cnt, sizeof(int32_t) * (size_t)c->B * V, "hit counts"));
     CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)c->B * V, st));
     for (int t = 0; t < c->B; ++t)
-        CUDA_TRY(k_hit_counts(c->row_ptr, c->col, c->val, c->vdt, bp[t], bp[t + 1], cnt + (size_t)t * V, st));
+        CUDA_TRY(k_prep_block(c->row_ptr, c->col, c->val, c->vdt, c->b, bp[t], bp[t + 1], V, c->inv_norm2, c->cdt,
+                              cnt + (size_t)t * V, c->dflags, st));
+    CUDA_TRY(cudaMemcpyAsync(c->hint, c->dflags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (c->hint[0]) {
+        const int f = c->hint[0];
+        dev_free(cnt);
+        c->free_system();
+        return fail(NTVS_ERR_CSR, (f & 4) ? "column index outside [0, V)" : (f & 8) ? "non-finite matrix value"
+                                                                                    : "non-finite right-hand side");
+    }
     TRY(dev_alloc(&c->inv_s, csz * (size_t)c->B * V, "inverse hit counts"));
     CUDA_TRY(k_inv_counts(cnt, c->inv_s, c->cdt, (int64_t)c->B * V, st));
     CUDA_TRY(cudaStreamSynchronize(st));

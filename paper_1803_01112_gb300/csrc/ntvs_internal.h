@@ -21,17 +21,11 @@ int red_grid(int64_t n, int sm_count);
 // ------------------------------------------------------------------ load-time prep
 // flags |= 1 if row_ptr decreases, 2 if row_ptr[0] != 0
 cudaError_t k_validate_rows(const int64_t* row_ptr, int64_t M, int* flags, cudaStream_t s);
-// flags |= 4 if a column is outside [0, V), 8 if a value is not finite
-cudaError_t k_validate_entries(const int32_t* col, const void* val, int vdt, int64_t nnz, int64_t V,
-                               int* flags, cudaStream_t s);
-// flags |= 16 if a right-hand side is not finite
-cudaError_t k_validate_rhs(const void* b, int bdt, int64_t M, int* flags, cudaStream_t s);
-// inv_norm2[i] = 1 / sum_j a_ij^2 (FP64 sum of the stored values), 0 for a zero row
-cudaError_t k_row_inv_norm2(const int64_t* row_ptr, const void* val, int vdt, int64_t M, void* inv_norm2,
-                            int cdt, cudaStream_t s);
-// cnt[j] += 1 for every entry of rows [r0, r1) with a_ij != 0
-cudaError_t k_hit_counts(const int64_t* row_ptr, const int32_t* col, const void* val, int vdt, int64_t r0,
-                         int64_t r1, int32_t* cnt, cudaStream_t s);
+// fused pass over the rows [r0, r1) of one block: validation of columns, values and b
+// (flags 4 / 8 / 16), inv_norm2 of the rows and the block's hit counts cnt
+cudaError_t k_prep_block(const int64_t* row_ptr, const int32_t* col, const void* val, int vdt, const void* b,
+                         int64_t r0, int64_t r1, int64_t nvox, void* inv_norm2, int cdt, int32_t* cnt, int* flags,
+                         cudaStream_t s);
 // inv_s[j] = cnt[j] ? 1/cnt[j] : 0
 cudaError_t k_inv_counts(const int32_t* cnt, void* inv_s, int cdt, int64_t n, cudaStream_t s);
 
