@@ -58,6 +58,9 @@ def parse_args(argv=None):
     ap.add_argument("--batch-scale", type=float, default=1.0)
     ap.add_argument("--onthefly", type=int, default=1, help="also time on-the-fly rows on the 256x256x64 grid")
     ap.add_argument("--otf-histories", type=int, default=6_000_000)
+    ap.add_argument("--tile", default="4x4", help="internal voxel tile of the FP32 path (1x1: canonical order)")
+    ap.add_argument("--canonical", type=int, default=1,
+                    help="also time the canonical voxel order on the same workload (0: skip)")
     ap.add_argument("--cpu-rows", type=int, default=3_000_000, help="oracle sample: first rows of the workload")
     ap.add_argument("--ref-rows", type=int, default=1_000_000, help="reference arm: rows per step")
     ap.add_argument("--schedule", choices=["auto", "plain", "window", "pipeline"], default="auto",
@@ -398,7 +401,8 @@ def run_ntvs(args):
     shape = (spec.nx, spec.ny, spec.nz)
     stream = torch.cuda.Stream(device)   # the library launches on this stream; events are recorded on it
 
-    r = ntvs.Reconstructor(local, stream.cuda_stream)
+    tile = tuple(int(v) for v in args.tile.lower().split("x"))
+    r = ntvs.Reconstructor(local, stream.cuda_stream).set_voxel_tile(*tile)
     sched = {"auto": 0, "plain": 1, "window": 2, "pipeline": 3}[args.schedule]
     r.load(shape, s.row_ptr, s.col, s.val, b, n_blocks=spec.n_blocks, schedule=sched)
     r.set_params(**PARAMS)
@@ -445,16 +449,21 @@ def run_ntvs(args):
                 "avg_launch_ms": avg_ms}
     kernel_ms = {k: prof[k] / args.steps for k in ("drop_block_ms", "drop_apply_ms", "tv_ms")}
 
-    # ---- mixed precision on the same workload (FP32 arithmetic): BF16 lengths with int32
-    # or DELTA16 columns
+    # ---- the same workload in the canonical voxel order, and mixed precision (FP32
+    # arithmetic): BF16 lengths with int32 or DELTA16 columns
     variants = []
+    cases = []
+    if args.canonical and vdt == np.float32 and tile != (1, 1):
+        cases.append(("fp32, canonical voxel order", s.val, ntvs.NTVS_CSR32, vsz, 4, (1, 1)))
     if args.mixed and vdt == np.float32:
         import torch as _t
         vb = _t.from_numpy(s.val).to(_t.bfloat16)
-        for name, storage, ib in (("bf16 lengths + int32 columns", ntvs.NTVS_CSR32, 4),
-                                  ("bf16 lengths + delta16 columns", ntvs.NTVS_DELTA16, 2)):
-            rm = ntvs.Reconstructor(local, stream.cuda_stream)
-            rm.load(shape, s.row_ptr, s.col, vb, b, n_blocks=spec.n_blocks, storage=storage, schedule=sched)
+        cases.append(("bf16 lengths + int32 columns", vb, ntvs.NTVS_CSR32, 2, 4, tile))
+        cases.append(("bf16 lengths + delta16 columns", vb, ntvs.NTVS_DELTA16, 2, 2, tile))
+    if cases:
+        for name, vals, storage, vb_size, ib, vt in cases:
+            rm = ntvs.Reconstructor(local, stream.cuda_stream).set_voxel_tile(*vt)
+            rm.load(shape, s.row_ptr, s.col, vals, b, n_blocks=spec.n_blocks, storage=storage, schedule=sched)
             rm.set_params(**PARAMS)
             rm.set_image(x0)
             stm = rm.stats()
@@ -473,17 +482,18 @@ def run_ntvs(args):
             pm = rm.profile()
             rm.close()
             extra = 8 if storage == ntvs.NTVS_DELTA16 else 0
-            bytes_m = float(np.mean(algorithmic_drop_bytes(s, 2, 4, index_bytes=ib, extra_row_bytes=extra))) + \
+            bytes_m = float(np.mean(algorithmic_drop_bytes(s, vb_size, 4, index_bytes=ib, extra_row_bytes=extra))) + \
                 8.0 * stm["n_escaped"] / spec.n_blocks
             avg_m = pm["drop_block_ms"] / max(pm["drop_block_launches"], 1)
             ach = bytes_m / (avg_m / 1e3) / 1e9
             variants.append({"name": name, "value": world * spec.n_hist * args.steps / (msm / 1e3), "unit": UNIT,
-                             "ms_per_step": msm / args.steps, "vs_fp32": ms / msm,
+                             "ms_per_step": msm / args.steps, "vs_headline": ms / msm,
+                             "voxel_tile": f"{stm['voxel_tile_x']}x{stm['voxel_tile_y']}",
                              "drop_schedule": {1: "plain", 2: "window", 3: "pipeline"}.get(stm["drop_schedule"]),
                              "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                                           "frac": ach / peak, "algorithmic_bytes_per_launch": bytes_m,
                                           "avg_launch_ms": avg_m}})
-        del vb
+        cases = vb = None
 
     # ---- batched reconstructions: a parameter sweep over members of uneven size
     if args.batched:
@@ -503,7 +513,7 @@ def run_ntvs(args):
             barrier(world, device)
             torch.cuda.synchronize(device)
             t0 = time.perf_counter()
-            re = ntvs.Reconstructor(local, stream.cuda_stream)
+            re = ntvs.Reconstructor(local, stream.cuda_stream).set_voxel_tile(*tile)
             re.load(shape, s.row_ptr, s.col, s.val, b, n_blocks=spec.n_blocks, schedule=sched)
             t_l = time.perf_counter()
             re.set_params(**PARAMS)
@@ -537,6 +547,7 @@ def run_ntvs(args):
                            "storage": "csr32", "l2": L2_NOTE,
                            "drop_schedule": {1: "plain", 2: "window", 3: "pipeline"}.get(st0["drop_schedule"]),
                            "lanes_per_row": st0["lanes_per_row"],
+                           "voxel_tile": f"{st0['voxel_tile_x']}x{st0['voxel_tile_y']}",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "kernel_ms_per_step": kernel_ms, "clocks": clk, "variants": variants}

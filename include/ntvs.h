@@ -126,6 +126,8 @@ typedef struct {
     int32_t drop_schedule; /* NTVS_SCHED_PLAIN, _WINDOW or _PIPELINE (chosen at load)      */
     int32_t lanes_per_row; /* lanes per row of the DROP kernel                           */
     int64_t n_escaped;     /* DELTA16: column differences kept in the exception lists    */
+    int32_t voxel_tile_x;  /* internal voxel tile of the loaded system (1 = canonical)   */
+    int32_t voxel_tile_y;
 } ntvs_stats;
 
 /* Device time of the context's kernels, measured with CUDA events recorded on the
@@ -241,6 +243,18 @@ int ntvs_set_profiling(ntvs_ctx* ctx, int on);
 
 /* Totals of the launches timed since profiling was turned on (synchronizes the stream). */
 int ntvs_get_profile(ntvs_ctx* ctx, ntvs_profile* out);
+
+/* Internal voxel order of the FP32 path, applied at the next ntvs_load_system: the FP32
+ * gather copy of x, the DROP accumulator and the hit counts are stored in in-plane tiles
+ * of tx x ty voxels (each tile contiguous, slices contiguous), and the stored columns are
+ * rewritten into that order on the device (into a buffer of the context's own when the
+ * caller's columns are device memory: they are never modified).  Rows of a proton history
+ * then touch fewer distinct cache lines per slice.  The results are those of the
+ * canonical order up to the order of floating-point accumulation; images, gradients and
+ * every other public array stay canonical.  tx, ty in {1, 2, 4, 8, 16}; 1 x 1 is the
+ * canonical order; the default is 4 x 4.  The FP64 path and ntvs_load_paths always use the
+ * canonical order.  This layout has no counterpart in the paper.  NTVS_ERR_ARG on other sizes. */
+int ntvs_set_voxel_tile(ntvs_ctx* ctx, int tx, int ty);
 
 /* Test hook: replay ell_k for the next n cycles instead of drawing it (NULL clears). */
 int ntvs_set_ell_override(ntvs_ctx* ctx, const int64_t* ell_k, int64_t n);

@@ -207,6 +207,10 @@ def ntvs_get_profile(ctx: int) -> dict:
     return {f: getattr(pr, f) for f, _ in _ffi.ntvs_profile._fields_}
 
 
+def ntvs_set_voxel_tile(ctx: int, tx: int, ty: int) -> None:
+    check(lib().ntvs_set_voxel_tile(ctx, int(tx), int(ty)), "ntvs_set_voxel_tile")
+
+
 def ntvs_set_ell_override(ctx: int, ell) -> None:
     if ell is None:
         check(lib().ntvs_set_ell_override(ctx, None, 0), "ntvs_set_ell_override")
@@ -471,6 +475,11 @@ class Reconstructor:
 
     def set_ell_override(self, ell):
         ntvs_set_ell_override(self._ctx, ell)
+        return self
+
+    def set_voxel_tile(self, tx: int, ty: int):
+        """Internal voxel tile of the FP32 path, applied at the next load."""
+        ntvs_set_voxel_tile(self._ctx, tx, ty)
         return self
 
     def tv_gradient(self, dtype=np.float64):

@@ -59,7 +59,8 @@ class ntvs_stats(ctypes.Structure):
                 ("n_rows", ctypes.c_int64), ("n_blocks", ctypes.c_int32), ("compute_dtype", ctypes.c_int32),
                 ("last_tv", ctypes.c_double), ("n_launches", ctypes.c_int64),
                 ("drop_schedule", ctypes.c_int32), ("lanes_per_row", ctypes.c_int32),
-                ("n_escaped", ctypes.c_int64)]
+                ("n_escaped", ctypes.c_int64), ("voxel_tile_x", ctypes.c_int32),
+                ("voxel_tile_y", ctypes.c_int32)]
 
 
 class ntvs_profile(ctypes.Structure):
@@ -98,6 +99,7 @@ SIGNATURES = {
     "ntvs_set_state": (ctypes.c_int, [vp, i64, i64]),
     "ntvs_set_ell_override": (ctypes.c_int, [vp, vp, i64]),
     "ntvs_set_profiling": (ctypes.c_int, [vp, ctypes.c_int]),
+    "ntvs_set_voxel_tile": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
     "ntvs_get_profile": (ctypes.c_int, [vp, P(ntvs_profile)]),
     "ntvs_tv_gradient": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P(d)]),
     "ntvs_perturb": (ctypes.c_int, [vp, d]),

@@ -25,6 +25,17 @@ __device__ __forceinline__ double step_scale(double beta, const double* gnorm2) 
     return (n2 > 0.0) ? beta / sqrt(n2) : 0.0;
 }
 
+// internal index of canonical voxel j (see VoxMap)
+__device__ __forceinline__ int64_t vox_internal(const VoxMap& m, int64_t j) {
+    if (m.tx == 1 && m.ty == 1) return j;
+    const int ix = (int)(j % m.nx);
+    const int64_t t = j / m.nx;
+    const int iy = (int)(t % m.ny), iz = (int)(t / m.ny);
+    const int ntx = m.nxp / m.tx;
+    return (int64_t)iz * m.slice_p + (int64_t)((iy / m.ty) * ntx + ix / m.tx) * (m.tx * m.ty) +
+           (iy % m.ty) * m.tx + (ix % m.tx);
+}
+
 // inclusive prefix sum over the 32 lanes of a warp
 __device__ __forceinline__ int warp_inclusive_scan(int v) {
     const int lane = threadIdx.x & 31;

@@ -35,6 +35,28 @@ cudaError_t k_validate_rows(const int64_t* row_ptr, int64_t M, int* flags, cudaS
     return cudaGetLastError();
 }
 
+__global__ void remap_cols_kernel(const int32_t* __restrict__ in, int32_t* __restrict__ out, int64_t nnz, VoxMap m,
+                                  int* flags) {
+    const int64_t V = (int64_t)m.nx * m.ny * m.nz;
+    int f = 0;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = in[p];
+        if (c < 0 || (int64_t)c >= V) {
+            f |= 4;
+            out[p] = 0;
+        } else {
+            out[p] = (int32_t)vox_internal(m, c);
+        }
+    }
+    if (f) atomicOr(flags, f);
+}
+
+cudaError_t k_remap_cols(const int32_t* col_in, int32_t* col_out, int64_t nnz, VoxMap m, int* flags, cudaStream_t s) {
+    if (nnz <= 0) return cudaSuccess;
+    remap_cols_kernel<<<prep_grid(), 256, 0, s>>>(col_in, col_out, nnz, m, flags);
+    return cudaGetLastError();
+}
+
 cudaError_t k_inv_counts(const int32_t* cnt, void* inv_s, int cdt, int64_t n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     if (cdt == F64) inv_counts_kernel<double><<<prep_grid(), 256, 0, s>>>(cnt, (double*)inv_s, n);

@@ -102,14 +102,20 @@ tv_value_kernel(const double* __restrict__ x, const T* __restrict__ g, const dou
 // x <- x - sc*g on the master image (and its FP32 gather copy when present)
 template <typename T>
 __global__ void tv_apply_kernel(double* __restrict__ x, float* __restrict__ x32, const T* __restrict__ g,
-                                const double* gnorm2, double beta, const int* accept, int64_t V) {
+                                const double* gnorm2, double beta, const int* accept, int64_t V, VoxMap m) {
     if (accept && *accept == 0) return;
     const double sc = step_scale(beta, gnorm2);
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < V; p += (int64_t)gridDim.x * blockDim.x) {
         const double z = perturbed(x[p], sc, (double)g[p]);
         x[p] = z;
-        if (x32) x32[p] = (float)z;
+        if (x32) x32[vox_internal(m, p)] = (float)z;
     }
+}
+
+__global__ void x32_from_x64_kernel(const double* __restrict__ x, float* __restrict__ x32, VoxMap m) {
+    const int64_t V = (int64_t)m.nx * m.ny * m.nz;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < V; j += (int64_t)gridDim.x * blockDim.x)
+        x32[vox_internal(m, j)] = (float)x[j];
 }
 
 static int g_sm_count = 0;
@@ -146,12 +152,18 @@ cudaError_t k_tv_value(int cdt, const double* x, const void* g, const double* gn
 }
 
 cudaError_t k_tv_apply(int cdt, double* x, float* x32, const void* g, const double* gnorm2, double beta,
-                       const int* accept, int64_t V, cudaStream_t s) {
+                       const int* accept, int64_t V, VoxMap m, cudaStream_t s) {
     const int grid = red_grid(V, sm_count());
     if (cdt == F64)
-        tv_apply_kernel<double><<<grid, kRedThreads, 0, s>>>(x, x32, (const double*)g, gnorm2, beta, accept, V);
+        tv_apply_kernel<double><<<grid, kRedThreads, 0, s>>>(x, x32, (const double*)g, gnorm2, beta, accept, V, m);
     else
-        tv_apply_kernel<float><<<grid, kRedThreads, 0, s>>>(x, x32, (const float*)g, gnorm2, beta, accept, V);
+        tv_apply_kernel<float><<<grid, kRedThreads, 0, s>>>(x, x32, (const float*)g, gnorm2, beta, accept, V, m);
+    return cudaGetLastError();
+}
+
+cudaError_t k_x32_from_x64(const double* x, float* x32, VoxMap m, cudaStream_t s) {
+    const int64_t V = (int64_t)m.nx * m.ny * m.nz;
+    x32_from_x64_kernel<<<red_grid(V, sm_count()), kRedThreads, 0, s>>>(x, x32, m);
     return cudaGetLastError();
 }
 

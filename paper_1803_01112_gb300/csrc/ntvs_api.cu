@@ -92,6 +92,9 @@ struct ntvs_ctx {
     int nx = 0, ny = 0, nz = 0;
     int64_t V = 0, M = 0, nnz = 0;
     int B = 0;
+    // internal voxel order of x32, delta, inv_s and the stored columns (FP32 path)
+    VoxMap vm{};
+    int tile_req_x = 4, tile_req_y = 4;   // applied at the next load
     int vdt = F32, cdt = F32, storage = NTVS_CSR32;
     std::vector<int64_t> block_ptr;
     int64_t* row_ptr = nullptr;
@@ -266,6 +269,17 @@ int check_device_error(ntvs_ctx* c) {
     return NTVS_OK;
 }
 
+VoxMap make_voxmap(int nx, int ny, int nz, int tx, int ty) {
+    VoxMap m;
+    m.nx = nx; m.ny = ny; m.nz = nz;
+    m.tx = tx; m.ty = ty;
+    m.nxp = (nx + tx - 1) / tx * tx;
+    m.nyp = (ny + ty - 1) / ty * ty;
+    m.slice_p = (int64_t)m.nxp * m.nyp;
+    m.vint = m.slice_p * nz;
+    return m;
+}
+
 int copy_in(void** dst, bool* own, const void* src, size_t bytes, int mem_kind, cudaStream_t s, const char* what) {
     if (mem_kind == NTVS_MEM_DEVICE) {
         *dst = const_cast<void*>(src);
@@ -310,7 +324,7 @@ int checked_try(ntvs_ctx* c, double beta, int* acc) {
                           c->dscal + 1, c->daccept, c->stream);
     }));
     CUDA_TRY(timed_launch(c, KIND_TV, [&] {
-        return k_tv_apply(c->cdt, c->x, c->x32, c->g, c->dscal + 0, beta, c->daccept, c->V, c->stream);
+        return k_tv_apply(c->cdt, c->x, c->x32, c->g, c->dscal + 0, beta, c->daccept, c->V, c->vm, c->stream);
     }));
     CUDA_TRY(cudaMemcpyAsync(c->hint, c->daccept, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -327,7 +341,7 @@ int perturb_steps(ntvs_ctx* c, int64_t* ell_io) {
         if (!c->p.tv_check) {
             TRY(launch_grad(c, false));
             CUDA_TRY(timed_launch(c, KIND_TV, [&] {
-                return k_tv_apply(c->cdt, c->x, c->x32, c->g, c->dscal + 0, beta, nullptr, c->V, c->stream);
+                return k_tv_apply(c->cdt, c->x, c->x32, c->g, c->dscal + 0, beta, nullptr, c->V, c->vm, c->stream);
             }));
             ell += 1;
             tries = 1;
@@ -365,8 +379,9 @@ int drop_block(ntvs_ctx* c, int t) {
                               c->resid + t, c->stream);
         }));
         CUDA_TRY(timed_launch(c, KIND_APPLY, [&] {
-            return k_drop_apply(c->cdt, c->x, c->x32, c->delta, (const char*)c->inv_s + (size_t)t * c->V * c->csz(),
-                                c->V, c->apply_grid, c->stream);
+            return k_drop_apply(c->cdt, c->x, c->x32, c->delta,
+                                (const char*)c->inv_s + (size_t)t * c->vm.vint * c->csz(), c->V, c->vm,
+                                c->apply_grid, c->stream);
         }));
         return NTVS_OK;
     }
@@ -391,7 +406,7 @@ int drop_block(ntvs_ctx* c, int t) {
     a.d16 = c->d16();
     a.segs = nullptr;
     a.seg_begin = nullptr;
-    a.slice = (int64_t)c->nx * c->ny;
+    a.slice = c->vm.slice_p;
     if (c->schedule == NTVS_SCHED_WINDOW) {
         a.segs = c->segs;
         a.seg_begin = c->seg_begin + (size_t)t * (c->win_grid + 1);
@@ -406,7 +421,7 @@ int drop_block(ntvs_ctx* c, int t) {
         pa.inv_norm2 = c->inv_norm2;
         pa.stages = c->stages;
         pa.stage_begin = c->stage_begin + (size_t)t * (c->win_grid + 1);
-        pa.slice = (int64_t)c->nx * c->ny;
+        pa.slice = c->vm.slice_p;
         pa.x = a.x;
         pa.delta = c->delta;
         pa.lambda = c->p.lambda;
@@ -422,8 +437,8 @@ int drop_block(ntvs_ctx* c, int t) {
         CUDA_TRY(timed_launch(c, KIND_DROP, [&] { return k_drop_block(a, c->stream); }));
     }
     CUDA_TRY(timed_launch(c, KIND_APPLY, [&] {
-        return k_drop_apply(c->cdt, c->x, c->x32, c->delta, (const char*)c->inv_s + (size_t)t * c->V * c->csz(),
-                            c->V, c->apply_grid, c->stream);
+        return k_drop_apply(c->cdt, c->x, c->x32, c->delta, (const char*)c->inv_s + (size_t)t * c->vm.vint * c->csz(),
+                            c->V, c->vm, c->apply_grid, c->stream);
     }));
     return NTVS_OK;
 }
@@ -513,7 +528,7 @@ constexpr double kMinMeanRun = 8.0;
 static int plan_schedule(ntvs_ctx* c, int requested) {
     c->schedule = NTVS_SCHED_PLAIN;
     if (requested == NTVS_SCHED_PLAIN || c->M == 0) return NTVS_OK;
-    const int64_t slice = (int64_t)c->nx * c->ny;
+    const int64_t slice = c->vm.slice_p;
     int optin = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     const int64_t need = ((slice + 31) & ~31LL) * (int64_t)c->csz();
@@ -778,6 +793,12 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
     c->vdt = s->val_dtype;
     c->cdt = (s->val_dtype == NTVS_F64) ? F64 : F32;
     c->storage = s->storage;
+    // the FP64 path gathers the canonical master image: no internal order there
+    c->vm = (c->cdt == F32) ? make_voxmap(s->nx, s->ny, s->nz, c->tile_req_x, c->tile_req_y)
+                            : make_voxmap(s->nx, s->ny, s->nz, 1, 1);
+    if (c->vm.vint > 0x7fffffffLL) c->vm = make_voxmap(s->nx, s->ny, s->nz, 1, 1);
+    const bool tiled = c->vm.tx != 1 || c->vm.ty != 1;
+    const int64_t VI = c->vm.vint;
     cudaStream_t st = c->stream;
 
     // row_ptr and nnz
@@ -799,23 +820,35 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
     TRY(copy_in(&c->val, &c->own_val, s->val, vsz * (size_t)nnz, s->mem_kind, st, "val"));
     TRY(copy_in(&c->b, &c->own_b, s->b, csz * (size_t)M, s->mem_kind, st, "b"));
 
-    // validation
+    // validation; columns of the tiled order are rewritten into a buffer of the context's
+    // own (caller memory is never modified)
     CUDA_TRY(cudaMemsetAsync(c->dflags, 0, sizeof(int), st));
+    if (tiled && nnz > 0) {
+        if (!c->own_col) {
+            int32_t* mine = nullptr;
+            TRY(dev_alloc(&mine, sizeof(int32_t) * (size_t)nnz, "col (internal order)"));
+            CUDA_TRY(k_remap_cols(c->col, mine, nnz, c->vm, c->dflags, st));
+            c->col = mine;
+            c->own_col = true;
+        } else {
+            CUDA_TRY(k_remap_cols(c->col, c->col, nnz, c->vm, c->dflags, st));
+        }
+    }
     CUDA_TRY(k_validate_rows(c->row_ptr, M, c->dflags, st));
     CUDA_TRY(cudaMemcpyAsync(c->hint, c->dflags, sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
-    if (c->hint[0]) {
+    if (c->hint[0] & 3) {
         c->free_system();
         return fail(NTVS_ERR_CSR, (c->hint[0] & 2) ? "row_ptr[0] != 0" : "row_ptr decreases");
     }
     // one pass per block: entry / rhs validation, FP64 row norms, per-block hit counts
     TRY(dev_alloc(&c->inv_norm2, csz * (size_t)M, "inv_norm2"));
     int32_t* cnt = nullptr;
-    TRY(dev_alloc(&cnt, sizeof(int32_t) * (size_t)c->B * V, "hit counts"));
-    CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)c->B * V, st));
+    TRY(dev_alloc(&cnt, sizeof(int32_t) * (size_t)c->B * VI, "hit counts"));
+    CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)c->B * VI, st));
     for (int t = 0; t < c->B; ++t)
-        CUDA_TRY(k_prep_block(c->row_ptr, c->col, c->val, c->vdt, c->b, bp[t], bp[t + 1], V, c->inv_norm2, c->cdt,
-                              cnt + (size_t)t * V, c->dflags, st));
+        CUDA_TRY(k_prep_block(c->row_ptr, c->col, c->val, c->vdt, c->b, bp[t], bp[t + 1], VI, c->inv_norm2, c->cdt,
+                              cnt + (size_t)t * VI, c->dflags, st));
     CUDA_TRY(cudaMemcpyAsync(c->hint, c->dflags, sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     if (c->hint[0]) {
@@ -825,20 +858,20 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
         return fail(NTVS_ERR_CSR, (f & 4) ? "column index outside [0, V)" : (f & 8) ? "non-finite matrix value"
                                                                                     : "non-finite right-hand side");
     }
-    TRY(dev_alloc(&c->inv_s, csz * (size_t)c->B * V, "inverse hit counts"));
-    CUDA_TRY(k_inv_counts(cnt, c->inv_s, c->cdt, (int64_t)c->B * V, st));
+    TRY(dev_alloc(&c->inv_s, csz * (size_t)c->B * VI, "inverse hit counts"));
+    CUDA_TRY(k_inv_counts(cnt, c->inv_s, c->cdt, (int64_t)c->B * VI, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     dev_free(cnt);
 
-    // image state
+    // image state (x and g canonical; x32 and delta in the internal order, padding zero)
     TRY(dev_alloc(&c->x, sizeof(double) * (size_t)V, "x"));
-    if (c->cdt == F32) TRY(dev_alloc(&c->x32, sizeof(float) * (size_t)V, "x32"));
-    TRY(dev_alloc(&c->delta, csz * (size_t)V, "delta"));
+    if (c->cdt == F32) TRY(dev_alloc(&c->x32, sizeof(float) * (size_t)VI, "x32"));
+    TRY(dev_alloc(&c->delta, csz * (size_t)VI, "delta"));
     TRY(dev_alloc(&c->g, csz * (size_t)V, "g"));
     TRY(dev_alloc(&c->resid, sizeof(double) * (size_t)c->B, "residuals"));
     CUDA_TRY(cudaMemsetAsync(c->x, 0, sizeof(double) * (size_t)V, st));
-    if (c->x32) CUDA_TRY(cudaMemsetAsync(c->x32, 0, sizeof(float) * (size_t)V, st));
-    CUDA_TRY(cudaMemsetAsync(c->delta, 0, csz * (size_t)V, st));
+    if (c->x32) CUDA_TRY(cudaMemsetAsync(c->x32, 0, sizeof(float) * (size_t)VI, st));
+    CUDA_TRY(cudaMemsetAsync(c->delta, 0, csz * (size_t)VI, st));
     CUDA_TRY(cudaMemsetAsync(c->g, 0, csz * (size_t)V, st));
     CUDA_TRY(cudaMemsetAsync(c->resid, 0, sizeof(double) * (size_t)c->B, st));
 
@@ -905,6 +938,7 @@ int ntvs_load_paths(ntvs_ctx* c, const ntvs_paths* s) {
     c->cdt = F32;
     c->storage = NTVS_CSR32;
     c->nnz = 0;
+    c->vm = make_voxmap(s->nx, s->ny, s->nz, 1, 1);   // traced voxels are canonical
     TRY(copy_in((void**)&c->paths, &c->own_paths, s->paths, sizeof(float) * 10 * (size_t)M, s->mem_kind, st, "paths"));
     TRY(copy_in(&c->b, &c->own_b, s->b, sizeof(float) * (size_t)M, s->mem_kind, st, "b"));
     c->paths_mode = true;
@@ -994,7 +1028,7 @@ int ntvs_set_image(ntvs_ctx* c, const void* x, int dtype, int mem_kind) {
         CUDA_TRY(cudaMemcpyAsync(c->x, tmp.data(), tmp.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
         CUDA_TRY(cudaStreamSynchronize(c->stream));
     }
-    if (c->x32) CUDA_TRY(k_convert(c->x, NTVS_F64, c->x32, NTVS_F32, c->V, c->stream));
+    if (c->x32) CUDA_TRY(k_x32_from_x64(c->x, c->x32, c->vm, c->stream));
     return NTVS_OK;
 }
 
@@ -1065,6 +1099,8 @@ int ntvs_get_stats(ntvs_ctx* c, ntvs_stats* st) {
     st->drop_schedule = c->schedule;
     st->lanes_per_row = c->lpr;
     st->n_escaped = c->n_escaped;
+    st->voxel_tile_x = c->loaded ? c->vm.tx : 0;
+    st->voxel_tile_y = c->loaded ? c->vm.ty : 0;
     if (c->k > 0 && c->tvhist) {
         CUDA_TRY(cudaMemcpyAsync(c->hscal, c->tvhist + (c->k - 1), sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -1135,6 +1171,15 @@ int ntvs_get_profile(ntvs_ctx* c, ntvs_profile* out) {
     return NTVS_OK;
 }
 
+int ntvs_set_voxel_tile(ntvs_ctx* c, int tx, int ty) {
+    if (!c) return fail(NTVS_ERR_ARG, "null context");
+    auto ok = [](int v) { return v == 1 || v == 2 || v == 4 || v == 8 || v == 16; };
+    if (!ok(tx) || !ok(ty)) return fail(NTVS_ERR_ARG, "tile sizes must be 1, 2, 4, 8 or 16");
+    c->tile_req_x = tx;
+    c->tile_req_y = ty;
+    return NTVS_OK;
+}
+
 int ntvs_set_ell_override(ntvs_ctx* c, const int64_t* ell_k, int64_t n) {
     if (!c) return fail(NTVS_ERR_ARG, "null context");
     c->override_ell.clear();
@@ -1161,7 +1206,7 @@ int ntvs_perturb(ntvs_ctx* c, double beta) {
     TRY(need_system(c));
     TRY(launch_grad(c, false));
     CUDA_TRY(timed_launch(c, KIND_TV, [&] {
-        return k_tv_apply(c->cdt, c->x, c->x32, c->g, c->dscal + 0, beta, nullptr, c->V, c->stream);
+        return k_tv_apply(c->cdt, c->x, c->x32, c->g, c->dscal + 0, beta, nullptr, c->V, c->vm, c->stream);
     }));
     return NTVS_OK;
 }

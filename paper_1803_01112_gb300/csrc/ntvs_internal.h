@@ -13,6 +13,18 @@ enum Dt { F64 = 0, F32 = 1, F16 = 2, BF16 = 3 };
 
 inline size_t dt_size(int dt) { return dt == F64 ? 8 : dt == F32 ? 4 : 2; }
 
+// Internal voxel order of the FP32 gather copy, delta, hit counts and matrix columns:
+// in-plane tiles of tx x ty voxels, each tile contiguous, tiles row-major over a grid padded
+// to multiples of the tile, slices contiguous (slice_p voxels each).  tx = ty = 1 is the
+// canonical order (iz*ny + iy)*nx + ix.  Public images and the FP64 master stay canonical.
+struct VoxMap {
+    int nx, ny, nz;
+    int nxp, nyp;      // padded to multiples of tx, ty
+    int tx, ty;
+    int64_t slice_p;   // nxp * nyp
+    int64_t vint;      // nz * slice_p
+};
+
 // Grid used by every deterministic reduction: a fixed CTA count so the order of the
 // final sum over CTA partials never changes.
 constexpr int kRedThreads = 256;
@@ -26,6 +38,11 @@ cudaError_t k_validate_rows(const int64_t* row_ptr, int64_t M, int* flags, cudaS
 cudaError_t k_prep_block(const int64_t* row_ptr, const int32_t* col, const void* val, int vdt, const void* b,
                          int64_t r0, int64_t r1, int64_t nvox, void* inv_norm2, int cdt, int32_t* cnt, int* flags,
                          cudaStream_t s);
+// col_out[p] = internal index of voxel col_in[p]; flags |= 4 for a column outside [0, V)
+// (written as 0).  col_in == col_out is allowed.
+cudaError_t k_remap_cols(const int32_t* col_in, int32_t* col_out, int64_t nnz, VoxMap m, int* flags, cudaStream_t s);
+// x32[internal(j)] = (float)x[j] for the canonical voxels j < V
+cudaError_t k_x32_from_x64(const double* x, float* x32, VoxMap m, cudaStream_t s);
 // inv_s[j] = cnt[j] ? 1/cnt[j] : 0
 cudaError_t k_inv_counts(const int32_t* cnt, void* inv_s, int cdt, int64_t n, cudaStream_t s);
 
@@ -61,10 +78,10 @@ cudaError_t k_tv_grad(int cdt, const double* x, void* g, int nx, int ny, int nz,
 // gnorm2 == 0).  If phi_ref != nullptr, *accept = (*phi <= *phi_ref).
 cudaError_t k_tv_value(int cdt, const double* x, const void* g, const double* gnorm2, double beta, int nx, int ny,
                        int nz, RedScratch r, double* phi, const double* phi_ref, int* accept, cudaStream_t s);
-// x <- x - sc*g (sc as in k_tv_value), x32 (may be null) <- (float)x; skipped when
-// accept != nullptr and *accept == 0.
+// x <- x - sc*g (sc as in k_tv_value), x32 (may be null) <- (float)x at the internal
+// index; skipped when accept != nullptr and *accept == 0.
 cudaError_t k_tv_apply(int cdt, double* x, float* x32, const void* g, const double* gnorm2, double beta,
-                       const int* accept, int64_t V, cudaStream_t s);
+                       const int* accept, int64_t V, VoxMap m, cudaStream_t s);
 
 // ------------------------------------------------------------------ DROP
 // A run of consecutive rows [r0, r1) whose entries lie mostly in z-slice `home`.
@@ -100,9 +117,10 @@ cudaError_t k_drop_block(const DropArgs& a, cudaStream_t s);
 // home[i] = median z-slice of the first, middle and last entries of row i (-1: empty row)
 cudaError_t k_row_home(const int64_t* row_ptr, const int32_t* col, int64_t M, int64_t slice, int32_t* home, int grid,
                        cudaStream_t s);
-// x_j += delta_j * inv_s_j on the FP64 master (x32_j <- (float)x_j when x32 != null); delta_j = 0
-cudaError_t k_drop_apply(int cdt, double* x, float* x32, void* delta, const void* inv_s, int64_t V, int grid,
-                         cudaStream_t s);
+// x_j += delta_p * inv_s_p on the FP64 master (p the internal index of j; x32_p <- (float)x_j
+// when x32 != null); delta_p = 0
+cudaError_t k_drop_apply(int cdt, double* x, float* x32, void* delta, const void* inv_s, int64_t V, VoxMap m,
+                         int grid, cudaStream_t s);
 
 // TMA-fed pipeline (drop_pipe_kernel): a stage is a run of at most kStageRows whole rows
 // of one home slice whose entries [e0, e0 + nent) fit one ring slot (e0 and nent aligned
