@@ -17,6 +17,10 @@ Pins (what fixes each function independently of itself) live in ``tests/test_ora
   * orc_drop_block_at : equals orc_drop_block on every voxel of small cases.
   * orc_ntvs     : N = 0 is plain DROP; the check variant without rejections equals
     the variant without the check; accepted steps never raise phi; ell_k >= k.
+    OTVS and decoupled step rules: closed forms of the total shift of a two-voxel image
+    (every step moves both voxels by beta/sqrt(2)), including OTVS rejections worked by
+    hand; OTVS ell_k equals the running count of tries; decoupled with gamma = alpha
+    equals NTVS with ell_k = k replayed.
 """
 from __future__ import annotations
 
@@ -46,12 +50,14 @@ def build(force: bool = False) -> str:
 class _Params(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_double), ("alpha", ctypes.c_double), ("beta0", ctypes.c_double),
                 ("eps_tv", ctypes.c_double), ("N", ctypes.c_int32), ("tv_check", ctypes.c_int32),
-                ("max_retries", ctypes.c_int32), ("pad", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("max_retries", ctypes.c_int32), ("step_rule", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("gamma", ctypes.c_double)]
 
 
 class _Trace(ctypes.Structure):
     _fields_ = [("ell_k", ctypes.c_void_p), ("ell_step", ctypes.c_void_p), ("tries", ctypes.c_void_p),
-                ("accepted", ctypes.c_void_p), ("tv", ctypes.c_void_p), ("resid_ss", ctypes.c_void_p)]
+                ("accepted", ctypes.c_void_p), ("tv", ctypes.c_void_p), ("resid_ss", ctypes.c_void_p),
+                ("beta_step", ctypes.c_void_p)]
 
 
 _L = None
@@ -148,6 +154,11 @@ def drop_block_at(row_ptr, col, val, b, r0: int, r1: int, x, lam: float, vox) ->
 
 
 # ------------------------------------------------------------------ NTVS
+STEP_NTVS = 0        # ell_k = rand(k, ell_{k-1})                      (Appendix C)
+STEP_OTVS = 1        # ell_k = ell_{k-1}: ell never reset               (Appendix B)
+STEP_DECOUPLED = 2   # beta_{k,n} = beta0 alpha^n gamma^k, no check      (Sec. VI)
+
+
 @dataclass
 class Params:
     lam: float
@@ -158,6 +169,14 @@ class Params:
     seed: int = 0
     eps_tv: float = 1e-8
     max_retries: int = 64
+    step_rule: int = STEP_NTVS
+    gamma: float = 0.5
+
+    @staticmethod
+    def otvs(lam: float, **kw) -> "Params":
+        """The paper's OTVS (Appendix B): one checked step per cycle, beta = (1/2)^ell with
+        ell counting every try since the start."""
+        return Params(lam=lam, N=1, alpha=0.5, beta0=1.0, tv_check=True, step_rule=STEP_OTVS, **kw)
 
 
 @dataclass
@@ -170,6 +189,7 @@ class Result:
     tv: np.ndarray
     resid_ss: np.ndarray
     ell_prev: int
+    beta_step: np.ndarray
 
 
 def ntvs(row_ptr, col, val, b, block_ptr, shape, params: Params, K: int, x0,
@@ -187,14 +207,18 @@ def ntvs(row_ptr, col, val, b, block_ptr, shape, params: Params, K: int, x0,
     accepted = np.zeros(max(K * N, 1), np.int32)
     tvs = np.zeros(max(K, 1), np.float64)
     rss = np.zeros(max(K * B, 1), np.float64)
+    bst = np.zeros(max(K * N, 1), np.float64)
     tr = _Trace(ell_k.ctypes.data, ell_step.ctypes.data, tries.ctypes.data, accepted.ctypes.data,
-                tvs.ctypes.data, rss.ctypes.data)
+                tvs.ctypes.data, rss.ctypes.data, bst.ctypes.data)
     p = _Params(params.lam, params.alpha, params.beta0, params.eps_tv, N, int(params.tv_check),
-                params.max_retries, 0, params.seed)
+                params.max_retries, int(params.step_rule), params.seed, params.gamma)
     ep = ctypes.c_int64(ell_prev)
     ov = None if ell_override is None else np.ascontiguousarray(ell_override, np.int64)
-    _lib().orc_ntvs(rp.ctypes.data, c.ctypes.data, v.ctypes.data, bb.ctypes.data, bp.ctypes.data, B,
-                    nx, ny, nz, ctypes.byref(p), K, k0, ctypes.byref(ep), _ptr(ov), x.ctypes.data,
-                    ctypes.byref(tr))
+    rc = _lib().orc_ntvs(rp.ctypes.data, c.ctypes.data, v.ctypes.data, bb.ctypes.data, bp.ctypes.data, B,
+                         nx, ny, nz, ctypes.byref(p), K, k0, ctypes.byref(ep), _ptr(ov), x.ctypes.data,
+                         ctypes.byref(tr))
+    if rc != 0:
+        raise ValueError("oracle: unknown step rule, or the decoupled rule with the TV check")
     return Result(x, ell_k[:K], ell_step[:K * N].reshape(K, N), tries[:K * N].reshape(K, N),
-                  accepted[:K * N].reshape(K, N), tvs[:K], rss[:K * B].reshape(K, B), int(ep.value))
+                  accepted[:K * N].reshape(K, N), tvs[:K], rss[:K * B].reshape(K, B), int(ep.value),
+                  bst[:K * N].reshape(K, N))

@@ -13,6 +13,8 @@
  *   - ell schedule: ell_k = rand(k, ell_{k-1}), Sec. II-B (item 4) and Appendix C.
  *   - step size beta_{k,n} = alpha^{ell_k}, Sec. II-B and Appendix A; the paper's
  *     beta_0 = 1 is exposed as beta0.
+ *   - OTVS (Appendix B): ell is never reset between cycles, beta = (1/2)^ell.
+ *   - decoupled step size beta_{k,n} = alpha^n gamma^{f(k)}, f(k) = k (Sec. VI).
  *   - phi = TV, "sum of local variations over all voxels" (Sec. IV, ref. CCCNP10);
  *     v = -grad phi / ||grad phi|| (Appendix A).
  *   - P_T = one sweep of block-DROP (Sec. II-D cites the DROP algorithm of ref.
@@ -30,6 +32,9 @@
  *   - check variant: beta is recomputed as beta0*alpha^ell after each ell++ (the
  *     printed loop never updates beta); a tie phi(z) == phi(x) accepts; after
  *     max_retries rejected tries x is left unchanged.
+ *   - decoupled rule: n and k are counted from 0 as in the Appendix C loops, so the
+ *     first step of the first cycle is beta0; it is stated without the check, and is
+ *     only defined here without it.
  */
 #include <math.h>
 #include <stdint.h>
@@ -187,10 +192,18 @@ void orc_drop_block_at(const int64_t* row_ptr, const int32_t* col, const double*
 }
 
 /* ----------------------------------------------------------------- NTVS */
+/* step_rule: how the step sizes of cycle k are chosen.
+ *   0  NTVS (Appendix C): ell_k = rand(k, ell_{k-1}); step n uses beta0 * alpha^ell, ell++
+ *      after every try.
+ *   1  OTVS (Appendix B): ell is never reset: ell_k = ell_{k-1}, and otherwise as rule 0.
+ *      The paper's OTVS is this rule with N = 1, alpha = 1/2, beta0 = 1 and the TV check.
+ *   2  decoupled (Sec. VI): beta_{k,n} = beta0 * alpha^n * gamma^k for n = 0..N-1, with no
+ *      ell; defined without the TV check. */
 typedef struct {
     double lambda, alpha, beta0, eps_tv;
-    int32_t N, tv_check, max_retries, pad;
+    int32_t N, tv_check, max_retries, step_rule;
     uint64_t seed;
+    double gamma;
 } orc_params;
 
 typedef struct {
@@ -200,6 +213,7 @@ typedef struct {
     int32_t* accepted;     /* [K*N] 1 if step n changed x                              */
     double* tv;            /* [K]   phi(x^{k+1})                                       */
     double* resid_ss;      /* [K*B] per-block residual sum of squares                  */
+    double* beta_step;     /* [K*N] beta of the accepted / last try of step n          */
 } orc_trace;
 
 /* x <- x + beta * v, v = -g/||g|| (v = 0 when ||g|| = 0). */
@@ -209,37 +223,48 @@ static void perturb(double* z, const double* x, const double* g, double gnorm, d
 
 /* K cycles of NTVS (Appendix C) from x (in/out).  ell_override: if not NULL, ell_k is
  * taken from it instead of being drawn (replays a recorded schedule).  ell_prev_io
- * carries ell_{k-1} between calls (start with 0); k0 is the index of the first cycle. */
+ * carries ell_{k-1} between calls (start with 0); k0 is the index of the first cycle.
+ * Under the decoupled rule ell_k records k and ell_prev_io is left as it is.  Returns -1
+ * (nothing done) for an unknown rule or the decoupled rule with the TV check. */
 int orc_ntvs(const int64_t* row_ptr, const int32_t* col, const double* val, const double* b,
              const int64_t* block_ptr, int B, int nx, int ny, int nz, const orc_params* prm,
              int K, int k0, int64_t* ell_prev_io, const int64_t* ell_override, double* x, orc_trace* tr) {
     const int64_t V = (int64_t)nx * ny * nz;
     const int N = prm->N;
+    const int rule = prm->step_rule;
+    if (rule < 0 || rule > 2 || (rule == 2 && prm->tv_check)) return -1;
     double* g = (double*)malloc(sizeof(double) * (size_t)(V > 0 ? V : 1));
     double* z = (double*)malloc(sizeof(double) * (size_t)(V > 0 ? V : 1));
     int64_t ell_prev = *ell_prev_io;
     for (int kk = 0; kk < K; ++kk) {
         int64_t k = k0 + kk;
-        int64_t ell = ell_override ? ell_override[kk] : orc_rand_ell(prm->seed, k, ell_prev);
+        int64_t ell;
+        if (ell_override) ell = ell_override[kk];
+        else if (rule == 0) ell = orc_rand_ell(prm->seed, k, ell_prev);
+        else if (rule == 1) ell = ell_prev;
+        else ell = k;
         if (tr && tr->ell_k) tr->ell_k[kk] = ell;
         for (int n = 0; n < N; ++n) {
             orc_tv_grad(x, nx, ny, nz, prm->eps_tv, g);
             double gn = 0.0;
             for (int64_t j = 0; j < V; ++j) gn += g[j] * g[j];
             gn = sqrt(gn);
-            double beta = prm->beta0 * pow(prm->alpha, (double)ell);
+            double beta = (rule == 2) ? prm->beta0 * pow(prm->alpha, (double)n) * pow(prm->gamma, (double)k)
+                                      : prm->beta0 * pow(prm->alpha, (double)ell);
+            double beta_used = beta;
             int tries = 0, acc = 0;
             int64_t ell_used = ell;
             if (!prm->tv_check) {
                 perturb(x, x, g, gn, beta, V);
                 ell_used = ell;
-                ell += 1;
+                if (rule != 2) ell += 1;
                 tries = 1; acc = 1;
             } else {
                 double phi_x = orc_tv(x, nx, ny, nz, 0.0);
                 for (;;) {
                     perturb(z, x, g, gn, beta, V);
                     ell_used = ell;
+                    beta_used = beta;
                     ell += 1;
                     tries += 1;
                     if (orc_tv(z, nx, ny, nz, 0.0) <= phi_x) {
@@ -254,8 +279,9 @@ int orc_ntvs(const int64_t* row_ptr, const int32_t* col, const double* val, cons
             if (tr && tr->ell_step) tr->ell_step[(int64_t)kk * N + n] = ell_used;
             if (tr && tr->tries) tr->tries[(int64_t)kk * N + n] = tries;
             if (tr && tr->accepted) tr->accepted[(int64_t)kk * N + n] = acc;
+            if (tr && tr->beta_step) tr->beta_step[(int64_t)kk * N + n] = beta_used;
         }
-        ell_prev = ell;
+        if (rule != 2) ell_prev = ell;
         orc_drop_sweep(row_ptr, col, val, b, block_ptr, B, V, prm->lambda, x,
                        (tr && tr->resid_ss) ? tr->resid_ss + (int64_t)kk * B : NULL);
         if (tr && tr->tv) tr->tv[kk] = orc_tv(x, nx, ny, nz, 0.0);
