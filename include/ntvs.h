@@ -98,6 +98,15 @@ typedef struct {
 #define NTVS_SCHED_PIPELINE 3
 #define NTVS_SCHED_ONTHEFLY 4   /* reported for systems loaded with ntvs_load_paths */
 
+/* Step-size rules of the TV perturbations (ntvs_params.step_rule). */
+#define NTVS_STEP_NTVS 0       /* ell_k = rand(k, ell_{k-1}); try t of cycle k uses
+                                  beta0 * alpha^(ell_k + t) (Appendix C)                      */
+#define NTVS_STEP_OTVS 1       /* ell never reset: ell_k = ell_{k-1} (Appendix B); the paper's
+                                  OTVS is this rule with N = 1, alpha = 1/2, beta0 = 1 and
+                                  tv_check = 1                                                */
+#define NTVS_STEP_DECOUPLED 2  /* beta_{k,n} = beta0 * alpha^n * gamma^k, n = 0..N-1, k the
+                                  cycle index from 0 (Sec. VI); no ell, no TV check           */
+
 /* Parameters of NTVS (Sec. II-E, Appendix A/C). */
 typedef struct {
     double lambda;       /* DROP relaxation lambda                                        */
@@ -107,8 +116,9 @@ typedef struct {
     int32_t N;           /* TV perturbation steps per cycle, >= 0                          */
     int32_t tv_check;    /* 0: NTVS; 1: NTVS with the TV reduction requirement             */
     int32_t max_retries; /* tries per step in check mode before the step is skipped (>=1) */
-    int32_t reserved;    /* 0                                                              */
+    int32_t step_rule;   /* NTVS_STEP_NTVS (0), NTVS_STEP_OTVS or NTVS_STEP_DECOUPLED       */
     uint64_t seed;       /* stream of the ell draws (SplitMix64, output k for cycle k)     */
+    double gamma;        /* decoupled rule only: 0 < gamma < 1                             */
 } ntvs_params;
 
 typedef struct {

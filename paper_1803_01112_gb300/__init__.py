@@ -19,10 +19,10 @@ import numpy as np
 
 from . import _ffi
 from ._ffi import (NTVS_BF16, NTVS_CSR32, NTVS_DELTA16, NTVS_F16, NTVS_F32, NTVS_F64, NTVS_MEM_DEVICE,
-                   NTVS_MEM_HOST, NtvsError, check, lib)
+                   NTVS_MEM_HOST, NTVS_STEP_DECOUPLED, NTVS_STEP_NTVS, NTVS_STEP_OTVS, NtvsError, check, lib)
 
 __all__ = ["Reconstructor", "NtvsError", "build", "lib", "NTVS_F64", "NTVS_F32", "NTVS_F16", "NTVS_BF16",
-           "NTVS_CSR32", "NTVS_DELTA16"]
+           "NTVS_CSR32", "NTVS_DELTA16", "NTVS_STEP_NTVS", "NTVS_STEP_OTVS", "NTVS_STEP_DECOUPLED"]
 
 _NP_DT = {np.dtype(np.float64): NTVS_F64, np.dtype(np.float32): NTVS_F32, np.dtype(np.float16): NTVS_F16}
 
@@ -136,8 +136,10 @@ def ntvs_load_paths(ctx: int, nx: int, ny: int, nz: int, voxel, paths, b, n_bloc
 
 
 def ntvs_set_params(ctx: int, lam: float, N: int, alpha: float, beta0: float = 1.0, tv_check: bool = False,
-                    seed: int = 0, eps_tv: float = 1e-8, max_retries: int = 64) -> None:
-    p = _ffi.ntvs_params(lam, alpha, beta0, eps_tv, N, int(bool(tv_check)), max_retries, 0, seed)
+                    seed: int = 0, eps_tv: float = 1e-8, max_retries: int = 64, step_rule: int = 0,
+                    gamma: float = 0.5) -> None:
+    p = _ffi.ntvs_params(lam, alpha, beta0, eps_tv, N, int(bool(tv_check)), max_retries, int(step_rule), seed,
+                         gamma)
     check(lib().ntvs_set_params(ctx, ctypes.byref(p)), "ntvs_set_params")
 
 
@@ -279,7 +281,7 @@ def ntvs_batch_add(bt: int, shape, row_ptr, col, val, b, n_blocks: int, params: 
     nx, ny, nz = shape
     st, _keep = _system_struct(nx, ny, nz, row_ptr, col, val, b, n_blocks, block_ptr)
     p = _ffi.ntvs_params(params.lam, params.alpha, params.beta0, params.eps_tv, params.N, int(bool(params.tv_check)),
-                         params.max_retries, 0, params.seed)
+                         params.max_retries, int(params.step_rule), params.seed, params.gamma)
     xp, xk = _ptr_kind(x0)
     idx = ctypes.c_int()
     check(lib().ntvs_batch_add(bt, ctypes.byref(st), ctypes.byref(p), xp, _dtype_code(x0), xk, ctypes.byref(idx)),
@@ -334,6 +336,14 @@ class Params:
     seed: int = 0
     eps_tv: float = 1e-8
     max_retries: int = 64
+    step_rule: int = 0      # NTVS_STEP_NTVS / NTVS_STEP_OTVS / NTVS_STEP_DECOUPLED
+    gamma: float = 0.5      # decoupled rule: beta_{k,n} = beta0 alpha^n gamma^k
+
+    @staticmethod
+    def otvs(lam: float = 1e-4, **kw) -> "Params":
+        """The paper's OTVS (Appendix B): one checked step per cycle, beta = (1/2)^ell with
+        ell counting every try since the start of the run."""
+        return Params(lam=lam, N=1, alpha=0.5, beta0=1.0, tv_check=True, step_rule=NTVS_STEP_OTVS, **kw)
 
 
 class Batch:
@@ -424,7 +434,8 @@ class Reconstructor:
 
     def set_params(self, p: Params = None, **kw):
         p = p or Params(**kw)
-        ntvs_set_params(self._ctx, p.lam, p.N, p.alpha, p.beta0, p.tv_check, p.seed, p.eps_tv, p.max_retries)
+        ntvs_set_params(self._ctx, p.lam, p.N, p.alpha, p.beta0, p.tv_check, p.seed, p.eps_tv, p.max_retries,
+                        p.step_rule, p.gamma)
         return self
 
     def set_image(self, x):

@@ -24,6 +24,7 @@ NTVS_F64, NTVS_F32, NTVS_F16, NTVS_BF16 = 0, 1, 2, 3
 NTVS_MEM_HOST, NTVS_MEM_DEVICE = 0, 1
 NTVS_CSR32, NTVS_DELTA16 = 0, 1
 NTVS_SCHED_AUTO, NTVS_SCHED_PLAIN, NTVS_SCHED_WINDOW, NTVS_SCHED_PIPELINE, NTVS_SCHED_ONTHEFLY = 0, 1, 2, 3, 4
+NTVS_STEP_NTVS, NTVS_STEP_OTVS, NTVS_STEP_DECOUPLED = 0, 1, 2
 
 ERROR_NAMES = {NTVS_ERR_ARG: "NTVS_ERR_ARG", NTVS_ERR_CSR: "NTVS_ERR_CSR", NTVS_ERR_OOM: "NTVS_ERR_OOM",
                NTVS_ERR_CUDA: "NTVS_ERR_CUDA", NTVS_ERR_TIMEOUT: "NTVS_ERR_TIMEOUT",
@@ -50,7 +51,8 @@ class ntvs_paths(ctypes.Structure):
 class ntvs_params(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_double), ("alpha", ctypes.c_double), ("beta0", ctypes.c_double),
                 ("eps_tv", ctypes.c_double), ("N", ctypes.c_int32), ("tv_check", ctypes.c_int32),
-                ("max_retries", ctypes.c_int32), ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("max_retries", ctypes.c_int32), ("step_rule", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("gamma", ctypes.c_double)]
 
 
 class ntvs_stats(ctypes.Structure):

@@ -21,6 +21,7 @@
 
 #include "common.cuh"
 #include "ntvs.h"
+#include "step_rule.h"
 
 namespace ntvs {
 namespace {
@@ -240,13 +241,6 @@ int bfail(int code, const std::string& m) {
         if (r_ != NTVS_OK) return r_; \
     } while (0)
 
-uint64_t sm64(uint64_t seed, uint64_t n) {   // SplitMix64, output n of stream seed
-    uint64_t z = seed + (n + 1) * 0x9E3779B97F4A7C15ULL;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
-    return z ^ (z >> 31);
-}
-
 template <typename P>
 int balloc(P** p, size_t bytes, const char* what) {
     *p = nullptr;
@@ -393,6 +387,10 @@ int ntvs_batch_add(ntvs_batch* bt, const ntvs_system* s, const ntvs_params* p, c
     if (p->tv_check) return bfail(NTVS_ERR_ARG, "batched members run NTVS without the TV check");
     if (p->N < 0 || !(p->alpha > 0 && p->alpha < 1) || !(p->beta0 >= 0) || !(p->eps_tv >= 0))
         return bfail(NTVS_ERR_ARG, "bad parameters");
+    if (p->step_rule < NTVS_STEP_NTVS || p->step_rule > NTVS_STEP_DECOUPLED)
+        return bfail(NTVS_ERR_ARG, "unknown step_rule");
+    if (p->step_rule == NTVS_STEP_DECOUPLED && !(p->gamma > 0 && p->gamma < 1))
+        return bfail(NTVS_ERR_ARG, "gamma must lie in (0, 1)");
     if (s->nx < 1 || s->ny < 1 || s->nz < 1 || s->n_rows < 0) return bfail(NTVS_ERR_ARG, "bad sizes");
     if (x0_dtype != NTVS_F64 && x0_dtype != NTVS_F32) return bfail(NTVS_ERR_ARG, "x0 dtype must be F64 or F32");
     const int64_t V = (int64_t)s->nx * s->ny * s->nz;
@@ -615,13 +613,13 @@ int ntvs_batch_run(ntvs_batch* bt, int k_iters) {
         for (int r = 0; r < R; ++r) {
             auto& mm = bt->m[r];
             const int64_t k = mm.k;
-            const int64_t lo = std::min(k, mm.ell_prev), hi = std::max(k, mm.ell_prev);
-            int64_t ell = lo + (int64_t)(sm64(mm.p.seed, (uint64_t)k) % (uint64_t)(hi - lo + 1));
+            int64_t ell = cycle_ell(mm.p, k, mm.ell_prev);
+            const int64_t adv = ell_advances(mm.p) ? 1 : 0;
             for (int n = 0; n < bt->N_max; ++n) {
-                hb[(size_t)n * R + r] = (n < mm.p.N) ? mm.p.beta0 * std::pow(mm.p.alpha, (double)ell) : 0.0;
-                if (n < mm.p.N) ell += 1;
+                hb[(size_t)n * R + r] = (n < mm.p.N) ? step_beta(mm.p, k, n, ell) : 0.0;
+                if (n < mm.p.N) ell += adv;
             }
-            mm.ell_prev = ell;
+            if (adv) mm.ell_prev = ell;
             mm.k = k + 1;
         }
         BCUDA(cudaGraphLaunch(bt->graph[j], bt->stream));

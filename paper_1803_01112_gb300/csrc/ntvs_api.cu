@@ -15,6 +15,7 @@
 
 #include "ntvs.h"
 #include "ntvs_internal.h"
+#include "step_rule.h"
 
 using namespace ntvs;
 
@@ -41,21 +42,6 @@ std::string cuda_msg(const char* what, cudaError_t e) { return std::string(what)
         int r_ = (expr);            \
         if (r_ != NTVS_OK) return r_; \
     } while (0)
-
-// SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) in counter form: output n of stream seed.
-uint64_t splitmix64_at(uint64_t seed, uint64_t n) {
-    uint64_t z = seed + (n + 1) * 0x9E3779B97F4A7C15ULL;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
-    return z ^ (z >> 31);
-}
-
-// ell_k = rand(k, ell_{k-1}): uniform integer between the two (inclusive), draw k of the stream.
-int64_t draw_ell(uint64_t seed, int64_t k, int64_t ell_prev) {
-    const int64_t lo = k < ell_prev ? k : ell_prev, hi = k < ell_prev ? ell_prev : k;
-    const uint64_t span = (uint64_t)(hi - lo) + 1u;
-    return lo + (int64_t)(splitmix64_at(seed, (uint64_t)k) % span);
-}
 
 template <typename T>
 int dev_alloc(T** p, size_t bytes, const char* what) {
@@ -335,15 +321,16 @@ int checked_try(ntvs_ctx* c, double beta, int* acc) {
 int perturb_steps(ntvs_ctx* c, int64_t* ell_io) {
     int64_t ell = *ell_io;
     const int N = c->p.N;
+    const int64_t adv = ell_advances(c->p) ? 1 : 0;
     for (int n = 0; n < N; ++n) {
-        double beta = c->p.beta0 * std::pow(c->p.alpha, (double)ell);
+        double beta = step_beta(c->p, c->k, n, ell);
         int tries = 0, acc = 0;
         if (!c->p.tv_check) {
             TRY(launch_grad(c, false));
             CUDA_TRY(timed_launch(c, KIND_TV, [&] {
                 return k_tv_apply(c->cdt, c->x, c->x32, c->g, c->dscal + 0, beta, nullptr, c->V, c->vm, c->stream);
             }));
-            ell += 1;
+            ell += adv;
             tries = 1;
             acc = 1;
         } else {
@@ -351,11 +338,11 @@ int perturb_steps(ntvs_ctx* c, int64_t* ell_io) {
             for (;;) {
                 int a = 0;
                 TRY(checked_try(c, beta, &a));
-                ell += 1;
+                ell += adv;
                 tries += 1;
                 if (a) { acc = 1; break; }
                 if (tries >= c->p.max_retries) break;
-                beta = c->p.beta0 * std::pow(c->p.alpha, (double)ell);
+                beta = step_beta(c->p, c->k, n, ell);
             }
         }
         c->tries_trace.push_back(tries);
@@ -1005,6 +992,12 @@ int ntvs_set_params(ntvs_ctx* c, const ntvs_params* p) {
     if (!(p->eps_tv >= 0.0) || !std::isfinite(p->eps_tv)) return fail(NTVS_ERR_ARG, "eps_tv must be finite and >= 0");
     if (!std::isfinite(p->lambda)) return fail(NTVS_ERR_ARG, "lambda must be finite");
     if (p->tv_check && p->max_retries < 1) return fail(NTVS_ERR_ARG, "max_retries must be >= 1");
+    if (p->step_rule < NTVS_STEP_NTVS || p->step_rule > NTVS_STEP_DECOUPLED)
+        return fail(NTVS_ERR_ARG, "unknown step_rule");
+    if (p->step_rule == NTVS_STEP_DECOUPLED) {
+        if (!(p->gamma > 0.0 && p->gamma < 1.0)) return fail(NTVS_ERR_ARG, "gamma must lie in (0, 1)");
+        if (p->tv_check) return fail(NTVS_ERR_ARG, "the decoupled step rule is defined without the TV check");
+    }
     c->p = *p;
     return NTVS_OK;
 }
@@ -1047,10 +1040,10 @@ int ntvs_run(ntvs_ctx* c, int k_iters) {
     for (int kk = 0; kk < k_iters; ++kk) {
         int64_t ell;
         if (c->override_pos < c->override_ell.size()) ell = c->override_ell[c->override_pos++];
-        else ell = draw_ell(c->p.seed, c->k, c->ell_prev);
+        else ell = cycle_ell(c->p, c->k, c->ell_prev);
         c->ell_trace.push_back(ell);
         TRY(perturb_steps(c, &ell));
-        c->ell_prev = ell;
+        if (ell_advances(c->p)) c->ell_prev = ell;
         TRY(drop_sweep(c));
         CUDA_TRY(timed_launch(c, KIND_TV, [&] {
             return k_tv_value(c->cdt, c->x, nullptr, c->dscal, 0.0, c->nx, c->ny, c->nz, c->red, c->tvhist + c->k,
