@@ -443,4 +443,50 @@ cudaError_t k_row_home(const int64_t* row_ptr, const int32_t* col, int64_t M, in
     return cudaGetLastError();
 }
 
+// A warp per chunk of rows [cs[q], cs[q+1]) (at most 64): the lower median (element n/2
+// of the sorted values) of the home slices of its non-empty rows, -1 when all are empty.
+// Rows i >= 1 whose home and the previous row's home are both defined and differ are
+// counted into *changes.
+__global__ void chunk_home_kernel(const int32_t* __restrict__ home, const int64_t* __restrict__ cs, int64_t nchunks,
+                                  int32_t* __restrict__ out, unsigned long long* changes) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long ch = 0;
+    for (int64_t q = w0; q < nchunks; q += nw) {
+        const int64_t i0 = cs[q], i1 = cs[q + 1];
+        const int64_t ia = i0 + lane, ib = i0 + 32 + lane;
+        const int32_t ha = ia < i1 ? home[ia] : -1;
+        const int32_t hb = ib < i1 ? home[ib] : -1;
+        if (ia < i1 && ia > 0) { const int32_t p = home[ia - 1]; ch += (ha >= 0 && p >= 0 && ha != p) ? 1 : 0; }
+        if (ib < i1) { const int32_t p = home[ib - 1]; ch += (hb >= 0 && p >= 0 && hb != p) ? 1 : 0; }
+        const int nv = __popc(__ballot_sync(0xffffffffu, ha >= 0)) + __popc(__ballot_sync(0xffffffffu, hb >= 0));
+        if (nv == 0) {
+            if (lane == 0) out[q] = -1;
+            continue;
+        }
+        const int k = nv / 2;
+        int la = 0, ea = 0, lb = 0, eb = 0;   // defined values below / at most ha and hb
+        for (int src = 0; src < 32; ++src) {
+            const int32_t wa = __shfl_sync(0xffffffffu, ha, src), wb = __shfl_sync(0xffffffffu, hb, src);
+            if (wa >= 0) { la += wa < ha; ea += wa <= ha; lb += wa < hb; eb += wa <= hb; }
+            if (wb >= 0) { la += wb < ha; ea += wb <= ha; lb += wb < hb; eb += wb <= hb; }
+        }
+        const unsigned ma = __ballot_sync(0xffffffffu, ha >= 0 && la <= k && k < ea);
+        const unsigned mb = __ballot_sync(0xffffffffu, hb >= 0 && lb <= k && k < eb);
+        const int32_t va = __shfl_sync(0xffffffffu, ha, ma ? __ffs(ma) - 1 : 0);
+        const int32_t vb = __shfl_sync(0xffffffffu, hb, mb ? __ffs(mb) - 1 : 0);
+        if (lane == 0) out[q] = ma ? va : vb;
+    }
+    for (int o = 16; o > 0; o >>= 1) ch += __shfl_xor_sync(0xffffffffu, ch, o);
+    if (lane == 0 && ch) atomicAdd(changes, ch);
+}
+
+cudaError_t k_chunk_home(const int32_t* home, const int64_t* chunk_start, int64_t nchunks, int32_t* out,
+                         unsigned long long* changes, int grid, cudaStream_t s) {
+    if (nchunks <= 0) return cudaSuccess;
+    chunk_home_kernel<<<grid, 256, 0, s>>>(home, chunk_start, nchunks, out, changes);
+    return cudaGetLastError();
+}
+
 }  // namespace ntvs

@@ -71,6 +71,7 @@ struct ntvs_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t copy_stream = nullptr;   // load: host-to-device copies overlapped with preparation
     int sms = 1;
 
     // system
@@ -151,6 +152,7 @@ struct ntvs_ctx {
     size_t csz() const { return dt_size(cdt); }
 
     void free_system() {
+        if (copy_stream) cudaStreamSynchronize(copy_stream);   // no copy may still target a buffer
         if (own_row_ptr) dev_free(row_ptr);
         if (own_col) dev_free(col);
         if (own_val) dev_free(val);
@@ -259,6 +261,10 @@ VoxMap make_voxmap(int nx, int ny, int nz, int tx, int ty) {
     VoxMap m;
     m.nx = nx; m.ny = ny; m.nz = nz;
     m.tx = tx; m.ty = ty;
+    m.ltx = 0;
+    while ((1 << m.ltx) < tx) ++m.ltx;
+    m.lty = 0;
+    while ((1 << m.lty) < ty) ++m.lty;
     m.nxp = (nx + tx - 1) / tx * tx;
     m.nyp = (ny + ty - 1) / ty * ty;
     m.slice_p = (int64_t)m.nxp * m.nyp;
@@ -525,25 +531,49 @@ static int plan_schedule(ntvs_ctx* c, int requested) {
                                           " bytes of shared memory, the device allows " + std::to_string(optin));
         return NTVS_OK;
     }
-    // home slice of every row
+    // home slice of every row, then on the device the median home of every chunk of
+    // kChunkRows rows (chunks restart at each block) and the number of home changes
+    // between consecutive rows; only the chunk medians come back to the host
+    std::vector<int64_t> cstart;
+    std::vector<int64_t> block_chunk(c->B + 1, 0);
+    for (int t = 0; t < c->B; ++t) {
+        block_chunk[t] = (int64_t)cstart.size();
+        for (int64_t i = c->block_ptr[t]; i < c->block_ptr[t + 1]; i += kChunkRows) cstart.push_back(i);
+    }
+    block_chunk[c->B] = (int64_t)cstart.size();
+    const int64_t nch = (int64_t)cstart.size();
+    cstart.push_back(c->M);
     int32_t* dhome = nullptr;
+    int32_t* dchunk = nullptr;
+    int64_t* dstart = nullptr;
+    unsigned long long* dchanges = nullptr;
     TRY(dev_alloc(&dhome, sizeof(int32_t) * (size_t)c->M, "row home slices"));
-    std::vector<int32_t> home((size_t)c->M);
-    cudaError_t e = k_row_home(c->row_ptr, c->col, c->M, slice, dhome, c->sms * 8, c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(home.data(), dhome, sizeof(int32_t) * home.size(), cudaMemcpyDeviceToHost,
-                                              c->stream);
+    TRY(dev_alloc(&dchunk, sizeof(int32_t) * (size_t)std::max<int64_t>(nch, 1), "chunk home slices"));
+    TRY(dev_alloc(&dstart, sizeof(int64_t) * cstart.size(), "chunk starts"));
+    TRY(dev_alloc(&dchanges, sizeof(unsigned long long), "home changes"));
+    std::vector<int32_t> chome((size_t)nch);
+    unsigned long long changes = 0;
+    cudaError_t e = cudaMemcpyAsync(dstart, cstart.data(), sizeof(int64_t) * cstart.size(), cudaMemcpyHostToDevice,
+                                    c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dchanges, 0, sizeof(unsigned long long), c->stream);
+    if (e == cudaSuccess) e = k_row_home(c->row_ptr, c->col, c->M, slice, dhome, c->sms * 8, c->stream);
+    if (e == cudaSuccess) e = k_chunk_home(dhome, dstart, nch, dchunk, dchanges, c->sms * 8, c->stream);
+    if (e == cudaSuccess && nch > 0)
+        e = cudaMemcpyAsync(chome.data(), dchunk, sizeof(int32_t) * (size_t)nch, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&changes, dchanges, sizeof(changes), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     dev_free(dhome);
+    dev_free(dchunk);
+    dev_free(dstart);
+    dev_free(dchanges);
     if (e != cudaSuccess) return fail(NTVS_ERR_CUDA, cuda_msg("row home slices", e));
     int32_t last = 0;
-    for (auto& h : home) {   // empty rows join their predecessor's run
+    for (auto& h : chome) {   // chunks of empty rows join their predecessor's run
         if (h < 0) h = last;
         last = h;
     }
     // mean run length of equal home slices in stored order
-    int64_t runs = 1;
-    for (int64_t i = 1; i < c->M; ++i) runs += home[i] != home[i - 1];
-    const double mean_run = (double)c->M / (double)runs;
+    const double mean_run = (double)c->M / (double)(changes + 1);
     if (requested == NTVS_SCHED_AUTO && mean_run < kMinMeanRun) return NTVS_OK;
 
     const int G = c->sms;
@@ -554,13 +584,7 @@ static int plan_schedule(ntvs_ctx* c, int requested) {
     for (int t = 0; t < c->B; ++t) {
         const int64_t r0 = c->block_ptr[t], r1 = c->block_ptr[t + 1];
         ch.clear();
-        std::vector<int32_t> hh;
-        for (int64_t i = r0; i < r1; i += kChunkRows) {
-            const int64_t j = std::min<int64_t>(r1, i + kChunkRows);
-            hh.assign(home.begin() + i, home.begin() + j);
-            std::nth_element(hh.begin(), hh.begin() + hh.size() / 2, hh.end());
-            ch.push_back({i, j, hh[hh.size() / 2]});
-        }
+        for (int64_t q = block_chunk[t]; q < block_chunk[t + 1]; ++q) ch.push_back({cstart[q], cstart[q + 1], chome[q]});
         std::stable_sort(ch.begin(), ch.end(), [](const Chunk& a, const Chunk& b) { return a.home < b.home; });
         int32_t* bg = begin.data() + (size_t)t * (G + 1);
         const int64_t total = r1 - r0;
@@ -688,6 +712,14 @@ int ntvs_create(ntvs_ctx** out, int device, void* cuda_stream) {
         if (e != cudaSuccess) { delete c; return fail(NTVS_ERR_CUDA, cuda_msg("cudaStreamCreate", e)); }
         c->own_stream = true;
     }
+    {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            c->copy_stream = nullptr;
+            ntvs_destroy(c);
+            return fail(NTVS_ERR_CUDA, cuda_msg("cudaStreamCreate", e));
+        }
+    }
     const int maxgrid = c->sms * 8;
     c->red.grid = 1;
     if ((rc = dev_alloc(&c->red.partials, sizeof(double) * 2 * (size_t)maxgrid, "reduction partials")) ||
@@ -737,6 +769,7 @@ int ntvs_destroy(ntvs_ctx* c) {
     for (auto e : c->event_pool) cudaEventDestroy(e);
     if (c->hscal) cudaFreeHost(c->hscal);
     if (c->hint) cudaFreeHost(c->hint);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return NTVS_OK;
@@ -803,14 +836,53 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
     const size_t vsz = dt_size(c->vdt), csz = c->csz();
     TRY(copy_in((void**)&c->row_ptr, &c->own_row_ptr, s->row_ptr, sizeof(int64_t) * (size_t)(M + 1), s->mem_kind, st,
                 "row_ptr"));
-    TRY(copy_in((void**)&c->col, &c->own_col, s->col, sizeof(int32_t) * (size_t)nnz, s->mem_kind, st, "col"));
-    TRY(copy_in(&c->val, &c->own_val, s->val, vsz * (size_t)nnz, s->mem_kind, st, "val"));
     TRY(copy_in(&c->b, &c->own_b, s->b, csz * (size_t)M, s->mem_kind, st, "b"));
+    // Host arrays: col and val are copied block by block on the copy stream, and each
+    // block's preparation (on the context's stream) starts once its entries have arrived,
+    // so the preparation hides behind the host-to-device copy.  Block t's entry range
+    // comes from the host row_ptr, clamped to [0, nnz); a row_ptr that is not
+    // non-decreasing is rejected below before any block is prepared.
+    const bool piped = s->mem_kind == NTVS_MEM_HOST && nnz > 0 && c->copy_stream != nullptr;
+    std::vector<cudaEvent_t> arrived;
+    std::vector<int64_t> eb;   // [B+1] entry range of each block (piped)
+    struct EventGuard {
+        std::vector<cudaEvent_t>& v;
+        ~EventGuard() { for (auto e : v) cudaEventDestroy(e); }
+    } guard{arrived};
+    if (piped) {
+        TRY(dev_alloc(&c->col, sizeof(int32_t) * (size_t)nnz, "col"));
+        c->own_col = true;
+        TRY(dev_alloc(&c->val, vsz * (size_t)nnz, "val"));
+        c->own_val = true;
+        eb.resize((size_t)c->B + 1);
+        for (int t = 0; t <= c->B; ++t) {
+            int64_t e = s->row_ptr[bp[t]];
+            e = e < 0 ? 0 : (e > nnz ? nnz : e);
+            eb[t] = t > 0 && e < eb[t - 1] ? eb[t - 1] : e;
+        }
+        eb[c->B] = nnz;
+        for (int t = 0; t < c->B; ++t) {
+            const int64_t e0 = eb[t], n = eb[t + 1] - eb[t];
+            if (n > 0) {
+                CUDA_TRY(cudaMemcpyAsync(c->col + e0, s->col + e0, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice,
+                                         c->copy_stream));
+                CUDA_TRY(cudaMemcpyAsync((char*)c->val + vsz * (size_t)e0, (const char*)s->val + vsz * (size_t)e0,
+                                         vsz * (size_t)n, cudaMemcpyHostToDevice, c->copy_stream));
+            }
+            cudaEvent_t ev;
+            CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+            arrived.push_back(ev);
+            CUDA_TRY(cudaEventRecord(ev, c->copy_stream));
+        }
+    } else {
+        TRY(copy_in((void**)&c->col, &c->own_col, s->col, sizeof(int32_t) * (size_t)nnz, s->mem_kind, st, "col"));
+        TRY(copy_in(&c->val, &c->own_val, s->val, vsz * (size_t)nnz, s->mem_kind, st, "val"));
+    }
 
     // validation; columns of the tiled order are rewritten into a buffer of the context's
     // own (caller memory is never modified)
     CUDA_TRY(cudaMemsetAsync(c->dflags, 0, sizeof(int), st));
-    if (tiled && nnz > 0) {
+    if (tiled && nnz > 0 && !piped) {
         if (!c->own_col) {
             int32_t* mine = nullptr;
             TRY(dev_alloc(&mine, sizeof(int32_t) * (size_t)nnz, "col (internal order)"));
@@ -833,9 +905,14 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
     int32_t* cnt = nullptr;
     TRY(dev_alloc(&cnt, sizeof(int32_t) * (size_t)c->B * VI, "hit counts"));
     CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)c->B * VI, st));
-    for (int t = 0; t < c->B; ++t)
+    for (int t = 0; t < c->B; ++t) {
+        if (piped) {
+            CUDA_TRY(cudaStreamWaitEvent(st, arrived[t], 0));
+            if (tiled) CUDA_TRY(k_remap_cols(c->col + eb[t], c->col + eb[t], eb[t + 1] - eb[t], c->vm, c->dflags, st));
+        }
         CUDA_TRY(k_prep_block(c->row_ptr, c->col, c->val, c->vdt, c->b, bp[t], bp[t + 1], VI, c->inv_norm2, c->cdt,
                               cnt + (size_t)t * VI, c->dflags, st));
+    }
     CUDA_TRY(cudaMemcpyAsync(c->hint, c->dflags, sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     if (c->hint[0]) {

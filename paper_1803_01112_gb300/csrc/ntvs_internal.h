@@ -17,10 +17,12 @@ inline size_t dt_size(int dt) { return dt == F64 ? 8 : dt == F32 ? 4 : 2; }
 // in-plane tiles of tx x ty voxels, each tile contiguous, tiles row-major over a grid padded
 // to multiples of the tile, slices contiguous (slice_p voxels each).  tx = ty = 1 is the
 // canonical order (iz*ny + iy)*nx + ix.  Public images and the FP64 master stay canonical.
+// tx, ty are powers of two (ltx, lty their logarithms); V and vint stay below 2^31.
 struct VoxMap {
     int nx, ny, nz;
     int nxp, nyp;      // padded to multiples of tx, ty
     int tx, ty;
+    int ltx, lty;
     int64_t slice_p;   // nxp * nyp
     int64_t vint;      // nz * slice_p
 };
@@ -117,6 +119,11 @@ cudaError_t k_drop_block(const DropArgs& a, cudaStream_t s);
 // home[i] = median z-slice of the first, middle and last entries of row i (-1: empty row)
 cudaError_t k_row_home(const int64_t* row_ptr, const int32_t* col, int64_t M, int64_t slice, int32_t* home, int grid,
                        cudaStream_t s);
+// chunk q = rows [chunk_start[q], chunk_start[q+1]) (at most 64 rows): out[q] = lower median
+// of the defined home slices (-1 if none); *changes += rows whose defined home differs from
+// the previous row's defined home (*changes must be zeroed by the caller)
+cudaError_t k_chunk_home(const int32_t* home, const int64_t* chunk_start, int64_t nchunks, int32_t* out,
+                         unsigned long long* changes, int grid, cudaStream_t s);
 // x_j += delta_p * inv_s_p on the FP64 master (p the internal index of j; x32_p <- (float)x_j
 // when x32 != null); delta_p = 0
 cudaError_t k_drop_apply(int cdt, double* x, float* x32, void* delta, const void* inv_s, int64_t V, VoxMap m,
