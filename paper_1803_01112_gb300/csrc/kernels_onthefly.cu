@@ -19,6 +19,7 @@ namespace {
 
 struct Grid3 {
     float ox, oy, oz, hx, hy, hz;
+    float ihx, ihy, ihz;   // 1 / voxel size
     int nx, ny, nz;
 };
 
@@ -41,42 +42,57 @@ __device__ __forceinline__ void chord_normal(const float* pr, float& nxv, float&
     else { nxv = 1.f; nyv = 0.f; }
 }
 
-// Calls f(voxel, length) for every piece of segment P -> Q inside the grid.
+// Calls f(voxel, length) for every piece of segment P -> Q inside the grid.  The segment is
+// clipped to the grid, the crossings of the three plane families are merged in order of
+// their parameter t (each from its plane index: t = (o + k h - P) / D, computed with the
+// reciprocal of D), and a piece between consecutive crossings is credited to the voxel
+// between those planes: the voxel before the first crossing of each axis follows from
+// that crossing's plane index, and the index is stepped by one along the axis of every
+// crossing, so the voxel of a piece is always the one bounded by the planes around it
+// (the voxel holding the piece's midpoint).
 template <typename F>
 __device__ __forceinline__ void trace_segment(const Grid3& g, const float P[3], const float Q[3], F&& f) {
     const float D[3] = {Q[0] - P[0], Q[1] - P[1], Q[2] - P[2]};
     const float L = sqrtf(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
     if (!(L > 0.f)) return;
-    const float o[3] = {g.ox, g.oy, g.oz}, h[3] = {g.hx, g.hy, g.hz};
+    const float o[3] = {g.ox, g.oy, g.oz}, h[3] = {g.hx, g.hy, g.hz}, ih[3] = {g.ihx, g.ihy, g.ihz};
     const int n[3] = {g.nx, g.ny, g.nz};
+    float inv[3];
     float lo = 0.f, hi = 1.f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const float e0 = o[a], e1 = o[a] + n[a] * h[a];
+        inv[a] = D[a] != 0.f ? 1.f / D[a] : 0.f;
         if (D[a] == 0.f) {
             if (P[a] < e0 || P[a] > e1) return;
         } else {
-            float s0 = (e0 - P[a]) / D[a], s1 = (e1 - P[a]) / D[a];
+            float s0 = (e0 - P[a]) * inv[a], s1 = (e1 - P[a]) * inv[a];
             if (s0 > s1) { const float t = s0; s0 = s1; s1 = t; }
             lo = fmaxf(lo, s0);
             hi = fminf(hi, s1);
         }
     }
     if (!(hi > lo)) return;
-    // next crossing of each axis: plane index k, parameter (o + k h - P) / D
+    // next crossing of each axis: plane index k, parameter tn
     int k[3], step[3];
     float tn[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (D[a] == 0.f) { tn[a] = 2.f; step[a] = 0; k[a] = 0; continue; }
-        const float u = (P[a] + lo * D[a] - o[a]) / h[a];
+        const float u = (P[a] + lo * D[a] - o[a]) * ih[a];
         step[a] = D[a] > 0.f ? 1 : -1;
         k[a] = D[a] > 0.f ? (int)floorf(u) + 1 : (int)ceilf(u) - 1;
-        tn[a] = (o[a] + k[a] * h[a] - P[a]) / D[a];
+        tn[a] = (o[a] + k[a] * h[a] - P[a]) * inv[a];
         if (tn[a] <= lo) {   // the start lies on plane k: move to the next one
             k[a] += step[a];
-            tn[a] = (o[a] + k[a] * h[a] - P[a]) / D[a];
+            tn[a] = (o[a] + k[a] * h[a] - P[a]) * inv[a];
         }
+    }
+    int idx[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int i = step[a] > 0 ? k[a] - 1 : step[a] < 0 ? k[a] : (int)floorf((P[a] - o[a]) * ih[a]);
+        idx[a] = min(max(i, 0), n[a] - 1);
     }
     float t0 = lo;
     for (int guard = 0; guard < 4 * (g.nx + g.ny + g.nz) + 8; ++guard) {
@@ -86,19 +102,16 @@ __device__ __forceinline__ void trace_segment(const Grid3& g, const float P[3], 
         if (tn[2] < t1) { t1 = tn[2]; w = 2; }
         const bool last = !(t1 < hi);
         if (last) t1 = hi;
-        if (t1 - t0 > 1e-7f) {
-            const float tm = 0.5f * (t0 + t1);
-            int idx[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                int i = (int)floorf((P[a] + tm * D[a] - o[a]) / h[a]);
-                idx[a] = min(max(i, 0), n[a] - 1);
-            }
-            f(((idx[2] * g.ny) + idx[1]) * g.nx + idx[0], (t1 - t0) * L);
-        }
+        if (t1 - t0 > 1e-7f) f(((idx[2] * g.ny) + idx[1]) * g.nx + idx[0], (t1 - t0) * L);
         if (last) break;
-        k[w] += step[w];
-        tn[w] = (o[w] + k[w] * h[w] - P[w]) / D[w];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {   // constant indices keep the arrays in registers
+            if (a == w) {
+                idx[a] = min(max(idx[a] + step[a], 0), n[a] - 1);
+                k[a] += step[a];
+                tn[a] = (o[a] + k[a] * h[a] - P[a]) * inv[a];
+            }
+        }
         t0 = t1;
     }
 }
@@ -141,13 +154,25 @@ __global__ void otf_prep_kernel(const float* __restrict__ paths, int64_t r0, int
 
 // ---------------------------------------------------------------- the DROP block
 // A group of 16 lanes per row (2 rows per warp); lane s traces segments s, s + 16, ...
-__global__ void __launch_bounds__(256) otf_drop_kernel(const float* __restrict__ paths, const float* __restrict__ b,
-                                                       const float* __restrict__ inv_norm2, int64_t r0, int64_t r1,
-                                                       Grid3 g, int n_seg, float min_len, const float* __restrict__ x,
-                                                       float* __restrict__ delta, float lambda, double* resid_ss) {
+// The dot-product pass keeps the first kOtfCache accepted pieces of each lane (voxel,
+// length) in shared memory, and the scatter pass replays them; a lane with more pieces
+// traces its segments again and scatters only the pieces past the cached ones.
+constexpr int kOtfThreads = 256;
+constexpr int kOtfCache = 24;
+
+__global__ void __launch_bounds__(kOtfThreads) otf_drop_kernel(const float* __restrict__ paths,
+                                                                const float* __restrict__ b,
+                                                                const float* __restrict__ inv_norm2, int64_t r0,
+                                                                int64_t r1, Grid3 g, int n_seg, float min_len,
+                                                                const float* __restrict__ x, float* __restrict__ delta,
+                                                                float lambda, double* resid_ss) {
     constexpr int LPR = 16;
-    const int lane = threadIdx.x & 31, sub = lane % LPR;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    extern __shared__ __align__(16) unsigned char otf_smem[];
+    int32_t* cv = reinterpret_cast<int32_t*>(otf_smem);                 // [kOtfCache][kOtfThreads]
+    float* cl = reinterpret_cast<float*>(cv + kOtfCache * kOtfThreads);  // [kOtfCache][kOtfThreads]
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, sub = lane % LPR;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + tid) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double ss = 0.0;
     for (int64_t base = r0 + warp * 2; base < r1; base += nwarps * 2) {
@@ -159,13 +184,21 @@ __global__ void __launch_bounds__(256) otf_drop_kernel(const float* __restrict__
         float nxv, nyv;
         chord_normal(pr, nxv, nyv);
         float acc = 0.f;
+        int np = 0;   // accepted pieces of this lane
         if (valid) {
             for (int sg = sub; sg < n_seg; sg += LPR) {
                 float A[3], B[3];
                 path_point(pr, nxv, nyv, (float)sg / (float)n_seg, A);
                 path_point(pr, nxv, nyv, (float)(sg + 1) / (float)n_seg, B);
                 trace_segment(g, A, B, [&](int v, float l) {
-                    if (l >= min_len) acc += l * __ldg(x + v);
+                    if (l >= min_len) {
+                        acc += l * __ldg(x + v);
+                        if (np < kOtfCache) {
+                            cv[np * kOtfThreads + tid] = v;
+                            cl[np * kOtfThreads + tid] = l;
+                        }
+                        ++np;
+                    }
                 });
             }
         }
@@ -175,13 +208,21 @@ __global__ void __launch_bounds__(256) otf_drop_kernel(const float* __restrict__
         const float res = __ldg(b + i) - acc;
         const float r = lambda * res * __ldg(inv_norm2 + i);
         if (sub == 0) ss += (double)res * (double)res;
-        for (int sg = sub; sg < n_seg; sg += LPR) {
-            float A[3], B[3];
-            path_point(pr, nxv, nyv, (float)sg / (float)n_seg, A);
-            path_point(pr, nxv, nyv, (float)(sg + 1) / (float)n_seg, B);
-            trace_segment(g, A, B, [&](int v, float l) {
-                if (l >= min_len) atomicAdd(delta + v, r * l);
-            });
+        const int nc = np < kOtfCache ? np : kOtfCache;
+        for (int q = 0; q < nc; ++q) atomicAdd(delta + cv[q * kOtfThreads + tid], r * cl[q * kOtfThreads + tid]);
+        if (np > kOtfCache) {
+            int seen = 0;
+            for (int sg = sub; sg < n_seg; sg += LPR) {
+                float A[3], B[3];
+                path_point(pr, nxv, nyv, (float)sg / (float)n_seg, A);
+                path_point(pr, nxv, nyv, (float)(sg + 1) / (float)n_seg, B);
+                trace_segment(g, A, B, [&](int v, float l) {
+                    if (l >= min_len) {
+                        if (seen >= kOtfCache) atomicAdd(delta + v, r * l);
+                        ++seen;
+                    }
+                });
+            }
         }
     }
     __shared__ double sh[32];
@@ -207,6 +248,7 @@ static Grid3 make_grid(const OtfArgs& a) {
     Grid3 g;
     g.nx = a.nx; g.ny = a.ny; g.nz = a.nz;
     g.hx = (float)a.dx; g.hy = (float)a.dy; g.hz = (float)a.dz;
+    g.ihx = 1.f / g.hx; g.ihy = 1.f / g.hy; g.ihz = 1.f / g.hz;
     g.ox = (float)(-0.5 * a.nx * a.dx); g.oy = (float)(-0.5 * a.ny * a.dy); g.oz = 0.f;
     return g;
 }
@@ -226,8 +268,11 @@ cudaError_t k_otf_prep(const OtfArgs& a, int64_t r0, int64_t r1, float* inv_norm
 cudaError_t k_otf_drop(const OtfArgs& a, int64_t r0, int64_t r1, const float* inv_norm2, const float* x, float* delta,
                        double lambda, double* resid_ss, cudaStream_t s) {
     if (r1 <= r0) return cudaSuccess;
-    otf_drop_kernel<<<a.grid, 256, 0, s>>>(a.paths, a.b, inv_norm2, r0, r1, make_grid(a), a.n_seg, a.min_len, x,
-                                           delta, (float)lambda, resid_ss);
+    const size_t smem = (size_t)kOtfCache * kOtfThreads * (sizeof(int32_t) + sizeof(float));
+    cudaError_t e = cudaFuncSetAttribute(otf_drop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    otf_drop_kernel<<<a.grid, kOtfThreads, smem, s>>>(a.paths, a.b, inv_norm2, r0, r1, make_grid(a), a.n_seg,
+                                                      a.min_len, x, delta, (float)lambda, resid_ss);
     return cudaGetLastError();
 }
 
