@@ -192,15 +192,30 @@ __global__ void __launch_bounds__(kOtfThreads) otf_drop_kernel(const float* __re
                 path_point(pr, nxv, nyv, (float)(sg + 1) / (float)n_seg, B);
                 trace_segment(g, A, B, [&](int v, float l) {
                     if (l >= min_len) {
-                        acc += l * __ldg(x + v);
                         if (np < kOtfCache) {
                             cv[np * kOtfThreads + tid] = v;
                             cl[np * kOtfThreads + tid] = l;
+                        } else {
+                            acc += l * __ldg(x + v);
                         }
                         ++np;
                     }
                 });
             }
+            // the cached pieces' gathers are independent: issued back to back, four in flight
+            const int nc = np < kOtfCache ? np : kOtfCache;
+            int q = 0;
+            for (; q + 4 <= nc; q += 4) {
+                float xv[4], lv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    xv[u] = __ldg(x + cv[(q + u) * kOtfThreads + tid]);
+                    lv[u] = cl[(q + u) * kOtfThreads + tid];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc += lv[u] * xv[u];
+            }
+            for (; q < nc; ++q) acc += cl[q * kOtfThreads + tid] * __ldg(x + cv[q * kOtfThreads + tid]);
         }
 #pragma unroll
         for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
