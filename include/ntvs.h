@@ -204,6 +204,36 @@ typedef struct {
  * (non-finite path or b), NTVS_ERR_OOM, NTVS_ERR_CUDA. */
 int ntvs_load_paths(ntvs_ctx* ctx, const ntvs_paths* p);
 
+/* The same system given by the tracking data of each history (Sec. I: every proton is
+ * tracked and its most likely path predicted from that data).  History i (12 floats, mm):
+ * entry point P_in (x,y,z), exit point P_out (x,y,z), entry direction d_in and exit
+ * direction d_out (any length; a zero vector stands for the chord
+ * direction).  Its path is the cubic Hermite curve from P_in to P_out with end tangents
+ * L d_in/|d_in| and L d_out/|d_out|, L = |P_out - P_in| (the paper's most likely path is not
+ * defined in it; this curve stands in for it).  The curve is stored in the path-record form
+ * of ntvs_load_paths: the tangents' deviations from the chord, m - (P_out - P_in), are
+ * projected on the chord's in-plane normal n (A_lat, B_lat) and on z (A_z, B_z); their
+ * component along the chord's in-plane direction, which only re-times the walk along the
+ * curve, is dropped.  The conversion runs on the device; everything else is
+ * ntvs_load_paths.  The paper has no counterpart for this format. */
+typedef struct {
+    int32_t nx, ny, nz;
+    int32_t n_blocks;            /* contiguous blocks of ceil(M/B) rows when block_ptr is NULL */
+    double dx, dy, dz;           /* voxel size (mm)                                            */
+    int64_t n_rows;              /* M                                                          */
+    const float* hist;           /* [M][12] P_in, P_out, d_in, d_out (mem_kind; read at load)  */
+    const float* b;              /* [M] WEPL (mem_kind; device b is borrowed, host b copied)   */
+    const int64_t* block_ptr;    /* NULL or [B+1] HOST array                                   */
+    int32_t n_seg;               /* straight segments per path, 1..64                          */
+    int32_t mem_kind;            /* NTVS_MEM_HOST | NTVS_MEM_DEVICE                            */
+    double min_len;              /* pieces shorter than this are dropped (mm), >= 0            */
+} ntvs_histories;
+
+/* Load (replace) the system from history data; the context keeps the converted path
+ * records (40 B per history) and, for host input, its own copy of b.  Errors as
+ * ntvs_load_paths (NTVS_ERR_CSR for a non-finite history value or b). */
+int ntvs_load_histories(ntvs_ctx* ctx, const ntvs_histories* h);
+
 /* Set the NTVS parameters (Appendix C).  Validated: N >= 0, 0 < alpha < 1, beta0 >= 0,
  * eps_tv >= 0, lambda finite, max_retries >= 1 when tv_check.  Default before the first
  * call: lambda 1e-4, alpha 0.75, beta0 1, eps_tv 1e-8, N 0, no check, 64 retries, seed 0. */

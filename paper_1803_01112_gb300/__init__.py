@@ -135,6 +135,23 @@ def ntvs_load_paths(ctx: int, nx: int, ny: int, nz: int, voxel, paths, b, n_bloc
     check(lib().ntvs_load_paths(ctx, ctypes.byref(st)), "ntvs_load_paths")
 
 
+def ntvs_load_histories(ctx: int, nx: int, ny: int, nz: int, voxel, hist, b, n_blocks: int = 1, block_ptr=None,
+                        n_seg: int = 16, min_len: float = 1e-4) -> None:
+    """hist: float32 [M, 12] (P_in, P_out, d_in, d_out), b: float32 [M]; numpy (host) or CUDA tensors."""
+    hp, kind = _ptr_kind(hist)
+    bp_, kb = _ptr_kind(b)
+    if kind != kb:
+        raise ValueError("hist and b must both be host arrays or both device tensors")
+    bp = None
+    if block_ptr is not None:
+        bp = np.ascontiguousarray(block_ptr, dtype=np.int64)
+        n_blocks = bp.size - 1
+    dx, dy, dz = voxel
+    st = _ffi.ntvs_histories(nx, ny, nz, n_blocks, dx, dy, dz, hist.shape[0], hp, bp_,
+                             None if bp is None else bp.ctypes.data, n_seg, kind, min_len)
+    check(lib().ntvs_load_histories(ctx, ctypes.byref(st)), "ntvs_load_histories")
+
+
 def ntvs_set_params(ctx: int, lam: float, N: int, alpha: float, beta0: float = 1.0, tv_check: bool = False,
                     seed: int = 0, eps_tv: float = 1e-8, max_retries: int = 64, step_rule: int = 0,
                     gamma: float = 0.5) -> None:
@@ -419,6 +436,16 @@ class Reconstructor:
         nx, ny, nz = shape
         ntvs_load_system(self._ctx, nx, ny, nz, row_ptr, col, val, b, n_blocks, block_ptr, storage, schedule)
         self._keep = (row_ptr, col, val, b) if _is_torch(row_ptr) and row_ptr.is_cuda else ()
+        self.shape = (nx, ny, nz)
+        self.n_blocks = (len(block_ptr) - 1) if block_ptr is not None else n_blocks
+        return self
+
+    def load_histories(self, shape, voxel, hist, b, n_blocks: int = 1, block_ptr=None, n_seg: int = 16,
+                       min_len: float = 1e-4):
+        """System from per-history tracking data [M, 12] (entry/exit points and directions)."""
+        nx, ny, nz = shape
+        ntvs_load_histories(self._ctx, nx, ny, nz, voxel, hist, b, n_blocks, block_ptr, n_seg, min_len)
+        self._keep = (b,) if _is_torch(b) and b.is_cuda else ()
         self.shape = (nx, ny, nz)
         self.n_blocks = (len(block_ptr) - 1) if block_ptr is not None else n_blocks
         return self

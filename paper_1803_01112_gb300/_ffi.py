@@ -40,6 +40,14 @@ class ntvs_system(ctypes.Structure):
                 ("storage", ctypes.c_int32), ("schedule", ctypes.c_int32)]
 
 
+class ntvs_histories(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("n_blocks", ctypes.c_int32),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("n_rows", ctypes.c_int64), ("hist", ctypes.c_void_p), ("b", ctypes.c_void_p),
+                ("block_ptr", ctypes.c_void_p), ("n_seg", ctypes.c_int32), ("mem_kind", ctypes.c_int32),
+                ("min_len", ctypes.c_double)]
+
+
 class ntvs_paths(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("n_blocks", ctypes.c_int32),
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
@@ -89,6 +97,7 @@ SIGNATURES = {
     "ntvs_load_system": (ctypes.c_int, [vp, P(ntvs_system)]),
     "ntvs_set_params": (ctypes.c_int, [vp, P(ntvs_params)]),
     "ntvs_load_paths": (ctypes.c_int, [vp, P(ntvs_paths)]),
+    "ntvs_load_histories": (ctypes.c_int, [vp, P(ntvs_histories)]),
     "ntvs_set_image": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int]),
     "ntvs_get_image": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int]),
     "ntvs_run": (ctypes.c_int, [vp, ctypes.c_int]),

@@ -245,6 +245,40 @@ __global__ void __launch_bounds__(kOtfThreads) otf_drop_kernel(const float* __re
     if (threadIdx.x == 0 && tot != 0.0) atomicAdd(resid_ss, tot);
 }
 
+// History data (P_in, P_out, d_in, d_out) -> path record (P_in, P_out, A_lat, B_lat, A_z, B_z):
+// end tangents m = L d / |d| (chord direction for a zero d), deviations m - c projected on
+// the chord's in-plane normal and on z.  flags |= 32 on a non-finite history value.
+__global__ void hist_to_paths_kernel(const float* __restrict__ hist, int64_t M, float* __restrict__ rec, int* flags) {
+    int f = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        float h[12];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+            h[q] = hist[i * 12 + q];
+            if (!isfinite(h[q])) f |= 32;
+        }
+        const float c[3] = {h[3] - h[0], h[4] - h[1], h[5] - h[2]};
+        const float L = sqrtf(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+        float pr[10] = {h[0], h[1], h[2], h[3], h[4], h[5], 0.f, 0.f, 0.f, 0.f};
+        float nxv, nyv;
+        chord_normal(pr, nxv, nyv);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const float* d = h + 6 + 3 * e;
+            const float dl = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            float m[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) m[a] = dl > 0.f ? L * (d[a] / dl) : c[a];
+            const float dev[3] = {m[0] - c[0], m[1] - c[1], m[2] - c[2]};
+            pr[6 + e] = dev[0] * nxv + dev[1] * nyv;   // A_lat, B_lat
+            pr[8 + e] = dev[2];                         // A_z, B_z
+        }
+#pragma unroll
+        for (int q = 0; q < 10; ++q) rec[i * 10 + q] = pr[q];
+    }
+    if (f) atomicOr(flags, f);
+}
+
 // paths finite, n_seg sane: flags |= 32 on a non-finite path value, 16 on a non-finite b
 __global__ void otf_validate_kernel(const float* __restrict__ paths, const float* __restrict__ b, int64_t M,
                                     int* flags) {
@@ -266,6 +300,12 @@ static Grid3 make_grid(const OtfArgs& a) {
     g.ihx = 1.f / g.hx; g.ihy = 1.f / g.hy; g.ihz = 1.f / g.hz;
     g.ox = (float)(-0.5 * a.nx * a.dx); g.oy = (float)(-0.5 * a.ny * a.dy); g.oz = 0.f;
     return g;
+}
+
+cudaError_t k_hist_to_paths(const float* hist, int64_t M, float* rec, int* flags, int grid, cudaStream_t s) {
+    if (M <= 0) return cudaSuccess;
+    hist_to_paths_kernel<<<grid, 256, 0, s>>>(hist, M, rec, flags);
+    return cudaGetLastError();
 }
 
 cudaError_t k_otf_validate(const OtfArgs& a, int* flags, cudaStream_t s) {

@@ -1061,6 +1061,69 @@ int ntvs_load_paths(ntvs_ctx* c, const ntvs_paths* s) {
     return NTVS_OK;
 }
 
+int ntvs_load_histories(ntvs_ctx* c, const ntvs_histories* h) {
+    TRY(use_device(c));
+    if (!h) return fail(NTVS_ERR_ARG, "null histories");
+    if (h->n_rows < 0) return fail(NTVS_ERR_ARG, "n_rows < 0");
+    if (h->mem_kind != NTVS_MEM_HOST && h->mem_kind != NTVS_MEM_DEVICE) return fail(NTVS_ERR_ARG, "bad mem_kind");
+    const int64_t M = h->n_rows;
+    if (M > 0 && (!h->hist || !h->b)) return fail(NTVS_ERR_ARG, "null hist or b");
+    cudaStream_t st = c->stream;
+    // device copies the context will own: the converted records and, for host input, b
+    float* rec = nullptr;
+    float* bdev = nullptr;
+    float* hdev = nullptr;
+    auto release = [&]() { dev_free(rec); dev_free(bdev); dev_free(hdev); };
+    int rc = dev_alloc(&rec, sizeof(float) * 10 * (size_t)std::max<int64_t>(M, 1), "path records");
+    const float* src = h->hist;
+    const float* bsrc = h->b;
+    if (rc == NTVS_OK && h->mem_kind == NTVS_MEM_HOST) {
+        rc = dev_alloc(&hdev, sizeof(float) * 12 * (size_t)std::max<int64_t>(M, 1), "histories");
+        if (rc == NTVS_OK) rc = dev_alloc(&bdev, sizeof(float) * (size_t)std::max<int64_t>(M, 1), "b");
+        if (rc == NTVS_OK && M > 0) {
+            cudaError_t e = cudaMemcpyAsync(hdev, h->hist, sizeof(float) * 12 * (size_t)M, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(bdev, h->b, sizeof(float) * (size_t)M, cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) rc = fail(NTVS_ERR_CUDA, cuda_msg("history copy", e));
+        }
+        src = hdev;
+        bsrc = bdev;
+    }
+    if (rc == NTVS_OK) {
+        cudaError_t e = cudaMemsetAsync(c->dflags, 0, sizeof(int), st);
+        if (e == cudaSuccess) e = k_hist_to_paths(src, M, rec, c->dflags, c->sms * 8, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->hint, c->dflags, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = fail(NTVS_ERR_CUDA, cuda_msg("history conversion", e));
+        else if (c->hint[0]) rc = fail(NTVS_ERR_CSR, "non-finite history value");
+    }
+    dev_free(hdev);
+    hdev = nullptr;
+    if (rc != NTVS_OK) {
+        release();
+        return rc;
+    }
+    ntvs_paths p;
+    p.nx = h->nx; p.ny = h->ny; p.nz = h->nz;
+    p.n_blocks = h->n_blocks;
+    p.dx = h->dx; p.dy = h->dy; p.dz = h->dz;
+    p.n_rows = M;
+    p.paths = rec;
+    p.b = bsrc;
+    p.block_ptr = h->block_ptr;
+    p.n_seg = h->n_seg;
+    p.mem_kind = NTVS_MEM_DEVICE;
+    p.min_len = h->min_len;
+    rc = ntvs_load_paths(c, &p);
+    if (rc != NTVS_OK) {
+        release();
+        return rc;
+    }
+    c->own_paths = true;          // the records are the context's
+    if (bdev) c->own_b = true;    // and so is the copy of host b
+    return NTVS_OK;
+}
+
 int ntvs_set_params(ntvs_ctx* c, const ntvs_params* p) {
     if (!c || !p) return fail(NTVS_ERR_ARG, "null argument");
     if (p->N < 0) return fail(NTVS_ERR_ARG, "N must be >= 0");

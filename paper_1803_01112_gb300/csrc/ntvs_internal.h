@@ -178,6 +178,9 @@ struct OtfArgs {
     int grid;
 };
 cudaError_t k_otf_validate(const OtfArgs& a, int* flags, cudaStream_t s);
+// history data [M][12] (P_in, P_out, d_in, d_out) -> path records [M][10]; flags |= 32 on a
+// non-finite value
+cudaError_t k_hist_to_paths(const float* hist, int64_t M, float* rec, int* flags, int grid, cudaStream_t s);
 // inv_norm2 of rows [r0, r1) and the block's hit counts cnt (+= 1 per distinct voxel)
 cudaError_t k_otf_prep(const OtfArgs& a, int64_t r0, int64_t r1, float* inv_norm2, int32_t* cnt, cudaStream_t s);
 cudaError_t k_otf_drop(const OtfArgs& a, int64_t r0, int64_t r1, const float* inv_norm2, const float* x, float* delta,

@@ -103,3 +103,120 @@ def test_onthefly_rejects_bad_paths():
             r.load_paths((16, 16, 2), (spec.dx, spec.dy, spec.dz), pr.paths, pr.b.astype(np.float32), n_seg=0)
     finally:
         r.close()
+
+
+def _normal(c):
+    """In-plane unit normal (-c_y, c_x, 0) of each chord; (1, 0, 0) for a vertical chord."""
+    l = np.hypot(c[:, 0], c[:, 1])
+    n = np.zeros_like(c)
+    ok = l > 0
+    n[ok, 0] = -c[ok, 1] / l[ok]
+    n[ok, 1] = c[ok, 0] / l[ok]
+    n[~ok, 0] = 1.0
+    return n
+
+
+def _histories_from_records(paths):
+    """Tracking data of the generator's curves: entry and exit points and the curve's
+    tangents at both ends, c + A n + A_z e_z and c + B n + B_z e_z (as directions)."""
+    p = paths.astype(np.float64)
+    c = p[:, 3:6] - p[:, 0:3]
+    n = _normal(c)
+    ez = np.array([0.0, 0.0, 1.0])
+    d_in = c + p[:, 6:7] * n + p[:, 8:9] * ez
+    d_out = c + p[:, 7:8] * n + p[:, 9:10] * ez
+    return np.concatenate([p[:, 0:6], d_in, d_out], axis=1).astype(np.float32)
+
+
+def _records_from_histories(hist):
+    """The conversion ntvs_load_histories documents, restated in numpy (FP64)."""
+    h = hist.astype(np.float64)
+    c = h[:, 3:6] - h[:, 0:3]
+    L = np.linalg.norm(c, axis=1, keepdims=True)
+    n = _normal(c)
+    rec = np.zeros((h.shape[0], 10))
+    rec[:, 0:6] = h[:, 0:6]
+    for e, d in enumerate((h[:, 6:9], h[:, 9:12])):
+        dl = np.linalg.norm(d, axis=1, keepdims=True)
+        m = np.where(dl > 0, L * d / np.where(dl > 0, dl, 1.0), c)
+        dev = m - c
+        rec[:, 6 + e] = np.sum(dev * n, axis=1)
+        rec[:, 8 + e] = dev[:, 2]
+    return rec.astype(np.float32)
+
+
+def _sweep(ntvs, loader, x0):
+    r = ntvs.Reconstructor(0)
+    try:
+        loader(r)
+        r.set_params(lam=0.9, N=0, alpha=0.5)
+        r.set_image(x0)
+        r.drop_sweep()
+        return r.get_image(), r.stats()
+    finally:
+        r.close()
+
+
+@pytest.mark.parametrize("device", [False, True])
+def test_histories_equal_their_path_records(device):
+    """ntvs_load_histories traces the same rows as ntvs_load_paths on the records that its
+    documented conversion gives (host and device input)."""
+    ntvs = ntvs_module()
+    spec = synth.spec_scaled_3d(nx=40, ny=36, nz=4, n_hist=20_000, n_angles=40, n_blocks=4, seed=44)
+    pr = synth.generate_paths(spec)
+    hist = _histories_from_records(pr.paths)
+    rec = _records_from_histories(hist)
+    b = pr.b.astype(np.float32)
+    shape, vox = (spec.nx, spec.ny, spec.nz), (spec.dx, spec.dy, spec.dz)
+    x0 = 0.9 * pr.xstar + 0.05
+    if device:
+        import torch
+        h_in, b_in = torch.from_numpy(hist).cuda(), torch.from_numpy(b).cuda()
+    else:
+        h_in, b_in = hist, b
+    got, st = _sweep(ntvs, lambda r: r.load_histories(shape, vox, h_in, b_in, n_blocks=4, n_seg=spec.n_seg,
+                                                      min_len=spec.min_len), x0)
+    want, _ = _sweep(ntvs, lambda r: r.load_paths(shape, vox, rec, b, n_blocks=4, n_seg=spec.n_seg,
+                                                  min_len=spec.min_len), x0)
+    assert st["drop_schedule"] == 4
+    assert rel_l2(got, want) <= 1e-6
+    # the end tangents of the generator's curves differ from L d only in length, so the
+    # converted curves stay within tens of micrometres of the generator's
+    assert np.max(np.abs(rec[:, 6:] - pr.paths[:, 6:])) <= 0.05
+
+
+def test_straight_histories_have_no_offsets():
+    ntvs = ntvs_module()
+    spec = synth.spec_scaled_3d(nx=24, ny=24, nz=2, n_hist=4000, n_angles=12, n_blocks=2, seed=45, curved=False)
+    pr = synth.generate_paths(spec)
+    p = pr.paths.astype(np.float64)
+    c = p[:, 3:6] - p[:, 0:3]
+    hist = np.concatenate([p[:, 0:6], c, 2.5 * c], axis=1).astype(np.float32)   # lengths do not matter
+    zero = hist.copy()
+    zero[:, 6:] = 0.0                                                              # zero = chord direction
+    rec = pr.paths.copy()
+    rec[:, 6:] = 0.0
+    b = pr.b.astype(np.float32)
+    shape, vox = (spec.nx, spec.ny, spec.nz), (spec.dx, spec.dy, spec.dz)
+    x0 = pr.xstar + 0.1
+    want, _ = _sweep(ntvs, lambda r: r.load_paths(shape, vox, rec, b, n_blocks=2), x0)
+    for h in (hist, zero):
+        got, _ = _sweep(ntvs, lambda r: r.load_histories(shape, vox, h, b, n_blocks=2), x0)
+        assert rel_l2(got, want) <= 1e-6
+
+
+def test_histories_reject_bad_input():
+    ntvs = ntvs_module()
+    spec = synth.spec_scaled_3d(nx=16, ny=16, nz=2, n_hist=200, n_angles=8, n_blocks=1)
+    pr = synth.generate_paths(spec)
+    hist = _histories_from_records(pr.paths)
+    hist[5, 10] = np.inf
+    r = ntvs.Reconstructor(0)
+    try:
+        with pytest.raises(ntvs.NtvsError, match="non-finite history"):
+            r.load_histories((16, 16, 2), (spec.dx, spec.dy, spec.dz), hist, pr.b.astype(np.float32))
+        with pytest.raises(ntvs.NtvsError):
+            r.load_histories((16, 16, 2), (spec.dx, spec.dy, spec.dz), _histories_from_records(pr.paths),
+                             pr.b.astype(np.float32), n_seg=65)
+    finally:
+        r.close()
