@@ -27,7 +27,7 @@ namespace ntvs {
 namespace {
 
 constexpr int kTvItem = 2048;     // voxels per TV item (256 threads x 8)
-constexpr int kDropItem = 1024;   // rows per DROP item
+constexpr int kDropItem = 256;    // rows per DROP item (enough CTAs to fill every SM)
 
 struct MemberDev {
     const int64_t* row_ptr;
@@ -145,8 +145,10 @@ __global__ void __launch_bounds__(256) tvb_apply_kernel(const MemberDev* __restr
     }
 }
 
-// DROP block b of every member with b < B_r: a group of LPR lanes per row, global reductions
-template <int LPR>
+// DROP block b of every member with b < B_r: a group of LPR lanes per row; the first
+// CH * LPR entries of a row stay in registers between the dot product and the scatter
+// (the matrix is read once), longer rows re-read their tail; global reductions.
+template <int LPR, int CH>
 __global__ void __launch_bounds__(256) dropb_block_kernel(const MemberDev* __restrict__ mem,
                                                           const Item* __restrict__ items) {
     const Item it = items[blockIdx.x];
@@ -159,18 +161,33 @@ __global__ void __launch_bounds__(256) dropb_block_kernel(const MemberDev* __res
         const int64_t i = base + lane / LPR;
         const bool valid = i < it.i1;
         int64_t p0 = 0, p1 = 0;
-        if (valid) { p0 = m.row_ptr[i]; p1 = m.row_ptr[i + 1]; }
+        if (valid) { p0 = __ldg(m.row_ptr + i); p1 = __ldg(m.row_ptr + i + 1); }
+        int32_t c[CH];
+        float a[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            const int64_t q = p0 + (int64_t)u * LPR + sub;
+            if (q < p1) { c[u] = __ldcs(m.col + q); a[u] = __ldcs(m.val + q); }
+            else { c[u] = -1; a[u] = 0.f; }
+        }
         float acc = 0.f;
-        for (int64_t p = p0 + sub; p < p1; p += LPR) acc += m.val[p] * __ldg(m.x32 + m.col[p]);
+#pragma unroll
+        for (int u = 0; u < CH; ++u)
+            if (c[u] >= 0) acc += a[u] * __ldg(m.x32 + c[u]);
+        const int64_t tail0 = p0 + (int64_t)CH * LPR;
+        for (int64_t p = tail0 + sub; p < p1; p += LPR) acc += m.val[p] * __ldg(m.x32 + m.col[p]);
 #pragma unroll
         for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         float r = 0.f;
         if (valid) {
-            const float res = m.b[i] - acc;
-            r = m.lambda * res * m.inv_norm2[i];
+            const float res = __ldg(m.b + i) - acc;
+            r = m.lambda * res * __ldg(m.inv_norm2 + i);
             if (sub == 0) ss += (double)res * (double)res;
         }
-        for (int64_t p = p0 + sub; p < p1; p += LPR) atomicAdd(m.delta + m.col[p], r * m.val[p]);
+#pragma unroll
+        for (int u = 0; u < CH; ++u)
+            if (c[u] >= 0) atomicAdd(m.delta + c[u], r * a[u]);
+        for (int64_t p = tail0 + sub; p < p1; p += LPR) atomicAdd(m.delta + m.col[p], r * m.val[p]);
     }
     __shared__ double sh[32];
     const double tot = block_sum(ss, sh);
@@ -294,6 +311,15 @@ struct ntvs_batch {
 
 namespace {
 
+// lanes per row 8 / 16 / 32 with 16 / 10 / 6 register steps (128 / 160 / 192 entries)
+void launch_dropb(int lpr, int n_items, const MemberDev* mem, const Item* items, cudaStream_t s) {
+    switch (lpr) {
+        case 8: dropb_block_kernel<8, 16><<<n_items, 256, 0, s>>>(mem, items); break;
+        case 16: dropb_block_kernel<16, 10><<<n_items, 256, 0, s>>>(mem, items); break;
+        default: dropb_block_kernel<32, 6><<<n_items, 256, 0, s>>>(mem, items); break;
+    }
+}
+
 int launch_cycle(ntvs_batch* bt, const double* beta_src) {
     cudaStream_t s = bt->stream;
     const int R = (int)bt->m.size();
@@ -305,13 +331,7 @@ int launch_cycle(ntvs_batch* bt, const double* beta_src) {
     }
     for (int b = 0; b < bt->B_max; ++b) {
         zero_resid_kernel<<<(R + 127) / 128, 128, 0, s>>>(bt->dmem, R, b);
-        if (bt->n_drop_items[b] > 0) {
-            switch (bt->lpr) {
-                case 8: dropb_block_kernel<8><<<bt->n_drop_items[b], 256, 0, s>>>(bt->dmem, bt->drop_items[b]); break;
-                case 16: dropb_block_kernel<16><<<bt->n_drop_items[b], 256, 0, s>>>(bt->dmem, bt->drop_items[b]); break;
-                default: dropb_block_kernel<32><<<bt->n_drop_items[b], 256, 0, s>>>(bt->dmem, bt->drop_items[b]); break;
-            }
-        }
+        if (bt->n_drop_items[b] > 0) launch_dropb(bt->lpr, bt->n_drop_items[b], bt->dmem, bt->drop_items[b], s);
         dropb_apply_kernel<<<bt->n_tv_items, 256, 0, s>>>(bt->dmem, bt->tv_items, b);
     }
     tvb_value_kernel<<<bt->n_tv_items, 256, 0, s>>>(bt->dmem, bt->tv_items, bt->kk, bt->partials, bt->tickets);
@@ -562,11 +582,7 @@ int ntvs_batch_finalize(ntvs_batch* bt, int max_cycles) {
             float total = 0.f;
             for (int rep = 0; rep < 2; ++rep) {
                 BCUDA(cudaEventRecord(e0, bt->stream));
-                switch (lpr) {
-                    case 8: dropb_block_kernel<8><<<bt->n_drop_items[0], 256, 0, bt->stream>>>(bt->dmem, bt->drop_items[0]); break;
-                    case 16: dropb_block_kernel<16><<<bt->n_drop_items[0], 256, 0, bt->stream>>>(bt->dmem, bt->drop_items[0]); break;
-                    default: dropb_block_kernel<32><<<bt->n_drop_items[0], 256, 0, bt->stream>>>(bt->dmem, bt->drop_items[0]); break;
-                }
+                launch_dropb(lpr, bt->n_drop_items[0], bt->dmem, bt->drop_items[0], bt->stream);
                 BCUDA(cudaEventRecord(e1, bt->stream));
                 BCUDA(cudaEventSynchronize(e1));
                 float ms = 0.f;
