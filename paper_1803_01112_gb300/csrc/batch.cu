@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "voxel_coords.cuh"
 #include "ntvs.h"
 #include "step_rule.h"
 
@@ -93,9 +94,8 @@ __global__ void __launch_bounds__(256) tvb_grad_kernel(const MemberDev* __restri
     const float eps = m.eps;
     double acc = 0.0;
     for (int64_t p = it.i0 + threadIdx.x; p < it.i1; p += blockDim.x) {
-        const int ix = (int)(p % nx);
-        const int64_t t = p / nx;
-        const int iy = (int)(t % ny), iz = (int)(t / ny);
+        int ix, iy, iz;
+        voxel_coords(p, nx, ny, ix, iy, iz);
         const bool hx = ix + 1 < nx, hy = iy + 1 < ny, hz = iz + 1 < nz;
         const double xc = x[p];
         const float dx = (float)(hx ? x[p + 1] - xc : 0.0), dy = (float)(hy ? x[p + nx] - xc : 0.0),
@@ -219,9 +219,8 @@ __global__ void __launch_bounds__(256) tvb_value_kernel(const MemberDev* __restr
     const int64_t sxy = (int64_t)nx * ny;
     double acc = 0.0;
     for (int64_t p = it.i0 + threadIdx.x; p < it.i1; p += blockDim.x) {
-        const int ix = (int)(p % nx);
-        const int64_t t = p / nx;
-        const int iy = (int)(t % ny), iz = (int)(t / ny);
+        int ix, iy, iz;
+        voxel_coords(p, nx, ny, ix, iy, iz);
         const double xc = m.x[p];
         const double ex = (ix + 1 < nx) ? m.x[p + 1] - xc : 0.0, ey = (iy + 1 < ny) ? m.x[p + nx] - xc : 0.0,
                      ez = (iz + 1 < nz) ? m.x[p + sxy] - xc : 0.0;

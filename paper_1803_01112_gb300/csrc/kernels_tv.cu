@@ -4,6 +4,7 @@
 // index.  The image is tiny next to the system matrix (V floats), so these kernels live
 // in L2; every reduction is FP64 with a fixed reduction order (deterministic).
 #include "common.cuh"
+#include "voxel_coords.cuh"
 
 namespace ntvs {
 
@@ -26,9 +27,8 @@ tv_grad_kernel(const double* __restrict__ x, T* __restrict__ g, int nx, int ny, 
     const int64_t sxy = (int64_t)nx * ny, V = sxy * nz;
     double acc[2] = {0.0, 0.0};
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < V; p += (int64_t)gridDim.x * blockDim.x) {
-        const int ix = (int)(p % nx);
-        const int64_t t = p / nx;
-        const int iy = (int)(t % ny), iz = (int)(t / ny);
+        int ix, iy, iz;
+        voxel_coords(p, nx, ny, ix, iy, iz);
         const bool hx = ix + 1 < nx, hy = iy + 1 < ny, hz = iz + 1 < nz;
         const double xc = __ldg(x + p);
         const double ex = hx ? __ldg(x + p + 1) - xc : 0.0;
@@ -78,9 +78,8 @@ tv_value_kernel(const double* __restrict__ x, const T* __restrict__ g, const dou
     const double sc = g ? step_scale(beta, gnorm2) : 0.0;
     double acc[1] = {0.0};
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < V; p += (int64_t)gridDim.x * blockDim.x) {
-        const int ix = (int)(p % nx);
-        const int64_t t = p / nx;
-        const int iy = (int)(t % ny), iz = (int)(t / ny);
+        int ix, iy, iz;
+        voxel_coords(p, nx, ny, ix, iy, iz);
         auto zat = [&](int64_t q) -> double {
             return g ? perturbed(__ldg(x + q), sc, (double)__ldg(g + q)) : __ldg(x + q);
         };

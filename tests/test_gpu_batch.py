@@ -88,3 +88,47 @@ def test_batch_rejects_what_it_does_not_run():
             bt.run(3)
     finally:
         bt.close()
+
+
+def _shuffle_rows_within_blocks(s, seed):
+    """The same system with the rows of every block in random order (block-DROP does not
+    depend on the order inside a block), so its rows no longer come in runs of one slice."""
+    rng = np.random.default_rng(seed)
+    bp = s.block_ptr()
+    order = np.concatenate([bp[t] + rng.permutation(bp[t + 1] - bp[t]) for t in range(len(bp) - 1)])
+    lens = np.diff(s.row_ptr)[order]
+    rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    idx = np.concatenate([np.arange(s.row_ptr[i], s.row_ptr[i + 1]) for i in order]).astype(np.int64)
+    return rp, s.col[idx], s.val[idx], s.b[order], bp
+
+
+def test_batch_row_order_and_large_slices_match_oracle():
+    """Members with rows that run slice by slice, with rows in random order inside each
+    block, and with a 160x160 slice, in one batch: every member equals its oracle run."""
+    ntvs = ntvs_module()
+    K = 3
+    a = synth.generate(synth.spec_scaled_3d(nx=40, ny=40, nz=3, n_hist=12_000, n_angles=24, n_blocks=3, seed=50))
+    b = synth.generate(synth.spec_scaled_3d(nx=36, ny=32, nz=2, n_hist=9_000, n_angles=24, n_blocks=2, seed=51))
+    c = synth.generate(synth.spec_scaled_3d(nx=160, ny=160, nz=1, n_hist=6_000, n_angles=12, n_blocks=2, seed=52))
+    rp_b, col_b, val_b, b_b, bp_b = _shuffle_rows_within_blocks(b, 3)
+    cases = [((40, 40, 3), a.row_ptr, a.col, a.val, a.b, a.block_ptr(), a.xbar),
+             ((36, 32, 2), rp_b, col_b, val_b, b_b, bp_b, b.xbar),
+             ((160, 160, 1), c.row_ptr, c.col, c.val, c.b, c.block_ptr(), c.xbar)]
+    prms = [oracle.Params(lam=0.5, N=2, alpha=0.75, seed=60 + k, eps_tv=1e-4) for k in range(3)]
+    bt = ntvs.Batch(0)
+    try:
+        for (shape, rp, col, val, bb, bp, x0), prm in zip(cases, prms):
+            bt.add(shape, rp, col, val.astype(np.float32), bb.astype(np.float32), len(bp) - 1,
+                   ntvs.Params(lam=prm.lam, N=prm.N, alpha=prm.alpha, seed=prm.seed, eps_tv=prm.eps_tv), x0,
+                   block_ptr=bp)
+        bt.finalize(max_cycles=4)
+        bt.run(K)
+        imgs = [bt.get_image(i) for i in range(3)]
+        # per cycle: 2 steps x (grad, apply) + phi + k, and per block step reset, DROP, apply
+        assert bt.stats()["kernels_per_cycle"] == 2 * 2 + 2 + 3 * 3
+    finally:
+        bt.close()
+    for (shape, rp, col, val, bb, bp, x0), prm, img in zip(cases, prms, imgs):
+        v64, b64 = val.astype(np.float32).astype(np.float64), bb.astype(np.float32).astype(np.float64)
+        ref = oracle.ntvs(rp, col, v64, b64, bp, shape, prm, K, x0)
+        assert rel_l2(img, ref.x) <= 1e-5
