@@ -38,7 +38,8 @@ struct MemberDev {
     const float* inv_norm2;
     const float* inv_s;   // [B][V]
     double* x;
-    float* x32;
+    float* x32;           // fl32(x), canonical order
+    float* xl;            // fl32(x - x32): the TV stencil differences are formed from both
     float* delta;
     float* g;
     double* resid;        // [B]
@@ -90,36 +91,35 @@ __global__ void __launch_bounds__(256) tvb_grad_kernel(const MemberDev* __restri
     if (n_step >= m.N) return;   // uniform over the CTA: no reduction for this member
     const int nx = m.nx, ny = m.ny, nz = m.nz;
     const int64_t sxy = (int64_t)nx * ny;
-    const double* x = m.x;
+    const float* xh = m.x32;
+    const float* xl = m.xl;
     const float eps = m.eps;
+    auto dif = [&](int64_t a, int64_t b) -> float {
+        return (__ldg(xh + a) - __ldg(xh + b)) + (__ldg(xl + a) - __ldg(xl + b));
+    };
     double acc = 0.0;
     for (int64_t p = it.i0 + threadIdx.x; p < it.i1; p += blockDim.x) {
         int ix, iy, iz;
         voxel_coords(p, nx, ny, ix, iy, iz);
         const bool hx = ix + 1 < nx, hy = iy + 1 < ny, hz = iz + 1 < nz;
-        const double xc = x[p];
-        const float dx = (float)(hx ? x[p + 1] - xc : 0.0), dy = (float)(hy ? x[p + nx] - xc : 0.0),
-                    dz = (float)(hz ? x[p + sxy] - xc : 0.0);
+        const float dx = hx ? dif(p + 1, p) : 0.f, dy = hy ? dif(p + nx, p) : 0.f, dz = hz ? dif(p + sxy, p) : 0.f;
         const float D = sqrtf(eps + (dx * dx + dy * dy + dz * dz));
         float gq = (D > 0.f) ? -(dx + dy + dz) / D : 0.f;
         if (ix > 0) {
-            const double xm = x[p - 1];
-            const float a = (float)(xc - xm), bb = hy ? (float)(x[p - 1 + nx] - xm) : 0.f,
-                        c = hz ? (float)(x[p - 1 + sxy] - xm) : 0.f;
+            const int64_t q = p - 1;
+            const float a = dif(p, q), bb = hy ? dif(q + nx, q) : 0.f, c = hz ? dif(q + sxy, q) : 0.f;
             const float Dm = sqrtf(eps + (a * a + bb * bb + c * c));
             if (Dm > 0.f) gq += a / Dm;
         }
         if (iy > 0) {
-            const double xm = x[p - nx];
-            const float a = (float)(xc - xm), bb = hx ? (float)(x[p - nx + 1] - xm) : 0.f,
-                        c = hz ? (float)(x[p - nx + sxy] - xm) : 0.f;
+            const int64_t q = p - nx;
+            const float a = dif(p, q), bb = hx ? dif(q + 1, q) : 0.f, c = hz ? dif(q + sxy, q) : 0.f;
             const float Dm = sqrtf(eps + (a * a + bb * bb + c * c));
             if (Dm > 0.f) gq += a / Dm;
         }
         if (iz > 0) {
-            const double xm = x[p - sxy];
-            const float a = (float)(xc - xm), bb = hx ? (float)(x[p - sxy + 1] - xm) : 0.f,
-                        c = hy ? (float)(x[p - sxy + nx] - xm) : 0.f;
+            const int64_t q = p - sxy;
+            const float a = dif(p, q), bb = hx ? dif(q + 1, q) : 0.f, c = hy ? dif(q + nx, q) : 0.f;
             const float Dm = sqrtf(eps + (a * a + bb * bb + c * c));
             if (Dm > 0.f) gq += a / Dm;
         }
@@ -141,7 +141,9 @@ __global__ void __launch_bounds__(256) tvb_apply_kernel(const MemberDev* __restr
     for (int64_t p = it.i0 + threadIdx.x; p < it.i1; p += blockDim.x) {
         const double z = perturbed(m.x[p], sc, (double)m.g[p]);
         m.x[p] = z;
-        m.x32[p] = (float)z;
+        const float h = (float)z;
+        m.x32[p] = h;
+        m.xl[p] = (float)(z - (double)h);
     }
 }
 
@@ -201,10 +203,13 @@ __global__ void __launch_bounds__(256) dropb_apply_kernel(const MemberDev* __res
     const MemberDev m = mem[it.member];
     if (b >= m.B) return;
     const float* inv_s = m.inv_s + (int64_t)b * m.V;
+    const bool last = b == m.B - 1;   // xl is read by the next gradient only: written after the last block
     for (int64_t p = it.i0 + threadIdx.x; p < it.i1; p += blockDim.x) {
         const double v = m.x[p] + (double)m.delta[p] * (double)inv_s[p];
         m.x[p] = v;
-        m.x32[p] = (float)v;
+        const float h = (float)v;
+        m.x32[p] = h;
+        if (last) m.xl[p] = (float)(v - (double)h);
         m.delta[p] = 0.f;
     }
 }
@@ -485,8 +490,11 @@ int ntvs_batch_add(ntvs_batch* bt, const ntvs_system* s, const ntvs_params* p, c
             for (int64_t j = 0; j < V; ++j) x[j] = t[j];
         }
     }
-    std::vector<float> x32((size_t)V);
-    for (int64_t j = 0; j < V; ++j) x32[j] = (float)x[j];
+    std::vector<float> x32((size_t)V), xl((size_t)V);
+    for (int64_t j = 0; j < V; ++j) {
+        x32[j] = (float)x[j];
+        xl[j] = (float)(x[j] - (double)x32[j]);
+    }
     int rc = NTVS_OK;
     if ((rc = up((void**)&d.row_ptr, rp.data(), sizeof(int64_t) * rp.size(), "row_ptr")) ||
         (rc = up((void**)&d.col, col.data(), sizeof(int32_t) * col.size(), "col")) ||
@@ -496,6 +504,7 @@ int ntvs_batch_add(ntvs_batch* bt, const ntvs_system* s, const ntvs_params* p, c
         (rc = up((void**)&d.inv_s, inv_s.data(), sizeof(float) * inv_s.size(), "inv_s")) ||
         (rc = up((void**)&d.x, x.data(), sizeof(double) * V, "x")) ||
         (rc = up((void**)&d.x32, x32.data(), sizeof(float) * V, "x32")) ||
+        (rc = up((void**)&d.xl, xl.data(), sizeof(float) * V, "xl")) ||
         (rc = up((void**)&d.delta, nullptr, sizeof(float) * V, "delta")) ||
         (rc = up((void**)&d.g, nullptr, sizeof(float) * V, "g")) ||
         (rc = up((void**)&d.resid, nullptr, sizeof(double) * std::max(B, 1), "resid"))) {

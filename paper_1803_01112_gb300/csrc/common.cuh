@@ -38,6 +38,16 @@ __device__ __forceinline__ int64_t vox_internal(const VoxMap& m, int64_t j) {
                      ((iy & (uint32_t)(m.ty - 1)) << m.ltx) + (ix & (uint32_t)(m.tx - 1)));
 }
 
+// the FP32 copies of master value v of canonical voxel j
+__device__ __forceinline__ void store_copies(const ImgCopies& c, int64_t j, double v) {
+    if (c.x32) c.x32[vox_internal(c.m, j)] = (float)v;
+    if (c.xh) {
+        const float h = (float)v;
+        c.xh[j] = h;
+        c.xl[j] = (float)(v - (double)h);
+    }
+}
+
 // inclusive prefix sum over the 32 lanes of a warp
 __device__ __forceinline__ int warp_inclusive_scan(int v) {
     const int lane = threadIdx.x & 31;

@@ -316,13 +316,13 @@ drop_block_d16_kernel(const int64_t* __restrict__ row_ptr, Delta16 d16, const V*
 }
 
 template <typename T>
-__global__ void drop_apply_kernel(double* __restrict__ x, float* __restrict__ x32, T* __restrict__ delta,
-                                  const T* __restrict__ inv_s, int64_t V, VoxMap m) {
+__global__ void drop_apply_kernel(double* __restrict__ x, ImgCopies c, T* __restrict__ delta,
+                                  const T* __restrict__ inv_s, int64_t V) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < V; j += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = vox_internal(m, j);
+        const int64_t p = vox_internal(c.m, j);
         const double v = x[j] + (double)delta[p] * (double)__ldg(inv_s + p);
         x[j] = v;
-        if (x32) x32[p] = (float)v;
+        store_copies(c, j, v);
         delta[p] = (T)0;
     }
 }
@@ -414,11 +414,10 @@ cudaError_t k_drop_block(const DropArgs& a, cudaStream_t s) {
     }
 }
 
-cudaError_t k_drop_apply(int cdt, double* x, float* x32, void* delta, const void* inv_s, int64_t V, VoxMap m,
-                         int grid, cudaStream_t s) {
-    if (cdt == F64)
-        drop_apply_kernel<double><<<grid, 256, 0, s>>>(x, x32, (double*)delta, (const double*)inv_s, V, m);
-    else drop_apply_kernel<float><<<grid, 256, 0, s>>>(x, x32, (float*)delta, (const float*)inv_s, V, m);
+cudaError_t k_drop_apply(int cdt, double* x, ImgCopies c, void* delta, const void* inv_s, int64_t V, int grid,
+                         cudaStream_t s) {
+    if (cdt == F64) drop_apply_kernel<double><<<grid, 256, 0, s>>>(x, c, (double*)delta, (const double*)inv_s, V);
+    else drop_apply_kernel<float><<<grid, 256, 0, s>>>(x, c, (float*)delta, (const float*)inv_s, V);
     return cudaGetLastError();
 }
 

@@ -69,6 +69,49 @@ tv_grad_kernel(const double* __restrict__ x, T* __restrict__ g, int nx, int ny, 
     grid_reduce<2>(acc, partials, ticket, outs);
 }
 
+// The same gradient on the FP32 path from the split copies xh + xl of the master image:
+// every neighbour difference is (xh_a - xh_b) + (xl_a - xl_b) in FP32, so the stencil runs
+// without FP64 arithmetic (only ||g||^2 is accumulated in FP64).
+__global__ void __launch_bounds__(kRedThreads)
+tv_grad_split_kernel(const float* __restrict__ xh, const float* __restrict__ xl, float* __restrict__ g, int nx,
+                     int ny, int nz, float eps, double* partials, unsigned* ticket, double* gnorm2) {
+    const int64_t sxy = (int64_t)nx * ny, V = sxy * nz;
+    auto dif = [&](int64_t a, int64_t b) -> float {
+        return (__ldg(xh + a) - __ldg(xh + b)) + (__ldg(xl + a) - __ldg(xl + b));
+    };
+    double acc[1] = {0.0};
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < V; p += (int64_t)gridDim.x * blockDim.x) {
+        int ix, iy, iz;
+        voxel_coords(p, nx, ny, ix, iy, iz);
+        const bool hx = ix + 1 < nx, hy = iy + 1 < ny, hz = iz + 1 < nz;
+        const float dx = hx ? dif(p + 1, p) : 0.f, dy = hy ? dif(p + nx, p) : 0.f, dz = hz ? dif(p + sxy, p) : 0.f;
+        const float D = sqrtf(eps + (dx * dx + dy * dy + dz * dz));
+        float gq = (D > 0.f) ? -(dx + dy + dz) / D : 0.f;
+        if (ix > 0) {
+            const int64_t q = p - 1;
+            const float a = dif(p, q), b = hy ? dif(q + nx, q) : 0.f, c = hz ? dif(q + sxy, q) : 0.f;
+            const float Dm = sqrtf(eps + (a * a + b * b + c * c));
+            if (Dm > 0.f) gq += a / Dm;
+        }
+        if (iy > 0) {
+            const int64_t q = p - nx;
+            const float a = dif(p, q), b = hx ? dif(q + 1, q) : 0.f, c = hz ? dif(q + sxy, q) : 0.f;
+            const float Dm = sqrtf(eps + (a * a + b * b + c * c));
+            if (Dm > 0.f) gq += a / Dm;
+        }
+        if (iz > 0) {
+            const int64_t q = p - sxy;
+            const float a = dif(p, q), b = hx ? dif(q + 1, q) : 0.f, c = hy ? dif(q + nx, q) : 0.f;
+            const float Dm = sqrtf(eps + (a * a + b * b + c * c));
+            if (Dm > 0.f) gq += a / Dm;
+        }
+        g[p] = gq;
+        acc[0] += (double)gq * (double)gq;
+    }
+    double* const outs[1] = {gnorm2};
+    grid_reduce<1>(acc, partials, ticket, outs);
+}
+
 // phi_0(z), z = x - sc*g (z = x if g is null), FP64 from the master image.
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
@@ -100,21 +143,21 @@ tv_value_kernel(const double* __restrict__ x, const T* __restrict__ g, const dou
 
 // x <- x - sc*g on the master image (and its FP32 gather copy when present)
 template <typename T>
-__global__ void tv_apply_kernel(double* __restrict__ x, float* __restrict__ x32, const T* __restrict__ g,
-                                const double* gnorm2, double beta, const int* accept, int64_t V, VoxMap m) {
+__global__ void tv_apply_kernel(double* __restrict__ x, ImgCopies c, const T* __restrict__ g, const double* gnorm2,
+                                double beta, const int* accept, int64_t V) {
     if (accept && *accept == 0) return;
     const double sc = step_scale(beta, gnorm2);
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < V; p += (int64_t)gridDim.x * blockDim.x) {
         const double z = perturbed(x[p], sc, (double)g[p]);
         x[p] = z;
-        if (x32) x32[vox_internal(m, p)] = (float)z;
+        store_copies(c, p, z);
     }
 }
 
-__global__ void x32_from_x64_kernel(const double* __restrict__ x, float* __restrict__ x32, VoxMap m) {
-    const int64_t V = (int64_t)m.nx * m.ny * m.nz;
+__global__ void x32_from_x64_kernel(const double* __restrict__ x, ImgCopies c) {
+    const int64_t V = (int64_t)c.m.nx * c.m.ny * c.m.nz;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < V; j += (int64_t)gridDim.x * blockDim.x)
-        x32[vox_internal(m, j)] = (float)x[j];
+        store_copies(c, j, x[j]);
 }
 
 static int g_sm_count = 0;
@@ -128,9 +171,12 @@ static int sm_count() {
     return g_sm_count;
 }
 
-cudaError_t k_tv_grad(int cdt, const double* x, void* g, int nx, int ny, int nz, double eps, RedScratch r,
-                      double* gnorm2, double* phi, cudaStream_t s) {
-    if (cdt == F64)
+cudaError_t k_tv_grad(int cdt, const double* x, const float* xh, const float* xl, void* g, int nx, int ny, int nz,
+                      double eps, RedScratch r, double* gnorm2, double* phi, cudaStream_t s) {
+    if (cdt == F32 && xh && xl && !phi)
+        tv_grad_split_kernel<<<r.grid, kRedThreads, 0, s>>>(xh, xl, (float*)g, nx, ny, nz, (float)eps, r.partials,
+                                                           r.ticket, gnorm2);
+    else if (cdt == F64)
         tv_grad_kernel<double><<<r.grid, kRedThreads, 0, s>>>(x, (double*)g, nx, ny, nz, eps, r.partials, r.ticket,
                                                               gnorm2, phi);
     else
@@ -150,19 +196,19 @@ cudaError_t k_tv_value(int cdt, const double* x, const void* g, const double* gn
     return cudaGetLastError();
 }
 
-cudaError_t k_tv_apply(int cdt, double* x, float* x32, const void* g, const double* gnorm2, double beta,
-                       const int* accept, int64_t V, VoxMap m, cudaStream_t s) {
+cudaError_t k_tv_apply(int cdt, double* x, ImgCopies c, const void* g, const double* gnorm2, double beta,
+                       const int* accept, int64_t V, cudaStream_t s) {
     const int grid = red_grid(V, sm_count());
     if (cdt == F64)
-        tv_apply_kernel<double><<<grid, kRedThreads, 0, s>>>(x, x32, (const double*)g, gnorm2, beta, accept, V, m);
+        tv_apply_kernel<double><<<grid, kRedThreads, 0, s>>>(x, c, (const double*)g, gnorm2, beta, accept, V);
     else
-        tv_apply_kernel<float><<<grid, kRedThreads, 0, s>>>(x, x32, (const float*)g, gnorm2, beta, accept, V, m);
+        tv_apply_kernel<float><<<grid, kRedThreads, 0, s>>>(x, c, (const float*)g, gnorm2, beta, accept, V);
     return cudaGetLastError();
 }
 
-cudaError_t k_x32_from_x64(const double* x, float* x32, VoxMap m, cudaStream_t s) {
-    const int64_t V = (int64_t)m.nx * m.ny * m.nz;
-    x32_from_x64_kernel<<<red_grid(V, sm_count()), kRedThreads, 0, s>>>(x, x32, m);
+cudaError_t k_x32_from_x64(const double* x, ImgCopies c, cudaStream_t s) {
+    const int64_t V = (int64_t)c.m.nx * c.m.ny * c.m.nz;
+    x32_from_x64_kernel<<<red_grid(V, sm_count()), kRedThreads, 0, s>>>(x, c);
     return cudaGetLastError();
 }
 

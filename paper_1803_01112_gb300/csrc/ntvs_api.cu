@@ -119,6 +119,8 @@ struct ntvs_ctx {
     // FP32-path DROP kernels (null on the FP64 path)
     double* x = nullptr;
     float* x32 = nullptr;
+    float* xh = nullptr;   // FP32 path: fl32(x) and fl32(x - xh), canonical order (TV stencil)
+    float* xl = nullptr;
     void* delta = nullptr;
     void* g = nullptr;
     RedScratch red{nullptr, nullptr, 1};
@@ -150,6 +152,12 @@ struct ntvs_ctx {
     int64_t prof_n[3] = {0, 0, 0};
 
     size_t csz() const { return dt_size(cdt); }
+    // with_split = false leaves xh/xl stale (split_stale), to be refreshed before the next
+    // gradient: DROP blocks other than the last of a sweep skip them
+    ImgCopies copies(bool with_split = true) const {
+        return ImgCopies{x32, with_split ? xh : nullptr, with_split ? xl : nullptr, vm};
+    }
+    bool split_stale = false;
 
     void free_system() {
         if (copy_stream) cudaStreamSynchronize(copy_stream);   // no copy may still target a buffer
@@ -177,6 +185,8 @@ struct ntvs_ctx {
         schedule = NTVS_SCHED_PLAIN;
         dev_free(x);
         dev_free(x32);
+        dev_free(xh);
+        dev_free(xl);
         dev_free(delta);
         dev_free(g);
         dev_free(resid);
@@ -302,8 +312,14 @@ int ensure_tvhist(ntvs_ctx* c, int64_t need) {
 
 // ---- one TV perturbation step (Appendix C inner loop) --------------------------------
 int launch_grad(ntvs_ctx* c, bool with_phi) {
+    if (c->xh && c->split_stale) {
+        CUDA_TRY(timed_launch(c, KIND_TV, [&] {
+            return k_x32_from_x64(c->x, ImgCopies{nullptr, c->xh, c->xl, c->vm}, c->stream);
+        }));
+        c->split_stale = false;
+    }
     CUDA_TRY(timed_launch(c, KIND_TV, [&] {
-        return k_tv_grad(c->cdt, c->x, c->g, c->nx, c->ny, c->nz, c->p.eps_tv, c->red, c->dscal + 0,
+        return k_tv_grad(c->cdt, c->x, c->xh, c->xl, c->g, c->nx, c->ny, c->nz, c->p.eps_tv, c->red, c->dscal + 0,
                          with_phi ? c->dscal + 1 : nullptr, c->stream);
     }));
     return NTVS_OK;
@@ -316,7 +332,7 @@ int checked_try(ntvs_ctx* c, double beta, int* acc) {
                           c->dscal + 1, c->daccept, c->stream);
     }));
     CUDA_TRY(timed_launch(c, KIND_TV, [&] {
-        return k_tv_apply(c->cdt, c->x, c->x32, c->g, c->dscal + 0, beta, c->daccept, c->V, c->vm, c->stream);
+        return k_tv_apply(c->cdt, c->x, c->copies(), c->g, c->dscal + 0, beta, c->daccept, c->V, c->stream);
     }));
     CUDA_TRY(cudaMemcpyAsync(c->hint, c->daccept, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -334,7 +350,7 @@ int perturb_steps(ntvs_ctx* c, int64_t* ell_io) {
         if (!c->p.tv_check) {
             TRY(launch_grad(c, false));
             CUDA_TRY(timed_launch(c, KIND_TV, [&] {
-                return k_tv_apply(c->cdt, c->x, c->x32, c->g, c->dscal + 0, beta, nullptr, c->V, c->vm, c->stream);
+                return k_tv_apply(c->cdt, c->x, c->copies(), c->g, c->dscal + 0, beta, nullptr, c->V, c->stream);
             }));
             ell += adv;
             tries = 1;
@@ -364,6 +380,9 @@ int perturb_steps(ntvs_ctx* c, int64_t* ell_io) {
 // ---- block-DROP ------------------------------------------------------------------------
 int drop_block(ntvs_ctx* c, int t) {
     const int64_t r0 = c->block_ptr[t], r1 = c->block_ptr[t + 1];
+    // the split copies of x are written by the last block of a sweep only (the TV gradient
+    // reads them next); after any other block they are marked stale
+    const bool split = t == c->B - 1;
     CUDA_TRY(cudaMemsetAsync(c->resid + t, 0, sizeof(double), c->stream));
     if (r1 <= r0) return NTVS_OK;
     if (c->paths_mode) {
@@ -372,10 +391,11 @@ int drop_block(ntvs_ctx* c, int t) {
                               c->resid + t, c->stream);
         }));
         CUDA_TRY(timed_launch(c, KIND_APPLY, [&] {
-            return k_drop_apply(c->cdt, c->x, c->x32, c->delta,
-                                (const char*)c->inv_s + (size_t)t * c->vm.vint * c->csz(), c->V, c->vm,
-                                c->apply_grid, c->stream);
+            return k_drop_apply(c->cdt, c->x, c->copies(split), c->delta,
+                                (const char*)c->inv_s + (size_t)t * c->vm.vint * c->csz(), c->V, c->apply_grid,
+                                c->stream);
         }));
+        c->split_stale = !split;
         return NTVS_OK;
     }
     DropArgs a;
@@ -430,9 +450,11 @@ int drop_block(ntvs_ctx* c, int t) {
         CUDA_TRY(timed_launch(c, KIND_DROP, [&] { return k_drop_block(a, c->stream); }));
     }
     CUDA_TRY(timed_launch(c, KIND_APPLY, [&] {
-        return k_drop_apply(c->cdt, c->x, c->x32, c->delta, (const char*)c->inv_s + (size_t)t * c->vm.vint * c->csz(),
-                            c->V, c->vm, c->apply_grid, c->stream);
+        return k_drop_apply(c->cdt, c->x, c->copies(split), c->delta,
+                            (const char*)c->inv_s + (size_t)t * c->vm.vint * c->csz(), c->V, c->apply_grid,
+                            c->stream);
     }));
+    c->split_stale = !split;
     return NTVS_OK;
 }
 
@@ -929,12 +951,18 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
 
     // image state (x and g canonical; x32 and delta in the internal order, padding zero)
     TRY(dev_alloc(&c->x, sizeof(double) * (size_t)V, "x"));
-    if (c->cdt == F32) TRY(dev_alloc(&c->x32, sizeof(float) * (size_t)VI, "x32"));
+    if (c->cdt == F32) {
+        TRY(dev_alloc(&c->x32, sizeof(float) * (size_t)VI, "x32"));
+        TRY(dev_alloc(&c->xh, sizeof(float) * (size_t)V, "xh"));
+        TRY(dev_alloc(&c->xl, sizeof(float) * (size_t)V, "xl"));
+    }
     TRY(dev_alloc(&c->delta, csz * (size_t)VI, "delta"));
     TRY(dev_alloc(&c->g, csz * (size_t)V, "g"));
     TRY(dev_alloc(&c->resid, sizeof(double) * (size_t)c->B, "residuals"));
     CUDA_TRY(cudaMemsetAsync(c->x, 0, sizeof(double) * (size_t)V, st));
     if (c->x32) CUDA_TRY(cudaMemsetAsync(c->x32, 0, sizeof(float) * (size_t)VI, st));
+    if (c->xh) CUDA_TRY(cudaMemsetAsync(c->xh, 0, sizeof(float) * (size_t)V, st));
+    if (c->xl) CUDA_TRY(cudaMemsetAsync(c->xl, 0, sizeof(float) * (size_t)V, st));
     CUDA_TRY(cudaMemsetAsync(c->delta, 0, csz * (size_t)VI, st));
     CUDA_TRY(cudaMemsetAsync(c->g, 0, csz * (size_t)V, st));
     CUDA_TRY(cudaMemsetAsync(c->resid, 0, sizeof(double) * (size_t)c->B, st));
@@ -961,6 +989,7 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
     c->acc_trace.clear();
     c->n_steps = c->n_accepted = c->n_tries = 0;
     CUDA_TRY(cudaStreamSynchronize(st));
+    c->split_stale = false;
     c->loaded = true;
     return NTVS_OK;
 }
@@ -1036,11 +1065,15 @@ int ntvs_load_paths(ntvs_ctx* c, const ntvs_paths* s) {
     dev_free(cnt);
     TRY(dev_alloc(&c->x, sizeof(double) * (size_t)V, "x"));
     TRY(dev_alloc(&c->x32, sizeof(float) * (size_t)V, "x32"));
+    TRY(dev_alloc(&c->xh, sizeof(float) * (size_t)V, "xh"));
+    TRY(dev_alloc(&c->xl, sizeof(float) * (size_t)V, "xl"));
     TRY(dev_alloc(&c->delta, sizeof(float) * (size_t)V, "delta"));
     TRY(dev_alloc(&c->g, sizeof(float) * (size_t)V, "g"));
     TRY(dev_alloc(&c->resid, sizeof(double) * (size_t)c->B, "residuals"));
     CUDA_TRY(cudaMemsetAsync(c->x, 0, sizeof(double) * (size_t)V, st));
     CUDA_TRY(cudaMemsetAsync(c->x32, 0, sizeof(float) * (size_t)V, st));
+    CUDA_TRY(cudaMemsetAsync(c->xh, 0, sizeof(float) * (size_t)V, st));
+    CUDA_TRY(cudaMemsetAsync(c->xl, 0, sizeof(float) * (size_t)V, st));
     CUDA_TRY(cudaMemsetAsync(c->delta, 0, sizeof(float) * (size_t)V, st));
     CUDA_TRY(cudaMemsetAsync(c->resid, 0, sizeof(double) * (size_t)c->B, st));
     c->lpr = 16;
@@ -1057,6 +1090,7 @@ int ntvs_load_paths(ntvs_ctx* c, const ntvs_paths* s) {
     c->acc_trace.clear();
     c->n_steps = c->n_accepted = c->n_tries = 0;
     CUDA_TRY(cudaStreamSynchronize(st));
+    c->split_stale = false;
     c->loaded = true;
     return NTVS_OK;
 }
@@ -1161,7 +1195,8 @@ int ntvs_set_image(ntvs_ctx* c, const void* x, int dtype, int mem_kind) {
         CUDA_TRY(cudaMemcpyAsync(c->x, tmp.data(), tmp.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
         CUDA_TRY(cudaStreamSynchronize(c->stream));
     }
-    if (c->x32) CUDA_TRY(k_x32_from_x64(c->x, c->x32, c->vm, c->stream));
+    if (c->x32) CUDA_TRY(k_x32_from_x64(c->x, c->copies(), c->stream));
+    c->split_stale = false;
     return NTVS_OK;
 }
 
@@ -1339,7 +1374,7 @@ int ntvs_perturb(ntvs_ctx* c, double beta) {
     TRY(need_system(c));
     TRY(launch_grad(c, false));
     CUDA_TRY(timed_launch(c, KIND_TV, [&] {
-        return k_tv_apply(c->cdt, c->x, c->x32, c->g, c->dscal + 0, beta, nullptr, c->V, c->vm, c->stream);
+        return k_tv_apply(c->cdt, c->x, c->copies(), c->g, c->dscal + 0, beta, nullptr, c->V, c->stream);
     }));
     return NTVS_OK;
 }

@@ -27,6 +27,19 @@ struct VoxMap {
     int64_t vint;      // nz * slice_p
 };
 
+// FP32 copies of the FP64 master image, written together with it: x32 in the internal
+// voxel order (the DROP gathers), and on the FP32 path xh = fl32(x), xl = fl32(x - xh) in
+// canonical order, from which the TV stencil forms neighbour differences as
+// (xh_a - xh_b) + (xl_a - xl_b) in FP32 (the FP64 difference rounded to FP32 for
+// neighbours within a factor of two, as good as rounding it otherwise) with no FP64
+// arithmetic.  Null pointers are skipped.
+struct ImgCopies {
+    float* x32;
+    float* xh;
+    float* xl;
+    VoxMap m;
+};
+
 // Grid used by every deterministic reduction: a fixed CTA count so the order of the
 // final sum over CTA partials never changes.
 constexpr int kRedThreads = 256;
@@ -44,7 +57,7 @@ cudaError_t k_prep_block(const int64_t* row_ptr, const int32_t* col, const void*
 // (written as 0).  col_in == col_out is allowed.
 cudaError_t k_remap_cols(const int32_t* col_in, int32_t* col_out, int64_t nnz, VoxMap m, int* flags, cudaStream_t s);
 // x32[internal(j)] = (float)x[j] for the canonical voxels j < V
-cudaError_t k_x32_from_x64(const double* x, float* x32, VoxMap m, cudaStream_t s);
+cudaError_t k_x32_from_x64(const double* x, ImgCopies c, cudaStream_t s);
 // inv_s[j] = cnt[j] ? 1/cnt[j] : 0
 cudaError_t k_inv_counts(const int32_t* cnt, void* inv_s, int cdt, int64_t n, cudaStream_t s);
 
@@ -74,16 +87,17 @@ struct RedScratch {
 
 // The image x is always the FP64 master copy; g and the stencil arithmetic use cdt.
 // g = grad phi_eps(x); *gnorm2 = ||g||^2 (FP64); if phi != nullptr also *phi = phi_0(x).
-cudaError_t k_tv_grad(int cdt, const double* x, void* g, int nx, int ny, int nz, double eps, RedScratch r,
-                      double* gnorm2, double* phi, cudaStream_t s);
+// On the FP32 path without phi the stencil reads xh/xl (when not null) instead of x.
+cudaError_t k_tv_grad(int cdt, const double* x, const float* xh, const float* xl, void* g, int nx, int ny, int nz,
+                      double eps, RedScratch r, double* gnorm2, double* phi, cudaStream_t s);
 // *phi = phi_0(z), z = x - sc*g with sc = beta/sqrt(*gnorm2) (z = x when g == nullptr or
 // gnorm2 == 0).  If phi_ref != nullptr, *accept = (*phi <= *phi_ref).
 cudaError_t k_tv_value(int cdt, const double* x, const void* g, const double* gnorm2, double beta, int nx, int ny,
                        int nz, RedScratch r, double* phi, const double* phi_ref, int* accept, cudaStream_t s);
-// x <- x - sc*g (sc as in k_tv_value), x32 (may be null) <- (float)x at the internal
-// index; skipped when accept != nullptr and *accept == 0.
-cudaError_t k_tv_apply(int cdt, double* x, float* x32, const void* g, const double* gnorm2, double beta,
-                       const int* accept, int64_t V, VoxMap m, cudaStream_t s);
+// x <- x - sc*g (sc as in k_tv_value) and its FP32 copies; skipped when accept != nullptr
+// and *accept == 0.
+cudaError_t k_tv_apply(int cdt, double* x, ImgCopies c, const void* g, const double* gnorm2, double beta,
+                       const int* accept, int64_t V, cudaStream_t s);
 
 // ------------------------------------------------------------------ DROP
 // A run of consecutive rows [r0, r1) whose entries lie mostly in z-slice `home`.
@@ -124,10 +138,10 @@ cudaError_t k_row_home(const int64_t* row_ptr, const int32_t* col, int64_t M, in
 // the previous row's defined home (*changes must be zeroed by the caller)
 cudaError_t k_chunk_home(const int32_t* home, const int64_t* chunk_start, int64_t nchunks, int32_t* out,
                          unsigned long long* changes, int grid, cudaStream_t s);
-// x_j += delta_p * inv_s_p on the FP64 master (p the internal index of j; x32_p <- (float)x_j
-// when x32 != null); delta_p = 0
-cudaError_t k_drop_apply(int cdt, double* x, float* x32, void* delta, const void* inv_s, int64_t V, VoxMap m,
-                         int grid, cudaStream_t s);
+// x_j += delta_p * inv_s_p on the FP64 master (p the internal index of j) and its FP32
+// copies; delta_p = 0
+cudaError_t k_drop_apply(int cdt, double* x, ImgCopies c, void* delta, const void* inv_s, int64_t V, int grid,
+                         cudaStream_t s);
 
 // TMA-fed pipeline (drop_pipe_kernel): a stage is a run of at most kStageRows whole rows
 // of one home slice whose entries [e0, e0 + nent) fit one ring slot (e0 and nent aligned
