@@ -36,16 +36,18 @@ struct MemberDev {
     const float* val;
     const float* b;
     const float* inv_norm2;
-    const float* inv_s;   // [B][V]
+    const float* inv_s;   // [B][vint], internal voxel order
     double* x;
-    float* x32;           // fl32(x), canonical order
-    float* xl;            // fl32(x - x32): the TV stencil differences are formed from both
+    float* x32;           // fl32(x), internal voxel order (the DROP gathers)
+    float* xh;            // fl32(x) and fl32(x - xh), canonical order: the TV stencil
+    float* xl;            //   differences are formed from both
     float* delta;
     float* g;
     double* resid;        // [B]
     double* tv_hist;      // [cap]
     int nx, ny, nz, B, N;
     int64_t V;
+    VoxMap vm;            // internal order of x32, delta, inv_s and the stored columns
     float lambda, eps;
     int item0, nitems;    // this member's TV items
 };
@@ -91,7 +93,7 @@ __global__ void __launch_bounds__(256) tvb_grad_kernel(const MemberDev* __restri
     if (n_step >= m.N) return;   // uniform over the CTA: no reduction for this member
     const int nx = m.nx, ny = m.ny, nz = m.nz;
     const int64_t sxy = (int64_t)nx * ny;
-    const float* xh = m.x32;
+    const float* xh = m.xh;
     const float* xl = m.xl;
     const float eps = m.eps;
     auto dif = [&](int64_t a, int64_t b) -> float {
@@ -142,7 +144,8 @@ __global__ void __launch_bounds__(256) tvb_apply_kernel(const MemberDev* __restr
         const double z = perturbed(m.x[p], sc, (double)m.g[p]);
         m.x[p] = z;
         const float h = (float)z;
-        m.x32[p] = h;
+        m.x32[vox_internal(m.vm, p)] = h;
+        m.xh[p] = h;
         m.xl[p] = (float)(z - (double)h);
     }
 }
@@ -202,14 +205,18 @@ __global__ void __launch_bounds__(256) dropb_apply_kernel(const MemberDev* __res
     const Item it = items[blockIdx.x];
     const MemberDev m = mem[it.member];
     if (b >= m.B) return;
-    const float* inv_s = m.inv_s + (int64_t)b * m.V;
-    const bool last = b == m.B - 1;   // xl is read by the next gradient only: written after the last block
-    for (int64_t p = it.i0 + threadIdx.x; p < it.i1; p += blockDim.x) {
-        const double v = m.x[p] + (double)m.delta[p] * (double)inv_s[p];
-        m.x[p] = v;
+    const float* inv_s = m.inv_s + (int64_t)b * m.vm.vint;
+    const bool last = b == m.B - 1;   // xh, xl are read by the next gradient only: written after the last block
+    for (int64_t j = it.i0 + threadIdx.x; j < it.i1; j += blockDim.x) {
+        const int64_t p = vox_internal(m.vm, j);
+        const double v = m.x[j] + (double)m.delta[p] * (double)inv_s[p];
+        m.x[j] = v;
         const float h = (float)v;
         m.x32[p] = h;
-        if (last) m.xl[p] = (float)(v - (double)h);
+        if (last) {
+            m.xh[j] = h;
+            m.xl[j] = (float)(v - (double)h);
+        }
         m.delta[p] = 0.f;
     }
 }
@@ -455,7 +462,11 @@ int ntvs_batch_add(ntvs_batch* bt, const ntvs_system* s, const ntvs_params* p, c
         for (int t = 0; t <= s->n_blocks; ++t) bp.push_back(std::min<int64_t>((int64_t)t * per, M));
     }
     const int B = (int)bp.size() - 1;
-    std::vector<float> inn((size_t)M), inv_s((size_t)B * V, 0.f);
+    // internal voxel order (4x4 in-plane tiles, as the single-context FP32 path)
+    VoxMap vm = make_voxmap(s->nx, s->ny, s->nz, 4, 4);
+    if (vm.vint > 0x7fffffffLL) vm = make_voxmap(s->nx, s->ny, s->nz, 1, 1);
+    const int64_t VI = vm.vint;
+    std::vector<float> inn((size_t)M), inv_s((size_t)B * VI, 0.f);
     for (int64_t i = 0; i < M; ++i) {
         double n2 = 0.0;
         for (int64_t q = rp[i]; q < rp[i + 1]; ++q) n2 += (double)val[q] * (double)val[q];
@@ -467,7 +478,8 @@ int ntvs_batch_add(ntvs_batch* bt, const ntvs_system* s, const ntvs_params* p, c
             std::fill(cnt.begin(), cnt.end(), 0);
             for (int64_t q = rp[bp[t]]; q < rp[bp[t + 1]]; ++q)
                 if (val[q] != 0.f) cnt[col[q]] += 1;
-            for (int64_t j = 0; j < V; ++j) inv_s[(size_t)t * V + j] = cnt[j] ? (float)(1.0 / cnt[j]) : 0.f;
+            for (int64_t j = 0; j < V; ++j)
+                inv_s[(size_t)t * VI + vox_internal_host(vm, j)] = cnt[j] ? (float)(1.0 / cnt[j]) : 0.f;
         }
     }
     ntvs_batch::Member mm;
@@ -490,11 +502,13 @@ int ntvs_batch_add(ntvs_batch* bt, const ntvs_system* s, const ntvs_params* p, c
             for (int64_t j = 0; j < V; ++j) x[j] = t[j];
         }
     }
-    std::vector<float> x32((size_t)V), xl((size_t)V);
+    std::vector<float> x32((size_t)VI, 0.f), xh((size_t)V), xl((size_t)V);
     for (int64_t j = 0; j < V; ++j) {
-        x32[j] = (float)x[j];
-        xl[j] = (float)(x[j] - (double)x32[j]);
+        xh[j] = (float)x[j];
+        xl[j] = (float)(x[j] - (double)xh[j]);
+        x32[(size_t)vox_internal_host(vm, j)] = xh[j];
     }
+    for (auto& c : col) c = (int32_t)vox_internal_host(vm, c);   // validated above
     int rc = NTVS_OK;
     if ((rc = up((void**)&d.row_ptr, rp.data(), sizeof(int64_t) * rp.size(), "row_ptr")) ||
         (rc = up((void**)&d.col, col.data(), sizeof(int32_t) * col.size(), "col")) ||
@@ -503,17 +517,19 @@ int ntvs_batch_add(ntvs_batch* bt, const ntvs_system* s, const ntvs_params* p, c
         (rc = up((void**)&d.inv_norm2, inn.data(), sizeof(float) * inn.size(), "inv_norm2")) ||
         (rc = up((void**)&d.inv_s, inv_s.data(), sizeof(float) * inv_s.size(), "inv_s")) ||
         (rc = up((void**)&d.x, x.data(), sizeof(double) * V, "x")) ||
-        (rc = up((void**)&d.x32, x32.data(), sizeof(float) * V, "x32")) ||
+        (rc = up((void**)&d.x32, x32.data(), sizeof(float) * VI, "x32")) ||
+        (rc = up((void**)&d.xh, xh.data(), sizeof(float) * V, "xh")) ||
         (rc = up((void**)&d.xl, xl.data(), sizeof(float) * V, "xl")) ||
-        (rc = up((void**)&d.delta, nullptr, sizeof(float) * V, "delta")) ||
+        (rc = up((void**)&d.delta, nullptr, sizeof(float) * VI, "delta")) ||
         (rc = up((void**)&d.g, nullptr, sizeof(float) * V, "g")) ||
         (rc = up((void**)&d.resid, nullptr, sizeof(double) * std::max(B, 1), "resid"))) {
         for (void* q : mm.owned) cudaFree(q);
         return rc;
     }
-    BCUDA(cudaMemset((void*)d.delta, 0, sizeof(float) * V));
+    BCUDA(cudaMemset((void*)d.delta, 0, sizeof(float) * VI));
     BCUDA(cudaMemset((void*)d.resid, 0, sizeof(double) * std::max(B, 1)));
     d.nx = s->nx; d.ny = s->ny; d.nz = s->nz; d.B = B; d.N = p->N; d.V = V;
+    d.vm = vm;
     d.lambda = (float)p->lambda;
     d.eps = (float)p->eps_tv;
     mm.p = *p;
@@ -602,7 +618,7 @@ int ntvs_batch_finalize(ntvs_batch* bt, int max_cycles) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         for (auto& mm : bt->m) {
-            BCUDA(cudaMemsetAsync(mm.d.delta, 0, sizeof(float) * mm.d.V, bt->stream));
+            BCUDA(cudaMemsetAsync(mm.d.delta, 0, sizeof(float) * mm.d.vm.vint, bt->stream));
             BCUDA(cudaMemsetAsync(mm.d.resid, 0, sizeof(double) * std::max(mm.d.B, 1), bt->stream));
         }
         BCUDA(cudaStreamSynchronize(bt->stream));

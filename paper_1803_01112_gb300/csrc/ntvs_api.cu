@@ -267,21 +267,6 @@ int check_device_error(ntvs_ctx* c) {
     return NTVS_OK;
 }
 
-VoxMap make_voxmap(int nx, int ny, int nz, int tx, int ty) {
-    VoxMap m;
-    m.nx = nx; m.ny = ny; m.nz = nz;
-    m.tx = tx; m.ty = ty;
-    m.ltx = 0;
-    while ((1 << m.ltx) < tx) ++m.ltx;
-    m.lty = 0;
-    while ((1 << m.lty) < ty) ++m.lty;
-    m.nxp = (nx + tx - 1) / tx * tx;
-    m.nyp = (ny + ty - 1) / ty * ty;
-    m.slice_p = (int64_t)m.nxp * m.nyp;
-    m.vint = m.slice_p * nz;
-    return m;
-}
-
 int copy_in(void** dst, bool* own, const void* src, size_t bytes, int mem_kind, cudaStream_t s, const char* what) {
     if (mem_kind == NTVS_MEM_DEVICE) {
         *dst = const_cast<void*>(src);

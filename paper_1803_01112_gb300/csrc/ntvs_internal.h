@@ -27,6 +27,30 @@ struct VoxMap {
     int64_t vint;      // nz * slice_p
 };
 
+// tx, ty powers of two
+inline VoxMap make_voxmap(int nx, int ny, int nz, int tx, int ty) {
+    VoxMap m;
+    m.nx = nx; m.ny = ny; m.nz = nz;
+    m.tx = tx; m.ty = ty;
+    m.ltx = 0;
+    while ((1 << m.ltx) < tx) ++m.ltx;
+    m.lty = 0;
+    while ((1 << m.lty) < ty) ++m.lty;
+    m.nxp = (nx + tx - 1) / tx * tx;
+    m.nyp = (ny + ty - 1) / ty * ty;
+    m.slice_p = (int64_t)m.nxp * m.nyp;
+    m.vint = m.slice_p * nz;
+    return m;
+}
+
+// internal index of canonical voxel j on the host (the device has vox_internal)
+inline int64_t vox_internal_host(const VoxMap& m, int64_t j) {
+    if (m.tx == 1 && m.ty == 1) return j;
+    const int64_t ix = j % m.nx, t = j / m.nx, iy = t % m.ny, iz = t / m.ny;
+    const int64_t ntx = m.nxp / m.tx;
+    return iz * m.slice_p + ((iy / m.ty) * ntx + ix / m.tx) * (int64_t)(m.tx * m.ty) + (iy % m.ty) * m.tx + ix % m.tx;
+}
+
 // FP32 copies of the FP64 master image, written together with it: x32 in the internal
 // voxel order (the DROP gathers), and on the FP32 path xh = fl32(x), xl = fl32(x - xh) in
 // canonical order, from which the TV stencil forms neighbour differences as
