@@ -292,8 +292,10 @@ int ntvs_get_profile(ntvs_ctx* ctx, ntvs_profile* out);
  * then touch fewer distinct cache lines per slice.  The results are those of the
  * canonical order up to the order of floating-point accumulation; images, gradients and
  * every other public array stay canonical.  tx, ty in {1, 2, 4, 8, 16}; 1 x 1 is the
- * canonical order; the default is 4 x 4.  The FP64 path and ntvs_load_paths always use the
- * canonical order.  This layout has no counterpart in the paper.  NTVS_ERR_ARG on other sizes. */
+ * canonical order; the default is 4 x 4.  It applies to ntvs_load_paths and
+ * ntvs_load_histories too (the traced voxel indices are formed in that order); the FP64
+ * path always uses the canonical order.  This layout has no counterpart in the paper.
+ * NTVS_ERR_ARG on other sizes. */
 int ntvs_set_voxel_tile(ntvs_ctx* ctx, int tx, int ty);
 
 /* Test hook: replay ell_k for the next n cycles instead of drawing it (NULL clears). */

@@ -21,7 +21,16 @@ struct Grid3 {
     float ox, oy, oz, hx, hy, hz;
     float ihx, ihy, ihz;   // 1 / voxel size
     int nx, ny, nz;
+    int ltx, lty, ntx;     // internal voxel order: tiles of 2^ltx x 2^lty, ntx tiles per row
+    int slice_p;           // voxels per padded slice
 };
+
+// internal index (see VoxMap) of voxel (ix, iy, iz)
+__device__ __forceinline__ int grid_index(const Grid3& g, int ix, int iy, int iz) {
+    const int tile = (iy >> g.lty) * g.ntx + (ix >> g.ltx);
+    return iz * g.slice_p + (tile << (g.ltx + g.lty)) + ((iy & ((1 << g.lty) - 1)) << g.ltx) +
+           (ix & ((1 << g.ltx) - 1));
+}
 
 __device__ __forceinline__ float h10f(float s) { return s * s * s - 2.f * s * s + s; }
 __device__ __forceinline__ float h11f(float s) { return s * s * s - s * s; }
@@ -102,7 +111,7 @@ __device__ __forceinline__ void trace_segment(const Grid3& g, const float P[3], 
         if (tn[2] < t1) { t1 = tn[2]; w = 2; }
         const bool last = !(t1 < hi);
         if (last) t1 = hi;
-        if (t1 - t0 > 1e-7f) f(((idx[2] * g.ny) + idx[1]) * g.nx + idx[0], (t1 - t0) * L);
+        if (t1 - t0 > 1e-7f) f(grid_index(g, idx[0], idx[1], idx[2]), (t1 - t0) * L);
         if (last) break;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {   // constant indices keep the arrays in registers
@@ -298,6 +307,9 @@ static Grid3 make_grid(const OtfArgs& a) {
     g.nx = a.nx; g.ny = a.ny; g.nz = a.nz;
     g.hx = (float)a.dx; g.hy = (float)a.dy; g.hz = (float)a.dz;
     g.ihx = 1.f / g.hx; g.ihy = 1.f / g.hy; g.ihz = 1.f / g.hz;
+    g.ltx = a.vm.ltx; g.lty = a.vm.lty;
+    g.ntx = a.vm.nxp >> a.vm.ltx;
+    g.slice_p = (int)a.vm.slice_p;
     g.ox = (float)(-0.5 * a.nx * a.dx); g.oy = (float)(-0.5 * a.ny * a.dy); g.oz = 0.f;
     return g;
 }

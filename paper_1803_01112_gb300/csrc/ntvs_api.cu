@@ -1016,7 +1016,9 @@ int ntvs_load_paths(ntvs_ctx* c, const ntvs_paths* s) {
     c->cdt = F32;
     c->storage = NTVS_CSR32;
     c->nnz = 0;
-    c->vm = make_voxmap(s->nx, s->ny, s->nz, 1, 1);   // traced voxels are canonical
+    c->vm = make_voxmap(s->nx, s->ny, s->nz, c->tile_req_x, c->tile_req_y);
+    if (c->vm.vint > 0x7fffffffLL) c->vm = make_voxmap(s->nx, s->ny, s->nz, 1, 1);
+    const int64_t VI = c->vm.vint;
     TRY(copy_in((void**)&c->paths, &c->own_paths, s->paths, sizeof(float) * 10 * (size_t)M, s->mem_kind, st, "paths"));
     TRY(copy_in(&c->b, &c->own_b, s->b, sizeof(float) * (size_t)M, s->mem_kind, st, "b"));
     c->paths_mode = true;
@@ -1029,6 +1031,7 @@ int ntvs_load_paths(ntvs_ctx* c, const ntvs_paths* s) {
     o.n_seg = s->n_seg;
     o.min_len = (float)s->min_len;
     o.grid = c->sms * 8;
+    o.vm = c->vm;
     CUDA_TRY(cudaMemsetAsync(c->dflags, 0, sizeof(int), st));
     CUDA_TRY(k_otf_validate(o, c->dflags, st));
     CUDA_TRY(cudaMemcpyAsync(c->hint, c->dflags, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1040,26 +1043,26 @@ int ntvs_load_paths(ntvs_ctx* c, const ntvs_paths* s) {
     }
     TRY(dev_alloc(&c->inv_norm2, sizeof(float) * (size_t)std::max<int64_t>(M, 1), "inv_norm2"));
     int32_t* cnt = nullptr;
-    TRY(dev_alloc(&cnt, sizeof(int32_t) * (size_t)c->B * V, "hit counts"));
-    CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)c->B * V, st));
+    TRY(dev_alloc(&cnt, sizeof(int32_t) * (size_t)c->B * VI, "hit counts"));
+    CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)c->B * VI, st));
     for (int t = 0; t < c->B; ++t)
-        CUDA_TRY(k_otf_prep(o, bp[t], bp[t + 1], (float*)c->inv_norm2, cnt + (size_t)t * V, st));
-    TRY(dev_alloc(&c->inv_s, sizeof(float) * (size_t)c->B * V, "inverse hit counts"));
-    CUDA_TRY(k_inv_counts(cnt, c->inv_s, F32, (int64_t)c->B * V, st));
+        CUDA_TRY(k_otf_prep(o, bp[t], bp[t + 1], (float*)c->inv_norm2, cnt + (size_t)t * VI, st));
+    TRY(dev_alloc(&c->inv_s, sizeof(float) * (size_t)c->B * VI, "inverse hit counts"));
+    CUDA_TRY(k_inv_counts(cnt, c->inv_s, F32, (int64_t)c->B * VI, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     dev_free(cnt);
     TRY(dev_alloc(&c->x, sizeof(double) * (size_t)V, "x"));
-    TRY(dev_alloc(&c->x32, sizeof(float) * (size_t)V, "x32"));
+    TRY(dev_alloc(&c->x32, sizeof(float) * (size_t)VI, "x32"));
     TRY(dev_alloc(&c->xh, sizeof(float) * (size_t)V, "xh"));
     TRY(dev_alloc(&c->xl, sizeof(float) * (size_t)V, "xl"));
-    TRY(dev_alloc(&c->delta, sizeof(float) * (size_t)V, "delta"));
+    TRY(dev_alloc(&c->delta, sizeof(float) * (size_t)VI, "delta"));
     TRY(dev_alloc(&c->g, sizeof(float) * (size_t)V, "g"));
     TRY(dev_alloc(&c->resid, sizeof(double) * (size_t)c->B, "residuals"));
     CUDA_TRY(cudaMemsetAsync(c->x, 0, sizeof(double) * (size_t)V, st));
-    CUDA_TRY(cudaMemsetAsync(c->x32, 0, sizeof(float) * (size_t)V, st));
+    CUDA_TRY(cudaMemsetAsync(c->x32, 0, sizeof(float) * (size_t)VI, st));
     CUDA_TRY(cudaMemsetAsync(c->xh, 0, sizeof(float) * (size_t)V, st));
     CUDA_TRY(cudaMemsetAsync(c->xl, 0, sizeof(float) * (size_t)V, st));
-    CUDA_TRY(cudaMemsetAsync(c->delta, 0, sizeof(float) * (size_t)V, st));
+    CUDA_TRY(cudaMemsetAsync(c->delta, 0, sizeof(float) * (size_t)VI, st));
     CUDA_TRY(cudaMemsetAsync(c->resid, 0, sizeof(double) * (size_t)c->B, st));
     c->lpr = 16;
     c->schedule = NTVS_SCHED_ONTHEFLY;

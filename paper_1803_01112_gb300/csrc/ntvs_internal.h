@@ -214,6 +214,7 @@ struct OtfArgs {
     int n_seg;
     float min_len;
     int grid;
+    VoxMap vm;            // order of the traced voxel indices (x32, delta, hit counts)
 };
 cudaError_t k_otf_validate(const OtfArgs& a, int* flags, cudaStream_t s);
 // history data [M][12] (P_in, P_out, d_in, d_out) -> path records [M][10]; flags |= 32 on a
