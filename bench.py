@@ -453,6 +453,34 @@ def run_ntvs(args):
                 "avg_launch_ms": avg_ms}
     kernel_ms = {k: prof[k] / args.steps for k in ("drop_block_ms", "drop_apply_ms", "tv_ms")}
 
+    # ---- end to end through the C ABI from pinned host buffers; measured before the variant
+    # legs, whose many device allocations and frees slow later multi-GB allocations down
+    e2e = None
+    if not args.no_e2e and args.e2e_steps > 0:
+        h2d = s.row_ptr.nbytes + s.col.nbytes + s.val.nbytes + b.nbytes + x0.nbytes
+        out = pinned((spec.V,), vdt)
+        times, split = [], []
+        for _ in range(args.e2e_steps):
+            barrier(world, device)
+            torch.cuda.synchronize(device)
+            t0 = time.perf_counter()
+            re = ntvs.Reconstructor(local, stream.cuda_stream).set_voxel_tile(*tile)
+            re.load(shape, s.row_ptr, s.col, s.val, b, n_blocks=spec.n_blocks, schedule=sched)
+            t_l = time.perf_counter()
+            re.set_params(**PARAMS)
+            re.set_image(x0)
+            re.run(E2E_CYCLES)
+            ntvs.ntvs_get_image(re.handle, out)
+            t1 = time.perf_counter()
+            re.close()
+            times.append(max_over_ranks(t1 - t0, world, device))
+            split.append((t_l - t0, t1 - t_l))
+        t_e2e = statistics.mean(times)
+        e2e = {"value": world * spec.n_hist * E2E_CYCLES / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(out.nbytes), "cycles_per_step": E2E_CYCLES,
+               "seconds_per_step": t_e2e, "load_seconds": statistics.mean(x for x, _ in split),
+               "run_and_readback_seconds": statistics.mean(y for _, y in split)}
+
     # ---- the same workload in the canonical voxel order, and mixed precision (FP32
     # arithmetic): BF16 lengths with int32 or DELTA16 columns
     variants = []
@@ -506,33 +534,6 @@ def run_ntvs(args):
     # ---- on-the-fly rows on the large grid
     if args.onthefly:
         variants.append(run_onthefly_variant(args, ntvs, local, stream, world, device))
-
-    # ---- end to end through the C ABI from pinned host buffers
-    e2e = None
-    if not args.no_e2e and args.e2e_steps > 0:
-        h2d = s.row_ptr.nbytes + s.col.nbytes + s.val.nbytes + b.nbytes + x0.nbytes
-        out = pinned((spec.V,), vdt)
-        times, split = [], []
-        for _ in range(args.e2e_steps):
-            barrier(world, device)
-            torch.cuda.synchronize(device)
-            t0 = time.perf_counter()
-            re = ntvs.Reconstructor(local, stream.cuda_stream).set_voxel_tile(*tile)
-            re.load(shape, s.row_ptr, s.col, s.val, b, n_blocks=spec.n_blocks, schedule=sched)
-            t_l = time.perf_counter()
-            re.set_params(**PARAMS)
-            re.set_image(x0)
-            re.run(E2E_CYCLES)
-            ntvs.ntvs_get_image(re.handle, out)
-            t1 = time.perf_counter()
-            re.close()
-            times.append(max_over_ranks(t1 - t0, world, device))
-            split.append((t_l - t0, t1 - t_l))
-        t_e2e = statistics.mean(times)
-        e2e = {"value": world * spec.n_hist * E2E_CYCLES / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(out.nbytes), "cycles_per_step": E2E_CYCLES,
-               "seconds_per_step": t_e2e, "load_seconds": statistics.mean(x for x, _ in split),
-               "run_and_readback_seconds": statistics.mean(y for _, y in split)}
 
     # ---- CPU oracle baseline (rank 0, one GPU only)
     cpu = None
