@@ -181,6 +181,8 @@ def test_full_size_sampled_parity():
     rng = np.random.default_rng(0)
     try:
         r.load(shape, s.row_ptr, s.col, s.val, s.b.astype(np.float32), n_blocks=spec.n_blocks)
+        st0 = r.stats()   # the benchmark's configuration: windowed schedule, 4x4 voxel tiles
+        assert st0["drop_schedule"] == 2 and (st0["voxel_tile_x"], st0["voxel_tile_y"]) == (4, 4)
         x0 = s.xbar.astype(np.float32)
         r.set_params(lam=2e-4, N=3, alpha=0.75, seed=2)
         # one DROP block at full size (block 7: a middle block), sampled voxels
