@@ -61,6 +61,8 @@ def parse_args(argv=None):
     ap.add_argument("--tile", default="4x4", help="internal voxel tile of the FP32 path (1x1: canonical order)")
     ap.add_argument("--canonical", type=int, default=1,
                     help="also time the canonical voxel order on the same workload (0: skip)")
+    ap.add_argument("--check", type=int, default=1,
+                    help="also time the same workload with the TV-reduction check on (0: skip)")
     ap.add_argument("--cpu-rows", type=int, default=3_000_000, help="oracle sample: first rows of the workload")
     ap.add_argument("--ref-rows", type=int, default=1_000_000, help="reference arm: rows per step")
     ap.add_argument("--schedule", choices=["auto", "plain", "window", "pipeline"], default="auto",
@@ -486,17 +488,20 @@ def run_ntvs(args):
     variants = []
     cases = []
     if args.canonical and vdt == np.float32 and tile != (1, 1):
-        cases.append(("fp32, canonical voxel order", s.val, ntvs.NTVS_CSR32, vsz, 4, (1, 1)))
+        cases.append(("fp32, canonical voxel order", s.val, ntvs.NTVS_CSR32, vsz, 4, (1, 1), PARAMS))
+    if args.check and vdt == np.float32:
+        cases.append(("fp32, TV-reduction check on", s.val, ntvs.NTVS_CSR32, vsz, 4, tile,
+                      dict(PARAMS, tv_check=True)))
     if args.mixed and vdt == np.float32:
         import torch as _t
         vb = _t.from_numpy(s.val).to(_t.bfloat16)
-        cases.append(("bf16 lengths + int32 columns", vb, ntvs.NTVS_CSR32, 2, 4, tile))
-        cases.append(("bf16 lengths + delta16 columns", vb, ntvs.NTVS_DELTA16, 2, 2, tile))
+        cases.append(("bf16 lengths + int32 columns", vb, ntvs.NTVS_CSR32, 2, 4, tile, PARAMS))
+        cases.append(("bf16 lengths + delta16 columns", vb, ntvs.NTVS_DELTA16, 2, 2, tile, PARAMS))
     if cases:
-        for name, vals, storage, vb_size, ib, vt in cases:
+        for name, vals, storage, vb_size, ib, vt, prm in cases:
             rm = ntvs.Reconstructor(local, stream.cuda_stream).set_voxel_tile(*vt)
             rm.load(shape, s.row_ptr, s.col, vals, b, n_blocks=spec.n_blocks, storage=storage, schedule=sched)
-            rm.set_params(**PARAMS)
+            rm.set_params(**prm)
             rm.set_image(x0)
             stm = rm.stats()
             rm.run(args.warmup)
@@ -512,6 +517,7 @@ def run_ntvs(args):
             torch.cuda.synchronize(device)
             msm = max_over_ranks(f0.elapsed_time(f1), world, device)
             pm = rm.profile()
+            stf = rm.stats()
             rm.close()
             extra = 8 if storage == ntvs.NTVS_DELTA16 else 0
             bytes_m = float(np.mean(algorithmic_drop_bytes(s, vb_size, 4, index_bytes=ib, extra_row_bytes=extra))) + \
@@ -521,6 +527,7 @@ def run_ntvs(args):
             variants.append({"name": name, "value": world * spec.n_hist * args.steps / (msm / 1e3), "unit": UNIT,
                              "ms_per_step": msm / args.steps, "vs_headline": ms / msm,
                              "voxel_tile": f"{stm['voxel_tile_x']}x{stm['voxel_tile_y']}",
+                             "tries_per_step": stf["n_tries"] / max(stf["n_steps"], 1),
                              "drop_schedule": {1: "plain", 2: "window", 3: "pipeline"}.get(stm["drop_schedule"]),
                              "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                                           "frac": ach / peak, "algorithmic_bytes_per_launch": bytes_m,
