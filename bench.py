@@ -27,6 +27,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -120,7 +121,7 @@ class ClockSampler:
         ids = [v for v in vis.split(",") if v.strip()]
         self.index = ids[local_rank] if local_rank < len(ids) and ids[local_rank].strip().isdigit() else str(local_rank)
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{local_rank}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"ntvs_bench_clocks_rank{local_rank}.csv")
 
     def start(self):
         try:
