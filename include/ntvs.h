@@ -3,9 +3,9 @@
  *
  * NTVS = total variation superiorization with N normalized TV perturbation steps of
  * size beta0*alpha^ell between feasibility-seeking sweeps, with or without the TV
- * reduction check (arXiv 1803.01112, Sec. II-B, Appendix C).  The feasibility-seeking
+ * reduction check (arXiv 1803.01112, Sec. III-B, Appendix C).  The feasibility-seeking
  * operator P_T is one sweep of block-DROP over the blocks of proton histories
- * (Sec. II-D, DROP of ref. CEHN08):
+ * (Sec. III-D, DROP of ref. CEHN08):
  *
  *     for each block t, with every row i of the block seeing the same x:
  *       r_i  = (b_i - <a_i, x>) / ||a_i||^2            (0 when ||a_i|| = 0)
@@ -63,7 +63,7 @@ extern "C" {
 typedef struct ntvs_ctx ntvs_ctx;
 
 /* The linear system of one reconstruction: row i is proton history i, a_ij its
- * intersection length with voxel j, b_i its WEPL (Sec. I, Sec. II-D). */
+ * intersection length with voxel j, b_i its WEPL (Sec. I, Sec. III-D). */
 typedef struct {
     int32_t nx, ny, nz;          /* image grid, V = nx*ny*nz                                */
     int32_t n_blocks;            /* B; used when block_ptr is NULL: contiguous blocks of
@@ -107,7 +107,7 @@ typedef struct {
 #define NTVS_STEP_DECOUPLED 2  /* beta_{k,n} = beta0 * alpha^n * gamma^k, n = 0..N-1, k the
                                   cycle index from 0 (Sec. VI); no ell, no TV check           */
 
-/* Parameters of NTVS (Sec. II-E, Appendix A/C). */
+/* Parameters of NTVS (Sec. III-E, Appendix A/C). */
 typedef struct {
     double lambda;       /* DROP relaxation lambda                                        */
     double alpha;        /* perturbation kernel, 0 < alpha < 1                             */
@@ -371,9 +371,10 @@ int ntvs_batch_get_stats(ntvs_batch* bt, ntvs_batch_stats* st);
  * Nothing is allocated: the reduction scratch (4096 FP64 partials and a ticket word) is a
  * static device array that every GPU loading the library holds until the process exits.
  * Limit: V <= 16,777,216 voxels (4096 CTAs x 256 threads x 16 voxels); larger images
- * return NTVS_ERR_ARG.  The first call on a device looks up the scratch's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before any
- * stream capture.  All calls share the one scratch array, which keeps the last call's
+ * return NTVS_ERR_ARG.  Every call looks up the scratch's device address in the current
+ * context (cudaGetSymbolAddress, which allocates nothing); the first call on a device also
+ * loads the library's device code there, so make that first call before any stream
+ * capture.  All calls share the one scratch array, which keeps the last call's
  * contents: calls that overlap on the GPU (other streams, other threads) race and give
  * wrong results, so order them on one stream.  Errors: NTVS_ERR_ARG, NTVS_ERR_CUDA. */
 int ntvs_tv_value_static(const void* x, int dtype, int nx, int ny, int nz, double* tv_out, void* cuda_stream);

@@ -7,7 +7,7 @@ double precision); this module is argument marshalling.
 
 Pins (what fixes each function independently of itself) live in ``tests/test_oracle_*.py``:
   * orc_splitmix64 / orc_rand_ell : published SplitMix64 outputs, an independent
-    Python SplitMix64, and the N=1 no-check identity ell_k = k (Sec. II-B).
+    Python SplitMix64, and the N=1 no-check identity ell_k = k (Sec. III-B).
   * orc_tv       : phi(const) = 0, closed form of a step edge, homogeneity and shift
     invariance, the 1D total variation.
   * orc_tv_grad  : central finite differences of phi_eps, and a hand-expanded 2x2x1 case.

@@ -10,14 +10,14 @@
  *   - NTVS outer loop, without and with the TV-reduction check: Appendix C
  *     (Algorithm "NTVS" and its variant with the TV reduction requirement),
  *     notation of Appendix A.
- *   - ell schedule: ell_k = rand(k, ell_{k-1}), Sec. II-B (item 4) and Appendix C.
- *   - step size beta_{k,n} = alpha^{ell_k}, Sec. II-B and Appendix A; the paper's
+ *   - ell schedule: ell_k = rand(k, ell_{k-1}), Sec. III-B (item 4) and Appendix C.
+ *   - step size beta_{k,n} = alpha^{ell_k}, Sec. III-B and Appendix A; the paper's
  *     beta_0 = 1 is exposed as beta0.
  *   - OTVS (Appendix B): ell is never reset between cycles, beta = (1/2)^ell.
  *   - decoupled step size beta_{k,n} = alpha^n gamma^{f(k)}, f(k) = k (Sec. VI).
  *   - phi = TV, "sum of local variations over all voxels" (Sec. IV, ref. CCCNP10);
  *     v = -grad phi / ||grad phi|| (Appendix A).
- *   - P_T = one sweep of block-DROP (Sec. II-D cites the DROP algorithm of ref.
+ *   - P_T = one sweep of block-DROP (Sec. III-D cites the DROP algorithm of ref.
  *     CEHN08 without printing its update).
  * Readings where the paper is silent or garbled (all listed in the design notes):
  *   - DROP step for block t (rows B_t, all using the same x):

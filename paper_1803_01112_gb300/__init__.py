@@ -2,7 +2,7 @@
 
 Total variation superiorization with N normalized TV perturbation steps of size
 beta0*alpha^ell interleaved with block-DROP feasibility-seeking sweeps, with or without
-the TV reduction check (arXiv 1803.01112, Sec. II-B, Appendix C).
+the TV reduction check (arXiv 1803.01112, Sec. III-B, Appendix C).
 
 Every step of the computation runs in the CUDA kernels of ``libntvs.so``; this module
 only marshals arguments (numpy arrays = host memory, CUDA torch tensors = device

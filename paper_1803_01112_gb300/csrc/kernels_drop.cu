@@ -1,4 +1,4 @@
-// Block-DROP kernels (P_T of arXiv 1803.01112 Appendix C; DROP of ref. CEHN08, Sec. II-D).
+// Block-DROP kernels (P_T of arXiv 1803.01112 Appendix C; DROP of ref. CEHN08, Sec. III-D).
 //
 // drop_block: for every row i of block t (all rows see the same x):
 //     d_i = <a_i, x>                    (CSR gather, x is L2/L1-resident)

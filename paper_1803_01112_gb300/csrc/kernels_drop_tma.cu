@@ -1,5 +1,5 @@
 // Block-DROP with a TMA-fed pipeline (P_T of arXiv 1803.01112 Appendix C; DROP of ref.
-// CEHN08, Sec. II-D): the same update as drop_block_window_kernel,
+// CEHN08, Sec. III-D): the same update as drop_block_window_kernel,
 //     r_i = lambda (b_i - <a_i, x>) / ||a_i||^2,   delta_j += r_i a_ij,
 // with the matrix stream decoupled from the dependent gather -> dot -> scatter chain.
 //

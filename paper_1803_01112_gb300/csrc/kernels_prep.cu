@@ -1,6 +1,6 @@
 // Load-time preparation of the system (runs once per ntvs_load_system, outside the
 // iteration): validation, FP64 row norms ||a_i||^2 of the stored values, and the
-// per-block hit counts s_j^t of the block-DROP weights (Sec. II-D, DROP of ref. CEHN08).
+// per-block hit counts s_j^t of the block-DROP weights (Sec. III-D, DROP of ref. CEHN08).
 #include "common.cuh"
 
 namespace ntvs {

@@ -1,9 +1,9 @@
 // Host runtime and C ABI of the NTVS library (declared in include/ntvs.h).
 //
 // The outer loop of NTVS (arXiv 1803.01112, Appendix C) runs here on the host: it
-// draws ell_k = rand(k, ell_{k-1}) (Sec. II-B item 4), forms beta = beta0 * alpha^ell
+// draws ell_k = rand(k, ell_{k-1}) (Sec. III-B item 4), forms beta = beta0 * alpha^ell
 // (Appendix A) and queues the kernels of one cycle on the context's stream: N TV
-// perturbation steps, then one block-DROP sweep P_T (Sec. II-D), then phi(x) in FP64.
+// perturbation steps, then one block-DROP sweep P_T (Sec. III-D), then phi(x) in FP64.
 // Without the TV check nothing waits on the device; with it the host reads each
 // accept decision (one small device-to-host copy per try).
 #include <algorithm>

@@ -11,7 +11,6 @@
 // that every GPU loading the library holds until the process exits.  The grid is fixed by
 // the image size (kVoxelsPerThread voxels per thread), so the largest image is
 // kStaticCtas * 256 * kVoxelsPerThread voxels; larger images are rejected.
-#include <mutex>
 #include <string>
 
 #include "common.cuh"
@@ -31,12 +30,8 @@ struct StaticScratch {
 };
 
 // Host code must not use this name as a device address: it is a host-side stand-in.
-// The device address comes from cudaGetSymbolAddress, once per device, below.
+// The device address comes from cudaGetSymbolAddress on every call, below.
 static __device__ __align__(256) StaticScratch g_static_scratch;
-
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-StaticScratch* g_scratch_addr[kMaxDevices] = {};
 
 int static_fail(int code, const std::string& msg) {
     set_last_error(msg);   // read back with ntvs_last_error()
@@ -66,22 +61,17 @@ tv_value_static_kernel(const T* __restrict__ x, int nx, int ny, int nz, StaticSc
     grid_reduce<1>(acc, scratch->partials, &scratch->ticket, outs);
 }
 
-// Device address of the static scratch on the current device, looked up once per device.
+// Device address of the static scratch in the current device's current context.  It is
+// looked up on every call (cudaGetSymbolAddress allocates nothing): each CUDA context
+// loads its own copy of the module, so an address kept from an earlier call could belong
+// to a context that has since been reset or is not the one current now.
 int scratch_address(StaticScratch** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return static_fail(NTVS_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return static_fail(NTVS_ERR_ARG, "device index above the supported 64");
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess || !p)
-            return static_fail(NTVS_ERR_CUDA, std::string("cudaGetSymbolAddress of the static TV scratch: ") +
-                                                  cudaGetErrorString(e));
-        g_scratch_addr[dev] = (StaticScratch*)p;
-    }
-    *out = g_scratch_addr[dev];
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p)
+        return static_fail(NTVS_ERR_CUDA, std::string("cudaGetSymbolAddress of the static TV scratch: ") +
+                                              cudaGetErrorString(e));
+    *out = (StaticScratch*)p;
     return NTVS_OK;
 }
 

@@ -1,8 +1,8 @@
 """Seeded synthetic proton-CT systems (input generator shared by the CUDA path and the oracle).
 
-The paper's data (Geant4-simulated and experimental CTP404 scans, Sec. II-C) are not
+The paper's data (Geant4-simulated and experimental CTP404 scans, Sec. III-C) are not
 available, so inputs are synthesised with the paper's geometry: 1x1x2.5 mm voxels and
-200x200 slices (Sec. II-D), a 150 mm cylinder with 12.2 mm inserts on a 120 mm circle
+200x200 slices (Sec. III-D), a 150 mm cylinder with 12.2 mm inserts on a 120 mm circle
 carrying the simulated RSPs of Table I, parallel projections over a full turn.
 
 Each history contributes one row a_i of intersection lengths through the voxel grid and

@@ -1,7 +1,7 @@
 /*
  * Seeded synthetic proton-CT system generator.
  *
- * Stand-in for the paper's Geant4 / experimental CTP404 data (Sec. II-C, Table I):
+ * Stand-in for the paper's Geant4 / experimental CTP404 data (Sec. III-C, Table I):
  * a cylinder phantom with cylindrical inserts is voxelised, proton histories are
  * drawn per projection angle, each history's path through the voxel grid is
  * traced (straight line, or a cubic-Hermite bent path split into straight

@@ -1,4 +1,4 @@
-"""Pins of the oracle's block-DROP step (P_T of Appendix C; DROP of ref. CEHN08, Sec. II-D).
+"""Pins of the oracle's block-DROP step (P_T of Appendix C; DROP of ref. CEHN08, Sec. III-D).
 
 Reading used: x_j += lambda/s_j * sum_{i in block} a_ij (b_i - <a_i,x>)/||a_i||^2,
 s_j = number of rows of the block with a_ij != 0.  Pins: exact projection for one-row

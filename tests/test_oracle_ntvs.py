@@ -1,8 +1,8 @@
-"""Pins of the oracle's NTVS loop (Appendix C) and its ell schedule (Sec. II-B, item 4).
+"""Pins of the oracle's NTVS loop (Appendix C) and its ell schedule (Sec. III-B, item 4).
 
 * SplitMix64: published first outputs of the stream seeded with 0 and an independent
   stateful Python SplitMix64.
-* ell_k = rand(k, ell_{k-1}): bounds, and ell_k = k for N = 1 without the check (Sec. II-B).
+* ell_k = rand(k, ell_{k-1}): bounds, and ell_k = k for N = 1 without the check (Sec. III-B).
 * N = 0 is plain DROP; the check variant with no rejection equals the variant without it;
   accepted perturbations never raise phi; a budget of one rejected try leaves x unchanged.
 """
