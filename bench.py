@@ -54,6 +54,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mixed", type=int, default=1, help="also time BF16 lengths + DELTA16 columns (0: skip)")
+    ap.add_argument("--fp64-arith", type=int, default=1,
+                    help="also time FP64 arithmetic on the FP32-stored system (0: skip)")
     ap.add_argument("--batched", type=int, default=1, help="also time the batched parameter sweep (0: skip)")
     ap.add_argument("--batch-members", type=int, default=64)
     ap.add_argument("--batch-scale", type=float, default=1.0)
@@ -63,7 +65,7 @@ def parse_args(argv=None):
     ap.add_argument("--canonical", type=int, default=1,
                     help="also time the canonical voxel order on the same workload (0: skip)")
     ap.add_argument("--check", type=int, default=1,
-                    help="also time the same workload with the TV-reduction check on (0: skip)")
+                    help="also time N = 6 and the TV-reduction check on (N in {3, 6}) (0: skip)")
     ap.add_argument("--cpu-rows", type=int, default=3_000_000, help="oracle sample: first rows of the workload")
     ap.add_argument("--ref-rows", type=int, default=1_000_000, help="reference arm: rows per step")
     ap.add_argument("--schedule", choices=["auto", "plain", "window", "pipeline"], default="auto",
@@ -484,56 +486,77 @@ def run_ntvs(args):
                "seconds_per_step": t_e2e, "load_seconds": statistics.mean(x for x, _ in split),
                "run_and_readback_seconds": statistics.mean(y for _, y in split)}
 
-    # ---- the same workload in the canonical voxel order, and mixed precision (FP32
-    # arithmetic): BF16 lengths with int32 or DELTA16 columns
+    # ---- variants on the same workload: canonical voxel order, N = 6 and the TV-reduction
+    # check (the 2 x 2 of N in {3, 6} x check off/on), FP64 arithmetic on the FP32-stored
+    # system, and mixed precision (FP32 arithmetic): BF16 lengths with int32 or DELTA16 columns
     variants = []
     cases = []
-    if args.canonical and vdt == np.float32 and tile != (1, 1):
-        cases.append(("fp32, canonical voxel order", s.val, ntvs.NTVS_CSR32, vsz, 4, (1, 1), PARAMS))
-    if args.check and vdt == np.float32:
-        cases.append(("fp32, TV-reduction check on", s.val, ntvs.NTVS_CSR32, vsz, 4, tile,
-                      dict(PARAMS, tv_check=True)))
-    if args.mixed and vdt == np.float32:
-        import torch as _t
-        vb = _t.from_numpy(s.val).to(_t.bfloat16)
-        cases.append(("bf16 lengths + int32 columns", vb, ntvs.NTVS_CSR32, 2, 4, tile, PARAMS))
-        cases.append(("bf16 lengths + delta16 columns", vb, ntvs.NTVS_DELTA16, 2, 2, tile, PARAMS))
-    if cases:
-        for name, vals, storage, vb_size, ib, vt, prm in cases:
-            rm = ntvs.Reconstructor(local, stream.cuda_stream).set_voxel_tile(*vt)
-            rm.load(shape, s.row_ptr, s.col, vals, b, n_blocks=spec.n_blocks, storage=storage, schedule=sched)
-            rm.set_params(**prm)
-            rm.set_image(x0)
-            stm = rm.stats()
-            rm.run(args.warmup)
-            rm.sync()
-            barrier(world, device)
-            torch.cuda.synchronize(device)
-            rm.set_profiling(True)
-            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            f0.record(stream)
-            for _ in range(args.steps):
-                rm.run(1)
-            f1.record(stream)
-            torch.cuda.synchronize(device)
-            msm = max_over_ranks(f0.elapsed_time(f1), world, device)
-            pm = rm.profile()
-            stf = rm.stats()
-            rm.close()
-            extra = 8 if storage == ntvs.NTVS_DELTA16 else 0
-            bytes_m = float(np.mean(algorithmic_drop_bytes(s, vb_size, 4, index_bytes=ib, extra_row_bytes=extra))) + \
-                8.0 * stm["n_escaped"] / spec.n_blocks
-            avg_m = pm["drop_block_ms"] / max(pm["drop_block_launches"], 1)
-            ach = bytes_m / (avg_m / 1e3) / 1e9
-            variants.append({"name": name, "value": world * spec.n_hist * args.steps / (msm / 1e3), "unit": UNIT,
-                             "ms_per_step": msm / args.steps, "vs_headline": ms / msm,
-                             "voxel_tile": f"{stm['voxel_tile_x']}x{stm['voxel_tile_y']}",
-                             "tries_per_step": stf["n_tries"] / max(stf["n_steps"], 1),
-                             "drop_schedule": {1: "plain", 2: "window", 3: "pipeline"}.get(stm["drop_schedule"]),
-                             "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                                          "frac": ach / peak, "algorithmic_bytes_per_launch": bytes_m,
-                                          "avg_launch_ms": avg_m}})
-        cases = vb = None
+
+    def case(name, **kw):
+        c = dict(name=name, vals=s.val, storage=ntvs.NTVS_CSR32, vb=vsz, ib=4, tile=tile, prm=PARAMS,
+                 compute=ntvs.NTVS_F32)
+        c.update(kw)
+        cases.append(c)
+
+    if vdt == np.float32:
+        if args.canonical and tile != (1, 1):
+            case("fp32, canonical voxel order", tile=(1, 1))
+        if args.check:
+            case("fp32, TV-reduction check on", prm=dict(PARAMS, tv_check=True))
+            case("fp32, N=6", prm=dict(PARAMS, N=6))
+            case("fp32, N=6, TV-reduction check on", prm=dict(PARAMS, N=6, tv_check=True))
+        if args.fp64_arith:
+            case("fp64 arithmetic on fp32 storage", compute=ntvs.NTVS_F64)
+        if args.mixed:
+            import torch as _t
+            vbf = _t.from_numpy(s.val).to(_t.bfloat16)
+            case("bf16 lengths + int32 columns", vals=vbf, vb=2)
+            case("bf16 lengths + delta16 columns", vals=vbf, vb=2, ib=2, storage=ntvs.NTVS_DELTA16)
+    for c in cases:
+        rm = ntvs.Reconstructor(local, stream.cuda_stream).set_voxel_tile(*c["tile"])
+        rm.set_compute_dtype(c["compute"])
+        rm.load(shape, s.row_ptr, s.col, c["vals"], b, n_blocks=spec.n_blocks, storage=c["storage"], schedule=sched)
+        rm.set_params(**c["prm"])
+        rm.set_image(x0)
+        stm = rm.stats()
+        rm.run(args.warmup)
+        rm.sync()
+        barrier(world, device)
+        torch.cuda.synchronize(device)
+        rm.set_profiling(True)
+        n0 = rm.stats()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            rm.run(1)
+        f1.record(stream)
+        torch.cuda.synchronize(device)
+        msm = max_over_ranks(f0.elapsed_time(f1), world, device)
+        pm = rm.profile()
+        stf = rm.stats()
+        rm.close()
+        extra = 8 if c["storage"] == ntvs.NTVS_DELTA16 else 0
+        b_item = 8 if stm["compute_dtype"] == ntvs.NTVS_F64 else 4   # b and 1/||a||^2 per row
+        bytes_m = float(np.mean(algorithmic_drop_bytes(s, c["vb"], b_item, index_bytes=c["ib"],
+                                                       extra_row_bytes=extra))) + \
+            8.0 * stm["n_escaped"] / spec.n_blocks
+        avg_m = pm["drop_block_ms"] / max(pm["drop_block_launches"], 1)
+        ach = bytes_m / (avg_m / 1e3) / 1e9
+        steps_done = max(stf["n_steps"] - n0["n_steps"], 1)
+        variants.append({"name": c["name"], "value": world * spec.n_hist * args.steps / (msm / 1e3), "unit": UNIT,
+                         "ms_per_step": msm / args.steps, "vs_headline": ms / msm,
+                         "N": c["prm"]["N"], "tv_check": bool(c["prm"].get("tv_check", False)),
+                         "compute_dtype": "f64" if stm["compute_dtype"] == ntvs.NTVS_F64 else "f32",
+                         "voxel_tile": f"{stm['voxel_tile_x']}x{stm['voxel_tile_y']}",
+                         "tries_per_step": (stf["n_tries"] - n0["n_tries"]) / steps_done,
+                         "drop_schedule": {1: "plain", 2: "window", 3: "pipeline"}.get(stm["drop_schedule"]),
+                         "gpu_launches_per_step": (stf["n_launches"] - n0["n_launches"]) / args.steps,
+                         "kernel_ms_per_step": {k: pm[k] / args.steps for k in ("drop_block_ms", "drop_apply_ms",
+                                                                                "tv_ms")},
+                         "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                                      "frac": ach / peak, "algorithmic_bytes_per_launch": bytes_m,
+                                      "avg_launch_ms": avg_m}})
+    cases = vbf = None
 
     # ---- batched reconstructions: a parameter sweep over members of uneven size
     if args.batched:

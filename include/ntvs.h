@@ -72,7 +72,8 @@ typedef struct {
     const int64_t* row_ptr;      /* [M+1], row_ptr[0] = 0, non-decreasing (mem_kind)          */
     const int32_t* col;          /* [nnz] voxel index in [0, V) (mem_kind)                    */
     const void* val;             /* [nnz] a_ij, type val_dtype (mem_kind)                     */
-    const void* b;               /* [M] WEPL, double if val_dtype == NTVS_F64 else float      */
+    const void* b;               /* [M] WEPL, double if val_dtype == NTVS_F64 else float
+                                    (also with ntvs_set_compute_dtype(NTVS_F64))             */
     const int64_t* block_ptr;    /* NULL or [B+1] HOST array, block t = rows [bp[t], bp[t+1]) */
     int32_t val_dtype;           /* NTVS_F64 (FP64 path) | NTVS_F32 (FP32 path) |
                                     NTVS_F16 / NTVS_BF16 (FP32 arithmetic on half storage)   */
@@ -250,8 +251,12 @@ int ntvs_get_image(ntvs_ctx* ctx, void* out, int dtype, int mem_kind);
  * ell_k = rand(k, ell_{k-1}); N perturbation steps x <- x + beta0*alpha^ell v, ell++
  * (with the check: retry with ell++ until phi(z) <= phi(x), at most max_retries tries,
  * beta recomputed after every try); then x <- P_T(x); then phi(x) in FP64.
- * Without the check the call only queues work; with it the host waits for each
- * check decision. */
+ * The call only queues work.  With the check (NTVS and OTVS rules) every decision is
+ * taken on the device: ell_k is drawn there and each step's retry loop runs in one
+ * cooperative kernel, so no try waits for the host; the traces, the counters of
+ * ntvs_get_stats and ell_{k-1} stay on the device until one of ntvs_get_stats,
+ * ntvs_get_trace, ntvs_get_state, ntvs_set_state or a run without the check needs them
+ * (one synchronization then). */
 int ntvs_run(ntvs_ctx* ctx, int k_iters);
 
 /* Wait for the context's stream. */
@@ -298,7 +303,35 @@ int ntvs_get_profile(ntvs_ctx* ctx, ntvs_profile* out);
  * NTVS_ERR_ARG on other sizes. */
 int ntvs_set_voxel_tile(ntvs_ctx* ctx, int tx, int ty);
 
+/* Arithmetic of systems loaded with FP32 values, applied at the next ntvs_load_system:
+ * NTVS_F32 (default) computes dot products, scatters, the TV gradient and the image
+ * copies in FP32 (FP64 only for the decision-making reductions); NTVS_F64 computes every
+ * step in FP64 on the FP32-stored values and b (b is widened to FP64 once at load), as the
+ * FP64 path does for FP64 storage, while the matrix streams at 8 bytes per entry.  FP64
+ * systems always use FP64 arithmetic and FP16/BF16 systems FP32 arithmetic (NTVS_F64
+ * leaves them unchanged).  Why the option exists: NTVS with a small eps_tv amplifies
+ * perturbations of the image below sqrt(eps_tv) from one cycle to the next, so FP32
+ * rounding (relative 6e-8 per operation) grows to ~1e-4 relative L2 after 12 cycles at
+ * eps_tv = 1e-8; the FP64 oracle itself moves as far when b is perturbed by 6e-8.  FP64
+ * arithmetic keeps the result within ~1e-10 of the FP64 reference.  This choice has no
+ * counterpart in the paper.  NTVS_ERR_ARG for other values. */
+int ntvs_set_compute_dtype(ntvs_ctx* ctx, int dtype);
+
 /* Test hook: replay ell_k for the next n cycles instead of drawing it (NULL clears). */
+
+/* Failure-detection test hook.  Every device-side wait of the library (the pipelined DROP
+ * kernel's mbarrier waits, the TV-check loop's grid barrier) gives up after wait_ns
+ * nanoseconds (wait_ns <= 0: the default, 2 s), records an error code and lets its CTA
+ * leave with no copy in flight; the next synchronizing call returns NTVS_ERR_TIMEOUT and
+ * the image of that run is invalid, while the context stays usable.  flags make a wait run
+ * out on purpose: NTVS_HOOK_STARVE_PIPE (the pipelined schedule's producer withholds the
+ * first stage of every CTA) and NTVS_HOOK_STARVE_CHECK (the first CTA of the TV-check
+ * loop withholds its first barrier arrival).  0 restores normal operation.  Nothing here
+ * has a counterpart in the paper.  NTVS_ERR_ARG for unknown flags. */
+#define NTVS_HOOK_STARVE_PIPE 1
+#define NTVS_HOOK_STARVE_CHECK 2
+int ntvs_set_fault_hook(ntvs_ctx* ctx, int64_t wait_ns, int flags);
+
 int ntvs_set_ell_override(ntvs_ctx* ctx, const int64_t* ell_k, int64_t n);
 
 /* ---- single steps of the hot path (same kernels as ntvs_run) ---------------------- */

@@ -230,6 +230,14 @@ def ntvs_set_voxel_tile(ctx: int, tx: int, ty: int) -> None:
     check(lib().ntvs_set_voxel_tile(ctx, int(tx), int(ty)), "ntvs_set_voxel_tile")
 
 
+def ntvs_set_compute_dtype(ctx: int, dtype: int) -> None:
+    check(lib().ntvs_set_compute_dtype(ctx, int(dtype)), "ntvs_set_compute_dtype")
+
+
+def ntvs_set_fault_hook(ctx: int, wait_ns: int, flags: int) -> None:
+    check(lib().ntvs_set_fault_hook(ctx, int(wait_ns), int(flags)), "ntvs_set_fault_hook")
+
+
 def ntvs_set_ell_override(ctx: int, ell) -> None:
     if ell is None:
         check(lib().ntvs_set_ell_override(ctx, None, 0), "ntvs_set_ell_override")
@@ -518,6 +526,16 @@ class Reconstructor:
     def set_voxel_tile(self, tx: int, ty: int):
         """Internal voxel tile of the FP32 path, applied at the next load."""
         ntvs_set_voxel_tile(self._ctx, tx, ty)
+        return self
+
+    def set_compute_dtype(self, dtype: int):
+        """Arithmetic (NTVS_F32 or NTVS_F64) of FP32-stored systems, applied at the next load."""
+        ntvs_set_compute_dtype(self._ctx, dtype)
+        return self
+
+    def set_fault_hook(self, wait_ns: int = 0, flags: int = 0):
+        """Budget of every bounded device wait and the test flags that starve one."""
+        ntvs_set_fault_hook(self._ctx, wait_ns, flags)
         return self
 
     def tv_gradient(self, dtype=np.float64):

@@ -25,6 +25,7 @@ NTVS_MEM_HOST, NTVS_MEM_DEVICE = 0, 1
 NTVS_CSR32, NTVS_DELTA16 = 0, 1
 NTVS_SCHED_AUTO, NTVS_SCHED_PLAIN, NTVS_SCHED_WINDOW, NTVS_SCHED_PIPELINE, NTVS_SCHED_ONTHEFLY = 0, 1, 2, 3, 4
 NTVS_STEP_NTVS, NTVS_STEP_OTVS, NTVS_STEP_DECOUPLED = 0, 1, 2
+NTVS_HOOK_STARVE_PIPE, NTVS_HOOK_STARVE_CHECK = 1, 2
 
 ERROR_NAMES = {NTVS_ERR_ARG: "NTVS_ERR_ARG", NTVS_ERR_CSR: "NTVS_ERR_CSR", NTVS_ERR_OOM: "NTVS_ERR_OOM",
                NTVS_ERR_CUDA: "NTVS_ERR_CUDA", NTVS_ERR_TIMEOUT: "NTVS_ERR_TIMEOUT",
@@ -111,6 +112,8 @@ SIGNATURES = {
     "ntvs_set_ell_override": (ctypes.c_int, [vp, vp, i64]),
     "ntvs_set_profiling": (ctypes.c_int, [vp, ctypes.c_int]),
     "ntvs_set_voxel_tile": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
+    "ntvs_set_compute_dtype": (ctypes.c_int, [vp, ctypes.c_int]),
+    "ntvs_set_fault_hook": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.c_int]),
     "ntvs_get_profile": (ctypes.c_int, [vp, P(ntvs_profile)]),
     "ntvs_tv_gradient": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P(d)]),
     "ntvs_perturb": (ctypes.c_int, [vp, d]),

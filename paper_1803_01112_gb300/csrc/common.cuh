@@ -48,6 +48,13 @@ __device__ __forceinline__ void store_copies(const ImgCopies& c, int64_t j, doub
     }
 }
 
+// %globaltimer in nanoseconds (the clock of every bounded device-side wait)
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // inclusive prefix sum over the 32 lanes of a warp
 __device__ __forceinline__ int warp_inclusive_scan(int v) {
     const int lane = threadIdx.x & 31;

@@ -385,8 +385,9 @@ cudaError_t k_drop_block(const DropArgs& a, cudaStream_t s) {
     if (a.r1 <= a.r0) return cudaSuccess;
     if (a.use_d16) {
         if (a.segs) {   // windowed: a warp per row, 12 register chunks
-            if (a.cdt == F64) return a.vdt == F64 ? launch_window<double, double, 32, 12, 1, true>(a, s)
-                                                  : cudaErrorInvalidValue;
+            if (a.cdt == F64) return a.vdt == F64   ? launch_window<double, double, 32, 12, 1, true>(a, s)
+                                     : a.vdt == F32 ? launch_window<double, float, 32, 12, 1, true>(a, s)
+                                                    : cudaErrorInvalidValue;
             switch (a.vdt) {
                 case F32: return launch_window<float, float, 32, 12, 1, true>(a, s);
                 case F16: return launch_window<float, __half, 32, 12, 1, true>(a, s);
@@ -394,7 +395,8 @@ cudaError_t k_drop_block(const DropArgs& a, cudaStream_t s) {
                 default: return cudaErrorInvalidValue;
             }
         }
-        if (a.cdt == F64) return a.vdt == F64 ? launch_d16<double, double>(a, s) : cudaErrorInvalidValue;
+        if (a.cdt == F64) return a.vdt == F64 ? launch_d16<double, double>(a, s)
+                                              : a.vdt == F32 ? launch_d16<double, float>(a, s) : cudaErrorInvalidValue;
         switch (a.vdt) {
             case F32: return launch_d16<float, float>(a, s);
             case F16: return launch_d16<float, __half>(a, s);
@@ -402,9 +404,11 @@ cudaError_t k_drop_block(const DropArgs& a, cudaStream_t s) {
             default: return cudaErrorInvalidValue;
         }
     }
-    if (a.cdt == F64) {
-        if (a.vdt != F64 || a.vector4) return cudaErrorInvalidValue;
-        return dispatch<double, double>(a, s);
+    if (a.cdt == F64) {   // FP64 arithmetic on FP64 or FP32 storage
+        if (a.vector4) return cudaErrorInvalidValue;
+        if (a.vdt == F64) return dispatch<double, double>(a, s);
+        if (a.vdt == F32) return dispatch<double, float>(a, s);
+        return cudaErrorInvalidValue;
     }
     switch (a.vdt) {
         case F32: return dispatch<float, float>(a, s);

@@ -14,9 +14,11 @@
 // A consumer releases a slot by arriving on its "empty" mbarrier.  When the home slice
 // changes the consumers meet on a third mbarrier and flush the window.
 //
-// Every wait is bounded by a %globaltimer deadline: on expiry the thread records an
-// error code (read by the host as NTVS_ERR_TIMEOUT) and leaves, and the producer waits
-// (again bounded) for its own copies in flight before it exits.
+// Every wait is bounded by a %globaltimer deadline (a runtime budget, 2 s by default): on
+// expiry the thread records an error code (read by the host as NTVS_ERR_TIMEOUT) and
+// leaves, and the producer waits (again bounded) for each of its own copies in flight
+// before it exits.  A test hook makes the producer withhold every CTA's first stage, so
+// that the waits on it run out.
 #include "common.cuh"
 
 namespace ntvs {
@@ -27,15 +29,9 @@ constexpr int kStages = 4;                      // ring slots
 constexpr int kDescBatch = 32;                  // stage descriptors fetched per bulk copy
 constexpr int kThreads = 1024;
 constexpr int kConsumers = kThreads / 32 - 1;   // 31 consumer warps
-constexpr uint64_t kWaitNs = 2000000000ull;     // 2 s per wait
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ uint64_t now_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
 }
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
@@ -57,12 +53,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait for the phase with the given parity; false (and *err set) on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
+// Bounded wait (wait_ns) for the phase with the given parity; false (and *err set) on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code, uint64_t wait_ns) {
     if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = now_ns();
+    const uint64_t t0 = globaltimer_ns();
     while (!mbar_try_wait(bar, parity)) {
-        if (now_ns() - t0 > kWaitNs) {
+        if (globaltimer_ns() - t0 > wait_ns) {
             atomicExch(err, code);
             return false;
         }
@@ -153,7 +149,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 drop_pipe_kernel(const int64_t* __restrict__ row_ptr, const IdxT* __restrict__ col, const V* __restrict__ val,
                  const T* __restrict__ b, const T* __restrict__ inv_norm2, const DropStage* __restrict__ stages,
                  const int32_t* __restrict__ stage_begin, int64_t slice, int S, const T* __restrict__ x,
-                 T* __restrict__ delta, T lambda, double* resid_ss, int* err, Delta16 d16) {
+                 T* __restrict__ delta, T lambda, double* resid_ss, int* err, uint64_t wait_ns, int starve,
+                 Delta16 d16) {
     constexpr bool kD16 = sizeof(IdxT) == 2;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int W = (int)slice;
@@ -205,16 +202,18 @@ drop_pipe_kernel(const int64_t* __restrict__ row_ptr, const IdxT* __restrict__ c
             for (; k < n; ++k) {
                 const int m = k / kDescBatch;
                 if (k % kDescBatch == 0) {
-                    ok = mbar_wait(dbar + (m & 1), (m >> 1) & 1, err, 6);
+                    ok = mbar_wait(dbar + (m & 1), (m >> 1) & 1, err, 6, wait_ns);
                     if (!ok) break;
                     waited_b = m + 1;
                 }
                 const int slot = k % kStages;
-                if (k >= kStages && !(ok = mbar_wait(empty + slot, ((k / kStages) - 1) & 1, err, 1))) break;
+                if (k >= kStages && !(ok = mbar_wait(empty + slot, ((k / kStages) - 1) & 1, err, 1, wait_ns))) break;
                 // every consumer is past stage 32m - 1: batch m - 1's buffer may take batch m + 1
                 if (k % kDescBatch == kStages - 1 && m >= 1 && m + 1 < nb) { load_batch(m + 1); issued_b = m + 2; }
                 const DropStage& st = desc[(m & 1) * kDescBatch + (k % kDescBatch)];
-                if (st.nent > 0) {
+                if (k == 0 && starve) {
+                    // test hook: stage 0 is withheld, so every wait on it runs out
+                } else if (st.nent > 0) {
                     const uint32_t bc = (uint32_t)st.nent * (uint32_t)sizeof(IdxT);
                     const uint32_t bv = (uint32_t)st.nent * (uint32_t)sizeof(V);
                     mbar_arrive_expect_tx(full + slot, bc + bv);
@@ -224,11 +223,12 @@ drop_pipe_kernel(const int64_t* __restrict__ row_ptr, const IdxT* __restrict__ c
                     mbar_arrive(full + slot);   // rows read straight from global memory
                 }
             }
-            // copies possibly still landing: the last issued stages and unconsumed batches
+            // copies possibly still landing: the last issued stages and unconsumed batches; every
+            // one is waited for (bounded) even after another wait ran out, so no copy is in
+            // flight when the CTA exits (a withheld stage has none)
             for (int j = (k > kStages ? k - kStages : 0); j < k; ++j)
-                if (!mbar_wait(full + (j % kStages), (j / kStages) & 1, err, 2)) break;
-            for (int m = waited_b; m < issued_b; ++m)
-                if (!mbar_wait(dbar + (m & 1), (m >> 1) & 1, err, 7)) break;
+                if (!(j == 0 && starve)) mbar_wait(full + (j % kStages), (j / kStages) & 1, err, 2, wait_ns);
+            for (int m = waited_b; m < issued_b; ++m) mbar_wait(dbar + (m & 1), (m >> 1) & 1, err, 7, wait_ns);
             (void)ok;
         }
         return;
@@ -246,7 +246,7 @@ drop_pipe_kernel(const int64_t* __restrict__ row_ptr, const IdxT* __restrict__ c
     bool ok = true;
     for (int k = 0; k < n && ok; ++k) {
         const int slot = k % kStages;
-        ok = mbar_wait(full + slot, (k / kStages) & 1, err, 4);
+        ok = mbar_wait(full + slot, (k / kStages) & 1, err, 4, wait_ns);
         if (!ok) break;
         const DropStage& st = desc[((k / kDescBatch) & 1) * kDescBatch + (k % kDescBatch)];
         const int home = st.home, nrows = st.nrows, nent = st.nent;
@@ -255,13 +255,13 @@ drop_pipe_kernel(const int64_t* __restrict__ row_ptr, const IdxT* __restrict__ c
             if (cur >= 0) {   // flush the window of the previous slice (all consumers)
                 __syncwarp();
                 if (lane == 0) mbar_arrive(cbar);
-                ok = mbar_wait(cbar, cphase & 1, err, 3);
+                ok = mbar_wait(cbar, cphase & 1, err, 3, wait_ns);
                 cphase++;
                 if (!ok) break;
                 flush_w(win, Wp, delta, (int64_t)cur * slice, ctid, cthreads);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(cbar);
-                ok = mbar_wait(cbar, cphase & 1, err, 3);
+                ok = mbar_wait(cbar, cphase & 1, err, 3, wait_ns);
                 cphase++;
                 if (!ok) break;
             }
@@ -299,7 +299,7 @@ drop_pipe_kernel(const int64_t* __restrict__ row_ptr, const IdxT* __restrict__ c
     if (ok && cur >= 0) {
         __syncwarp();
         if (lane == 0) mbar_arrive(cbar);
-        if (mbar_wait(cbar, cphase & 1, err, 5)) flush_w(win, Wp, delta, (int64_t)cur * slice, ctid, cthreads);
+        if (mbar_wait(cbar, cphase & 1, err, 5, wait_ns)) flush_w(win, Wp, delta, (int64_t)cur * slice, ctid, cthreads);
     }
     if (lane == 0 && ss != 0.0) atomicAdd(resid_ss, ss);
 }
@@ -327,7 +327,8 @@ static cudaError_t launch_pipe_idx(const DropPipeArgs& a, const IdxT* col, cudaS
     if (e != cudaSuccess) return e;
     kern<<<a.grid, kThreads, smem, s>>>(a.row_ptr, col, (const V*)a.val, (const T*)a.b, (const T*)a.inv_norm2,
                                          a.stages, a.stage_begin, a.slice, pipe_stage_entries(a.vdt, sizeof(IdxT)),
-                                         (const T*)a.x, (T*)a.delta, (T)a.lambda, a.resid_ss, a.err, a.d16);
+                                         (const T*)a.x, (T*)a.delta, (T)a.lambda, a.resid_ss, a.err, a.wait_ns,
+                                         a.starve, a.d16);
     return cudaGetLastError();
 }
 
@@ -338,9 +339,10 @@ static cudaError_t launch_pipe(const DropPipeArgs& a, cudaStream_t s) {
 }
 
 cudaError_t k_drop_pipe(const DropPipeArgs& a, cudaStream_t s) {
-    if (a.cdt == F64) {
-        if (a.vdt != F64) return cudaErrorInvalidValue;
-        return launch_pipe<double, double>(a, s);
+    if (a.cdt == F64) {   // FP64 arithmetic on FP64 or FP32 storage
+        if (a.vdt == F64) return launch_pipe<double, double>(a, s);
+        if (a.vdt == F32) return launch_pipe<double, float>(a, s);
+        return cudaErrorInvalidValue;
     }
     switch (a.vdt) {
         case F32: return launch_pipe<float, float>(a, s);

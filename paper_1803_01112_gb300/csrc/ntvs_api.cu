@@ -23,6 +23,9 @@ namespace {
 
 thread_local std::string g_err;
 
+constexpr uint64_t kDefaultWaitNs = 2000000000ull;   // 2 s per bounded device wait
+constexpr int kBetaTab = 4096;                        // step sizes tabulated on the host
+
 int fail(int code, const std::string& msg) {
     g_err = msg;
     return code;
@@ -82,6 +85,7 @@ struct ntvs_ctx {
     // internal voxel order of x32, delta, inv_s and the stored columns (FP32 path)
     VoxMap vm{};
     int tile_req_x = 4, tile_req_y = 4;   // applied at the next load
+    int compute_req = F32;                // arithmetic of FP32-stored systems, applied at the next load
     int vdt = F32, cdt = F32, storage = NTVS_CSR32;
     std::vector<int64_t> block_ptr;
     int64_t* row_ptr = nullptr;
@@ -132,6 +136,25 @@ struct ntvs_ctx {
     int64_t tvcap = 0;
     double* hscal = nullptr;   // pinned [8]
     int* hint = nullptr;       // pinned [4]
+    int64_t* hll = nullptr;    // pinned [4]
+
+    // TV check decided on the device: ell and the traces stay on the device while runs are
+    // queued; the host pulls them (one synchronization) when it needs them
+    CheckState* cstate = nullptr;
+    int64_t* dev_ell_tr = nullptr;    // ell_k per cycle, indexed like ell_trace
+    int32_t* dev_tries = nullptr;     // per step, indexed like tries_trace
+    int32_t* dev_acc = nullptr;
+    int64_t dtr_cap_k = 0, dtr_cap_s = 0;
+    bool dev_pending = false;         // cycles [pend_k0, ell_trace.size()) still on the device
+    int64_t pend_k0 = 0, pend_s0 = 0;
+    bool dstate_valid = false;        // device ell == ell_prev
+    double* beta_tab = nullptr;       // beta0 * alpha^ell, ell < kBetaTab (host-computed)
+    double tab_beta0 = -1.0, tab_alpha = -1.0;
+    int check_grid = 0;               // co-resident grid of the retry loop (0: host decisions)
+
+    // bounded device waits: budget per wait and the test hook that starves a wait
+    uint64_t wait_ns = kDefaultWaitNs;
+    int hook_flags = 0;
 
     // parameters and state
     ntvs_params p{};
@@ -261,8 +284,9 @@ int check_device_error(ntvs_ctx* c) {
     if (code) {
         CUDA_TRY(cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream));
         CUDA_TRY(cudaStreamSynchronize(c->stream));
-        return fail(NTVS_ERR_TIMEOUT, "a bounded wait in the pipelined DROP kernel ran out (code " +
-                                          std::to_string(code) + "); the image of this run is invalid");
+        return fail(NTVS_ERR_TIMEOUT, std::string("a bounded device wait ran out (") +
+                                          (code == kErrCheckBarrier ? "TV-check loop barrier" : "pipelined DROP kernel") +
+                                          ", code " + std::to_string(code) + "); the image of this run is invalid");
     }
     return NTVS_OK;
 }
@@ -322,6 +346,118 @@ int checked_try(ntvs_ctx* c, double beta, int* acc) {
     CUDA_TRY(cudaMemcpyAsync(c->hint, c->daccept, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     *acc = c->hint[0];
+    return NTVS_OK;
+}
+
+// Brings the traces, counters and ell of device-decided cycles to the host (one stream
+// synchronization); a no-op when nothing is pending.
+int pull_device_trace(ntvs_ctx* c) {
+    if (!c->dev_pending) return NTVS_OK;
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->dev_pending = false;
+    const int rc = check_device_error(c);
+    if (rc != NTVS_OK) {   // the traces of the failed run stay zero; the host's ell is kept
+        c->dstate_valid = false;
+        return rc;
+    }
+    const int64_t nk = (int64_t)c->ell_trace.size() - c->pend_k0;
+    const int64_t ns = (int64_t)c->tries_trace.size() - c->pend_s0;
+    if (nk > 0)
+        CUDA_TRY(cudaMemcpy(c->ell_trace.data() + c->pend_k0, c->dev_ell_tr + c->pend_k0, sizeof(int64_t) * nk,
+                            cudaMemcpyDeviceToHost));
+    if (ns > 0) {
+        CUDA_TRY(cudaMemcpy(c->tries_trace.data() + c->pend_s0, c->dev_tries + c->pend_s0, sizeof(int32_t) * ns,
+                            cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpy(c->acc_trace.data() + c->pend_s0, c->dev_acc + c->pend_s0, sizeof(int32_t) * ns,
+                            cudaMemcpyDeviceToHost));
+    }
+    for (int64_t q = c->pend_s0; q < (int64_t)c->tries_trace.size(); ++q) {
+        c->n_tries += c->tries_trace[q];
+        c->n_accepted += c->acc_trace[q];
+    }
+    CUDA_TRY(cudaMemcpy(c->hll, &c->cstate->ell, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    c->ell_prev = c->hll[0];
+    c->dstate_valid = true;
+    return NTVS_OK;
+}
+
+// Device-side set-up before k_iters checked cycles: trace capacity, the step-size table of
+// the current (beta0, alpha), and the device ell when the host holds the current one.
+int prepare_device_check(ntvs_ctx* c, int k_iters) {
+    const int64_t need_k = (int64_t)c->ell_trace.size() + k_iters;
+    const int64_t need_s = (int64_t)c->tries_trace.size() + (int64_t)k_iters * c->p.N;
+    if (need_k > c->dtr_cap_k || need_s > c->dtr_cap_s) {
+        TRY(pull_device_trace(c));   // nothing pending: the old buffers need no copy
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        int64_t ck = std::max<int64_t>(c->dtr_cap_k, 1024), cs = std::max<int64_t>(c->dtr_cap_s, 4096);
+        while (ck < need_k) ck *= 2;
+        while (cs < need_s) cs *= 2;
+        dev_free(c->dev_ell_tr);
+        dev_free(c->dev_tries);
+        dev_free(c->dev_acc);
+        c->dtr_cap_k = c->dtr_cap_s = 0;
+        TRY(dev_alloc(&c->dev_ell_tr, sizeof(int64_t) * (size_t)ck, "ell trace"));
+        TRY(dev_alloc(&c->dev_tries, sizeof(int32_t) * (size_t)cs, "tries trace"));
+        TRY(dev_alloc(&c->dev_acc, sizeof(int32_t) * (size_t)cs, "accept trace"));
+        c->dtr_cap_k = ck;
+        c->dtr_cap_s = cs;
+    }
+    if (c->tab_beta0 != c->p.beta0 || c->tab_alpha != c->p.alpha) {
+        CUDA_TRY(cudaStreamSynchronize(c->stream));   // the table may still be read by queued work
+        std::vector<double> tab(kBetaTab);
+        for (int l = 0; l < kBetaTab; ++l) tab[l] = step_beta(c->p, 0, 0, l);
+        CUDA_TRY(cudaMemcpy(c->beta_tab, tab.data(), sizeof(double) * kBetaTab, cudaMemcpyHostToDevice));
+        c->tab_beta0 = c->p.beta0;
+        c->tab_alpha = c->p.alpha;
+    }
+    if (!c->dstate_valid) {
+        c->hll[0] = c->ell_prev;
+        CUDA_TRY(cudaMemcpyAsync(&c->cstate->ell, c->hll, sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        c->dstate_valid = true;
+    }
+    if (!c->dev_pending) {
+        c->pend_k0 = (int64_t)c->ell_trace.size();
+        c->pend_s0 = (int64_t)c->tries_trace.size();
+        c->dev_pending = true;
+    }
+    return NTVS_OK;
+}
+
+// N checked steps of cycle k with every decision on the device (ell drawn at cycle start
+// by the caller): per step the gradient pass and one cooperative retry loop.
+int perturb_steps_device(ntvs_ctx* c) {
+    for (int n = 0; n < c->p.N; ++n) {
+        TRY(launch_grad(c, true));
+        const int64_t sidx = (int64_t)c->tries_trace.size();
+        CheckLoopArgs a;
+        a.cdt = c->cdt;
+        a.x = c->x;
+        a.copies = c->copies();
+        a.g = c->g;
+        a.gnorm2 = c->dscal + 0;
+        a.phi_x = c->dscal + 1;
+        a.st = c->cstate;
+        a.beta_tab = c->beta_tab;
+        a.tab_len = kBetaTab;
+        a.beta0 = c->p.beta0;
+        a.alpha = c->p.alpha;
+        a.max_retries = c->p.max_retries;
+        a.partials = c->red.partials;
+        a.grid = std::max(1, std::min(c->red.grid, c->check_grid));
+        a.err = c->derr;
+        a.wait_ns = c->wait_ns;
+        a.starve = (c->hook_flags & NTVS_HOOK_STARVE_CHECK) ? 1 : 0;
+        a.tries_out = c->dev_tries + sidx;
+        a.acc_out = c->dev_acc + sidx;
+        a.nx = c->nx;
+        a.ny = c->ny;
+        a.nz = c->nz;
+        CUDA_TRY(timed_launch(c, KIND_TV, [&] { return k_tv_check_loop(a, c->stream); }));
+        c->tries_trace.push_back(0);   // filled by pull_device_trace
+        c->acc_trace.push_back(0);
+        c->n_steps += 1;
+    }
     return NTVS_OK;
 }
 
@@ -425,6 +561,8 @@ int drop_block(ntvs_ctx* c, int t) {
         pa.lambda = c->p.lambda;
         pa.resid_ss = c->resid + t;
         pa.err = c->derr;
+        pa.wait_ns = c->wait_ns;
+        pa.starve = (c->hook_flags & NTVS_HOOK_STARVE_PIPE) ? 1 : 0;
         pa.vdt = c->vdt;
         pa.cdt = c->cdt;
         pa.grid = c->win_grid;
@@ -734,7 +872,9 @@ int ntvs_create(ntvs_ctx** out, int device, void* cuda_stream) {
         (rc = dev_alloc(&c->dscal, sizeof(double) * 8, "scalars")) ||
         (rc = dev_alloc(&c->daccept, sizeof(int) * 4, "accept flag")) ||
         (rc = dev_alloc(&c->dflags, sizeof(int) * 4, "flags")) ||
-        (rc = dev_alloc(&c->derr, sizeof(int), "error word"))) {
+        (rc = dev_alloc(&c->derr, sizeof(int), "error word")) ||
+        (rc = dev_alloc(&c->cstate, sizeof(CheckState), "check state")) ||
+        (rc = dev_alloc(&c->beta_tab, sizeof(double) * kBetaTab, "step-size table"))) {
         ntvs_destroy(c);
         return rc;
     }
@@ -743,6 +883,8 @@ int ntvs_create(ntvs_ctx** out, int device, void* cuda_stream) {
     if (e2 == cudaSuccess) e2 = cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream);
     cudaError_t e3 = cudaHostAlloc((void**)&c->hscal, sizeof(double) * 8, cudaHostAllocDefault);
     cudaError_t e4 = cudaHostAlloc((void**)&c->hint, sizeof(int) * 4, cudaHostAllocDefault);
+    if (e4 == cudaSuccess) e4 = cudaHostAlloc((void**)&c->hll, sizeof(int64_t) * 4, cudaHostAllocDefault);
+    if (e4 == cudaSuccess) e4 = cudaMemsetAsync(c->cstate, 0, sizeof(CheckState), c->stream);
     cudaError_t e5 = cudaStreamSynchronize(c->stream);
     if (e1 || e2 || e3 || e4 || e5) {
         ntvs_destroy(c);
@@ -772,6 +914,12 @@ int ntvs_destroy(ntvs_ctx* c) {
     dev_free(c->dflags);
     dev_free(c->derr);
     dev_free(c->tvhist);
+    dev_free(c->cstate);
+    dev_free(c->beta_tab);
+    dev_free(c->dev_ell_tr);
+    dev_free(c->dev_tries);
+    dev_free(c->dev_acc);
+    if (c->hll) cudaFreeHost(c->hll);
     for (auto& t : c->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
     for (auto e : c->event_pool) cudaEventDestroy(e);
     if (c->hscal) cudaFreeHost(c->hscal);
@@ -818,7 +966,7 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
     c->B = (int)bp.size() - 1;
     c->block_ptr = bp;
     c->vdt = s->val_dtype;
-    c->cdt = (s->val_dtype == NTVS_F64) ? F64 : F32;
+    c->cdt = (s->val_dtype == NTVS_F64 || (s->val_dtype == NTVS_F32 && c->compute_req == F64)) ? F64 : F32;
     c->storage = s->storage;
     // the FP64 path gathers the canonical master image: no internal order there
     c->vm = (c->cdt == F32) ? make_voxmap(s->nx, s->ny, s->nz, c->tile_req_x, c->tile_req_y)
@@ -843,7 +991,21 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
     const size_t vsz = dt_size(c->vdt), csz = c->csz();
     TRY(copy_in((void**)&c->row_ptr, &c->own_row_ptr, s->row_ptr, sizeof(int64_t) * (size_t)(M + 1), s->mem_kind, st,
                 "row_ptr"));
-    TRY(copy_in(&c->b, &c->own_b, s->b, csz * (size_t)M, s->mem_kind, st, "b"));
+    if (dt_size(c->vdt) == csz || c->vdt != NTVS_F32) {
+        TRY(copy_in(&c->b, &c->own_b, s->b, csz * (size_t)M, s->mem_kind, st, "b"));
+    } else {   // FP64 arithmetic on FP32 storage: b arrives as float and is widened once
+        TRY(dev_alloc(&c->b, sizeof(double) * (size_t)M, "b (FP64)"));
+        c->own_b = true;
+        if (M > 0 && s->mem_kind == NTVS_MEM_DEVICE) {
+            CUDA_TRY(k_convert(s->b, F32, c->b, F64, M, st));
+        } else if (M > 0) {
+            std::vector<double> tmp((size_t)M);
+            const float* bf = (const float*)s->b;
+            for (int64_t i = 0; i < M; ++i) tmp[(size_t)i] = (double)bf[i];
+            CUDA_TRY(cudaMemcpyAsync(c->b, tmp.data(), sizeof(double) * (size_t)M, cudaMemcpyHostToDevice, st));
+            CUDA_TRY(cudaStreamSynchronize(st));
+        }
+    }
     // Host arrays: col and val are copied block by block on the copy stream, and each
     // block's preparation (on the context's stream) starts once its entries have arrived,
     // so the preparation hides behind the host-to-device copy.  Block t's entry range
@@ -973,6 +1135,9 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
     c->tries_trace.clear();
     c->acc_trace.clear();
     c->n_steps = c->n_accepted = c->n_tries = 0;
+    c->dev_pending = false;
+    c->dstate_valid = false;
+    c->check_grid = check_loop_max_grid(c->cdt, c->sms);
     CUDA_TRY(cudaStreamSynchronize(st));
     c->split_stale = false;
     c->loaded = true;
@@ -1077,6 +1242,9 @@ int ntvs_load_paths(ntvs_ctx* c, const ntvs_paths* s) {
     c->tries_trace.clear();
     c->acc_trace.clear();
     c->n_steps = c->n_accepted = c->n_tries = 0;
+    c->dev_pending = false;
+    c->dstate_valid = false;
+    c->check_grid = check_loop_max_grid(c->cdt, c->sms);
     CUDA_TRY(cudaStreamSynchronize(st));
     c->split_stale = false;
     c->loaded = true;
@@ -1200,13 +1368,32 @@ int ntvs_run(ntvs_ctx* c, int k_iters) {
     TRY(need_system(c));
     if (k_iters < 0) return fail(NTVS_ERR_ARG, "k_iters < 0");
     TRY(ensure_tvhist(c, c->k + k_iters));
+    // with the TV check every decision (and ell) stays on the device; without it the host
+    // knows ell at every step and draws it itself
+    const bool dev_check = c->p.tv_check && c->check_grid > 0 && c->p.step_rule != NTVS_STEP_DECOUPLED;
+    if (dev_check) TRY(prepare_device_check(c, k_iters));
+    else TRY(pull_device_trace(c));
     for (int kk = 0; kk < k_iters; ++kk) {
-        int64_t ell;
-        if (c->override_pos < c->override_ell.size()) ell = c->override_ell[c->override_pos++];
-        else ell = cycle_ell(c->p, c->k, c->ell_prev);
-        c->ell_trace.push_back(ell);
-        TRY(perturb_steps(c, &ell));
-        if (ell_advances(c->p)) c->ell_prev = ell;
+        if (dev_check) {
+            const bool has = c->override_pos < c->override_ell.size();
+            const int64_t ov = has ? c->override_ell[c->override_pos++] : 0;
+            int64_t* slot = c->dev_ell_tr + (int64_t)c->ell_trace.size();
+            CUDA_TRY(timed_launch(c, KIND_TV, [&] {
+                return k_check_cycle_begin(c->cstate, c->p.step_rule, c->p.seed, c->k, has, ov, slot, c->stream);
+            }));
+            c->ell_trace.push_back(0);   // filled by pull_device_trace
+            TRY(perturb_steps_device(c));
+        } else {
+            int64_t ell;
+            if (c->override_pos < c->override_ell.size()) ell = c->override_ell[c->override_pos++];
+            else ell = cycle_ell(c->p, c->k, c->ell_prev);
+            c->ell_trace.push_back(ell);
+            TRY(perturb_steps(c, &ell));
+            if (ell_advances(c->p)) {
+                c->ell_prev = ell;
+                c->dstate_valid = false;
+            }
+        }
         TRY(drop_sweep(c));
         CUDA_TRY(timed_launch(c, KIND_TV, [&] {
             return k_tv_value(c->cdt, c->x, nullptr, c->dscal, 0.0, c->nx, c->ny, c->nz, c->red, c->tvhist + c->k,
@@ -1240,6 +1427,7 @@ int ntvs_get_tv(ntvs_ctx* c, double* tv) {
 int ntvs_get_stats(ntvs_ctx* c, ntvs_stats* st) {
     TRY(use_device(c));
     if (!st) return fail(NTVS_ERR_ARG, "null output");
+    TRY(pull_device_trace(c));
     std::memset(st, 0, sizeof(*st));
     st->k = c->k;
     st->ell_prev = c->ell_prev;
@@ -1277,7 +1465,8 @@ int ntvs_get_block_resid(ntvs_ctx* c, double* out, int cap) {
 }
 
 int ntvs_get_trace(ntvs_ctx* c, int64_t* ell_k, int32_t* tries, int32_t* accepted, int64_t cap, int64_t* n_cycles) {
-    if (!c) return fail(NTVS_ERR_ARG, "null context");
+    TRY(use_device(c));
+    TRY(pull_device_trace(c));
     const int64_t nk = (int64_t)c->ell_trace.size();
     const int64_t ns = (int64_t)c->tries_trace.size();
     if (ell_k) for (int64_t i = 0; i < nk && i < cap; ++i) ell_k[i] = c->ell_trace[i];
@@ -1288,17 +1477,20 @@ int ntvs_get_trace(ntvs_ctx* c, int64_t* ell_k, int32_t* tries, int32_t* accepte
 }
 
 int ntvs_get_state(ntvs_ctx* c, int64_t* k, int64_t* ell_prev) {
-    if (!c) return fail(NTVS_ERR_ARG, "null context");
+    TRY(use_device(c));
+    TRY(pull_device_trace(c));
     if (k) *k = c->k;
     if (ell_prev) *ell_prev = c->ell_prev;
     return NTVS_OK;
 }
 
 int ntvs_set_state(ntvs_ctx* c, int64_t k, int64_t ell_prev) {
-    if (!c) return fail(NTVS_ERR_ARG, "null context");
+    TRY(use_device(c));
     if (k < 0 || ell_prev < 0) return fail(NTVS_ERR_ARG, "k and ell_prev must be >= 0");
+    TRY(pull_device_trace(c));
     c->k = k;
     c->ell_prev = ell_prev;
+    c->dstate_valid = false;
     return NTVS_OK;
 }
 
@@ -1333,6 +1525,21 @@ int ntvs_set_voxel_tile(ntvs_ctx* c, int tx, int ty) {
     if (!ok(tx) || !ok(ty)) return fail(NTVS_ERR_ARG, "tile sizes must be 1, 2, 4, 8 or 16");
     c->tile_req_x = tx;
     c->tile_req_y = ty;
+    return NTVS_OK;
+}
+
+int ntvs_set_fault_hook(ntvs_ctx* c, int64_t wait_ns, int flags) {
+    if (!c) return fail(NTVS_ERR_ARG, "null context");
+    if (flags & ~(NTVS_HOOK_STARVE_PIPE | NTVS_HOOK_STARVE_CHECK)) return fail(NTVS_ERR_ARG, "unknown hook flag");
+    c->wait_ns = wait_ns > 0 ? (uint64_t)wait_ns : kDefaultWaitNs;
+    c->hook_flags = flags;
+    return NTVS_OK;
+}
+
+int ntvs_set_compute_dtype(ntvs_ctx* c, int dtype) {
+    if (!c) return fail(NTVS_ERR_ARG, "null context");
+    if (dtype != NTVS_F32 && dtype != NTVS_F64) return fail(NTVS_ERR_ARG, "compute dtype must be NTVS_F32 or NTVS_F64");
+    c->compute_req = dtype;
     return NTVS_OK;
 }
 

@@ -195,6 +195,8 @@ struct DropPipeArgs {
     double lambda;
     double* resid_ss;
     int* err;                     // set (nonzero) when a bounded wait runs out
+    uint64_t wait_ns;             // bound of each wait
+    int starve;                   // test hook: the producer withholds every CTA's first stage
     int vdt, cdt;
     int grid;
     bool use_d16;                 // DELTA16 index storage (d16) instead of col
@@ -224,6 +226,47 @@ cudaError_t k_hist_to_paths(const float* hist, int64_t M, float* rec, int* flags
 cudaError_t k_otf_prep(const OtfArgs& a, int64_t r0, int64_t r1, float* inv_norm2, int32_t* cnt, cudaStream_t s);
 cudaError_t k_otf_drop(const OtfArgs& a, int64_t r0, int64_t r1, const float* inv_norm2, const float* x, float* delta,
                        double lambda, double* resid_ss, cudaStream_t s);
+
+// ------------------------------------------------------------------ TV check on the device
+// Error codes written to the device error word by bounded waits (the host reports them as
+// NTVS_ERR_TIMEOUT): 1-7 the pipelined DROP kernel, 8 the TV-check loop's grid barrier.
+constexpr int kErrCheckBarrier = 8;
+
+// Device-resident state of the checked variant: the current ell (ell_{k-1} between
+// cycles) and the arrival counter of the retry loop's grid barrier.
+struct CheckState {
+    int64_t ell;
+    unsigned bar;
+    int pad;
+};
+// ell_k of cycle k into st->ell and *ell_slot: the override when given, else ell_{k-1}
+// under the OTVS rule, else rand(k, ell_{k-1}) of stream `seed`.
+cudaError_t k_check_cycle_begin(CheckState* st, int rule, uint64_t seed, int64_t k, bool has_override,
+                                int64_t override_ell, int64_t* ell_slot, cudaStream_t s);
+struct CheckLoopArgs {
+    int cdt;
+    double* x;                 // FP64 master image, updated on accept
+    ImgCopies copies;          // its FP32 copies (null members skipped)
+    const void* g;             // gradient (compute type)
+    const double* gnorm2;      // ||g||^2
+    const double* phi_x;       // phi(x) of the same gradient pass
+    CheckState* st;
+    const double* beta_tab;    // beta0 * alpha^ell for ell < tab_len (host-computed)
+    int tab_len;
+    double beta0, alpha;       // beyond the table: beta0 * pow(alpha, ell) on the device
+    int max_retries;
+    double* partials;          // >= 2 * grid doubles
+    int grid;                  // <= check_loop_max_grid (co-resident)
+    int* err;
+    uint64_t wait_ns;          // bound of each barrier wait
+    int starve;                // test hook: CTA 0 withholds its first barrier arrival
+    int32_t* tries_out;        // this step's tries and accept flag
+    int32_t* acc_out;
+    int nx, ny, nz;
+};
+cudaError_t k_tv_check_loop(const CheckLoopArgs& a, cudaStream_t s);
+// largest co-resident grid of the retry-loop kernel (0 if the query fails)
+int check_loop_max_grid(int cdt, int sms);
 
 // ------------------------------------------------------------------ misc
 // sets the calling thread's ntvs_last_error() text

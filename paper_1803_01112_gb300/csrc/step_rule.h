@@ -1,5 +1,5 @@
-// Host-side step-size schedule of the TV perturbations (shared by the single-context and
-// the batched drivers).
+// Step-size schedule of the TV perturbations (shared by the single-context and the
+// batched drivers; the ell draw is also used on the device by the TV-check cycle kernel).
 //   NTVS (Appendix C): ell_k = rand(k, ell_{k-1}), a uniform integer between the two
 //     (inclusive) taken from draw k of a SplitMix64 stream; try t of the cycle uses
 //     beta0 * alpha^(ell_k + t).
@@ -13,10 +13,16 @@
 
 #include "ntvs.h"
 
+#ifdef __CUDACC__
+#define NTVS_HD __host__ __device__
+#else
+#define NTVS_HD
+#endif
+
 namespace ntvs {
 
 // SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) in counter form: output n of stream seed.
-inline uint64_t splitmix64_at(uint64_t seed, uint64_t n) {
+NTVS_HD inline uint64_t splitmix64_at(uint64_t seed, uint64_t n) {
     uint64_t z = seed + (n + 1) * 0x9E3779B97F4A7C15ULL;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
@@ -24,7 +30,7 @@ inline uint64_t splitmix64_at(uint64_t seed, uint64_t n) {
 }
 
 // rand(k, ell_{k-1}) of the NTVS rule
-inline int64_t draw_ell(uint64_t seed, int64_t k, int64_t ell_prev) {
+NTVS_HD inline int64_t draw_ell(uint64_t seed, int64_t k, int64_t ell_prev) {
     const int64_t lo = k < ell_prev ? k : ell_prev, hi = k < ell_prev ? ell_prev : k;
     const uint64_t span = (uint64_t)(hi - lo) + 1u;
     return lo + (int64_t)(splitmix64_at(seed, (uint64_t)k) % span);

@@ -1,9 +1,11 @@
 """GPU parity of whole NTVS runs (Appendix C: N TV steps + a DROP sweep per cycle) with the
 FP64 oracle, through the C ABI.
 
-Bars: FP64 path relative L2 <= 1e-10 (summation order only); FP32 path relative L2
-<= 1e-5 after k cycles (the FP32 bar of the method's specification); ell traces and
-check-mode decision traces identical.
+Bars: FP64 arithmetic (FP64 or FP32 storage) relative L2 <= 1e-10, or 1e-8 after 12
+cycles at eps_tv = 1e-8 (summation order only); FP32 arithmetic relative L2 <= 1e-5 after
+k cycles where the problem's conditioning allows it, and within 4x the oracle's own
+movement under one FP32 rounding of b where it does not; ell traces and check-mode
+decision traces identical.
 """
 import numpy as np
 import pytest
@@ -44,12 +46,14 @@ def test_slice_2d_fp64_matches_oracle(lam):
     np.testing.assert_allclose(res, ref.resid_ss[-1], rtol=1e-9)
 
 
-# At eps_tv = 1e-8 the normalized TV gradient is close to a sign function of voxel
-# differences far below sqrt(eps) = 1e-4, so each cycle amplifies rounding differences by
-# roughly 10x: two FP64 summation orders end 1e-10 apart after 12 cycles, and the FP32
-# DROP's ~1e-11 rounding grows to ~1e-4.  The FP32 bar of 1e-5 is therefore held at
-# eps_tv = 1e-4 for the full 12 cycles (measured ~1e-9) and at eps_tv = 1e-8 for short runs
-# or strong DROP steps; the FP64 path is held at 1e-8 for the full run at eps_tv = 1e-8.
+# At eps_tv = 1e-8 the normalized TV step amplifies image perturbations below
+# sqrt(eps) = 1e-4 from one cycle to the next: the FP64 oracle itself, given b perturbed by
+# one FP32 rounding (relative 6e-8), ends ~1e-4 away after 12 cycles at lambda = 2e-4
+# (tests/test_oracle_conditioning.py).  FP32 arithmetic, whose every stage rounds at that
+# level, can therefore not hold 1e-5 there; it is held to 1e-5 where the conditioning
+# allows (eps_tv = 1e-4 for 12 cycles, eps_tv = 1e-8 for short runs or strong DROP steps)
+# and, at the benchmarked parameters, to a bar derived from the oracle's own sensitivity
+# (below).  FP64 arithmetic on the same FP32-stored system holds 1e-6 at those parameters.
 @pytest.mark.parametrize("lam,N,K,eps", [(2e-4, 3, 12, 1e-4), (2e-4, 6, 12, 1e-4), (2e-4, 3, 3, 1e-8),
                                          (0.3, 3, 12, 1e-8), (0.3, 6, 4, 1e-8)])
 def test_scaled_3d_fp32_matches_oracle(lam, N, K, eps):
@@ -66,6 +70,63 @@ def test_scaled_3d_fp32_matches_oracle(lam, N, K, eps):
     err = rel_l2(x, ref.x)
     assert err <= 1e-5, f"relative L2 {err:.3e}"
     np.testing.assert_array_equal(ell, ref.ell_k)
+
+
+@pytest.mark.parametrize("N", [3, 6])
+def test_fp64_arithmetic_on_fp32_storage_at_benchmark_parameters(N):
+    """The benchmarked parameters (eps_tv = 1e-8, lambda = 2e-4, alpha = 0.75, 12 cycles) on
+    the FP32-stored system with FP64 arithmetic (ntvs_set_compute_dtype): relative L2 within
+    1e-6 of the oracle on the same stored values.  Only the summation order differs, but the
+    conditioning amplifies that too (measured 1e-10 with N = 3 and 2e-8 with N = 6)."""
+    ntvs = ntvs_module()
+    s = synth.generate(synth.spec_scaled_3d(nx=48, ny=48, nz=4, n_hist=60_000, n_angles=60, n_blocks=5))
+    val, b = s.val.astype(np.float32), s.b.astype(np.float32)
+    r = ntvs.Reconstructor(0)
+    prm = oracle.Params(lam=2e-4, N=N, alpha=0.75, seed=2, eps_tv=1e-8)
+    try:
+        r.set_compute_dtype(ntvs.NTVS_F64)
+        r.load((48, 48, 4), s.row_ptr, s.col, val, b, n_blocks=5)
+        st = r.stats()
+        assert st["compute_dtype"] == ntvs.NTVS_F64
+        x, ell, *_ = _run_gpu(r, prm, 12, s.xbar, np.float32)
+    finally:
+        r.close()
+    ref = oracle_run(s, val.astype(np.float64), b.astype(np.float64), prm, 12, s.xbar)
+    err = rel_l2(x, ref.x)
+    assert err <= 1e-6, f"relative L2 {err:.3e}"
+    np.testing.assert_array_equal(ell, ref.ell_k)
+
+
+def _oracle_sensitivity(s, val64, b64, prm, K, ell, seeds=(11, 12, 13)):
+    """Median relative L2 by which the FP64 oracle's K-cycle result moves when b is
+    perturbed by one FP32 rounding (relative 2^-24 times a standard normal)."""
+    ref = oracle_run(s, val64, b64, prm, K, s.xbar, ell_override=ell)
+    out = []
+    for sd in seeds:
+        bp = b64 * (1.0 + 2.0 ** -24 * np.random.default_rng(sd).standard_normal(b64.size))
+        out.append(rel_l2(oracle_run(s, val64, bp, prm, K, s.xbar, ell_override=ell).x, ref.x))
+    return float(np.median(out))
+
+
+@pytest.mark.parametrize("N", [3, 6])
+def test_fp32_arithmetic_at_benchmark_parameters_within_conditioning(N):
+    """FP32 arithmetic at the benchmarked parameters (eps_tv = 1e-8, lambda = 2e-4, 12
+    cycles): its distance from the oracle is at most 4x the distance the oracle itself moves
+    under one FP32 rounding of b -- the FP32 path is as accurate as FP32 data allows."""
+    ntvs = ntvs_module()
+    s = synth.generate(synth.spec_scaled_3d(nx=48, ny=48, nz=4, n_hist=60_000, n_angles=60, n_blocks=5))
+    r, val64, b64 = load(ntvs, s, np.float32)
+    prm = oracle.Params(lam=2e-4, N=N, alpha=0.75, seed=2, eps_tv=1e-8)
+    try:
+        x, ell, *_ = _run_gpu(r, prm, 12, s.xbar, np.float32)
+    finally:
+        r.close()
+    ref = oracle_run(s, val64, b64, prm, 12, s.xbar)
+    np.testing.assert_array_equal(ell, ref.ell_k)
+    err = rel_l2(x, ref.x)
+    sens = _oracle_sensitivity(s, val64, b64, prm, 12, ref.ell_k)
+    assert sens > 1e-5     # the bar of 1e-5 lies below the problem's own conditioning here
+    assert err <= 4.0 * sens, f"relative L2 {err:.3e} vs oracle sensitivity {sens:.3e}"
 
 
 def test_scaled_3d_fp64_matches_oracle_at_small_eps():
@@ -102,6 +163,78 @@ def test_check_mode_matches_oracle(dtype):
     assert ref.tries.max() > 1
     assert rel_l2(x, ref.x) <= (1e-10 if dtype == np.float64 else 1e-5)
     assert st["n_tries"] == ref.tries.sum() and st["n_accepted"] == ref.accepted.sum()
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_check_decisions_stay_on_the_device(dtype):
+    """With the check every decision is taken on the device: a cycle launches the same
+    kernels whatever the number of tries (cycle start, N x (gradient + retry loop), 2 per
+    DROP block, phi), and the traces read back afterwards equal the oracle's."""
+    ntvs = ntvs_module()
+    s = synth.generate(synth.spec_scaled_3d(nx=32, ny=32, nz=3, n_hist=20_000, n_angles=40, n_blocks=4))
+    r, val64, b64 = load(ntvs, s, dtype)
+    prm = oracle.Params(lam=0.3, N=6, alpha=0.75, seed=9, tv_check=True)
+    K = 4
+    try:
+        r.set_params(lam=prm.lam, N=prm.N, alpha=prm.alpha, seed=prm.seed, tv_check=True)
+        r.set_image(s.xbar.astype(dtype))
+        n0 = r.stats()["n_launches"]
+        r.run(K)
+        st = r.stats()
+        x = r.get_image()
+        ell, tries, acc = r.trace()
+    finally:
+        r.close()
+    ref = oracle_run(s, val64, b64, prm, K, s.xbar)
+    np.testing.assert_array_equal(tries, ref.tries.reshape(-1))
+    np.testing.assert_array_equal(acc, ref.accepted.reshape(-1))
+    np.testing.assert_array_equal(ell, ref.ell_k)
+    assert ref.tries.sum() > ref.tries.size            # rejections happened
+    per_cycle = 1 + 2 * prm.N + 2 * 4 + 1
+    assert st["n_launches"] - n0 == K * per_cycle      # independent of the tries
+    assert st["ell_prev"] == ref.ell_prev
+    assert st["n_tries"] == ref.tries.sum() and st["n_accepted"] == ref.accepted.sum()
+    assert rel_l2(x, ref.x) <= (1e-10 if dtype == np.float64 else 1e-5)
+
+
+def test_check_mode_replays_an_ell_override():
+    ntvs = ntvs_module()
+    s = synth.generate(synth.spec_slice_2d().replace(n_hist=4000, n_blocks=2))
+    r, val64, b64 = load(ntvs, s, np.float64)
+    forced = np.array([0, 5, 2, 9])
+    prm = oracle.Params(lam=0.5, N=3, alpha=0.6, seed=1, tv_check=True)
+    try:
+        r.set_ell_override(forced)
+        x, ell, tries, acc, st, _ = _run_gpu(r, prm, 4, s.xbar, np.float64)
+    finally:
+        r.close()
+    ref = oracle_run(s, val64, b64, prm, 4, s.xbar, ell_override=forced)
+    np.testing.assert_array_equal(ell, forced)
+    np.testing.assert_array_equal(tries, ref.tries.reshape(-1))
+    assert rel_l2(x, ref.x) < 1e-10
+
+
+def test_check_runs_interleave_with_unchecked_runs():
+    """ell_{k-1} moves between the device (checked cycles) and the host (unchecked ones)."""
+    ntvs = ntvs_module()
+    s = synth.generate(synth.spec_slice_2d().replace(n_hist=6000, n_blocks=3))
+    r, val64, b64 = load(ntvs, s, np.float64)
+    shape = (s.spec.nx, s.spec.ny, s.spec.nz)
+    try:
+        x = s.xbar.copy()
+        k, ell_prev = 0, 0
+        r.set_image(x)
+        for check in (True, False, True, True, False):
+            prm = oracle.Params(lam=0.4, N=3, alpha=0.7, seed=3, tv_check=check)
+            r.set_params(lam=prm.lam, N=prm.N, alpha=prm.alpha, seed=prm.seed, tv_check=check)
+            r.run(1)
+            ref = oracle.ntvs(s.row_ptr, s.col, val64, b64, s.block_ptr(), shape, prm, 1, x, k0=k, ell_prev=ell_prev)
+            x, k, ell_prev = ref.x, k + 1, ref.ell_prev
+            assert r.state() == (k, ell_prev)
+        got = r.get_image()
+    finally:
+        r.close()
+    assert rel_l2(got, x) < 1e-10
 
 
 def test_N0_is_plain_drop_on_gpu():
