@@ -73,16 +73,20 @@ namespace ntvs {
 // outside [0, V) (the entry is then skipped), 8 for a non-finite value, 16 for a
 // non-finite b; inv_norm2[i] = 1 / sum a^2 (FP64 sum of the stored values, 0 for a zero
 // row); cnt[j] += 1 for every entry with a != 0.  Requires a validated row_ptr.
+// With colsum != nullptr it also accumulates colsum[j] += |a_ij| (the block's column sums
+// of lengths) and *rb = max over the rows of |b_i| / ||a_i||^2 (as float bits, an atomic
+// max of non-negative floats): the scale statistics of the fixed-point DROP window.
 template <typename V, typename T>
 __global__ void __launch_bounds__(256) prep_block_kernel(const int64_t* __restrict__ row_ptr,
                                                          const int32_t* __restrict__ col, const V* __restrict__ val,
                                                          const T* __restrict__ b, int64_t r0, int64_t r1, int64_t nvox,
                                                          T* __restrict__ inv_norm2, int32_t* __restrict__ cnt,
-                                                         int* flags) {
+                                                         int* flags, float* __restrict__ colsum, unsigned* rb) {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int f = 0;
+    float bmax = 0.f;
     for (int64_t i = r0 + w0; i < r1; i += nw) {
         const int64_t p0 = __ldg(row_ptr + i), p1 = __ldg(row_ptr + i + 1);
         double sq = 0.0;
@@ -93,39 +97,73 @@ __global__ void __launch_bounds__(256) prep_block_kernel(const int64_t* __restri
             if (!isfinite(a)) f |= 8;
             sq += a * a;
             if (c < 0 || (int64_t)c >= nvox) f |= 4;
-            else if (a != 0.0) atomicAdd(cnt + c, 1);
+            else if (a != 0.0) {
+                atomicAdd(cnt + c, 1);
+                if (colsum) atomicAdd(colsum + c, (float)fabs(a));
+            }
         }
         sq = warp_sum(sq);
         if (lane == 0) {
-            inv_norm2[i] = (sq > 0.0 && isfinite(sq)) ? (T)(1.0 / sq) : (T)0;
-            if (!isfinite((double)b[i])) f |= 16;
+            const double inv = (sq > 0.0 && isfinite(sq)) ? 1.0 / sq : 0.0;
+            inv_norm2[i] = (T)inv;
+            const double bi = (double)b[i];
+            if (!isfinite(bi)) f |= 16;
+            else bmax = fmaxf(bmax, (float)(fabs(bi) * inv));
         }
     }
     if (f) atomicOr(flags, f);
+    if (rb) {
+        for (int o = 16; o > 0; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+        if (lane == 0 && bmax > 0.f) atomicMax(rb, __float_as_uint(bmax));
+    }
+}
+
+// *out = max(*out, max_j v[j]) for non-negative v (float bits compared as unsigned)
+__global__ void colmax_kernel(const float* __restrict__ v, int64_t n, unsigned* out) {
+    float m = 0.f;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, v[j]);
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(out, __float_as_uint(m));
+}
+
+cudaError_t k_colmax(const float* v, int64_t n, float* out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    colmax_kernel<<<prep_grid(), 256, 0, s>>>(v, n, reinterpret_cast<unsigned*>(out));
+    return cudaGetLastError();
 }
 
 template <typename V>
 static cudaError_t launch_prep(const int64_t* rp, const int32_t* col, const V* val, const void* b, int64_t r0,
-                               int64_t r1, int64_t nvox, void* inn, int cdt, int32_t* cnt, int* flags, cudaStream_t s) {
+                               int64_t r1, int64_t nvox, void* inn, int cdt, int32_t* cnt, int* flags, float* colsum,
+                               float* rb, cudaStream_t s) {
+    unsigned* rbu = reinterpret_cast<unsigned*>(rb);
     if (cdt == F64)
         prep_block_kernel<V, double><<<prep_grid(), 256, 0, s>>>(rp, col, val, (const double*)b, r0, r1, nvox,
-                                                                 (double*)inn, cnt, flags);
+                                                                 (double*)inn, cnt, flags, colsum, rbu);
     else
         prep_block_kernel<V, float><<<prep_grid(), 256, 0, s>>>(rp, col, val, (const float*)b, r0, r1, nvox,
-                                                                (float*)inn, cnt, flags);
+                                                                (float*)inn, cnt, flags, colsum, rbu);
     return cudaGetLastError();
 }
 
 cudaError_t k_prep_block(const int64_t* row_ptr, const int32_t* col, const void* val, int vdt, const void* b,
                          int64_t r0, int64_t r1, int64_t nvox, void* inv_norm2, int cdt, int32_t* cnt, int* flags,
-                         cudaStream_t s) {
+                         float* colsum, float* rb, cudaStream_t s) {
     if (r1 <= r0) return cudaSuccess;
     switch (vdt) {
-        case F64: return launch_prep(row_ptr, col, (const double*)val, b, r0, r1, nvox, inv_norm2, cdt, cnt, flags, s);
-        case F32: return launch_prep(row_ptr, col, (const float*)val, b, r0, r1, nvox, inv_norm2, cdt, cnt, flags, s);
-        case F16: return launch_prep(row_ptr, col, (const __half*)val, b, r0, r1, nvox, inv_norm2, cdt, cnt, flags, s);
+        case F64:
+            return launch_prep(row_ptr, col, (const double*)val, b, r0, r1, nvox, inv_norm2, cdt, cnt, flags, colsum,
+                               rb, s);
+        case F32:
+            return launch_prep(row_ptr, col, (const float*)val, b, r0, r1, nvox, inv_norm2, cdt, cnt, flags, colsum,
+                               rb, s);
+        case F16:
+            return launch_prep(row_ptr, col, (const __half*)val, b, r0, r1, nvox, inv_norm2, cdt, cnt, flags, colsum,
+                               rb, s);
         case BF16:
-            return launch_prep(row_ptr, col, (const __nv_bfloat16*)val, b, r0, r1, nvox, inv_norm2, cdt, cnt, flags, s);
+            return launch_prep(row_ptr, col, (const __nv_bfloat16*)val, b, r0, r1, nvox, inv_norm2, cdt, cnt, flags,
+                               colsum, rb, s);
         default: return cudaErrorInvalidValue;
     }
 }

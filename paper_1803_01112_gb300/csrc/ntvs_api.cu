@@ -105,6 +105,7 @@ struct ntvs_ctx {
     DropStage* stages = nullptr;       // pipelined schedule: all blocks' stages
     int32_t* stage_begin = nullptr;    // [B][win_grid + 1]
     int win_grid = 0;
+    float* wstat = nullptr;            // FP32 window scale per block: lmax [B], bound [B], observed [B]
     int* derr = nullptr;               // device error word (bounded waits that ran out)
     // DELTA16 index storage (packed at load from the int32 columns)
     int16_t* col16 = nullptr;
@@ -194,6 +195,7 @@ struct ntvs_ctx {
         dev_free(inv_s);
         dev_free(segs);
         dev_free(seg_begin);
+        dev_free(wstat);
         dev_free(stages);
         dev_free(stage_begin);
         dev_free(col16);
@@ -514,7 +516,7 @@ int drop_block(ntvs_ctx* c, int t) {
         CUDA_TRY(timed_launch(c, KIND_APPLY, [&] {
             return k_drop_apply(c->cdt, c->x, c->copies(split), c->delta,
                                 (const char*)c->inv_s + (size_t)t * c->vm.vint * c->csz(), c->V, c->apply_grid,
-                                c->stream);
+                                nullptr, nullptr, c->stream);
         }));
         c->split_stale = !split;
         return NTVS_OK;
@@ -541,10 +543,20 @@ int drop_block(ntvs_ctx* c, int t) {
     a.segs = nullptr;
     a.seg_begin = nullptr;
     a.slice = c->vm.slice_p;
+    a.wlmax = nullptr;
+    a.wbound = nullptr;
+    a.wobs = nullptr;
+    float* wb = nullptr;
+    float* wo = nullptr;
     if (c->schedule == NTVS_SCHED_WINDOW) {
         a.segs = c->segs;
         a.seg_begin = c->seg_begin + (size_t)t * (c->win_grid + 1);
         a.grid = c->win_grid;
+        if (c->wstat) {
+            a.wlmax = c->wstat + t;
+            a.wbound = wb = c->wstat + c->B + t;
+            a.wobs = wo = c->wstat + 2 * c->B + t;
+        }
     }
     if (c->schedule == NTVS_SCHED_PIPELINE) {
         DropPipeArgs pa;
@@ -574,7 +586,7 @@ int drop_block(ntvs_ctx* c, int t) {
     }
     CUDA_TRY(timed_launch(c, KIND_APPLY, [&] {
         return k_drop_apply(c->cdt, c->x, c->copies(split), c->delta,
-                            (const char*)c->inv_s + (size_t)t * c->vm.vint * c->csz(), c->V, c->apply_grid,
+                            (const char*)c->inv_s + (size_t)t * c->vm.vint * c->csz(), c->V, c->apply_grid, wb, wo,
                             c->stream);
     }));
     c->split_stale = !split;
@@ -1074,13 +1086,27 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
     int32_t* cnt = nullptr;
     TRY(dev_alloc(&cnt, sizeof(int32_t) * (size_t)c->B * VI, "hit counts"));
     CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)c->B * VI, st));
+    // FP32 path: per-block scale statistics of the fixed-point DROP window (lmax = the
+    // largest column sum of |a_ij|, the bound seeded with max_i |b_i| / ||a_i||^2)
+    float* colsum = nullptr;
+    struct FreeColsum {
+        float*& p;
+        ~FreeColsum() { dev_free(p); }
+    } colsum_guard{colsum};
+    if (c->cdt == F32) {
+        TRY(dev_alloc(&c->wstat, sizeof(float) * 3 * (size_t)c->B, "window scale statistics"));
+        CUDA_TRY(cudaMemsetAsync(c->wstat, 0, sizeof(float) * 3 * (size_t)c->B, st));
+        TRY(dev_alloc(&colsum, sizeof(float) * (size_t)VI, "column sums"));
+    }
     for (int t = 0; t < c->B; ++t) {
         if (piped) {
             CUDA_TRY(cudaStreamWaitEvent(st, arrived[t], 0));
             if (tiled) CUDA_TRY(k_remap_cols(c->col + eb[t], c->col + eb[t], eb[t + 1] - eb[t], c->vm, c->dflags, st));
         }
+        if (colsum) CUDA_TRY(cudaMemsetAsync(colsum, 0, sizeof(float) * (size_t)VI, st));
         CUDA_TRY(k_prep_block(c->row_ptr, c->col, c->val, c->vdt, c->b, bp[t], bp[t + 1], VI, c->inv_norm2, c->cdt,
-                              cnt + (size_t)t * VI, c->dflags, st));
+                              cnt + (size_t)t * VI, c->dflags, colsum, colsum ? c->wstat + c->B + t : nullptr, st));
+        if (colsum) CUDA_TRY(k_colmax(colsum, VI, c->wstat + t, st));
     }
     CUDA_TRY(cudaMemcpyAsync(c->hint, c->dflags, sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));

@@ -73,10 +73,13 @@ int red_grid(int64_t n, int sm_count);
 // flags |= 1 if row_ptr decreases, 2 if row_ptr[0] != 0
 cudaError_t k_validate_rows(const int64_t* row_ptr, int64_t M, int* flags, cudaStream_t s);
 // fused pass over the rows [r0, r1) of one block: validation of columns, values and b
-// (flags 4 / 8 / 16), inv_norm2 of the rows and the block's hit counts cnt
+// (flags 4 / 8 / 16), inv_norm2 of the rows and the block's hit counts cnt; with colsum
+// (nullable) also colsum[j] += |a_ij| and *rb = max(*rb, max_i |b_i| / ||a_i||^2)
 cudaError_t k_prep_block(const int64_t* row_ptr, const int32_t* col, const void* val, int vdt, const void* b,
                          int64_t r0, int64_t r1, int64_t nvox, void* inv_norm2, int cdt, int32_t* cnt, int* flags,
-                         cudaStream_t s);
+                         float* colsum, float* rb, cudaStream_t s);
+// *out = max(*out, max_j v[j]) for n non-negative floats
+cudaError_t k_colmax(const float* v, int64_t n, float* out, cudaStream_t s);
 // col_out[p] = internal index of voxel col_in[p]; flags |= 4 for a column outside [0, V)
 // (written as 0).  col_in == col_out is allowed.
 cudaError_t k_remap_cols(const int32_t* col_in, int32_t* col_out, int64_t nnz, VoxMap m, int* flags, cudaStream_t s);
@@ -152,6 +155,14 @@ struct DropArgs {
     const DropSegment* segs;
     const int32_t* seg_begin;
     int64_t slice;
+    // FP32 windowed schedule: the window accumulates in int32 fixed point with quantum
+    // Q = |lambda| * bound * lmax / 2^30, where lmax = max_j sum_{i in block} |a_ij| and
+    // bound = *wbound (a bound on |b_i - <a_i,x>| / ||a_i||^2); rows above the bound
+    // scatter with global FP32 reductions instead.  *wobs receives the block's observed
+    // max of that ratio (atomic max of float bits).  All three point at block t's slot.
+    const float* wlmax;
+    const float* wbound;
+    float* wobs;
 };
 cudaError_t k_drop_block(const DropArgs& a, cudaStream_t s);
 // home[i] = median z-slice of the first, middle and last entries of row i (-1: empty row)
@@ -163,9 +174,10 @@ cudaError_t k_row_home(const int64_t* row_ptr, const int32_t* col, int64_t M, in
 cudaError_t k_chunk_home(const int32_t* home, const int64_t* chunk_start, int64_t nchunks, int32_t* out,
                          unsigned long long* changes, int grid, cudaStream_t s);
 // x_j += delta_p * inv_s_p on the FP64 master (p the internal index of j) and its FP32
-// copies; delta_p = 0
+// copies; delta_p = 0.  With wbound (block t's slot, nullable): *wbound = 2 * *wobs when
+// the block observed a ratio (the next sweep's bound), *wobs = 0.
 cudaError_t k_drop_apply(int cdt, double* x, ImgCopies c, void* delta, const void* inv_s, int64_t V, int grid,
-                         cudaStream_t s);
+                         float* wbound, float* wobs, cudaStream_t s);
 
 // TMA-fed pipeline (drop_pipe_kernel): a stage is a run of at most kStageRows whole rows
 // of one home slice whose entries [e0, e0 + nent) fit one ring slot (e0 and nent aligned

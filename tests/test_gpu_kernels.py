@@ -193,6 +193,33 @@ def test_drop_schedules_match_oracle(dtype, schedule):
     np.testing.assert_allclose(res, ss, rtol=1e-10 if dtype == np.float64 else 1e-4)
 
 
+def test_fixed_point_window_follows_its_bound():
+    """The FP32 windowed schedule accumulates its slice window in int32 fixed point with a
+    per-block scale bounded by the previous sweep's largest |residual| / ||a||^2; rows above
+    the bound (here: every row, after the image jumps tenfold) scatter with global
+    reductions, and the next sweep's bound covers them again.  Every sweep equals the
+    oracle's."""
+    ntvs = ntvs_module()
+    from paper_1803_01112_gb300._ffi import NTVS_SCHED_WINDOW
+    s = synth.generate(synth.spec_scaled_3d(nx=40, ny=40, nz=5, n_hist=30_000, n_angles=36, n_blocks=4, seed=8))
+    val, b = s.val.astype(np.float32), s.b.astype(np.float32)
+    val64, b64 = val.astype(np.float64), b.astype(np.float64)
+    r = ntvs.Reconstructor(0)
+    try:
+        r.load((40, 40, 5), s.row_ptr, s.col, val, b, n_blocks=4, schedule=NTVS_SCHED_WINDOW)
+        assert r.stats()["drop_schedule"] == NTVS_SCHED_WINDOW
+        r.set_params(lam=0.9, N=0, alpha=0.5)
+        for x0 in (s.xbar, 10.0 * s.xbar, 10.0 * s.xbar, -3.0 * s.xstar):
+            r.set_image(x0)
+            r.drop_sweep()
+            got = r.get_image()
+            want, ss = oracle.drop_sweep(s.row_ptr, s.col, val64, b64, s.block_ptr(), x0, 0.9)
+            assert rel_l2(got, want) < 1e-6
+            np.testing.assert_allclose(r.block_resid(), ss, rtol=1e-4)
+    finally:
+        r.close()
+
+
 def test_window_schedule_on_rows_without_slice_order():
     """Forcing the windowed schedule on rows in random order is slower but still exact."""
     ntvs = ntvs_module()

@@ -1,8 +1,11 @@
 """On-the-fly rows on the GPU: the system is given as path records and traced in every DROP
 sweep (FP32 geometry).  The oracle runs on the generator's stored rows (the same paths,
 traced in FP64 on the host), so the bar accounts for FP32 path geometry: coordinates of
-~100 mm carry ~1e-5 mm of rounding, i.e. ~1e-5 relative per intersection length; the
-images are held to 3e-5 relative L2 (10x the dot-product error this implies)."""
+~100 mm carry ~1e-5 mm of rounding, i.e. ~1e-5 relative per intersection length and far
+more on short pieces.  Measured on GB300: 5.7e-6 to 9.9e-6 relative L2 after one sweep and
+6.7e-6 after three NTVS cycles, against 1.1e-8 to 1.4e-8 for the same rows stored as FP32
+CSR in the same sweeps -- the geometry, not the arithmetic.  The images are held to 2e-5
+(2x the largest measured)."""
 import numpy as np
 import pytest
 
@@ -36,7 +39,7 @@ def test_onthefly_sweep_matches_oracle_on_stored_rows(curved):
             r.drop_sweep()
             got = r.get_image()
             want, ss = oracle.drop_sweep(s.row_ptr, s.col, s.val, b32, s.block_ptr(), x0, 0.8)
-            assert rel_l2(got, want) <= 3e-5
+            assert rel_l2(got, want) <= 2e-5
             np.testing.assert_allclose(r.block_resid(), ss, rtol=1e-3)
     finally:
         r.close()
@@ -58,7 +61,7 @@ def test_onthefly_ntvs_run_matches_oracle():
     finally:
         r.close()
     ref = oracle.ntvs(s.row_ptr, s.col, s.val, b32, s.block_ptr(), (32, 32, 3), prm, 3, s.xbar)
-    assert rel_l2(got, ref.x) <= 3e-5
+    assert rel_l2(got, ref.x) <= 2e-5
 
 
 def test_onthefly_equals_stored_fp32_rows_on_gpu():
@@ -86,7 +89,7 @@ def test_onthefly_equals_stored_fp32_rows_on_gpu():
         outs.append(r.get_image())
     finally:
         r.close()
-    assert rel_l2(outs[0], outs[1]) <= 3e-5
+    assert rel_l2(outs[0], outs[1]) <= 2e-5
 
 
 def test_onthefly_rejects_bad_paths():
