@@ -72,6 +72,9 @@ def parse_args(argv=None):
                     help="DROP kernel schedule (auto picks the windowed one for slice-ordered rows)")
     ap.add_argument("--rows", type=int, default=0,
                     help="profiling case: only the first ROWS histories, in blocks of the full workload's size")
+    ap.add_argument("--shard", action="store_true",
+                    help="one reconstruction with the rows of every block split over the ranks (strong scaling; "
+                         "delta summed per block by an NCCL all-reduce) instead of one replica per rank")
     return ap.parse_args(argv)
 
 
@@ -375,6 +378,87 @@ def run_onthefly_variant(args, ntvs, local, stream, world, device):
             "note": "6M histories (the 60M-history layout with 1/10 of the histories); b traced on the host"}
 
 
+def shard_system(spec, vdt, rank, world):
+    """This rank's rows of the workload: block t's rows cut into `world` contiguous runs,
+    run `rank` of each, generated run by run (no rank builds the whole system)."""
+    import synth
+    per = -(-spec.n_hist // spec.n_blocks)
+    parts, bp = [], [0]
+    for t in range(spec.n_blocks):
+        b0, b1 = min(t * per, spec.n_hist), min((t + 1) * per, spec.n_hist)
+        lo, hi = b0 + (b1 - b0) * rank // world, b0 + (b1 - b0) * (rank + 1) // world
+        parts.append(synth.generate(spec, vdt, rows=(lo, hi)) if hi > lo else None)
+        bp.append(bp[-1] + hi - lo)
+    live = [q for q in parts if q is not None]
+    rp = [np.zeros(1, np.int64)]
+    off = 0
+    for q in live:
+        rp.append(q.row_ptr[1:] + off)
+        off += int(q.row_ptr[-1])
+    col = np.concatenate([q.col for q in live])
+    val = np.concatenate([q.val for q in live])
+    b = np.concatenate([q.b for q in live]).astype(vdt)
+    return np.concatenate(rp), col, val, b, np.asarray(bp, np.int64), live[0].xbar
+
+
+def run_sharded(args):
+    """One reconstruction of the workload row-sharded over the ranks: every rank holds its
+    runs of every block's rows, the TV steps run on every rank on identical images, and
+    each DROP block's delta (and residual) is summed over the ranks by an NCCL all-reduce
+    on the library's stream before it is applied with the global hit counts.  Strong
+    scaling: value = the workload's histories per cycle / max rank time.  With one rank
+    the collective is the identity."""
+    import torch
+
+    import paper_1803_01112_gb300 as ntvs
+    from paper_1803_01112_gb300 import _ffi
+    rank, world, local = dist_env()
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+    ntvs.lib()
+    spec, vdt = workload_spec(args.workload)
+    rp, col, val, b, sbp, xbar = shard_system(spec, vdt, rank, world)
+    stream = torch.cuda.Stream(device)
+    tile = tuple(int(v) for v in args.tile.lower().split("x"))
+    r = ntvs.Reconstructor(local, stream.cuda_stream).set_voxel_tile(*tile)
+    r.load((spec.nx, spec.ny, spec.nz), rp, col, val, b, n_blocks=len(sbp) - 1, block_ptr=sbp)
+    fn = ntvs.torch_allreduce(device=local) if world > 1 else _ffi.ALLREDUCE_FN(lambda *a: 0)
+    r.set_allreduce(fn)
+    r.set_params(**PARAMS)
+    r.set_image(xbar.astype(vdt))
+    r.run(args.warmup)
+    r.sync()
+    barrier(world, device)
+    torch.cuda.synchronize(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        r.run(1)
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    ms = max_over_ranks(e0.elapsed_time(e1), world, device)
+    launches = r.stats()["n_launches"]
+    r.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": spec.n_hist * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+                "dtype": "f32" if vdt == np.float32 else "f64", "data": "synthetic",
+                "config": {"workload": spec.name, "histories": spec.n_hist, "n_blocks": spec.n_blocks, **PARAMS,
+                           "tv_check": False, "l2": L2_NOTE,
+                           "parallelism": f"row-sharded DROP over {world} GPU(s): NCCL all-reduce of delta per block"},
+                "gpu_launches": launches,
+                "note": "measured only with one GPU here (identity collective); multi-GPU runs unmeasured on hardware"}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def run_ntvs(args):
     import torch
 
@@ -421,11 +505,11 @@ def run_ntvs(args):
     r.sync()
     torch.cuda.synchronize(device)
 
-    # ---- timed region: K cycles, events on the launching stream
+    # ---- timed region: K cycles, events on the launching stream (no per-launch events here:
+    # an event recorded around each of the ~47 launches of a cycle costs ~2.5 % of it)
     clocks = ClockSampler(local)
     barrier(world, device)
     torch.cuda.synchronize(device)
-    r.set_profiling(True)
     launches0 = r.stats()["n_launches"]
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -438,11 +522,25 @@ def run_ntvs(args):
     clk = clocks.stop()
     barrier(world, device)
     launches = r.stats()["n_launches"] - launches0
-    prof = r.profile()
-    r.set_profiling(False)
     ms = max_over_ranks(ms_local, world, device)
     ms_step = ms / args.steps
     value = world * spec.n_hist * args.steps / (ms / 1e3)
+
+    # ---- second timed pass of K cycles with CUDA events around every launch on the same
+    # stream: per-kernel device time, and the DROP kernel's average launch for the roofline
+    barrier(world, device)
+    torch.cuda.synchronize(device)
+    r.set_profiling(True)
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(args.steps):
+        r.run(1)
+    p1.record(stream)
+    torch.cuda.synchronize(device)
+    ms_prof_pass = p0.elapsed_time(p1)
+    prof = r.profile()
+    r.set_profiling(False)
 
     # ---- roofline of the dominant kernel (DROP gather + scatter)
     vsz = np.dtype(vdt).itemsize
@@ -455,7 +553,9 @@ def run_ntvs(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": ncu_traffic_per_launch(), "kernel": kname,
                 "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": avg_bytes,
-                "avg_launch_ms": avg_ms}
+                "avg_launch_ms": avg_ms,
+                "timing": f"CUDA events around every launch in a second timed pass of {args.steps} cycles "
+                          f"({ms_prof_pass / args.steps:.3f} ms per cycle with the events)"}
     kernel_ms = {k: prof[k] / args.steps for k in ("drop_block_ms", "drop_apply_ms", "tv_ms")}
 
     # ---- end to end through the C ABI from pinned host buffers; measured before the variant
@@ -598,6 +698,8 @@ def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.shard:
+        return run_sharded(args)
     return run_ntvs(args)
 
 

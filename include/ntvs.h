@@ -354,6 +354,55 @@ int ntvs_drop_block(ntvs_ctx* ctx, int t);
 /* One full DROP sweep P_T (blocks 0..B-1 in order). */
 int ntvs_drop_sweep(ntvs_ctx* ctx);
 
+/* ---- row-sharded DROP ---------------------------------------------------------------
+ * All rows of a block see the same x (Sec. III-D, block-DROP of ref. CEHN08), so the rows
+ * of every block may be split over several GPUs: each forms the sum over its rows,
+ *     delta_j = lambda * sum_{i in its rows of block t} a_ij (b_i - <a_i, x>) / ||a_i||^2,
+ * the deltas are summed over the GPUs, and each applies x_j += delta_j / s_j^t with the
+ * GLOBAL hit count s_j^t of the block.  The paper runs on one GPU (Sec. IV); this split is
+ * the library's own.  The library never reads another GPU's memory: the sums are the
+ * caller's collective (e.g. NCCL). */
+
+/* Element type of hit counts in the all-reduce callback. */
+#define NTVS_I32 4
+
+/* delta of rows [r0, r1) of block t (r0 = r1 = -1: all of the block's rows; otherwise
+ * block_ptr[t] <= r0 <= r1 <= block_ptr[t+1]) on the current image, NOT applied: V values
+ * of dtype (NTVS_F32 / NTVS_F64) in canonical voxel order into delta_out (caller-owned,
+ * host or device).  *resid_ss (may be NULL) receives sum (b_i - <a_i, x>)^2 over those rows
+ * (FP64).  A proper sub-range runs the plain schedule.  Synchronous for host output or
+ * resid_ss, else queued.  Errors: NTVS_ERR_ARG, NTVS_ERR_STATE, NTVS_ERR_CUDA. */
+int ntvs_drop_block_partial(ntvs_ctx* ctx, int t, int64_t r0, int64_t r1, void* delta_out, int dtype, int mem_kind,
+                            double* resid_ss);
+
+/* x_j += delta[j] / s_j^t for an externally summed delta (V values of dtype, canonical
+ * order, host or device) with the context's hit counts of block t (see below). */
+int ntvs_apply_delta(ntvs_ctx* ctx, int t, const void* delta, int dtype, int mem_kind);
+
+/* The hit counts s_j^t of block t (V int32, canonical order, host or device): the counts
+ * of this context's rows after ntvs_load_system; a shard replaces them by the sum over all
+ * shards before applying deltas.  Counts must be >= 0. */
+int ntvs_get_hit_counts(ntvs_ctx* ctx, int t, int32_t* out, int mem_kind);
+int ntvs_set_hit_counts(ntvs_ctx* ctx, int t, const int32_t* counts, int mem_kind);
+
+/* Collective of a row-sharded reconstruction: sum buf[0..n) (device memory, element type
+ * dtype: NTVS_F32, NTVS_F64 or NTVS_I32) over all ranks in place, queued on cuda_stream
+ * (the context's stream) so that work queued after it sees the sum; return 0 on success.
+ * Every rank must make the same sequence of calls. */
+typedef int (*ntvs_allreduce_fn)(void* buf, int64_t n, int dtype, void* cuda_stream, void* user);
+
+/* Turn the context into one rank of a row-sharded reconstruction.  Call it on every rank
+ * after ntvs_load_system with that rank's rows (same grid, blocks, parameters, voxel tile
+ * and image on every rank).  It sums the hit counts of all blocks over the ranks through fn
+ * once (every rank then holds the global counts), and from then on every DROP block of
+ * ntvs_run / ntvs_drop_sweep / ntvs_drop_block sums the block's delta (the internal-order
+ * accumulator, n = the padded voxel count) and its residual sum of squares through fn
+ * before applying them.  The TV steps run on every rank on identical images.  fn = NULL
+ * leaves sharded mode (the counts stay global until the next load).  Loading a system
+ * clears the callback.  Errors: NTVS_ERR_STATE (no system, or a callback already set),
+ * NTVS_ERR_CUDA (fn returned nonzero). */
+int ntvs_set_allreduce(ntvs_ctx* ctx, ntvs_allreduce_fn fn, void* user);
+
 /* ---- batched reconstructions ----------------------------------------------------------
  * Many independent NTVS reconstructions (Appendix C, without the TV check) advanced
  * together on one GPU: every member has its own grid, system, blocks and parameters, and

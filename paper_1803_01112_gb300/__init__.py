@@ -234,6 +234,97 @@ def ntvs_set_compute_dtype(ctx: int, dtype: int) -> None:
     check(lib().ntvs_set_compute_dtype(ctx, int(dtype)), "ntvs_set_compute_dtype")
 
 
+def ntvs_drop_block_partial(ctx: int, t: int, out, r0: int = -1, r1: int = -1) -> float:
+    """delta of rows [r0, r1) of block t (default: the whole block) into `out` (V values,
+    F32/F64, numpy = host or CUDA tensor = device), not applied; returns the rows' residual
+    sum of squares."""
+    ptr, kind = _ptr_kind(out)
+    ss = ctypes.c_double()
+    check(lib().ntvs_drop_block_partial(ctx, int(t), int(r0), int(r1), ptr, _dtype_code(out), kind, ctypes.byref(ss)),
+          "ntvs_drop_block_partial")
+    return ss.value
+
+
+def ntvs_apply_delta(ctx: int, t: int, delta) -> None:
+    ptr, kind = _ptr_kind(delta)
+    check(lib().ntvs_apply_delta(ctx, int(t), ptr, _dtype_code(delta), kind), "ntvs_apply_delta")
+
+
+def _require_int32(a, what):
+    name = str(a.dtype)
+    if not name.endswith("int32"):
+        raise TypeError(f"{what} must be int32, got {name}")
+
+
+def ntvs_get_hit_counts(ctx: int, t: int, out) -> None:
+    _require_int32(out, "hit counts")
+    ptr, kind = _ptr_kind(out)
+    check(lib().ntvs_get_hit_counts(ctx, int(t), ptr, kind), "ntvs_get_hit_counts")
+
+
+def ntvs_set_hit_counts(ctx: int, t: int, counts) -> None:
+    _require_int32(counts, "hit counts")
+    ptr, kind = _ptr_kind(counts)
+    check(lib().ntvs_set_hit_counts(ctx, int(t), ptr, kind), "ntvs_set_hit_counts")
+
+
+def shard_rows(row_ptr, col, val, b, block_ptr, rank: int, world: int):
+    """Rank `rank`'s rows of a system split over `world` ranks for row-sharded DROP: the
+    rows of every block t are cut into `world` contiguous, nearly equal runs and the rank
+    keeps run `rank` of each.  Returns (row_ptr, col, val, b, block_ptr) of the shard (host
+    arrays; block t of the shard holds the rank's rows of block t)."""
+    rp = np.asarray(row_ptr, np.int64)
+    bp = np.asarray(block_ptr, np.int64)
+    keep, nbp = [], [0]
+    for t in range(bp.size - 1):
+        n = int(bp[t + 1] - bp[t])
+        lo, hi = int(bp[t]) + n * rank // world, int(bp[t]) + n * (rank + 1) // world
+        keep.append(np.arange(lo, hi, dtype=np.int64))
+        nbp.append(nbp[-1] + hi - lo)
+    rows = np.concatenate(keep) if keep else np.zeros(0, np.int64)
+    lens = rp[rows + 1] - rp[rows]
+    srp = np.zeros(rows.size + 1, np.int64)
+    np.cumsum(lens, out=srp[1:])
+    idx = np.concatenate([np.arange(rp[i], rp[i + 1], dtype=np.int64) for i in rows]) if rows.size else \
+        np.zeros(0, np.int64)
+    return srp, np.ascontiguousarray(col[idx]), np.ascontiguousarray(val[idx]), np.ascontiguousarray(b[rows]), \
+        np.asarray(nbp, np.int64)
+
+
+def ntvs_set_allreduce(ctx: int, fn, user=None) -> None:
+    """fn: an _ffi.ALLREDUCE_FN (keep a reference while the context uses it) or None."""
+    check(lib().ntvs_set_allreduce(ctx, fn if fn is not None else _ffi.ALLREDUCE_FN(), user), "ntvs_set_allreduce")
+
+
+class _DeviceArray:
+    """A raw device buffer described through __cuda_array_interface__ (no copy)."""
+    _TYPESTR = {NTVS_F32: "<f4", NTVS_F64: "<f8", _ffi.NTVS_I32: "<i4"}
+
+    def __init__(self, ptr: int, n: int, dtype: int):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": self._TYPESTR[dtype],
+                                         "data": (int(ptr), False), "version": 2}
+
+
+def torch_allreduce(group=None, device: Optional[int] = None):
+    """An all-reduce callback for ntvs_set_allreduce backed by torch.distributed (NCCL on
+    GPUs): the library's buffer is wrapped as a tensor and summed over `group` on the
+    context's stream.  Keep the returned object alive while the context uses it."""
+    import torch
+    import torch.distributed as dist
+    dev = torch.cuda.current_device() if device is None else device
+
+    def cb(buf, n, dtype, stream, user):
+        try:
+            t = torch.as_tensor(_DeviceArray(buf, n, dtype), device=f"cuda:{dev}")
+            with torch.cuda.stream(torch.cuda.ExternalStream(stream, device=f"cuda:{dev}")):
+                dist.all_reduce(t, group=group)
+            return 0
+        except Exception:   # reported to the library as a failed collective
+            return 1
+
+    return _ffi.ALLREDUCE_FN(cb)
+
+
 def ntvs_set_fault_hook(ctx: int, wait_ns: int, flags: int) -> None:
     check(lib().ntvs_set_fault_hook(ctx, int(wait_ns), int(flags)), "ntvs_set_fault_hook")
 
@@ -531,6 +622,34 @@ class Reconstructor:
     def set_compute_dtype(self, dtype: int):
         """Arithmetic (NTVS_F32 or NTVS_F64) of FP32-stored systems, applied at the next load."""
         ntvs_set_compute_dtype(self._ctx, dtype)
+        return self
+
+    def drop_block_partial(self, t: int, out=None, r0: int = -1, r1: int = -1):
+        """(delta, residual sum of squares) of rows [r0, r1) of block t, not applied."""
+        if out is None:
+            out = np.empty(int(np.prod(self.shape)), np.float64)
+        ss = ntvs_drop_block_partial(self._ctx, t, out, r0, r1)
+        return out, ss
+
+    def apply_delta(self, t: int, delta):
+        ntvs_apply_delta(self._ctx, t, delta)
+        return self
+
+    def hit_counts(self, t: int, out=None):
+        if out is None:
+            out = np.empty(int(np.prod(self.shape)), np.int32)
+        ntvs_get_hit_counts(self._ctx, t, out)
+        return out
+
+    def set_hit_counts(self, t: int, counts):
+        ntvs_set_hit_counts(self._ctx, t, counts)
+        return self
+
+    def set_allreduce(self, fn):
+        """Row-sharded mode with all-reduce callback fn (an _ffi.ALLREDUCE_FN, e.g.
+        torch_allreduce()); None leaves it."""
+        ntvs_set_allreduce(self._ctx, fn)
+        self._allreduce = fn   # the library calls it until it is replaced
         return self
 
     def set_fault_hook(self, wait_ns: int = 0, flags: int = 0):

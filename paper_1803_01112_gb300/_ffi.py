@@ -21,6 +21,7 @@ NTVS_ERR_TIMEOUT = -5
 NTVS_ERR_STATE = -6
 
 NTVS_F64, NTVS_F32, NTVS_F16, NTVS_BF16 = 0, 1, 2, 3
+NTVS_I32 = 4
 NTVS_MEM_HOST, NTVS_MEM_DEVICE = 0, 1
 NTVS_CSR32, NTVS_DELTA16 = 0, 1
 NTVS_SCHED_AUTO, NTVS_SCHED_PLAIN, NTVS_SCHED_WINDOW, NTVS_SCHED_PIPELINE, NTVS_SCHED_ONTHEFLY = 0, 1, 2, 3, 4
@@ -89,6 +90,9 @@ class ntvs_batch_stats(ctypes.Structure):
 vp, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
 P = ctypes.POINTER
 
+# int (*ntvs_allreduce_fn)(void* buf, int64_t n, int dtype, void* cuda_stream, void* user)
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, vp, i64, ctypes.c_int, vp, vp)
+
 # name -> (restype, argtypes); the list is the whole header
 SIGNATURES = {
     "ntvs_version": (ctypes.c_char_p, []),
@@ -120,6 +124,11 @@ SIGNATURES = {
     "ntvs_perturb_checked": (ctypes.c_int, [vp, d, P(ctypes.c_int), P(d), P(d)]),
     "ntvs_drop_block": (ctypes.c_int, [vp, ctypes.c_int]),
     "ntvs_drop_sweep": (ctypes.c_int, [vp]),
+    "ntvs_drop_block_partial": (ctypes.c_int, [vp, ctypes.c_int, i64, i64, vp, ctypes.c_int, ctypes.c_int, P(d)]),
+    "ntvs_apply_delta": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int]),
+    "ntvs_get_hit_counts": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int]),
+    "ntvs_set_hit_counts": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int]),
+    "ntvs_set_allreduce": (ctypes.c_int, [vp, ALLREDUCE_FN, vp]),
     "ntvs_batch_create": (ctypes.c_int, [P(vp), ctypes.c_int, vp]),
     "ntvs_batch_destroy": (ctypes.c_int, [vp]),
     "ntvs_batch_add": (ctypes.c_int, [vp, P(ntvs_system), P(ntvs_params), vp, ctypes.c_int, ctypes.c_int,

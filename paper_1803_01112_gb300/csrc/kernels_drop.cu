@@ -17,6 +17,8 @@
 //   ~1 global L2 atomic per matrix entry by ~0.2.
 //   Plain variant (any row order): every scatter is a global reduction.
 // drop_apply: x_j += delta_j / s_j^t (inverse counts precomputed), delta_j = 0.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace ntvs {
@@ -40,16 +42,19 @@ __device__ __forceinline__ void load4(const __nv_bfloat16* p, float (&o)[4]) {
     o[0] = f0.x; o[1] = f0.y; o[2] = f1.x; o[3] = f1.y;
 }
 
+// The windowed kernel's dynamic shared memory: the slice window, voxels [w0, w0 + W).
+extern __shared__ __align__(16) unsigned char drop_win_smem[];
+
 struct Window {
-    void* win;     // shared-memory delta of voxels [w0, w0 + W)
     int w0;        // voxel indices stay below 2^31
     int W;
 };
 
 // Scale of the FP32 fixed-point window, uniform over the CTA (kept in shared memory so
-// that the row loop's registers hold the matrix entries): quantum Q = 1 / invQ, rows with
-// |r_i / lambda| above `bound` scatter globally (invQ = 0 sends every row there); `obs`
-// collects the largest |r_i / lambda| seen (float bits, atomic max).
+// that the row loop's registers hold the matrix entries): quantum Q = 1 / invQ; rows with
+// |r_i / lambda| above `bound` scatter globally (invQ = 0 sends every row there), which
+// keeps every window slot below 2^30 Q and every converted term below 2^22 in magnitude;
+// `obs` collects the largest |r_i / lambda| seen (float bits, atomic max).
 struct WinScale {
     float invQ;
     float bound;
@@ -71,12 +76,13 @@ __device__ __forceinline__ void scatter(T* delta, const Window& w, int32_t c, T 
         const int rel = c - w.w0;
         if ((unsigned)rel < (unsigned)w.W) {
             if constexpr (sizeof(T) == 4) {
-                if (rowfix) {
-                    atomicAdd(reinterpret_cast<int*>(w.win) + swz(rel), __float2int_rn(rq * (float)a));
+                if (rowfix) {   // |rq a| < 2^22: adding 1.5 * 2^23 rounds it to the nearest integer
+                    const int y = __float_as_int(fmaf(rq, (float)a, 12582912.0f)) - 0x4B400000;
+                    atomicAdd(reinterpret_cast<int*>(drop_win_smem) + swz(rel), y);
                     return;
                 }
             } else {
-                atomicAdd(reinterpret_cast<T*>(w.win) + swz(rel), r * a);
+                atomicAdd(reinterpret_cast<T*>(drop_win_smem) + swz(rel), r * a);
                 return;
             }
         }
@@ -102,17 +108,37 @@ __device__ __forceinline__ void row_factor(bool valid, bool first_lane, T res, T
     }
 }
 
+// A row's extent, loaded one row ahead of its use by the row loops (the row pointer,
+// col/val and x gathers are otherwise three dependent round trips per row).
+struct RowHead {
+    int64_t p0, p1;
+};
+
+__device__ __forceinline__ RowHead load_head(int64_t i, bool valid, const int64_t* __restrict__ row_ptr) {
+    RowHead h{0, 0};
+    if (valid) {
+        h.p0 = __ldg(row_ptr + i);
+        h.p1 = __ldg(row_ptr + i + 1);
+    }
+    return h;
+}
+
 // One row per group of LPR lanes (all lanes of the warp call this together).
 // VW entries per lane per step from aligned addresses; CH steps held in registers.
 template <typename T, typename V, int LPR, int CH, int VW, bool WIN>
-__device__ __forceinline__ void drop_row(int64_t i, bool valid, int sub, const int64_t* __restrict__ row_ptr,
+__device__ __forceinline__ void drop_row(int64_t i, const RowHead& h, bool valid, int sub,
                                          const int32_t* __restrict__ col, const V* __restrict__ val,
                                          const T* __restrict__ b, const T* __restrict__ inv_norm2,
                                          const T* __restrict__ x, T* __restrict__ delta, T lambda, const Window& w,
                                          double& ss, WinScale* ws) {
-    int64_t p0 = 0, p1 = 0;
-    if (valid) { p0 = __ldg(row_ptr + i); p1 = __ldg(row_ptr + i + 1); }
+    const int64_t p0 = h.p0, p1 = h.p1;
     const int64_t pa = p0 & ~(int64_t)(VW - 1);
+    // entries relative to the aligned start in 32 bits (the register steps cover far fewer
+    // than 2^31 entries; the tail loop below runs in 64 bits)
+    const int32_t* colr = col + pa;
+    const V* valr = val + pa;
+    const int lo = (int)(p0 - pa);
+    const int hi = (int)((p1 - pa) < (int64_t)0x7fffffff ? (p1 - pa) : (int64_t)0x7fffffff);
     // Every register step is predicated rather than skipped: with a branch per step the
     // gathers of later steps could not be issued ahead of the earlier steps' arithmetic
     // (measured 0.47 against 0.33 ms per 500k-row block).
@@ -120,21 +146,21 @@ __device__ __forceinline__ void drop_row(int64_t i, bool valid, int sub, const i
     T a[CH][VW];
 #pragma unroll
     for (int u = 0; u < CH; ++u) {
-        const int64_t q = pa + ((int64_t)u * LPR + sub) * VW;
-        if (q < p1) {
+        const int q = (u * LPR + sub) * VW;
+        if (q < hi) {
             if constexpr (VW == 4) {
-                const int4 cv = __ldcs(reinterpret_cast<const int4*>(col + q));
+                const int4 cv = __ldcs(reinterpret_cast<const int4*>(colr + q));
                 float av[4];
-                load4(val + q, av);
+                load4(valr + q, av);
                 c[u][0] = cv.x; c[u][1] = cv.y; c[u][2] = cv.z; c[u][3] = cv.w;
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     a[u][e] = (T)av[e];
-                    if (q + e < p0 || q + e >= p1) c[u][e] = -1;
+                    if (q + e < lo || q + e >= hi) c[u][e] = -1;
                 }
             } else {
-                c[u][0] = __ldcs(col + q);
-                a[u][0] = (T)to_compute(val[q]);
+                c[u][0] = __ldcs(colr + q);
+                a[u][0] = (T)to_compute(valr[q]);
             }
         } else {
 #pragma unroll
@@ -252,12 +278,17 @@ drop_block_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const Window w{nullptr, 0, 0};
+    const Window w{0, 0};
     double ss = 0.0;
+    int64_t i = r0 + warp * G + lane / LPR;
+    RowHead h = load_head(i, i < r1, row_ptr);
     for (int64_t base = r0 + warp * G; base < r1; base += nwarps * G) {
-        const int64_t i = base + lane / LPR;
-        drop_row<T, V, LPR, CH, VW, false>(i, i < r1, lane % LPR, row_ptr, col, val, b, inv_norm2, x, delta, lambda,
-                                           w, ss, nullptr);
+        const int64_t in = i + nwarps * G;
+        const RowHead hn = load_head(in, in < r1, row_ptr);   // next row, ahead of use
+        drop_row<T, V, LPR, CH, VW, false>(i, h, i < r1, lane % LPR, col, val, b, inv_norm2, x, delta, lambda, w, ss,
+                                           nullptr);
+        i = in;
+        h = hn;
     }
     __shared__ double sh[32];
     const double tot = block_sum(ss, sh);
@@ -296,10 +327,11 @@ drop_block_window_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __r
                          const V* __restrict__ val, const T* __restrict__ b, const T* __restrict__ inv_norm2,
                          const DropSegment* __restrict__ segs, const int32_t* __restrict__ seg_begin,
                          int64_t slice, const T* __restrict__ x, T* __restrict__ delta, T lambda,
-                         double* resid_ss, Delta16 d16, const float* wlmax, const float* wbound, float* wobs) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* win = reinterpret_cast<T*>(smem_raw);
+                         double* resid_ss, Delta16 d16, const float* wlmax, const float* wbound, float* wobs,
+                         const float* wamax) {
+    T* win = reinterpret_cast<T*>(drop_win_smem);
     __shared__ WinScale ws;
+    __shared__ double ss_grp[32][32 / LPR];                     // per row group: sum of res^2 (one writer)
     const int W = (int)slice;
     const int Wp = (W + 31) & ~31;
     constexpr int G = 32 / LPR;
@@ -307,21 +339,24 @@ drop_block_window_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __r
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     for (int j = threadIdx.x; j < Wp; j += blockDim.x) win[j] = (T)0;   // int 0 has the bits of 0.0f
-    // |window slot| <= |lambda| * bound * lmax = 2^30 Q: no int32 overflow
-    const float bound = wbound ? *wbound : 0.f, lmax = wlmax ? *wlmax : 0.f;
-    const float Q = fabsf((float)lambda) * bound * lmax * 0x1p-30f;
+    for (int q = threadIdx.x; q < 32 * G; q += blockDim.x) (&ss_grp[0][0])[q] = 0.0;
+    // rows with |r/lambda| <= bound keep |window slot| <= |lambda| bound lmax = 2^30 Q (no
+    // int32 overflow); rows also below 2^22 Q / (|lambda| amax) keep every term below 2^22
+    const float bound = wbound ? *wbound : 0.f, lmax = wlmax ? *wlmax : 0.f, amax = wamax ? *wamax : 0.f;
+    const float lam = fabsf((float)lambda);
+    const float Q = lam * bound * lmax * 0x1p-30f;
     if (threadIdx.x == 0) {
         const float iq = 1.f / Q;
-        const bool fix = sizeof(T) == 4 && bound > 0.f && Q > 0.f && isfinite(Q) && isfinite(iq);
+        const bool fix = sizeof(T) == 4 && bound > 0.f && amax > 0.f && Q > 0.f && isfinite(Q) && isfinite(iq);
         ws.invQ = fix ? iq : 0.f;
-        ws.bound = bound;
+        ws.bound = fix ? fminf(bound, 0x1p22f * Q / (lam * amax)) : 0.f;
         ws.obs = 0u;
     }
     __syncthreads();
     const int s0 = seg_begin[blockIdx.x], s1 = seg_begin[blockIdx.x + 1];
     int cur = s0 < s1 ? segs[s0].home : 0;
-    Window w{win, (int)(cur * slice), W};
-    double ss = 0.0;
+    Window w{(int)(cur * slice), W};
+    double ss = 0.0;   // DELTA16 rows
     for (int s = s0; s < s1; ++s) {
         const DropSegment sg = segs[s];
         if (sg.home != cur) {   // uniform across the CTA
@@ -331,19 +366,25 @@ drop_block_window_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __r
             cur = sg.home;
             w.w0 = (int)(cur * slice);
         }
-        for (int64_t base = sg.r0 + (int64_t)warp * G; base < sg.r1; base += (int64_t)nwarps * G) {
-            const int64_t i = base + lane / LPR;
-            if constexpr (D16) {
+        if constexpr (D16) {
+            for (int64_t base = sg.r0 + (int64_t)warp * G; base < sg.r1; base += (int64_t)nwarps * G) {
+                const int64_t i = base + lane / LPR;
                 drop_row_d16<T, V, CH, true>(i, i < sg.r1, row_ptr, d16, val, b, inv_norm2, x, delta, lambda, w, ss,
                                              &ws);
-            } else {
-                drop_row<T, V, LPR, CH, VW, true>(i, i < sg.r1, lane % LPR, row_ptr, col, val, b, inv_norm2, x, delta,
-                                                  lambda, w, ss, &ws);
+            }
+        } else {
+            const int grp = lane / LPR;
+            for (int64_t base = sg.r0 + (int64_t)warp * G; base < sg.r1; base += (int64_t)nwarps * G) {
+                const int64_t i = base + grp;
+                const RowHead h = load_head(i, i < sg.r1, row_ptr);
+                drop_row<T, V, LPR, CH, VW, true>(i, h, i < sg.r1, lane % LPR, col, val, b, inv_norm2, x, delta,
+                                                  lambda, w, ss_grp[warp][grp], &ws);
             }
         }
     }
     __syncthreads();
     flush_window<T>(win, Wp, delta, w.w0, Q);
+    if (!D16 && lane < G) ss = ss_grp[warp][lane];
     __shared__ double sh[32];
     const double tot = block_sum(ss, sh);   // synchronizes the CTA
     if (threadIdx.x == 0) {
@@ -420,7 +461,7 @@ static cudaError_t launch_window(const DropArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     kern<<<a.grid, 1024, smem, s>>>(a.row_ptr, a.col, (const V*)a.val, (const T*)a.b, (const T*)a.inv_norm2, a.segs,
                                     a.seg_begin, a.slice, (const T*)a.x, (T*)a.delta, (T)a.lambda, a.resid_ss, a.d16,
-                                    a.wlmax, a.wbound, a.wobs);
+                                    a.wlmax, a.wbound, a.wobs, a.wamax);
     return cudaGetLastError();
 }
 
@@ -447,6 +488,18 @@ static cudaError_t dispatch(const DropArgs& a, cudaStream_t s) {
             case 32: return launch_cfg<T, V, 32, 3, 4>(a, s);
             default: return cudaErrorInvalidValue;
         }
+        }
+    }
+    // windowed FP32 compute with a warp per row: as many register steps as the block's
+    // longest row needs (8..12; longer rows finish in the tail loop), so blocks of short rows
+    // do not evaluate empty steps
+    if constexpr (sizeof(T) == 4 && (std::is_same<V, float>::value || std::is_same<V, __nv_bfloat16>::value)) {
+        if (a.segs && a.lanes_per_row == 32) {
+            const int need = (int)((a.max_row + 31) / 32);
+            if (need <= 8) return launch_cfg<T, V, 32, 8, 1>(a, s);
+            if (need == 9) return launch_cfg<T, V, 32, 9, 1>(a, s);
+            if (need == 10) return launch_cfg<T, V, 32, 10, 1>(a, s);
+            if (need == 11) return launch_cfg<T, V, 32, 11, 1>(a, s);
         }
     }
     switch (a.lanes_per_row) {
@@ -509,6 +562,27 @@ cudaError_t k_drop_apply(int cdt, double* x, ImgCopies c, void* delta, const voi
         drop_apply_kernel<double><<<grid, 256, 0, s>>>(x, c, (double*)delta, (const double*)inv_s, V, wbound, wobs);
     else
         drop_apply_kernel<float><<<grid, 256, 0, s>>>(x, c, (float*)delta, (const float*)inv_s, V, wbound, wobs);
+    return cudaGetLastError();
+}
+
+// *out = max(*out, longest row of rows [r0, r1))
+__global__ void row_maxlen_kernel(const int64_t* __restrict__ row_ptr, int64_t r0, int64_t r1, unsigned long long* out) {
+    unsigned long long m = 0;
+    for (int64_t i = r0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < r1; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t l = row_ptr[i + 1] - row_ptr[i];
+        m = l > (int64_t)m ? (unsigned long long)l : m;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+        m = v > m ? v : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
+cudaError_t k_row_maxlen(const int64_t* row_ptr, int64_t r0, int64_t r1, unsigned long long* out, int grid,
+                         cudaStream_t s) {
+    if (r1 <= r0) return cudaSuccess;
+    row_maxlen_kernel<<<grid, 256, 0, s>>>(row_ptr, r0, r1, out);
     return cudaGetLastError();
 }
 

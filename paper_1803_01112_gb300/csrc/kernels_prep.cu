@@ -74,8 +74,9 @@ namespace ntvs {
 // non-finite b; inv_norm2[i] = 1 / sum a^2 (FP64 sum of the stored values, 0 for a zero
 // row); cnt[j] += 1 for every entry with a != 0.  Requires a validated row_ptr.
 // With colsum != nullptr it also accumulates colsum[j] += |a_ij| (the block's column sums
-// of lengths) and *rb = max over the rows of |b_i| / ||a_i||^2 (as float bits, an atomic
-// max of non-negative floats): the scale statistics of the fixed-point DROP window.
+// of lengths), rb[0] = max over the rows of |b_i| / ||a_i||^2 and rb[1] = max |a_ij| (as
+// float bits, atomic maxima of non-negative floats): the scale statistics of the
+// fixed-point DROP window.
 template <typename V, typename T>
 __global__ void __launch_bounds__(256) prep_block_kernel(const int64_t* __restrict__ row_ptr,
                                                          const int32_t* __restrict__ col, const V* __restrict__ val,
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__(256) prep_block_kernel(const int64_t* __restri
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int f = 0;
-    float bmax = 0.f;
+    float bmax = 0.f, amax = 0.f;
     for (int64_t i = r0 + w0; i < r1; i += nw) {
         const int64_t p0 = __ldg(row_ptr + i), p1 = __ldg(row_ptr + i + 1);
         double sq = 0.0;
@@ -99,7 +100,10 @@ __global__ void __launch_bounds__(256) prep_block_kernel(const int64_t* __restri
             if (c < 0 || (int64_t)c >= nvox) f |= 4;
             else if (a != 0.0) {
                 atomicAdd(cnt + c, 1);
-                if (colsum) atomicAdd(colsum + c, (float)fabs(a));
+                if (colsum) {
+                    atomicAdd(colsum + c, (float)fabs(a));
+                    amax = fmaxf(amax, (float)fabs(a));
+                }
             }
         }
         sq = warp_sum(sq);
@@ -113,8 +117,12 @@ __global__ void __launch_bounds__(256) prep_block_kernel(const int64_t* __restri
     }
     if (f) atomicOr(flags, f);
     if (rb) {
-        for (int o = 16; o > 0; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+        for (int o = 16; o > 0; o >>= 1) {
+            bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+            amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        }
         if (lane == 0 && bmax > 0.f) atomicMax(rb, __float_as_uint(bmax));
+        if (lane == 0 && amax > 0.f) atomicMax(rb + 1, __float_as_uint(amax));
     }
 }
 
@@ -231,6 +239,106 @@ cudaError_t k_delta16_fill(const int64_t* row_ptr, const int32_t* col, int64_t M
                            int16_t* col16, int32_t* base, int2* exc, cudaStream_t s) {
     if (M <= 0) return cudaSuccess;
     delta16_fill_kernel<<<prep_grid(), 256, 0, s>>>(row_ptr, col, M, exc_off, col16, base, exc);
+    return cudaGetLastError();
+}
+
+}  // namespace ntvs
+
+namespace ntvs {
+
+// ------------------------------------------------------------------ row-sharded DROP
+// Conversions between the internal voxel order of a block's accumulator / inverse hit
+// counts and the canonical order of the public arrays (all V voxels, one pass each).
+
+// out[j] = delta[internal(j)] (as F32 or F64), delta[internal(j)] = 0
+template <typename T, typename O>
+__global__ void delta_out_kernel(T* __restrict__ delta, VoxMap m, O* __restrict__ out, int64_t V) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < V; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = vox_internal(m, j);
+        out[j] = (O)delta[p];
+        delta[p] = (T)0;
+    }
+}
+
+// x_j += d[j] * inv_s[internal(j)] on the FP64 master and its FP32 copies
+template <typename T, typename D>
+__global__ void apply_ext_kernel(double* __restrict__ x, ImgCopies c, const D* __restrict__ d,
+                                 const T* __restrict__ inv_s, int64_t V) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < V; j += (int64_t)gridDim.x * blockDim.x) {
+        const double v = x[j] + (double)d[j] * (double)inv_s[vox_internal(c.m, j)];
+        x[j] = v;
+        store_copies(c, j, v);
+    }
+}
+
+// counts <-> inverse counts over n slots of one order (1/(1/s) rounds back to s exactly in
+// FP64, and in FP32 for every count below 2^22)
+template <typename T>
+__global__ void counts_from_inv_kernel(const T* __restrict__ inv_s, int32_t* __restrict__ cnt, int64_t n) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const double v = (double)inv_s[j];
+        cnt[j] = v > 0.0 ? (int32_t)rint(1.0 / v) : 0;
+    }
+}
+
+// the same between canonical counts and internal-order inverse counts
+template <typename T>
+__global__ void counts_out_kernel(const T* __restrict__ inv_s, VoxMap m, int32_t* __restrict__ cnt, int64_t V) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < V; j += (int64_t)gridDim.x * blockDim.x) {
+        const double v = (double)inv_s[vox_internal(m, j)];
+        cnt[j] = v > 0.0 ? (int32_t)rint(1.0 / v) : 0;
+    }
+}
+template <typename T>
+__global__ void counts_in_kernel(const int32_t* __restrict__ cnt, VoxMap m, T* __restrict__ inv_s, int64_t V) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < V; j += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = cnt[j];
+        inv_s[vox_internal(m, j)] = s > 0 ? (T)(1.0 / (double)s) : (T)0;
+    }
+}
+
+cudaError_t k_delta_out(int cdt, void* delta, VoxMap m, void* out, int odt, cudaStream_t s) {
+    const int64_t V = (int64_t)m.nx * m.ny * m.nz;
+    if (V <= 0) return cudaSuccess;
+    if (cdt == F64 && odt == F64) delta_out_kernel<double, double><<<prep_grid(), 256, 0, s>>>((double*)delta, m, (double*)out, V);
+    else if (cdt == F64 && odt == F32) delta_out_kernel<double, float><<<prep_grid(), 256, 0, s>>>((double*)delta, m, (float*)out, V);
+    else if (cdt == F32 && odt == F64) delta_out_kernel<float, double><<<prep_grid(), 256, 0, s>>>((float*)delta, m, (double*)out, V);
+    else if (cdt == F32 && odt == F32) delta_out_kernel<float, float><<<prep_grid(), 256, 0, s>>>((float*)delta, m, (float*)out, V);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t k_apply_ext(int cdt, double* x, ImgCopies c, const void* d, int ddt, const void* inv_s, cudaStream_t s) {
+    const int64_t V = (int64_t)c.m.nx * c.m.ny * c.m.nz;
+    if (V <= 0) return cudaSuccess;
+    if (cdt == F64 && ddt == F64) apply_ext_kernel<double, double><<<prep_grid(), 256, 0, s>>>(x, c, (const double*)d, (const double*)inv_s, V);
+    else if (cdt == F64 && ddt == F32) apply_ext_kernel<double, float><<<prep_grid(), 256, 0, s>>>(x, c, (const float*)d, (const double*)inv_s, V);
+    else if (cdt == F32 && ddt == F64) apply_ext_kernel<float, double><<<prep_grid(), 256, 0, s>>>(x, c, (const double*)d, (const float*)inv_s, V);
+    else if (cdt == F32 && ddt == F32) apply_ext_kernel<float, float><<<prep_grid(), 256, 0, s>>>(x, c, (const float*)d, (const float*)inv_s, V);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t k_counts_from_inv(int cdt, const void* inv_s, int32_t* cnt, int64_t n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (cdt == F64) counts_from_inv_kernel<double><<<prep_grid(), 256, 0, s>>>((const double*)inv_s, cnt, n);
+    else counts_from_inv_kernel<float><<<prep_grid(), 256, 0, s>>>((const float*)inv_s, cnt, n);
+    return cudaGetLastError();
+}
+
+cudaError_t k_counts_out(int cdt, const void* inv_s, VoxMap m, int32_t* cnt, cudaStream_t s) {
+    const int64_t V = (int64_t)m.nx * m.ny * m.nz;
+    if (V <= 0) return cudaSuccess;
+    if (cdt == F64) counts_out_kernel<double><<<prep_grid(), 256, 0, s>>>((const double*)inv_s, m, cnt, V);
+    else counts_out_kernel<float><<<prep_grid(), 256, 0, s>>>((const float*)inv_s, m, cnt, V);
+    return cudaGetLastError();
+}
+
+cudaError_t k_counts_in(int cdt, const int32_t* cnt, VoxMap m, void* inv_s, cudaStream_t s) {
+    const int64_t V = (int64_t)m.nx * m.ny * m.nz;
+    if (V <= 0) return cudaSuccess;
+    if (cdt == F64) counts_in_kernel<double><<<prep_grid(), 256, 0, s>>>(cnt, m, (double*)inv_s, V);
+    else counts_in_kernel<float><<<prep_grid(), 256, 0, s>>>(cnt, m, (float*)inv_s, V);
     return cudaGetLastError();
 }
 

@@ -88,6 +88,7 @@ struct ntvs_ctx {
     int compute_req = F32;                // arithmetic of FP32-stored systems, applied at the next load
     int vdt = F32, cdt = F32, storage = NTVS_CSR32;
     std::vector<int64_t> block_ptr;
+    std::vector<int64_t> block_maxrow;   // longest row of each block
     int64_t* row_ptr = nullptr;
     int32_t* col = nullptr;
     void* val = nullptr;
@@ -105,7 +106,8 @@ struct ntvs_ctx {
     DropStage* stages = nullptr;       // pipelined schedule: all blocks' stages
     int32_t* stage_begin = nullptr;    // [B][win_grid + 1]
     int win_grid = 0;
-    float* wstat = nullptr;            // FP32 window scale per block: lmax [B], bound [B], observed [B]
+    float* wstat = nullptr;            // FP32 window scale per block: lmax [B], bound [B], observed [B],
+                                       // then per block the seed bound and max |a| [2B]
     int* derr = nullptr;               // device error word (bounded waits that ran out)
     // DELTA16 index storage (packed at load from the int32 columns)
     int16_t* col16 = nullptr;
@@ -152,6 +154,12 @@ struct ntvs_ctx {
     double* beta_tab = nullptr;       // beta0 * alpha^ell, ell < kBetaTab (host-computed)
     double tab_beta0 = -1.0, tab_alpha = -1.0;
     int check_grid = 0;               // co-resident grid of the retry loop (0: host decisions)
+
+    // row-sharded reconstruction: every DROP block's delta is summed over ranks by this
+    // callback before it is applied (null: this context holds every row)
+    ntvs_allreduce_fn ar_fn = nullptr;
+    void* ar_user = nullptr;
+    void* ext = nullptr;              // staging of host-side deltas and hit counts (V x 8 bytes)
 
     // bounded device waits: budget per wait and the test hook that starves a wait
     uint64_t wait_ns = kDefaultWaitNs;
@@ -501,24 +509,20 @@ int perturb_steps(ntvs_ctx* c, int64_t* ell_io) {
 }
 
 // ---- block-DROP ------------------------------------------------------------------------
-int drop_block(ntvs_ctx* c, int t) {
-    const int64_t r0 = c->block_ptr[t], r1 = c->block_ptr[t + 1];
-    // the split copies of x are written by the last block of a sweep only (the TV gradient
-    // reads them next); after any other block they are marked stale
-    const bool split = t == c->B - 1;
-    CUDA_TRY(cudaMemsetAsync(c->resid + t, 0, sizeof(double), c->stream));
+// Launches the DROP gather + scatter kernel of rows [r0, r1) of block t into delta
+// (nothing applied), its residual sum of squares into *resid.  The whole block runs the
+// context's schedule; a proper sub-range of it runs the plain schedule (the windowed and
+// pipelined plans cover whole blocks).  *wb / *wo receive the block's window-scale slots
+// for the apply kernel (null when the schedule has none).
+int launch_drop_kernel(ntvs_ctx* c, int t, int64_t r0, int64_t r1, double* resid, float** wb, float** wo) {
+    *wb = *wo = nullptr;
     if (r1 <= r0) return NTVS_OK;
+    const bool whole = r0 == c->block_ptr[t] && r1 == c->block_ptr[t + 1];
     if (c->paths_mode) {
         CUDA_TRY(timed_launch(c, KIND_DROP, [&] {
             return k_otf_drop(c->otf, r0, r1, (const float*)c->inv_norm2, c->x32, (float*)c->delta, c->p.lambda,
-                              c->resid + t, c->stream);
+                              resid, c->stream);
         }));
-        CUDA_TRY(timed_launch(c, KIND_APPLY, [&] {
-            return k_drop_apply(c->cdt, c->x, c->copies(split), c->delta,
-                                (const char*)c->inv_s + (size_t)t * c->vm.vint * c->csz(), c->V, c->apply_grid,
-                                nullptr, nullptr, c->stream);
-        }));
-        c->split_stale = !split;
         return NTVS_OK;
     }
     DropArgs a;
@@ -532,7 +536,7 @@ int drop_block(ntvs_ctx* c, int t) {
     a.x = (c->cdt == F64) ? (const void*)c->x : (const void*)c->x32;
     a.delta = c->delta;
     a.lambda = c->p.lambda;
-    a.resid_ss = c->resid + t;
+    a.resid_ss = resid;
     a.vdt = c->vdt;
     a.cdt = c->cdt;
     a.lanes_per_row = c->lpr;
@@ -546,19 +550,20 @@ int drop_block(ntvs_ctx* c, int t) {
     a.wlmax = nullptr;
     a.wbound = nullptr;
     a.wobs = nullptr;
-    float* wb = nullptr;
-    float* wo = nullptr;
-    if (c->schedule == NTVS_SCHED_WINDOW) {
+    a.wamax = nullptr;
+    a.max_row = t < (int)c->block_maxrow.size() ? c->block_maxrow[t] : (int64_t)1 << 40;
+    if (whole && c->schedule == NTVS_SCHED_WINDOW) {
         a.segs = c->segs;
         a.seg_begin = c->seg_begin + (size_t)t * (c->win_grid + 1);
         a.grid = c->win_grid;
         if (c->wstat) {
             a.wlmax = c->wstat + t;
-            a.wbound = wb = c->wstat + c->B + t;
-            a.wobs = wo = c->wstat + 2 * c->B + t;
+            a.wbound = *wb = c->wstat + c->B + t;
+            a.wobs = *wo = c->wstat + 2 * c->B + t;
+            a.wamax = c->wstat + 3 * c->B + 2 * t + 1;
         }
     }
-    if (c->schedule == NTVS_SCHED_PIPELINE) {
+    if (whole && c->schedule == NTVS_SCHED_PIPELINE) {
         DropPipeArgs pa;
         pa.row_ptr = c->row_ptr;
         pa.col = c->col;
@@ -571,7 +576,7 @@ int drop_block(ntvs_ctx* c, int t) {
         pa.x = a.x;
         pa.delta = c->delta;
         pa.lambda = c->p.lambda;
-        pa.resid_ss = c->resid + t;
+        pa.resid_ss = resid;
         pa.err = c->derr;
         pa.wait_ns = c->wait_ns;
         pa.starve = (c->hook_flags & NTVS_HOOK_STARVE_PIPE) ? 1 : 0;
@@ -583,6 +588,29 @@ int drop_block(ntvs_ctx* c, int t) {
         CUDA_TRY(timed_launch(c, KIND_DROP, [&] { return k_drop_pipe(pa, c->stream); }));
     } else {
         CUDA_TRY(timed_launch(c, KIND_DROP, [&] { return k_drop_block(a, c->stream); }));
+    }
+    return NTVS_OK;
+}
+
+// One block-DROP step: this context's rows of block t into delta, the sum over ranks
+// through the all-reduce callback when one is set (row-sharded reconstruction), then
+// x += delta / s^t.
+int drop_block(ntvs_ctx* c, int t) {
+    const int64_t r0 = c->block_ptr[t], r1 = c->block_ptr[t + 1];
+    // the split copies of x are written by the last block of a sweep only (the TV gradient
+    // reads them next); after any other block they are marked stale
+    const bool split = t == c->B - 1;
+    CUDA_TRY(cudaMemsetAsync(c->resid + t, 0, sizeof(double), c->stream));
+    if (r1 <= r0 && !c->ar_fn) return NTVS_OK;
+    float* wb = nullptr;
+    float* wo = nullptr;
+    TRY(launch_drop_kernel(c, t, r0, r1, c->resid + t, &wb, &wo));
+    if (c->ar_fn) {
+        int rc = c->ar_fn(c->delta, c->vm.vint, c->cdt, (void*)c->stream, c->ar_user);
+        if (rc == 0) rc = c->ar_fn(c->resid + t, 1, NTVS_F64, (void*)c->stream, c->ar_user);
+        if (rc != 0)
+            return fail(NTVS_ERR_CUDA, "the all-reduce callback failed on block " + std::to_string(t) + " (returned " +
+                                           std::to_string(rc) + ")");
     }
     CUDA_TRY(timed_launch(c, KIND_APPLY, [&] {
         return k_drop_apply(c->cdt, c->x, c->copies(split), c->delta,
@@ -681,8 +709,9 @@ static int plan_schedule(ntvs_ctx* c, int requested) {
     const int64_t slice = c->vm.slice_p;
     int optin = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
-    const int64_t need = ((slice + 31) & ~31LL) * (int64_t)c->csz();
-    if (need + 1024 > optin) {
+    // the window plus the kernel's static shared memory (row-extent slots, reductions)
+    const int64_t need = ((slice + 31) & ~31LL) * (int64_t)c->csz() + 9 * 1024;
+    if (need > optin) {
         if (requested == NTVS_SCHED_WINDOW || requested == NTVS_SCHED_PIPELINE)
             return fail(NTVS_ERR_ARG, "windowed schedule: an nx*ny slice needs " + std::to_string(need) +
                                           " bytes of shared memory, the device allows " + std::to_string(optin));
@@ -931,6 +960,7 @@ int ntvs_destroy(ntvs_ctx* c) {
     dev_free(c->dev_ell_tr);
     dev_free(c->dev_tries);
     dev_free(c->dev_acc);
+    dev_free(c->ext);
     if (c->hll) cudaFreeHost(c->hll);
     for (auto& t : c->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
     for (auto e : c->event_pool) cudaEventDestroy(e);
@@ -1094,8 +1124,8 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
         ~FreeColsum() { dev_free(p); }
     } colsum_guard{colsum};
     if (c->cdt == F32) {
-        TRY(dev_alloc(&c->wstat, sizeof(float) * 3 * (size_t)c->B, "window scale statistics"));
-        CUDA_TRY(cudaMemsetAsync(c->wstat, 0, sizeof(float) * 3 * (size_t)c->B, st));
+        TRY(dev_alloc(&c->wstat, sizeof(float) * 5 * (size_t)c->B, "window scale statistics"));
+        CUDA_TRY(cudaMemsetAsync(c->wstat, 0, sizeof(float) * 5 * (size_t)c->B, st));
         TRY(dev_alloc(&colsum, sizeof(float) * (size_t)VI, "column sums"));
     }
     for (int t = 0; t < c->B; ++t) {
@@ -1105,8 +1135,30 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
         }
         if (colsum) CUDA_TRY(cudaMemsetAsync(colsum, 0, sizeof(float) * (size_t)VI, st));
         CUDA_TRY(k_prep_block(c->row_ptr, c->col, c->val, c->vdt, c->b, bp[t], bp[t + 1], VI, c->inv_norm2, c->cdt,
-                              cnt + (size_t)t * VI, c->dflags, colsum, colsum ? c->wstat + c->B + t : nullptr, st));
+                              cnt + (size_t)t * VI, c->dflags, colsum, colsum ? c->wstat + 3 * c->B + 2 * t : nullptr,
+                              st));
         if (colsum) CUDA_TRY(k_colmax(colsum, VI, c->wstat + t, st));
+    }
+    {   // longest row of every block
+        unsigned long long* dm = nullptr;
+        TRY(dev_alloc(&dm, sizeof(unsigned long long) * (size_t)c->B, "row lengths"));
+        std::vector<unsigned long long> hm((size_t)c->B, 0);
+        cudaError_t e = cudaMemsetAsync(dm, 0, sizeof(unsigned long long) * (size_t)c->B, st);
+        for (int t = 0; t < c->B && e == cudaSuccess; ++t) e = k_row_maxlen(c->row_ptr, bp[t], bp[t + 1], dm + t, c->sms * 4, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(hm.data(), dm, sizeof(unsigned long long) * (size_t)c->B, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        dev_free(dm);
+        if (e != cudaSuccess) return fail(NTVS_ERR_CUDA, cuda_msg("row lengths", e));
+        c->block_maxrow.assign(hm.begin(), hm.end());
+    }
+    if (c->wstat) {   // the first sweep's bound: max |b_i| / ||a_i||^2 (the residual at x = 0)
+        std::vector<float> ws((size_t)5 * c->B);
+        CUDA_TRY(cudaMemcpyAsync(ws.data(), c->wstat, sizeof(float) * ws.size(), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        for (int t = 0; t < c->B; ++t) ws[(size_t)c->B + t] = ws[(size_t)3 * c->B + 2 * t];
+        CUDA_TRY(cudaMemcpyAsync(c->wstat, ws.data(), sizeof(float) * ws.size(), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
     }
     CUDA_TRY(cudaMemcpyAsync(c->hint, c->dflags, sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
@@ -1164,6 +1216,8 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
     c->dev_pending = false;
     c->dstate_valid = false;
     c->check_grid = check_loop_max_grid(c->cdt, c->sms);
+    c->ar_fn = nullptr;   // a new system starts with its own (local) hit counts
+    c->ar_user = nullptr;
     CUDA_TRY(cudaStreamSynchronize(st));
     c->split_stale = false;
     c->loaded = true;
@@ -1271,6 +1325,8 @@ int ntvs_load_paths(ntvs_ctx* c, const ntvs_paths* s) {
     c->dev_pending = false;
     c->dstate_valid = false;
     c->check_grid = check_loop_max_grid(c->cdt, c->sms);
+    c->ar_fn = nullptr;   // a new system starts with its own (local) hit counts
+    c->ar_user = nullptr;
     CUDA_TRY(cudaStreamSynchronize(st));
     c->split_stale = false;
     c->loaded = true;
@@ -1627,6 +1683,141 @@ int ntvs_drop_sweep(ntvs_ctx* c) {
     TRY(use_device(c));
     TRY(need_system(c));
     return drop_sweep(c);
+}
+
+}  // extern "C"
+
+namespace {
+
+int ensure_ext(ntvs_ctx* c) {
+    if (!c->ext) TRY(dev_alloc(&c->ext, sizeof(double) * (size_t)std::max<int64_t>(c->V, 1), "staging buffer"));
+    return NTVS_OK;
+}
+
+int check_block_and_image(ntvs_ctx* c, int t, int dtype, int mem_kind) {
+    if (t < 0 || t >= c->B) return fail(NTVS_ERR_ARG, "block index out of range");
+    if (dtype != NTVS_F64 && dtype != NTVS_F32) return fail(NTVS_ERR_ARG, "dtype must be NTVS_F64 or NTVS_F32");
+    if (mem_kind != NTVS_MEM_HOST && mem_kind != NTVS_MEM_DEVICE) return fail(NTVS_ERR_ARG, "bad mem_kind");
+    return NTVS_OK;
+}
+
+const void* inv_s_of(ntvs_ctx* c, int t) { return (const char*)c->inv_s + (size_t)t * c->vm.vint * c->csz(); }
+
+}  // namespace
+
+extern "C" {
+
+int ntvs_drop_block_partial(ntvs_ctx* c, int t, int64_t r0, int64_t r1, void* delta_out, int dtype, int mem_kind,
+                            double* resid_ss) {
+    TRY(use_device(c));
+    TRY(need_system(c));
+    TRY(check_block_and_image(c, t, dtype, mem_kind));
+    if (!delta_out) return fail(NTVS_ERR_ARG, "null delta_out");
+    if (r0 < 0 && r1 < 0) {
+        r0 = c->block_ptr[t];
+        r1 = c->block_ptr[t + 1];
+    }
+    if (r0 < c->block_ptr[t] || r1 > c->block_ptr[t + 1] || r0 > r1)
+        return fail(NTVS_ERR_ARG, "rows [r0, r1) must lie inside block t");
+    CUDA_TRY(cudaMemsetAsync(c->dscal + 4, 0, sizeof(double), c->stream));
+    float* wb = nullptr;
+    float* wo = nullptr;
+    TRY(launch_drop_kernel(c, t, r0, r1, c->dscal + 4, &wb, &wo));
+    const size_t bytes = (size_t)c->V * dt_size(dtype);
+    if (mem_kind == NTVS_MEM_DEVICE) {
+        CUDA_TRY(k_delta_out(c->cdt, c->delta, c->vm, delta_out, dtype, c->stream));
+    } else {
+        TRY(ensure_ext(c));
+        CUDA_TRY(k_delta_out(c->cdt, c->delta, c->vm, c->ext, dtype, c->stream));
+        CUDA_TRY(cudaMemcpyAsync(delta_out, c->ext, bytes, cudaMemcpyDeviceToHost, c->stream));
+    }
+    if (resid_ss) CUDA_TRY(cudaMemcpyAsync(c->hscal + 4, c->dscal + 4, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (resid_ss || mem_kind == NTVS_MEM_HOST) {
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        if (resid_ss) *resid_ss = c->hscal[4];
+    }
+    return NTVS_OK;
+}
+
+int ntvs_apply_delta(ntvs_ctx* c, int t, const void* delta, int dtype, int mem_kind) {
+    TRY(use_device(c));
+    TRY(need_system(c));
+    TRY(check_block_and_image(c, t, dtype, mem_kind));
+    if (!delta) return fail(NTVS_ERR_ARG, "null delta");
+    const void* src = delta;
+    if (mem_kind == NTVS_MEM_HOST) {
+        TRY(ensure_ext(c));
+        CUDA_TRY(cudaMemcpyAsync(c->ext, delta, (size_t)c->V * dt_size(dtype), cudaMemcpyHostToDevice, c->stream));
+        src = c->ext;
+    }
+    CUDA_TRY(timed_launch(c, KIND_APPLY, [&] {
+        return k_apply_ext(c->cdt, c->x, c->copies(), src, dtype, inv_s_of(c, t), c->stream);
+    }));
+    c->split_stale = false;
+    if (mem_kind == NTVS_MEM_HOST) CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return NTVS_OK;
+}
+
+int ntvs_get_hit_counts(ntvs_ctx* c, int t, int32_t* out, int mem_kind) {
+    TRY(use_device(c));
+    TRY(need_system(c));
+    TRY(check_block_and_image(c, t, NTVS_F32, mem_kind));
+    if (!out) return fail(NTVS_ERR_ARG, "null output");
+    if (mem_kind == NTVS_MEM_DEVICE) {
+        CUDA_TRY(k_counts_out(c->cdt, inv_s_of(c, t), c->vm, out, c->stream));
+        return NTVS_OK;
+    }
+    TRY(ensure_ext(c));
+    CUDA_TRY(k_counts_out(c->cdt, inv_s_of(c, t), c->vm, (int32_t*)c->ext, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(out, c->ext, sizeof(int32_t) * (size_t)c->V, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return NTVS_OK;
+}
+
+int ntvs_set_hit_counts(ntvs_ctx* c, int t, const int32_t* counts, int mem_kind) {
+    TRY(use_device(c));
+    TRY(need_system(c));
+    TRY(check_block_and_image(c, t, NTVS_F32, mem_kind));
+    if (!counts) return fail(NTVS_ERR_ARG, "null counts");
+    const int32_t* src = counts;
+    if (mem_kind == NTVS_MEM_HOST) {
+        for (int64_t j = 0; j < c->V; ++j)
+            if (counts[j] < 0) return fail(NTVS_ERR_ARG, "hit counts must be >= 0");
+        TRY(ensure_ext(c));
+        CUDA_TRY(cudaMemcpyAsync(c->ext, counts, sizeof(int32_t) * (size_t)c->V, cudaMemcpyHostToDevice, c->stream));
+        src = (const int32_t*)c->ext;
+    }
+    CUDA_TRY(k_counts_in(c->cdt, src, c->vm, const_cast<void*>(inv_s_of(c, t)), c->stream));
+    if (mem_kind == NTVS_MEM_HOST) CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return NTVS_OK;
+}
+
+int ntvs_set_allreduce(ntvs_ctx* c, ntvs_allreduce_fn fn, void* user) {
+    TRY(use_device(c));
+    TRY(need_system(c));
+    if (!fn) {
+        c->ar_fn = nullptr;
+        c->ar_user = nullptr;
+        return NTVS_OK;
+    }
+    if (c->ar_fn) return fail(NTVS_ERR_STATE, "an all-reduce callback is already set (the counts are global)");
+    // global hit counts: this rank's counts of every block, summed over the ranks
+    const int64_t n = (int64_t)c->B * c->vm.vint;
+    int32_t* cnt = nullptr;
+    TRY(dev_alloc(&cnt, sizeof(int32_t) * (size_t)std::max<int64_t>(n, 1), "hit counts"));
+    struct Free {
+        int32_t*& p;
+        ~Free() { dev_free(p); }
+    } guard{cnt};
+    CUDA_TRY(k_counts_from_inv(c->cdt, c->inv_s, cnt, n, c->stream));
+    const int rc = fn(cnt, n, NTVS_I32, (void*)c->stream, user);
+    if (rc != 0) return fail(NTVS_ERR_CUDA, "the all-reduce callback failed on the hit counts (returned " +
+                                                std::to_string(rc) + ")");
+    CUDA_TRY(k_inv_counts(cnt, c->inv_s, c->cdt, n, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->ar_fn = fn;
+    c->ar_user = user;
+    return NTVS_OK;
 }
 
 }  // extern "C"

@@ -74,7 +74,8 @@ int red_grid(int64_t n, int sm_count);
 cudaError_t k_validate_rows(const int64_t* row_ptr, int64_t M, int* flags, cudaStream_t s);
 // fused pass over the rows [r0, r1) of one block: validation of columns, values and b
 // (flags 4 / 8 / 16), inv_norm2 of the rows and the block's hit counts cnt; with colsum
-// (nullable) also colsum[j] += |a_ij| and *rb = max(*rb, max_i |b_i| / ||a_i||^2)
+// (nullable) also colsum[j] += |a_ij|, rb[0] = max(rb[0], max_i |b_i| / ||a_i||^2) and
+// rb[1] = max(rb[1], max |a_ij|)
 cudaError_t k_prep_block(const int64_t* row_ptr, const int32_t* col, const void* val, int vdt, const void* b,
                          int64_t r0, int64_t r1, int64_t nvox, void* inv_norm2, int cdt, int32_t* cnt, int* flags,
                          float* colsum, float* rb, cudaStream_t s);
@@ -163,8 +164,13 @@ struct DropArgs {
     const float* wlmax;
     const float* wbound;
     float* wobs;
+    const float* wamax;   // max |a_ij| of the block: rows whose terms could reach 2^22 Q go global
+    int64_t max_row;      // longest row of the block (register steps of the windowed kernel)
 };
 cudaError_t k_drop_block(const DropArgs& a, cudaStream_t s);
+// *out = max(*out, longest row of rows [r0, r1)); *out zeroed by the caller
+cudaError_t k_row_maxlen(const int64_t* row_ptr, int64_t r0, int64_t r1, unsigned long long* out, int grid,
+                         cudaStream_t s);
 // home[i] = median z-slice of the first, middle and last entries of row i (-1: empty row)
 cudaError_t k_row_home(const int64_t* row_ptr, const int32_t* col, int64_t M, int64_t slice, int32_t* home, int grid,
                        cudaStream_t s);
@@ -238,6 +244,17 @@ cudaError_t k_hist_to_paths(const float* hist, int64_t M, float* rec, int* flags
 cudaError_t k_otf_prep(const OtfArgs& a, int64_t r0, int64_t r1, float* inv_norm2, int32_t* cnt, cudaStream_t s);
 cudaError_t k_otf_drop(const OtfArgs& a, int64_t r0, int64_t r1, const float* inv_norm2, const float* x, float* delta,
                        double lambda, double* resid_ss, cudaStream_t s);
+
+// ------------------------------------------------------------------ row-sharded DROP
+// out[j] = delta[internal(j)] in type odt (F32/F64), then delta = 0 (canonical j < V)
+cudaError_t k_delta_out(int cdt, void* delta, VoxMap m, void* out, int odt, cudaStream_t s);
+// x_j += d[j] * inv_s[internal(j)], d canonical of type ddt (F32/F64), and the FP32 copies
+cudaError_t k_apply_ext(int cdt, double* x, ImgCopies c, const void* d, int ddt, const void* inv_s, cudaStream_t s);
+// cnt[p] = round(1 / inv_s[p]) (0 where inv_s = 0), n slots of one order
+cudaError_t k_counts_from_inv(int cdt, const void* inv_s, int32_t* cnt, int64_t n, cudaStream_t s);
+// canonical counts of a block from its internal-order inverse counts, and back
+cudaError_t k_counts_out(int cdt, const void* inv_s, VoxMap m, int32_t* cnt, cudaStream_t s);
+cudaError_t k_counts_in(int cdt, const int32_t* cnt, VoxMap m, void* inv_s, cudaStream_t s);
 
 // ------------------------------------------------------------------ TV check on the device
 // Error codes written to the device error word by bounded waits (the host reports them as
