@@ -611,7 +611,7 @@ def run_ntvs(args):
             import torch as _t
             vbf = _t.from_numpy(s.val).to(_t.bfloat16)
             case("bf16 lengths + int32 columns", vals=vbf, vb=2)
-            case("bf16 lengths + delta16 columns", vals=vbf, vb=2, ib=2, storage=ntvs.NTVS_DELTA16)
+            case("bf16 lengths + delta16 columns", vals=vbf, vb=2, ib=2.125, storage=ntvs.NTVS_DELTA16)
     for c in cases:
         rm = ntvs.Reconstructor(local, stream.cuda_stream).set_voxel_tile(*c["tile"])
         rm.set_compute_dtype(c["compute"])
@@ -635,11 +635,10 @@ def run_ntvs(args):
         pm = rm.profile()
         stf = rm.stats()
         rm.close()
-        extra = 8 if c["storage"] == ntvs.NTVS_DELTA16 else 0
         b_item = 8 if stm["compute_dtype"] == ntvs.NTVS_F64 else 4   # b and 1/||a||^2 per row
-        bytes_m = float(np.mean(algorithmic_drop_bytes(s, c["vb"], b_item, index_bytes=c["ib"],
-                                                       extra_row_bytes=extra))) + \
-            8.0 * stm["n_escaped"] / spec.n_blocks
+        # DELTA16: 2-byte offsets plus a 4-byte base per 32 entries, 128 bytes per escaped chunk
+        bytes_m = float(np.mean(algorithmic_drop_bytes(s, c["vb"], b_item, index_bytes=c["ib"]))) + \
+            128.0 * stm["n_escaped"] / spec.n_blocks
         avg_m = pm["drop_block_ms"] / max(pm["drop_block_launches"], 1)
         ach = bytes_m / (avg_m / 1e3) / 1e9
         steps_done = max(stf["n_steps"] - n0["n_steps"], 1)

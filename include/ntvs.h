@@ -58,7 +58,11 @@ extern "C" {
 
 /* index storage of the system on the device */
 #define NTVS_CSR32 0     /* int32 column per entry                                      */
-#define NTVS_DELTA16 1   /* uint16 column deltas along each row, packed at load time    */
+#define NTVS_DELTA16 1   /* 16-bit columns, packed at load time: the entries are cut into
+                            aligned chunks of 32; each chunk keeps its smallest column as an
+                            int32 base and every entry its uint16 offset from it (a chunk
+                            whose columns span more than 65535 keeps full int32 columns);
+                            2.125 bytes per entry plus escapes                              */
 
 typedef struct ntvs_ctx ntvs_ctx;
 
@@ -136,7 +140,7 @@ typedef struct {
     int64_t n_launches;    /* kernels this context has launched (all entry points)       */
     int32_t drop_schedule; /* NTVS_SCHED_PLAIN, _WINDOW or _PIPELINE (chosen at load)      */
     int32_t lanes_per_row; /* lanes per row of the DROP kernel                           */
-    int64_t n_escaped;     /* DELTA16: column differences kept in the exception lists    */
+    int64_t n_escaped;     /* DELTA16: 32-entry chunks stored with full columns          */
     int32_t voxel_tile_x;  /* internal voxel tile of the loaded system (1 = canonical)   */
     int32_t voxel_tile_y;
 } ntvs_stats;

@@ -16,7 +16,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 SO = os.path.join(PKG, "libntvs.so")
-SOURCES = ["ntvs_api.cu", "kernels_tv.cu", "kernels_prep.cu", "kernels_drop.cu", "kernels_drop_tma.cu",
+SOURCES = ["ntvs_api.cu", "kernels_tv.cu", "kernels_prep.cu", "kernels_drop.cu", "kernels_drop_d16.cu",
+           "kernels_drop_tma.cu",
            "kernels_onthefly.cu", "batch.cu", "tv_static.cu",
            "kernels_check.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

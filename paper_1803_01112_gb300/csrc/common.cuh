@@ -55,36 +55,6 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
     return t;
 }
 
-// inclusive prefix sum over the 32 lanes of a warp
-__device__ __forceinline__ int warp_inclusive_scan(int v) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += t;
-    }
-    return v;
-}
-
-// DELTA16 decoding of one 32-entry chunk of a row (all lanes together): this lane's
-// stored difference d16 at entry k of the row (valid lanes only); escaped differences
-// come from the row's exception list ex[0..ne).  carry holds the column of the entry
-// before the chunk (the row's base column before the first chunk, whose difference is 0)
-// and is advanced to the chunk's last column.
-__device__ __forceinline__ int decode_delta16(int d16, bool valid, int k, const int2* ex, int ne, int& carry) {
-    int d = valid ? d16 : 0;
-    if (valid && d16 == kDeltaEscape) {
-        d = 0;
-        for (int e = 0; e < ne; ++e) {
-            const int2 v = __ldg(ex + e);
-            if (v.x == k) { d = v.y; break; }
-        }
-    }
-    const int c = carry + warp_inclusive_scan(d);
-    carry = __shfl_sync(0xffffffffu, c, 31);
-    return c;
-}
-
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -101,36 +101,32 @@ __device__ __forceinline__ void pipe_row(const int32_t* cs, const V* vs, int o0,
     for (int q = o0 + lane; q < o1; q += 32) scatter_w(win, W, w0, delta, cs[q], r * (T)to_compute(vs[q]));
 }
 
-// the same on DELTA16 storage: cs holds the row's int16 column differences
+// the same on DELTA16 storage: cs holds the row's 16-bit column offsets, cs[o0] being the
+// row's first entry, system entry g0 + o0; entry q's column adds the base of its chunk,
+// slot (p0 >> 5) + i + (q - o0) / 32, or comes from the escape table
+__device__ __forceinline__ int32_t d16_col_of(const Delta16& d, const int32_t* cbr, int rel, int o) {
+    const int32_t base = __ldg(cbr + (rel >> 5));
+    return base >= 0 ? base + o : __ldg(d.exc + ((int64_t)(-1 - base) << 5) + (rel & 31));
+}
+
 template <typename T, typename V>
-__device__ __forceinline__ void pipe_row_d16(const int16_t* cs, const V* vs, int o0, int o1, int64_t i,
+__device__ __forceinline__ void pipe_row_d16(const uint16_t* cs, const V* vs, int o0, int o1, int64_t g0, int64_t i,
                                              const Delta16& d16, const T* b, const T* inv_norm2, const T* x, T* win,
                                              int W, int64_t w0, T* delta, T lambda, double& ss) {
     const int lane = threadIdx.x & 31;
     const T bi = __ldg(b + i), ni = __ldg(inv_norm2 + i);
-    const int32_t base = __ldg(d16.base + i);
-    const int e0 = __ldg(d16.exc_off + i), ne = __ldg(d16.exc_off + i + 1) - e0;
-    const int2* ex = d16.exc + e0;
+    const int32_t* cbr = d16.cbase + ((g0 + o0) >> 5) + i;
     T acc = (T)0;
-    int carry = base;
-    for (int qb = o0; qb < o1; qb += 32) {
-        const int q = qb + lane;
-        const bool valid = q < o1;
-        const int c = decode_delta16(valid ? (int)cs[q] : 0, valid, q - o0, ex, ne, carry);
-        if (valid) acc += (T)to_compute(vs[q]) * __ldg(x + c);
-    }
+#pragma unroll 4
+    for (int q = o0 + lane; q < o1; q += 32) acc += (T)to_compute(vs[q]) * __ldg(x + d16_col_of(d16, cbr, q - o0, cs[q]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     const T res = bi - acc;
     const T r = lambda * res * ni;
     if (lane == 0) ss += (double)res * (double)res;
-    carry = base;
-    for (int qb = o0; qb < o1; qb += 32) {
-        const int q = qb + lane;
-        const bool valid = q < o1;
-        const int c = decode_delta16(valid ? (int)cs[q] : 0, valid, q - o0, ex, ne, carry);
-        if (valid) scatter_w(win, W, w0, delta, c, r * (T)to_compute(vs[q]));
-    }
+#pragma unroll 4
+    for (int q = o0 + lane; q < o1; q += 32)
+        scatter_w(win, W, w0, delta, d16_col_of(d16, cbr, q - o0, cs[q]), r * (T)to_compute(vs[q]));
 }
 
 template <typename T>
@@ -274,11 +270,11 @@ drop_pipe_kernel(const int64_t* __restrict__ row_ptr, const IdxT* __restrict__ c
             if constexpr (kD16) {
                 if (nent > 0) {
                     pipe_row_d16<T, V>(ring_c + (size_t)slot * S, ring_v + (size_t)slot * S, st.off[j], st.off[j + 1],
-                                       i, d16, b, inv_norm2, x, win, W, w0, delta, lambda, ss);
+                                       st.e0, i, d16, b, inv_norm2, x, win, W, w0, delta, lambda, ss);
                 } else {
                     const int64_t p0 = row_ptr[i], p1 = row_ptr[i + 1];
-                    pipe_row_d16<T, V>(col + p0, val + p0, 0, (int)(p1 - p0), i, d16, b, inv_norm2, x, win, W, w0,
-                                       delta, lambda, ss);
+                    pipe_row_d16<T, V>(col + p0, val + p0, 0, (int)(p1 - p0), p0, i, d16, b, inv_norm2, x, win, W,
+                                       w0, delta, lambda, ss);
                 }
             } else {
                 if (nent > 0) {
@@ -334,7 +330,7 @@ static cudaError_t launch_pipe_idx(const DropPipeArgs& a, const IdxT* col, cudaS
 
 template <typename T, typename V>
 static cudaError_t launch_pipe(const DropPipeArgs& a, cudaStream_t s) {
-    if (a.use_d16) return launch_pipe_idx<T, V, int16_t>(a, a.d16.col16, s);
+    if (a.use_d16) return launch_pipe_idx<T, V, uint16_t>(a, a.d16.off, s);
     return launch_pipe_idx<T, V, int32_t>(a, a.col, s);
 }
 

@@ -177,68 +177,73 @@ cudaError_t k_prep_block(const int64_t* row_ptr, const int32_t* col, const void*
 }
 
 // ------------------------------------------------------------------ DELTA16 packing
-// Row i stores base[i] = col[p0] and, for every entry k of the row, the int16 difference
-// d_k = col[p0+k] - col[p0+k-1] (d_0 = 0).  A difference outside [-32767, 32767] is stored
-// as kDeltaEscape and its value goes to the row's exception list (entry index, delta).
+// A warp per row, chunk by chunk: the chunk's smallest and largest column decide between
+// base + 16-bit offsets and an escaped chunk of full columns.
 
-// exceptions per row
+__device__ __forceinline__ void chunk_range(const int32_t* __restrict__ col, int64_t p, int64_t p1, int32_t& c,
+                                            int32_t& lo, int32_t& hi) {
+    c = p < p1 ? col[p] : -1;
+    lo = __reduce_min_sync(0xffffffffu, p < p1 ? c : 0x7fffffff);
+    hi = __reduce_max_sync(0xffffffffu, c);
+}
+
 __global__ void delta16_count_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int64_t M,
-                                     int32_t* __restrict__ cnt) {
+                                     unsigned long long* n_esc) {
     const int lane = threadIdx.x & 31;
-    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = w0; i < M; i += nw) {
+    unsigned long long n = 0;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < M;
+         i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         const int64_t p0 = row_ptr[i], p1 = row_ptr[i + 1];
-        int n = 0;
-        for (int64_t p = p0 + 1 + lane; p < p1; p += 32) {
-            const int64_t d = (int64_t)col[p] - (int64_t)col[p - 1];
-            n += (d < -32767 || d > 32767) ? 1 : 0;
+        for (int64_t pc = p0; pc < p1; pc += 32) {
+            int32_t c, lo, hi;
+            chunk_range(col, pc + lane, p1, c, lo, hi);
+            if ((int64_t)hi - (int64_t)lo > 65535) ++n;
         }
-        for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
-        if (lane == 0) cnt[i] = n;
     }
+    if (lane == 0 && n) atomicAdd(n_esc, n);
 }
 
 __global__ void delta16_fill_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int64_t M,
-                                    const int32_t* __restrict__ exc_off, int16_t* __restrict__ col16,
-                                    int32_t* __restrict__ base, int2* __restrict__ exc) {
+                                    uint16_t* __restrict__ off, int32_t* __restrict__ cbase, int32_t* __restrict__ exc,
+                                    uint8_t* __restrict__ rowesc, unsigned long long* slot) {
     const int lane = threadIdx.x & 31;
-    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = w0; i < M; i += nw) {
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < M;
+         i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         const int64_t p0 = row_ptr[i], p1 = row_ptr[i + 1];
-        if (lane == 0) base[i] = (p1 > p0) ? col[p0] : 0;
-        int written = 0;   // exceptions of this row written so far (warp-uniform)
-        for (int64_t pb = p0; pb < p1; pb += 32) {
-            const int64_t p = pb + lane;
-            bool esc = false;
-            int32_t d = 0;
-            if (p < p1 && p > p0) {
-                const int64_t dd = (int64_t)col[p] - (int64_t)col[p - 1];
-                esc = dd < -32767 || dd > 32767;
-                d = (int32_t)dd;
+        int32_t* cb = cbase + (p0 >> 5) + i;
+        bool any = false;
+        for (int64_t pc = p0, k = 0; pc < p1; pc += 32, ++k) {
+            const int64_t p = pc + lane;
+            int32_t c, lo, hi;
+            chunk_range(col, p, p1, c, lo, hi);
+            if ((int64_t)hi - (int64_t)lo <= 65535) {
+                if (p < p1) off[p] = (uint16_t)(c - lo);
+                if (lane == 0) cb[k] = lo;
+            } else {
+                unsigned long long e = 0;
+                if (lane == 0) e = atomicAdd(slot, 1ull);
+                e = __shfl_sync(0xffffffffu, e, 0);
+                exc[(int64_t)(e << 5) + lane] = p < p1 ? c : 0;
+                if (p < p1) off[p] = 0;
+                if (lane == 0) cb[k] = -1 - (int32_t)e;
+                any = true;
             }
-            if (p < p1) col16[p] = esc ? (int16_t)kDeltaEscape : (int16_t)d;
-            const unsigned m = __ballot_sync(0xffffffffu, esc);
-            if (esc) {
-                const int rank = __popc(m & ((1u << lane) - 1));
-                exc[exc_off[i] + written + rank] = make_int2((int)(p - p0), d);
-            }
-            written += __popc(m);
         }
+        if (lane == 0) rowesc[i] = any ? 1 : 0;
     }
 }
 
-cudaError_t k_delta16_count(const int64_t* row_ptr, const int32_t* col, int64_t M, int32_t* cnt, cudaStream_t s) {
+cudaError_t k_delta16_count(const int64_t* row_ptr, const int32_t* col, int64_t M, unsigned long long* n_esc,
+                            cudaStream_t s) {
     if (M <= 0) return cudaSuccess;
-    delta16_count_kernel<<<prep_grid(), 256, 0, s>>>(row_ptr, col, M, cnt);
+    delta16_count_kernel<<<prep_grid(), 256, 0, s>>>(row_ptr, col, M, n_esc);
     return cudaGetLastError();
 }
 
-cudaError_t k_delta16_fill(const int64_t* row_ptr, const int32_t* col, int64_t M, const int32_t* exc_off,
-                           int16_t* col16, int32_t* base, int2* exc, cudaStream_t s) {
+cudaError_t k_delta16_fill(const int64_t* row_ptr, const int32_t* col, int64_t M, uint16_t* off, int32_t* cbase,
+                           int32_t* exc, uint8_t* rowesc, unsigned long long* slot, cudaStream_t s) {
     if (M <= 0) return cudaSuccess;
-    delta16_fill_kernel<<<prep_grid(), 256, 0, s>>>(row_ptr, col, M, exc_off, col16, base, exc);
+    delta16_fill_kernel<<<prep_grid(), 256, 0, s>>>(row_ptr, col, M, off, cbase, exc, rowesc, slot);
     return cudaGetLastError();
 }
 

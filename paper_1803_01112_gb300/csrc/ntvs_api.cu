@@ -110,17 +110,17 @@ struct ntvs_ctx {
                                        // then per block the seed bound and max |a| [2B]
     int* derr = nullptr;               // device error word (bounded waits that ran out)
     // DELTA16 index storage (packed at load from the int32 columns)
-    int16_t* col16 = nullptr;
-    int32_t* rbase = nullptr;
-    int32_t* exc_off = nullptr;
-    int2* exc = nullptr;
-    int64_t n_escaped = 0;
+    uint16_t* d16off = nullptr;        // [nnz] column - chunk base
+    int32_t* d16base = nullptr;        // [ceil(nnz/32)] chunk bases (negative: escaped chunk)
+    int32_t* d16exc = nullptr;         // [escaped chunks][32] full columns
+    uint8_t* d16rowesc = nullptr;      // [M] rows touching an escaped chunk
+    int64_t n_escaped = 0;             // escaped chunks
     // on-the-fly rows (ntvs_load_paths): path records and b, traced every sweep
     bool paths_mode = false;
     float* paths = nullptr;
     bool own_paths = false;
     OtfArgs otf{};
-    Delta16 d16() const { return Delta16{col16, rbase, exc_off, exc}; }
+    Delta16 d16() const { return Delta16{d16off, d16base, d16exc, d16rowesc}; }
 
     // image and scratch: x is the FP64 master image; x32 its FP32 copy gathered by the
     // FP32-path DROP kernels (null on the FP64 path)
@@ -206,10 +206,10 @@ struct ntvs_ctx {
         dev_free(wstat);
         dev_free(stages);
         dev_free(stage_begin);
-        dev_free(col16);
-        dev_free(rbase);
-        dev_free(exc_off);
-        dev_free(exc);
+        dev_free(d16off);
+        dev_free(d16base);
+        dev_free(d16exc);
+        dev_free(d16rowesc);
         n_escaped = 0;
         if (own_paths) dev_free(paths);
         paths = nullptr;
@@ -658,33 +658,30 @@ int copy_image_out(ntvs_ctx* c, const void* src, int sdt, void* out, int dtype, 
 }  // namespace
 
 // ---- DELTA16 packing (load time) -----------------------------------------------------------
-// Exceptions are counted per row on the device, offsets are summed on the host, then the
-// int16 differences, row bases and exception lists are written; int32 columns that the
-// context owns are released afterwards.
+// Escaped chunks are counted on the device, then offsets, chunk bases, the escape table and
+// the row flags are written (escape slots handed out by an atomic counter: their order does
+// not matter); int32 columns that the context owns are released afterwards.
 static int pack_delta16(ntvs_ctx* c) {
-    const int64_t M = c->M;
-    int32_t* cnt = nullptr;
-    TRY(dev_alloc(&cnt, sizeof(int32_t) * (size_t)std::max<int64_t>(M, 1), "DELTA16 exception counts"));
-    std::vector<int32_t> h((size_t)M + 1, 0);
-    cudaError_t e = k_delta16_count(c->row_ptr, c->col, M, cnt, c->stream);
-    if (e == cudaSuccess && M > 0)
-        e = cudaMemcpyAsync(h.data() + 1, cnt, sizeof(int32_t) * (size_t)M, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    dev_free(cnt);
-    if (e != cudaSuccess) return fail(NTVS_ERR_CUDA, cuda_msg("DELTA16 exception count", e));
-    int64_t total = 0;
-    for (int64_t i = 0; i < M; ++i) {   // h[i+1] holds row i's count; turn into offsets
-        total += h[(size_t)i + 1];
-        if (total > INT32_MAX) return fail(NTVS_ERR_ARG, "DELTA16: too many escaped differences");
-        h[(size_t)i + 1] = (int32_t)total;
-    }
-    TRY(dev_alloc(&c->col16, sizeof(int16_t) * (size_t)std::max<int64_t>(c->nnz, 8), "DELTA16 columns"));
-    TRY(dev_alloc(&c->rbase, sizeof(int32_t) * (size_t)std::max<int64_t>(M, 1), "DELTA16 row bases"));
-    TRY(dev_alloc(&c->exc_off, sizeof(int32_t) * h.size(), "DELTA16 exception offsets"));
-    TRY(dev_alloc(&c->exc, sizeof(int2) * (size_t)std::max<int64_t>(total, 1), "DELTA16 exceptions"));
-    c->n_escaped = total;
-    CUDA_TRY(cudaMemcpyAsync(c->exc_off, h.data(), sizeof(int32_t) * h.size(), cudaMemcpyHostToDevice, c->stream));
-    CUDA_TRY(k_delta16_fill(c->row_ptr, c->col, M, c->exc_off, c->col16, c->rbase, c->exc, c->stream));
+    const int64_t nnz = c->nnz, nch = delta16_slots(nnz, c->M);
+    unsigned long long* ctr = nullptr;
+    TRY(dev_alloc(&ctr, 2 * sizeof(unsigned long long), "DELTA16 counters"));
+    struct Free {
+        unsigned long long*& p;
+        ~Free() { dev_free(p); }
+    } guard{ctr};
+    unsigned long long n_esc = 0;
+    CUDA_TRY(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned long long), c->stream));
+    CUDA_TRY(k_delta16_count(c->row_ptr, c->col, c->M, ctr, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(&n_esc, ctr, sizeof(n_esc), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    TRY(dev_alloc(&c->d16off, sizeof(uint16_t) * (size_t)std::max<int64_t>(nnz, 8), "DELTA16 offsets"));
+    TRY(dev_alloc(&c->d16base, sizeof(int32_t) * (size_t)std::max<int64_t>(nch, 1), "DELTA16 chunk bases"));
+    TRY(dev_alloc(&c->d16exc, sizeof(int32_t) * 32 * (size_t)std::max<unsigned long long>(n_esc, 1),
+                  "DELTA16 escaped chunks"));
+    c->n_escaped = (int64_t)n_esc;
+    TRY(dev_alloc(&c->d16rowesc, (size_t)std::max<int64_t>(c->M, 1), "DELTA16 row flags"));
+    CUDA_TRY(k_delta16_fill(c->row_ptr, c->col, c->M, c->d16off, c->d16base, c->d16exc, c->d16rowesc, ctr + 1,
+                            c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (c->own_col) {
         dev_free(c->col);

@@ -89,20 +89,27 @@ cudaError_t k_x32_from_x64(const double* x, ImgCopies c, cudaStream_t s);
 // inv_s[j] = cnt[j] ? 1/cnt[j] : 0
 cudaError_t k_inv_counts(const int32_t* cnt, void* inv_s, int cdt, int64_t n, cudaStream_t s);
 
-// DELTA16 index storage: base[i] = first column of row i; col16[p] = column difference to
-// the previous entry of the row (0 for the first), or kDeltaEscape when it does not fit
-// in [-32767, 32767]; the row's escaped differences are (entry index, difference) pairs
-// exc[exc_off[i] .. exc_off[i+1]).
-constexpr int kDeltaEscape = -32768;
+// DELTA16 index storage: every row is cut into chunks of 32 entries from its first entry;
+// chunk k of row i (entries p0 + 32k ..) has slot (p0 >> 5) + i + k (no two chunks share a
+// slot, since a row of n entries has at most n/32 + 1 chunks) and stores base cbase[slot] =
+// its smallest column, every entry the 16-bit offset off[p] = col[p] - base.  A chunk whose
+// columns span more than 65535 is escaped: cbase[slot] = -1 - e and its columns are
+// exc[32 e + (p - p0 - 32k)].  rowesc[i] = 1 when row i has an escaped chunk: only those
+// rows pay for the check; the others decode every column with one add.
 struct Delta16 {
-    const int16_t* col16;
-    const int32_t* base;
-    const int32_t* exc_off;   // [M + 1]
-    const int2* exc;
+    const uint16_t* off;      // [nnz]
+    const int32_t* cbase;     // [(nnz >> 5) + M + 1]
+    const int32_t* exc;       // [escaped chunks][32]
+    const uint8_t* rowesc;    // [M]
 };
-cudaError_t k_delta16_count(const int64_t* row_ptr, const int32_t* col, int64_t M, int32_t* cnt, cudaStream_t s);
-cudaError_t k_delta16_fill(const int64_t* row_ptr, const int32_t* col, int64_t M, const int32_t* exc_off,
-                           int16_t* col16, int32_t* base, int2* exc, cudaStream_t s);
+// slots of the chunk bases for nnz entries in M rows
+inline int64_t delta16_slots(int64_t nnz, int64_t M) { return (nnz >> 5) + M + 1; }
+// escaped chunks: *n_esc += their number (zeroed by the caller)
+cudaError_t k_delta16_count(const int64_t* row_ptr, const int32_t* col, int64_t M, unsigned long long* n_esc,
+                            cudaStream_t s);
+// writes off, cbase, exc and rowesc (escape slots taken from *slot, zeroed by the caller)
+cudaError_t k_delta16_fill(const int64_t* row_ptr, const int32_t* col, int64_t M, uint16_t* off, int32_t* cbase,
+                           int32_t* exc, uint8_t* rowesc, unsigned long long* slot, cudaStream_t s);
 
 // ------------------------------------------------------------------ TV
 // Scratch of the deterministic reductions: partials[2*grid] doubles and a ticket word
@@ -168,6 +175,7 @@ struct DropArgs {
     int64_t max_row;      // longest row of the block (register steps of the windowed kernel)
 };
 cudaError_t k_drop_block(const DropArgs& a, cudaStream_t s);
+cudaError_t k_drop_block_d16(const DropArgs& a, cudaStream_t s);   // the same on DELTA16 storage
 // *out = max(*out, longest row of rows [r0, r1)); *out zeroed by the caller
 cudaError_t k_row_maxlen(const int64_t* row_ptr, int64_t r0, int64_t r1, unsigned long long* out, int grid,
                          cudaStream_t s);

@@ -65,6 +65,54 @@ def test_delta16_with_many_escaped_jumps():
     assert rel_l2(got, want) < 1e-12
 
 
+@pytest.mark.parametrize("schedule", ["plain", "window", "pipeline"])
+def test_delta16_chunks_mix_packed_and_escaped(schedule):
+    """Rows of slowly varying columns with rare far jumps: most 32-entry chunks of a row are
+    stored as base + 16-bit offsets, the chunks holding a jump as full columns.  The count of
+    escaped chunks follows the format's definition exactly, and every schedule gives the
+    oracle's sweep."""
+    ntvs = ntvs_module()
+    from paper_1803_01112_gb300._ffi import NTVS_DELTA16, NTVS_SCHED_PIPELINE, NTVS_SCHED_PLAIN, NTVS_SCHED_WINDOW
+    sched = {"plain": NTVS_SCHED_PLAIN, "window": NTVS_SCHED_WINDOW, "pipeline": NTVS_SCHED_PIPELINE}[schedule]
+    rng = np.random.default_rng(11)
+    shape = (120, 120, 8)   # V = 115200 > 65535; an FP64 slice window of 115 KB
+    V = int(np.prod(shape))
+    M = 3000
+    lens = rng.integers(1, 140, size=M)
+    rp = np.zeros(M + 1, np.int64)
+    rp[1:] = np.cumsum(lens)
+    cols = []
+    for i, n in enumerate(lens):   # a walk of small steps inside one slice, a far jump now and then
+        z = (i * 8) // M
+        c = z * 14400 + int(rng.integers(0, 9000)) + np.cumsum(rng.integers(1, 40, size=n))
+        jump = rng.random(n) < 0.01
+        c = np.where(jump, rng.integers(0, V, size=n), c % V)
+        cols.append(c)
+    col = np.concatenate(cols).astype(np.int32)
+    val = rng.uniform(0.1, 1.0, size=col.size)
+    b = rng.uniform(5, 40, size=M)
+    x0 = rng.uniform(0.5, 1.5, size=V)
+    # chunks of 32 entries from each row's first entry; escaped when their columns span > 65535
+    spans = [np.ptp(c[k:k + 32]) for c in cols for k in range(0, len(c), 32)]
+    want_esc = int(sum(sp > 65535 for sp in spans))
+    n_chunks = len(spans)
+    r = ntvs.Reconstructor(0)
+    try:
+        r.set_voxel_tile(1, 1)
+        r.load(shape, rp, col, val, b, n_blocks=3, storage=NTVS_DELTA16, schedule=sched)
+        st = r.stats()
+        r.set_params(lam=0.9, N=0, alpha=0.5)
+        r.set_image(x0)
+        r.drop_sweep()
+        got = r.get_image()
+    finally:
+        r.close()
+    assert st["drop_schedule"] == sched
+    assert st["n_escaped"] == want_esc and 0 < want_esc < n_chunks // 2
+    want, _ = oracle.drop_sweep(rp, col, val, b, synth.block_partition(M, 3), x0, 0.9)
+    assert rel_l2(got, want) < 1e-12
+
+
 @pytest.mark.parametrize("kind", ["fp16", "bf16"])
 @pytest.mark.parametrize("storage", ["csr32", "delta16"])
 def test_half_values_match_oracle_on_stored_system(kind, storage):
