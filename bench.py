@@ -60,14 +60,17 @@ def parse_args(argv=None):
     ap.add_argument("--batch-members", type=int, default=64)
     ap.add_argument("--batch-scale", type=float, default=1.0)
     ap.add_argument("--onthefly", type=int, default=1, help="also time on-the-fly rows on the 256x256x64 grid")
-    ap.add_argument("--otf-histories", type=int, default=6_000_000)
+    ap.add_argument("--otf-histories", type=int, default=60_000_000)
     ap.add_argument("--tile", default="4x4", help="internal voxel tile of the FP32 path (1x1: canonical order)")
     ap.add_argument("--canonical", type=int, default=1,
                     help="also time the canonical voxel order on the same workload (0: skip)")
     ap.add_argument("--check", type=int, default=1,
                     help="also time N = 6 and the TV-reduction check on (N in {3, 6}) (0: skip)")
-    ap.add_argument("--cpu-rows", type=int, default=3_000_000, help="oracle sample: first rows of the workload")
-    ap.add_argument("--ref-rows", type=int, default=1_000_000, help="reference arm: rows per step")
+    ap.add_argument("--cpu-rows", type=int, default=3_000_000,
+                    help="single-threaded oracle sample: first rows of the workload")
+    ap.add_argument("--cpu-omp-rows", type=int, default=10_000_000,
+                    help="OpenMP oracle sample: first rows of the workload (default: all)")
+    ap.add_argument("--ref-rows", type=int, default=2_000_000, help="reference arm: rows per step")
     ap.add_argument("--schedule", choices=["auto", "plain", "window", "pipeline"], default="auto",
                     help="DROP kernel schedule (auto picks the windowed one for slice-ordered rows)")
     ap.add_argument("--rows", type=int, default=0,
@@ -212,9 +215,27 @@ def algorithmic_drop_bytes(s, val_itemsize, b_itemsize, index_bytes=4, extra_row
 
 
 # ------------------------------------------------------------------ CPU oracle timing
-def time_oracle(spec, vdt, rows, K=1):
+def host_cpu():
+    """(logical cores, CPU model) of this host."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return os.cpu_count() or 1, model
+
+
+def time_oracle(spec, vdt, rows, K=1, omp=False):
     """Oracle cycles on the first `rows` histories of the workload (blocks of the same
-    size as the workload's).  Returns (seconds per cycle, rows, blocks)."""
+    size as the workload's), with the single-threaded checker or its OpenMP timing build
+    (all host cores).  Returns (seconds per cycle, rows, blocks)."""
     import oracle
     import synth
     rows = min(rows, spec.n_hist)
@@ -226,8 +247,9 @@ def time_oracle(spec, vdt, rows, K=1):
     b = s.b.astype(vdt).astype(np.float64)
     shape = (spec.nx, spec.ny, spec.nz)
     prm = oracle.Params(lam=PARAMS["lam"], N=PARAMS["N"], alpha=PARAMS["alpha"], seed=PARAMS["seed"])
+    oracle.build(omp=omp)
     t0 = time.perf_counter()
-    oracle.ntvs(s.row_ptr, s.col, val, b, bp, shape, prm, K, s.xbar)
+    oracle.ntvs(s.row_ptr, s.col, val, b, bp, shape, prm, K, s.xbar, omp=omp)
     return (time.perf_counter() - t0) / K, rows, B
 
 
@@ -248,24 +270,27 @@ def run_reference(args):
     b = s.b.astype(vdt).astype(np.float64)
     shape = (spec.nx, spec.ny, spec.nz)
     prm = oracle.Params(lam=PARAMS["lam"], N=PARAMS["N"], alpha=PARAMS["alpha"], seed=PARAMS["seed"])
+    ncores, model = host_cpu()
+    oracle.build(omp=True)
     x = s.xbar.copy()
     ell = 0
     for k in range(args.warmup):
-        res = oracle.ntvs(s.row_ptr, s.col, val, b, bp, shape, prm, 1, x, k0=k, ell_prev=ell)
+        res = oracle.ntvs(s.row_ptr, s.col, val, b, bp, shape, prm, 1, x, k0=k, ell_prev=ell, omp=True)
         x, ell = res.x, res.ell_prev
     t0 = time.perf_counter()
     for k in range(args.warmup, args.warmup + args.steps):
-        res = oracle.ntvs(s.row_ptr, s.col, val, b, bp, shape, prm, 1, x, k0=k, ell_prev=ell)
+        res = oracle.ntvs(s.row_ptr, s.col, val, b, bp, shape, prm, 1, x, k0=k, ell_prev=ell, omp=True)
         x, ell = res.x, res.ell_prev
     dt = (time.perf_counter() - t0) / args.steps
     value = rows / dt
     sample = (f"first {rows} of {spec.n_hist} histories ({B} blocks of {per} rows), one NTVS cycle per step, "
-              "FP64 oracle in plain C")
+              f"FP64 C oracle built with OpenMP on {ncores} threads ({model})")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": spec.name, "n_blocks": spec.n_blocks, **PARAMS, "tv_check": False},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": ncores, "kind": "oracle", "sample": sample,
+                             "cpu_model": model},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -341,17 +366,47 @@ def run_batched_variant(args, ntvs, local, stream, world, device):
                       "4-8 random inserts, 20 blocks, (N, alpha, lambda) from the 72-combination sweep, no TV check"}
 
 
+def otf_kernel_hash():
+    h = hashlib.sha256()
+    for f in ("kernels_onthefly.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1803_01112_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def otf_profile_fractions():
+    """SM and L2 throughput (% of peak) of the on-the-fly DROP kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "otf_drop_kernel_fractions.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_src_sha256") != otf_kernel_hash():
+        return None
+    return {k: d[k] for k in ("sm_throughput_pct", "l2_throughput_pct", "dram_throughput_pct", "source")}
+
+
 def run_onthefly_variant(args, ntvs, local, stream, world, device):
     """256x256x64 grid (0.8x0.8x1.25 mm), bent paths over 720 angles, 40 blocks, N = 4,
-    rows traced in every sweep from 44-byte history records (10 path floats + b)."""
+    rows traced in every sweep from 44-byte history records (10 path floats + b).  The
+    path records come from the generator; b = (A x*)(1 + sigma z) is formed on the device by
+    projecting the phantom through the same traced paths (ntvs_forward_project) with the
+    generator's 1 % Gaussian noise from a seeded device generator."""
     import torch
 
     import synth
     spec = synth.spec_large_onthefly(n_hist=args.otf_histories)
-    pr = synth.generate_paths(spec)
+    pr = synth.generate_paths(spec, with_rhs=False)
+    paths = torch.from_numpy(pr.paths).to(device)
+    shape, voxel = (spec.nx, spec.ny, spec.nz), (spec.dx, spec.dy, spec.dz)
+    kw = dict(n_blocks=spec.n_blocks, n_seg=spec.n_seg, min_len=spec.min_len)
     r = ntvs.Reconstructor(local, stream.cuda_stream)
-    r.load_paths((spec.nx, spec.ny, spec.nz), (spec.dx, spec.dy, spec.dz), pr.paths, pr.b.astype(np.float32),
-                 n_blocks=spec.n_blocks, n_seg=spec.n_seg, min_len=spec.min_len)
+    r.load_paths(shape, voxel, paths, torch.zeros(spec.n_hist, dtype=torch.float32, device=device), **kw)
+    bclean = torch.empty(spec.n_hist, dtype=torch.float32, device=device)
+    r.forward_project(pr.xstar, out=bclean)
+    gen = torch.Generator(device=device).manual_seed(spec.seed)
+    b = bclean * (1.0 + spec.noise_sigma * torch.randn(spec.n_hist, generator=gen, device=device))
+    del bclean
+    r.load_paths(shape, voxel, paths, b, **kw)
     r.set_params(lam=2e-4, N=4, alpha=0.75, seed=5)
     r.set_image(pr.xbar)
     r.run(1)
@@ -359,13 +414,14 @@ def run_onthefly_variant(args, ntvs, local, stream, world, device):
     steps = max(1, min(args.steps, 5))
     barrier(world, device)
     torch.cuda.synchronize(device)
-    r.set_profiling(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     r.run(steps)
     e1.record(stream)
     torch.cuda.synchronize(device)
     ms = max_over_ranks(e0.elapsed_time(e1), world, device)
+    r.set_profiling(True)
+    r.run(1)
     prof = r.profile()
     r.close()
     avg = prof["drop_block_ms"] / max(prof["drop_block_launches"], 1)
@@ -375,7 +431,8 @@ def run_onthefly_variant(args, ntvs, local, stream, world, device):
             "histories": spec.n_hist, "drop_launch_ms": avg,
             "hbm_gb_s_per_drop_launch": hbm_bytes / (avg / 1e3) / 1e9,
             "bound": "alu + L2 atomics (path tracing; 60 B of HBM per history and launch)",
-            "note": "6M histories (the 60M-history layout with 1/10 of the histories); b traced on the host"}
+            "ncu_fractions": otf_profile_fractions(),
+            "note": "b = (A x*)(1 + 0.01 z) formed on the device through the traced paths"}
 
 
 def shard_system(spec, vdt, rank, world):
@@ -665,12 +722,18 @@ def run_ntvs(args):
     if args.onthefly:
         variants.append(run_onthefly_variant(args, ntvs, local, stream, world, device))
 
-    # ---- CPU oracle baseline (rank 0, one GPU only)
+    # ---- CPU oracle baseline (rank 0, one GPU only): the OpenMP timing build of the oracle on
+    # all host cores over the whole workload, and the single-threaded checker on a sample
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sec, rows, B = time_oracle(spec, vdt, args.cpu_rows)
-        cpu = {"value": rows / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"first {rows} of {spec.n_hist} histories ({B} blocks), one NTVS cycle, FP64 plain C"}
+        ncores, model = host_cpu()
+        sec, rows, B = time_oracle(spec, vdt, args.cpu_omp_rows, omp=True)
+        sec1, rows1, B1 = time_oracle(spec, vdt, args.cpu_rows)
+        cpu = {"value": rows / sec, "unit": UNIT, "cores": ncores, "kind": "oracle", "cpu_model": model,
+               "sample": f"first {rows} of {spec.n_hist} histories ({B} blocks), one NTVS cycle, FP64 C oracle "
+                         f"built with OpenMP on {ncores} threads (same source as the checker)",
+               "single_thread": {"value": rows1 / sec1, "cores": 1,
+                                 "sample": f"first {rows1} histories ({B1} blocks), one cycle, the checker build"}}
 
     r.close()
     if rank == 0:

@@ -358,6 +358,15 @@ int ntvs_drop_block(ntvs_ctx* ctx, int t);
 /* One full DROP sweep P_T (blocks 0..B-1 in order). */
 int ntvs_drop_sweep(ntvs_ctx* ctx);
 
+/* Forward projection: out[i] = <a_i, x> for every row i of the loaded system (the stored
+ * values, or the traced paths of ntvs_load_paths / ntvs_load_histories exactly as the DROP
+ * sweeps trace them), in the context's compute precision.  x: V values of x_dtype
+ * (NTVS_F64 / NTVS_F32, canonical order, host or device); out: M values of out_dtype (host
+ * or device, caller-owned).  The current image is not touched.  Allocates temporaries;
+ * synchronous.  The rows are the paper's system (Sec. I, Sec. III-D); the entry point
+ * itself (e.g. for synthetic right-hand sides b = A x) has no counterpart in the paper. */
+int ntvs_forward_project(ntvs_ctx* ctx, const void* x, int x_dtype, int x_mem, void* out, int out_dtype, int out_mem);
+
 /* ---- row-sharded DROP ---------------------------------------------------------------
  * All rows of a block see the same x (Sec. III-D, block-DROP of ref. CEHN08), so the rows
  * of every block may be split over several GPUs: each forms the sum over its rows,

@@ -35,16 +35,19 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ntvs_oracle.c")
 _SO = os.path.join(_HERE, "libntvs_oracle.so")
+_SO_OMP = os.path.join(_HERE, "libntvs_oracle_omp.so")   # timing build on all host cores
 
 
-def build_command(out: str = _SO):
-    return ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", out, _SRC, "-lm"]
+def build_command(out: str = _SO, omp: bool = False):
+    return ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared"] + (["-fopenmp"] if omp else []) + \
+        ["-o", out, _SRC, "-lm"]
 
 
-def build(force: bool = False) -> str:
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
-        subprocess.run(build_command(), check=True)
-    return _SO
+def build(force: bool = False, omp: bool = False) -> str:
+    so = _SO_OMP if omp else _SO
+    if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(_SRC):
+        subprocess.run(build_command(so, omp), check=True)
+    return so
 
 
 class _Params(ctypes.Structure):
@@ -60,14 +63,13 @@ class _Trace(ctypes.Structure):
                 ("beta_step", ctypes.c_void_p)]
 
 
-_L = None
+_L = {}
 
 
-def _lib():
-    global _L
-    if _L is None:
-        build()
-        L = ctypes.CDLL(_SO)
+def _lib(omp: bool = False):
+    """The checker (single-threaded) or, with omp, the OpenMP timing build of the same source."""
+    if omp not in _L:
+        L = ctypes.CDLL(build(omp=omp))
         vp, i64, u64, d, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_int32
         L.orc_splitmix64.argtypes = [u64, u64]; L.orc_splitmix64.restype = u64
         L.orc_rand_ell.argtypes = [u64, i64, i64]; L.orc_rand_ell.restype = i64
@@ -80,8 +82,8 @@ def _lib():
         L.orc_ntvs.argtypes = [vp, vp, vp, vp, vp, i32, i32, i32, i32, ctypes.POINTER(_Params),
                                i32, i32, ctypes.POINTER(i64), vp, vp, ctypes.POINTER(_Trace)]
         L.orc_ntvs.restype = i32
-        _L = L
-    return _L
+        _L[omp] = L
+    return _L[omp]
 
 
 def _f64(a):
@@ -193,8 +195,10 @@ class Result:
 
 
 def ntvs(row_ptr, col, val, b, block_ptr, shape, params: Params, K: int, x0,
-         k0: int = 0, ell_prev: int = 0, ell_override: Optional[np.ndarray] = None) -> Result:
-    """K cycles of NTVS from x0 (Appendix C); returns the image and the traces."""
+         k0: int = 0, ell_prev: int = 0, ell_override: Optional[np.ndarray] = None, omp: bool = False) -> Result:
+    """K cycles of NTVS from x0 (Appendix C); returns the image and the traces.  omp=True
+    runs the OpenMP timing build (all host cores; summation order differs) -- for timing
+    only, never as the checker."""
     nx, ny, nz = shape
     rp, c, v, bb = _csr(row_ptr, col, val, b)
     bp = np.ascontiguousarray(block_ptr, np.int64)
@@ -214,7 +218,7 @@ def ntvs(row_ptr, col, val, b, block_ptr, shape, params: Params, K: int, x0,
                 params.max_retries, int(params.step_rule), params.seed, params.gamma)
     ep = ctypes.c_int64(ell_prev)
     ov = None if ell_override is None else np.ascontiguousarray(ell_override, np.int64)
-    rc = _lib().orc_ntvs(rp.ctypes.data, c.ctypes.data, v.ctypes.data, bb.ctypes.data, bp.ctypes.data, B,
+    rc = _lib(omp).orc_ntvs(rp.ctypes.data, c.ctypes.data, v.ctypes.data, bb.ctypes.data, bp.ctypes.data, B,
                          nx, ny, nz, ctypes.byref(p), K, k0, ctypes.byref(ep), _ptr(ov), x.ctypes.data,
                          ctypes.byref(tr))
     if rc != 0:

@@ -36,10 +36,22 @@
  *     first step of the first cycle is beta0; it is stated without the check, and is
  *     only defined here without it.
  */
+/* The OpenMP pragmas below only act in the separate timing build (compiled with
+ * -fopenmp, used to time the method on all host cores); the checker is compiled without
+ * OpenMP, where they are ignored and every loop runs in the order written. */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+static int orc_nthreads(void) { return omp_get_max_threads(); }
+static int orc_thread(void) { return omp_get_thread_num(); }
+#else
+static int orc_nthreads(void) { return 1; }
+static int orc_thread(void) { return 0; }
+#endif
 
 /* ------------------------------------------------------------------ RNG */
 /* SplitMix64 (Steele, Lea, Flood 2014), counter form: output n of stream seed. */
@@ -74,6 +86,7 @@ static void fwd_diff(const double* x, int nx, int ny, int nz, int ix, int iy, in
 /* phi_eps(x) = sum_p sqrt(eps + sum_a d_a(p)^2); eps = 0 gives the TV phi. */
 double orc_tv(const double* x, int nx, int ny, int nz, double eps) {
     double s = 0.0;
+#pragma omp parallel for collapse(2) reduction(+ : s) schedule(static)
     for (int iz = 0; iz < nz; ++iz)
         for (int iy = 0; iy < ny; ++iy)
             for (int ix = 0; ix < nx; ++ix) {
@@ -97,6 +110,7 @@ static double Dval(const double* x, int nx, int ny, int nz, int ix, int iy, int 
  * A term whose D is 0 is 0 (its numerator is 0 as well). */
 void orc_tv_grad(const double* x, int nx, int ny, int nz, double eps, double* g) {
     const int n[3] = {nx, ny, nz};
+#pragma omp parallel for collapse(2) schedule(static)
     for (int iz = 0; iz < nz; ++iz)
         for (int iy = 0; iy < ny; ++iy)
             for (int ix = 0; ix < nx; ++ix) {
@@ -129,6 +143,7 @@ void orc_drop_block(const int64_t* row_ptr, const int32_t* col, const double* va
     double* num = (double*)calloc((size_t)V, sizeof(double));
     int64_t* s = (int64_t*)calloc((size_t)V, sizeof(int64_t));
     double ss = 0.0;
+#pragma omp parallel for reduction(+ : ss) schedule(static)
     for (int64_t i = r0; i < r1; ++i) {
         double dot = 0.0, nrm2 = 0.0;
         for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
@@ -139,11 +154,37 @@ void orc_drop_block(const int64_t* row_ptr, const int32_t* col, const double* va
         ss += res * res;
         r[i - r0] = (nrm2 > 0.0) ? res / nrm2 : 0.0;
     }
-    for (int64_t i = r0; i < r1; ++i)
-        for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
-            num[col[p]] += val[p] * r[i - r0];
-            if (val[p] != 0.0) s[col[p]] += 1;
+    /* num_j = sum_i a_ij r_i and s_j: each thread sums its rows into its own arrays, which
+     * are then added voxel by voxel (one thread: the rows in order, then 0 + that sum) */
+    const int nt = orc_nthreads();
+    double** pn = (double**)calloc((size_t)nt, sizeof(double*));
+    int64_t** ps = (int64_t**)calloc((size_t)nt, sizeof(int64_t*));
+#pragma omp parallel num_threads(nt)
+    {
+        const int t = orc_thread();
+        double* num_t = pn[t] = (double*)calloc((size_t)V, sizeof(double));
+        int64_t* s_t = ps[t] = (int64_t*)calloc((size_t)V, sizeof(int64_t));
+#pragma omp for schedule(static)
+        for (int64_t i = r0; i < r1; ++i)
+            for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
+                num_t[col[p]] += val[p] * r[i - r0];
+                if (val[p] != 0.0) s_t[col[p]] += 1;
+            }
+#pragma omp for schedule(static)
+        for (int64_t j = 0; j < V; ++j) {
+            double a = 0.0;
+            int64_t c = 0;
+            for (int u = 0; u < nt; ++u) {
+                a += pn[u][j];
+                c += ps[u][j];
+            }
+            num[j] = a;
+            s[j] = c;
         }
+    }
+    for (int u = 0; u < nt; ++u) { free(pn[u]); free(ps[u]); }
+    free(pn); free(ps);
+#pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < V; ++j)
         if (s[j] > 0) x[j] += lambda * num[j] / (double)s[j];
     if (resid_ss) *resid_ss = ss;
@@ -218,6 +259,7 @@ typedef struct {
 
 /* x <- x + beta * v, v = -g/||g|| (v = 0 when ||g|| = 0). */
 static void perturb(double* z, const double* x, const double* g, double gnorm, double beta, int64_t V) {
+#pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < V; ++j) z[j] = x[j] + ((gnorm > 0.0) ? beta * (-g[j] / gnorm) : 0.0);
 }
 
@@ -247,6 +289,7 @@ int orc_ntvs(const int64_t* row_ptr, const int32_t* col, const double* val, cons
         for (int n = 0; n < N; ++n) {
             orc_tv_grad(x, nx, ny, nz, prm->eps_tv, g);
             double gn = 0.0;
+#pragma omp parallel for reduction(+ : gn) schedule(static)
             for (int64_t j = 0; j < V; ++j) gn += g[j] * g[j];
             gn = sqrt(gn);
             double beta = (rule == 2) ? prm->beta0 * pow(prm->alpha, (double)n) * pow(prm->gamma, (double)k)

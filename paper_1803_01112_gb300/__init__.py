@@ -234,6 +234,13 @@ def ntvs_set_compute_dtype(ctx: int, dtype: int) -> None:
     check(lib().ntvs_set_compute_dtype(ctx, int(dtype)), "ntvs_set_compute_dtype")
 
 
+def ntvs_forward_project(ctx: int, x, out) -> None:
+    """out[i] = <a_i, x> for every row (x: V values, out: M values; F32/F64, host or device)."""
+    xp, xk = _ptr_kind(x)
+    op, ok = _ptr_kind(out)
+    check(lib().ntvs_forward_project(ctx, xp, _dtype_code(x), xk, op, _dtype_code(out), ok), "ntvs_forward_project")
+
+
 def ntvs_drop_block_partial(ctx: int, t: int, out, r0: int = -1, r1: int = -1) -> float:
     """delta of rows [r0, r1) of block t (default: the whole block) into `out` (V values,
     F32/F64, numpy = host or CUDA tensor = device), not applied; returns the rows' residual
@@ -623,6 +630,13 @@ class Reconstructor:
         """Arithmetic (NTVS_F32 or NTVS_F64) of FP32-stored systems, applied at the next load."""
         ntvs_set_compute_dtype(self._ctx, dtype)
         return self
+
+    def forward_project(self, x, out=None):
+        """A x for the loaded system (every row), as float64 unless `out` is given."""
+        if out is None:
+            out = np.empty(int(self.stats()["n_rows"]), np.float64)
+        ntvs_forward_project(self._ctx, x, out)
+        return out
 
     def drop_block_partial(self, t: int, out=None, r0: int = -1, r1: int = -1):
         """(delta, residual sum of squares) of rows [r0, r1) of block t, not applied."""

@@ -124,6 +124,7 @@ SIGNATURES = {
     "ntvs_perturb_checked": (ctypes.c_int, [vp, d, P(ctypes.c_int), P(d), P(d)]),
     "ntvs_drop_block": (ctypes.c_int, [vp, ctypes.c_int]),
     "ntvs_drop_sweep": (ctypes.c_int, [vp]),
+    "ntvs_forward_project": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int]),
     "ntvs_drop_block_partial": (ctypes.c_int, [vp, ctypes.c_int, i64, i64, vp, ctypes.c_int, ctypes.c_int, P(d)]),
     "ntvs_apply_delta": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int]),
     "ntvs_get_hit_counts": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int]),

@@ -64,6 +64,55 @@ cudaError_t k_drop_apply(int cdt, double* x, ImgCopies c, void* delta, const voi
     return cudaGetLastError();
 }
 
+// out_i = <a_i, x> for rows [0, M), a warp per row (x in the gather order of the stored
+// columns), for CSR32 or DELTA16 storage; accumulated in the compute type T.
+template <typename T, typename V, bool D16>
+__global__ void __launch_bounds__(256)
+project_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, Delta16 d16,
+               const V* __restrict__ val, int64_t M, const T* __restrict__ x, T* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w0; i < M; i += nw) {
+        const int64_t p0 = __ldg(row_ptr + i), p1 = __ldg(row_ptr + i + 1);
+        const int32_t* cbr = D16 ? d16.cbase + (p0 >> 5) + i : nullptr;
+        const uint16_t* offr = D16 ? d16.off + p0 : nullptr;
+        T acc = (T)0;
+        for (int64_t p = p0 + lane; p < p1; p += 32) {
+            const int32_t c = D16 ? d16_col<true>(d16, cbr, offr, (int)(p - p0)) : __ldg(col + p);
+            acc += (T)to_compute(val[p]) * __ldg(x + c);
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) out[i] = acc;
+    }
+}
+
+template <typename T, typename V>
+static cudaError_t launch_project(const DropArgs& a, int64_t M, const void* x, void* out, cudaStream_t s) {
+    if (a.use_d16)
+        project_kernel<T, V, true><<<a.grid, 256, 0, s>>>(a.row_ptr, a.col, a.d16, (const V*)a.val, M,
+                                                          (const T*)x, (T*)out);
+    else
+        project_kernel<T, V, false><<<a.grid, 256, 0, s>>>(a.row_ptr, a.col, a.d16, (const V*)a.val, M,
+                                                           (const T*)x, (T*)out);
+    return cudaGetLastError();
+}
+
+cudaError_t k_project(const DropArgs& a, int64_t M, const void* x, void* out, cudaStream_t s) {
+    if (M <= 0) return cudaSuccess;
+    if (a.cdt == F64) {
+        if (a.vdt == F64) return launch_project<double, double>(a, M, x, out, s);
+        if (a.vdt == F32) return launch_project<double, float>(a, M, x, out, s);
+        return cudaErrorInvalidValue;
+    }
+    switch (a.vdt) {
+        case F32: return launch_project<float, float>(a, M, x, out, s);
+        case F16: return launch_project<float, __half>(a, M, x, out, s);
+        case BF16: return launch_project<float, __nv_bfloat16>(a, M, x, out, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 // *out = max(*out, longest row of rows [r0, r1))
 __global__ void row_maxlen_kernel(const int64_t* __restrict__ row_ptr, int64_t r0, int64_t r1, unsigned long long* out) {
     unsigned long long m = 0;

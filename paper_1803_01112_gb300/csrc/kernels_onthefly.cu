@@ -254,6 +254,41 @@ __global__ void __launch_bounds__(kOtfThreads) otf_drop_kernel(const float* __re
     if (threadIdx.x == 0 && tot != 0.0) atomicAdd(resid_ss, tot);
 }
 
+// ---------------------------------------------------------------- forward projection
+// out_i = sum of l * x_v over the accepted pieces (voxel v, length l >= min_len) of history
+// i's path, the rows the DROP sweeps use; 16 lanes per row, each tracing every 16th segment.
+__global__ void __launch_bounds__(256) otf_project_kernel(const float* __restrict__ paths, int64_t M, Grid3 g,
+                                                           int n_seg, float min_len, const float* __restrict__ x,
+                                                           float* __restrict__ out) {
+    constexpr int LPR = 16;
+    const int lane = threadIdx.x & 31, sub = lane % LPR;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp * 2; base < M; base += nwarps * 2) {
+        const int64_t i = base + lane / LPR;
+        const bool valid = i < M;
+        float acc = 0.f;
+        if (valid) {
+            float pr[10];
+#pragma unroll
+            for (int q = 0; q < 10; ++q) pr[q] = __ldg(paths + i * 10 + q);
+            float nxv, nyv;
+            chord_normal(pr, nxv, nyv);
+            for (int sg = sub; sg < n_seg; sg += LPR) {
+                float A[3], B[3];
+                path_point(pr, nxv, nyv, (float)sg / (float)n_seg, A);
+                path_point(pr, nxv, nyv, (float)(sg + 1) / (float)n_seg, B);
+                trace_segment(g, A, B, [&](int v, float l) {
+                    if (l >= min_len) acc += l * __ldg(x + v);
+                });
+            }
+        }
+#pragma unroll
+        for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (valid && sub == 0) out[i] = acc;
+    }
+}
+
 // History data (P_in, P_out, d_in, d_out) -> path record (P_in, P_out, A_lat, B_lat, A_z, B_z):
 // end tangents m = L d / |d| (chord direction for a zero d), deviations m - c projected on
 // the chord's in-plane normal and on z.  flags |= 32 on a non-finite history value.
@@ -340,6 +375,12 @@ cudaError_t k_otf_drop(const OtfArgs& a, int64_t r0, int64_t r1, const float* in
     if (e != cudaSuccess) return e;
     otf_drop_kernel<<<a.grid, kOtfThreads, smem, s>>>(a.paths, a.b, inv_norm2, r0, r1, make_grid(a), a.n_seg,
                                                       a.min_len, x, delta, (float)lambda, resid_ss);
+    return cudaGetLastError();
+}
+
+cudaError_t k_otf_project(const OtfArgs& a, const float* x, float* out, cudaStream_t s) {
+    if (a.M <= 0) return cudaSuccess;
+    otf_project_kernel<<<a.grid, 256, 0, s>>>(a.paths, a.M, make_grid(a), a.n_seg, a.min_len, x, out);
     return cudaGetLastError();
 }
 

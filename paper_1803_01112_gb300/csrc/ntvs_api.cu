@@ -1704,6 +1704,76 @@ const void* inv_s_of(ntvs_ctx* c, int t) { return (const char*)c->inv_s + (size_
 
 extern "C" {
 
+int ntvs_forward_project(ntvs_ctx* c, const void* x, int x_dtype, int x_mem, void* out, int out_dtype, int out_mem) {
+    TRY(use_device(c));
+    TRY(need_system(c));
+    if (!x || (!out && c->M > 0)) return fail(NTVS_ERR_ARG, "null image or output");
+    if ((x_dtype != NTVS_F64 && x_dtype != NTVS_F32) || (out_dtype != NTVS_F64 && out_dtype != NTVS_F32))
+        return fail(NTVS_ERR_ARG, "dtypes must be NTVS_F64 or NTVS_F32");
+    if ((x_mem != NTVS_MEM_HOST && x_mem != NTVS_MEM_DEVICE) || (out_mem != NTVS_MEM_HOST && out_mem != NTVS_MEM_DEVICE))
+        return fail(NTVS_ERR_ARG, "bad mem_kind");
+    double* x64 = nullptr;
+    float* xg = nullptr;
+    void* oc = nullptr;
+    struct Free {
+        double*& a;
+        float*& b;
+        void*& c;
+        ~Free() { dev_free(a); dev_free(b); dev_free(c); }
+    } guard{x64, xg, oc};
+    cudaStream_t st = c->stream;
+    // x as FP64 canonical, then in the gather order of the stored columns
+    TRY(dev_alloc(&x64, sizeof(double) * (size_t)c->V, "projection image"));
+    if (x_mem == NTVS_MEM_DEVICE) {
+        CUDA_TRY(k_convert(x, x_dtype, x64, NTVS_F64, c->V, st));
+    } else if (x_dtype == NTVS_F64) {
+        CUDA_TRY(cudaMemcpyAsync(x64, x, sizeof(double) * (size_t)c->V, cudaMemcpyHostToDevice, st));
+    } else {
+        std::vector<double> tmp((size_t)c->V);
+        const float* xf = (const float*)x;
+        for (int64_t j = 0; j < c->V; ++j) tmp[(size_t)j] = xf[j];
+        CUDA_TRY(cudaMemcpyAsync(x64, tmp.data(), sizeof(double) * (size_t)c->V, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    const void* xs = x64;
+    if (c->cdt == F32) {
+        TRY(dev_alloc(&xg, sizeof(float) * (size_t)c->vm.vint, "projection gather image"));
+        CUDA_TRY(cudaMemsetAsync(xg, 0, sizeof(float) * (size_t)c->vm.vint, st));
+        CUDA_TRY(k_x32_from_x64(x64, ImgCopies{xg, nullptr, nullptr, c->vm}, st));
+        xs = xg;
+    }
+    TRY(dev_alloc(&oc, c->csz() * (size_t)std::max<int64_t>(c->M, 1), "projection"));
+    if (c->paths_mode) {
+        CUDA_TRY(k_otf_project(c->otf, (const float*)xs, (float*)oc, st));
+    } else {
+        DropArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.row_ptr = c->row_ptr;
+        a.col = c->col;
+        a.val = c->val;
+        a.vdt = c->vdt;
+        a.cdt = c->cdt;
+        a.grid = c->drop_grid;
+        a.use_d16 = c->storage == NTVS_DELTA16;
+        a.d16 = c->d16();
+        CUDA_TRY(k_project(a, c->M, xs, oc, st));
+    }
+    if (out_mem == NTVS_MEM_DEVICE) {
+        CUDA_TRY(k_convert(oc, c->cdt, out, out_dtype, c->M, st));
+        CUDA_TRY(cudaStreamSynchronize(st));   // the temporaries are released on return
+        return NTVS_OK;
+    }
+    std::vector<unsigned char> h(c->csz() * (size_t)c->M);
+    if (c->M > 0) CUDA_TRY(cudaMemcpyAsync(h.data(), oc, h.size(), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    for (int64_t i = 0; i < c->M; ++i) {
+        const double v = c->cdt == F64 ? ((const double*)h.data())[i] : (double)((const float*)h.data())[i];
+        if (out_dtype == NTVS_F64) ((double*)out)[i] = v;
+        else ((float*)out)[i] = (float)v;
+    }
+    return NTVS_OK;
+}
+
 int ntvs_drop_block_partial(ntvs_ctx* c, int t, int64_t r0, int64_t r1, void* delta_out, int dtype, int mem_kind,
                             double* resid_ss) {
     TRY(use_device(c));

@@ -176,6 +176,9 @@ struct DropArgs {
 };
 cudaError_t k_drop_block(const DropArgs& a, cudaStream_t s);
 cudaError_t k_drop_block_d16(const DropArgs& a, cudaStream_t s);   // the same on DELTA16 storage
+// out[i] = <a_i, x> for the M rows (x: compute type, in the order of the stored columns;
+// out: compute type); a.row_ptr, col / d16, val, vdt, cdt, use_d16 and grid are used
+cudaError_t k_project(const DropArgs& a, int64_t M, const void* x, void* out, cudaStream_t s);
 // *out = max(*out, longest row of rows [r0, r1)); *out zeroed by the caller
 cudaError_t k_row_maxlen(const int64_t* row_ptr, int64_t r0, int64_t r1, unsigned long long* out, int grid,
                          cudaStream_t s);
@@ -252,6 +255,8 @@ cudaError_t k_hist_to_paths(const float* hist, int64_t M, float* rec, int* flags
 cudaError_t k_otf_prep(const OtfArgs& a, int64_t r0, int64_t r1, float* inv_norm2, int32_t* cnt, cudaStream_t s);
 cudaError_t k_otf_drop(const OtfArgs& a, int64_t r0, int64_t r1, const float* inv_norm2, const float* x, float* delta,
                        double lambda, double* resid_ss, cudaStream_t s);
+// out[i] = <a_i, x> of every traced row (x in the internal voxel order)
+cudaError_t k_otf_project(const OtfArgs& a, const float* x, float* out, cudaStream_t s);
 
 // ------------------------------------------------------------------ row-sharded DROP
 // out[j] = delta[internal(j)] in type odt (F32/F64), then delta = 0 (canonical j < V)

@@ -416,3 +416,29 @@ def test_device_pointers_match_host(dtype):
     finally:
         r_host.close()
         r_dev.close()
+
+
+@pytest.mark.parametrize("storage", ["csr32", "delta16"])
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_forward_project_equals_the_stored_rows(storage, dtype):
+    """ntvs_forward_project gives A x of the loaded rows (the dot products of the DROP sweep)."""
+    ntvs = ntvs_module()
+    from paper_1803_01112_gb300._ffi import NTVS_CSR32, NTVS_DELTA16
+    s = synth.generate(synth.spec_scaled_3d(nx=40, ny=40, nz=5, n_hist=20_000, n_angles=36, n_blocks=4, seed=6))
+    val = s.val.astype(dtype)
+    x = s.xstar * 0.8 + 0.1
+    r = ntvs.Reconstructor(0)
+    try:
+        r.load((40, 40, 5), s.row_ptr, s.col, val, s.b.astype(dtype), n_blocks=4,
+               storage={"csr32": NTVS_CSR32, "delta16": NTVS_DELTA16}[storage])
+        r.set_image(s.xbar)
+        got = r.forward_project(x)
+        got32 = r.forward_project(x.astype(np.float32), out=np.empty(s.M, np.float32))
+        assert np.array_equal(r.get_image(), s.xbar)   # the current image is untouched
+    finally:
+        r.close()
+    rows = np.repeat(np.arange(s.M), np.diff(s.row_ptr))
+    want = np.bincount(rows, weights=val.astype(np.float64) * x[s.col], minlength=s.M)
+    tol = 1e-13 if dtype == np.float64 else 2e-6
+    np.testing.assert_allclose(got, want, rtol=tol, atol=tol * np.abs(want).max())
+    np.testing.assert_allclose(got32, want, rtol=2e-6, atol=2e-6 * np.abs(want).max())

@@ -223,3 +223,18 @@ def test_histories_reject_bad_input():
                              pr.b.astype(np.float32), n_seg=65)
     finally:
         r.close()
+
+
+def test_onthefly_forward_project_equals_noise_free_rhs():
+    """Projecting the phantom through the traced paths gives the noise-free WEPL b = A x*
+    that the generator traces in FP64 (within the FP32 geometry's error)."""
+    ntvs = ntvs_module()
+    spec = synth.spec_scaled_3d(nx=40, ny=36, nz=4, n_hist=20_000, n_angles=40, n_blocks=5, seed=41).replace(
+        noise_sigma=0.0)
+    pr = synth.generate_paths(spec)
+    r = _load(ntvs, spec, pr)
+    try:
+        got = r.forward_project(pr.xstar)
+    finally:
+        r.close()
+    assert rel_l2(got, pr.b) <= 2e-5
