@@ -75,6 +75,7 @@ struct ntvs_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaStream_t copy_stream = nullptr;   // load: host-to-device copies overlapped with preparation
+    cudaStream_t copy_stream2 = nullptr;  // (columns on one, values on the other: two copies in flight)
     int sms = 1;
 
     // system
@@ -193,6 +194,7 @@ struct ntvs_ctx {
 
     void free_system() {
         if (copy_stream) cudaStreamSynchronize(copy_stream);   // no copy may still target a buffer
+        if (copy_stream2) cudaStreamSynchronize(copy_stream2);
         if (own_row_ptr) dev_free(row_ptr);
         if (own_col) dev_free(col);
         if (own_val) dev_free(val);
@@ -897,8 +899,10 @@ int ntvs_create(ntvs_ctx** out, int device, void* cuda_stream) {
     }
     {
         cudaError_t e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) c->copy_stream = nullptr;
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->copy_stream2, cudaStreamNonBlocking);
         if (e != cudaSuccess) {
-            c->copy_stream = nullptr;
+            c->copy_stream2 = nullptr;
             ntvs_destroy(c);
             return fail(NTVS_ERR_CUDA, cuda_msg("cudaStreamCreate", e));
         }
@@ -964,6 +968,7 @@ int ntvs_destroy(ntvs_ctx* c) {
     if (c->hscal) cudaFreeHost(c->hscal);
     if (c->hint) cudaFreeHost(c->hint);
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    if (c->copy_stream2) cudaStreamDestroy(c->copy_stream2);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return NTVS_OK;
@@ -1050,7 +1055,7 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
     // so the preparation hides behind the host-to-device copy.  Block t's entry range
     // comes from the host row_ptr, clamped to [0, nnz); a row_ptr that is not
     // non-decreasing is rejected below before any block is prepared.
-    const bool piped = s->mem_kind == NTVS_MEM_HOST && nnz > 0 && c->copy_stream != nullptr;
+    const bool piped = s->mem_kind == NTVS_MEM_HOST && nnz > 0 && c->copy_stream && c->copy_stream2;
     std::vector<cudaEvent_t> arrived;
     std::vector<int64_t> eb;   // [B+1] entry range of each block (piped)
     struct EventGuard {
@@ -1075,12 +1080,14 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
                 CUDA_TRY(cudaMemcpyAsync(c->col + e0, s->col + e0, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice,
                                          c->copy_stream));
                 CUDA_TRY(cudaMemcpyAsync((char*)c->val + vsz * (size_t)e0, (const char*)s->val + vsz * (size_t)e0,
-                                         vsz * (size_t)n, cudaMemcpyHostToDevice, c->copy_stream));
+                                         vsz * (size_t)n, cudaMemcpyHostToDevice, c->copy_stream2));
             }
-            cudaEvent_t ev;
-            CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-            arrived.push_back(ev);
-            CUDA_TRY(cudaEventRecord(ev, c->copy_stream));
+            for (cudaStream_t cs : {c->copy_stream, c->copy_stream2}) {
+                cudaEvent_t ev;
+                CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+                arrived.push_back(ev);
+                CUDA_TRY(cudaEventRecord(ev, cs));
+            }
         }
     } else {
         TRY(copy_in((void**)&c->col, &c->own_col, s->col, sizeof(int32_t) * (size_t)nnz, s->mem_kind, st, "col"));
@@ -1127,7 +1134,8 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
     }
     for (int t = 0; t < c->B; ++t) {
         if (piped) {
-            CUDA_TRY(cudaStreamWaitEvent(st, arrived[t], 0));
+            CUDA_TRY(cudaStreamWaitEvent(st, arrived[2 * t], 0));
+            CUDA_TRY(cudaStreamWaitEvent(st, arrived[2 * t + 1], 0));
             if (tiled) CUDA_TRY(k_remap_cols(c->col + eb[t], c->col + eb[t], eb[t + 1] - eb[t], c->vm, c->dflags, st));
         }
         if (colsum) CUDA_TRY(cudaMemsetAsync(colsum, 0, sizeof(float) * (size_t)VI, st));
