@@ -2,8 +2,8 @@
 
 Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline / reference arm of
 ``bench.py`` may import this package.  The product library never uses it and shares
-no code with it.  The arithmetic is in ``ntvs_oracle.c`` (plain single-threaded C,
-double precision); this module is argument marshalling.
+no code with it.  The arithmetic is in ``ntvs_oracle.c`` and ``fbp_oracle.c`` (plain
+single-threaded C, double precision); this module is argument marshalling.
 
 Pins (what fixes each function independently of itself) live in ``tests/test_oracle_*.py``:
   * orc_splitmix64 / orc_rand_ell : published SplitMix64 outputs, an independent
@@ -15,6 +15,10 @@ Pins (what fixes each function independently of itself) live in ``tests/test_ora
     the one-row closed form, fixed points of consistent systems, convergence to the
     numpy least-squares solution, a hand-computed 3-voxel 4-row block.
   * orc_drop_block_at : equals orc_drop_block on every voxel of small cases.
+  * orc_fbp_* / orc_median / orc_hull / orc_initial_iterate (fbp_oracle.c): analytic
+    disc projections reconstruct to the disc, hand-worked bins and angle folds,
+    hand-made median cases and scipy's median filter on interior voxels, the noise-free
+    phantom reconstructed end to end.
   * orc_ntvs     : N = 0 is plain DROP; the check variant without rejections equals
     the variant without the check; accepted steps never raise phi; ell_k >= k.
     OTVS and decoupled step rules: closed forms of the total shift of a two-voxel image
@@ -34,18 +38,20 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ntvs_oracle.c")
+_SRC_FBP = os.path.join(_HERE, "fbp_oracle.c")   # the initial iterate (FBP, median, hull)
 _SO = os.path.join(_HERE, "libntvs_oracle.so")
 _SO_OMP = os.path.join(_HERE, "libntvs_oracle_omp.so")   # timing build on all host cores
 
 
 def build_command(out: str = _SO, omp: bool = False):
     return ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared"] + (["-fopenmp"] if omp else []) + \
-        ["-o", out, _SRC, "-lm"]
+        ["-o", out, _SRC, _SRC_FBP, "-lm"]
 
 
 def build(force: bool = False, omp: bool = False) -> str:
     so = _SO_OMP if omp else _SO
-    if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_FBP))
+    if force or not os.path.exists(so) or os.path.getmtime(so) < newest:
         subprocess.run(build_command(so, omp), check=True)
     return so
 
@@ -61,6 +67,20 @@ class _Trace(ctypes.Structure):
     _fields_ = [("ell_k", ctypes.c_void_p), ("ell_step", ctypes.c_void_p), ("tries", ctypes.c_void_p),
                 ("accepted", ctypes.c_void_p), ("tv", ctypes.c_void_p), ("resid_ss", ctypes.c_void_p),
                 ("beta_step", ctypes.c_void_p)]
+
+
+class FbpGeom(ctypes.Structure):
+    """Geometry of the initial-iterate pipeline: image grid (in-plane centred on the
+    origin, slice iz over z in [iz dz, (iz+1) dz)), n_theta angle bins of width pi/n_theta
+    from theta0, and n_t lateral bins of width dt centred on t = 0."""
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("n_theta", ctypes.c_int32), ("n_t", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("dt", ctypes.c_double), ("theta0", ctypes.c_double)]
+
+
+def fbp_geom(nx, ny, nz, dx, dy, dz, n_theta, n_t, dt, theta0=0.0) -> FbpGeom:
+    return FbpGeom(nx, ny, nz, n_theta, n_t, 0, dx, dy, dz, dt, theta0)
 
 
 _L = {}
@@ -82,6 +102,18 @@ def _lib(omp: bool = False):
         L.orc_ntvs.argtypes = [vp, vp, vp, vp, vp, i32, i32, i32, i32, ctypes.POINTER(_Params),
                                i32, i32, ctypes.POINTER(i64), vp, vp, ctypes.POINTER(_Trace)]
         L.orc_ntvs.restype = i32
+        G = ctypes.POINTER(FbpGeom)
+        L.orc_fbp_line.argtypes = [vp, vp, vp, vp]; L.orc_fbp_line.restype = i32
+        L.orc_fbp_bin_of.argtypes = [vp, G, vp, vp, vp]; L.orc_fbp_bin_of.restype = i32
+        L.orc_fbp_bin.argtypes = [vp, vp, i64, G, vp, vp]; L.orc_fbp_bin.restype = None
+        L.orc_ramlak.argtypes = [i64, d]; L.orc_ramlak.restype = d
+        L.orc_fbp_filter.argtypes = [vp, G, vp]; L.orc_fbp_filter.restype = None
+        L.orc_fbp_backproject.argtypes = [vp, G, vp]; L.orc_fbp_backproject.restype = None
+        L.orc_median_window.argtypes = [i32, i32, vp]; L.orc_median_window.restype = i32
+        L.orc_median.argtypes = [vp, i32, i32, i32, i32, i32, vp]; L.orc_median.restype = None
+        L.orc_hull.argtypes = [vp, i64, d]; L.orc_hull.restype = None
+        L.orc_initial_iterate.argtypes = [vp, vp, i64, G, i32, i32, i32, d, vp]
+        L.orc_initial_iterate.restype = None
         _L[omp] = L
     return _L[omp]
 
@@ -226,3 +258,88 @@ def ntvs(row_ptr, col, val, b, block_ptr, shape, params: Params, K: int, x0,
     return Result(x, ell_k[:K], ell_step[:K * N].reshape(K, N), tries[:K * N].reshape(K, N),
                   accepted[:K * N].reshape(K, N), tvs[:K], rss[:K * B].reshape(K, B), int(ep.value),
                   bst[:K * N].reshape(K, N))
+
+
+# ------------------------------------------------------------------ initial iterate (FBP, median, hull)
+def _paths32(paths):
+    p = np.ascontiguousarray(paths, np.float32)
+    assert p.ndim == 2 and p.shape[1] == 10
+    return p
+
+
+def fbp_line(rec):
+    """(theta, t, z) of one history's chord line, or None for an empty record."""
+    r = np.ascontiguousarray(rec, np.float32).reshape(10)
+    th, t, z = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    ok = _lib().orc_fbp_line(r.ctypes.data, ctypes.byref(th), ctypes.byref(t), ctypes.byref(z))
+    return (th.value, t.value, z.value) if ok else None
+
+
+def fbp_bin_of(rec, g: FbpGeom):
+    """(slice, angle bin, lateral bin) of one history, or None outside the bins."""
+    r = np.ascontiguousarray(rec, np.float32).reshape(10)
+    iz, ia, it = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    ok = _lib().orc_fbp_bin_of(r.ctypes.data, ctypes.byref(g), ctypes.byref(iz), ctypes.byref(ia),
+                               ctypes.byref(it))
+    return (iz.value, ia.value, it.value) if ok else None
+
+
+def fbp_bin(paths, wepl, g: FbpGeom):
+    """Sinogram [nz, n_theta, n_t] of mean WEPL per bin and the history counts."""
+    p = _paths32(paths)
+    w = _f64(wepl)
+    sino = np.empty((g.nz, g.n_theta, g.n_t), np.float64)
+    cnt = np.empty((g.nz, g.n_theta, g.n_t), np.int64)
+    _lib().orc_fbp_bin(p.ctypes.data, w.ctypes.data, p.shape[0], ctypes.byref(g), sino.ctypes.data,
+                       cnt.ctypes.data)
+    return sino, cnt
+
+
+def ramlak(m: int, dt: float) -> float:
+    return float(_lib().orc_ramlak(m, dt))
+
+
+def fbp_filter(sino, g: FbpGeom) -> np.ndarray:
+    s = _f64(sino).reshape(g.nz, g.n_theta, g.n_t)
+    q = np.empty_like(s)
+    _lib().orc_fbp_filter(s.ctypes.data, ctypes.byref(g), q.ctypes.data)
+    return q
+
+
+def fbp_backproject(q, g: FbpGeom) -> np.ndarray:
+    qq = _f64(q).reshape(g.nz, g.n_theta, g.n_t)
+    img = np.empty(g.nx * g.ny * g.nz, np.float64)
+    _lib().orc_fbp_backproject(qq.ctypes.data, ctypes.byref(g), img.ctypes.data)
+    return img
+
+
+def median_window(r: int, ball: bool) -> np.ndarray:
+    n = _lib().orc_median_window(r, int(ball), None)
+    off = np.empty((n, 3), np.int32)
+    _lib().orc_median_window(r, int(ball), off.ctypes.data)
+    return off
+
+
+def median(img, shape, r: int, ball: bool = False) -> np.ndarray:
+    nx, ny, nz = shape
+    x = _f64(img).reshape(-1)
+    assert x.size == nx * ny * nz
+    out = np.empty_like(x)
+    _lib().orc_median(x.ctypes.data, nx, ny, nz, r, int(ball), out.ctypes.data)
+    return out
+
+
+def hull(img, tau: float) -> np.ndarray:
+    x = _f64(img).reshape(-1).copy()
+    _lib().orc_hull(x.ctypes.data, x.size, tau)
+    return x
+
+
+def initial_iterate(paths, wepl, g: FbpGeom, median_r: int = 2, median_ball: bool = False,
+                    use_hull: bool = False, tau: float = 0.0) -> np.ndarray:
+    p = _paths32(paths)
+    w = _f64(wepl)
+    out = np.empty(g.nx * g.ny * g.nz, np.float64)
+    _lib().orc_initial_iterate(p.ctypes.data, w.ctypes.data, p.shape[0], ctypes.byref(g), median_r,
+                               int(median_ball), int(use_hull), tau, out.ctypes.data)
+    return out
