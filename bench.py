@@ -61,6 +61,8 @@ def parse_args(argv=None):
     ap.add_argument("--batch-scale", type=float, default=1.0)
     ap.add_argument("--onthefly", type=int, default=1, help="also time on-the-fly rows on the 256x256x64 grid")
     ap.add_argument("--otf-histories", type=int, default=60_000_000)
+    ap.add_argument("--fbp", type=int, default=1,
+                    help="also time the initial iterate (FBP + median r=2 + hull) on the workload's histories")
     ap.add_argument("--tile", default="4x4", help="internal voxel tile of the FP32 path (1x1: canonical order)")
     ap.add_argument("--canonical", type=int, default=1,
                     help="also time the canonical voxel order on the same workload (0: skip)")
@@ -435,6 +437,71 @@ def run_onthefly_variant(args, ntvs, local, stream, world, device):
             "note": "b = (A x*)(1 + 0.01 z) formed on the device through the traced paths"}
 
 
+def run_fbp_variant(args, ntvs, stream, world, device, spec, b):
+    """The initial iterate x-bar of the workload's own histories: chord binning into 180
+    angle bins centred on whole degrees x 160 lateral bins of 1 mm x the workload's
+    slices, Ram-Lak filter, back-projection onto its grid, median filter r = 2 per slice,
+    threshold hull at 0.3 (include/ntvs_fbp.h).  Timed with CUDA events on the stream,
+    whole chain and stage by stage."""
+    import math
+
+    import torch
+
+    import synth
+    pr = synth.generate_paths(spec, with_rhs=False)
+    paths = torch.from_numpy(pr.paths).to(device)
+    wepl = torch.from_numpy(np.ascontiguousarray(b, np.float64)).to(device)
+    del pr
+    g = ntvs.fbp_geom(spec.nx, spec.ny, spec.nz, spec.dx, spec.dy, spec.dz, 180, 160, 1.0, theta0=-math.pi / 360)
+    S, V = spec.nz * 180 * 160, spec.V
+    out = torch.empty(V, dtype=torch.float64, device=device)
+    ws = torch.empty(ntvs.ntvs_fbp_workspace_bytes(g), dtype=torch.uint8, device=device)
+    sino = torch.empty(S, dtype=torch.float64, device=device)
+    cnt = torch.empty(S, dtype=torch.int32, device=device)
+    q = torch.empty(S, dtype=torch.float64, device=device)
+    img = torch.empty(V, dtype=torch.float64, device=device)
+    cs = stream.cuda_stream
+
+    def chain():
+        ntvs.ntvs_initial_iterate(g, paths, wepl, out, median_radius=2, use_hull=True, tau=0.3, workspace=ws,
+                                  stream=cs)
+
+    stages = [("bin", lambda: ntvs.ntvs_fbp_bin(g, paths, wepl, sino, cnt, stream=cs)),
+              ("filter", lambda: ntvs.ntvs_fbp_filter(g, sino, q, stream=cs)),
+              ("backproject", lambda: ntvs.ntvs_fbp_backproject(g, q, img, stream=cs)),
+              ("median_hull", lambda: ntvs.ntvs_median_filter(img, out, (spec.nx, spec.ny, spec.nz), 2,
+                                                              use_hull=True, tau=0.3, stream=cs))]
+    for _ in range(3):
+        chain()
+    reps = 10
+    torch.cuda.synchronize(device)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 + 2 * len(stages))]
+    ev[0].record(stream)
+    for _ in range(reps):
+        chain()
+    ev[1].record(stream)
+    stage_ms = {}
+    for i, (name, fn) in enumerate(stages):
+        ev[2 + 2 * i].record(stream)
+        for _ in range(reps):
+            fn()
+        ev[3 + 2 * i].record(stream)
+    torch.cuda.synchronize(device)
+    ms = max_over_ranks(ev[0].elapsed_time(ev[1]) / reps, world, device)
+    for i, (name, _) in enumerate(stages):
+        stage_ms[name] = ev[2 + 2 * i].elapsed_time(ev[3 + 2 * i]) / reps
+    # back-projection: per (voxel, angle) 12 FP64 operations (two products and sums for t,
+    # one FMA for u, floor, three for the weights, two products and two sums)
+    bp_flops = 12.0 * V * 180
+    res = {"name": "initial iterate: FBP + median r=2 + hull, " + spec.name, "value": world * spec.n_hist / (ms / 1e3),
+           "unit": "histories/s", "ms_per_call": ms, "histories": spec.n_hist, "bins": [spec.nz, 180, 160],
+           "stage_ms": stage_ms, "gpu_launches_per_call": 7,
+           "backproject_fp64_gflops": bp_flops / (stage_ms["backproject"] / 1e3) / 1e9,
+           "arithmetic": "f64"}
+    del paths, wepl, out, ws, sino, cnt, q, img
+    return res
+
+
 def shard_system(spec, vdt, rank, world):
     """This rank's rows of the workload: block t's rows cut into `world` contiguous runs,
     run `rank` of each, generated run by run (no rank builds the whole system)."""
@@ -721,6 +788,10 @@ def run_ntvs(args):
     # ---- on-the-fly rows on the large grid
     if args.onthefly:
         variants.append(run_onthefly_variant(args, ntvs, local, stream, world, device))
+
+    # ---- the initial iterate from the same histories
+    if args.fbp:
+        variants.append(run_fbp_variant(args, ntvs, stream, world, device, spec, s.b))
 
     # ---- CPU oracle baseline (rank 0, one GPU only): the OpenMP timing build of the oracle on
     # all host cores over the whole workload, and the single-threaded checker on a sample

@@ -448,6 +448,100 @@ def ntvs_tv_value_static(x, shape, out, stream: Optional[int] = None) -> None:
     check(lib().ntvs_tv_value_static(ptr, _dtype_code(x), nx, ny, nz, optr, stream), "ntvs_tv_value_static")
 
 
+# ----------------------------------------------------------------- initial iterate (include/ntvs_fbp.h)
+def fbp_geom(nx: int, ny: int, nz: int, dx: float, dy: float, dz: float, n_theta: int, n_t: int, dt: float,
+             theta0: float = 0.0) -> "_ffi.ntvs_fbp_geom":
+    """Geometry of the initial-iterate pipeline (ntvs_fbp_geom of include/ntvs_fbp.h)."""
+    return _ffi.ntvs_fbp_geom(nx, ny, nz, n_theta, n_t, 0, dx, dy, dz, dt, theta0)
+
+
+def _cuda(a, dtype, name: str, numel: Optional[int] = None) -> int:
+    """Device pointer of a contiguous CUDA tensor of the given torch dtype (and size)."""
+    if not _is_torch(a) or not a.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not a.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if a.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {a.dtype}")
+    if numel is not None and a.numel() != numel:
+        raise ValueError(f"{name}: expected {numel} elements, got {a.numel()}")
+    return a.data_ptr()
+
+
+def _fbp_sizes(g):
+    return g.nz * g.n_theta * g.n_t, g.nx * g.ny * g.nz
+
+
+def ntvs_fbp_bin(g, paths, wepl, sino, count, stream: Optional[int] = None) -> None:
+    """Step 1: sino (float64) and count (int32), [nz, n_theta, n_t], from paths (float32
+    [M, 10]) and wepl (float64 [M]); CUDA tensors."""
+    import torch
+    S, _ = _fbp_sizes(g)
+    M = int(wepl.numel())
+    pp = _cuda(paths, torch.float32, "paths", 10 * M)
+    wp = _cuda(wepl, torch.float64, "wepl")
+    check(lib().ntvs_fbp_bin(ctypes.byref(g), pp, wp, M, _cuda(sino, torch.float64, "sino", S),
+                             _cuda(count, torch.int32, "count", S), stream), "ntvs_fbp_bin")
+
+
+def ntvs_fbp_filter(g, sino, q, stream: Optional[int] = None) -> None:
+    """Step 2: q = Ram-Lak filter of sino along t (float64 CUDA tensors of nz*n_theta*n_t)."""
+    import torch
+    S, _ = _fbp_sizes(g)
+    check(lib().ntvs_fbp_filter(ctypes.byref(g), _cuda(sino, torch.float64, "sino", S),
+                                _cuda(q, torch.float64, "q", S), stream), "ntvs_fbp_filter")
+
+
+def ntvs_fbp_backproject(g, q, img, stream: Optional[int] = None) -> None:
+    """Step 3: img (float64, nz*ny*nx) = back-projection of the filtered sinogram q."""
+    import torch
+    S, V = _fbp_sizes(g)
+    check(lib().ntvs_fbp_backproject(ctypes.byref(g), _cuda(q, torch.float64, "q", S),
+                                     _cuda(img, torch.float64, "img", V), stream), "ntvs_fbp_backproject")
+
+
+def ntvs_median_filter(inp, out, shape, radius: int = 2, ball: bool = False, use_hull: bool = False,
+                       tau: float = 0.0, stream: Optional[int] = None) -> None:
+    """Step 4 (and the hull when use_hull): out = median filter of inp (float64 CUDA
+    tensors of nx*ny*nz voxels, shape = (nx, ny, nz))."""
+    import torch
+    nx, ny, nz = shape
+    V = nx * ny * nz
+    check(lib().ntvs_median_filter(_cuda(inp, torch.float64, "inp", V), _cuda(out, torch.float64, "out", V),
+                                   nx, ny, nz, radius, int(ball), int(use_hull), tau, stream), "ntvs_median_filter")
+
+
+def ntvs_hull(img, tau: float, stream: Optional[int] = None) -> None:
+    """Step 5 in place: voxels <= tau become 0 (float64 CUDA tensor)."""
+    import torch
+    check(lib().ntvs_hull(_cuda(img, torch.float64, "img"), int(img.numel()), tau, stream), "ntvs_hull")
+
+
+def ntvs_fbp_workspace_bytes(g) -> int:
+    n = int(lib().ntvs_fbp_workspace_bytes(ctypes.byref(g)))
+    if n < 0:
+        check(n, "ntvs_fbp_workspace_bytes")
+    return n
+
+
+def ntvs_initial_iterate(g, paths, wepl, out, median_radius: int = 2, median_ball: bool = False,
+                         use_hull: bool = False, tau: float = 0.0, workspace=None,
+                         stream: Optional[int] = None) -> None:
+    """Steps 1-5 into out (float64 CUDA tensor of nz*ny*nx voxels).  workspace: a uint8
+    CUDA tensor of at least ntvs_fbp_workspace_bytes(g) bytes, allocated here when None."""
+    import torch
+    _, V = _fbp_sizes(g)
+    M = int(wepl.numel())
+    need = ntvs_fbp_workspace_bytes(g)
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=out.device)
+    wsp = _cuda(workspace, torch.uint8, "workspace")
+    check(lib().ntvs_initial_iterate(ctypes.byref(g), _cuda(paths, torch.float32, "paths", 10 * M),
+                                     _cuda(wepl, torch.float64, "wepl"), M, median_radius, int(median_ball),
+                                     int(use_hull), tau, wsp, int(workspace.numel()),
+                                     _cuda(out, torch.float64, "out", V), stream), "ntvs_initial_iterate")
+
+
 # ----------------------------------------------------------------- object wrapper
 @dataclass
 class Params:

@@ -19,7 +19,7 @@ SO = os.path.join(PKG, "libntvs.so")
 SOURCES = ["ntvs_api.cu", "kernels_tv.cu", "kernels_prep.cu", "kernels_drop.cu", "kernels_drop_d16.cu",
            "kernels_drop_tma.cu",
            "kernels_onthefly.cu", "batch.cu", "tv_static.cu",
-           "kernels_check.cu"]
+           "kernels_check.cu", "kernels_fbp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -35,7 +35,7 @@ def compile_flags():
 
 def _deps():
     hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
-    return hdrs + [os.path.join(INCLUDE, "ntvs.h")]
+    return hdrs + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
 
 
 def _stale(obj: str, src: str) -> bool:

@@ -1,4 +1,5 @@
-"""ctypes declarations of the C ABI in include/ntvs.h (argument marshalling only).
+"""ctypes declarations of the C ABI in include/ntvs.h and include/ntvs_fbp.h (argument
+marshalling only).
 
 Every function of the header is bound here under its C name.  The library is the
 in-tree ``libntvs.so`` built by ``paper_1803_01112_gb300._build``; importing this module
@@ -93,7 +94,14 @@ P = ctypes.POINTER
 # int (*ntvs_allreduce_fn)(void* buf, int64_t n, int dtype, void* cuda_stream, void* user)
 ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, vp, i64, ctypes.c_int, vp, vp)
 
-# name -> (restype, argtypes); the list is the whole header
+class ntvs_fbp_geom(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("n_theta", ctypes.c_int32), ("n_t", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("dt", ctypes.c_double), ("theta0", ctypes.c_double)]
+
+
+# name -> (restype, argtypes); the list is the whole of both headers
 SIGNATURES = {
     "ntvs_version": (ctypes.c_char_p, []),
     "ntvs_last_error": (ctypes.c_char_p, []),
@@ -140,6 +148,16 @@ SIGNATURES = {
     "ntvs_batch_get_tv": (ctypes.c_int, [vp, ctypes.c_int, P(d)]),
     "ntvs_batch_get_stats": (ctypes.c_int, [vp, P(ntvs_batch_stats)]),
     "ntvs_tv_value_static": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]),
+    # include/ntvs_fbp.h: the initial iterate
+    "ntvs_fbp_bin": (ctypes.c_int, [P(ntvs_fbp_geom), vp, vp, i64, vp, vp, vp]),
+    "ntvs_fbp_filter": (ctypes.c_int, [P(ntvs_fbp_geom), vp, vp, vp]),
+    "ntvs_fbp_backproject": (ctypes.c_int, [P(ntvs_fbp_geom), vp, vp, vp]),
+    "ntvs_median_filter": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_int, d, vp]),
+    "ntvs_hull": (ctypes.c_int, [vp, i64, d, vp]),
+    "ntvs_fbp_workspace_bytes": (i64, [P(ntvs_fbp_geom)]),
+    "ntvs_initial_iterate": (ctypes.c_int, [P(ntvs_fbp_geom), vp, vp, i64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            d, vp, i64, vp, vp]),
 }
 
 _lib = None
