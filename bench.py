@@ -300,8 +300,9 @@ def run_reference(args):
 
 def batch_members(n_members, seed=4, scale=1.0):
     """Members of the batched sweep: grids nx = ny in {64..128} (step 8), nz in {8..16},
-    histories U(0.05, 0.4) * 1e6 * scale, and (N, alpha, lambda) drawn from
-    {1..6} x {0.5, 0.6, 0.75, 0.9} x {1e-4, 2e-4, 5e-4} without repetition."""
+    histories U(0.5, 4) * 1e6 * scale (bent paths over 90 angles, 4-8 random inserts,
+    20 blocks), and (N, alpha, lambda) drawn from {1..6} x {0.5, 0.6, 0.75, 0.9} x
+    {1e-4, 2e-4, 5e-4} without repetition."""
     import synth
     rng = np.random.default_rng(seed)
     combos = [(N, a, l) for N in range(1, 7) for a in (0.5, 0.6, 0.75, 0.9) for l in (1e-4, 2e-4, 5e-4)]
@@ -310,44 +311,120 @@ def batch_members(n_members, seed=4, scale=1.0):
     for k in range(n_members):
         n = int(rng.integers(8, 17)) * 8
         nz = int(rng.integers(8, 17))
-        m = int(rng.uniform(0.05, 0.4) * 1e6 * scale)
+        m = max(1000, int(rng.uniform(0.5, 4.0) * 1e6 * scale))
         N, a, l = combos[pick[k]]
         out.append((synth.spec_batch_member(1000 + k, n, n, nz, m), dict(lam=l, N=N, alpha=a, seed=2000 + k)))
     return out
 
 
+def batch_cycle_bytes(members):
+    """Algorithmic HBM bytes of one batched cycle: per member each stored entry's value
+    and column once, 16 B per row (row_ptr, b, 1/||a||^2), and per voxel 44 B per TV step
+    (gradient: x split read, g written; step: x, g read, x and its three FP32 copies
+    written), 32 B per DROP block (x, delta, 1/s read; x, its copy, delta written) and 8 B
+    for phi."""
+    return sum(8.0 * nnz + 16.0 * M + V * (44.0 * N + 32.0 * B + 8.0) for (nnz, M, V, N, B) in members)
+
+
 def run_batched_variant(args, ntvs, local, stream, world, device):
+    """The batched parameter sweep at its stated size.  Members are generated as path
+    records on the host; on the device b = (A x*)(1 + 0.01 z) is formed by projecting the
+    phantom through the traced paths, and ntvs_batch_add_paths traces and stores the rows.
+    The same members run once without and once with the TV check."""
+    import time
+
     import torch
 
     import synth
     members = batch_members(args.batch_members, scale=args.batch_scale)
-    systems = [(synth.generate(sp, np.float32), prm) for sp, prm in members]
-    total_rows = sum(s.M for s, _ in systems)
-    bt = ntvs.Batch(local, stream.cuda_stream)
-    for s, prm in systems:
-        sp = s.spec
-        bt.add((sp.nx, sp.ny, sp.nz), s.row_ptr, s.col, s.val, s.b.astype(np.float32), sp.n_blocks,
-               ntvs.Params(**prm), s.xbar)
-    bt.finalize(max_cycles=args.warmup + args.steps + 1)
-    bt.run(args.warmup)
-    torch.cuda.synchronize(device)
-    barrier(world, device)
-    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    g0.record(stream)
-    bt.run(args.steps)
-    g1.record(stream)
-    torch.cuda.synchronize(device)
-    ms_b = max_over_ranks(g0.elapsed_time(g1), world, device)
-    bst = bt.stats()
-    bt.close()
-    # the same members one after another through single contexts (FP32, default schedule)
-    seq_ms = 0.0
-    for s, prm in systems:
-        sp = s.spec
+    t_gen = t_load = 0.0
+    dev = []   # (spec, params, paths on the device, b on the device, xbar)
+    for sp, prm in members:
+        t0 = time.perf_counter()
+        P = synth.generate_paths(sp, with_rhs=False)
+        t1 = time.perf_counter()
+        pd = torch.from_numpy(P.paths).to(device)
+        shape, voxel = (sp.nx, sp.ny, sp.nz), (sp.dx, sp.dy, sp.dz)
         r = ntvs.Reconstructor(local, stream.cuda_stream)
-        r.load((sp.nx, sp.ny, sp.nz), s.row_ptr, s.col, s.val, s.b.astype(np.float32), n_blocks=sp.n_blocks)
+        r.load_paths(shape, voxel, pd, torch.zeros(sp.n_hist, dtype=torch.float32, device=device),
+                     n_blocks=sp.n_blocks, n_seg=sp.n_seg, min_len=sp.min_len)
+        bclean = torch.empty(sp.n_hist, dtype=torch.float32, device=device)
+        r.forward_project(P.xstar, out=bclean)
+        r.close()
+        gen = torch.Generator(device=device).manual_seed(sp.seed)
+        b = bclean * (1.0 + sp.noise_sigma * torch.randn(sp.n_hist, generator=gen, device=device))
+        del bclean
+        torch.cuda.synchronize(device)
+        t_gen += t1 - t0
+        t_load += time.perf_counter() - t1
+        dev.append((sp, prm, pd, b, P.xbar))
+    lines = []
+    for check in (False, True):
+        bt = ntvs.Batch(local, stream.cuda_stream)
+        t0 = time.perf_counter()
+        for sp, prm, pd, b, xbar in dev:
+            bt.add_paths((sp.nx, sp.ny, sp.nz), (sp.dx, sp.dy, sp.dz), pd, b, sp.n_blocks,
+                         ntvs.Params(tv_check=check, **prm), xbar, n_seg=sp.n_seg, min_len=sp.min_len)
+        t_add = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        bt.finalize(max_cycles=args.warmup + args.steps + 1)
+        t_fin = time.perf_counter() - t0
+        bt.run(args.warmup)
+        bt.sync()
+        barrier(world, device)
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        bt.run(args.steps)
+        g1.record(stream)
+        bt.sync()
+        ms_b = max_over_ranks(g0.elapsed_time(g1), world, device)
+        bst = bt.stats()
+        mems = [bt.member(i) for i in range(len(dev))]
+        sizes = [(bt.sizes(i)[1], sp.n_hist, sp.V, prm["N"], sp.n_blocks)
+                 for i, (sp, prm, _, _, _) in enumerate(dev)]
+        total_rows = sum(sp.n_hist for sp, *_ in dev)
+        cyc_bytes = batch_cycle_bytes(sizes)
+        ms_cycle = ms_b / args.steps
+        peak, peak_src = measured_peaks()
+        ach = cyc_bytes / (ms_cycle / 1e3) / 1e9
+        seq = None
+        if not check:
+            seq = sequential_sample(args, ntvs, local, stream, world, device, bt, dev, min(4, len(dev)))
+        bt.close()
+        line = {"name": f"batched sweep of {len(dev)} members" + (", TV-reduction check on" if check else ""),
+                "value": world * total_rows * args.steps / (ms_b / 1e3), "unit": UNIT, "ms_per_step": ms_cycle,
+                "members": len(dev), "total_histories": int(total_rows), "total_nnz": int(bst["total_nnz"]),
+                "kernels_per_cycle": int(bst["kernels_per_cycle"]),
+                "gpu_launches_per_step": bst["n_launches"] / max(bst["cycles"], 1),
+                "schedule": {"rows_per_item": bst["rows_per_item"], "window_floats": bst["window_floats"],
+                             "ctas": bst["ctas"], "lanes_per_row": [bst["lanes_per_row_min"], bst["lanes_per_row"]]},
+                "tries_per_step": sum(m["n_tries"] for m in mems) / max(sum(m["n_steps"] for m in mems), 1),
+                "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                             "algorithmic_bytes_per_cycle": cyc_bytes, "peak_source": peak_src,
+                             "kernel": "batch_cycle_kernel (the whole cycle is one launch)"},
+                "load_seconds": {"host_path_generation": t_gen, "device_b_projection": t_load,
+                                 "add_paths_tracing_and_prep": t_add, "finalize_and_tuning": t_fin},
+                "recipe": "nx=ny in {64..128}, nz in {8..16}, 0.5-4M bent histories each (x batch_scale), 4-8 "
+                          "random inserts, 20 blocks, (N, alpha, lambda) from the 72-combination sweep; rows traced "
+                          "on the device from path records"}
+        if seq is not None:
+            line.update(seq)
+        lines.append(line)
+    return lines
+
+
+def sequential_sample(args, ntvs, local, stream, world, device, bt, dev, n):
+    """The first n members one after another through single FP32 contexts loaded with the
+    batch's stored rows: time per cycle, scaled to all members by their histories."""
+    import torch
+    seq_ms, rows_n = 0.0, 0
+    for i in range(n):
+        sp, prm, pd, b, xbar = dev[i]
+        rp, col, val = bt.rows(i)
+        r = ntvs.Reconstructor(local, stream.cuda_stream)
+        r.load((sp.nx, sp.ny, sp.nz), rp, col, val, b.cpu().numpy(), n_blocks=sp.n_blocks)
         r.set_params(**prm)
-        r.set_image(s.xbar)
+        r.set_image(xbar)
         r.run(1)
         r.sync()
         h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -356,16 +433,12 @@ def run_batched_variant(args, ntvs, local, stream, world, device):
         h1.record(stream)
         torch.cuda.synchronize(device)
         seq_ms += h0.elapsed_time(h1)
+        rows_n += sp.n_hist
         r.close()
-    seq_ms = max_over_ranks(seq_ms, world, device)
-    return {"name": f"batched sweep of {len(systems)} members", "value": world * total_rows * args.steps / (ms_b / 1e3),
-            "unit": UNIT, "ms_per_step": ms_b / args.steps,
-            "sequential_value": world * total_rows * args.steps / (seq_ms / 1e3),
-            "vs_sequential": seq_ms / ms_b, "members": len(systems), "total_histories": int(total_rows),
-            "total_nnz": int(bst["total_nnz"]), "kernels_per_cycle": int(bst["kernels_per_cycle"]),
-            "lanes_per_row": int(bst["lanes_per_row"]),
-            "recipe": "nx=ny in {64..128}, nz in {8..16}, 0.05-0.4M bent histories each (scaled by batch_scale), "
-                      "4-8 random inserts, 20 blocks, (N, alpha, lambda) from the 72-combination sweep, no TV check"}
+    total = sum(d[0].n_hist for d in dev)
+    seq_all = max_over_ranks(seq_ms * total / rows_n, world, device)
+    return {"sequential_value": world * total * args.steps / (seq_all / 1e3),
+            "sequential_sample": f"first {n} members through single contexts, scaled by histories"}
 
 
 def otf_kernel_hash():
@@ -783,7 +856,7 @@ def run_ntvs(args):
 
     # ---- batched reconstructions: a parameter sweep over members of uneven size
     if args.batched:
-        variants.append(run_batched_variant(args, ntvs, local, stream, world, device))
+        variants.extend(run_batched_variant(args, ntvs, local, stream, world, device))
 
     # ---- on-the-fly rows on the large grid
     if args.onthefly:

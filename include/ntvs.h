@@ -417,39 +417,81 @@ typedef int (*ntvs_allreduce_fn)(void* buf, int64_t n, int dtype, void* cuda_str
 int ntvs_set_allreduce(ntvs_ctx* ctx, ntvs_allreduce_fn fn, void* user);
 
 /* ---- batched reconstructions ----------------------------------------------------------
- * Many independent NTVS reconstructions (Appendix C, without the TV check) advanced
- * together on one GPU: every member has its own grid, system, blocks and parameters, and
- * one cycle of all members costs one kernel launch per step type (2*N_max TV launches,
- * 3 per DROP block step, 2 more), replayed from a CUDA graph; only the members' step sizes
- * beta_{k,n} (host-drawn ell schedules, as in ntvs_run) are copied in per cycle.  Members
- * take FP32 values in CSR32 storage (host or device arrays, copied at ntvs_batch_add).
- * The DROP kernel's lanes per row are chosen at finalize by timing block step 0. */
+ * Many independent NTVS reconstructions (Appendix C) advanced together on one GPU: every
+ * member has its own grid, system, blocks and parameters, with or without the TV check
+ * (Sec. III-E).  A cycle of all members is two kernel launches replayed from a CUDA graph:
+ * a setup kernel, and one persistent kernel whose CTAs take work items (runs of voxels or
+ * of DROP rows of one member's current phase) from per-member counters; the last item of
+ * a phase publishes the member's next phase, so members overlap and none waits for the
+ * others.  A CTA that finds no item polls for at most the hook's wait (2 s by default);
+ * when that runs out the cycle stops and the next synchronizing call returns
+ * NTVS_ERR_TIMEOUT (the images are then undefined: destroy the batch).  Members without
+ * the check take their step sizes beta_{k,n} from the host (the ell schedule of
+ * ntvs_run, copied in per cycle); checked members draw ell_k on the device and try up
+ * to max_retries step sizes, four per pass.  Members take FP32 values in CSR32 storage,
+ * given as a matrix (ntvs_batch_add) or traced on the device from path records
+ * (ntvs_batch_add_paths); all preparation (validation, norms, hit counts) runs on the
+ * device.  Arithmetic as the single-context FP32 path: FP32 rows and gathers, FP64 image,
+ * reductions in a fixed order. */
 typedef struct ntvs_batch ntvs_batch;
 
 typedef struct {
     int32_t members;            /* reconstructions in the batch                          */
-    int32_t lanes_per_row;      /* DROP lanes per row picked by the finalize-time tuning  */
+    int32_t lanes_per_row;      /* largest DROP lanes per row of any member (8, 16, 32)   */
     int64_t cycles;             /* cycles run                                             */
     int64_t n_launches;         /* kernels launched by ntvs_batch_run                     */
-    int64_t kernels_per_cycle;  /* kernels in one cycle's graph                           */
+    int64_t kernels_per_cycle;  /* kernels in one cycle's graph (2)                       */
     int64_t total_rows, total_nnz, total_voxels;
+    int32_t rows_per_item;      /* DROP rows per work item (tuned at finalize)           */
+    int32_t window_floats;      /* shared scatter window per CTA, 0: global scatter      */
+    int32_t ctas;               /* CTAs of the persistent kernel                          */
+    int32_t lanes_per_row_min;  /* smallest DROP lanes per row of any member              */
 } ntvs_batch_stats;
+
+/* Test hook of the batch (ntvs_batch_set_fault_hook): member 0 never leaves its first
+ * phase, so every other CTA runs out of work and the bounded wait ends the cycle. */
+#define NTVS_HOOK_STARVE_BATCH 4
 
 int ntvs_batch_create(ntvs_batch** out, int device, void* cuda_stream);
 int ntvs_batch_destroy(ntvs_batch* bt);
-/* Add a member: system (val_dtype NTVS_F32, storage NTVS_CSR32, validated on the host),
- * parameters (tv_check must be 0) and initial image x0 (V values, F64 or F32, host or
- * device).  *index (may be NULL) receives the member's index.  Before finalize only. */
+/* Add a member: system (val_dtype NTVS_F32, storage NTVS_CSR32, host or device arrays,
+ * copied and validated on the device), parameters and initial image x0 (V values, F64 or
+ * F32, host or device).  *index (may be NULL) receives the member's index.  Before
+ * finalize only.  Errors: NTVS_ERR_ARG, NTVS_ERR_CSR (row_ptr, columns, non-finite
+ * values), NTVS_ERR_STATE, NTVS_ERR_OOM, NTVS_ERR_CUDA. */
 int ntvs_batch_add(ntvs_batch* bt, const ntvs_system* sys, const ntvs_params* p, const void* x0, int x0_dtype,
                    int x0_mem, int* index);
-/* Build the work lists, tune the DROP kernel and capture the cycle graph; max_cycles
- * bounds the cycles that may be run (per-member phi history). */
+/* Add a member given as path records (the format of ntvs_load_paths): its rows are traced
+ * once on the device (one thread per history, the path's pieces in order, consecutive
+ * pieces of one voxel merged, merged pieces shorter than min_len dropped) and stored as
+ * FP32 CSR32.  Errors as ntvs_batch_add (NTVS_ERR_CSR for a non-finite path value or b). */
+int ntvs_batch_add_paths(ntvs_batch* bt, const ntvs_paths* paths, const ntvs_params* p, const void* x0,
+                         int x0_dtype, int x0_mem, int* index);
+/* Fix the persistent kernel's schedule instead of timing candidates at finalize:
+ * rows_per_item > 0 DROP rows per work item (0: tuned), window_floats >= 0 floats of the
+ * shared scatter window (0: global scatter only; -1: tuned).  Before finalize only. */
+int ntvs_batch_set_schedule(ntvs_batch* bt, int rows_per_item, int window_floats);
+/* Bounded-wait limit (wait_ns > 0; 0 restores 2 s) and test hooks (NTVS_HOOK_STARVE_BATCH)
+ * of the cycles run after finalize.  Before finalize only.  The paper has no counterpart. */
+int ntvs_batch_set_fault_hook(ntvs_batch* bt, int64_t wait_ns, int flags);
+/* Lay out the work tables, pick the schedule (ntvs_batch_set_schedule, or by timing a few
+ * cycles of each candidate with the images restored afterwards) and capture the cycle
+ * graph; max_cycles bounds the cycles that may be run (per-member phi history). */
 int ntvs_batch_finalize(ntvs_batch* bt, int max_cycles);
-/* Run k_iters cycles of every member (queued on the batch's stream). */
+/* Queue k_iters cycles of every member on the batch's stream. */
 int ntvs_batch_run(ntvs_batch* bt, int k_iters);
+/* Wait for the queued cycles; NTVS_ERR_TIMEOUT when a bounded wait ran out. */
+int ntvs_batch_sync(ntvs_batch* bt);
 /* Member `index`'s image (synchronous); phi after its last cycle (FP64). */
 int ntvs_batch_get_image(ntvs_batch* bt, int index, void* out, int dtype, int mem_kind);
 int ntvs_batch_get_tv(ntvs_batch* bt, int index, double* tv);
+/* Member `index`'s counters (synchronous): out5 = {cycles, ell (ell_{k-1} of the next
+ * cycle), TV steps, accepted steps, tries}. */
+int ntvs_batch_get_member(ntvs_batch* bt, int index, int64_t* out5);
+/* Member `index`'s stored rows (synchronous; host arrays, each may be NULL): n_rows, nnz,
+ * row_ptr [M+1], col [nnz] (canonical voxel index), val [nnz]. */
+int ntvs_batch_get_rows(ntvs_batch* bt, int index, int64_t* n_rows, int64_t* nnz, int64_t* row_ptr, int32_t* col,
+                        float* val);
 int ntvs_batch_get_stats(ntvs_batch* bt, ntvs_batch_stats* st);
 
 /* ---- allocation-free entry point --------------------------------------------------- */

@@ -403,13 +403,80 @@ def ntvs_batch_destroy(bt: int) -> None:
 def ntvs_batch_add(bt: int, shape, row_ptr, col, val, b, n_blocks: int, params: "Params", x0, block_ptr=None) -> int:
     nx, ny, nz = shape
     st, _keep = _system_struct(nx, ny, nz, row_ptr, col, val, b, n_blocks, block_ptr)
-    p = _ffi.ntvs_params(params.lam, params.alpha, params.beta0, params.eps_tv, params.N, int(bool(params.tv_check)),
-                         params.max_retries, int(params.step_rule), params.seed, params.gamma)
+    p = _params_struct(params)
     xp, xk = _ptr_kind(x0)
     idx = ctypes.c_int()
     check(lib().ntvs_batch_add(bt, ctypes.byref(st), ctypes.byref(p), xp, _dtype_code(x0), xk, ctypes.byref(idx)),
           "ntvs_batch_add")
     return idx.value
+
+
+def _params_struct(params: "Params"):
+    return _ffi.ntvs_params(params.lam, params.alpha, params.beta0, params.eps_tv, params.N,
+                            int(bool(params.tv_check)), params.max_retries, int(params.step_rule), params.seed,
+                            params.gamma)
+
+
+def ntvs_batch_add_paths(bt: int, shape, voxel, paths, b, n_blocks: int, params: "Params", x0, block_ptr=None,
+                         n_seg: int = 16, min_len: float = 1e-4) -> int:
+    """A member from path records (float32 [M, 10]) and b (float32 [M]); numpy or CUDA tensors."""
+    nx, ny, nz = shape
+    pp, kind = _ptr_kind(paths)
+    bp_, kb = _ptr_kind(b)
+    if kind != kb:
+        raise ValueError("paths and b must both be host arrays or both device tensors")
+    bp = None
+    if block_ptr is not None:
+        bp = np.ascontiguousarray(block_ptr, dtype=np.int64)
+        n_blocks = bp.size - 1
+    dx, dy, dz = voxel
+    st = _ffi.ntvs_paths(nx, ny, nz, n_blocks, dx, dy, dz, paths.shape[0], pp, bp_,
+                         None if bp is None else bp.ctypes.data, n_seg, kind, min_len)
+    p = _params_struct(params)
+    xp, xk = _ptr_kind(x0)
+    idx = ctypes.c_int()
+    check(lib().ntvs_batch_add_paths(bt, ctypes.byref(st), ctypes.byref(p), xp, _dtype_code(x0), xk,
+                                     ctypes.byref(idx)), "ntvs_batch_add_paths")
+    return idx.value
+
+
+def ntvs_batch_set_schedule(bt: int, rows_per_item: int = 0, window_floats: int = -1) -> None:
+    check(lib().ntvs_batch_set_schedule(bt, rows_per_item, window_floats), "ntvs_batch_set_schedule")
+
+
+def ntvs_batch_set_fault_hook(bt: int, wait_ns: int = 0, flags: int = 0) -> None:
+    check(lib().ntvs_batch_set_fault_hook(bt, int(wait_ns), flags), "ntvs_batch_set_fault_hook")
+
+
+def ntvs_batch_sync(bt: int) -> None:
+    check(lib().ntvs_batch_sync(bt), "ntvs_batch_sync")
+
+
+def ntvs_batch_get_member(bt: int, index: int) -> dict:
+    out = np.zeros(5, np.int64)
+    check(lib().ntvs_batch_get_member(bt, index, out.ctypes.data), "ntvs_batch_get_member")
+    return dict(zip(("k", "ell_prev", "n_steps", "n_accepted", "n_tries"), (int(v) for v in out)))
+
+
+def ntvs_batch_get_sizes(bt: int, index: int):
+    """(rows, stored entries) of a member."""
+    M, nnz = ctypes.c_int64(), ctypes.c_int64()
+    check(lib().ntvs_batch_get_rows(bt, index, ctypes.byref(M), ctypes.byref(nnz), None, None, None),
+          "ntvs_batch_get_rows")
+    return M.value, nnz.value
+
+
+def ntvs_batch_get_rows(bt: int, index: int):
+    """(row_ptr, col, val) of a member's stored rows (canonical voxel indices)."""
+    M, nnz = ctypes.c_int64(), ctypes.c_int64()
+    check(lib().ntvs_batch_get_rows(bt, index, ctypes.byref(M), ctypes.byref(nnz), None, None, None),
+          "ntvs_batch_get_rows")
+    rp = np.empty(M.value + 1, np.int64)
+    col = np.empty(nnz.value, np.int32)
+    val = np.empty(nnz.value, np.float32)
+    check(lib().ntvs_batch_get_rows(bt, index, None, None, rp.ctypes.data, col.ctypes.data, val.ctypes.data),
+          "ntvs_batch_get_rows")
+    return rp, col, val
 
 
 def ntvs_batch_finalize(bt: int, max_cycles: int) -> None:
@@ -575,9 +642,36 @@ class Batch:
         self.shapes.append(tuple(shape))
         return i
 
+    def add_paths(self, shape, voxel, paths, b, n_blocks: int, params: "Params", x0, block_ptr=None,
+                  n_seg: int = 16, min_len: float = 1e-4) -> int:
+        i = ntvs_batch_add_paths(self._bt, shape, voxel, paths, b, n_blocks, params, x0, block_ptr, n_seg, min_len)
+        self.shapes.append(tuple(shape))
+        return i
+
+    def set_schedule(self, rows_per_item: int = 0, window_floats: int = -1):
+        ntvs_batch_set_schedule(self._bt, rows_per_item, window_floats)
+        return self
+
+    def set_fault_hook(self, wait_ns: int = 0, flags: int = 0):
+        ntvs_batch_set_fault_hook(self._bt, wait_ns, flags)
+        return self
+
     def finalize(self, max_cycles: int = 1024):
         ntvs_batch_finalize(self._bt, max_cycles)
         return self
+
+    def sync(self):
+        ntvs_batch_sync(self._bt)
+        return self
+
+    def member(self, index: int) -> dict:
+        return ntvs_batch_get_member(self._bt, index)
+
+    def rows(self, index: int):
+        return ntvs_batch_get_rows(self._bt, index)
+
+    def sizes(self, index: int):
+        return ntvs_batch_get_sizes(self._bt, index)
 
     def run(self, k: int):
         ntvs_batch_run(self._bt, k)

@@ -27,7 +27,7 @@ NTVS_MEM_HOST, NTVS_MEM_DEVICE = 0, 1
 NTVS_CSR32, NTVS_DELTA16 = 0, 1
 NTVS_SCHED_AUTO, NTVS_SCHED_PLAIN, NTVS_SCHED_WINDOW, NTVS_SCHED_PIPELINE, NTVS_SCHED_ONTHEFLY = 0, 1, 2, 3, 4
 NTVS_STEP_NTVS, NTVS_STEP_OTVS, NTVS_STEP_DECOUPLED = 0, 1, 2
-NTVS_HOOK_STARVE_PIPE, NTVS_HOOK_STARVE_CHECK = 1, 2
+NTVS_HOOK_STARVE_PIPE, NTVS_HOOK_STARVE_CHECK, NTVS_HOOK_STARVE_BATCH = 1, 2, 4
 
 ERROR_NAMES = {NTVS_ERR_ARG: "NTVS_ERR_ARG", NTVS_ERR_CSR: "NTVS_ERR_CSR", NTVS_ERR_OOM: "NTVS_ERR_OOM",
                NTVS_ERR_CUDA: "NTVS_ERR_CUDA", NTVS_ERR_TIMEOUT: "NTVS_ERR_TIMEOUT",
@@ -85,7 +85,8 @@ class ntvs_profile(ctypes.Structure):
 class ntvs_batch_stats(ctypes.Structure):
     _fields_ = [("members", ctypes.c_int32), ("lanes_per_row", ctypes.c_int32), ("cycles", ctypes.c_int64),
                 ("n_launches", ctypes.c_int64), ("kernels_per_cycle", ctypes.c_int64), ("total_rows", ctypes.c_int64),
-                ("total_nnz", ctypes.c_int64), ("total_voxels", ctypes.c_int64)]
+                ("total_nnz", ctypes.c_int64), ("total_voxels", ctypes.c_int64), ("rows_per_item", ctypes.c_int32),
+                ("window_floats", ctypes.c_int32), ("ctas", ctypes.c_int32), ("lanes_per_row_min", ctypes.c_int32)]
 
 
 vp, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
@@ -142,6 +143,13 @@ SIGNATURES = {
     "ntvs_batch_destroy": (ctypes.c_int, [vp]),
     "ntvs_batch_add": (ctypes.c_int, [vp, P(ntvs_system), P(ntvs_params), vp, ctypes.c_int, ctypes.c_int,
                                       P(ctypes.c_int)]),
+    "ntvs_batch_add_paths": (ctypes.c_int, [vp, P(ntvs_paths), P(ntvs_params), vp, ctypes.c_int, ctypes.c_int,
+                                            P(ctypes.c_int)]),
+    "ntvs_batch_set_schedule": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
+    "ntvs_batch_set_fault_hook": (ctypes.c_int, [vp, i64, ctypes.c_int]),
+    "ntvs_batch_sync": (ctypes.c_int, [vp]),
+    "ntvs_batch_get_member": (ctypes.c_int, [vp, ctypes.c_int, vp]),
+    "ntvs_batch_get_rows": (ctypes.c_int, [vp, ctypes.c_int, P(i64), P(i64), vp, vp, vp]),
     "ntvs_batch_finalize": (ctypes.c_int, [vp, ctypes.c_int]),
     "ntvs_batch_run": (ctypes.c_int, [vp, ctypes.c_int]),
     "ntvs_batch_get_image": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int]),

@@ -1,18 +1,32 @@
 // Batched NTVS: many independent reconstructions (each with its own grid, system, block
-// partition and (lambda, N, alpha, beta0, eps, seed)) advanced together, one kernel
-// launch per step type per cycle instead of one per reconstruction (arXiv 1803.01112,
-// Appendix C, applied to every reconstruction of the batch; the variant without the TV
-// check, whose control flow is the same for every member).
+// partition and (lambda, N, alpha, beta0, eps, seed, TV check)) advanced together by one
+// persistent kernel per cycle (arXiv 1803.01112, Appendix C, for every member; the TV
+// check of Sec. III-E as a per-member option).
 //
-// Work lists pack the members: a TV item is a run of <= kTvItem voxels of one member, a
-// DROP item a run of <= kDropItem rows of one member's block b.  One cycle is
-//     for n < N_max:  grad (items of members with n < N_r) ; apply
-//     for b < B_max:  drop block b (items of members with b < B_r) ; apply block b
-//     phi of every member
-// Per-member reductions (||g||^2, phi) are FP64 partials per item, summed in a fixed order
-// by the last item of the member to finish (per-member ticket): deterministic.
-// The cycle's launches are captured once in a CUDA graph; what changes from cycle to cycle
-// (the step sizes beta_{k,n} of every member) is a device table refreshed by one copy.
+// Work model.  A member's cycle is a sequence of phases,
+//     [GRAD(n), (TRY(n) ...), APPLY(n)] for n < N,  [DROP(b), DAPPLY(b)] for b < B,  PHI,
+// each cut into items: runs of kTvItem voxels (GRAD, TRY, APPLY, DAPPLY, PHI) or of a
+// member-specific number of rows of block b (DROP).  Phases of one member run in order;
+// phases of different members overlap.  Every member has a 64-bit word (phase epoch |
+// items in the phase | cursor); a CTA takes an item with one atomic add on the cursor,
+// processes it without waiting on anything, and counts it done.  The CTA that finishes a
+// phase's last item does the phase's reductions (in a fixed order: deterministic), decides
+// the next phase and publishes it with one atomic exchange of the word.  A CTA that finds
+// no item waits (polling, bounded by %globaltimer); since no item ever waits, every taken
+// item completes and the cycle ends without co-residency or grid barriers.  When the wait
+// runs out the CTA records an error and every CTA leaves (NTVS_ERR_TIMEOUT on the host).
+//
+// TV check (TRY): each pass evaluates phi(z_t), z_t = x - beta_{ell+t} g / ||g||, for
+// kSpec consecutive tries t at once (x and g read once for all of them); the first t with
+// phi(z_t) <= phi(x) is the accepted try, as if the tries had run one by one; a pass with
+// no acceptance is followed by another until max_retries tries were made.
+//
+// DROP items process rows with LPR lanes per row (8, 16 or 32, per member from its row
+// length) holding the row's first CH*LPR entries in registers between the dot product
+// and the scatter.  The scatter either goes to global memory (FP32 reductions) or is staged
+// in a shared window of the CTA (the item's whole column range when it fits, else the
+// range centred on its mean column, whose outside entries still go to global memory),
+// flushed once per item: only the window's nonzero entries become global reductions.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -27,80 +41,106 @@
 namespace ntvs {
 namespace {
 
-constexpr int kTvItem = 2048;     // voxels per TV item (256 threads x 8)
-constexpr int kDropItem = 256;    // rows per DROP item (enough CTAs to fill every SM)
+constexpr int kThreads = 256;     // threads per CTA of the persistent kernel
+constexpr int kTvItem = 2048;     // voxels per voxel item (256 threads x 8)
+constexpr int kSpec = 4;          // TV-check tries evaluated per pass
+constexpr int kBetaTab = 4096;    // beta0 alpha^ell from the host for ell < kBetaTab
+constexpr unsigned long long kM24 = 0xffffffull;
+constexpr int kErrBatchStall = 16;   // error word: an idle CTA's bounded wait ran out
 
+enum : int { PH_GRAD = 0, PH_TRY = 1, PH_APPLY = 2, PH_DROP = 3, PH_DAPPLY = 4, PH_PHI = 5, PH_DONE = 6 };
+
+// Read-only description of one member (pointers owned by the batch).
 struct MemberDev {
     const int64_t* row_ptr;
-    const int32_t* col;
+    const int32_t* col;        // internal voxel order
     const float* val;
     const float* b;
     const float* inv_norm2;
-    const float* inv_s;   // [B][vint], internal voxel order
-    double* x;
-    float* x32;           // fl32(x), internal voxel order (the DROP gathers)
-    float* xh;            // fl32(x) and fl32(x - xh), canonical order: the TV stencil
-    float* xl;            //   differences are formed from both
-    float* delta;
-    float* g;
-    double* resid;        // [B]
-    double* tv_hist;      // [cap]
+    const float* inv_s;        // [B][vint], internal voxel order
+    const int64_t* block_ptr;  // [B+1]
+    const int32_t* win_lo;     // [n_drop_items] first column of each DROP item's window, -1: none
+    const int32_t* item0;      // [B] index of block b's first DROP item in win_lo
+    const double* beta_tab;    // [kBetaTab] beta0 alpha^ell (TV check)
+    double* x;                 // master image, canonical order
+    float* x32;                // fl32(x), internal order (the DROP gathers)
+    float* xh;                 // fl32(x) and fl32(x - xh), canonical order (gradient stencil)
+    float* xl;
+    float* delta;              // internal order
+    float* g;                  // canonical order
+    double* resid;             // [B]
+    double* tv_hist;           // [cap]
     int nx, ny, nz, B, N;
     int64_t V;
-    VoxMap vm;            // internal order of x32, delta, inv_s and the stored columns
+    VoxMap vm;
     float lambda, eps;
-    int item0, nitems;    // this member's TV items
+    double beta0, alpha;
+    int check, max_retries, rule;
+    uint64_t seed;
+    int lpr, rows_per_item, n_vox_items, part_off;
 };
 
-struct Item {
-    int member;
-    int pad;
-    int64_t i0, i1;   // voxel or row range
+// Mutable per-member state of the schedule.
+struct MemberState {
+    unsigned long long word;   // [63:48] epoch, [47:24] items of the phase, [23:0] cursor
+    unsigned done;             // items of the phase finished
+    int phase, n, b, tries;    // tries: of the current TV step (TV check)
+    int64_t ell, k;            // ell (TV check, carried across cycles); cycles completed
+    double gnorm2, phi_x, sc;
+    int64_t n_tries, n_accepted, n_steps;
 };
 
-__device__ __forceinline__ double block_sum_d(double v, double* sh) { return block_sum(v, sh); }
+struct RunState {
+    unsigned members_done;
+    int err, err_member, err_phase;
+};
 
-// per-member deterministic reduction of one value: partials[item], ticket per member
-__device__ __forceinline__ void member_reduce(double v, int item, const MemberDev& m, int r, double* partials,
-                                              unsigned* tickets, double* out) {
-    __shared__ double sh[32];
-    __shared__ bool last;
-    const double tot = block_sum_d(v, sh);
-    if (threadIdx.x == 0) {
-        partials[item] = tot;
-        __threadfence();
-        const unsigned t = atomicAdd(tickets + r, 1u);
-        last = (t == (unsigned)m.nitems - 1);
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    double a = 0.0;
-    for (int q = threadIdx.x; q < m.nitems; q += blockDim.x) a += __ldcg(partials + m.item0 + q);
-    a = block_sum_d(a, sh);
-    if (threadIdx.x == 0) {
-        *out = a;
-        tickets[r] = 0u;
-    }
+struct CycleArgs {
+    const MemberDev* mem;
+    MemberState* st;
+    RunState* run;
+    int R;
+    double* part;      // [total voxel items] ||g||^2 or phi partials
+    double* part2;     // [total voxel items] phi(x) partials (TV check)
+    double* part_try;  // [total voxel items][kSpec] phi(z_t) partials
+    const double* beta;   // [N_max][R] beta_{k,n} of the cycle (no TV check)
+    uint64_t wait_ns;
+    int starve;        // test hook: member 0's first phase never ends
+    int win_cap;       // floats of the shared scatter window (0: global scatter only)
+};
+
+__device__ __forceinline__ unsigned long long pack_word(unsigned epoch, unsigned items) {
+    return ((unsigned long long)(epoch & 0xffffu) << 48) | ((unsigned long long)(items & kM24) << 24);
 }
 
-// grad phi_eps of member r over the item's voxels; ||g||^2 into gnorm2[r]
-__global__ void __launch_bounds__(256) tvb_grad_kernel(const MemberDev* __restrict__ mem, const Item* __restrict__ items,
-                                                       int n_step, double* partials, unsigned* tickets,
-                                                       double* gnorm2) {
-    const Item it = items[blockIdx.x];
-    const MemberDev m = mem[it.member];
-    if (n_step >= m.N) return;   // uniform over the CTA: no reduction for this member
+__device__ __forceinline__ unsigned long long ld_word(const unsigned long long* p) {
+    return *(volatile const unsigned long long*)p;
+}
+
+// sum over i < n of a[i * stride] in a fixed order (every thread a strided subset, then the
+// block tree): the same order whichever CTA does it
+__device__ __forceinline__ double ordered_sum(const double* a, int n, int stride, double* sh) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += __ldcg(a + (size_t)i * stride);
+    return block_sum(s, sh);   // valid in thread 0
+}
+
+// ---------------------------------------------------------------- voxel items
+
+// gradient of phi_eps (FP32 stencil on x = xh + xl) on the item's voxels; partials of
+// ||g||^2 and (TV check) of phi(x) from the FP64 image
+__device__ void grad_item(const MemberDev& m, int idx, double* part, double* part2, double* sh) {
     const int nx = m.nx, ny = m.ny, nz = m.nz;
     const int64_t sxy = (int64_t)nx * ny;
+    const int64_t i0 = (int64_t)idx * kTvItem, i1 = min(m.V, i0 + kTvItem);
     const float* xh = m.xh;
     const float* xl = m.xl;
     const float eps = m.eps;
     auto dif = [&](int64_t a, int64_t b) -> float {
-        return (__ldg(xh + a) - __ldg(xh + b)) + (__ldg(xl + a) - __ldg(xl + b));
+        return (__ldcg(xh + a) - __ldcg(xh + b)) + (__ldcg(xl + a) - __ldcg(xl + b));
     };
-    double acc = 0.0;
-    for (int64_t p = it.i0 + threadIdx.x; p < it.i1; p += blockDim.x) {
+    double acc = 0.0, phi = 0.0;
+    for (int64_t p = i0 + threadIdx.x; p < i1; p += blockDim.x) {
         int ix, iy, iz;
         voxel_coords(p, nx, ny, ix, iy, iz);
         const bool hx = ix + 1 < nx, hy = iy + 1 < ny, hz = iz + 1 < nz;
@@ -127,21 +167,69 @@ __global__ void __launch_bounds__(256) tvb_grad_kernel(const MemberDev* __restri
         }
         m.g[p] = gq;
         acc += (double)gq * (double)gq;
+        if (m.check) {
+            const double xc = __ldcg(m.x + p);
+            const double ex = hx ? __ldcg(m.x + p + 1) - xc : 0.0, ey = hy ? __ldcg(m.x + p + nx) - xc : 0.0,
+                         ez = hz ? __ldcg(m.x + p + sxy) - xc : 0.0;
+            phi += sqrt(ex * ex + ey * ey + ez * ez);
+        }
     }
-    member_reduce(acc, blockIdx.x, m, it.member, partials, tickets, gnorm2 + it.member);
+    const double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[m.part_off + idx] = t;
+    if (m.check) {
+        const double tp = block_sum(phi, sh);
+        if (threadIdx.x == 0) part2[m.part_off + idx] = tp;
+    }
 }
 
-// x <- x - beta_r / ||g_r|| * g on the items' voxels (members with n_step < N_r)
-__global__ void __launch_bounds__(256) tvb_apply_kernel(const MemberDev* __restrict__ mem,
-                                                        const Item* __restrict__ items, int n_step,
-                                                        const double* __restrict__ beta, int R,
-                                                        const double* __restrict__ gnorm2) {
-    const Item it = items[blockIdx.x];
-    const MemberDev m = mem[it.member];
-    if (n_step >= m.N) return;
-    const double sc = step_scale(beta[(int64_t)n_step * R + it.member], gnorm2 + it.member);
-    for (int64_t p = it.i0 + threadIdx.x; p < it.i1; p += blockDim.x) {
-        const double z = perturbed(m.x[p], sc, (double)m.g[p]);
+__device__ __forceinline__ double beta_of(const MemberDev& m, int64_t ell) {
+    return (ell >= 0 && ell < kBetaTab) ? __ldg(m.beta_tab + ell) : m.beta0 * pow(m.alpha, (double)ell);
+}
+
+// phi(z_t) partials of the item's voxels for the pass's tries t < T (z_t = x - sc_t g)
+__device__ void try_item(const MemberDev& m, int idx, int64_t ell, int T, double gnorm2, double* part_try, double* sh) {
+    const int nx = m.nx, ny = m.ny, nz = m.nz;
+    const int64_t sxy = (int64_t)nx * ny;
+    const int64_t i0 = (int64_t)idx * kTvItem, i1 = min(m.V, i0 + kTvItem);
+    double sc[kSpec], acc[kSpec];
+#pragma unroll
+    for (int t = 0; t < kSpec; ++t) {
+        sc[t] = (t < T && gnorm2 > 0.0) ? beta_of(m, ell + t) / sqrt(gnorm2) : 0.0;
+        acc[t] = 0.0;
+    }
+    for (int64_t p = i0 + threadIdx.x; p < i1; p += blockDim.x) {
+        int ix, iy, iz;
+        voxel_coords(p, nx, ny, ix, iy, iz);
+        const double xc = __ldcg(m.x + p), gc = (double)__ldcg(m.g + p);
+        const bool hx = ix + 1 < nx, hy = iy + 1 < ny, hz = iz + 1 < nz;
+        const double xx = hx ? __ldcg(m.x + p + 1) : 0.0, gx = hx ? (double)__ldcg(m.g + p + 1) : 0.0;
+        const double xy = hy ? __ldcg(m.x + p + nx) : 0.0, gy = hy ? (double)__ldcg(m.g + p + nx) : 0.0;
+        const double xz = hz ? __ldcg(m.x + p + sxy) : 0.0, gz = hz ? (double)__ldcg(m.g + p + sxy) : 0.0;
+#pragma unroll
+        for (int t = 0; t < kSpec; ++t) {
+            if (t < T) {
+                const double zc = perturbed(xc, sc[t], gc);
+                const double ex = hx ? perturbed(xx, sc[t], gx) - zc : 0.0;
+                const double ey = hy ? perturbed(xy, sc[t], gy) - zc : 0.0;
+                const double ez = hz ? perturbed(xz, sc[t], gz) - zc : 0.0;
+                acc[t] += sqrt(ex * ex + ey * ey + ez * ez);
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < kSpec; ++t) {
+        if (t < T) {
+            const double s = block_sum(acc[t], sh);
+            if (threadIdx.x == 0) part_try[(size_t)(m.part_off + idx) * kSpec + t] = s;
+        }
+    }
+}
+
+// x <- x - sc g on the item's voxels, and the FP32 copies
+__device__ void apply_item(const MemberDev& m, int idx, double sc) {
+    const int64_t i0 = (int64_t)idx * kTvItem, i1 = min(m.V, i0 + kTvItem);
+    for (int64_t p = i0 + threadIdx.x; p < i1; p += blockDim.x) {
+        const double z = perturbed(__ldcg(m.x + p), sc, (double)__ldcg(m.g + p));
         m.x[p] = z;
         const float h = (float)z;
         m.x32[vox_internal(m.vm, p)] = h;
@@ -150,21 +238,63 @@ __global__ void __launch_bounds__(256) tvb_apply_kernel(const MemberDev* __restr
     }
 }
 
-// DROP block b of every member with b < B_r: a group of LPR lanes per row; the first
-// CH * LPR entries of a row stay in registers between the dot product and the scatter
-// (the matrix is read once), longer rows re-read their tail; global reductions.
+// x += delta / s for block b on the item's voxels; delta cleared; after the last block
+// also xh, xl (read by the next cycle's gradient only)
+__device__ void dapply_item(const MemberDev& m, int idx, int b) {
+    const int64_t i0 = (int64_t)idx * kTvItem, i1 = min(m.V, i0 + kTvItem);
+    const float* inv_s = m.inv_s + (int64_t)b * m.vm.vint;
+    const bool last = b == m.B - 1;
+    for (int64_t j = i0 + threadIdx.x; j < i1; j += blockDim.x) {
+        const int64_t p = vox_internal(m.vm, j);
+        const double v = __ldcg(m.x + j) + (double)__ldcg(m.delta + p) * (double)__ldg(inv_s + p);
+        m.x[j] = v;
+        const float h = (float)v;
+        m.x32[p] = h;
+        if (last) {
+            m.xh[j] = h;
+            m.xl[j] = (float)(v - (double)h);
+        }
+        m.delta[p] = 0.f;
+    }
+}
+
+// phi(x) partial of the item's voxels (FP64)
+__device__ void phi_item(const MemberDev& m, int idx, double* part, double* sh) {
+    const int nx = m.nx, ny = m.ny, nz = m.nz;
+    const int64_t sxy = (int64_t)nx * ny;
+    const int64_t i0 = (int64_t)idx * kTvItem, i1 = min(m.V, i0 + kTvItem);
+    double acc = 0.0;
+    for (int64_t p = i0 + threadIdx.x; p < i1; p += blockDim.x) {
+        int ix, iy, iz;
+        voxel_coords(p, nx, ny, ix, iy, iz);
+        const double xc = __ldcg(m.x + p);
+        const double ex = (ix + 1 < nx) ? __ldcg(m.x + p + 1) - xc : 0.0,
+                     ey = (iy + 1 < ny) ? __ldcg(m.x + p + nx) - xc : 0.0,
+                     ez = (iz + 1 < nz) ? __ldcg(m.x + p + sxy) - xc : 0.0;
+        acc += sqrt(ex * ex + ey * ey + ez * ez);
+    }
+    const double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[m.part_off + idx] = t;
+}
+
+// ---------------------------------------------------------------- DROP items
+
+extern __shared__ float batch_win[];   // the shared scatter window (win_cap floats)
+
+// rows [i0, i1) of member m: LPR lanes per row, CH register steps; when w0 >= 0 the
+// entries with columns in [w0, w0 + win_cap) are scattered into the shared window and the
+// others into global delta, else every entry into global delta
 template <int LPR, int CH>
-__global__ void __launch_bounds__(256) dropb_block_kernel(const MemberDev* __restrict__ mem,
-                                                          const Item* __restrict__ items) {
-    const Item it = items[blockIdx.x];
-    const MemberDev m = mem[it.member];
+__device__ void drop_rows(const MemberDev& m, int64_t i0, int64_t i1, int w0, int win_cap, double* resid_b,
+                          double* sh) {
     constexpr int G = 32 / LPR;
     const int lane = threadIdx.x & 31, sub = lane % LPR;
     const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const bool win = w0 >= 0;
     double ss = 0.0;
-    for (int64_t base = it.i0 + (int64_t)warp * G; base < it.i1; base += (int64_t)nw * G) {
+    for (int64_t base = i0 + (int64_t)warp * G; base < i1; base += (int64_t)nw * G) {
         const int64_t i = base + lane / LPR;
-        const bool valid = i < it.i1;
+        const bool valid = i < i1;
         int64_t p0 = 0, p1 = 0;
         if (valid) { p0 = __ldg(m.row_ptr + i); p1 = __ldg(m.row_ptr + i + 1); }
         int32_t c[CH];
@@ -178,9 +308,9 @@ __global__ void __launch_bounds__(256) dropb_block_kernel(const MemberDev* __res
         float acc = 0.f;
 #pragma unroll
         for (int u = 0; u < CH; ++u)
-            if (c[u] >= 0) acc += a[u] * __ldg(m.x32 + c[u]);
+            if (c[u] >= 0) acc += a[u] * __ldcg(m.x32 + c[u]);
         const int64_t tail0 = p0 + (int64_t)CH * LPR;
-        for (int64_t p = tail0 + sub; p < p1; p += LPR) acc += m.val[p] * __ldg(m.x32 + m.col[p]);
+        for (int64_t q = tail0 + sub; q < p1; q += LPR) acc += __ldg(m.val + q) * __ldcg(m.x32 + __ldg(m.col + q));
 #pragma unroll
         for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         float r = 0.f;
@@ -189,69 +319,456 @@ __global__ void __launch_bounds__(256) dropb_block_kernel(const MemberDev* __res
             r = m.lambda * res * __ldg(m.inv_norm2 + i);
             if (sub == 0) ss += (double)res * (double)res;
         }
+        if (win) {   // entries inside the window to shared memory, the others to global memory
 #pragma unroll
-        for (int u = 0; u < CH; ++u)
-            if (c[u] >= 0) atomicAdd(m.delta + c[u], r * a[u]);
-        for (int64_t p = tail0 + sub; p < p1; p += LPR) atomicAdd(m.delta + m.col[p], r * m.val[p]);
-    }
-    __shared__ double sh[32];
-    const double tot = block_sum(ss, sh);
-    if (threadIdx.x == 0 && tot != 0.0) atomicAdd(m.resid + it.pad, tot);   // pad carries the block index
-}
-
-// x += delta / s for block b of members with b < B_r (TV items cover every voxel)
-__global__ void __launch_bounds__(256) dropb_apply_kernel(const MemberDev* __restrict__ mem,
-                                                          const Item* __restrict__ items, int b) {
-    const Item it = items[blockIdx.x];
-    const MemberDev m = mem[it.member];
-    if (b >= m.B) return;
-    const float* inv_s = m.inv_s + (int64_t)b * m.vm.vint;
-    const bool last = b == m.B - 1;   // xh, xl are read by the next gradient only: written after the last block
-    for (int64_t j = it.i0 + threadIdx.x; j < it.i1; j += blockDim.x) {
-        const int64_t p = vox_internal(m.vm, j);
-        const double v = m.x[j] + (double)m.delta[p] * (double)inv_s[p];
-        m.x[j] = v;
-        const float h = (float)v;
-        m.x32[p] = h;
-        if (last) {
-            m.xh[j] = h;
-            m.xl[j] = (float)(v - (double)h);
+            for (int u = 0; u < CH; ++u) {
+                if (c[u] >= 0) {
+                    const unsigned o = (unsigned)(c[u] - w0);
+                    if (o < (unsigned)win_cap) atomicAdd(batch_win + o, r * a[u]);
+                    else atomicAdd(m.delta + c[u], r * a[u]);
+                }
+            }
+            for (int64_t q = tail0 + sub; q < p1; q += LPR) {
+                const int cq = __ldg(m.col + q);
+                const unsigned o = (unsigned)(cq - w0);
+                if (o < (unsigned)win_cap) atomicAdd(batch_win + o, r * __ldg(m.val + q));
+                else atomicAdd(m.delta + cq, r * __ldg(m.val + q));
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < CH; ++u)
+                if (c[u] >= 0) atomicAdd(m.delta + c[u], r * a[u]);
+            for (int64_t q = tail0 + sub; q < p1; q += LPR) atomicAdd(m.delta + __ldg(m.col + q), r * __ldg(m.val + q));
         }
-        m.delta[p] = 0.f;
+    }
+    const double tot = block_sum(ss, sh);
+    if (threadIdx.x == 0 && tot != 0.0) atomicAdd(resid_b, tot);
+}
+
+__device__ void drop_item(const MemberDev& m, int b, int idx, int win_cap, double* sh) {
+    const int64_t r0 = __ldg(m.block_ptr + b) + (int64_t)idx * m.rows_per_item;
+    const int64_t r1 = min(__ldg(m.block_ptr + b + 1), r0 + m.rows_per_item);
+    const int w0 = win_cap > 0 ? __ldg(m.win_lo + __ldg(m.item0 + b) + idx) : -1;
+    if (w0 >= 0) {
+        for (int j = threadIdx.x; j < win_cap; j += blockDim.x) batch_win[j] = 0.f;
+        __syncthreads();
+    }
+    switch (m.lpr) {
+        case 8: drop_rows<8, 16>(m, r0, r1, w0, win_cap, m.resid + b, sh); break;
+        case 16: drop_rows<16, 10>(m, r0, r1, w0, win_cap, m.resid + b, sh); break;
+        default: drop_rows<32, 6>(m, r0, r1, w0, win_cap, m.resid + b, sh); break;
+    }
+    if (w0 >= 0) {
+        __syncthreads();
+        const int64_t n = min((int64_t)win_cap, m.vm.vint - (int64_t)w0);
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            const float v = batch_win[j];
+            if (v != 0.f) atomicAdd(m.delta + w0 + j, v);
+        }
     }
 }
 
-// phi of every member into tv_hist[k]
-__global__ void __launch_bounds__(256) tvb_value_kernel(const MemberDev* __restrict__ mem,
-                                                        const Item* __restrict__ items, const int64_t* __restrict__ kk,
-                                                        double* partials, unsigned* tickets) {
-    const Item it = items[blockIdx.x];
-    const MemberDev m = mem[it.member];
-    const int nx = m.nx, ny = m.ny, nz = m.nz;
-    const int64_t sxy = (int64_t)nx * ny;
-    double acc = 0.0;
-    for (int64_t p = it.i0 + threadIdx.x; p < it.i1; p += blockDim.x) {
-        int ix, iy, iz;
-        voxel_coords(p, nx, ny, ix, iy, iz);
-        const double xc = m.x[p];
-        const double ex = (ix + 1 < nx) ? m.x[p + 1] - xc : 0.0, ey = (iy + 1 < ny) ? m.x[p + nx] - xc : 0.0,
-                     ez = (iz + 1 < nz) ? m.x[p + sxy] - xc : 0.0;
-        acc += sqrt(ex * ex + ey * ey + ez * ez);
+// ---------------------------------------------------------------- the phase machine
+
+__device__ __forceinline__ int drop_items_of(const MemberDev& m, int b) {
+    const int64_t rows = __ldg(m.block_ptr + b + 1) - __ldg(m.block_ptr + b);
+    return (int)((rows + m.rows_per_item - 1) / m.rows_per_item);
+}
+
+// The first phase at or after (phase, n, b) that has items (DROP of an empty block is
+// skipped; its DAPPLY still runs); returns its item count, 0 for DONE.
+__device__ int settle(const MemberDev& m, int& phase, int& n, int& b) {
+    for (int guard = 0; guard < 4; ++guard) {
+        if (phase == PH_GRAD && n >= m.N) {
+            phase = PH_DROP;
+            b = 0;
+        }
+        if (phase == PH_DROP && b >= m.B) phase = PH_PHI;
+        if (phase == PH_DROP) {
+            const int k = drop_items_of(m, b);
+            if (k > 0) return k;
+            phase = PH_DAPPLY;
+        }
+        if (phase == PH_DONE) return 0;
+        return m.n_vox_items;
     }
-    member_reduce(acc, blockIdx.x, m, it.member, partials, tickets, m.tv_hist + kk[it.member]);
+    return 0;
 }
 
-__global__ void zero_resid_kernel(const MemberDev* __restrict__ mem, int R, int b) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < R && b < mem[r].B) mem[r].resid[b] = 0.0;
+// Reductions of the phase just finished (all threads), then thread 0 sets the next phase
+// and publishes it.  items: the finished phase's item count; word: its schedule word.
+__device__ void finish_phase(const CycleArgs& a, int r, int phase, int items, unsigned long long word, int tries_done,
+                             double* sh) {
+    const MemberDev& m = a.mem[r];
+    double t0 = 0.0, t1 = 0.0;
+    double tt[kSpec];
+    int T = 0;
+    if (phase == PH_GRAD || phase == PH_PHI) t0 = ordered_sum(a.part + m.part_off, items, 1, sh);
+    if (phase == PH_GRAD && m.check) t1 = ordered_sum(a.part2 + m.part_off, items, 1, sh);
+    if (phase == PH_TRY) {
+        T = min(kSpec, m.max_retries - tries_done);
+#pragma unroll
+        for (int t = 0; t < kSpec; ++t)
+            tt[t] = (t < T) ? ordered_sum(a.part_try + (size_t)m.part_off * kSpec + t, items, kSpec, sh) : 0.0;
+    }
+    if (threadIdx.x != 0) return;
+    if (a.starve && r == 0) return;   // test hook: member 0 never leaves its first phase
+    MemberState* st = a.st + r;
+    volatile MemberState* vs = st;
+    int ph = phase, n = vs->n, b = vs->b;
+    switch (phase) {
+        case PH_GRAD:
+            st->gnorm2 = t0;
+            if (m.check) {
+                st->phi_x = t1;
+                st->tries = 0;
+                ph = PH_TRY;
+            } else {
+                st->sc = step_scale(__ldg(a.beta + (size_t)n * a.R + r), &st->gnorm2);
+                st->n_steps += 1;
+                st->n_tries += 1;
+                if (st->sc != 0.0) st->n_accepted += 1;
+                ph = PH_APPLY;
+            }
+            break;
+        case PH_TRY: {
+            const double gn2 = vs->gnorm2, px = vs->phi_x;
+            int acc = -1;
+            for (int t = 0; t < T; ++t)
+                if (tt[t] <= px) { acc = t; break; }   // ties accept
+            const int64_t ell = vs->ell;
+            if (acc >= 0) {
+                st->sc = gn2 > 0.0 ? beta_of(m, ell + acc) / sqrt(gn2) : 0.0;
+                st->ell = ell + acc + 1;
+                st->tries = tries_done + acc + 1;
+                st->n_tries += acc + 1;
+                st->n_accepted += 1;
+                st->n_steps += 1;
+                ph = PH_APPLY;
+            } else {
+                st->ell = ell + T;
+                st->tries = tries_done + T;
+                st->n_tries += T;
+                if (tries_done + T >= m.max_retries) {   // the step is skipped
+                    st->n_steps += 1;
+                    ph = PH_GRAD;
+                    n += 1;
+                }
+            }
+            break;
+        }
+        case PH_APPLY:
+            ph = PH_GRAD;
+            n += 1;
+            break;
+        case PH_DROP:
+            ph = PH_DAPPLY;
+            break;
+        case PH_DAPPLY:
+            ph = PH_DROP;
+            b += 1;
+            break;
+        case PH_PHI: {
+            const int64_t k = vs->k;
+            m.tv_hist[k] = t0;
+            st->k = k + 1;
+            ph = PH_DONE;
+            break;
+        }
+        default:
+            break;
+    }
+    const int nitems = settle(m, ph, n, b);
+    st->phase = ph;
+    st->n = n;
+    st->b = b;
+    st->done = 0u;
+    __threadfence();
+    atomicExch(&st->word, pack_word((unsigned)(word >> 48) + 1u, (unsigned)nitems));
+    if (ph == PH_DONE) atomicAdd(&a.run->members_done, 1u);
 }
 
-__global__ void advance_k_kernel(int64_t* kk, int R) {
+// Start of a cycle (one thread per member): ell_k of checked members, residual sums
+// cleared, the first phase published.
+__global__ void cycle_setup_kernel(const MemberDev* __restrict__ mem, MemberState* st, RunState* run, int R) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < R) kk[r] += 1;
+    if (r == 0) run->members_done = 0u;
+    if (r >= R) return;
+    const MemberDev& m = mem[r];
+    MemberState& s = st[r];
+    if (m.check && m.rule == NTVS_STEP_NTVS) s.ell = draw_ell(m.seed, s.k, s.ell);
+    for (int b = 0; b < m.B; ++b) m.resid[b] = 0.0;
+    int ph = PH_GRAD, n = 0, b = 0;
+    const int items = settle(m, ph, n, b);
+    s.phase = ph;
+    s.n = n;
+    s.b = b;
+    s.tries = 0;
+    s.done = 0u;
+    s.word = pack_word((unsigned)(s.word >> 48) + 1u, (unsigned)items);
 }
+
+// One cycle of every member (see the file comment).
+__global__ void __launch_bounds__(kThreads) batch_cycle_kernel(CycleArgs a) {
+    __shared__ double sh[32];
+    __shared__ int s_r, s_idx, s_items, s_last, s_exit, s_phase, s_b, s_tries;
+    __shared__ unsigned long long s_word;
+    __shared__ int64_t s_ell;
+    __shared__ double s_gnorm2, s_sc;
+    const int lane = threadIdx.x & 31;
+    int start = blockIdx.x % a.R;
+    uint64_t idle0 = 0;
+    for (;;) {
+        if (threadIdx.x < 32) {   // warp 0 looks for an item, 32 members per probe
+            int got = -1, gidx = 0, gitems = 0;
+            unsigned long long gword = 0ull;
+            for (int base = 0; base < a.R && got < 0; base += 32) {
+                int r = start + base + lane;
+                if (r >= a.R) r -= a.R;
+                bool avail = false;
+                if (base + lane < a.R) {
+                    const unsigned long long w = ld_word(&a.st[r].word);
+                    avail = (w & kM24) < ((w >> 24) & kM24);
+                }
+                unsigned bal = __ballot_sync(0xffffffffu, avail);
+                while (bal != 0u) {
+                    const int L = __ffs(bal) - 1;
+                    bal &= bal - 1u;
+                    const int rr = __shfl_sync(0xffffffffu, r, L);
+                    unsigned long long old = 0ull;
+                    if (lane == 0) old = atomicAdd(&a.st[rr].word, 1ull);
+                    old = __shfl_sync(0xffffffffu, old, 0);
+                    const unsigned cur = (unsigned)(old & kM24), n = (unsigned)((old >> 24) & kM24);
+                    if (cur < n) {
+                        got = rr;
+                        gidx = (int)cur;
+                        gitems = (int)n;
+                        gword = old;
+                        break;
+                    }
+                }
+            }
+            if (lane == 0) {
+                s_r = got;
+                s_idx = gidx;
+                s_items = gitems;
+                s_word = gword;
+            }
+        }
+        __syncthreads();
+        const int r = s_r;
+        if (r < 0) {   // nothing to take: done, failed, or wait (bounded) for a phase to end
+            if (threadIdx.x == 0) {
+                int ex = 0;
+                if (*(volatile int*)&a.run->err != 0 || *(volatile unsigned*)&a.run->members_done >= (unsigned)a.R) {
+                    ex = 1;
+                } else {
+                    const uint64_t now = globaltimer_ns();
+                    if (idle0 == 0) {
+                        idle0 = now;
+                    } else if (now - idle0 > a.wait_ns) {
+                        if (atomicCAS(&a.run->err, 0, kErrBatchStall) == 0) {
+                            // the first member that has not finished its cycle, for the report
+                            for (int q = 0; q < a.R; ++q)
+                                if (((volatile MemberState*)(a.st + q))->phase != PH_DONE) {
+                                    a.run->err_member = q;
+                                    a.run->err_phase = ((volatile MemberState*)(a.st + q))->phase;
+                                    break;
+                                }
+                        }
+                        ex = 1;
+                    }
+                    if (!ex) __nanosleep(256);
+                }
+                s_exit = ex;
+            }
+            __syncthreads();
+            if (s_exit) break;
+            continue;
+        }
+        idle0 = 0;
+        start = r;
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const volatile MemberState* vs = a.st + r;
+            s_phase = vs->phase;
+            s_b = vs->b;
+            s_tries = vs->tries;
+            s_ell = vs->ell;
+            s_gnorm2 = vs->gnorm2;
+            s_sc = vs->sc;
+        }
+        __syncthreads();
+        const MemberDev& m = a.mem[r];
+        const int idx = s_idx, phase = s_phase;
+        switch (phase) {
+            case PH_GRAD: grad_item(m, idx, a.part, a.part2, sh); break;
+            case PH_TRY: try_item(m, idx, s_ell, min(kSpec, m.max_retries - s_tries), s_gnorm2, a.part_try, sh); break;
+            case PH_APPLY: apply_item(m, idx, s_sc); break;
+            case PH_DROP: drop_item(m, s_b, idx, a.win_cap, sh); break;
+            case PH_DAPPLY: dapply_item(m, idx, s_b); break;
+            case PH_PHI: phi_item(m, idx, a.part, sh); break;
+            default: break;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const unsigned d = atomicAdd(&a.st[r].done, 1u);
+            s_last = (d + 1u == (unsigned)s_items) ? 1 : 0;
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            finish_phase(a, r, phase, s_items, s_word, s_tries, sh);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- member preparation
+
+// flags |= 1 row_ptr not non-decreasing from 0 to nnz, 2 column outside [0, V),
+// 4 non-finite value, 8 non-finite right-hand side
+__global__ void validate_kernel(const int64_t* __restrict__ rp, int64_t M, const int32_t* __restrict__ col,
+                                const float* __restrict__ val, int64_t nnz, const float* __restrict__ b, int64_t V,
+                                int* flags) {
+    int f = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x, t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t i = t0; i < M; i += stride) {
+        if (rp[i] > rp[i + 1]) f |= 1;
+        if (!isfinite(b[i])) f |= 8;
+    }
+    if (t0 == 0 && (rp[0] != 0 || rp[M] != nnz)) f |= 1;
+    for (int64_t q = t0; q < nnz; q += stride) {
+        const int32_t c = col[q];
+        if (c < 0 || (int64_t)c >= V) f |= 2;
+        if (!isfinite(val[q])) f |= 4;
+    }
+    if (f) atomicOr(flags, f);
+}
+
+__global__ void remap_kernel(int32_t* __restrict__ col, int64_t nnz, VoxMap vm) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nnz; q += (int64_t)gridDim.x * blockDim.x)
+        col[q] = (int32_t)vox_internal(vm, col[q]);
+}
+
+// canonical index of internal slot p (the inverse of vox_internal on real voxels)
+__device__ __forceinline__ int64_t vox_canonical(const VoxMap& m, int64_t p) {
+    if (m.tx == 1 && m.ty == 1) return p;
+    const int64_t iz = p / m.slice_p, rem = p - iz * m.slice_p;
+    const int64_t tile = rem >> (m.ltx + m.lty), in = rem & ((1 << (m.ltx + m.lty)) - 1);
+    const int64_t ntx = m.nxp >> m.ltx;
+    const int64_t ty = tile / ntx, tx = tile - ty * ntx;
+    const int64_t ix = (tx << m.ltx) + (in & (m.tx - 1)), iy = (ty << m.lty) + (in >> m.ltx);
+    return (iz * m.ny + iy) * m.nx + ix;
+}
+
+__global__ void unmap_kernel(const int32_t* __restrict__ col, int32_t* __restrict__ out, int64_t nnz, VoxMap vm) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nnz; q += (int64_t)gridDim.x * blockDim.x)
+        out[q] = (int32_t)vox_canonical(vm, col[q]);
+}
+
+// 1 / ||a_i||^2 (FP64 sum), a warp per row
+__global__ void norm_kernel(const int64_t* __restrict__ rp, const float* __restrict__ val, int64_t M,
+                            float* __restrict__ inn) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < M;
+         i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        double s = 0.0;
+        for (int64_t q = rp[i] + lane; q < rp[i + 1]; q += 32) s += (double)val[q] * (double)val[q];
+        s = warp_sum(s);
+        if (lane == 0) inn[i] = s > 0.0 ? (float)(1.0 / s) : 0.f;
+    }
+}
+
+// hit counts of rows [r0, r1): cnt[col] += 1 per nonzero entry (internal order)
+__global__ void count_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                             const float* __restrict__ val, int64_t r0, int64_t r1, int32_t* __restrict__ cnt) {
+    const int64_t q0 = rp[r0], q1 = rp[r1];
+    for (int64_t q = q0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < q1; q += (int64_t)gridDim.x * blockDim.x)
+        if (val[q] != 0.f) atomicAdd(cnt + col[q], 1);
+}
+
+__global__ void inv_count_kernel(const int32_t* __restrict__ cnt, float* __restrict__ inv_s, int64_t n) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = cnt[p];
+        inv_s[p] = c ? (float)(1.0 / (double)c) : 0.f;
+    }
+}
+
+// image copies from x0 (canonical, F64 or F32)
+__global__ void image_init_kernel(const void* __restrict__ x0, int f64, int64_t V, VoxMap vm, double* __restrict__ x,
+                                  float* __restrict__ x32, float* __restrict__ xh, float* __restrict__ xl) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < V; j += (int64_t)gridDim.x * blockDim.x) {
+        const double v = f64 ? ((const double*)x0)[j] : (double)((const float*)x0)[j];
+        x[j] = v;
+        const float h = (float)v;
+        x32[vox_internal(vm, j)] = h;
+        xh[j] = h;
+        xl[j] = (float)(v - (double)h);
+    }
+}
+
+// column range and mean column (internal order) of each DROP item of one block
+__global__ void item_range_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col, int64_t r0,
+                                  int64_t r1, int rows_per_item, int32_t* __restrict__ lo, int32_t* __restrict__ hi,
+                                  int32_t* __restrict__ mean) {
+    const int it = blockIdx.x;
+    const int64_t a = r0 + (int64_t)it * rows_per_item, e = min(r1, a + rows_per_item);
+    int mn = INT32_MAX, mx = -1;
+    long long sum = 0;
+    for (int64_t q = rp[a] + threadIdx.x; q < rp[e]; q += blockDim.x) {
+        const int c = col[q];
+        mn = min(mn, c);
+        mx = max(mx, c);
+        sum += c;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    }
+    __shared__ int smn[32], smx[32];
+    __shared__ long long ssum[32];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { smn[w] = mn; smx[w] = mx; ssum[w] = sum; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) { mn = min(mn, smn[q]); mx = max(mx, smx[q]); sum += ssum[q]; }
+        const int64_t n = rp[e] - rp[a];
+        lo[it] = mn;
+        hi[it] = mx;
+        mean[it] = n > 0 ? (int32_t)(sum / n) : -1;
+    }
+}
+
+// window start of each item for a window of cap floats: lo when all of the item's columns
+// fit; otherwise the window centred on the item's mean column, clamped to [0, vint - cap]
+// (the item's other entries go to global memory); -1 without entries or without a window
+__global__ void window_kernel(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                              const int32_t* __restrict__ mean, int n, int cap, int64_t vint,
+                              int32_t* __restrict__ win) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int32_t w = -1;
+        if (cap > 0 && hi[i] >= lo[i]) {
+            if (hi[i] - lo[i] < cap) {
+                w = lo[i];
+            } else {
+                const int64_t top = vint > cap ? vint - cap : 0;
+                w = (int32_t)max((int64_t)0, min(top, (int64_t)mean[i] - cap / 2));
+            }
+        }
+        win[i] = w;
+    }
+}
+
+}  // namespace
+}  // namespace ntvs
 
 // ------------------------------------------------------------------ host side
+namespace ntvs {
+namespace {
+
 int bfail(int code, const std::string& m) {
     set_last_error(m);
     return code;
@@ -281,6 +798,11 @@ int balloc(P** p, size_t bytes, const char* what) {
     return NTVS_OK;
 }
 
+int grid_of(int64_t n, int threads = 256) {
+    const int64_t g = (n + threads - 1) / threads;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
+}
+
 }  // namespace
 }  // namespace ntvs
 
@@ -295,66 +817,271 @@ struct ntvs_batch {
         MemberDev d{};
         ntvs_params p{};
         std::vector<int64_t> block_ptr;
-        int64_t M = 0, nnz = 0, k = 0, ell_prev = 0;
+        int64_t M = 0, nnz = 0, k = 0, ell_prev = 0;   // k, ell_prev: host schedule (no TV check)
         std::vector<void*> owned;
+        int32_t* item_lo = nullptr;   // [n_drop_items] column range of each DROP item
+        int32_t* item_hi = nullptr;
+        int32_t* item_mean = nullptr;
+        int32_t* win = nullptr;
+        int32_t* item0 = nullptr;     // [B]
+        int n_drop_items = 0;
     };
     std::vector<Member> m;
-    // device tables
     MemberDev* dmem = nullptr;
-    Item* tv_items = nullptr;
-    int n_tv_items = 0;
-    std::vector<Item*> drop_items;   // per block step b
-    std::vector<int> n_drop_items;
-    double* partials = nullptr;
-    unsigned* tickets = nullptr;
-    double* gnorm2 = nullptr;
+    MemberState* dst = nullptr;
+    RunState* drun = nullptr;
+    double* part = nullptr;
+    double* part2 = nullptr;
+    double* part_try = nullptr;
     double* beta = nullptr;          // [N_max][R]
     double* hbeta[2] = {nullptr, nullptr};
-    int64_t* kk = nullptr;           // per-member cycle index (tv_hist slot)
-    int N_max = 0, B_max = 0;
-    int lpr = 32;
+    int N_max = 0;
+    int total_vox_items = 0;
     int64_t tv_cap = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     cudaEvent_t used[2] = {nullptr, nullptr};
     int next = 0;
     int64_t launches = 0, cycles = 0;
+    // schedule of the persistent kernel (fixed by the caller or tuned at finalize)
+    int grid = 0, win_cap = -1, rows_per_item = 0;
+    int req_rows = 0, req_win = -1;
+    uint64_t wait_ns = 2000000000ull;
+    int hook = 0;
 };
 
 namespace {
 
-// lanes per row 8 / 16 / 32 with 16 / 10 / 6 register steps (128 / 160 / 192 entries)
-void launch_dropb(int lpr, int n_items, const MemberDev* mem, const Item* items, cudaStream_t s) {
-    switch (lpr) {
-        case 8: dropb_block_kernel<8, 16><<<n_items, 256, 0, s>>>(mem, items); break;
-        case 16: dropb_block_kernel<16, 10><<<n_items, 256, 0, s>>>(mem, items); break;
-        default: dropb_block_kernel<32, 6><<<n_items, 256, 0, s>>>(mem, items); break;
-    }
+void free_member(ntvs_batch::Member& mm) {
+    for (void* q : mm.owned) cudaFree(q);
+    mm.owned.clear();
 }
 
-int launch_cycle(ntvs_batch* bt, const double* beta_src) {
+int member_alloc(ntvs_batch::Member& mm, void** dst, size_t bytes, const char* what) {
+    BTRY(balloc(dst, bytes, what));
+    mm.owned.push_back(*dst);
+    return NTVS_OK;
+}
+
+// lanes per row: the smallest LPR whose register-held entries (LPR x CH) cover 1.15x the
+// member's mean row length
+int pick_lpr(int64_t M, int64_t nnz) {
+    const double mean = M > 0 ? (double)nnz / (double)M : 0.0;
+    if (1.15 * mean <= 8 * 16) return 8;
+    if (1.15 * mean <= 16 * 10) return 16;
+    return 32;
+}
+
+int check_params(const ntvs_params* p) {
+    if (p->N < 0 || !(p->alpha > 0 && p->alpha < 1) || !(p->beta0 >= 0) || !(p->eps_tv >= 0) || !(p->lambda == p->lambda))
+        return bfail(NTVS_ERR_ARG, "bad parameters");
+    if (p->step_rule < NTVS_STEP_NTVS || p->step_rule > NTVS_STEP_DECOUPLED)
+        return bfail(NTVS_ERR_ARG, "unknown step_rule");
+    if (p->step_rule == NTVS_STEP_DECOUPLED && !(p->gamma > 0 && p->gamma < 1))
+        return bfail(NTVS_ERR_ARG, "gamma must lie in (0, 1)");
+    if (p->tv_check && p->step_rule == NTVS_STEP_DECOUPLED)
+        return bfail(NTVS_ERR_ARG, "the decoupled rule is defined without the TV check");
+    if (p->tv_check && p->max_retries < 1) return bfail(NTVS_ERR_ARG, "max_retries must be >= 1");
+    return NTVS_OK;
+}
+
+int plan_blocks(const int64_t* block_ptr, int n_blocks, int64_t M, std::vector<int64_t>& bp) {
+    bp.clear();
+    if (block_ptr) {
+        if (n_blocks < 1) return bfail(NTVS_ERR_ARG, "n_blocks must be >= 1");
+        bp.assign(block_ptr, block_ptr + n_blocks + 1);
+        if (bp.front() != 0 || bp.back() != M) return bfail(NTVS_ERR_ARG, "block_ptr must run from 0 to n_rows");
+        for (int t = 0; t < n_blocks; ++t)
+            if (bp[t] > bp[t + 1]) return bfail(NTVS_ERR_ARG, "block_ptr decreases");
+    } else {
+        if (n_blocks < 1) return bfail(NTVS_ERR_ARG, "n_blocks must be >= 1");
+        const int64_t per = (M + n_blocks - 1) / n_blocks;
+        for (int t = 0; t <= n_blocks; ++t) bp.push_back(std::min<int64_t>((int64_t)t * per, M));
+    }
+    return NTVS_OK;
+}
+
+// Everything after the rows are on the device in internal column order: norms, per-block
+// hit counts, block table, image copies, scratch.
+int member_prep(ntvs_batch* bt, ntvs_batch::Member& mm, const void* x0, int x0_dtype, int x0_mem) {
+    MemberDev& d = mm.d;
     cudaStream_t s = bt->stream;
-    const int R = (int)bt->m.size();
-    BCUDA(cudaMemcpyAsync(bt->beta, beta_src, sizeof(double) * (size_t)bt->N_max * R, cudaMemcpyHostToDevice, s));
-    for (int n = 0; n < bt->N_max; ++n) {
-        tvb_grad_kernel<<<bt->n_tv_items, 256, 0, s>>>(bt->dmem, bt->tv_items, n, bt->partials, bt->tickets,
-                                                        bt->gnorm2);
-        tvb_apply_kernel<<<bt->n_tv_items, 256, 0, s>>>(bt->dmem, bt->tv_items, n, bt->beta, R, bt->gnorm2);
+    const int64_t M = mm.M, nnz = mm.nnz, V = d.V, VI = d.vm.vint;
+    const int B = (int)mm.block_ptr.size() - 1;
+    BTRY(member_alloc(mm, (void**)&d.inv_norm2, sizeof(float) * std::max<int64_t>(M, 1), "inv_norm2"));
+    BTRY(member_alloc(mm, (void**)&d.inv_s, sizeof(float) * (size_t)B * VI, "inv_s"));
+    BTRY(member_alloc(mm, (void**)&d.block_ptr, sizeof(int64_t) * (B + 1), "block_ptr"));
+    BTRY(member_alloc(mm, (void**)&d.x, sizeof(double) * V, "x"));
+    BTRY(member_alloc(mm, (void**)&d.x32, sizeof(float) * VI, "x32"));
+    BTRY(member_alloc(mm, (void**)&d.xh, sizeof(float) * V, "xh"));
+    BTRY(member_alloc(mm, (void**)&d.xl, sizeof(float) * V, "xl"));
+    BTRY(member_alloc(mm, (void**)&d.delta, sizeof(float) * VI, "delta"));
+    BTRY(member_alloc(mm, (void**)&d.g, sizeof(float) * V, "g"));
+    BTRY(member_alloc(mm, (void**)&d.resid, sizeof(double) * B, "resid"));
+    BCUDA(cudaMemcpyAsync((void*)d.block_ptr, mm.block_ptr.data(), sizeof(int64_t) * (B + 1), cudaMemcpyHostToDevice, s));
+    if (M > 0) norm_kernel<<<grid_of(M * 32), 256, 0, s>>>(d.row_ptr, d.val, M, (float*)d.inv_norm2);
+    int32_t* cnt = nullptr;
+    BTRY(balloc(&cnt, sizeof(int32_t) * VI, "hit counts"));
+    for (int t = 0; t < B; ++t) {
+        cudaMemsetAsync(cnt, 0, sizeof(int32_t) * VI, s);
+        if (mm.block_ptr[t + 1] > mm.block_ptr[t])
+            count_kernel<<<grid_of(nnz), 256, 0, s>>>(d.row_ptr, d.col, d.val, mm.block_ptr[t], mm.block_ptr[t + 1], cnt);
+        inv_count_kernel<<<grid_of(VI), 256, 0, s>>>(cnt, (float*)d.inv_s + (size_t)t * VI, VI);
     }
-    for (int b = 0; b < bt->B_max; ++b) {
-        zero_resid_kernel<<<(R + 127) / 128, 128, 0, s>>>(bt->dmem, R, b);
-        if (bt->n_drop_items[b] > 0) launch_dropb(bt->lpr, bt->n_drop_items[b], bt->dmem, bt->drop_items[b], s);
-        dropb_apply_kernel<<<bt->n_tv_items, 256, 0, s>>>(bt->dmem, bt->tv_items, b);
+    // x0 on the device (copied when it is host memory)
+    const size_t xb = (x0_dtype == NTVS_F64 ? sizeof(double) : sizeof(float)) * (size_t)V;
+    void* xdev = (void*)x0;
+    void* xtmp = nullptr;
+    if (x0_mem == NTVS_MEM_HOST) {
+        cudaError_t e = cudaMalloc(&xtmp, xb);
+        if (e != cudaSuccess) {
+            cudaFree(cnt);
+            return bfail(NTVS_ERR_OOM, "batch: x0 staging");
+        }
+        cudaMemcpyAsync(xtmp, x0, xb, cudaMemcpyHostToDevice, s);
+        xdev = xtmp;
     }
-    tvb_value_kernel<<<bt->n_tv_items, 256, 0, s>>>(bt->dmem, bt->tv_items, bt->kk, bt->partials, bt->tickets);
-    advance_k_kernel<<<(R + 127) / 128, 128, 0, s>>>(bt->kk, R);
+    cudaMemsetAsync(d.x32, 0, sizeof(float) * VI, s);
+    image_init_kernel<<<grid_of(V), 256, 0, s>>>(xdev, x0_dtype == NTVS_F64 ? 1 : 0, V, d.vm, d.x, d.x32, d.xh, d.xl);
+    cudaMemsetAsync(d.delta, 0, sizeof(float) * VI, s);
+    cudaMemsetAsync(d.resid, 0, sizeof(double) * B, s);
+    cudaError_t e = cudaGetLastError();
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    cudaFree(cnt);
+    if (xtmp) cudaFree(xtmp);
+    if (e != cudaSuccess || e2 != cudaSuccess)
+        return bfail(NTVS_ERR_CUDA, std::string("batch member preparation: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    d.B = B;
+    d.lpr = pick_lpr(M, nnz);
+    return NTVS_OK;
+}
+
+void set_member_params(ntvs_batch::Member& mm, int nx, int ny, int nz, const ntvs_params* p) {
+    MemberDev& d = mm.d;
+    d.nx = nx; d.ny = ny; d.nz = nz;
+    d.V = (int64_t)nx * ny * nz;
+    d.N = p->N;
+    d.lambda = (float)p->lambda;
+    d.eps = (float)p->eps_tv;
+    d.beta0 = p->beta0;
+    d.alpha = p->alpha;
+    d.check = p->tv_check ? 1 : 0;
+    d.max_retries = p->tv_check ? p->max_retries : 1;
+    d.rule = p->step_rule;
+    d.seed = p->seed;
+    d.vm = make_voxmap(nx, ny, nz, 4, 4);
+    if (d.vm.vint > 0x7fffffffLL) d.vm = make_voxmap(nx, ny, nz, 1, 1);
+    mm.p = *p;
+}
+
+int common_checks(ntvs_batch* bt, const ntvs_params* p, int nx, int ny, int nz, int x0_dtype, int x0_mem) {
+    if (bt->finalized) return bfail(NTVS_ERR_STATE, "batch already finalized");
+    BTRY(check_params(p));
+    if (nx < 1 || ny < 1 || nz < 1) return bfail(NTVS_ERR_ARG, "bad sizes");
+    if ((int64_t)nx * ny * nz > 0x7fffffffLL) return bfail(NTVS_ERR_ARG, "V too large");
+    if (x0_dtype != NTVS_F64 && x0_dtype != NTVS_F32) return bfail(NTVS_ERR_ARG, "x0 dtype must be F64 or F32");
+    if (x0_mem != NTVS_MEM_HOST && x0_mem != NTVS_MEM_DEVICE) return bfail(NTVS_ERR_ARG, "bad x0 memory kind");
+    return NTVS_OK;
+}
+
+// Item tables of every member for a number of rows per item, and the windows for cap.
+int build_items(ntvs_batch* bt, int rows_per_item, int cap) {
+    cudaStream_t s = bt->stream;
+    for (auto& mm : bt->m) {
+        MemberDev& d = mm.d;
+        const int B = d.B;
+        std::vector<int32_t> item0(B);
+        int n = 0;
+        for (int t = 0; t < B; ++t) {
+            item0[t] = n;
+            n += (int)((mm.block_ptr[t + 1] - mm.block_ptr[t] + rows_per_item - 1) / rows_per_item);
+        }
+        if (mm.item_lo) {
+            cudaFree(mm.item_lo); cudaFree(mm.item_hi); cudaFree(mm.item_mean); cudaFree(mm.win); cudaFree(mm.item0);
+        }
+        mm.item_lo = mm.item_hi = mm.item_mean = mm.win = mm.item0 = nullptr;
+        BTRY(balloc(&mm.item_lo, sizeof(int32_t) * std::max(n, 1), "item ranges"));
+        BTRY(balloc(&mm.item_hi, sizeof(int32_t) * std::max(n, 1), "item ranges"));
+        BTRY(balloc(&mm.item_mean, sizeof(int32_t) * std::max(n, 1), "item ranges"));
+        BTRY(balloc(&mm.win, sizeof(int32_t) * std::max(n, 1), "item windows"));
+        BTRY(balloc(&mm.item0, sizeof(int32_t) * std::max(B, 1), "item table"));
+        BCUDA(cudaMemcpyAsync(mm.item0, item0.data(), sizeof(int32_t) * B, cudaMemcpyHostToDevice, s));
+        for (int t = 0; t < B; ++t) {
+            const int k = (t + 1 < B ? item0[t + 1] : n) - item0[t];
+            if (k > 0)
+                item_range_kernel<<<k, 256, 0, s>>>(d.row_ptr, d.col, mm.block_ptr[t], mm.block_ptr[t + 1], rows_per_item,
+                                                    mm.item_lo + item0[t], mm.item_hi + item0[t],
+                                                    mm.item_mean + item0[t]);
+        }
+        if (n > 0)
+            window_kernel<<<grid_of(n), 256, 0, s>>>(mm.item_lo, mm.item_hi, mm.item_mean, n, cap, d.vm.vint, mm.win);
+        mm.n_drop_items = n;
+        d.rows_per_item = rows_per_item;
+        d.win_lo = mm.win;
+        d.item0 = mm.item0;
+    }
+    std::vector<MemberDev> md;
+    for (auto& mm : bt->m) md.push_back(mm.d);
+    BCUDA(cudaMemcpyAsync(bt->dmem, md.data(), sizeof(MemberDev) * md.size(), cudaMemcpyHostToDevice, s));
+    BCUDA(cudaStreamSynchronize(s));
     BCUDA(cudaGetLastError());
     return NTVS_OK;
 }
 
-int kernels_per_cycle(const ntvs_batch* bt) {
-    int n = 2 * bt->N_max + 2;
-    for (int b = 0; b < bt->B_max; ++b) n += 2 + (bt->n_drop_items[b] > 0 ? 1 : 0);
-    return n;
+CycleArgs cycle_args(ntvs_batch* bt, bool hooks) {
+    CycleArgs a;
+    a.mem = bt->dmem;
+    a.st = bt->dst;
+    a.run = bt->drun;
+    a.R = (int)bt->m.size();
+    a.part = bt->part;
+    a.part2 = bt->part2;
+    a.part_try = bt->part_try;
+    a.beta = bt->beta;
+    a.wait_ns = bt->wait_ns;
+    a.starve = hooks && (bt->hook & NTVS_HOOK_STARVE_BATCH) ? 1 : 0;
+    a.win_cap = bt->win_cap;
+    return a;
+}
+
+int launch_cycle(ntvs_batch* bt, const double* beta_src, bool hooks) {
+    cudaStream_t s = bt->stream;
+    const int R = (int)bt->m.size();
+    BCUDA(cudaMemcpyAsync(bt->beta, beta_src, sizeof(double) * (size_t)std::max(bt->N_max, 1) * R,
+                          cudaMemcpyHostToDevice, s));
+    cycle_setup_kernel<<<(R + 127) / 128, 128, 0, s>>>(bt->dmem, bt->dst, bt->drun, R);
+    batch_cycle_kernel<<<bt->grid, kThreads, sizeof(float) * (size_t)bt->win_cap, s>>>(cycle_args(bt, hooks));
+    BCUDA(cudaGetLastError());
+    return NTVS_OK;
+}
+
+// beta_{k,n} of the next cycle of every member without the TV check (host ell schedule)
+void fill_betas(ntvs_batch* bt, double* hb, bool advance) {
+    const int R = (int)bt->m.size();
+    for (int r = 0; r < R; ++r) {
+        auto& mm = bt->m[r];
+        const int64_t k = mm.k;
+        int64_t ell = mm.p.tv_check ? 0 : cycle_ell(mm.p, k, mm.ell_prev);
+        const int64_t adv = ell_advances(mm.p) ? 1 : 0;
+        for (int n = 0; n < std::max(bt->N_max, 1); ++n) {
+            hb[(size_t)n * R + r] = (!mm.p.tv_check && n < mm.p.N) ? step_beta(mm.p, k, n, ell) : 0.0;
+            if (!mm.p.tv_check && n < mm.p.N) ell += adv;
+        }
+        if (advance) {
+            if (!mm.p.tv_check && adv) mm.ell_prev = ell;
+            mm.k = k + 1;
+        }
+    }
+}
+
+int device_error(ntvs_batch* bt) {
+    RunState rs;
+    BCUDA(cudaMemcpyAsync(&rs, bt->drun, sizeof(RunState), cudaMemcpyDeviceToHost, bt->stream));
+    BCUDA(cudaStreamSynchronize(bt->stream));
+    if (rs.err != 0)
+        return bfail(NTVS_ERR_TIMEOUT, "batch: an idle CTA's bounded wait ran out (member " +
+                                           std::to_string(rs.err_member) + " stopped in phase " +
+                                           std::to_string(rs.err_phase) + "); the batch's images are undefined");
+    return NTVS_OK;
 }
 
 }  // namespace
@@ -388,16 +1115,21 @@ int ntvs_batch_destroy(ntvs_batch* bt) {
     if (!bt) return NTVS_OK;
     cudaSetDevice(bt->device);
     if (bt->stream) cudaStreamSynchronize(bt->stream);
-    for (auto& mm : bt->m)
-        for (void* p : mm.owned) cudaFree(p);
+    for (auto& mm : bt->m) {
+        free_member(mm);
+        cudaFree(mm.item_lo);
+        cudaFree(mm.item_hi);
+        cudaFree(mm.item_mean);
+        cudaFree(mm.win);
+        cudaFree(mm.item0);
+    }
     cudaFree(bt->dmem);
-    cudaFree(bt->tv_items);
-    for (Item* p : bt->drop_items) cudaFree(p);
-    cudaFree(bt->partials);
-    cudaFree(bt->tickets);
-    cudaFree(bt->gnorm2);
+    cudaFree(bt->dst);
+    cudaFree(bt->drun);
+    cudaFree(bt->part);
+    cudaFree(bt->part2);
+    cudaFree(bt->part_try);
     cudaFree(bt->beta);
-    cudaFree(bt->kk);
     for (int j = 0; j < 2; ++j) {
         if (bt->hbeta[j]) cudaFreeHost(bt->hbeta[j]);
         if (bt->graph[j]) cudaGraphExecDestroy(bt->graph[j]);
@@ -411,133 +1143,188 @@ int ntvs_batch_destroy(ntvs_batch* bt) {
 int ntvs_batch_add(ntvs_batch* bt, const ntvs_system* s, const ntvs_params* p, const void* x0, int x0_dtype,
                    int x0_mem, int* index) {
     if (!bt || !s || !p || !x0) return bfail(NTVS_ERR_ARG, "null argument");
-    if (bt->finalized) return bfail(NTVS_ERR_STATE, "batch already finalized");
+    BTRY(common_checks(bt, p, s->nx, s->ny, s->nz, x0_dtype, x0_mem));
     BCUDA(cudaSetDevice(bt->device));
     if (s->val_dtype != NTVS_F32 || s->storage != NTVS_CSR32)
         return bfail(NTVS_ERR_ARG, "batched members take FP32 values in CSR32 storage");
-    if (p->tv_check) return bfail(NTVS_ERR_ARG, "batched members run NTVS without the TV check");
-    if (p->N < 0 || !(p->alpha > 0 && p->alpha < 1) || !(p->beta0 >= 0) || !(p->eps_tv >= 0))
-        return bfail(NTVS_ERR_ARG, "bad parameters");
-    if (p->step_rule < NTVS_STEP_NTVS || p->step_rule > NTVS_STEP_DECOUPLED)
-        return bfail(NTVS_ERR_ARG, "unknown step_rule");
-    if (p->step_rule == NTVS_STEP_DECOUPLED && !(p->gamma > 0 && p->gamma < 1))
-        return bfail(NTVS_ERR_ARG, "gamma must lie in (0, 1)");
-    if (s->nx < 1 || s->ny < 1 || s->nz < 1 || s->n_rows < 0) return bfail(NTVS_ERR_ARG, "bad sizes");
-    if (x0_dtype != NTVS_F64 && x0_dtype != NTVS_F32) return bfail(NTVS_ERR_ARG, "x0 dtype must be F64 or F32");
-    const int64_t V = (int64_t)s->nx * s->ny * s->nz;
-    if (V > 0x7fffffffLL) return bfail(NTVS_ERR_ARG, "V too large");
-    const int64_t M = s->n_rows;
-    // host copies of the structure (blocks are planned on the host)
-    std::vector<int64_t> rp((size_t)M + 1);
-    const bool host = s->mem_kind == NTVS_MEM_HOST;
-    if (host) std::memcpy(rp.data(), s->row_ptr, sizeof(int64_t) * rp.size());
-    else BCUDA(cudaMemcpy(rp.data(), s->row_ptr, sizeof(int64_t) * rp.size(), cudaMemcpyDeviceToHost));
-    if (rp[0] != 0) return bfail(NTVS_ERR_CSR, "row_ptr[0] != 0");
-    for (int64_t i = 0; i < M; ++i)
-        if (rp[i] > rp[i + 1]) return bfail(NTVS_ERR_CSR, "row_ptr decreases");
-    const int64_t nnz = rp[M];
-    std::vector<int32_t> col((size_t)nnz);
-    std::vector<float> val((size_t)nnz), b((size_t)M);
-    if (host) {
-        std::memcpy(col.data(), s->col, sizeof(int32_t) * col.size());
-        std::memcpy(val.data(), s->val, sizeof(float) * val.size());
-        std::memcpy(b.data(), s->b, sizeof(float) * b.size());
-    } else {
-        BCUDA(cudaMemcpy(col.data(), s->col, sizeof(int32_t) * col.size(), cudaMemcpyDeviceToHost));
-        BCUDA(cudaMemcpy(val.data(), s->val, sizeof(float) * val.size(), cudaMemcpyDeviceToHost));
-        BCUDA(cudaMemcpy(b.data(), s->b, sizeof(float) * b.size(), cudaMemcpyDeviceToHost));
-    }
-    for (int64_t q = 0; q < nnz; ++q)
-        if (col[q] < 0 || col[q] >= V || !std::isfinite(val[q])) return bfail(NTVS_ERR_CSR, "bad column or value");
-    for (int64_t i = 0; i < M; ++i)
-        if (!std::isfinite(b[i])) return bfail(NTVS_ERR_CSR, "non-finite right-hand side");
-    // blocks, norms, hit counts (host, FP64)
-    std::vector<int64_t> bp;
-    if (s->block_ptr) {
-        bp.assign(s->block_ptr, s->block_ptr + s->n_blocks + 1);
-        if (bp.front() != 0 || bp.back() != M) return bfail(NTVS_ERR_ARG, "block_ptr must run from 0 to n_rows");
-    } else {
-        if (s->n_blocks < 1) return bfail(NTVS_ERR_ARG, "n_blocks must be >= 1");
-        const int64_t per = (M + s->n_blocks - 1) / s->n_blocks;
-        for (int t = 0; t <= s->n_blocks; ++t) bp.push_back(std::min<int64_t>((int64_t)t * per, M));
-    }
-    const int B = (int)bp.size() - 1;
-    // internal voxel order (4x4 in-plane tiles, as the single-context FP32 path)
-    VoxMap vm = make_voxmap(s->nx, s->ny, s->nz, 4, 4);
-    if (vm.vint > 0x7fffffffLL) vm = make_voxmap(s->nx, s->ny, s->nz, 1, 1);
-    const int64_t VI = vm.vint;
-    std::vector<float> inn((size_t)M), inv_s((size_t)B * VI, 0.f);
-    for (int64_t i = 0; i < M; ++i) {
-        double n2 = 0.0;
-        for (int64_t q = rp[i]; q < rp[i + 1]; ++q) n2 += (double)val[q] * (double)val[q];
-        inn[i] = n2 > 0.0 ? (float)(1.0 / n2) : 0.f;
-    }
-    {
-        std::vector<int32_t> cnt((size_t)V);
-        for (int t = 0; t < B; ++t) {
-            std::fill(cnt.begin(), cnt.end(), 0);
-            for (int64_t q = rp[bp[t]]; q < rp[bp[t + 1]]; ++q)
-                if (val[q] != 0.f) cnt[col[q]] += 1;
-            for (int64_t j = 0; j < V; ++j)
-                inv_s[(size_t)t * VI + vox_internal_host(vm, j)] = cnt[j] ? (float)(1.0 / cnt[j]) : 0.f;
-        }
-    }
+    if (s->n_rows < 0) return bfail(NTVS_ERR_ARG, "n_rows < 0");
+    if (s->mem_kind != NTVS_MEM_HOST && s->mem_kind != NTVS_MEM_DEVICE) return bfail(NTVS_ERR_ARG, "bad mem_kind");
+    if (!s->row_ptr || (s->n_rows > 0 && !s->b)) return bfail(NTVS_ERR_ARG, "null row_ptr or b");
     ntvs_batch::Member mm;
+    set_member_params(mm, s->nx, s->ny, s->nz, p);
+    const int64_t M = s->n_rows;
+    mm.M = M;
+    const cudaMemcpyKind kind = s->mem_kind == NTVS_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    int64_t nnz = 0;
+    if (s->mem_kind == NTVS_MEM_HOST) nnz = s->row_ptr[M];
+    else BCUDA(cudaMemcpy(&nnz, s->row_ptr + M, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    if (nnz < 0) return bfail(NTVS_ERR_CSR, "row_ptr[M] < 0");
+    if (nnz > 0 && (!s->col || !s->val)) return bfail(NTVS_ERR_ARG, "null col or val");
+    mm.nnz = nnz;
+    int rc = plan_blocks(s->block_ptr, s->n_blocks, M, mm.block_ptr);
+    if (rc != NTVS_OK) return rc;
     MemberDev& d = mm.d;
-    auto up = [&](void** dst, const void* src, size_t bytes, const char* what) -> int {
-        BTRY(balloc(dst, bytes, what));
-        mm.owned.push_back(*dst);
-        if (src && bytes) BCUDA(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
-        return NTVS_OK;
-    };
-    std::vector<double> x((size_t)V);
-    if (x0_mem == NTVS_MEM_HOST) {
-        if (x0_dtype == NTVS_F64) std::memcpy(x.data(), x0, sizeof(double) * V);
-        else for (int64_t j = 0; j < V; ++j) x[j] = ((const float*)x0)[j];
-    } else {
-        if (x0_dtype == NTVS_F64) BCUDA(cudaMemcpy(x.data(), x0, sizeof(double) * V, cudaMemcpyDeviceToHost));
-        else {
-            std::vector<float> t((size_t)V);
-            BCUDA(cudaMemcpy(t.data(), x0, sizeof(float) * V, cudaMemcpyDeviceToHost));
-            for (int64_t j = 0; j < V; ++j) x[j] = t[j];
-        }
-    }
-    std::vector<float> x32((size_t)VI, 0.f), xh((size_t)V), xl((size_t)V);
-    for (int64_t j = 0; j < V; ++j) {
-        xh[j] = (float)x[j];
-        xl[j] = (float)(x[j] - (double)xh[j]);
-        x32[(size_t)vox_internal_host(vm, j)] = xh[j];
-    }
-    for (auto& c : col) c = (int32_t)vox_internal_host(vm, c);   // validated above
-    int rc = NTVS_OK;
-    if ((rc = up((void**)&d.row_ptr, rp.data(), sizeof(int64_t) * rp.size(), "row_ptr")) ||
-        (rc = up((void**)&d.col, col.data(), sizeof(int32_t) * col.size(), "col")) ||
-        (rc = up((void**)&d.val, val.data(), sizeof(float) * val.size(), "val")) ||
-        (rc = up((void**)&d.b, b.data(), sizeof(float) * b.size(), "b")) ||
-        (rc = up((void**)&d.inv_norm2, inn.data(), sizeof(float) * inn.size(), "inv_norm2")) ||
-        (rc = up((void**)&d.inv_s, inv_s.data(), sizeof(float) * inv_s.size(), "inv_s")) ||
-        (rc = up((void**)&d.x, x.data(), sizeof(double) * V, "x")) ||
-        (rc = up((void**)&d.x32, x32.data(), sizeof(float) * VI, "x32")) ||
-        (rc = up((void**)&d.xh, xh.data(), sizeof(float) * V, "xh")) ||
-        (rc = up((void**)&d.xl, xl.data(), sizeof(float) * V, "xl")) ||
-        (rc = up((void**)&d.delta, nullptr, sizeof(float) * VI, "delta")) ||
-        (rc = up((void**)&d.g, nullptr, sizeof(float) * V, "g")) ||
-        (rc = up((void**)&d.resid, nullptr, sizeof(double) * std::max(B, 1), "resid"))) {
-        for (void* q : mm.owned) cudaFree(q);
+    int* flags = nullptr;
+    cudaStream_t st = bt->stream;
+    if ((rc = member_alloc(mm, (void**)&d.row_ptr, sizeof(int64_t) * (M + 1), "row_ptr")) ||
+        (rc = member_alloc(mm, (void**)&d.col, sizeof(int32_t) * std::max<int64_t>(nnz, 1), "col")) ||
+        (rc = member_alloc(mm, (void**)&d.val, sizeof(float) * std::max<int64_t>(nnz, 1), "val")) ||
+        (rc = member_alloc(mm, (void**)&d.b, sizeof(float) * std::max<int64_t>(M, 1), "b")) ||
+        (rc = balloc(&flags, sizeof(int), "flags"))) {
+        free_member(mm);
         return rc;
     }
-    BCUDA(cudaMemset((void*)d.delta, 0, sizeof(float) * VI));
-    BCUDA(cudaMemset((void*)d.resid, 0, sizeof(double) * std::max(B, 1)));
-    d.nx = s->nx; d.ny = s->ny; d.nz = s->nz; d.B = B; d.N = p->N; d.V = V;
-    d.vm = vm;
-    d.lambda = (float)p->lambda;
-    d.eps = (float)p->eps_tv;
-    mm.p = *p;
-    mm.block_ptr = bp;
-    mm.M = M;
-    mm.nnz = nnz;
+    cudaMemsetAsync(flags, 0, sizeof(int), st);
+    cudaMemcpyAsync((void*)d.row_ptr, s->row_ptr, sizeof(int64_t) * (M + 1), kind, st);
+    if (nnz > 0) {
+        cudaMemcpyAsync((void*)d.col, s->col, sizeof(int32_t) * nnz, kind, st);
+        cudaMemcpyAsync((void*)d.val, s->val, sizeof(float) * nnz, kind, st);
+    }
+    if (M > 0) cudaMemcpyAsync((void*)d.b, s->b, sizeof(float) * M, kind, st);
+    validate_kernel<<<grid_of(std::max(M, nnz)), 256, 0, st>>>(d.row_ptr, M, d.col, d.val, nnz, d.b, d.V, flags);
+    int hf = 0;
+    cudaMemcpyAsync(&hf, flags, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaFree(flags);
+    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+        free_member(mm);
+        return bfail(NTVS_ERR_CUDA, std::string("batch: copying or validating the system: ") + cudaGetErrorString(e));
+    }
+    if (hf) {
+        free_member(mm);
+        return bfail(NTVS_ERR_CSR, (hf & 1) ? "row_ptr must run non-decreasing from 0 to nnz"
+                                   : (hf & 2) ? "column outside [0, V)"
+                                   : (hf & 4) ? "non-finite value" : "non-finite right-hand side");
+    }
+    if (nnz > 0) remap_kernel<<<grid_of(nnz), 256, 0, st>>>((int32_t*)d.col, nnz, d.vm);
+    if ((rc = member_prep(bt, mm, x0, x0_dtype, x0_mem)) != NTVS_OK) {
+        free_member(mm);
+        return rc;
+    }
     bt->m.push_back(std::move(mm));
     if (index) *index = (int)bt->m.size() - 1;
+    return NTVS_OK;
+}
+
+int ntvs_batch_add_paths(ntvs_batch* bt, const ntvs_paths* p, const ntvs_params* prm, const void* x0, int x0_dtype,
+                         int x0_mem, int* index) {
+    if (!bt || !p || !prm || !x0) return bfail(NTVS_ERR_ARG, "null argument");
+    BTRY(common_checks(bt, prm, p->nx, p->ny, p->nz, x0_dtype, x0_mem));
+    BCUDA(cudaSetDevice(bt->device));
+    if (p->n_rows < 0 || p->n_seg < 1 || p->n_seg > 64 || !(p->min_len >= 0) || !(p->dx > 0) || !(p->dy > 0) ||
+        !(p->dz > 0))
+        return bfail(NTVS_ERR_ARG, "bad path geometry");
+    if (p->mem_kind != NTVS_MEM_HOST && p->mem_kind != NTVS_MEM_DEVICE) return bfail(NTVS_ERR_ARG, "bad mem_kind");
+    if (p->n_rows > 0 && (!p->paths || !p->b)) return bfail(NTVS_ERR_ARG, "null paths or b");
+    ntvs_batch::Member mm;
+    set_member_params(mm, p->nx, p->ny, p->nz, prm);
+    const int64_t M = p->n_rows;
+    mm.M = M;
+    int rc = plan_blocks(p->block_ptr, p->n_blocks, M, mm.block_ptr);
+    if (rc != NTVS_OK) return rc;
+    MemberDev& d = mm.d;
+    cudaStream_t st = bt->stream;
+    const cudaMemcpyKind kind = p->mem_kind == NTVS_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    // the path records on the device (borrowed when they already are), b copied
+    float* paths = (float*)p->paths;
+    float* ptmp = nullptr;
+    int* flags = nullptr;
+    int32_t* nrow = nullptr;
+    auto cleanup = [&]() {
+        if (ptmp) cudaFree(ptmp);
+        if (flags) cudaFree(flags);
+        if (nrow) cudaFree(nrow);
+    };
+    if ((rc = member_alloc(mm, (void**)&d.b, sizeof(float) * std::max<int64_t>(M, 1), "b")) ||
+        (rc = member_alloc(mm, (void**)&d.row_ptr, sizeof(int64_t) * (M + 1), "row_ptr")) ||
+        (rc = balloc(&flags, sizeof(int), "flags")) ||
+        (rc = balloc(&nrow, sizeof(int32_t) * std::max<int64_t>(M, 1), "row lengths"))) {
+        cleanup();
+        free_member(mm);
+        return rc;
+    }
+    if (p->mem_kind == NTVS_MEM_HOST && M > 0) {
+        if ((rc = balloc(&ptmp, sizeof(float) * 10 * (size_t)M, "path staging")) != NTVS_OK) {
+            cleanup();
+            free_member(mm);
+            return rc;
+        }
+        cudaMemcpyAsync(ptmp, p->paths, sizeof(float) * 10 * (size_t)M, cudaMemcpyHostToDevice, st);
+        paths = ptmp;
+    }
+    if (M > 0) cudaMemcpyAsync((void*)d.b, p->b, sizeof(float) * M, kind, st);
+    cudaMemsetAsync(flags, 0, sizeof(int), st);
+    OtfArgs oa;
+    oa.paths = paths;
+    oa.b = d.b;
+    oa.M = M;
+    oa.nx = p->nx; oa.ny = p->ny; oa.nz = p->nz;
+    oa.dx = p->dx; oa.dy = p->dy; oa.dz = p->dz;
+    oa.n_seg = p->n_seg;
+    oa.min_len = (float)p->min_len;
+    oa.grid = grid_of(M, 128);
+    oa.vm = d.vm;   // rows traced straight into the internal voxel order
+    k_otf_validate(oa, flags, st);
+    k_otf_count_rows(oa, nrow, st);
+    int hf = 0;
+    std::vector<int32_t> lens((size_t)M);
+    cudaMemcpyAsync(&hf, flags, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (M > 0) cudaMemcpyAsync(lens.data(), nrow, sizeof(int32_t) * M, cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+        cleanup();
+        free_member(mm);
+        return bfail(NTVS_ERR_CUDA, std::string("batch: tracing the paths: ") + cudaGetErrorString(e));
+    }
+    if (hf) {
+        cleanup();
+        free_member(mm);
+        return bfail(NTVS_ERR_CSR, (hf & 32) ? "non-finite path value" : "non-finite right-hand side");
+    }
+    std::vector<int64_t> rp((size_t)M + 1, 0);
+    for (int64_t i = 0; i < M; ++i) rp[i + 1] = rp[i] + lens[i];
+    const int64_t nnz = rp[M];
+    mm.nnz = nnz;
+    if ((rc = member_alloc(mm, (void**)&d.col, sizeof(int32_t) * std::max<int64_t>(nnz, 1), "col")) ||
+        (rc = member_alloc(mm, (void**)&d.val, sizeof(float) * std::max<int64_t>(nnz, 1), "val"))) {
+        cleanup();
+        free_member(mm);
+        return rc;
+    }
+    cudaMemcpyAsync((void*)d.row_ptr, rp.data(), sizeof(int64_t) * (M + 1), cudaMemcpyHostToDevice, st);
+    k_otf_fill_rows(oa, d.row_ptr, (int32_t*)d.col, (float*)d.val, st);
+    e = cudaStreamSynchronize(st);
+    cleanup();
+    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+        free_member(mm);
+        return bfail(NTVS_ERR_CUDA, std::string("batch: writing the traced rows: ") + cudaGetErrorString(e));
+    }
+    if ((rc = member_prep(bt, mm, x0, x0_dtype, x0_mem)) != NTVS_OK) {
+        free_member(mm);
+        return rc;
+    }
+    bt->m.push_back(std::move(mm));
+    if (index) *index = (int)bt->m.size() - 1;
+    return NTVS_OK;
+}
+
+int ntvs_batch_set_schedule(ntvs_batch* bt, int rows_per_item, int window_floats) {
+    if (!bt) return bfail(NTVS_ERR_ARG, "null batch");
+    if (bt->finalized) return bfail(NTVS_ERR_STATE, "batch already finalized");
+    if (rows_per_item < 0 || rows_per_item > (1 << 20)) return bfail(NTVS_ERR_ARG, "rows_per_item out of range");
+    if (window_floats < -1 || window_floats > 49152) return bfail(NTVS_ERR_ARG, "window_floats out of range");
+    bt->req_rows = rows_per_item;
+    bt->req_win = window_floats;
+    return NTVS_OK;
+}
+
+int ntvs_batch_set_fault_hook(ntvs_batch* bt, int64_t wait_ns, int flags) {
+    if (!bt) return bfail(NTVS_ERR_ARG, "null batch");
+    if (bt->finalized) return bfail(NTVS_ERR_STATE, "set the hook before ntvs_batch_finalize");
+    if (flags & ~NTVS_HOOK_STARVE_BATCH) return bfail(NTVS_ERR_ARG, "unknown hook flags");
+    if (wait_ns < 0) return bfail(NTVS_ERR_ARG, "wait_ns < 0");
+    bt->wait_ns = wait_ns > 0 ? (uint64_t)wait_ns : 2000000000ull;
+    bt->hook = flags;
     return NTVS_OK;
 }
 
@@ -548,87 +1335,129 @@ int ntvs_batch_finalize(ntvs_batch* bt, int max_cycles) {
     if (max_cycles < 1) return bfail(NTVS_ERR_ARG, "max_cycles must be >= 1");
     BCUDA(cudaSetDevice(bt->device));
     const int R = (int)bt->m.size();
-    // TV items (every voxel of every member) and DROP items per block step
-    std::vector<Item> tv;
-    bt->N_max = 0;
-    bt->B_max = 0;
-    for (int r = 0; r < R; ++r) {
-        MemberDev& d = bt->m[r].d;
-        d.item0 = (int)tv.size();
-        for (int64_t v = 0; v < d.V; v += kTvItem) tv.push_back({r, 0, v, std::min<int64_t>(d.V, v + kTvItem)});
-        d.nitems = (int)tv.size() - d.item0;
-        bt->N_max = std::max(bt->N_max, d.N);
-        bt->B_max = std::max(bt->B_max, d.B);
-        BTRY(balloc(&d.tv_hist, sizeof(double) * (size_t)max_cycles, "tv history"));
-        bt->m[r].owned.push_back(d.tv_hist);
-    }
+    if (R > (1 << 20)) return bfail(NTVS_ERR_ARG, "too many members");
+    cudaStream_t s = bt->stream;
+    constexpr int kTrialCycles = 3;
     bt->tv_cap = max_cycles;
-    bt->n_tv_items = (int)tv.size();
-    BTRY(balloc(&bt->tv_items, sizeof(Item) * tv.size(), "TV items"));
-    BCUDA(cudaMemcpy(bt->tv_items, tv.data(), sizeof(Item) * tv.size(), cudaMemcpyHostToDevice));
-    for (int b = 0; b < bt->B_max; ++b) {
-        std::vector<Item> it;
-        for (int r = 0; r < R; ++r) {
-            const auto& mm = bt->m[r];
-            if (b >= mm.d.B) continue;
-            for (int64_t i = mm.block_ptr[b]; i < mm.block_ptr[b + 1]; i += kDropItem)
-                it.push_back({r, b, i, std::min<int64_t>(mm.block_ptr[b + 1], i + kDropItem)});
+    bt->N_max = 0;
+    int off = 0;
+    for (auto& mm : bt->m) {
+        MemberDev& d = mm.d;
+        d.n_vox_items = (int)((d.V + kTvItem - 1) / kTvItem);
+        if ((int64_t)d.n_vox_items > (int64_t)(kM24 >> 1)) return bfail(NTVS_ERR_ARG, "member too large");
+        d.part_off = off;
+        off += d.n_vox_items;
+        bt->N_max = std::max(bt->N_max, d.N);
+        BTRY(member_alloc(mm, (void**)&d.tv_hist, sizeof(double) * (size_t)(max_cycles + kTrialCycles), "tv history"));
+        if (d.check) {
+            std::vector<double> tab(kBetaTab);
+            for (int l = 0; l < kBetaTab; ++l) tab[l] = mm.p.beta0 * std::pow(mm.p.alpha, (double)l);
+            BTRY(member_alloc(mm, (void**)&d.beta_tab, sizeof(double) * kBetaTab, "beta table"));
+            BCUDA(cudaMemcpy((void*)d.beta_tab, tab.data(), sizeof(double) * kBetaTab, cudaMemcpyHostToDevice));
         }
-        Item* di = nullptr;
-        BTRY(balloc(&di, sizeof(Item) * std::max<size_t>(it.size(), 1), "DROP items"));
-        if (!it.empty()) BCUDA(cudaMemcpy(di, it.data(), sizeof(Item) * it.size(), cudaMemcpyHostToDevice));
-        bt->drop_items.push_back(di);
-        bt->n_drop_items.push_back((int)it.size());
     }
-    std::vector<MemberDev> md;
-    for (auto& mm : bt->m) md.push_back(mm.d);
+    bt->total_vox_items = off;
     BTRY(balloc(&bt->dmem, sizeof(MemberDev) * R, "member table"));
-    BCUDA(cudaMemcpy(bt->dmem, md.data(), sizeof(MemberDev) * R, cudaMemcpyHostToDevice));
-    BTRY(balloc(&bt->partials, sizeof(double) * std::max(bt->n_tv_items, 1), "partials"));
-    BTRY(balloc(&bt->tickets, sizeof(unsigned) * R, "tickets"));
-    BTRY(balloc(&bt->gnorm2, sizeof(double) * R, "gnorm2"));
+    BTRY(balloc(&bt->dst, sizeof(MemberState) * R, "member states"));
+    BTRY(balloc(&bt->drun, sizeof(RunState), "run state"));
+    BTRY(balloc(&bt->part, sizeof(double) * off, "partials"));
+    BTRY(balloc(&bt->part2, sizeof(double) * off, "partials"));
+    BTRY(balloc(&bt->part_try, sizeof(double) * off * kSpec, "partials"));
     BTRY(balloc(&bt->beta, sizeof(double) * std::max(bt->N_max, 1) * R, "beta table"));
-    BTRY(balloc(&bt->kk, sizeof(int64_t) * R, "cycle index"));
-    BCUDA(cudaMemset(bt->tickets, 0, sizeof(unsigned) * R));
-    BCUDA(cudaMemset(bt->kk, 0, sizeof(int64_t) * R));
+    BCUDA(cudaMemset(bt->dst, 0, sizeof(MemberState) * R));
+    BCUDA(cudaMemset(bt->drun, 0, sizeof(RunState)));
     for (int j = 0; j < 2; ++j) {
         BCUDA(cudaHostAlloc((void**)&bt->hbeta[j], sizeof(double) * std::max(bt->N_max, 1) * R, cudaHostAllocDefault));
         std::memset(bt->hbeta[j], 0, sizeof(double) * std::max(bt->N_max, 1) * R);
         BCUDA(cudaEventCreateWithFlags(&bt->used[j], cudaEventDisableTiming));
     }
-    // autotune lanes per row on block step 0 (delta is cleared afterwards; x is untouched)
-    if (bt->B_max > 0 && bt->n_drop_items[0] > 0) {
+    int sms = 0;
+    BCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, bt->device));
+    BCUDA(cudaFuncSetAttribute(batch_cycle_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 49152 * 4));
+    auto set_grid = [&](int cap) -> int {
+        int per = 0;
+        BCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_cycle_kernel, kThreads, sizeof(float) * cap));
+        if (per < 1) return bfail(NTVS_ERR_CUDA, "batch: the persistent kernel does not fit on an SM");
+        bt->grid = per * sms;
+        return NTVS_OK;
+    };
+    // schedule: fixed by the caller, else timed over kTrialCycles cycles per candidate
+    // (images and schedule state saved before and restored after)
+    std::vector<int> rows_c = bt->req_rows > 0 ? std::vector<int>{bt->req_rows} : std::vector<int>{128, 256, 512};
+    std::vector<int> win_c = bt->req_win >= 0 ? std::vector<int>{bt->req_win} : std::vector<int>{0, 8192, 16384};
+    if (rows_c.size() * win_c.size() == 1) {
+        bt->rows_per_item = rows_c[0];
+        bt->win_cap = win_c[0];
+    } else {
+        std::vector<void*> saved;
+        auto save = [&](const void* src, size_t bytes) -> int {
+            void* q = nullptr;
+            BTRY(balloc(&q, bytes, "tuning snapshot"));
+            saved.push_back(q);
+            BCUDA(cudaMemcpyAsync(q, src, bytes, cudaMemcpyDeviceToDevice, s));
+            return NTVS_OK;
+        };
+        auto restore = [&]() -> int {
+            size_t i = 0;
+            for (auto& mm : bt->m) {
+                const MemberDev& d = mm.d;
+                BCUDA(cudaMemcpyAsync(d.x, saved[i++], sizeof(double) * d.V, cudaMemcpyDeviceToDevice, s));
+                BCUDA(cudaMemcpyAsync(d.x32, saved[i++], sizeof(float) * d.vm.vint, cudaMemcpyDeviceToDevice, s));
+                BCUDA(cudaMemcpyAsync(d.xh, saved[i++], sizeof(float) * d.V, cudaMemcpyDeviceToDevice, s));
+                BCUDA(cudaMemcpyAsync(d.xl, saved[i++], sizeof(float) * d.V, cudaMemcpyDeviceToDevice, s));
+            }
+            BCUDA(cudaMemsetAsync(bt->dst, 0, sizeof(MemberState) * R, s));
+            BCUDA(cudaMemsetAsync(bt->drun, 0, sizeof(RunState), s));
+            return NTVS_OK;
+        };
+        for (auto& mm : bt->m) {
+            const MemberDev& d = mm.d;
+            BTRY(save(d.x, sizeof(double) * d.V));
+            BTRY(save(d.x32, sizeof(float) * d.vm.vint));
+            BTRY(save(d.xh, sizeof(float) * d.V));
+            BTRY(save(d.xl, sizeof(float) * d.V));
+        }
         cudaEvent_t e0, e1;
         BCUDA(cudaEventCreate(&e0));
         BCUDA(cudaEventCreate(&e1));
         float best = 1e30f;
-        for (int lpr : {8, 16, 32}) {
-            float total = 0.f;
-            for (int rep = 0; rep < 2; ++rep) {
-                BCUDA(cudaEventRecord(e0, bt->stream));
-                launch_dropb(lpr, bt->n_drop_items[0], bt->dmem, bt->drop_items[0], bt->stream);
-                BCUDA(cudaEventRecord(e1, bt->stream));
-                BCUDA(cudaEventSynchronize(e1));
+        int best_rows = rows_c[0], best_win = win_c[0];
+        int rc = NTVS_OK;
+        for (int rows : rows_c) {
+            for (int cap : win_c) {
+                if ((rc = build_items(bt, rows, cap)) != NTVS_OK || (rc = set_grid(cap)) != NTVS_OK) break;
+                bt->win_cap = cap;
+                if ((rc = launch_cycle(bt, bt->hbeta[0], false)) != NTVS_OK) break;   // warm-up
+                cudaEventRecord(e0, s);
+                for (int c = 1; c < kTrialCycles && rc == NTVS_OK; ++c) rc = launch_cycle(bt, bt->hbeta[0], false);
+                cudaEventRecord(e1, s);
+                if (rc != NTVS_OK) break;
+                if (cudaEventSynchronize(e1) != cudaSuccess) { rc = bfail(NTVS_ERR_CUDA, "batch tuning"); break; }
+                if ((rc = device_error(bt)) != NTVS_OK) break;
                 float ms = 0.f;
-                BCUDA(cudaEventElapsedTime(&ms, e0, e1));
-                if (rep) total += ms;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) { best = ms; best_rows = rows; best_win = cap; }
+                if ((rc = restore()) != NTVS_OK) break;
             }
-            if (total < best) { best = total; bt->lpr = lpr; }
+            if (rc != NTVS_OK) break;
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        for (auto& mm : bt->m) {
-            BCUDA(cudaMemsetAsync(mm.d.delta, 0, sizeof(float) * mm.d.vm.vint, bt->stream));
-            BCUDA(cudaMemsetAsync(mm.d.resid, 0, sizeof(double) * std::max(mm.d.B, 1), bt->stream));
-        }
-        BCUDA(cudaStreamSynchronize(bt->stream));
+        if (rc == NTVS_OK) rc = restore();
+        cudaStreamSynchronize(s);
+        for (void* q : saved) cudaFree(q);
+        if (rc != NTVS_OK) return rc;
+        bt->rows_per_item = best_rows;
+        bt->win_cap = best_win;
     }
-    // one graph per pinned beta buffer
+    BTRY(build_items(bt, bt->rows_per_item, bt->win_cap));
+    BTRY(set_grid(bt->win_cap));
+    // one graph per pinned beta buffer: beta copy, cycle setup, the persistent kernel
     for (int j = 0; j < 2; ++j) {
         cudaGraph_t g = nullptr;
-        BCUDA(cudaStreamBeginCapture(bt->stream, cudaStreamCaptureModeThreadLocal));
-        int rc = launch_cycle(bt, bt->hbeta[j]);
-        cudaError_t e = cudaStreamEndCapture(bt->stream, &g);
+        BCUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        int rc = launch_cycle(bt, bt->hbeta[j], true);
+        cudaError_t e = cudaStreamEndCapture(s, &g);
         if (rc != NTVS_OK) return rc;
         if (e != cudaSuccess) return bfail(NTVS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
         e = cudaGraphInstantiate(&bt->graph[j], g, 0);
@@ -643,43 +1472,38 @@ int ntvs_batch_run(ntvs_batch* bt, int k_iters) {
     if (!bt) return bfail(NTVS_ERR_ARG, "null batch");
     if (!bt->finalized) return bfail(NTVS_ERR_STATE, "batch not finalized");
     if (k_iters < 0) return bfail(NTVS_ERR_ARG, "k_iters < 0");
+    if (bt->cycles + k_iters > bt->tv_cap) return bfail(NTVS_ERR_STATE, "more cycles than finalize's max_cycles");
     BCUDA(cudaSetDevice(bt->device));
-    const int R = (int)bt->m.size();
     for (int it = 0; it < k_iters; ++it) {
-        if (bt->cycles >= bt->tv_cap) return bfail(NTVS_ERR_STATE, "more cycles than finalize's max_cycles");
         const int j = bt->next;
         BCUDA(cudaEventSynchronize(bt->used[j]));   // the graph that last read this buffer has copied it
-        double* hb = bt->hbeta[j];
-        for (int r = 0; r < R; ++r) {
-            auto& mm = bt->m[r];
-            const int64_t k = mm.k;
-            int64_t ell = cycle_ell(mm.p, k, mm.ell_prev);
-            const int64_t adv = ell_advances(mm.p) ? 1 : 0;
-            for (int n = 0; n < bt->N_max; ++n) {
-                hb[(size_t)n * R + r] = (n < mm.p.N) ? step_beta(mm.p, k, n, ell) : 0.0;
-                if (n < mm.p.N) ell += adv;
-            }
-            if (adv) mm.ell_prev = ell;
-            mm.k = k + 1;
-        }
+        fill_betas(bt, bt->hbeta[j], true);
         BCUDA(cudaGraphLaunch(bt->graph[j], bt->stream));
         BCUDA(cudaEventRecord(bt->used[j], bt->stream));
         bt->next ^= 1;
         bt->cycles += 1;
-        bt->launches += kernels_per_cycle(bt);
+        bt->launches += 2;
     }
     return NTVS_OK;
+}
+
+int ntvs_batch_sync(ntvs_batch* bt) {
+    if (!bt) return bfail(NTVS_ERR_ARG, "null batch");
+    BCUDA(cudaSetDevice(bt->device));
+    BCUDA(cudaStreamSynchronize(bt->stream));
+    if (!bt->finalized) return NTVS_OK;
+    return device_error(bt);
 }
 
 int ntvs_batch_get_image(ntvs_batch* bt, int index, void* out, int dtype, int mem_kind) {
     if (!bt || !out) return bfail(NTVS_ERR_ARG, "null argument");
     if (index < 0 || index >= (int)bt->m.size()) return bfail(NTVS_ERR_ARG, "member index out of range");
     if (dtype != NTVS_F64 && dtype != NTVS_F32) return bfail(NTVS_ERR_ARG, "dtype must be F64 or F32");
-    BCUDA(cudaSetDevice(bt->device));
+    if (mem_kind != NTVS_MEM_HOST && mem_kind != NTVS_MEM_DEVICE) return bfail(NTVS_ERR_ARG, "bad mem_kind");
+    BTRY(ntvs_batch_sync(bt));
     const MemberDev& d = bt->m[index].d;
     std::vector<double> x((size_t)d.V);
-    BCUDA(cudaMemcpyAsync(x.data(), d.x, sizeof(double) * d.V, cudaMemcpyDeviceToHost, bt->stream));
-    BCUDA(cudaStreamSynchronize(bt->stream));
+    BCUDA(cudaMemcpy(x.data(), d.x, sizeof(double) * d.V, cudaMemcpyDeviceToHost));
     if (mem_kind == NTVS_MEM_HOST) {
         if (dtype == NTVS_F64) std::memcpy(out, x.data(), sizeof(double) * d.V);
         else for (int64_t j = 0; j < d.V; ++j) ((float*)out)[j] = (float)x[j];
@@ -698,11 +1522,48 @@ int ntvs_batch_get_image(ntvs_batch* bt, int index, void* out, int dtype, int me
 int ntvs_batch_get_tv(ntvs_batch* bt, int index, double* tv) {
     if (!bt || !tv) return bfail(NTVS_ERR_ARG, "null argument");
     if (index < 0 || index >= (int)bt->m.size()) return bfail(NTVS_ERR_ARG, "member index out of range");
+    if (bt->cycles == 0) return bfail(NTVS_ERR_STATE, "no cycle run yet");
+    BTRY(ntvs_batch_sync(bt));
+    BCUDA(cudaMemcpy(tv, bt->m[index].d.tv_hist + (bt->cycles - 1), sizeof(double), cudaMemcpyDeviceToHost));
+    return NTVS_OK;
+}
+
+int ntvs_batch_get_member(ntvs_batch* bt, int index, int64_t* out5) {
+    if (!bt || !out5) return bfail(NTVS_ERR_ARG, "null argument");
+    if (index < 0 || index >= (int)bt->m.size()) return bfail(NTVS_ERR_ARG, "member index out of range");
+    if (!bt->finalized) return bfail(NTVS_ERR_STATE, "batch not finalized");
+    BTRY(ntvs_batch_sync(bt));
+    MemberState st;
+    BCUDA(cudaMemcpy(&st, bt->dst + index, sizeof(MemberState), cudaMemcpyDeviceToHost));
     const auto& mm = bt->m[index];
-    if (mm.k == 0) return bfail(NTVS_ERR_STATE, "no cycle run yet");
+    out5[0] = st.k;
+    out5[1] = mm.p.tv_check ? st.ell : mm.ell_prev;
+    out5[2] = st.n_steps;
+    out5[3] = st.n_accepted;
+    out5[4] = st.n_tries;
+    return NTVS_OK;
+}
+
+int ntvs_batch_get_rows(ntvs_batch* bt, int index, int64_t* n_rows, int64_t* nnz, int64_t* row_ptr, int32_t* col,
+                        float* val) {
+    if (!bt) return bfail(NTVS_ERR_ARG, "null batch");
+    if (index < 0 || index >= (int)bt->m.size()) return bfail(NTVS_ERR_ARG, "member index out of range");
     BCUDA(cudaSetDevice(bt->device));
-    BCUDA(cudaMemcpyAsync(tv, mm.d.tv_hist + (mm.k - 1), sizeof(double), cudaMemcpyDeviceToHost, bt->stream));
+    const auto& mm = bt->m[index];
+    if (n_rows) *n_rows = mm.M;
+    if (nnz) *nnz = mm.nnz;
     BCUDA(cudaStreamSynchronize(bt->stream));
+    if (row_ptr) BCUDA(cudaMemcpy(row_ptr, mm.d.row_ptr, sizeof(int64_t) * (mm.M + 1), cudaMemcpyDeviceToHost));
+    if (val && mm.nnz > 0) BCUDA(cudaMemcpy(val, mm.d.val, sizeof(float) * mm.nnz, cudaMemcpyDeviceToHost));
+    if (col && mm.nnz > 0) {
+        int32_t* tmp = nullptr;
+        BTRY(balloc(&tmp, sizeof(int32_t) * mm.nnz, "column read-back"));
+        unmap_kernel<<<grid_of(mm.nnz), 256, 0, bt->stream>>>(mm.d.col, tmp, mm.nnz, mm.d.vm);
+        cudaError_t e = cudaMemcpyAsync(col, tmp, sizeof(int32_t) * mm.nnz, cudaMemcpyDeviceToHost, bt->stream);
+        cudaError_t e2 = cudaStreamSynchronize(bt->stream);
+        cudaFree(tmp);
+        if (e != cudaSuccess || e2 != cudaSuccess) return bfail(NTVS_ERR_CUDA, "batch: column read-back");
+    }
     return NTVS_OK;
 }
 
@@ -710,15 +1571,22 @@ int ntvs_batch_get_stats(ntvs_batch* bt, ntvs_batch_stats* st) {
     if (!bt || !st) return bfail(NTVS_ERR_ARG, "null argument");
     std::memset(st, 0, sizeof(*st));
     st->members = (int32_t)bt->m.size();
-    st->lanes_per_row = bt->lpr;
     st->cycles = bt->cycles;
     st->n_launches = bt->launches;
-    st->kernels_per_cycle = bt->finalized ? kernels_per_cycle(bt) : 0;
+    st->kernels_per_cycle = bt->finalized ? 2 : 0;
+    st->rows_per_item = bt->rows_per_item;
+    st->window_floats = bt->win_cap < 0 ? 0 : bt->win_cap;
+    st->ctas = bt->grid;
+    int lmin = 32, lmax = 0;
     for (const auto& mm : bt->m) {
         st->total_rows += mm.M;
         st->total_nnz += mm.nnz;
         st->total_voxels += mm.d.V;
+        lmin = std::min(lmin, mm.d.lpr);
+        lmax = std::max(lmax, mm.d.lpr);
     }
+    st->lanes_per_row = bt->m.empty() ? 0 : lmax;
+    st->lanes_per_row_min = bt->m.empty() ? 0 : lmin;
     return NTVS_OK;
 }
 

@@ -161,6 +161,52 @@ __global__ void otf_prep_kernel(const float* __restrict__ paths, int64_t r0, int
     }
 }
 
+// ---------------------------------------------------------------- stored rows from paths
+// Row i as the load-time statistics see it: the path traced in order by one thread,
+// consecutive pieces of one voxel merged, merged pieces shorter than min_len dropped.
+// Pass 1 counts the entries of every row; pass 2 writes them (voxel index in the order of
+// g, length) from row_ptr[i].  Both passes run the same code, so they agree entry by entry.
+template <bool FILL>
+__global__ void otf_rows_kernel(const float* __restrict__ paths, int64_t M, Grid3 g, int n_seg, float min_len,
+                                int32_t* __restrict__ nnz_row, const int64_t* __restrict__ row_ptr,
+                                int32_t* __restrict__ col, float* __restrict__ val) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        float pr[10];
+#pragma unroll
+        for (int q = 0; q < 10; ++q) pr[q] = paths[i * 10 + q];
+        float nxv, nyv;
+        chord_normal(pr, nxv, nyv);
+        int64_t pos = FILL ? row_ptr[i] : 0;
+        int n = 0;
+        int cur = -1;
+        float acc = 0.f;
+        auto close = [&]() {
+            if (cur >= 0 && acc >= min_len) {
+                if (FILL) {
+                    col[pos] = cur;
+                    val[pos] = acc;
+                    ++pos;
+                }
+                ++n;
+            }
+        };
+        float A[3], B[3];
+        path_point(pr, nxv, nyv, 0.f, A);
+        for (int sg = 0; sg < n_seg; ++sg) {
+            path_point(pr, nxv, nyv, (float)(sg + 1) / (float)n_seg, B);
+            trace_segment(g, A, B, [&](int v, float l) {
+                if (v == cur) { acc += l; return; }
+                close();
+                cur = v;
+                acc = l;
+            });
+            A[0] = B[0]; A[1] = B[1]; A[2] = B[2];
+        }
+        close();
+        if (!FILL) nnz_row[i] = n;
+    }
+}
+
 // ---------------------------------------------------------------- the DROP block
 // A group of 16 lanes per row (2 rows per warp); lane s traces segments s, s + 16, ...
 // The dot-product pass keeps the first kOtfCache accepted pieces of each lane (voxel,
@@ -375,6 +421,20 @@ cudaError_t k_otf_drop(const OtfArgs& a, int64_t r0, int64_t r1, const float* in
     if (e != cudaSuccess) return e;
     otf_drop_kernel<<<a.grid, kOtfThreads, smem, s>>>(a.paths, a.b, inv_norm2, r0, r1, make_grid(a), a.n_seg,
                                                       a.min_len, x, delta, (float)lambda, resid_ss);
+    return cudaGetLastError();
+}
+
+cudaError_t k_otf_count_rows(const OtfArgs& a, int32_t* nnz_row, cudaStream_t s) {
+    if (a.M <= 0) return cudaSuccess;
+    otf_rows_kernel<false><<<a.grid, 128, 0, s>>>(a.paths, a.M, make_grid(a), a.n_seg, a.min_len, nnz_row, nullptr,
+                                                  nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t k_otf_fill_rows(const OtfArgs& a, const int64_t* row_ptr, int32_t* col, float* val, cudaStream_t s) {
+    if (a.M <= 0) return cudaSuccess;
+    otf_rows_kernel<true><<<a.grid, 128, 0, s>>>(a.paths, a.M, make_grid(a), a.n_seg, a.min_len, nullptr, row_ptr,
+                                                 col, val);
     return cudaGetLastError();
 }
 

@@ -257,6 +257,9 @@ cudaError_t k_otf_drop(const OtfArgs& a, int64_t r0, int64_t r1, const float* in
                        double lambda, double* resid_ss, cudaStream_t s);
 // out[i] = <a_i, x> of every traced row (x in the internal voxel order)
 cudaError_t k_otf_project(const OtfArgs& a, const float* x, float* out, cudaStream_t s);
+// stored rows from paths: entries per row, then (voxel in the order of a.vm, length) from row_ptr
+cudaError_t k_otf_count_rows(const OtfArgs& a, int32_t* nnz_row, cudaStream_t s);
+cudaError_t k_otf_fill_rows(const OtfArgs& a, const int64_t* row_ptr, int32_t* col, float* val, cudaStream_t s);
 
 // ------------------------------------------------------------------ row-sharded DROP
 // out[j] = delta[internal(j)] in type odt (F32/F64), then delta = 0 (canonical j < V)
