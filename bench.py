@@ -379,6 +379,7 @@ def run_batched_variant(args, ntvs, local, stream, world, device):
         bt.sync()
         ms_b = max_over_ranks(g0.elapsed_time(g1), world, device)
         bst = bt.stats()
+        tuning = bt.tuning()
         mems = [bt.member(i) for i in range(len(dev))]
         sizes = [(bt.sizes(i)[1], sp.n_hist, sp.V, prm["N"], sp.n_blocks)
                  for i, (sp, prm, _, _, _) in enumerate(dev)]
@@ -397,7 +398,9 @@ def run_batched_variant(args, ntvs, local, stream, world, device):
                 "kernels_per_cycle": int(bst["kernels_per_cycle"]),
                 "gpu_launches_per_step": bst["n_launches"] / max(bst["cycles"], 1),
                 "schedule": {"rows_per_item": bst["rows_per_item"], "window_floats": bst["window_floats"],
-                             "ctas": bst["ctas"], "lanes_per_row": [bst["lanes_per_row_min"], bst["lanes_per_row"]]},
+                             "ctas": bst["ctas"], "ctas_per_sm": bst["ctas_per_sm"],
+                             "lanes_per_row": [bst["lanes_per_row_min"], bst["lanes_per_row"]],
+                             "tuning_ms": [[r, w, c, round(ms, 3)] for r, w, c, ms in tuning]},
                 "tries_per_step": sum(m["n_tries"] for m in mems) / max(sum(m["n_steps"] for m in mems), 1),
                 "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                              "algorithmic_bytes_per_cycle": cyc_bytes, "peak_source": peak_src,

@@ -479,6 +479,17 @@ def ntvs_batch_get_rows(bt: int, index: int):
     return rp, col, val
 
 
+def ntvs_batch_get_tuning(bt: int) -> list:
+    """[(rows_per_item, window_floats, ctas_per_sm, ms_per_cycle)] timed at finalize."""
+    n = ctypes.c_int()
+    check(lib().ntvs_batch_get_tuning(bt, None, None, 0, ctypes.byref(n)), "ntvs_batch_get_tuning")
+    cand = np.zeros(3 * max(n.value, 1), np.int32)
+    ms = np.zeros(max(n.value, 1), np.float32)
+    check(lib().ntvs_batch_get_tuning(bt, cand.ctypes.data, ms.ctypes.data, n.value, ctypes.byref(n)),
+          "ntvs_batch_get_tuning")
+    return [(int(cand[3 * i]), int(cand[3 * i + 1]), int(cand[3 * i + 2]), float(ms[i])) for i in range(n.value)]
+
+
 def ntvs_batch_finalize(bt: int, max_cycles: int) -> None:
     check(lib().ntvs_batch_finalize(bt, max_cycles), "ntvs_batch_finalize")
 
@@ -672,6 +683,9 @@ class Batch:
 
     def sizes(self, index: int):
         return ntvs_batch_get_sizes(self._bt, index)
+
+    def tuning(self) -> list:
+        return ntvs_batch_get_tuning(self._bt)
 
     def run(self, k: int):
         ntvs_batch_run(self._bt, k)

@@ -86,7 +86,8 @@ class ntvs_batch_stats(ctypes.Structure):
     _fields_ = [("members", ctypes.c_int32), ("lanes_per_row", ctypes.c_int32), ("cycles", ctypes.c_int64),
                 ("n_launches", ctypes.c_int64), ("kernels_per_cycle", ctypes.c_int64), ("total_rows", ctypes.c_int64),
                 ("total_nnz", ctypes.c_int64), ("total_voxels", ctypes.c_int64), ("rows_per_item", ctypes.c_int32),
-                ("window_floats", ctypes.c_int32), ("ctas", ctypes.c_int32), ("lanes_per_row_min", ctypes.c_int32)]
+                ("window_floats", ctypes.c_int32), ("ctas", ctypes.c_int32), ("lanes_per_row_min", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 vp, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
@@ -150,6 +151,7 @@ SIGNATURES = {
     "ntvs_batch_sync": (ctypes.c_int, [vp]),
     "ntvs_batch_get_member": (ctypes.c_int, [vp, ctypes.c_int, vp]),
     "ntvs_batch_get_rows": (ctypes.c_int, [vp, ctypes.c_int, P(i64), P(i64), vp, vp, vp]),
+    "ntvs_batch_get_tuning": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, P(ctypes.c_int)]),
     "ntvs_batch_finalize": (ctypes.c_int, [vp, ctypes.c_int]),
     "ntvs_batch_run": (ctypes.c_int, [vp, ctypes.c_int]),
     "ntvs_batch_get_image": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int]),

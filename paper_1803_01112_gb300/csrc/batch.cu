@@ -16,6 +16,14 @@
 // item completes and the cycle ends without co-residency or grid barriers.  When the wait
 // runs out the CTA records an error and every CTA leaves (NTVS_ERR_TIMEOUT on the host).
 //
+// Memory ordering.  Data written inside the kernel (the image and its copies, g, delta,
+// partials) is read with plain loads, which may be served by the SM's L1: every item is
+// taken by an atomic on the schedule word followed by a gpu-scope fence and a CTA barrier
+// (an acquire), and every phase is published by a fence before the exchange (a release),
+// so by the PTX memory model the loads of an item see everything its member's earlier
+// phases wrote.  The non-coherent read-only path (__ldg) is used only for data that no
+// phase writes (rows, b, 1/||a||^2, 1/s, tables).
+//
 // TV check (TRY): each pass evaluates phi(z_t), z_t = x - beta_{ell+t} g / ||g||, for
 // kSpec consecutive tries t at once (x and g read once for all of them); the first t with
 // phi(z_t) <= phi(x) is the accepted try, as if the tries had run one by one; a pass with
@@ -121,7 +129,7 @@ __device__ __forceinline__ unsigned long long ld_word(const unsigned long long* 
 // block tree): the same order whichever CTA does it
 __device__ __forceinline__ double ordered_sum(const double* a, int n, int stride, double* sh) {
     double s = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s += __ldcg(a + (size_t)i * stride);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += a[(size_t)i * stride];
     return block_sum(s, sh);   // valid in thread 0
 }
 
@@ -137,7 +145,7 @@ __device__ void grad_item(const MemberDev& m, int idx, double* part, double* par
     const float* xl = m.xl;
     const float eps = m.eps;
     auto dif = [&](int64_t a, int64_t b) -> float {
-        return (__ldcg(xh + a) - __ldcg(xh + b)) + (__ldcg(xl + a) - __ldcg(xl + b));
+        return (xh[a] - xh[b]) + (xl[a] - xl[b]);
     };
     double acc = 0.0, phi = 0.0;
     for (int64_t p = i0 + threadIdx.x; p < i1; p += blockDim.x) {
@@ -168,9 +176,9 @@ __device__ void grad_item(const MemberDev& m, int idx, double* part, double* par
         m.g[p] = gq;
         acc += (double)gq * (double)gq;
         if (m.check) {
-            const double xc = __ldcg(m.x + p);
-            const double ex = hx ? __ldcg(m.x + p + 1) - xc : 0.0, ey = hy ? __ldcg(m.x + p + nx) - xc : 0.0,
-                         ez = hz ? __ldcg(m.x + p + sxy) - xc : 0.0;
+            const double xc = m.x[p];
+            const double ex = hx ? m.x[p + 1] - xc : 0.0, ey = hy ? m.x[p + nx] - xc : 0.0,
+                         ez = hz ? m.x[p + sxy] - xc : 0.0;
             phi += sqrt(ex * ex + ey * ey + ez * ez);
         }
     }
@@ -200,11 +208,11 @@ __device__ void try_item(const MemberDev& m, int idx, int64_t ell, int T, double
     for (int64_t p = i0 + threadIdx.x; p < i1; p += blockDim.x) {
         int ix, iy, iz;
         voxel_coords(p, nx, ny, ix, iy, iz);
-        const double xc = __ldcg(m.x + p), gc = (double)__ldcg(m.g + p);
+        const double xc = m.x[p], gc = (double)m.g[p];
         const bool hx = ix + 1 < nx, hy = iy + 1 < ny, hz = iz + 1 < nz;
-        const double xx = hx ? __ldcg(m.x + p + 1) : 0.0, gx = hx ? (double)__ldcg(m.g + p + 1) : 0.0;
-        const double xy = hy ? __ldcg(m.x + p + nx) : 0.0, gy = hy ? (double)__ldcg(m.g + p + nx) : 0.0;
-        const double xz = hz ? __ldcg(m.x + p + sxy) : 0.0, gz = hz ? (double)__ldcg(m.g + p + sxy) : 0.0;
+        const double xx = hx ? m.x[p + 1] : 0.0, gx = hx ? (double)m.g[p + 1] : 0.0;
+        const double xy = hy ? m.x[p + nx] : 0.0, gy = hy ? (double)m.g[p + nx] : 0.0;
+        const double xz = hz ? m.x[p + sxy] : 0.0, gz = hz ? (double)m.g[p + sxy] : 0.0;
 #pragma unroll
         for (int t = 0; t < kSpec; ++t) {
             if (t < T) {
@@ -229,7 +237,7 @@ __device__ void try_item(const MemberDev& m, int idx, int64_t ell, int T, double
 __device__ void apply_item(const MemberDev& m, int idx, double sc) {
     const int64_t i0 = (int64_t)idx * kTvItem, i1 = min(m.V, i0 + kTvItem);
     for (int64_t p = i0 + threadIdx.x; p < i1; p += blockDim.x) {
-        const double z = perturbed(__ldcg(m.x + p), sc, (double)__ldcg(m.g + p));
+        const double z = perturbed(m.x[p], sc, (double)m.g[p]);
         m.x[p] = z;
         const float h = (float)z;
         m.x32[vox_internal(m.vm, p)] = h;
@@ -246,7 +254,7 @@ __device__ void dapply_item(const MemberDev& m, int idx, int b) {
     const bool last = b == m.B - 1;
     for (int64_t j = i0 + threadIdx.x; j < i1; j += blockDim.x) {
         const int64_t p = vox_internal(m.vm, j);
-        const double v = __ldcg(m.x + j) + (double)__ldcg(m.delta + p) * (double)__ldg(inv_s + p);
+        const double v = m.x[j] + (double)m.delta[p] * (double)__ldg(inv_s + p);
         m.x[j] = v;
         const float h = (float)v;
         m.x32[p] = h;
@@ -267,10 +275,9 @@ __device__ void phi_item(const MemberDev& m, int idx, double* part, double* sh) 
     for (int64_t p = i0 + threadIdx.x; p < i1; p += blockDim.x) {
         int ix, iy, iz;
         voxel_coords(p, nx, ny, ix, iy, iz);
-        const double xc = __ldcg(m.x + p);
-        const double ex = (ix + 1 < nx) ? __ldcg(m.x + p + 1) - xc : 0.0,
-                     ey = (iy + 1 < ny) ? __ldcg(m.x + p + nx) - xc : 0.0,
-                     ez = (iz + 1 < nz) ? __ldcg(m.x + p + sxy) - xc : 0.0;
+        const double xc = m.x[p];
+        const double ex = (ix + 1 < nx) ? m.x[p + 1] - xc : 0.0, ey = (iy + 1 < ny) ? m.x[p + nx] - xc : 0.0,
+                     ez = (iz + 1 < nz) ? m.x[p + sxy] - xc : 0.0;
         acc += sqrt(ex * ex + ey * ey + ez * ez);
     }
     const double t = block_sum(acc, sh);
@@ -308,9 +315,9 @@ __device__ void drop_rows(const MemberDev& m, int64_t i0, int64_t i1, int w0, in
         float acc = 0.f;
 #pragma unroll
         for (int u = 0; u < CH; ++u)
-            if (c[u] >= 0) acc += a[u] * __ldcg(m.x32 + c[u]);
+            if (c[u] >= 0) acc += a[u] * m.x32[c[u]];
         const int64_t tail0 = p0 + (int64_t)CH * LPR;
-        for (int64_t q = tail0 + sub; q < p1; q += LPR) acc += __ldg(m.val + q) * __ldcg(m.x32 + __ldg(m.col + q));
+        for (int64_t q = tail0 + sub; q < p1; q += LPR) acc += __ldg(m.val + q) * m.x32[__ldg(m.col + q)];
 #pragma unroll
         for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         float r = 0.f;
@@ -508,8 +515,10 @@ __global__ void cycle_setup_kernel(const MemberDev* __restrict__ mem, MemberStat
     s.word = pack_word((unsigned)(s.word >> 48) + 1u, (unsigned)items);
 }
 
-// One cycle of every member (see the file comment).
-__global__ void __launch_bounds__(kThreads) batch_cycle_kernel(CycleArgs a) {
+// One cycle of every member (see the file comment).  MINB: CTAs per SM the register
+// allocation is fitted to (3: no spills; 4: 64 registers, a few spills).
+template <int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) batch_cycle_kernel(CycleArgs a) {
     __shared__ double sh[32];
     __shared__ int s_r, s_idx, s_items, s_last, s_exit, s_phase, s_b, s_tries;
     __shared__ unsigned long long s_word;
@@ -843,10 +852,12 @@ struct ntvs_batch {
     int next = 0;
     int64_t launches = 0, cycles = 0;
     // schedule of the persistent kernel (fixed by the caller or tuned at finalize)
-    int grid = 0, win_cap = -1, rows_per_item = 0;
+    int grid = 0, win_cap = -1, rows_per_item = 0, minb = 3;
     int req_rows = 0, req_win = -1;
     uint64_t wait_ns = 2000000000ull;
     int hook = 0;
+    std::vector<int32_t> tune_cand;   // (rows per item, window floats, CTAs per SM) per timed candidate
+    std::vector<float> tune_ms;       // its cycle time
 };
 
 namespace {
@@ -1049,7 +1060,9 @@ int launch_cycle(ntvs_batch* bt, const double* beta_src, bool hooks) {
     BCUDA(cudaMemcpyAsync(bt->beta, beta_src, sizeof(double) * (size_t)std::max(bt->N_max, 1) * R,
                           cudaMemcpyHostToDevice, s));
     cycle_setup_kernel<<<(R + 127) / 128, 128, 0, s>>>(bt->dmem, bt->dst, bt->drun, R);
-    batch_cycle_kernel<<<bt->grid, kThreads, sizeof(float) * (size_t)bt->win_cap, s>>>(cycle_args(bt, hooks));
+    const size_t smem = sizeof(float) * (size_t)bt->win_cap;
+    if (bt->minb == 4) batch_cycle_kernel<4><<<bt->grid, kThreads, smem, s>>>(cycle_args(bt, hooks));
+    else batch_cycle_kernel<3><<<bt->grid, kThreads, smem, s>>>(cycle_args(bt, hooks));
     BCUDA(cudaGetLastError());
     return NTVS_OK;
 }
@@ -1337,7 +1350,7 @@ int ntvs_batch_finalize(ntvs_batch* bt, int max_cycles) {
     const int R = (int)bt->m.size();
     if (R > (1 << 20)) return bfail(NTVS_ERR_ARG, "too many members");
     cudaStream_t s = bt->stream;
-    constexpr int kTrialCycles = 3;
+    constexpr int kTrialCycles = 2;   // per tuning candidate: one warm-up, one timed
     bt->tv_cap = max_cycles;
     bt->N_max = 0;
     int off = 0;
@@ -1373,21 +1386,28 @@ int ntvs_batch_finalize(ntvs_batch* bt, int max_cycles) {
     }
     int sms = 0;
     BCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, bt->device));
-    BCUDA(cudaFuncSetAttribute(batch_cycle_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 49152 * 4));
-    auto set_grid = [&](int cap) -> int {
+    BCUDA(cudaFuncSetAttribute(batch_cycle_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 49152 * 4));
+    BCUDA(cudaFuncSetAttribute(batch_cycle_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 49152 * 4));
+    auto set_grid = [&](int cap, int minb) -> int {
         int per = 0;
-        BCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_cycle_kernel, kThreads, sizeof(float) * cap));
+        if (minb == 4)
+            BCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_cycle_kernel<4>, kThreads, sizeof(float) * cap));
+        else
+            BCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_cycle_kernel<3>, kThreads, sizeof(float) * cap));
         if (per < 1) return bfail(NTVS_ERR_CUDA, "batch: the persistent kernel does not fit on an SM");
         bt->grid = per * sms;
+        bt->minb = minb;
         return NTVS_OK;
     };
     // schedule: fixed by the caller, else timed over kTrialCycles cycles per candidate
     // (images and schedule state saved before and restored after)
-    std::vector<int> rows_c = bt->req_rows > 0 ? std::vector<int>{bt->req_rows} : std::vector<int>{128, 256, 512};
+    std::vector<int> rows_c = bt->req_rows > 0 ? std::vector<int>{bt->req_rows} : std::vector<int>{256, 512, 1024};
     std::vector<int> win_c = bt->req_win >= 0 ? std::vector<int>{bt->req_win} : std::vector<int>{0, 8192, 16384};
-    if (rows_c.size() * win_c.size() == 1) {
+    std::vector<int> minb_c = (bt->req_rows > 0 && bt->req_win >= 0) ? std::vector<int>{3} : std::vector<int>{3, 4};
+    if (rows_c.size() * win_c.size() * minb_c.size() == 1) {
         bt->rows_per_item = rows_c[0];
         bt->win_cap = win_c[0];
+        bt->minb = minb_c[0];
     } else {
         std::vector<void*> saved;
         auto save = [&](const void* src, size_t bytes) -> int {
@@ -1421,23 +1441,30 @@ int ntvs_batch_finalize(ntvs_batch* bt, int max_cycles) {
         BCUDA(cudaEventCreate(&e0));
         BCUDA(cudaEventCreate(&e1));
         float best = 1e30f;
-        int best_rows = rows_c[0], best_win = win_c[0];
+        int best_rows = rows_c[0], best_win = win_c[0], best_minb = minb_c[0];
         int rc = NTVS_OK;
         for (int rows : rows_c) {
+            if ((rc = build_items(bt, rows, 0)) != NTVS_OK) break;
             for (int cap : win_c) {
-                if ((rc = build_items(bt, rows, cap)) != NTVS_OK || (rc = set_grid(cap)) != NTVS_OK) break;
-                bt->win_cap = cap;
-                if ((rc = launch_cycle(bt, bt->hbeta[0], false)) != NTVS_OK) break;   // warm-up
-                cudaEventRecord(e0, s);
-                for (int c = 1; c < kTrialCycles && rc == NTVS_OK; ++c) rc = launch_cycle(bt, bt->hbeta[0], false);
-                cudaEventRecord(e1, s);
+                if (cap > 0 && (rc = build_items(bt, rows, cap)) != NTVS_OK) break;
+                for (int minb : minb_c) {
+                    if ((rc = set_grid(cap, minb)) != NTVS_OK) break;
+                    bt->win_cap = cap;
+                    if ((rc = launch_cycle(bt, bt->hbeta[0], false)) != NTVS_OK) break;   // warm-up
+                    cudaEventRecord(e0, s);
+                    for (int c = 1; c < kTrialCycles && rc == NTVS_OK; ++c) rc = launch_cycle(bt, bt->hbeta[0], false);
+                    cudaEventRecord(e1, s);
+                    if (rc != NTVS_OK) break;
+                    if (cudaEventSynchronize(e1) != cudaSuccess) { rc = bfail(NTVS_ERR_CUDA, "batch tuning"); break; }
+                    if ((rc = device_error(bt)) != NTVS_OK) break;
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    bt->tune_cand.insert(bt->tune_cand.end(), {rows, cap, minb});
+                    bt->tune_ms.push_back(ms / (float)(kTrialCycles - 1));
+                    if (ms < best) { best = ms; best_rows = rows; best_win = cap; best_minb = minb; }
+                    if ((rc = restore()) != NTVS_OK) break;
+                }
                 if (rc != NTVS_OK) break;
-                if (cudaEventSynchronize(e1) != cudaSuccess) { rc = bfail(NTVS_ERR_CUDA, "batch tuning"); break; }
-                if ((rc = device_error(bt)) != NTVS_OK) break;
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < best) { best = ms; best_rows = rows; best_win = cap; }
-                if ((rc = restore()) != NTVS_OK) break;
             }
             if (rc != NTVS_OK) break;
         }
@@ -1449,9 +1476,10 @@ int ntvs_batch_finalize(ntvs_batch* bt, int max_cycles) {
         if (rc != NTVS_OK) return rc;
         bt->rows_per_item = best_rows;
         bt->win_cap = best_win;
+        bt->minb = best_minb;
     }
     BTRY(build_items(bt, bt->rows_per_item, bt->win_cap));
-    BTRY(set_grid(bt->win_cap));
+    BTRY(set_grid(bt->win_cap, bt->minb));
     // one graph per pinned beta buffer: beta copy, cycle setup, the persistent kernel
     for (int j = 0; j < 2; ++j) {
         cudaGraph_t g = nullptr;
@@ -1567,6 +1595,18 @@ int ntvs_batch_get_rows(ntvs_batch* bt, int index, int64_t* n_rows, int64_t* nnz
     return NTVS_OK;
 }
 
+int ntvs_batch_get_tuning(ntvs_batch* bt, int32_t* cand, float* ms, int cap, int* n) {
+    if (!bt || !n) return bfail(NTVS_ERR_ARG, "null argument");
+    if (cap < 0 || (cap > 0 && (!cand || !ms))) return bfail(NTVS_ERR_ARG, "bad output arrays");
+    const int k = (int)bt->tune_ms.size();
+    *n = k;
+    for (int i = 0; i < std::min(k, cap); ++i) {
+        for (int q = 0; q < 3; ++q) cand[3 * i + q] = bt->tune_cand[3 * (size_t)i + q];
+        ms[i] = bt->tune_ms[i];
+    }
+    return NTVS_OK;
+}
+
 int ntvs_batch_get_stats(ntvs_batch* bt, ntvs_batch_stats* st) {
     if (!bt || !st) return bfail(NTVS_ERR_ARG, "null argument");
     std::memset(st, 0, sizeof(*st));
@@ -1577,6 +1617,7 @@ int ntvs_batch_get_stats(ntvs_batch* bt, ntvs_batch_stats* st) {
     st->rows_per_item = bt->rows_per_item;
     st->window_floats = bt->win_cap < 0 ? 0 : bt->win_cap;
     st->ctas = bt->grid;
+    st->ctas_per_sm = bt->minb;
     int lmin = 32, lmax = 0;
     for (const auto& mm : bt->m) {
         st->total_rows += mm.M;
