@@ -13,7 +13,7 @@
  *     s_j^t = number of stored entries (i, j) of block t with a_ij != 0.
  *
  * phi = TV = sum over voxels of the Euclidean length of the forward-difference
- * vector (Sec. IV, ref. CCCNP10), index spacing, difference past the last index = 0.
+ * vector (TV is introduced in Sec. II with ref. CCCNP10), index spacing, difference past the last index = 0.
  * The perturbation direction is v = -grad phi_eps / ||grad phi_eps|| (Appendix A),
  * phi_eps(x) = sum_p sqrt(eps + |forward differences at p|^2); v = 0 if the gradient is 0.
  *

@@ -2,8 +2,8 @@
  * proton histories, a median filter and a threshold hull, on the GPU in FP64.
  *
  * The paper starts the reconstruction from x-bar (Appendix A), an FBP image (FBP is the
- * transform method of Sec. I; Sec. II-D leaves the preprocessing to earlier work) to
- * which a median filter of radius 2 is applied (Sec. IV-A).  The paper defines none of
+ * transform method of Sec. II; Sec. III-D leaves the preprocessing to earlier work) to
+ * which a median filter of radius 2 is applied (Sec. V-A).  The paper defines none of
  * these steps; this library specifies them as follows.
  *
  *   1. Binning (ntvs_fbp_bin).  A history is taken as its chord P_in -> P_out (the path

@@ -4,9 +4,9 @@
  * the product library shares no code with it.
  *
  * The paper reconstructs from an initial iterate x-bar (Appendix A) made by filtered
- * back-projection (FBP, the transform method of Sec. I; the preprocessing itself is left
- * to earlier work in Sec. II-D), to which a median filter of radius r = 2 is applied
- * (Sec. IV-A).  It gives no formulas, so the library states its own specification and
+ * back-projection (FBP, the transform method of Sec. II; the preprocessing itself is left
+ * to earlier work in Sec. III-D), to which a median filter of radius r = 2 is applied
+ * (Sec. V-A).  It gives no formulas, so the library states its own specification and
  * this file is each step's plain definition, in the order of that specification:
  *   1. binning: every history by its chord (straight-line approximation), into
  *      (slice, angle, lateral) bins of a parallel-beam sinogram; a bin holds the mean

@@ -15,7 +15,8 @@
  *     beta_0 = 1 is exposed as beta0.
  *   - OTVS (Appendix B): ell is never reset between cycles, beta = (1/2)^ell.
  *   - decoupled step size beta_{k,n} = alpha^n gamma^{f(k)}, f(k) = k (Sec. VI).
- *   - phi = TV, "sum of local variations over all voxels" (Sec. IV, ref. CCCNP10);
+ *   - phi = TV, the sum over the voxels of the local variation (introduced in Sec. II
+ *     with ref. CCCNP10);
  *     v = -grad phi / ||grad phi|| (Appendix A).
  *   - P_T = one sweep of block-DROP (Sec. III-D cites the DROP algorithm of ref.
  *     CEHN08 without printing its update).

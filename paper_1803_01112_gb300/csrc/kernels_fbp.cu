@@ -1,5 +1,5 @@
-// Initial iterate x-bar (arXiv 1803.01112: x-bar of Appendix A, FBP of Sec. I, median
-// filter of radius 2 on the initial iterate in Sec. IV-A): chord binning, Ram-Lak filter,
+// Initial iterate x-bar (arXiv 1803.01112: x-bar of Appendix A, FBP of Sec. II, median
+// filter of radius 2 on the initial iterate in Sec. V-A): chord binning, Ram-Lak filter,
 // back-projection, median filter and threshold hull, all in FP64.  The steps follow the
 // specification in include/ntvs_fbp.h.
 //

@@ -1,6 +1,6 @@
 // On-the-fly DROP rows (P_T of arXiv 1803.01112 Appendix C with the system never stored):
 // row i is the intersection-length vector of history i's path with the voxel grid
-// (Sec. I: "intersection lengths of tracked protons through individual object voxels").
+// (Sec. I: a row holds the lengths of one tracked proton's path through the voxels).
 // A path is a chord P_in -> P_out plus cubic-Hermite offsets A h10(s) + B h11(s) along the
 // in-plane normal and along z, split into n_seg straight segments; every sweep traces it
 // again, in FP32: each segment is cut at every voxel plane it crosses (three per-axis

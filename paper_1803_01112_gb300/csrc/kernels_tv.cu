@@ -1,6 +1,6 @@
 // TV kernels: gradient of phi_eps with its FP64 norm, phi in FP64, and the perturbation
 // x <- x + beta v, v = -g/||g|| (arXiv 1803.01112, Appendix A/C; phi = TV as the sum of
-// local variations, Sec. IV).  Forward differences on index spacing, zero past the last
+// local variations, introduced in Sec. II).  Forward differences on index spacing, zero past the last
 // index.  The image is tiny next to the system matrix (V floats), so these kernels live
 // in L2; every reduction is FP64 with a fixed reduction order (deterministic).
 #include "common.cuh"

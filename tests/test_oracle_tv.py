@@ -1,4 +1,4 @@
-"""Pins of the oracle's TV value and gradient (phi = TV, Sec. IV; v = -grad/||grad||, Appendix A).
+"""Pins of the oracle's TV value and gradient (phi = TV, Sec. II; v = -grad/||grad||, Appendix A).
 
 Nothing here re-types the oracle's stencil: each check is a closed form, an invariant,
 a hand expansion (tests/golden/tv_2x2.json) or a finite-difference derivative.
