@@ -186,7 +186,7 @@ def measured_peaks():
 
 def drop_kernel_hash():
     h = hashlib.sha256()
-    for f in ("kernels_drop.cu", "kernels_drop_tma.cu", "common.cuh"):
+    for f in ("kernels_drop.cuh", "kernels_drop.cu", "kernels_drop_tma.cu", "common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1803_01112_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 

@@ -44,8 +44,29 @@ __device__ __forceinline__ void load4(const __nv_bfloat16* p, float (&o)[4]) {
     o[0] = f0.x; o[1] = f0.y; o[2] = f1.x; o[3] = f1.y;
 }
 
-// The windowed kernel's dynamic shared memory: the slice window, voxels [w0, w0 + W).
+// The windowed kernel's dynamic shared memory: the stage of the current run of kRowStage
+// rows (row pointers, b, 1/||a||^2) at fixed offsets, then the slice window, voxels
+// [w0, w0 + W).  Fixed offsets keep the addresses out of the row loop's registers.
 extern __shared__ __align__(16) unsigned char drop_win_smem[];
+constexpr int kRowStage = 1024;   // rows staged at once by the windowed kernel
+template <typename T>
+__host__ __device__ constexpr size_t stage_bytes() {
+    return ((sizeof(int64_t) * (kRowStage + 1) + 15) & ~(size_t)15) + 2 * sizeof(T) * kRowStage;
+}
+template <typename T>
+__device__ __forceinline__ int64_t* stage_rp() { return reinterpret_cast<int64_t*>(drop_win_smem); }
+template <typename T>
+__device__ __forceinline__ T* stage_b() {
+    return reinterpret_cast<T*>(drop_win_smem + ((sizeof(int64_t) * (kRowStage + 1) + 15) & ~(size_t)15));
+}
+template <typename T>
+__device__ __forceinline__ T* stage_inv() { return stage_b<T>() + kRowStage; }
+template <typename T>
+__device__ __forceinline__ unsigned char* window_base() { return drop_win_smem + stage_bytes<T>(); }
+inline size_t window_smem_bytes(int64_t slice, size_t tsize) {
+    const size_t stage = tsize == 8 ? stage_bytes<double>() : stage_bytes<float>();
+    return stage + (size_t)((slice + 31) & ~31LL) * tsize;
+}
 
 struct Window {
     int w0;        // voxel indices stay below 2^31
@@ -80,11 +101,11 @@ __device__ __forceinline__ void scatter(T* delta, const Window& w, int32_t c, T 
             if constexpr (sizeof(T) == 4) {
                 if (rowfix) {   // |rq a| < 2^22: adding 1.5 * 2^23 rounds it to the nearest integer
                     const int y = __float_as_int(fmaf(rq, (float)a, 12582912.0f)) - 0x4B400000;
-                    atomicAdd(reinterpret_cast<int*>(drop_win_smem) + swz(rel), y);
+                    atomicAdd(reinterpret_cast<int*>(window_base<T>()) + swz(rel), y);
                     return;
                 }
             } else {
-                atomicAdd(reinterpret_cast<T*>(drop_win_smem) + swz(rel), r * a);
+                atomicAdd(reinterpret_cast<T*>(window_base<T>()) + swz(rel), r * a);
                 return;
             }
         }
@@ -139,8 +160,7 @@ __device__ __forceinline__ int32_t d16_col(const Delta16& d, const int32_t* cbr,
 template <typename T, typename V, int LPR, int CH, int VW, bool WIN, bool D16, bool ESC = false>
 __device__ __forceinline__ void drop_row(int64_t i, const RowHead& h, bool valid, int sub,
                                          const int32_t* __restrict__ col, const Delta16& d16,
-                                         const V* __restrict__ val, const T* __restrict__ b,
-                                         const T* __restrict__ inv_norm2, const T* __restrict__ x,
+                                         const V* __restrict__ val, T bval, T ival, const T* __restrict__ x,
                                          T* __restrict__ delta, T lambda, const Window& w, double& ss, WinScale* ws) {
     static_assert(!D16 || VW == 1, "DELTA16 rows are read one entry per lane");
     const int64_t p0 = h.p0, p1 = h.p1;
@@ -200,8 +220,8 @@ __device__ __forceinline__ void drop_row(int64_t i, const RowHead& h, bool valid
     for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     T res = (T)0, inv = (T)0;
     if (valid) {
-        res = __ldg(b + i) - acc;
-        inv = __ldg(inv_norm2 + i);
+        res = bval - acc;
+        inv = ival;
         if (sub == 0) ss += (double)res * (double)res;
     }
     T r;
@@ -223,19 +243,18 @@ __device__ __forceinline__ void drop_row(int64_t i, const RowHead& h, bool valid
 template <typename T, typename V, int LPR, int CH, int VW, bool WIN, bool D16>
 __device__ __forceinline__ void drop_row_any(int64_t i, const RowHead& h, bool valid, int sub,
                                              const int32_t* __restrict__ col, const Delta16& d16,
-                                             const V* __restrict__ val, const T* __restrict__ b,
-                                             const T* __restrict__ inv_norm2, const T* __restrict__ x,
+                                             const V* __restrict__ val, T bval, T ival, const T* __restrict__ x,
                                              T* __restrict__ delta, T lambda, const Window& w, double& ss,
                                              WinScale* ws) {
     if constexpr (D16) {
         if (valid && __ldg(d16.rowesc + i))
-            drop_row<T, V, LPR, CH, VW, WIN, true, true>(i, h, valid, sub, col, d16, val, b, inv_norm2, x, delta,
+            drop_row<T, V, LPR, CH, VW, WIN, true, true>(i, h, valid, sub, col, d16, val, bval, ival, x, delta,
                                                         lambda, w, ss, ws);
         else
-            drop_row<T, V, LPR, CH, VW, WIN, true, false>(i, h, valid, sub, col, d16, val, b, inv_norm2, x, delta,
+            drop_row<T, V, LPR, CH, VW, WIN, true, false>(i, h, valid, sub, col, d16, val, bval, ival, x, delta,
                                                          lambda, w, ss, ws);
     } else {
-        drop_row<T, V, LPR, CH, VW, WIN, false>(i, h, valid, sub, col, d16, val, b, inv_norm2, x, delta, lambda, w,
+        drop_row<T, V, LPR, CH, VW, WIN, false>(i, h, valid, sub, col, d16, val, bval, ival, x, delta, lambda, w,
                                                 ss, ws);
     }
 }
@@ -257,8 +276,10 @@ drop_block_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict
     for (int64_t base = r0 + warp * G; base < r1; base += nwarps * G) {
         const int64_t in = i + nwarps * G;
         const RowHead hn = load_head(in, in < r1, row_ptr);   // next row, ahead of use
-        drop_row_any<T, V, LPR, CH, VW, false, D16>(i, h, i < r1, lane % LPR, col, d16, val, b, inv_norm2, x, delta,
-                                                    lambda, w, ss, nullptr);
+        const bool valid = i < r1;
+        const T bi = valid ? __ldg(b + i) : (T)0, ii = valid ? __ldg(inv_norm2 + i) : (T)0;
+        drop_row_any<T, V, LPR, CH, VW, false, D16>(i, h, valid, lane % LPR, col, d16, val, bi, ii, x, delta, lambda,
+                                                    w, ss, nullptr);
         i = in;
         h = hn;
     }
@@ -301,11 +322,11 @@ drop_block_window_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __r
                          int64_t slice, const T* __restrict__ x, T* __restrict__ delta, T lambda,
                          double* resid_ss, Delta16 d16, const float* wlmax, const float* wbound, float* wobs,
                          const float* wamax) {
-    T* win = reinterpret_cast<T*>(drop_win_smem);
-    __shared__ WinScale ws;
-    __shared__ double ss_grp[32][32 / LPR];                     // per row group: sum of res^2 (one writer)
+    T* win = reinterpret_cast<T*>(window_base<T>());
     const int W = (int)slice;
     const int Wp = (W + 31) & ~31;
+    __shared__ WinScale ws;
+    __shared__ double ss_grp[32][32 / LPR];                     // per row group: sum of res^2 (one writer)
     constexpr int G = 32 / LPR;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -339,11 +360,29 @@ drop_block_window_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __r
             w.w0 = (int)(cur * slice);
         }
         const int grp = lane / LPR;
-        for (int64_t base = sg.r0 + (int64_t)warp * G; base < sg.r1; base += (int64_t)nwarps * G) {
-            const int64_t i = base + grp;
-            const RowHead h = load_head(i, i < sg.r1, row_ptr);
-            drop_row_any<T, V, LPR, CH, VW, true, D16>(i, h, i < sg.r1, lane % LPR, col, d16, val, b, inv_norm2, x,
-                                                       delta, lambda, w, ss_grp[warp][grp], &ws);
+        // the segment's rows in runs of kRowStage: one coalesced load of their row
+        // pointers, b and 1/||a||^2 into shared memory, so that a row starts from its
+        // entries' addresses instead of a round trip to HBM for its row pointer
+        for (int64_t c0 = sg.r0; c0 < sg.r1; c0 += kRowStage) {
+            const int n = (int)min((int64_t)kRowStage, sg.r1 - c0);
+            __syncthreads();   // the previous run's rows are done with the stage
+            for (int j = threadIdx.x; j <= n; j += blockDim.x) {
+                stage_rp<T>()[j] = __ldg(row_ptr + c0 + j);
+                if (j < n) {
+                    stage_b<T>()[j] = __ldg(b + c0 + j);
+                    stage_inv<T>()[j] = __ldg(inv_norm2 + c0 + j);
+                }
+            }
+            __syncthreads();
+            for (int base = warp * G; base < n; base += nwarps * G) {
+                const int k = base + grp;
+                const bool valid = k < n;
+                const RowHead h{valid ? stage_rp<T>()[k] : 0, valid ? stage_rp<T>()[k + 1] : 0};
+                drop_row_any<T, V, LPR, CH, VW, true, D16>(c0 + k, h, valid, lane % LPR, col, d16, val,
+                                                           valid ? stage_b<T>()[k] : (T)0,
+                                                           valid ? stage_inv<T>()[k] : (T)0, x, delta, lambda, w,
+                                                           ss_grp[warp][grp], &ws);
+            }
         }
     }
     __syncthreads();
@@ -361,7 +400,7 @@ drop_block_window_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __r
 template <typename T, typename V, int LPR, int CH, int VW, bool D16>
 cudaError_t launch_window(const DropArgs& a, cudaStream_t s) {
     auto kern = drop_block_window_kernel<T, V, LPR, CH, VW, D16>;
-    const size_t smem = (size_t)((a.slice + 31) & ~31LL) * sizeof(T);
+    const size_t smem = window_smem_bytes(a.slice, sizeof(T));
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<a.grid, 1024, smem, s>>>(a.row_ptr, a.col, (const V*)a.val, (const T*)a.b, (const T*)a.inv_norm2, a.segs,

@@ -174,6 +174,8 @@ struct DropArgs {
     const float* wamax;   // max |a_ij| of the block: rows whose terms could reach 2^22 Q go global
     int64_t max_row;      // longest row of the block (register steps of the windowed kernel)
 };
+// dynamic shared memory of the windowed DROP kernel for a slice of `slice` voxels
+int64_t k_window_smem_bytes(int64_t slice, int csz);
 cudaError_t k_drop_block(const DropArgs& a, cudaStream_t s);
 cudaError_t k_drop_block_d16(const DropArgs& a, cudaStream_t s);   // the same on DELTA16 storage
 // out[i] = <a_i, x> for the M rows (x: compute type, in the order of the stored columns;
