@@ -48,7 +48,7 @@ __device__ __forceinline__ void load4(const __nv_bfloat16* p, float (&o)[4]) {
 // rows (row pointers, b, 1/||a||^2) at fixed offsets, then the slice window, voxels
 // [w0, w0 + W).  Fixed offsets keep the addresses out of the row loop's registers.
 extern __shared__ __align__(16) unsigned char drop_win_smem[];
-constexpr int kRowStage = 1024;   // rows staged at once by the windowed kernel
+constexpr int kRowStage = 2048;   // rows staged at once by the windowed kernel
 template <typename T>
 __host__ __device__ constexpr size_t stage_bytes() {
     return ((sizeof(int64_t) * (kRowStage + 1) + 15) & ~(size_t)15) + 2 * sizeof(T) * kRowStage;
@@ -291,10 +291,32 @@ drop_block_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict
 // Windowed variant: CTA b processes segments [seg_begin[b], seg_begin[b+1]) in order.
 // The window holds Wp = W rounded up to 32 slots (swizzled); slots past W stay 0.  FP32
 // compute keeps int32 multiples of the quantum Q, FP64 compute doubles.
+// 4 consecutive floats added to global memory with one vector reduction (16-byte aligned)
+__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
+
 template <typename T>
-__device__ __forceinline__ void flush_window(void* winp, int Wp, T* delta, int w0, float Q) {
+__device__ __forceinline__ void flush_window(void* winp, int W, int Wp, T* delta, int w0, float Q) {
     if constexpr (sizeof(T) == 4) {
         int* win = reinterpret_cast<int*>(winp);
+        if (((w0 | W) & 3) == 0 && ((uintptr_t)delta & 15) == 0) {
+            // Four voxel offsets j..j+3 (j a multiple of 4) lie in one group of 32 slots,
+            // and swz maps them to the aligned slots swz(j) & ~3 in the order
+            // e -> (swz(j) & 3) ^ e: one 16-byte shared load and one vector reduction each
+            for (int j = 4 * threadIdx.x; j < W; j += 4 * blockDim.x) {
+                const int sj = swz(j);
+                int4* slot = reinterpret_cast<int4*>(win + (sj & ~3));
+                const int4 v4 = *slot;
+                if ((v4.x | v4.y | v4.z | v4.w) == 0) continue;
+                const int v[4] = {v4.x, v4.y, v4.z, v4.w};
+                const int k = sj & 3;
+                red_add_v4(reinterpret_cast<float*>(delta) + w0 + j, (float)v[k] * Q, (float)v[k ^ 1] * Q,
+                           (float)v[k ^ 2] * Q, (float)v[k ^ 3] * Q);
+                *slot = make_int4(0, 0, 0, 0);
+            }
+            return;
+        }
         for (int jj = threadIdx.x; jj < Wp; jj += blockDim.x) {
             const int v = win[jj];
             if (v != 0) {
@@ -354,7 +376,7 @@ drop_block_window_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __r
         const DropSegment sg = segs[s];
         if (sg.home != cur) {   // uniform across the CTA
             __syncthreads();
-            flush_window<T>(win, Wp, delta, w.w0, Q);
+            flush_window<T>(win, W, Wp, delta, w.w0, Q);
             __syncthreads();
             cur = sg.home;
             w.w0 = (int)(cur * slice);
@@ -386,7 +408,7 @@ drop_block_window_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __r
         }
     }
     __syncthreads();
-    flush_window<T>(win, Wp, delta, w.w0, Q);
+    flush_window<T>(win, W, Wp, delta, w.w0, Q);
     if (lane < G) ss = ss_grp[warp][lane];
     __shared__ double sh[32];
     const double tot = block_sum(ss, sh);   // synchronizes the CTA

