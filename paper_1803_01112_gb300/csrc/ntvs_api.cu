@@ -809,6 +809,7 @@ static int plan_schedule(ntvs_ctx* c, int requested) {
                                  c->stream));
         CUDA_TRY(cudaStreamSynchronize(c->stream));
         const int64_t S = pipe_stage_entries(c->vdt, idx_bytes);
+        const int64_t nnz_all = rp[c->M];
         // entries per 16 bytes of both the column and the value arrays
         const int64_t A = 16 / std::min<int64_t>(idx_bytes, (int64_t)dt_size(c->vdt));
         auto down = [&](int64_t e) { return (e / A) * A; };
@@ -829,7 +830,11 @@ static int plan_schedule(ntvs_ctx* c, int requested) {
                         st.home = (int16_t)sg.home;
                         const int64_t e0 = down(rp[i]);
                         int64_t j = i;
-                        while (j < sg.r1 && j - i < kStageRows && up(rp[j + 1]) - e0 <= S) ++j;
+                        // a stage's aligned copy never reaches past the last entry (the arrays
+                        // may be the caller's, sized exactly): a row that would is read from
+                        // global memory by the consumers
+                        while (j < sg.r1 && j - i < kStageRows && up(rp[j + 1]) - e0 <= S && up(rp[j + 1]) <= nnz_all)
+                            ++j;
                         if (j == i) {   // one row longer than a slot: consumers read it from global memory
                             st.e0 = rp[i];
                             st.nent = 0;
@@ -849,6 +854,9 @@ static int plan_schedule(ntvs_ctx* c, int requested) {
             sb[G] = (int32_t)stages.size();
         }
         if (stages.size() > (size_t)INT32_MAX) return fail(NTVS_ERR_ARG, "too many pipeline stages");
+        for (const DropStage& st : stages)
+            if (st.nent > 0 && st.e0 + st.nent > nnz_all)
+                return fail(NTVS_ERR_ARG, "pipelined schedule: a stage reaches past the last entry");
         TRY(dev_alloc(&c->stages, sizeof(DropStage) * std::max<size_t>(stages.size(), 1), "DROP stages"));
         TRY(dev_alloc(&c->stage_begin, sizeof(int32_t) * sbeg.size(), "DROP stage index"));
         CUDA_TRY(cudaMemcpyAsync(c->stages, stages.data(), sizeof(DropStage) * stages.size(), cudaMemcpyHostToDevice,

@@ -193,6 +193,43 @@ def test_drop_schedules_match_oracle(dtype, schedule):
     np.testing.assert_allclose(res, ss, rtol=1e-10 if dtype == np.float64 else 1e-4)
 
 
+def test_pipeline_stages_stay_inside_exact_sized_arrays():
+    """The pipelined schedule copies stages of whole rows with 16-byte aligned bulk copies;
+    with BF16 values and int32 columns (8-entry alignment) and nnz not a multiple of 8, the
+    last rows must not be copied past the end of the caller's exact-sized device arrays
+    (the library refuses a plan that would, and such rows are read from global memory);
+    the sweep still equals the oracle's."""
+    ntvs = ntvs_module()
+    import torch
+    from paper_1803_01112_gb300._ffi import NTVS_SCHED_PIPELINE
+    s = synth.generate(synth.spec_scaled_3d(nx=40, ny=40, nz=5, n_hist=30_000, n_angles=36, n_blocks=4, seed=8))
+    M = s.M
+    while int(s.row_ptr[M]) % 8 == 0:   # drop rows from the end until nnz is not a multiple of 8
+        M -= 1
+    nnz = int(s.row_ptr[M])
+    rp = torch.from_numpy(s.row_ptr[:M + 1].copy()).cuda()
+    col = torch.from_numpy(s.col[:nnz].copy()).cuda()
+    val = torch.from_numpy(s.val[:nnz].astype(np.float32)).to(torch.bfloat16).cuda()
+    b = torch.from_numpy(s.b[:M].astype(np.float32)).cuda()
+    assert col.numel() == nnz and nnz % 8 != 0
+    x0 = s.xstar * 0.9 + 0.05
+    r = ntvs.Reconstructor(0)
+    try:
+        r.load((40, 40, 5), rp, col, val, b, n_blocks=4, schedule=NTVS_SCHED_PIPELINE)
+        assert r.stats()["drop_schedule"] == NTVS_SCHED_PIPELINE
+        r.set_params(lam=1.1, N=0, alpha=0.5)
+        r.set_image(x0)
+        r.drop_sweep()
+        got = r.get_image()
+    finally:
+        r.close()
+    v64 = val.float().cpu().numpy().astype(np.float64)
+    bp = synth.block_partition(M, 4)
+    want, _ = oracle.drop_sweep(s.row_ptr[:M + 1], s.col[:nnz], v64, s.b[:M].astype(np.float32).astype(np.float64),
+                                bp, x0, 1.1)
+    assert rel_l2(got, want) < 1e-6
+
+
 def test_fixed_point_window_follows_its_bound():
     """The FP32 windowed schedule accumulates its slice window in int32 fixed point with a
     per-block scale bounded by the previous sweep's largest |residual| / ||a||^2; rows above
