@@ -49,6 +49,19 @@ __device__ __forceinline__ void load4(const __nv_bfloat16* p, float (&o)[4]) {
 // [w0, w0 + W).  Fixed offsets keep the addresses out of the row loop's registers.
 extern __shared__ __align__(16) unsigned char drop_win_smem[];
 constexpr int kRowStage = 2048;   // rows staged at once by the windowed kernel
+constexpr int kPrefetchRows = 1;  // the windowed kernel asks L2 for the entries of the row this many ahead
+
+// L2 prefetch of the 128-byte lines holding entries [q0, q1) of the index array (int32
+// columns or DELTA16 offsets) and of val, one line per lane (rows longer than the warp's
+// 32 lines prefetch their first lines only)
+template <typename I, typename V>
+__device__ __forceinline__ void prefetch_row_l2(const I* col, const V* val, int64_t q0, int64_t q1, int lane) {
+    const uintptr_t c0 = (uintptr_t)(col + q0) & ~(uintptr_t)127, c1 = (uintptr_t)(col + q1);
+    const uintptr_t v0 = (uintptr_t)(val + q0) & ~(uintptr_t)127, v1 = (uintptr_t)(val + q1);
+    const int nc = (int)((c1 - c0 + 127) >> 7), nv = (int)((v1 - v0 + 127) >> 7);
+    if (lane < nc) asm volatile("prefetch.global.L2 [%0];" ::"l"(c0 + ((uintptr_t)lane << 7)));
+    else if (lane - nc < nv) asm volatile("prefetch.global.L2 [%0];" ::"l"(v0 + ((uintptr_t)(lane - nc) << 7)));
+}
 template <typename T>
 __host__ __device__ constexpr size_t stage_bytes() {
     return ((sizeof(int64_t) * (kRowStage + 1) + 15) & ~(size_t)15) + 2 * sizeof(T) * kRowStage;
@@ -399,6 +412,19 @@ drop_block_window_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __r
             for (int base = warp * G; base < n; base += nwarps * G) {
                 const int k = base + grp;
                 const bool valid = k < n;
+                if constexpr (kPrefetchRows > 0 && LPR == 32) {
+                    const int kp = k + kPrefetchRows * nwarps;   // this warp's row that many iterations ahead
+                    if (kp < n) {
+                        const int64_t q0 = stage_rp<T>()[kp], q1 = stage_rp<T>()[kp + 1];
+                        if constexpr (D16) {
+                            prefetch_row_l2(d16.off, val, q0, q1, lane);
+                            // and the row's chunk bases (slots (q0 >> 5) + row + k, one short run)
+                            if (lane == 31) asm volatile("prefetch.global.L2 [%0];" ::"l"(d16.cbase + (q0 >> 5) + c0 + kp));
+                        } else {
+                            prefetch_row_l2(col, val, q0, q1, lane);
+                        }
+                    }
+                }
                 const RowHead h{valid ? stage_rp<T>()[k] : 0, valid ? stage_rp<T>()[k + 1] : 0};
                 drop_row_any<T, V, LPR, CH, VW, true, D16>(c0 + k, h, valid, lane % LPR, col, d16, val,
                                                            valid ? stage_b<T>()[k] : (T)0,
