@@ -50,6 +50,7 @@ __device__ __forceinline__ void load4(const __nv_bfloat16* p, float (&o)[4]) {
 extern __shared__ __align__(16) unsigned char drop_win_smem[];
 constexpr int kRowStage = 2048;   // rows staged at once by the windowed kernel
 constexpr int kPrefetchRows = 1;  // the windowed kernel asks L2 for the entries of the row this many ahead
+constexpr int kShortSteps = 8;    // register steps of the windowed kernel's body for short rows
 
 // L2 prefetch of the 128-byte lines holding entries [q0, q1) of the index array (int32
 // columns or DELTA16 offsets) and of val, one line per lane (rows longer than the warp's
@@ -266,6 +267,15 @@ __device__ __forceinline__ void drop_row_any(int64_t i, const RowHead& h, bool v
         else
             drop_row<T, V, LPR, CH, VW, WIN, true, false>(i, h, valid, sub, col, d16, val, bval, ival, x, delta,
                                                          lambda, w, ss, ws);
+    } else if constexpr (WIN && LPR == 32 && VW == 1 && CH > kShortSteps) {
+        // rows of at most kShortSteps x 32 entries take a body with fewer register steps:
+        // with the block's deepest body a short row would issue its empty steps predicated off
+        if (h.p1 - h.p0 <= (int64_t)kShortSteps * 32)
+            drop_row<T, V, LPR, kShortSteps, VW, WIN, false>(i, h, valid, sub, col, d16, val, bval, ival, x, delta,
+                                                            lambda, w, ss, ws);
+        else
+            drop_row<T, V, LPR, CH, VW, WIN, false>(i, h, valid, sub, col, d16, val, bval, ival, x, delta, lambda, w,
+                                                    ss, ws);
     } else {
         drop_row<T, V, LPR, CH, VW, WIN, false>(i, h, valid, sub, col, d16, val, bval, ival, x, delta, lambda, w,
                                                 ss, ws);
