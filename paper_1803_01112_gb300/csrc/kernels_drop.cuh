@@ -264,6 +264,9 @@ __device__ __forceinline__ void drop_row_any(int64_t i, const RowHead& h, bool v
         if (valid && __ldg(d16.rowesc + i))
             drop_row<T, V, LPR, CH, VW, WIN, true, true>(i, h, valid, sub, col, d16, val, bval, ival, x, delta,
                                                         lambda, w, ss, ws);
+        else if (WIN && LPR == 32 && CH > kShortSteps && h.p1 - h.p0 <= (int64_t)kShortSteps * 32)
+            drop_row<T, V, LPR, (CH > kShortSteps ? kShortSteps : CH), VW, WIN, true, false>(
+                i, h, valid, sub, col, d16, val, bval, ival, x, delta, lambda, w, ss, ws);
         else
             drop_row<T, V, LPR, CH, VW, WIN, true, false>(i, h, valid, sub, col, d16, val, bval, ival, x, delta,
                                                          lambda, w, ss, ws);
