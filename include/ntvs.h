@@ -59,10 +59,11 @@ extern "C" {
 /* index storage of the system on the device */
 #define NTVS_CSR32 0     /* int32 column per entry                                      */
 #define NTVS_DELTA16 1   /* 16-bit columns, packed at load time: the entries are cut into
-                            aligned chunks of 32; each chunk keeps its smallest column as an
-                            int32 base and every entry its uint16 offset from it (a chunk
-                            whose columns span more than 65535 keeps full int32 columns);
-                            2.125 bytes per entry plus escapes                              */
+                            aligned chunks of 32; each chunk keeps an int32 base and every
+                            entry its uint16 offset from it: the row's smallest column for a
+                            row whose columns span at most 65535, else the chunk's smallest
+                            column (a chunk whose columns span more than 65535 keeps full
+                            int32 columns); 2.125 bytes per entry plus escapes            */
 
 typedef struct ntvs_ctx ntvs_ctx;
 

@@ -38,7 +38,9 @@ __global__ void drop_apply_kernel(double* __restrict__ x, ImgCopies c, T* __rest
     }
 }
 
-int64_t k_window_smem_bytes(int64_t slice, int csz) { return (int64_t)window_smem_bytes(slice, (size_t)csz); }
+int64_t k_window_smem_bytes(int64_t slice, int csz, bool d16) {
+    return (int64_t)window_smem_bytes(slice, (size_t)csz, d16);
+}
 
 cudaError_t k_drop_block(const DropArgs& a, cudaStream_t s) {
     if (a.r1 <= a.r0) return cudaSuccess;

@@ -67,6 +67,12 @@ template <typename T>
 __host__ __device__ constexpr size_t stage_bytes() {
     return ((sizeof(int64_t) * (kRowStage + 1) + 15) & ~(size_t)15) + 2 * sizeof(T) * kRowStage;
 }
+// DELTA16 rows also stage their flags (1 byte) and their first chunk base (the base of a
+// narrow row), so that neither is a dependent global load at the start of a row
+template <typename T, bool D16>
+__host__ __device__ constexpr size_t stage_bytes_all() {
+    return stage_bytes<T>() + (D16 ? ((size_t)kRowStage + 4 * (size_t)kRowStage) : 0);
+}
 template <typename T>
 __device__ __forceinline__ int64_t* stage_rp() { return reinterpret_cast<int64_t*>(drop_win_smem); }
 template <typename T>
@@ -76,9 +82,16 @@ __device__ __forceinline__ T* stage_b() {
 template <typename T>
 __device__ __forceinline__ T* stage_inv() { return stage_b<T>() + kRowStage; }
 template <typename T>
-__device__ __forceinline__ unsigned char* window_base() { return drop_win_smem + stage_bytes<T>(); }
-inline size_t window_smem_bytes(int64_t slice, size_t tsize) {
-    const size_t stage = tsize == 8 ? stage_bytes<double>() : stage_bytes<float>();
+__device__ __forceinline__ uint8_t* stage_fl() { return drop_win_smem + stage_bytes<T>(); }
+template <typename T>
+__device__ __forceinline__ int32_t* stage_rb() {
+    return reinterpret_cast<int32_t*>(drop_win_smem + stage_bytes<T>() + kRowStage);
+}
+template <typename T, bool D16>
+__device__ __forceinline__ unsigned char* window_base() { return drop_win_smem + stage_bytes_all<T, D16>(); }
+inline size_t window_smem_bytes(int64_t slice, size_t tsize, bool d16) {
+    const size_t stage = tsize == 8 ? (d16 ? stage_bytes_all<double, true>() : stage_bytes_all<double, false>())
+                                    : (d16 ? stage_bytes_all<float, true>() : stage_bytes_all<float, false>());
     return stage + (size_t)((slice + 31) & ~31LL) * tsize;
 }
 
@@ -107,7 +120,7 @@ __device__ __forceinline__ int swz(int j) { return j ^ ((j >> 5) & 31); }
 // int32 fixed-point slot with a native shared-memory integer atomic when the row is
 // within the bound (rowfix), else the row's entries take the global path; FP64 compute
 // adds r * a to a double slot.  Outside the window: a global reduction.
-template <typename T, bool WIN>
+template <typename T, bool WIN, bool D16>
 __device__ __forceinline__ void scatter(T* delta, const Window& w, int32_t c, T r, T a, bool rowfix, float rq) {
     if (WIN) {
         const int rel = c - w.w0;
@@ -115,11 +128,11 @@ __device__ __forceinline__ void scatter(T* delta, const Window& w, int32_t c, T 
             if constexpr (sizeof(T) == 4) {
                 if (rowfix) {   // |rq a| < 2^22: adding 1.5 * 2^23 rounds it to the nearest integer
                     const int y = __float_as_int(fmaf(rq, (float)a, 12582912.0f)) - 0x4B400000;
-                    atomicAdd(reinterpret_cast<int*>(window_base<T>()) + swz(rel), y);
+                    atomicAdd(reinterpret_cast<int*>(window_base<T, D16>()) + swz(rel), y);
                     return;
                 }
             } else {
-                atomicAdd(reinterpret_cast<T*>(window_base<T>()) + swz(rel), r * a);
+                atomicAdd(reinterpret_cast<T*>(window_base<T, D16>()) + swz(rel), r * a);
                 return;
             }
         }
@@ -171,11 +184,13 @@ __device__ __forceinline__ int32_t d16_col(const Delta16& d, const int32_t* cbr,
     return base + o;
 }
 
-template <typename T, typename V, int LPR, int CH, int VW, bool WIN, bool D16, bool ESC = false>
+template <typename T, typename V, int LPR, int CH, int VW, bool WIN, bool D16, bool ESC = false,
+          bool NARROW = false>
 __device__ __forceinline__ void drop_row(int64_t i, const RowHead& h, bool valid, int sub,
                                          const int32_t* __restrict__ col, const Delta16& d16,
                                          const V* __restrict__ val, T bval, T ival, const T* __restrict__ x,
-                                         T* __restrict__ delta, T lambda, const Window& w, double& ss, WinScale* ws) {
+                                         T* __restrict__ delta, T lambda, const Window& w, double& ss, WinScale* ws,
+                                         int32_t rbase = 0) {
     static_assert(!D16 || VW == 1, "DELTA16 rows are read one entry per lane");
     const int64_t p0 = h.p0, p1 = h.p1;
     const int64_t pa = p0 & ~(int64_t)(VW - 1);
@@ -193,6 +208,7 @@ __device__ __forceinline__ void drop_row(int64_t i, const RowHead& h, bool valid
     // (measured 0.47 against 0.33 ms per 500k-row block).
     int32_t c[CH][VW];
     T a[CH][VW];
+    // a narrow DELTA16 row: all its chunk bases are rbase, the row's base (staged by the caller)
 #pragma unroll
     for (int u = 0; u < CH; ++u) {
         const int q = (u * LPR + sub) * VW;
@@ -208,7 +224,9 @@ __device__ __forceinline__ void drop_row(int64_t i, const RowHead& h, bool valid
                     if (q + e < lo || q + e >= hi) c[u][e] = -1;
                 }
             } else {
-                if constexpr (D16) {
+                if constexpr (D16 && NARROW) {
+                    c[u][0] = rbase + (int)__ldcs(offr + q);
+                } else if constexpr (D16) {
                     c[u][0] = d16_col<ESC>(d16, cbr, offr, q);   // with a warp per row: one base per step
                 } else {
                     c[u][0] = __ldcs(colr + q);
@@ -246,9 +264,9 @@ __device__ __forceinline__ void drop_row(int64_t i, const RowHead& h, bool valid
     for (int u = 0; u < CH; ++u)
 #pragma unroll
         for (int e = 0; e < VW; ++e)
-            if (c[u][e] >= 0) scatter<T, WIN>(delta, w, c[u][e], r, a[u][e], rowfix, rq);
+            if (c[u][e] >= 0) scatter<T, WIN, D16>(delta, w, c[u][e], r, a[u][e], rowfix, rq);
     for (int64_t p = (tail0 > p0 ? tail0 : p0) + sub; p < p1; p += LPR)
-        scatter<T, WIN>(delta, w, D16 ? d16_col<true>(d16, cbr, offr, (int)(p - pa)) : col[p], r,
+        scatter<T, WIN, D16>(delta, w, D16 ? d16_col<true>(d16, cbr, offr, (int)(p - pa)) : col[p], r,
                         (T)to_compute(val[p]), rowfix, rq);
 }
 
@@ -259,12 +277,21 @@ __device__ __forceinline__ void drop_row_any(int64_t i, const RowHead& h, bool v
                                              const int32_t* __restrict__ col, const Delta16& d16,
                                              const V* __restrict__ val, T bval, T ival, const T* __restrict__ x,
                                              T* __restrict__ delta, T lambda, const Window& w, double& ss,
-                                             WinScale* ws) {
+                                             WinScale* ws, int fl_staged = -1, int32_t rbase = 0) {
     if constexpr (D16) {
-        if (valid && __ldg(d16.rowesc + i))
+        // DELTA16 row flags: staged by the windowed kernel, else read here
+        const unsigned fl = fl_staged >= 0 ? (unsigned)fl_staged : (valid ? __ldg(d16.rowesc + i) : 0u);
+        if (fl & 1u)
             drop_row<T, V, LPR, CH, VW, WIN, true, true>(i, h, valid, sub, col, d16, val, bval, ival, x, delta,
                                                         lambda, w, ss, ws);
-        else if (WIN && LPR == 32 && CH > kShortSteps && h.p1 - h.p0 <= (int64_t)kShortSteps * 32)
+        else if (WIN && LPR == 32 && fl_staged >= 0 && (fl & 2u)) {   // narrow rows: the staged base
+            if (CH > kShortSteps && h.p1 - h.p0 <= (int64_t)kShortSteps * 32)
+                drop_row<T, V, LPR, (CH > kShortSteps ? kShortSteps : CH), VW, WIN, true, false, true>(
+                    i, h, valid, sub, col, d16, val, bval, ival, x, delta, lambda, w, ss, ws, rbase);
+            else
+                drop_row<T, V, LPR, CH, VW, WIN, true, false, true>(i, h, valid, sub, col, d16, val, bval, ival, x,
+                                                                   delta, lambda, w, ss, ws, rbase);
+        } else if (WIN && LPR == 32 && CH > kShortSteps && h.p1 - h.p0 <= (int64_t)kShortSteps * 32)
             drop_row<T, V, LPR, (CH > kShortSteps ? kShortSteps : CH), VW, WIN, true, false>(
                 i, h, valid, sub, col, d16, val, bval, ival, x, delta, lambda, w, ss, ws);
         else
@@ -370,7 +397,7 @@ drop_block_window_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __r
                          int64_t slice, const T* __restrict__ x, T* __restrict__ delta, T lambda,
                          double* resid_ss, Delta16 d16, const float* wlmax, const float* wbound, float* wobs,
                          const float* wamax) {
-    T* win = reinterpret_cast<T*>(window_base<T>());
+    T* win = reinterpret_cast<T*>(window_base<T, D16>());
     const int W = (int)slice;
     const int Wp = (W + 31) & ~31;
     __shared__ WinScale ws;
@@ -415,10 +442,15 @@ drop_block_window_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __r
             const int n = (int)min((int64_t)kRowStage, sg.r1 - c0);
             __syncthreads();   // the previous run's rows are done with the stage
             for (int j = threadIdx.x; j <= n; j += blockDim.x) {
-                stage_rp<T>()[j] = __ldg(row_ptr + c0 + j);
+                const int64_t rp = __ldg(row_ptr + c0 + j);
+                stage_rp<T>()[j] = rp;
                 if (j < n) {
                     stage_b<T>()[j] = __ldg(b + c0 + j);
                     stage_inv<T>()[j] = __ldg(inv_norm2 + c0 + j);
+                    if constexpr (D16) {
+                        stage_fl<T>()[j] = __ldg(d16.rowesc + c0 + j);
+                        stage_rb<T>()[j] = __ldg(d16.cbase + (rp >> 5) + c0 + j);   // the row's first chunk base
+                    }
                 }
             }
             __syncthreads();
@@ -431,18 +463,19 @@ drop_block_window_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __r
                         const int64_t q0 = stage_rp<T>()[kp], q1 = stage_rp<T>()[kp + 1];
                         if constexpr (D16) {
                             prefetch_row_l2(d16.off, val, q0, q1, lane);
-                            // and the row's chunk bases (slots (q0 >> 5) + row + k, one short run)
-                            if (lane == 31) asm volatile("prefetch.global.L2 [%0];" ::"l"(d16.cbase + (q0 >> 5) + c0 + kp));
+                            // and the chunk bases of a row that is not narrow (one short run)
+                            if (lane == 31 && !(stage_fl<T>()[kp] & 2))
+                                asm volatile("prefetch.global.L2 [%0];" ::"l"(d16.cbase + (q0 >> 5) + c0 + kp));
                         } else {
                             prefetch_row_l2(col, val, q0, q1, lane);
                         }
                     }
                 }
                 const RowHead h{valid ? stage_rp<T>()[k] : 0, valid ? stage_rp<T>()[k + 1] : 0};
-                drop_row_any<T, V, LPR, CH, VW, true, D16>(c0 + k, h, valid, lane % LPR, col, d16, val,
-                                                           valid ? stage_b<T>()[k] : (T)0,
-                                                           valid ? stage_inv<T>()[k] : (T)0, x, delta, lambda, w,
-                                                           ss_grp[warp][grp], &ws);
+                drop_row_any<T, V, LPR, CH, VW, true, D16>(
+                    c0 + k, h, valid, lane % LPR, col, d16, val, valid ? stage_b<T>()[k] : (T)0,
+                    valid ? stage_inv<T>()[k] : (T)0, x, delta, lambda, w, ss_grp[warp][grp], &ws,
+                    D16 ? (valid ? (int)stage_fl<T>()[k] : 0) : -1, (D16 && valid) ? stage_rb<T>()[k] : 0);
             }
         }
     }
@@ -461,7 +494,7 @@ drop_block_window_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __r
 template <typename T, typename V, int LPR, int CH, int VW, bool D16>
 cudaError_t launch_window(const DropArgs& a, cudaStream_t s) {
     auto kern = drop_block_window_kernel<T, V, LPR, CH, VW, D16>;
-    const size_t smem = window_smem_bytes(a.slice, sizeof(T));
+    const size_t smem = window_smem_bytes(a.slice, sizeof(T), D16);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<a.grid, 1024, smem, s>>>(a.row_ptr, a.col, (const V*)a.val, (const T*)a.b, (const T*)a.inv_norm2, a.segs,

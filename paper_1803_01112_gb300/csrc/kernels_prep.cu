@@ -177,14 +177,30 @@ cudaError_t k_prep_block(const int64_t* row_ptr, const int32_t* col, const void*
 }
 
 // ------------------------------------------------------------------ DELTA16 packing
-// A warp per row, chunk by chunk: the chunk's smallest and largest column decide between
-// base + 16-bit offsets and an escaped chunk of full columns.
+// A warp per row.  A row whose columns span at most 65535 is narrow: every entry keeps its
+// offset from the row's smallest column, which is the base of all of the row's chunks
+// (rowesc bit 1).  Otherwise chunk by chunk: the chunk's smallest and largest column
+// decide between base + 16-bit offsets and an escaped chunk of full columns (rowesc bit 0
+// when the row has one).
 
 __device__ __forceinline__ void chunk_range(const int32_t* __restrict__ col, int64_t p, int64_t p1, int32_t& c,
                                             int32_t& lo, int32_t& hi) {
     c = p < p1 ? col[p] : -1;
     lo = __reduce_min_sync(0xffffffffu, p < p1 ? c : 0x7fffffff);
     hi = __reduce_max_sync(0xffffffffu, c);
+}
+
+// smallest and largest column of row [p0, p1) (warp-uniform result; lo > hi for an empty row)
+__device__ __forceinline__ void row_range(const int32_t* __restrict__ col, int64_t p0, int64_t p1, int lane,
+                                          int32_t& lo, int32_t& hi) {
+    lo = 0x7fffffff;
+    hi = -1;
+    for (int64_t pc = p0; pc < p1; pc += 32) {
+        int32_t c, l, h;
+        chunk_range(col, pc + lane, p1, c, l, h);
+        lo = min(lo, l);
+        hi = max(hi, h);
+    }
 }
 
 __global__ void delta16_count_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int64_t M,
@@ -194,6 +210,9 @@ __global__ void delta16_count_kernel(const int64_t* __restrict__ row_ptr, const 
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < M;
          i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         const int64_t p0 = row_ptr[i], p1 = row_ptr[i + 1];
+        int32_t rlo, rhi;
+        row_range(col, p0, p1, lane, rlo, rhi);
+        if ((int64_t)rhi - (int64_t)rlo <= 65535) continue;   // narrow: no escaped chunk
         for (int64_t pc = p0; pc < p1; pc += 32) {
             int32_t c, lo, hi;
             chunk_range(col, pc + lane, p1, c, lo, hi);
@@ -211,6 +230,17 @@ __global__ void delta16_fill_kernel(const int64_t* __restrict__ row_ptr, const i
          i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         const int64_t p0 = row_ptr[i], p1 = row_ptr[i + 1];
         int32_t* cb = cbase + (p0 >> 5) + i;
+        int32_t rlo, rhi;
+        row_range(col, p0, p1, lane, rlo, rhi);
+        if ((int64_t)rhi - (int64_t)rlo <= 65535) {   // narrow row: one base for all of its chunks
+            for (int64_t pc = p0, k = 0; pc < p1; pc += 32, ++k) {
+                const int64_t p = pc + lane;
+                if (p < p1) off[p] = (uint16_t)(col[p] - rlo);
+                if (lane == 0) cb[k] = rlo;
+            }
+            if (lane == 0) rowesc[i] = 2;
+            continue;
+        }
         bool any = false;
         for (int64_t pc = p0, k = 0; pc < p1; pc += 32, ++k) {
             const int64_t p = pc + lane;

@@ -709,7 +709,7 @@ static int plan_schedule(ntvs_ctx* c, int requested) {
     int optin = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     // the window and the row stage plus the kernel's static shared memory (reductions)
-    const int64_t need = k_window_smem_bytes(slice, c->csz()) + 9 * 1024;
+    const int64_t need = k_window_smem_bytes(slice, c->csz(), c->storage == NTVS_DELTA16) + 9 * 1024;
     if (need > optin) {
         if (requested == NTVS_SCHED_WINDOW || requested == NTVS_SCHED_PIPELINE)
             return fail(NTVS_ERR_ARG, "windowed schedule: an nx*ny slice needs " + std::to_string(need) +

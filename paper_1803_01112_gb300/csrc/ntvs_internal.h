@@ -94,8 +94,10 @@ cudaError_t k_inv_counts(const int32_t* cnt, void* inv_s, int cdt, int64_t n, cu
 // slot, since a row of n entries has at most n/32 + 1 chunks) and stores base cbase[slot] =
 // its smallest column, every entry the 16-bit offset off[p] = col[p] - base.  A chunk whose
 // columns span more than 65535 is escaped: cbase[slot] = -1 - e and its columns are
-// exc[32 e + (p - p0 - 32k)].  rowesc[i] = 1 when row i has an escaped chunk: only those
-// rows pay for the check; the others decode every column with one add.
+// exc[32 e + (p - p0 - 32k)].  rowesc[i] bit 0: row i has an escaped chunk (only those rows
+// pay for the check; the others decode every column with one add); bit 1: row i is narrow
+// (its columns span at most 65535: every chunk base is the row's smallest column, so the
+// windowed kernel loads the base once per row).
 struct Delta16 {
     const uint16_t* off;      // [nnz]
     const int32_t* cbase;     // [(nnz >> 5) + M + 1]
@@ -175,7 +177,7 @@ struct DropArgs {
     int64_t max_row;      // longest row of the block (register steps of the windowed kernel)
 };
 // dynamic shared memory of the windowed DROP kernel for a slice of `slice` voxels
-int64_t k_window_smem_bytes(int64_t slice, int csz);
+int64_t k_window_smem_bytes(int64_t slice, int csz, bool d16);
 cudaError_t k_drop_block(const DropArgs& a, cudaStream_t s);
 cudaError_t k_drop_block_d16(const DropArgs& a, cudaStream_t s);   // the same on DELTA16 storage
 // out[i] = <a_i, x> for the M rows (x: compute type, in the order of the stored columns;

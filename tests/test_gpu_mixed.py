@@ -67,10 +67,10 @@ def test_delta16_with_many_escaped_jumps():
 
 @pytest.mark.parametrize("schedule", ["plain", "window", "pipeline"])
 def test_delta16_chunks_mix_packed_and_escaped(schedule):
-    """Rows of slowly varying columns with rare far jumps: most 32-entry chunks of a row are
-    stored as base + 16-bit offsets, the chunks holding a jump as full columns.  The count of
-    escaped chunks follows the format's definition exactly, and every schedule gives the
-    oracle's sweep."""
+    """Rows of slowly varying columns with rare far jumps: rows without a jump are narrow (one
+    base), in the others most 32-entry chunks are stored as base + 16-bit offsets and the
+    chunks holding a jump as full columns.  The count of escaped chunks follows the
+    format's definition exactly, and every schedule gives the oracle's sweep."""
     ntvs = ntvs_module()
     from paper_1803_01112_gb300._ffi import NTVS_DELTA16, NTVS_SCHED_PIPELINE, NTVS_SCHED_PLAIN, NTVS_SCHED_WINDOW
     sched = {"plain": NTVS_SCHED_PLAIN, "window": NTVS_SCHED_WINDOW, "pipeline": NTVS_SCHED_PIPELINE}[schedule]
@@ -92,10 +92,14 @@ def test_delta16_chunks_mix_packed_and_escaped(schedule):
     val = rng.uniform(0.1, 1.0, size=col.size)
     b = rng.uniform(5, 40, size=M)
     x0 = rng.uniform(0.5, 1.5, size=V)
-    # chunks of 32 entries from each row's first entry; escaped when their columns span > 65535
-    spans = [np.ptp(c[k:k + 32]) for c in cols for k in range(0, len(c), 32)]
+    # a row whose columns span at most 65535 is narrow (one base, no escape); in the other
+    # rows, chunks of 32 entries from the row's first entry are escaped when their columns
+    # span more than 65535
+    spans = [np.ptp(c[k:k + 32]) for c in cols if np.ptp(c) > 65535 for k in range(0, len(c), 32)]
     want_esc = int(sum(sp > 65535 for sp in spans))
-    n_chunks = len(spans)
+    n_chunks = sum((len(c) + 31) // 32 for c in cols)
+    n_narrow = sum(np.ptp(c) <= 65535 for c in cols)
+    assert 0 < n_narrow < M   # both kinds of rows occur
     r = ntvs.Reconstructor(0)
     try:
         r.set_voxel_tile(1, 1)
