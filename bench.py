@@ -400,7 +400,8 @@ def run_batched_variant(args, ntvs, local, stream, world, device):
                 "schedule": {"rows_per_item": bst["rows_per_item"], "window_floats": bst["window_floats"],
                              "ctas": bst["ctas"], "ctas_per_sm": bst["ctas_per_sm"],
                              "lanes_per_row": [bst["lanes_per_row_min"], bst["lanes_per_row"]],
-                             "tuning_ms": [[r, w, c, round(ms, 3)] for r, w, c, ms in tuning]},
+                             "lanes_per_row_all": bst["lanes_per_row_all"],
+                             "tuning_ms": [[r, w, c, l, round(ms, 3)] for r, w, c, l, ms in tuning]},
                 "tries_per_step": sum(m["n_tries"] for m in mems) / max(sum(m["n_steps"] for m in mems), 1),
                 "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                              "algorithmic_bytes_per_cycle": cyc_bytes, "peak_source": peak_src,

@@ -448,7 +448,8 @@ typedef struct {
     int32_t ctas;               /* CTAs of the persistent kernel                          */
     int32_t lanes_per_row_min;  /* smallest DROP lanes per row of any member              */
     int32_t ctas_per_sm;        /* register fit of the persistent kernel (3 or 4 CTAs/SM) */
-    int32_t reserved;
+    int32_t lanes_per_row_all;  /* lanes per row of every member picked by the tuning, 0:
+                                   each member's own (from its mean row length)             */
 } ntvs_batch_stats;
 
 /* Test hook of the batch (ntvs_batch_set_fault_hook): member 0 never leaves its first
@@ -479,8 +480,10 @@ int ntvs_batch_set_schedule(ntvs_batch* bt, int rows_per_item, int window_floats
 int ntvs_batch_set_fault_hook(ntvs_batch* bt, int64_t wait_ns, int flags);
 /* Lay out the work tables, pick the schedule (ntvs_batch_set_schedule, or by timing one
  * cycle of each candidate: rows per item {256, 512, 1024} x window {0, 8192, 16384} x
- * {3, 4} CTAs per SM, with the images restored afterwards) and capture the cycle graph;
- * max_cycles bounds the cycles that may be run (per-member phi history). */
+ * {3, 4} CTAs per SM, then on the best of those the rows per warp: lanes per row 32, 16
+ * or 8 for every member against each member's own; images restored afterwards) and
+ * capture the cycle graph; max_cycles bounds the cycles that may be run (per-member phi
+ * history). */
 int ntvs_batch_finalize(ntvs_batch* bt, int max_cycles);
 /* Queue k_iters cycles of every member on the batch's stream. */
 int ntvs_batch_run(ntvs_batch* bt, int k_iters);
@@ -498,8 +501,9 @@ int ntvs_batch_get_rows(ntvs_batch* bt, int index, int64_t* n_rows, int64_t* nnz
                         float* val);
 int ntvs_batch_get_stats(ntvs_batch* bt, ntvs_batch_stats* st);
 /* The schedule candidates timed at finalize: *n of them (0 when the schedule was fixed);
- * the first min(*n, cap) are written as cand[3i..3i+2] = (rows per item, window floats,
- * CTAs per SM) and ms[i] = its cycle time (ms). */
+ * the first min(*n, cap) are written as cand[4i..4i+3] = (rows per item, window floats,
+ * CTAs per SM, lanes per row of every member or 0 for each member's own) and ms[i] = its
+ * cycle time (ms). */
 int ntvs_batch_get_tuning(ntvs_batch* bt, int32_t* cand, float* ms, int cap, int* n);
 
 /* ---- allocation-free entry point --------------------------------------------------- */

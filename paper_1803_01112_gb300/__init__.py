@@ -480,14 +480,15 @@ def ntvs_batch_get_rows(bt: int, index: int):
 
 
 def ntvs_batch_get_tuning(bt: int) -> list:
-    """[(rows_per_item, window_floats, ctas_per_sm, ms_per_cycle)] timed at finalize."""
+    """[(rows_per_item, window_floats, ctas_per_sm, lanes_per_row_all, ms_per_cycle)] timed at
+    finalize (lanes_per_row_all 0: each member's own)."""
     n = ctypes.c_int()
     check(lib().ntvs_batch_get_tuning(bt, None, None, 0, ctypes.byref(n)), "ntvs_batch_get_tuning")
-    cand = np.zeros(3 * max(n.value, 1), np.int32)
+    cand = np.zeros(4 * max(n.value, 1), np.int32)
     ms = np.zeros(max(n.value, 1), np.float32)
     check(lib().ntvs_batch_get_tuning(bt, cand.ctypes.data, ms.ctypes.data, n.value, ctypes.byref(n)),
           "ntvs_batch_get_tuning")
-    return [(int(cand[3 * i]), int(cand[3 * i + 1]), int(cand[3 * i + 2]), float(ms[i])) for i in range(n.value)]
+    return [tuple(int(v) for v in cand[4 * i:4 * i + 4]) + (float(ms[i]),) for i in range(n.value)]
 
 
 def ntvs_batch_finalize(bt: int, max_cycles: int) -> None:

@@ -87,7 +87,7 @@ class ntvs_batch_stats(ctypes.Structure):
                 ("n_launches", ctypes.c_int64), ("kernels_per_cycle", ctypes.c_int64), ("total_rows", ctypes.c_int64),
                 ("total_nnz", ctypes.c_int64), ("total_voxels", ctypes.c_int64), ("rows_per_item", ctypes.c_int32),
                 ("window_floats", ctypes.c_int32), ("ctas", ctypes.c_int32), ("lanes_per_row_min", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("lanes_per_row_all", ctypes.c_int32)]
 
 
 vp, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double

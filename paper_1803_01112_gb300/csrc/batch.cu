@@ -834,6 +834,7 @@ struct ntvs_batch {
         int32_t* win = nullptr;
         int32_t* item0 = nullptr;     // [B]
         int n_drop_items = 0;
+        int lpr_own = 32;             // lanes per row from the member's mean row length
     };
     std::vector<Member> m;
     MemberDev* dmem = nullptr;
@@ -856,8 +857,10 @@ struct ntvs_batch {
     int req_rows = 0, req_win = -1;
     uint64_t wait_ns = 2000000000ull;
     int hook = 0;
-    std::vector<int32_t> tune_cand;   // (rows per item, window floats, CTAs per SM) per timed candidate
+    std::vector<int32_t> tune_cand;   // (rows per item, window floats, CTAs per SM, lanes per row) per
+                                      // timed candidate; lanes per row 0: each member's own (from its rows)
     std::vector<float> tune_ms;       // its cycle time
+    int lpr_policy = 0;               // lanes per row of every member, 0: each member's own
 };
 
 namespace {
@@ -963,6 +966,7 @@ int member_prep(ntvs_batch* bt, ntvs_batch::Member& mm, const void* x0, int x0_d
         return bfail(NTVS_ERR_CUDA, std::string("batch member preparation: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
     d.B = B;
     d.lpr = pick_lpr(M, nnz);
+    mm.lpr_own = d.lpr;
     return NTVS_OK;
 }
 
@@ -1459,7 +1463,7 @@ int ntvs_batch_finalize(ntvs_batch* bt, int max_cycles) {
                     if ((rc = device_error(bt)) != NTVS_OK) break;
                     float ms = 0.f;
                     cudaEventElapsedTime(&ms, e0, e1);
-                    bt->tune_cand.insert(bt->tune_cand.end(), {rows, cap, minb});
+                    bt->tune_cand.insert(bt->tune_cand.end(), {rows, cap, minb, 0});
                     bt->tune_ms.push_back(ms / (float)(kTrialCycles - 1));
                     if (ms < best) { best = ms; best_rows = rows; best_win = cap; best_minb = minb; }
                     if ((rc = restore()) != NTVS_OK) break;
@@ -1468,6 +1472,30 @@ int ntvs_batch_finalize(ntvs_batch* bt, int max_cycles) {
             }
             if (rc != NTVS_OK) break;
         }
+        // then the rows per warp: every member with 1 row per warp, 2 or 4 (lanes per row 32,
+        // 16, 8) against each member's own choice, on the best schedule found
+        int best_lpr = 0;
+        for (int lpr : {32, 16, 8}) {
+            if (rc != NTVS_OK) break;
+            for (auto& mm : bt->m) mm.d.lpr = lpr;
+            if ((rc = build_items(bt, best_rows, best_win)) != NTVS_OK || (rc = set_grid(best_win, best_minb)) != NTVS_OK)
+                break;
+            bt->win_cap = best_win;
+            if ((rc = launch_cycle(bt, bt->hbeta[0], false)) != NTVS_OK) break;   // warm-up
+            cudaEventRecord(e0, s);
+            for (int c = 1; c < kTrialCycles && rc == NTVS_OK; ++c) rc = launch_cycle(bt, bt->hbeta[0], false);
+            cudaEventRecord(e1, s);
+            if (rc != NTVS_OK) break;
+            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = bfail(NTVS_ERR_CUDA, "batch tuning"); break; }
+            if ((rc = device_error(bt)) != NTVS_OK) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            bt->tune_cand.insert(bt->tune_cand.end(), {best_rows, best_win, best_minb, lpr});
+            bt->tune_ms.push_back(ms / (float)(kTrialCycles - 1));
+            if (ms < best) { best = ms; best_lpr = lpr; }
+            if ((rc = restore()) != NTVS_OK) break;
+        }
+        for (auto& mm : bt->m) mm.d.lpr = mm.lpr_own;
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         if (rc == NTVS_OK) rc = restore();
@@ -1477,7 +1505,10 @@ int ntvs_batch_finalize(ntvs_batch* bt, int max_cycles) {
         bt->rows_per_item = best_rows;
         bt->win_cap = best_win;
         bt->minb = best_minb;
+        bt->lpr_policy = best_lpr;
     }
+    if (bt->lpr_policy > 0)
+        for (auto& mm : bt->m) mm.d.lpr = bt->lpr_policy;
     BTRY(build_items(bt, bt->rows_per_item, bt->win_cap));
     BTRY(set_grid(bt->win_cap, bt->minb));
     // one graph per pinned beta buffer: beta copy, cycle setup, the persistent kernel
@@ -1601,7 +1632,7 @@ int ntvs_batch_get_tuning(ntvs_batch* bt, int32_t* cand, float* ms, int cap, int
     const int k = (int)bt->tune_ms.size();
     *n = k;
     for (int i = 0; i < std::min(k, cap); ++i) {
-        for (int q = 0; q < 3; ++q) cand[3 * i + q] = bt->tune_cand[3 * (size_t)i + q];
+        for (int q = 0; q < 4; ++q) cand[4 * i + q] = bt->tune_cand[4 * (size_t)i + q];
         ms[i] = bt->tune_ms[i];
     }
     return NTVS_OK;
@@ -1628,6 +1659,7 @@ int ntvs_batch_get_stats(ntvs_batch* bt, ntvs_batch_stats* st) {
     }
     st->lanes_per_row = bt->m.empty() ? 0 : lmax;
     st->lanes_per_row_min = bt->m.empty() ? 0 : lmin;
+    st->lanes_per_row_all = bt->lpr_policy;
     return NTVS_OK;
 }
 
