@@ -50,7 +50,7 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ntvs", "reference"], default="ntvs")
     ap.add_argument("--workload", choices=["ctp404_full", "slice2d"], default="ctp404_full")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mixed", type=int, default=1, help="also time BF16 lengths + DELTA16 columns (0: skip)")
@@ -785,7 +785,8 @@ def run_ntvs(args):
         e2e = {"value": world * spec.n_hist * E2E_CYCLES / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(out.nbytes), "cycles_per_step": E2E_CYCLES,
                "seconds_per_step": t_e2e, "load_seconds": statistics.mean(x for x, _ in split),
-               "run_and_readback_seconds": statistics.mean(y for _, y in split)}
+               "run_and_readback_seconds": statistics.mean(y for _, y in split),
+               "load_seconds_each": [round(x, 4) for x, _ in split]}
 
     # ---- variants on the same workload: canonical voxel order, N = 6 and the TV-reduction
     # check (the 2 x 2 of N in {3, 6} x check off/on), FP64 arithmetic on the FP32-stored
