@@ -15,6 +15,13 @@ __device__ __forceinline__ double to_compute(double v) { return v; }
 __device__ __forceinline__ float to_compute(__half v) { return __half2float(v); }
 __device__ __forceinline__ float to_compute(__nv_bfloat16 v) { return __bfloat162float(v); }
 
+// the 16-bit value in the high half of a DELTA16 word: BF16 bits are the FP32 value's high half
+template <typename V>
+__device__ __forceinline__ float word_value(uint32_t e) {
+    if constexpr (std::is_same<V, __nv_bfloat16>::value) return __uint_as_float(e & 0xffff0000u);
+    else return __half2float(__ushort_as_half((unsigned short)(e >> 16)));
+}
+
 // fused x - s*g on the FP64 master image, spelled out so every kernel that forms a
 // perturbed voxel rounds alike
 __device__ __forceinline__ double perturbed(double x, double s, double g) { return __fma_rn(-s, g, x); }

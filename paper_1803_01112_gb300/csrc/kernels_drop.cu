@@ -69,7 +69,8 @@ cudaError_t k_drop_apply(int cdt, double* x, ImgCopies c, void* delta, const voi
 }
 
 // out_i = <a_i, x> for rows [0, M), a warp per row (x in the gather order of the stored
-// columns), for CSR32 or DELTA16 storage; accumulated in the compute type T.
+// columns), for CSR32 (packed pairs for FP32 values) or DELTA16 storage (words for 16-bit
+// values); accumulated in the compute type T.
 template <typename T, typename V, bool D16>
 __global__ void __launch_bounds__(256)
 project_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, Delta16 d16,
@@ -80,11 +81,12 @@ project_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ 
     for (int64_t i = w0; i < M; i += nw) {
         const int64_t p0 = __ldg(row_ptr + i), p1 = __ldg(row_ptr + i + 1);
         const int32_t* cbr = D16 ? d16.cbase + (p0 >> 5) + i : nullptr;
-        const uint16_t* offr = D16 ? d16.off + p0 : nullptr;
         T acc = (T)0;
         for (int64_t p = p0 + lane; p < p1; p += 32) {
-            const int32_t c = D16 ? d16_col<true>(d16, cbr, offr, (int)(p - p0)) : __ldg(col + p);
-            acc += (T)to_compute(val[p]) * __ldg(x + c);
+            int32_t c;
+            T a;
+            entry_any<T, V, D16>(col, d16, val, cbr, p, (int)(p - p0), c, a);
+            acc += a * __ldg(x + c);
         }
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) out[i] = acc;
@@ -99,6 +101,36 @@ static cudaError_t launch_project(const DropArgs& a, int64_t M, const void* x, v
     else
         project_kernel<T, V, false><<<a.grid, 256, 0, s>>>(a.row_ptr, a.col, a.d16, (const V*)a.val, M,
                                                            (const T*)x, (T*)out);
+    return cudaGetLastError();
+}
+
+// ent[p] = {col[p], bits of val[p]} for entries [0, n)
+__global__ void pack_entries_kernel(const int32_t* __restrict__ col, const float* __restrict__ val, int64_t n,
+                                    int2* __restrict__ ent) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+        ent[p] = make_int2(__ldcs(col + p), __float_as_int(__ldcs(val + p)));
+}
+
+cudaError_t k_pack_entries(const int32_t* col, const float* val, int64_t n, int32_t* ent, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t need = (n + 255) / 256;
+    const int grid = (int)(need < 4096 ? need : 4096);
+    pack_entries_kernel<<<grid, 256, 0, s>>>(col, val, n, reinterpret_cast<int2*>(ent));
+    return cudaGetLastError();
+}
+
+// word[p] = off[p] | val[p] << 16 (16-bit value bits) for entries [0, n)
+__global__ void pack_words_kernel(const uint16_t* __restrict__ off, const uint16_t* __restrict__ val, int64_t n,
+                                  uint32_t* __restrict__ word) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+        word[p] = (uint32_t)__ldcs(off + p) | ((uint32_t)__ldcs(val + p) << 16);
+}
+
+cudaError_t k_pack_words(const uint16_t* off, const uint16_t* val, int64_t n, uint32_t* word, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t need = (n + 255) / 256;
+    const int grid = (int)(need < 4096 ? need : 4096);
+    pack_words_kernel<<<grid, 256, 0, s>>>(off, val, n, word);
     return cudaGetLastError();
 }
 

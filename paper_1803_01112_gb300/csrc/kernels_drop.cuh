@@ -5,8 +5,8 @@
 //     d_i = <a_i, x>                    (CSR gather, x is L2/L1-resident)
 //     r_i = lambda (b_i - d_i) / ||a_i||^2
 //     delta_j += r_i a_ij               (scatter-add)
-//   A group of LPR lanes owns a row; each lane loads VW consecutive entries per step
-//   (16-byte column and value vectors for 4-byte values), and the row's entries stay in
+//   A group of LPR lanes owns a row; each lane loads one entry per step (FP32 values:
+//   the packed {column, value} pair, one 8-byte load), and the row's entries stay in
 //   registers between the dot product and the scatter, so the matrix streams from HBM
 //   exactly once.
 //
@@ -62,6 +62,13 @@ __device__ __forceinline__ void prefetch_row_l2(const I* col, const V* val, int6
     const int nc = (int)((c1 - c0 + 127) >> 7), nv = (int)((v1 - v0 + 127) >> 7);
     if (lane < nc) asm volatile("prefetch.global.L2 [%0];" ::"l"(c0 + ((uintptr_t)lane << 7)));
     else if (lane - nc < nv) asm volatile("prefetch.global.L2 [%0];" ::"l"(v0 + ((uintptr_t)(lane - nc) << 7)));
+}
+// the same for entries [q0, q1) of one array (packed pairs)
+template <typename E>
+__device__ __forceinline__ void prefetch_lines_l2(const E* a, int64_t q0, int64_t q1, int lane) {
+    const uintptr_t a0 = (uintptr_t)(a + q0) & ~(uintptr_t)127, a1 = (uintptr_t)(a + q1);
+    const int na = (int)((a1 - a0 + 127) >> 7);
+    if (lane < na) asm volatile("prefetch.global.L2 [%0];" ::"l"(a0 + ((uintptr_t)lane << 7)));
 }
 template <typename T>
 __host__ __device__ constexpr size_t stage_bytes() {
@@ -177,11 +184,37 @@ __device__ __forceinline__ RowHead load_head(int64_t i, bool valid, const int64_
 // start at cbr: the chunk's base plus the entry's offset, or, when the row has escaped
 // chunks (ESC), the full column of an escaped chunk.
 template <bool ESC>
-__device__ __forceinline__ int32_t d16_col(const Delta16& d, const int32_t* cbr, const uint16_t* offr, int q) {
+__device__ __forceinline__ int32_t d16_col_o(const Delta16& d, const int32_t* cbr, int o, int q) {
     const int32_t base = __ldg(cbr + (q >> 5));
-    const int o = __ldcs(offr + q);
     if constexpr (ESC) return base >= 0 ? base + o : __ldg(d.exc + ((int64_t)(-1 - base) << 5) + (q & 31));
     return base + o;
+}
+template <bool ESC>
+__device__ __forceinline__ int32_t d16_col(const Delta16& d, const int32_t* cbr, const uint16_t* offr, int q) {
+    return d16_col_o<ESC>(d, cbr, (int)__ldcs(offr + q), q);
+}
+
+// entry p of a row (q = p minus the row's aligned start) as column and value, from whichever
+// storage the kernel has: packed pairs, DELTA16 words, DELTA16 offsets with values, or int32
+// columns with values
+template <typename T, typename V, bool D16>
+__device__ __forceinline__ void entry_any(const int32_t* col, const Delta16& d16, const V* val, const int32_t* cbr,
+                                          int64_t p, int q, int32_t& c, T& a) {
+    if constexpr (packed_entries<V, D16>()) {
+        const int2 e = reinterpret_cast<const int2*>(col)[p];
+        c = e.x;
+        a = (T)__int_as_float(e.y);
+    } else if constexpr (delta16_words<V, D16>()) {
+        const uint32_t e = d16.word[p];
+        c = d16_col_o<true>(d16, cbr, (int)(e & 0xffffu), q);
+        a = (T)word_value<V>(e);
+    } else if constexpr (D16) {
+        c = d16_col_o<true>(d16, cbr, (int)d16.off[p], q);
+        a = (T)to_compute(val[p]);
+    } else {
+        c = col[p];
+        a = (T)to_compute(val[p]);
+    }
 }
 
 template <typename T, typename V, int LPR, int CH, int VW, bool WIN, bool D16, bool ESC = false,
@@ -192,15 +225,20 @@ __device__ __forceinline__ void drop_row(int64_t i, const RowHead& h, bool valid
                                          T* __restrict__ delta, T lambda, const Window& w, double& ss, WinScale* ws,
                                          int32_t rbase = 0) {
     static_assert(!D16 || VW == 1, "DELTA16 rows are read one entry per lane");
+    constexpr bool PK = packed_entries<V, D16>();   // {column, value} pairs: one 8-byte load per entry
+    constexpr bool W16 = delta16_words<V, D16>();   // DELTA16 {offset, value} words: one 4-byte load
+    static_assert(!PK || VW == 1, "packed pairs are read one entry per lane");
     const int64_t p0 = h.p0, p1 = h.p1;
     const int64_t pa = p0 & ~(int64_t)(VW - 1);
     // entries relative to the aligned start in 32 bits (the register steps cover far fewer
     // than 2^31 entries; the tail loop below runs in 64 bits)
-    const int32_t* colr = D16 ? nullptr : col + pa;
-    // DELTA16: the row's offsets and its chunk bases (slot (p0 >> 5) + i + k), in 32 bits
-    const uint16_t* offr = D16 ? d16.off + pa : nullptr;
+    const int32_t* colr = (D16 || PK) ? nullptr : col + pa;
+    const int2* entr = PK ? reinterpret_cast<const int2*>(col) + pa : nullptr;
+    // DELTA16: the row's offsets (or words) and its chunk bases (slot (p0 >> 5) + i + k), in 32 bits
+    const uint16_t* offr = (D16 && !W16) ? d16.off + pa : nullptr;
+    const uint32_t* wr = W16 ? d16.word + pa : nullptr;
     const int32_t* cbr = D16 ? d16.cbase + (pa >> 5) + i : nullptr;
-    const V* valr = val + pa;
+    const V* valr = (PK || W16) ? nullptr : val + pa;
     const int lo = (int)(p0 - pa);
     const int hi = (int)((p1 - pa) < (int64_t)0x7fffffff ? (p1 - pa) : (int64_t)0x7fffffff);
     // Every register step is predicated rather than skipped: with a branch per step the
@@ -224,14 +262,23 @@ __device__ __forceinline__ void drop_row(int64_t i, const RowHead& h, bool valid
                     if (q + e < lo || q + e >= hi) c[u][e] = -1;
                 }
             } else {
-                if constexpr (D16 && NARROW) {
+                if constexpr (W16) {
+                    const uint32_t e = __ldcs(wr + q);
+                    if constexpr (NARROW) c[u][0] = rbase + (int)(e & 0xffffu);
+                    else c[u][0] = d16_col_o<ESC>(d16, cbr, (int)(e & 0xffffu), q);
+                    a[u][0] = (T)word_value<V>(e);
+                } else if constexpr (D16 && NARROW) {
                     c[u][0] = rbase + (int)__ldcs(offr + q);
                 } else if constexpr (D16) {
                     c[u][0] = d16_col<ESC>(d16, cbr, offr, q);   // with a warp per row: one base per step
+                } else if constexpr (PK) {
+                    const int2 e = __ldcs(entr + q);
+                    c[u][0] = e.x;
+                    a[u][0] = (T)__int_as_float(e.y);
                 } else {
                     c[u][0] = __ldcs(colr + q);
                 }
-                a[u][0] = (T)to_compute(valr[q]);
+                if constexpr (!PK && !W16) a[u][0] = (T)to_compute(valr[q]);
             }
         } else {
 #pragma unroll
@@ -246,8 +293,12 @@ __device__ __forceinline__ void drop_row(int64_t i, const RowHead& h, bool valid
             if (c[u][e] >= 0) acc += a[u][e] * __ldg(x + c[u][e]);
     // entries beyond the register-held steps (long rows): scalar, re-read for the scatter
     const int64_t tail0 = pa + (int64_t)CH * LPR * VW;
-    for (int64_t p = (tail0 > p0 ? tail0 : p0) + sub; p < p1; p += LPR)
-        acc += (T)to_compute(val[p]) * __ldg(x + (D16 ? d16_col<true>(d16, cbr, offr, (int)(p - pa)) : col[p]));
+    for (int64_t p = (tail0 > p0 ? tail0 : p0) + sub; p < p1; p += LPR) {
+        int32_t cp;
+        T ap;
+        entry_any<T, V, D16>(col, d16, val, cbr, p, (int)(p - pa), cp, ap);
+        acc += ap * __ldg(x + cp);
+    }
 #pragma unroll
     for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     T res = (T)0, inv = (T)0;
@@ -265,9 +316,12 @@ __device__ __forceinline__ void drop_row(int64_t i, const RowHead& h, bool valid
 #pragma unroll
         for (int e = 0; e < VW; ++e)
             if (c[u][e] >= 0) scatter<T, WIN, D16>(delta, w, c[u][e], r, a[u][e], rowfix, rq);
-    for (int64_t p = (tail0 > p0 ? tail0 : p0) + sub; p < p1; p += LPR)
-        scatter<T, WIN, D16>(delta, w, D16 ? d16_col<true>(d16, cbr, offr, (int)(p - pa)) : col[p], r,
-                        (T)to_compute(val[p]), rowfix, rq);
+    for (int64_t p = (tail0 > p0 ? tail0 : p0) + sub; p < p1; p += LPR) {
+        int32_t cp;
+        T ap;
+        entry_any<T, V, D16>(col, d16, val, cbr, p, (int)(p - pa), cp, ap);
+        scatter<T, WIN, D16>(delta, w, cp, r, ap, rowfix, rq);
+    }
 }
 
 // One row, DELTA16 rows touching an escaped chunk through the checked body (a branch that
@@ -462,10 +516,13 @@ drop_block_window_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __r
                     if (kp < n) {
                         const int64_t q0 = stage_rp<T>()[kp], q1 = stage_rp<T>()[kp + 1];
                         if constexpr (D16) {
-                            prefetch_row_l2(d16.off, val, q0, q1, lane);
+                            if constexpr (delta16_words<V, D16>()) prefetch_lines_l2(d16.word, q0, q1, lane);
+                            else prefetch_row_l2(d16.off, val, q0, q1, lane);
                             // and the chunk bases of a row that is not narrow (one short run)
                             if (lane == 31 && !(stage_fl<T>()[kp] & 2))
                                 asm volatile("prefetch.global.L2 [%0];" ::"l"(d16.cbase + (q0 >> 5) + c0 + kp));
+                        } else if constexpr (packed_entries<V, D16>()) {
+                            prefetch_lines_l2(reinterpret_cast<const int2*>(col), q0, q1, lane);
                         } else {
                             prefetch_row_l2(col, val, q0, q1, lane);
                         }

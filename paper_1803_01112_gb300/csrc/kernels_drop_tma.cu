@@ -6,6 +6,7 @@
 // One CTA per SM.  Warp 0 is the producer: one thread walks the CTA's stage list
 // (planned at load time: runs of whole rows of one home z-slice, at most kStageRows rows
 // and S entries, start aligned to 16 bytes) and copies each stage's columns and values
+// (for FP32 values: its packed {column, value} pairs, one copy)
 // into a ring of kStages shared-memory slots with cp.async.bulk, completing on the
 // slot's "full" mbarrier.  Warps 1..31 are consumers: they walk the same stages in order,
 // each taking every 31st row, compute the row's dot product from shared memory (x
@@ -82,23 +83,46 @@ __device__ __forceinline__ void scatter_w(T* win, int W, int64_t w0, T* delta, i
     else atomicAdd(delta + c, v);
 }
 
+// entry q: int32 column + value, or a packed {column, value bits} pair (FP32 values)
+template <typename T, typename V, typename IdxT>
+__device__ __forceinline__ void entry_at(const IdxT* cs, const V* vs, int q, int32_t& c, T& a) {
+    if constexpr (std::is_same<IdxT, int2>::value) {
+        const int2 e = cs[q];
+        c = e.x;
+        a = (T)__int_as_float(e.y);
+    } else {
+        c = cs[q];
+        a = (T)to_compute(vs[q]);
+    }
+}
+
 // one row of a stage: entries [o0, o1) of the stage buffers (or of global memory)
-template <typename T, typename V>
-__device__ __forceinline__ void pipe_row(const int32_t* cs, const V* vs, int o0, int o1, int64_t i, const T* b,
+template <typename T, typename V, typename IdxT>
+__device__ __forceinline__ void pipe_row(const IdxT* cs, const V* vs, int o0, int o1, int64_t i, const T* b,
                                          const T* inv_norm2, const T* x, T* win, int W, int64_t w0, T* delta, T lambda,
                                          double& ss) {
     const int lane = threadIdx.x & 31;
     const T bi = __ldg(b + i), ni = __ldg(inv_norm2 + i);
     T acc = (T)0;
 #pragma unroll 4
-    for (int q = o0 + lane; q < o1; q += 32) acc += (T)to_compute(vs[q]) * __ldg(x + cs[q]);
+    for (int q = o0 + lane; q < o1; q += 32) {
+        int32_t c;
+        T a;
+        entry_at<T, V, IdxT>(cs, vs, q, c, a);
+        acc += a * __ldg(x + c);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     const T res = bi - acc;
     const T r = lambda * res * ni;
     if (lane == 0) ss += (double)res * (double)res;
 #pragma unroll 4
-    for (int q = o0 + lane; q < o1; q += 32) scatter_w(win, W, w0, delta, cs[q], r * (T)to_compute(vs[q]));
+    for (int q = o0 + lane; q < o1; q += 32) {
+        int32_t c;
+        T a;
+        entry_at<T, V, IdxT>(cs, vs, q, c, a);
+        scatter_w(win, W, w0, delta, c, r * a);
+    }
 }
 
 // the same on DELTA16 storage: cs holds the row's 16-bit column offsets, cs[o0] being the
@@ -109,8 +133,21 @@ __device__ __forceinline__ int32_t d16_col_of(const Delta16& d, const int32_t* c
     return base >= 0 ? base + o : __ldg(d.exc + ((int64_t)(-1 - base) << 5) + (rel & 31));
 }
 
-template <typename T, typename V>
-__device__ __forceinline__ void pipe_row_d16(const uint16_t* cs, const V* vs, int o0, int o1, int64_t g0, int64_t i,
+// entry q's offset and value: a 16-bit offset with a separate value, or a DELTA16 word
+template <typename T, typename V, typename IdxT>
+__device__ __forceinline__ void offset_at(const IdxT* cs, const V* vs, int q, int& o, T& a) {
+    if constexpr (std::is_same<IdxT, uint32_t>::value) {
+        const uint32_t e = cs[q];
+        o = (int)(e & 0xffffu);
+        a = (T)word_value<V>(e);
+    } else {
+        o = cs[q];
+        a = (T)to_compute(vs[q]);
+    }
+}
+
+template <typename T, typename V, typename IdxT>
+__device__ __forceinline__ void pipe_row_d16(const IdxT* cs, const V* vs, int o0, int o1, int64_t g0, int64_t i,
                                              const Delta16& d16, const T* b, const T* inv_norm2, const T* x, T* win,
                                              int W, int64_t w0, T* delta, T lambda, double& ss) {
     const int lane = threadIdx.x & 31;
@@ -118,15 +155,24 @@ __device__ __forceinline__ void pipe_row_d16(const uint16_t* cs, const V* vs, in
     const int32_t* cbr = d16.cbase + ((g0 + o0) >> 5) + i;
     T acc = (T)0;
 #pragma unroll 4
-    for (int q = o0 + lane; q < o1; q += 32) acc += (T)to_compute(vs[q]) * __ldg(x + d16_col_of(d16, cbr, q - o0, cs[q]));
+    for (int q = o0 + lane; q < o1; q += 32) {
+        int o;
+        T a;
+        offset_at<T, V, IdxT>(cs, vs, q, o, a);
+        acc += a * __ldg(x + d16_col_of(d16, cbr, q - o0, o));
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     const T res = bi - acc;
     const T r = lambda * res * ni;
     if (lane == 0) ss += (double)res * (double)res;
 #pragma unroll 4
-    for (int q = o0 + lane; q < o1; q += 32)
-        scatter_w(win, W, w0, delta, d16_col_of(d16, cbr, q - o0, cs[q]), r * (T)to_compute(vs[q]));
+    for (int q = o0 + lane; q < o1; q += 32) {
+        int o;
+        T a;
+        offset_at<T, V, IdxT>(cs, vs, q, o, a);
+        scatter_w(win, W, w0, delta, d16_col_of(d16, cbr, q - o0, o), r * a);
+    }
 }
 
 template <typename T>
@@ -147,16 +193,19 @@ drop_pipe_kernel(const int64_t* __restrict__ row_ptr, const IdxT* __restrict__ c
                  const int32_t* __restrict__ stage_begin, int64_t slice, int S, const T* __restrict__ x,
                  T* __restrict__ delta, T lambda, double* resid_ss, int* err, uint64_t wait_ns, int starve,
                  Delta16 d16) {
-    constexpr bool kD16 = sizeof(IdxT) == 2;
+    constexpr bool kW = std::is_same<IdxT, uint32_t>::value;   // DELTA16 words
+    constexpr bool kD16 = sizeof(IdxT) == 2 || kW;
+    constexpr bool kPk = std::is_same<IdxT, int2>::value;      // packed pairs
+    constexpr bool kNoVal = kPk || kW;                         // values inside the index ring
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int W = (int)slice;
     const int Wp = (W + 31) & ~31;
-    // layout: window | ring of columns | ring of values | 2 x kDescBatch descriptors | mbarriers
+    // layout: window | ring of columns (or pairs) | ring of values | 2 x kDescBatch descriptors | mbarriers
     T* win = reinterpret_cast<T*>(smem_raw);
     IdxT* ring_c = reinterpret_cast<IdxT*>(smem_raw + (size_t)Wp * sizeof(T));
     V* ring_v = reinterpret_cast<V*>(reinterpret_cast<unsigned char*>(ring_c) + (size_t)kStages * S * sizeof(IdxT));
     DropStage* desc = reinterpret_cast<DropStage*>(reinterpret_cast<unsigned char*>(ring_v) +
-                                                   (size_t)kStages * S * sizeof(V));
+                                                   (kNoVal ? (size_t)0 : (size_t)kStages * S * sizeof(V)));
     uint64_t* bars = reinterpret_cast<uint64_t*>(desc + 2 * kDescBatch);
     uint64_t* full = bars;
     uint64_t* empty = bars + kStages;
@@ -211,10 +260,10 @@ drop_pipe_kernel(const int64_t* __restrict__ row_ptr, const IdxT* __restrict__ c
                     // test hook: stage 0 is withheld, so every wait on it runs out
                 } else if (st.nent > 0) {
                     const uint32_t bc = (uint32_t)st.nent * (uint32_t)sizeof(IdxT);
-                    const uint32_t bv = (uint32_t)st.nent * (uint32_t)sizeof(V);
+                    const uint32_t bv = kNoVal ? 0u : (uint32_t)st.nent * (uint32_t)sizeof(V);
                     mbar_arrive_expect_tx(full + slot, bc + bv);
                     bulk_g2s(ring_c + (size_t)slot * S, col + st.e0, bc, full + slot);
-                    bulk_g2s(ring_v + (size_t)slot * S, val + st.e0, bv, full + slot);
+                    if (!kNoVal) bulk_g2s(ring_v + (size_t)slot * S, val + st.e0, bv, full + slot);
                 } else {
                     mbar_arrive(full + slot);   // rows read straight from global memory
                 }
@@ -269,21 +318,22 @@ drop_pipe_kernel(const int64_t* __restrict__ row_ptr, const IdxT* __restrict__ c
             const int64_t i = r0 + j;
             if constexpr (kD16) {
                 if (nent > 0) {
-                    pipe_row_d16<T, V>(ring_c + (size_t)slot * S, ring_v + (size_t)slot * S, st.off[j], st.off[j + 1],
-                                       st.e0, i, d16, b, inv_norm2, x, win, W, w0, delta, lambda, ss);
+                    pipe_row_d16<T, V, IdxT>(ring_c + (size_t)slot * S, kNoVal ? nullptr : ring_v + (size_t)slot * S,
+                                             st.off[j], st.off[j + 1], st.e0, i, d16, b, inv_norm2, x, win, W, w0,
+                                             delta, lambda, ss);
                 } else {
                     const int64_t p0 = row_ptr[i], p1 = row_ptr[i + 1];
-                    pipe_row_d16<T, V>(col + p0, val + p0, 0, (int)(p1 - p0), p0, i, d16, b, inv_norm2, x, win, W,
-                                       w0, delta, lambda, ss);
+                    pipe_row_d16<T, V, IdxT>(col + p0, kNoVal ? nullptr : val + p0, 0, (int)(p1 - p0), p0, i, d16, b,
+                                             inv_norm2, x, win, W, w0, delta, lambda, ss);
                 }
             } else {
                 if (nent > 0) {
-                    pipe_row<T, V>(ring_c + (size_t)slot * S, ring_v + (size_t)slot * S, st.off[j], st.off[j + 1], i,
-                                   b, inv_norm2, x, win, W, w0, delta, lambda, ss);
+                    pipe_row<T, V, IdxT>(ring_c + (size_t)slot * S, kPk ? nullptr : ring_v + (size_t)slot * S,
+                                         st.off[j], st.off[j + 1], i, b, inv_norm2, x, win, W, w0, delta, lambda, ss);
                 } else {
                     const int64_t p0 = row_ptr[i], p1 = row_ptr[i + 1];
-                    pipe_row<T, V>(col + p0, val + p0, 0, (int)(p1 - p0), i, b, inv_norm2, x, win, W, w0, delta,
-                                   lambda, ss);
+                    pipe_row<T, V, IdxT>(col + p0, kPk ? nullptr : val + p0, 0, (int)(p1 - p0), i, b, inv_norm2, x,
+                                         win, W, w0, delta, lambda, ss);
                 }
             }
             next += kConsumers;
@@ -302,27 +352,30 @@ drop_pipe_kernel(const int64_t* __restrict__ row_ptr, const IdxT* __restrict__ c
 
 }  // namespace
 
-int pipe_stage_entries(int vdt, int idx_bytes) {
+int pipe_stage_entries(int ring_bytes) {
     // ring of kStages slots, 64 KB in total, slot length a multiple of 8 entries
-    const int per = idx_bytes + (int)dt_size(vdt);
+    const int per = ring_bytes;
     return ((65536 / (kStages * per)) / 8) * 8;
 }
 
-size_t pipe_smem_bytes(int cdt, int vdt, int idx_bytes, int64_t slice) {
+size_t pipe_smem_bytes(int cdt, int ring_bytes, int64_t slice) {
     const size_t Wp = (size_t)((slice + 31) & ~31LL);
-    const size_t S = (size_t)pipe_stage_entries(vdt, idx_bytes);
-    return Wp * dt_size(cdt) + kStages * S * (idx_bytes + dt_size(vdt)) + 2 * kDescBatch * sizeof(DropStage) +
+    const size_t S = (size_t)pipe_stage_entries(ring_bytes);
+    return Wp * dt_size(cdt) + kStages * S * (size_t)ring_bytes + 2 * kDescBatch * sizeof(DropStage) +
            (2 * kStages + 3) * sizeof(uint64_t);
 }
 
 template <typename T, typename V, typename IdxT>
 static cudaError_t launch_pipe_idx(const DropPipeArgs& a, const IdxT* col, cudaStream_t s) {
     auto kern = drop_pipe_kernel<T, V, IdxT>;
-    const size_t smem = pipe_smem_bytes(a.cdt, a.vdt, (int)sizeof(IdxT), a.slice);
+    // bytes per entry in the rings: the pairs and the words carry their values
+    constexpr int ring_bytes = (std::is_same<IdxT, int2>::value || std::is_same<IdxT, uint32_t>::value)
+                                   ? (int)sizeof(IdxT) : (int)(sizeof(IdxT) + sizeof(V));
+    const size_t smem = pipe_smem_bytes(a.cdt, ring_bytes, a.slice);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<a.grid, kThreads, smem, s>>>(a.row_ptr, col, (const V*)a.val, (const T*)a.b, (const T*)a.inv_norm2,
-                                         a.stages, a.stage_begin, a.slice, pipe_stage_entries(a.vdt, sizeof(IdxT)),
+                                         a.stages, a.stage_begin, a.slice, pipe_stage_entries(ring_bytes),
                                          (const T*)a.x, (T*)a.delta, (T)a.lambda, a.resid_ss, a.err, a.wait_ns,
                                          a.starve, a.d16);
     return cudaGetLastError();
@@ -330,8 +383,14 @@ static cudaError_t launch_pipe_idx(const DropPipeArgs& a, const IdxT* col, cudaS
 
 template <typename T, typename V>
 static cudaError_t launch_pipe(const DropPipeArgs& a, cudaStream_t s) {
-    if (a.use_d16) return launch_pipe_idx<T, V, uint16_t>(a, a.d16.off, s);
-    return launch_pipe_idx<T, V, int32_t>(a, a.col, s);
+    if (a.use_d16) {
+        if constexpr (delta16_words<V, true>()) return launch_pipe_idx<T, V, uint32_t>(a, a.d16.word, s);
+        else return launch_pipe_idx<T, V, uint16_t>(a, a.d16.off, s);
+    }
+    if constexpr (packed_entries<V, false>())
+        return launch_pipe_idx<T, V, int2>(a, reinterpret_cast<const int2*>(a.col), s);
+    else
+        return launch_pipe_idx<T, V, int32_t>(a, a.col, s);
 }
 
 cudaError_t k_drop_pipe(const DropPipeArgs& a, cudaStream_t s) {

@@ -95,6 +95,12 @@ struct ntvs_ctx {
     void* val = nullptr;
     void* b = nullptr;
     bool own_row_ptr = false, own_col = false, own_val = false, own_b = false;
+    // CSR32 storage with FP32 values: [nnz] {column, value bits} pairs packed at load (the
+    // DROP, projection and pipelined kernels read one 8-byte pair per entry); col and val
+    // are released once the schedule is planned
+    int32_t* ent = nullptr;
+    // the column array the DROP kernels take: the packed pairs when there are any
+    const int32_t* drop_cols() const { return ent ? ent : col; }
     void* inv_norm2 = nullptr;
     void* inv_s = nullptr;
     int lpr = 32;
@@ -115,13 +121,14 @@ struct ntvs_ctx {
     int32_t* d16base = nullptr;        // [ceil(nnz/32)] chunk bases (negative: escaped chunk)
     int32_t* d16exc = nullptr;         // [escaped chunks][32] full columns
     uint8_t* d16rowesc = nullptr;      // [M] rows touching an escaped chunk
+    uint32_t* d16word = nullptr;       // [nnz] 16-bit values: offset | value bits << 16 (replaces d16off, val)
     int64_t n_escaped = 0;             // escaped chunks
     // on-the-fly rows (ntvs_load_paths): path records and b, traced every sweep
     bool paths_mode = false;
     float* paths = nullptr;
     bool own_paths = false;
     OtfArgs otf{};
-    Delta16 d16() const { return Delta16{d16off, d16base, d16exc, d16rowesc}; }
+    Delta16 d16() const { return Delta16{d16off, d16base, d16exc, d16rowesc, d16word}; }
 
     // image and scratch: x is the FP64 master image; x32 its FP32 copy gathered by the
     // FP32-path DROP kernels (null on the FP64 path)
@@ -201,6 +208,7 @@ struct ntvs_ctx {
         if (own_b) dev_free(b);
         row_ptr = nullptr; col = nullptr; val = nullptr; b = nullptr;
         own_row_ptr = own_col = own_val = own_b = false;
+        dev_free(ent);
         dev_free(inv_norm2);
         dev_free(inv_s);
         dev_free(segs);
@@ -212,6 +220,7 @@ struct ntvs_ctx {
         dev_free(d16base);
         dev_free(d16exc);
         dev_free(d16rowesc);
+        dev_free(d16word);
         n_escaped = 0;
         if (own_paths) dev_free(paths);
         paths = nullptr;
@@ -529,7 +538,7 @@ int launch_drop_kernel(ntvs_ctx* c, int t, int64_t r0, int64_t r1, double* resid
     }
     DropArgs a;
     a.row_ptr = c->row_ptr;
-    a.col = c->col;
+    a.col = c->drop_cols();
     a.val = c->val;
     a.b = c->b;
     a.inv_norm2 = c->inv_norm2;
@@ -568,7 +577,7 @@ int launch_drop_kernel(ntvs_ctx* c, int t, int64_t r0, int64_t r1, double* resid
     if (whole && c->schedule == NTVS_SCHED_PIPELINE) {
         DropPipeArgs pa;
         pa.row_ptr = c->row_ptr;
-        pa.col = c->col;
+        pa.col = c->drop_cols();
         pa.val = c->val;
         pa.b = c->b;
         pa.inv_norm2 = c->inv_norm2;
@@ -684,12 +693,22 @@ static int pack_delta16(ntvs_ctx* c) {
     TRY(dev_alloc(&c->d16rowesc, (size_t)std::max<int64_t>(c->M, 1), "DELTA16 row flags"));
     CUDA_TRY(k_delta16_fill(c->row_ptr, c->col, c->M, c->d16off, c->d16base, c->d16exc, c->d16rowesc, ctr + 1,
                             c->stream));
+    if (dt_size(c->vdt) == 2) {   // 16-bit values: offset and value bits in one word per entry
+        TRY(dev_alloc(&c->d16word, sizeof(uint32_t) * (size_t)std::max<int64_t>(nnz, 4), "DELTA16 words"));
+        CUDA_TRY(k_pack_words(c->d16off, (const uint16_t*)c->val, nnz, c->d16word, c->stream));
+    }
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (c->own_col) {
         dev_free(c->col);
         c->own_col = false;
     }
     c->col = nullptr;
+    if (c->d16word) {
+        dev_free(c->d16off);
+        if (c->own_val) dev_free(c->val);
+        c->val = nullptr;
+        c->own_val = false;
+    }
     return NTVS_OK;
 }
 
@@ -791,10 +810,15 @@ static int plan_schedule(ntvs_ctx* c, int requested) {
 
     // pipelined schedule: cut every segment into ring-slot stages of whole rows
     const bool d16 = c->storage == NTVS_DELTA16;
-    const int idx_bytes = d16 ? 2 : 4;
-    // DELTA16 columns are packed into a buffer of our own (aligned); the int32 ones may be borrowed
-    const bool aligned = (d16 || (uintptr_t)c->col % 16 == 0) && ((uintptr_t)c->val % 16 == 0);
-    const bool pipe_fits = (int64_t)pipe_smem_bytes(c->cdt, c->vdt, idx_bytes, slice) + 1024 <= optin;
+    const int64_t vsz = (int64_t)dt_size(c->vdt);
+    // one array per entry (packed pairs, DELTA16 words) or an index array beside the values
+    const bool packed = !d16 && c->vdt == F32, words = d16 && vsz == 2;
+    const int64_t idx_bytes = packed ? 8 : words ? 4 : d16 ? 2 : 4;
+    const int ring_bytes = (int)((packed || words) ? idx_bytes : idx_bytes + vsz);
+    // DELTA16 columns, words and packed pairs are buffers of our own (aligned); the int32
+    // columns and the values may be borrowed
+    const bool aligned = packed || words || ((d16 || (uintptr_t)c->col % 16 == 0) && ((uintptr_t)c->val % 16 == 0));
+    const bool pipe_fits = (int64_t)pipe_smem_bytes(c->cdt, ring_bytes, slice) + 1024 <= optin;
     // AUTO takes the windowed kernel (measured faster than the pipelined one on the
     // 200x200x16 workload); the pipelined one only on request
     const bool want_pipe = requested == NTVS_SCHED_PIPELINE;
@@ -808,10 +832,10 @@ static int plan_schedule(ntvs_ctx* c, int requested) {
         CUDA_TRY(cudaMemcpyAsync(rp.data(), c->row_ptr, sizeof(int64_t) * rp.size(), cudaMemcpyDeviceToHost,
                                  c->stream));
         CUDA_TRY(cudaStreamSynchronize(c->stream));
-        const int64_t S = pipe_stage_entries(c->vdt, idx_bytes);
+        const int64_t S = pipe_stage_entries(ring_bytes);
         const int64_t nnz_all = rp[c->M];
-        // entries per 16 bytes of both the column and the value arrays
-        const int64_t A = 16 / std::min<int64_t>(idx_bytes, (int64_t)dt_size(c->vdt));
+        // entries per 16 bytes of the single array, or of both the index and the value arrays
+        const int64_t A = (packed || words) ? 16 / idx_bytes : 16 / std::min<int64_t>(idx_bytes, vsz);
         auto down = [&](int64_t e) { return (e / A) * A; };
         auto up = [&](int64_t e) { return ((e + A - 1) / A) * A; };
         std::vector<DropStage> stages;
@@ -1140,6 +1164,10 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
         CUDA_TRY(cudaMemsetAsync(c->wstat, 0, sizeof(float) * 5 * (size_t)c->B, st));
         TRY(dev_alloc(&colsum, sizeof(float) * (size_t)VI, "column sums"));
     }
+    // CSR32 storage with FP32 values: every block's entries are packed into {column, value}
+    // pairs once they are validated and remapped (during the copy of the later blocks)
+    if (c->storage == NTVS_CSR32 && c->vdt == F32)
+        TRY(dev_alloc(&c->ent, sizeof(int32_t) * 2 * (size_t)std::max<int64_t>(nnz, 1), "packed entries"));
     for (int t = 0; t < c->B; ++t) {
         if (piped) {
             CUDA_TRY(cudaStreamWaitEvent(st, arrived[2 * t], 0));
@@ -1151,7 +1179,11 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
                               cnt + (size_t)t * VI, c->dflags, colsum, colsum ? c->wstat + 3 * c->B + 2 * t : nullptr,
                               st));
         if (colsum) CUDA_TRY(k_colmax(colsum, VI, c->wstat + t, st));
+        if (c->ent && piped)
+            CUDA_TRY(k_pack_entries(c->col + eb[t], (const float*)c->val + eb[t], eb[t + 1] - eb[t], c->ent + 2 * eb[t],
+                                    st));
     }
+    if (c->ent && !piped) CUDA_TRY(k_pack_entries(c->col, (const float*)c->val, nnz, c->ent, st));
     {   // longest row of every block
         unsigned long long* dm = nullptr;
         TRY(dev_alloc(&dm, sizeof(unsigned long long) * (size_t)c->B, "row lengths"));
@@ -1215,6 +1247,14 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
     c->vector4 = false;
     TRY(plan_schedule(c, s->schedule));
     if (c->storage == NTVS_DELTA16) TRY(pack_delta16(c));
+    if (c->ent) {   // the pairs replace the column and value arrays (which the planning read)
+        CUDA_TRY(cudaStreamSynchronize(st));
+        if (c->own_col) dev_free(c->col);
+        if (c->own_val) dev_free(c->val);
+        c->col = nullptr;
+        c->val = nullptr;
+        c->own_col = c->own_val = false;
+    }
     {
         const int64_t need = (V + 255) / 256;
         c->apply_grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)c->sms * 8));
@@ -1766,7 +1806,7 @@ int ntvs_forward_project(ntvs_ctx* c, const void* x, int x_dtype, int x_mem, voi
         DropArgs a;
         std::memset(&a, 0, sizeof(a));
         a.row_ptr = c->row_ptr;
-        a.col = c->col;
+        a.col = c->drop_cols();
         a.val = c->val;
         a.vdt = c->vdt;
         a.cdt = c->cdt;

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <type_traits>
 
 namespace ntvs {
 
@@ -97,13 +98,19 @@ cudaError_t k_inv_counts(const int32_t* cnt, void* inv_s, int cdt, int64_t n, cu
 // exc[32 e + (p - p0 - 32k)].  rowesc[i] bit 0: row i has an escaped chunk (only those rows
 // pay for the check; the others decode every column with one add); bit 1: row i is narrow
 // (its columns span at most 65535: every chunk base is the row's smallest column, so the
-// windowed kernel loads the base once per row).
+// windowed kernel loads the base once per row).  With 16-bit values the offset and the
+// value's bits share one word (offset in the low half), read with one 4-byte load.
 struct Delta16 {
-    const uint16_t* off;      // [nnz]
+    const uint16_t* off;      // [nnz] (FP32/FP64 values)
     const int32_t* cbase;     // [(nnz >> 5) + M + 1]
     const int32_t* exc;       // [escaped chunks][32]
     const uint8_t* rowesc;    // [M]
+    const uint32_t* word;     // [nnz] 16-bit values: offset | value bits << 16 (off and val unused)
 };
+// DELTA16 storage with 16-bit (FP16/BF16) values keeps each entry as one 32-bit word
+template <typename V, bool D16>
+__host__ __device__ constexpr bool delta16_words() { return D16 && sizeof(V) == 2; }
+cudaError_t k_pack_words(const uint16_t* off, const uint16_t* val, int64_t n, uint32_t* word, cudaStream_t s);
 // slots of the chunk bases for nnz entries in M rows
 inline int64_t delta16_slots(int64_t nnz, int64_t M) { return (nnz >> 5) + M + 1; }
 // escaped chunks: *n_esc += their number (zeroed by the caller)
@@ -143,10 +150,19 @@ struct DropSegment {
     int32_t home, pad;
 };
 
+// CSR32 storage with FP32 values is packed at load: entry p is the pair {column, bits of
+// the value} (int2, 8 bytes), so a lane reads its entry with one load.  The DROP,
+// projection and pipelined kernels take the pair array through their column pointer and
+// leave the value pointer unused: a kernel on FP32 values without DELTA16 indices
+// (packed_entries) reads pairs.
+template <typename V, bool D16>
+__host__ __device__ constexpr bool packed_entries() { return !D16 && std::is_same<V, float>::value; }
+cudaError_t k_pack_entries(const int32_t* col, const float* val, int64_t n, int32_t* ent, cudaStream_t s);
+
 struct DropArgs {
     const int64_t* row_ptr;
-    const int32_t* col;
-    const void* val;       // storage type vdt
+    const int32_t* col;    // int32 columns, or (CSR32 with FP32 values) the packed pairs
+    const void* val;       // storage type vdt; unused with packed pairs
     const void* b;         // compute type
     const void* inv_norm2; // compute type
     int64_t r0, r1;
@@ -216,8 +232,8 @@ struct DropStage {
 };
 struct DropPipeArgs {
     const int64_t* row_ptr;
-    const int32_t* col;
-    const void* val;
+    const int32_t* col;   // int32 columns, or the packed pairs (FP32 values)
+    const void* val;      // unused with packed pairs
     const void* b;
     const void* inv_norm2;
     const DropStage* stages;
@@ -236,8 +252,11 @@ struct DropPipeArgs {
     Delta16 d16;
 };
 cudaError_t k_drop_pipe(const DropPipeArgs& a, cudaStream_t s);
-int pipe_stage_entries(int vdt, int idx_bytes);                             // entries per ring slot
-size_t pipe_smem_bytes(int cdt, int vdt, int idx_bytes, int64_t slice);     // dynamic shared memory
+// entries per ring slot and dynamic shared memory, for ring_bytes bytes per entry: the
+// index plus the value (int32 columns or DELTA16 offsets with separate values), or the
+// single 8-byte pair or 4-byte DELTA16 word
+int pipe_stage_entries(int ring_bytes);
+size_t pipe_smem_bytes(int cdt, int ring_bytes, int64_t slice);
 
 // ------------------------------------------------------------------ on-the-fly rows
 struct OtfArgs {
