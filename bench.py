@@ -782,11 +782,31 @@ def run_ntvs(args):
             times.append(max_over_ranks(t1 - t0, world, device))
             split.append((t_l - t0, t1 - t_l))
         t_e2e = statistics.mean(times)
+        # the floor under the load: a plain copy of the same column and value bytes from the
+        # same pinned host buffers into device memory on two streams (what the loader
+        # overlaps its device work with)
+        floor = None
+        try:
+            cs = [torch.cuda.Stream(device), torch.cuda.Stream(device)]
+            srcs = [torch.from_numpy(a.reshape(-1).view(np.uint8)) for a in (s.col, s.val)]
+            dsts = [torch.empty(t.numel(), dtype=torch.uint8, device=device) for t in srcs]
+            torch.cuda.synchronize(device)
+            t0 = time.perf_counter()
+            for k, (dst_t, src_t) in enumerate(zip(dsts, srcs)):
+                with torch.cuda.stream(cs[k]):
+                    dst_t.copy_(src_t, non_blocking=True)
+            torch.cuda.synchronize(device)
+            floor = time.perf_counter() - t0
+            del dsts
+        except RuntimeError:   # not enough device memory beside the context's
+            floor = None
+        torch.cuda.empty_cache()   # the library allocates with cudaMalloc, not from torch's cache
         e2e = {"value": world * spec.n_hist * E2E_CYCLES / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(out.nbytes), "cycles_per_step": E2E_CYCLES,
                "seconds_per_step": t_e2e, "load_seconds": statistics.mean(x for x, _ in split),
                "run_and_readback_seconds": statistics.mean(y for _, y in split),
-               "load_seconds_each": [round(x, 4) for x, _ in split]}
+               "load_seconds_each": [round(x, 4) for x, _ in split],
+               "h2d_copy_floor_seconds": floor}
 
     # ---- variants on the same workload: canonical voxel order, N = 6 and the TV-reduction
     # check (the 2 x 2 of N in {3, 6} x check off/on), FP64 arithmetic on the FP32-stored
