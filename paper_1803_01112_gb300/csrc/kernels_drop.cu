@@ -191,6 +191,38 @@ cudaError_t k_row_home(const int64_t* row_ptr, const int32_t* col, int64_t M, in
     return cudaGetLastError();
 }
 
+// A warp per chunk of rows: the chunk's work in issued register steps (k_chunk_cost); a
+// chunk of a block without a per-block depth (ch = 0) counts its rows
+__global__ void chunk_cost_kernel(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ cs,
+                                  const int8_t* __restrict__ ch, int64_t nchunks, int64_t* __restrict__ cost) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t q = w0; q < nchunks; q += nw) {
+        const int64_t r0 = cs[q], r1 = cs[q + 1];
+        const int64_t d = ch[q];
+        long long acc = 0;
+        for (int64_t i = r0 + lane; i < r1; i += 32) {
+            if (d <= 0) {
+                acc += 1;
+                continue;
+            }
+            const int64_t steps = (row_ptr[i + 1] - row_ptr[i] + 31) / 32;
+            const int64_t body = (steps <= kShortBody && d > kShortBody) ? kShortBody : d;
+            acc += 1 + body + 2 * (steps > d ? steps - d : 0);
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) cost[q] = acc;
+    }
+}
+
+cudaError_t k_chunk_cost(const int64_t* row_ptr, const int64_t* cs, const int8_t* ch, int64_t nchunks, int64_t* cost,
+                         int grid, cudaStream_t s) {
+    if (nchunks <= 0) return cudaSuccess;
+    chunk_cost_kernel<<<grid, 256, 0, s>>>(row_ptr, cs, ch, nchunks, cost);
+    return cudaGetLastError();
+}
+
 // A warp per chunk of rows [cs[q], cs[q+1]) (at most 64): the lower median (element n/2
 // of the sorted values) of the home slices of its non-empty rows, -1 when all are empty.
 // Rows i >= 1 whose home and the previous row's home are both defined and differ are

@@ -50,7 +50,7 @@ __device__ __forceinline__ void load4(const __nv_bfloat16* p, float (&o)[4]) {
 extern __shared__ __align__(16) unsigned char drop_win_smem[];
 constexpr int kRowStage = 2048;   // rows staged at once by the windowed kernel
 constexpr int kPrefetchRows = 1;  // the windowed kernel asks L2 for the entries of the row this many ahead
-constexpr int kShortSteps = 8;    // register steps of the windowed kernel's body for short rows
+constexpr int kShortSteps = kShortBody;   // register steps of the windowed kernel's body for short rows
 
 // L2 prefetch of the 128-byte lines holding entries [q0, q1) of the index array (int32
 // columns or DELTA16 offsets) and of val, one line per lane (rows longer than the warp's
@@ -576,15 +576,18 @@ template <typename T, typename V, bool D16>
 static cudaError_t dispatch(const DropArgs& a, cudaStream_t s) {
     if (a.vector4) return cudaErrorInvalidValue;   // 4-entry vector loads measured slower; not built
     // windowed FP32 compute with a warp per row: as many register steps as the block's
-    // longest row needs (8..12; longer rows finish in the tail loop), so blocks of short rows
-    // do not evaluate empty steps
+    // longest row needs (window_register_steps: 8..12; longer rows finish in the tail loop),
+    // so blocks of short rows do not evaluate empty steps; the schedule planner balances the
+    // CTAs by the same rule
     if constexpr (sizeof(T) == 4 && (std::is_same<V, float>::value || std::is_same<V, __nv_bfloat16>::value)) {
-        if (a.segs && a.lanes_per_row == 32) {
-            const int need = (int)((a.max_row + 31) / 32);
-            if (need <= 8) return launch_cfg<T, V, 32, 8, 1, D16>(a, s);
-            if (need == 9) return launch_cfg<T, V, 32, 9, 1, D16>(a, s);
-            if (need == 10) return launch_cfg<T, V, 32, 10, 1, D16>(a, s);
-            if (need == 11) return launch_cfg<T, V, 32, 11, 1, D16>(a, s);
+        if (a.segs) {
+            switch (window_register_steps(a.max_row, a.cdt, a.vdt, a.lanes_per_row)) {
+                case 8: return launch_cfg<T, V, 32, 8, 1, D16>(a, s);
+                case 9: return launch_cfg<T, V, 32, 9, 1, D16>(a, s);
+                case 10: return launch_cfg<T, V, 32, 10, 1, D16>(a, s);
+                case 11: return launch_cfg<T, V, 32, 11, 1, D16>(a, s);
+                default: break;   // 12: the fixed depth below
+            }
         }
     }
     switch (a.lanes_per_row) {

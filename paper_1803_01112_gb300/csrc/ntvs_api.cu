@@ -716,8 +716,11 @@ static int pack_delta16(ntvs_ctx* c) {
 // Each block's rows are cut into chunks of kChunkRows consecutive rows; a chunk's home
 // slice is the median of its rows' home slices (so a few rows that bend out of their
 // slice do not break a run).  Per block, chunks are ordered by home slice and dealt to the
-// win_grid CTAs in contiguous runs of about equal row count; consecutive chunks of one
-// CTA with the same home slice and adjacent rows merge into one segment.
+// win_grid CTAs in contiguous runs of about equal work; consecutive chunks of one CTA with
+// the same home slice and adjacent rows merge into one segment.  A chunk's work is counted
+// in the register steps its rows issue (k_chunk_cost): a row costs the depth of the body
+// it runs, not its entry count, since every step of a body issues whether or not it holds
+// entries (measured: the busiest SM's excess over the mean follows this count).
 constexpr int kChunkRows = 64;
 constexpr double kMinMeanRun = 8.0;
 
@@ -747,29 +750,48 @@ static int plan_schedule(ntvs_ctx* c, int requested) {
     block_chunk[c->B] = (int64_t)cstart.size();
     const int64_t nch = (int64_t)cstart.size();
     cstart.push_back(c->M);
+    // the register depth of every chunk's block body (0: rows are counted instead)
+    std::vector<int8_t> chunk_ch((size_t)std::max<int64_t>(nch, 1), 0);
+    for (int t = 0; t < c->B; ++t) {
+        const int64_t mr = t < (int)c->block_maxrow.size() ? c->block_maxrow[t] : 0;
+        const int8_t d = (int8_t)window_register_steps(mr, c->cdt, c->vdt, c->lpr);
+        for (int64_t q = block_chunk[t]; q < block_chunk[t + 1]; ++q) chunk_ch[(size_t)q] = d;
+    }
     int32_t* dhome = nullptr;
     int32_t* dchunk = nullptr;
     int64_t* dstart = nullptr;
     unsigned long long* dchanges = nullptr;
+    int8_t* dch = nullptr;
+    int64_t* dcost = nullptr;
     TRY(dev_alloc(&dhome, sizeof(int32_t) * (size_t)c->M, "row home slices"));
     TRY(dev_alloc(&dchunk, sizeof(int32_t) * (size_t)std::max<int64_t>(nch, 1), "chunk home slices"));
     TRY(dev_alloc(&dstart, sizeof(int64_t) * cstart.size(), "chunk starts"));
     TRY(dev_alloc(&dchanges, sizeof(unsigned long long), "home changes"));
+    TRY(dev_alloc(&dch, chunk_ch.size(), "chunk body depths"));
+    TRY(dev_alloc(&dcost, sizeof(int64_t) * (size_t)std::max<int64_t>(nch, 1), "chunk costs"));
     std::vector<int32_t> chome((size_t)nch);
+    std::vector<int64_t> ccost((size_t)nch);
     unsigned long long changes = 0;
     cudaError_t e = cudaMemcpyAsync(dstart, cstart.data(), sizeof(int64_t) * cstart.size(), cudaMemcpyHostToDevice,
                                     c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dch, chunk_ch.data(), chunk_ch.size(), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(dchanges, 0, sizeof(unsigned long long), c->stream);
     if (e == cudaSuccess) e = k_row_home(c->row_ptr, c->col, c->M, slice, dhome, c->sms * 8, c->stream);
     if (e == cudaSuccess) e = k_chunk_home(dhome, dstart, nch, dchunk, dchanges, c->sms * 8, c->stream);
+    if (e == cudaSuccess) e = k_chunk_cost(c->row_ptr, dstart, dch, nch, dcost, c->sms * 8, c->stream);
     if (e == cudaSuccess && nch > 0)
         e = cudaMemcpyAsync(chome.data(), dchunk, sizeof(int32_t) * (size_t)nch, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && nch > 0)
+        e = cudaMemcpyAsync(ccost.data(), dcost, sizeof(int64_t) * (size_t)nch, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&changes, dchanges, sizeof(changes), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     dev_free(dhome);
     dev_free(dchunk);
     dev_free(dstart);
     dev_free(dchanges);
+    dev_free(dch);
+    dev_free(dcost);
     if (e != cudaSuccess) return fail(NTVS_ERR_CUDA, cuda_msg("row home slices", e));
     int32_t last = 0;
     for (auto& h : chome) {   // chunks of empty rows join their predecessor's run
@@ -781,17 +803,20 @@ static int plan_schedule(ntvs_ctx* c, int requested) {
     if (requested == NTVS_SCHED_AUTO && mean_run < kMinMeanRun) return NTVS_OK;
 
     const int G = c->sms;
-    struct Chunk { int64_t r0, r1; int32_t home; };
+    struct Chunk { int64_t r0, r1; int32_t home; int64_t cost; };
     std::vector<DropSegment> segs;
     std::vector<int32_t> begin((size_t)c->B * (G + 1), 0);
     std::vector<Chunk> ch;
     for (int t = 0; t < c->B; ++t) {
-        const int64_t r0 = c->block_ptr[t], r1 = c->block_ptr[t + 1];
         ch.clear();
-        for (int64_t q = block_chunk[t]; q < block_chunk[t + 1]; ++q) ch.push_back({cstart[q], cstart[q + 1], chome[q]});
+        int64_t total = 0;   // the block's work (a chunk costs at least one unit per row)
+        for (int64_t q = block_chunk[t]; q < block_chunk[t + 1]; ++q) {
+            const int64_t w = std::max<int64_t>(ccost[(size_t)q], cstart[q + 1] - cstart[q]);
+            ch.push_back({cstart[q], cstart[q + 1], chome[q], w});
+            total += w;
+        }
         std::stable_sort(ch.begin(), ch.end(), [](const Chunk& a, const Chunk& b) { return a.home < b.home; });
         int32_t* bg = begin.data() + (size_t)t * (G + 1);
-        const int64_t total = r1 - r0;
         int cta = 0;
         bg[0] = (int32_t)segs.size();
         int64_t cum = 0;
@@ -801,7 +826,7 @@ static int plan_schedule(ntvs_ctx* c, int requested) {
             const bool own_last = (int64_t)segs.size() > bg[cta];
             if (own_last && segs.back().home == k.home && segs.back().r1 == k.r0) segs.back().r1 = k.r1;
             else segs.push_back({k.r0, k.r1, k.home, 0});
-            cum += k.r1 - k.r0;
+            cum += k.cost;
         }
         while (cta < G) bg[++cta] = (int32_t)segs.size();
     }
