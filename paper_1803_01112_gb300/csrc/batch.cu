@@ -31,7 +31,8 @@
 //
 // DROP items process rows with LPR lanes per row (8, 16 or 32, per member from its row
 // length) holding the row's first CH*LPR entries in registers between the dot product
-// and the scatter.  The scatter either goes to global memory (FP32 reductions) or is staged
+// and the scatter; a member's entries are stored as {column, value} pairs, one 8-byte
+// load each.  The scatter either goes to global memory (FP32 reductions) or is staged
 // in a shared window of the CTA (the item's whole column range when it fits, else the
 // range centred on its mean column, whose outside entries still go to global memory),
 // flushed once per item: only the window's nonzero entries become global reductions.
@@ -61,8 +62,9 @@ enum : int { PH_GRAD = 0, PH_TRY = 1, PH_APPLY = 2, PH_DROP = 3, PH_DAPPLY = 4, 
 // Read-only description of one member (pointers owned by the batch).
 struct MemberDev {
     const int64_t* row_ptr;
-    const int32_t* col;        // internal voxel order
+    const int32_t* col;        // internal voxel order (until the member is prepared)
     const float* val;
+    const int2* ent;           // [nnz] {column, value bits}: the prepared member's entries
     const float* b;
     const float* inv_norm2;
     const float* inv_s;        // [B][vint], internal voxel order
@@ -309,15 +311,24 @@ __device__ void drop_rows(const MemberDev& m, int64_t i0, int64_t i1, int w0, in
 #pragma unroll
         for (int u = 0; u < CH; ++u) {
             const int64_t q = p0 + (int64_t)u * LPR + sub;
-            if (q < p1) { c[u] = __ldcs(m.col + q); a[u] = __ldcs(m.val + q); }
-            else { c[u] = -1; a[u] = 0.f; }
+            if (q < p1) {
+                const int2 e = __ldcs(m.ent + q);   // one 8-byte load per entry
+                c[u] = e.x;
+                a[u] = __int_as_float(e.y);
+            } else {
+                c[u] = -1;
+                a[u] = 0.f;
+            }
         }
         float acc = 0.f;
 #pragma unroll
         for (int u = 0; u < CH; ++u)
             if (c[u] >= 0) acc += a[u] * m.x32[c[u]];
         const int64_t tail0 = p0 + (int64_t)CH * LPR;
-        for (int64_t q = tail0 + sub; q < p1; q += LPR) acc += __ldg(m.val + q) * m.x32[__ldg(m.col + q)];
+        for (int64_t q = tail0 + sub; q < p1; q += LPR) {
+            const int2 e = __ldg(m.ent + q);
+            acc += __int_as_float(e.y) * m.x32[e.x];
+        }
 #pragma unroll
         for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         float r = 0.f;
@@ -336,16 +347,19 @@ __device__ void drop_rows(const MemberDev& m, int64_t i0, int64_t i1, int w0, in
                 }
             }
             for (int64_t q = tail0 + sub; q < p1; q += LPR) {
-                const int cq = __ldg(m.col + q);
-                const unsigned o = (unsigned)(cq - w0);
-                if (o < (unsigned)win_cap) atomicAdd(batch_win + o, r * __ldg(m.val + q));
-                else atomicAdd(m.delta + cq, r * __ldg(m.val + q));
+                const int2 e = __ldg(m.ent + q);
+                const unsigned o = (unsigned)(e.x - w0);
+                if (o < (unsigned)win_cap) atomicAdd(batch_win + o, r * __int_as_float(e.y));
+                else atomicAdd(m.delta + e.x, r * __int_as_float(e.y));
             }
         } else {
 #pragma unroll
             for (int u = 0; u < CH; ++u)
                 if (c[u] >= 0) atomicAdd(m.delta + c[u], r * a[u]);
-            for (int64_t q = tail0 + sub; q < p1; q += LPR) atomicAdd(m.delta + __ldg(m.col + q), r * __ldg(m.val + q));
+            for (int64_t q = tail0 + sub; q < p1; q += LPR) {
+                const int2 e = __ldg(m.ent + q);
+                atomicAdd(m.delta + e.x, r * __int_as_float(e.y));
+            }
         }
     }
     const double tot = block_sum(ss, sh);
@@ -672,9 +686,21 @@ __device__ __forceinline__ int64_t vox_canonical(const VoxMap& m, int64_t p) {
     return (iz * m.ny + iy) * m.nx + ix;
 }
 
-__global__ void unmap_kernel(const int32_t* __restrict__ col, int32_t* __restrict__ out, int64_t nnz, VoxMap vm) {
+// the canonical columns and the values of a member's packed entries
+__global__ void unmap_kernel(const int2* __restrict__ ent, int32_t* __restrict__ col, float* __restrict__ val,
+                             int64_t nnz, VoxMap vm) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nnz; q += (int64_t)gridDim.x * blockDim.x) {
+        const int2 e = ent[q];
+        if (col) col[q] = (int32_t)vox_canonical(vm, e.x);
+        if (val) val[q] = __int_as_float(e.y);
+    }
+}
+
+// ent[q] = {col[q], bits of val[q]}
+__global__ void pack_pairs_kernel(const int32_t* __restrict__ col, const float* __restrict__ val, int64_t nnz,
+                                  int2* __restrict__ ent) {
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nnz; q += (int64_t)gridDim.x * blockDim.x)
-        out[q] = (int32_t)vox_canonical(vm, col[q]);
+        ent[q] = make_int2(col[q], __float_as_int(val[q]));
 }
 
 // 1 / ||a_i||^2 (FP64 sum), a warp per row
@@ -719,7 +745,7 @@ __global__ void image_init_kernel(const void* __restrict__ x0, int f64, int64_t 
 }
 
 // column range and mean column (internal order) of each DROP item of one block
-__global__ void item_range_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col, int64_t r0,
+__global__ void item_range_kernel(const int64_t* __restrict__ rp, const int2* __restrict__ ent, int64_t r0,
                                   int64_t r1, int rows_per_item, int32_t* __restrict__ lo, int32_t* __restrict__ hi,
                                   int32_t* __restrict__ mean) {
     const int it = blockIdx.x;
@@ -727,7 +753,7 @@ __global__ void item_range_kernel(const int64_t* __restrict__ rp, const int32_t*
     int mn = INT32_MAX, mx = -1;
     long long sum = 0;
     for (int64_t q = rp[a] + threadIdx.x; q < rp[e]; q += blockDim.x) {
-        const int c = col[q];
+        const int c = ent[q].x;
         mn = min(mn, c);
         mx = max(mx, c);
         sum += c;
@@ -876,6 +902,16 @@ int member_alloc(ntvs_batch::Member& mm, void** dst, size_t bytes, const char* w
     return NTVS_OK;
 }
 
+// frees one of the member's buffers before the member is destroyed
+void member_release(ntvs_batch::Member& mm, const void* q) {
+    for (size_t i = 0; i < mm.owned.size(); ++i)
+        if (mm.owned[i] == q) {
+            cudaFree(mm.owned[i]);
+            mm.owned.erase(mm.owned.begin() + (long)i);
+            return;
+        }
+}
+
 // lanes per row: the smallest LPR whose register-held entries (LPR x CH) cover 1.15x the
 // member's mean row length
 int pick_lpr(int64_t M, int64_t nnz) {
@@ -964,6 +1000,18 @@ int member_prep(ntvs_batch* bt, ntvs_batch::Member& mm, const void* x0, int x0_d
     if (xtmp) cudaFree(xtmp);
     if (e != cudaSuccess || e2 != cudaSuccess)
         return bfail(NTVS_ERR_CUDA, std::string("batch member preparation: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    // the entries as {column, value} pairs (one 8-byte load each in the DROP items); the
+    // separate arrays are released
+    BTRY(member_alloc(mm, (void**)&d.ent, sizeof(int2) * (size_t)std::max<int64_t>(nnz, 1), "packed entries"));
+    if (nnz > 0) pack_pairs_kernel<<<grid_of(nnz), 256, 0, s>>>(d.col, d.val, nnz, (int2*)d.ent);
+    e = cudaGetLastError();
+    e2 = cudaStreamSynchronize(s);
+    if (e != cudaSuccess || e2 != cudaSuccess)
+        return bfail(NTVS_ERR_CUDA, std::string("batch entry packing: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    member_release(mm, d.col);
+    member_release(mm, d.val);
+    d.col = nullptr;
+    d.val = nullptr;
     d.B = B;
     d.lpr = pick_lpr(M, nnz);
     mm.lpr_own = d.lpr;
@@ -1023,7 +1071,7 @@ int build_items(ntvs_batch* bt, int rows_per_item, int cap) {
         for (int t = 0; t < B; ++t) {
             const int k = (t + 1 < B ? item0[t + 1] : n) - item0[t];
             if (k > 0)
-                item_range_kernel<<<k, 256, 0, s>>>(d.row_ptr, d.col, mm.block_ptr[t], mm.block_ptr[t + 1], rows_per_item,
+                item_range_kernel<<<k, 256, 0, s>>>(d.row_ptr, d.ent, mm.block_ptr[t], mm.block_ptr[t + 1], rows_per_item,
                                                     mm.item_lo + item0[t], mm.item_hi + item0[t],
                                                     mm.item_mean + item0[t]);
         }
@@ -1613,15 +1661,27 @@ int ntvs_batch_get_rows(ntvs_batch* bt, int index, int64_t* n_rows, int64_t* nnz
     if (nnz) *nnz = mm.nnz;
     BCUDA(cudaStreamSynchronize(bt->stream));
     if (row_ptr) BCUDA(cudaMemcpy(row_ptr, mm.d.row_ptr, sizeof(int64_t) * (mm.M + 1), cudaMemcpyDeviceToHost));
-    if (val && mm.nnz > 0) BCUDA(cudaMemcpy(val, mm.d.val, sizeof(float) * mm.nnz, cudaMemcpyDeviceToHost));
-    if (col && mm.nnz > 0) {
-        int32_t* tmp = nullptr;
-        BTRY(balloc(&tmp, sizeof(int32_t) * mm.nnz, "column read-back"));
-        unmap_kernel<<<grid_of(mm.nnz), 256, 0, bt->stream>>>(mm.d.col, tmp, mm.nnz, mm.d.vm);
-        cudaError_t e = cudaMemcpyAsync(col, tmp, sizeof(int32_t) * mm.nnz, cudaMemcpyDeviceToHost, bt->stream);
+    if ((col || val) && mm.nnz > 0) {   // unpacked from the pairs, columns back in canonical order
+        int32_t* tc = nullptr;
+        float* tv = nullptr;
+        if (col) BTRY(balloc(&tc, sizeof(int32_t) * mm.nnz, "column read-back"));
+        if (val) {
+            const int rc = balloc(&tv, sizeof(float) * mm.nnz, "value read-back");
+            if (rc != NTVS_OK) {
+                cudaFree(tc);
+                return rc;
+            }
+        }
+        unmap_kernel<<<grid_of(mm.nnz), 256, 0, bt->stream>>>(mm.d.ent, tc, tv, mm.nnz, mm.d.vm);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess && col)
+            e = cudaMemcpyAsync(col, tc, sizeof(int32_t) * mm.nnz, cudaMemcpyDeviceToHost, bt->stream);
+        if (e == cudaSuccess && val)
+            e = cudaMemcpyAsync(val, tv, sizeof(float) * mm.nnz, cudaMemcpyDeviceToHost, bt->stream);
         cudaError_t e2 = cudaStreamSynchronize(bt->stream);
-        cudaFree(tmp);
-        if (e != cudaSuccess || e2 != cudaSuccess) return bfail(NTVS_ERR_CUDA, "batch: column read-back");
+        cudaFree(tc);
+        cudaFree(tv);
+        if (e != cudaSuccess || e2 != cudaSuccess) return bfail(NTVS_ERR_CUDA, "batch: row read-back");
     }
     return NTVS_OK;
 }

@@ -161,7 +161,9 @@ __device__ __forceinline__ void row_factor(bool valid, bool first_lane, T res, T
         const float iq = ws->invQ;
         rowfix = iq > 0.f && arn <= ws->bound;
         rq = (float)r * iq;
-        if (valid && first_lane && arn > 0.f) atomicMax(&ws->obs, __float_as_uint(arn));
+        // the block's largest |r/lambda|: a plain read first skips the atomic for most rows
+        if (valid && first_lane && __float_as_uint(arn) > *(volatile unsigned*)&ws->obs)
+            atomicMax(&ws->obs, __float_as_uint(arn));
     }
 }
 
