@@ -79,6 +79,8 @@ struct MemberDev {
     float* delta;              // internal order
     float* g;                  // canonical order
     double* resid;             // [B]
+    float* wstat;              // [4B] per block: lmax, bound, observed max (float bits), amax (the
+                               // fixed-point DROP window's scale, as in the single-context kernel)
     double* tv_hist;           // [cap]
     int nx, ny, nz, B, N;
     int64_t V;
@@ -295,7 +297,7 @@ extern __shared__ float batch_win[];   // the shared scatter window (win_cap flo
 // others into global delta, else every entry into global delta
 template <int LPR, int CH>
 __device__ void drop_rows(const MemberDev& m, int64_t i0, int64_t i1, int w0, int win_cap, double* resid_b,
-                          double* sh) {
+                          double* sh, float invQ, float bnd, unsigned* obs) {
     constexpr int G = 32 / LPR;
     const int lane = threadIdx.x & 31, sub = lane % LPR;
     const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -331,26 +333,41 @@ __device__ void drop_rows(const MemberDev& m, int64_t i0, int64_t i1, int w0, in
         }
 #pragma unroll
         for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        float r = 0.f;
+        float r = 0.f, rn = 0.f;
         if (valid) {
             const float res = __ldg(m.b + i) - acc;
-            r = m.lambda * res * __ldg(m.inv_norm2 + i);
+            rn = res * __ldg(m.inv_norm2 + i);
+            r = m.lambda * rn;
             if (sub == 0) ss += (double)res * (double)res;
+            // the block's largest |r / lambda| (the next sweep's window bound); a plain read
+            // first skips the atomic for most rows
+            const unsigned arn = __float_as_uint(fabsf(rn));
+            if (sub == 0 && obs && arn > *(volatile unsigned*)obs) atomicMax(obs, arn);
         }
+        // a row within the bound adds its terms to the window as int32 multiples of the
+        // quantum (every term below 2^22 quanta, every slot below 2^30): r / Q = r * invQ
+        const bool rowfix = invQ > 0.f && fabsf(rn) <= bnd;
+        const float rq = r * invQ;
+        int* wint = reinterpret_cast<int*>(batch_win);
         if (win) {   // entries inside the window to shared memory, the others to global memory
 #pragma unroll
             for (int u = 0; u < CH; ++u) {
                 if (c[u] >= 0) {
                     const unsigned o = (unsigned)(c[u] - w0);
-                    if (o < (unsigned)win_cap) atomicAdd(batch_win + o, r * a[u]);
-                    else atomicAdd(m.delta + c[u], r * a[u]);
+                    if (rowfix && o < (unsigned)win_cap)   // adding 1.5 * 2^23 rounds to the nearest integer
+                        atomicAdd(wint + o, __float_as_int(fmaf(rq, a[u], 12582912.0f)) - 0x4B400000);
+                    else
+                        atomicAdd(m.delta + c[u], r * a[u]);
                 }
             }
             for (int64_t q = tail0 + sub; q < p1; q += LPR) {
                 const int2 e = __ldg(m.ent + q);
                 const unsigned o = (unsigned)(e.x - w0);
-                if (o < (unsigned)win_cap) atomicAdd(batch_win + o, r * __int_as_float(e.y));
-                else atomicAdd(m.delta + e.x, r * __int_as_float(e.y));
+                const float av = __int_as_float(e.y);
+                if (rowfix && o < (unsigned)win_cap)
+                    atomicAdd(wint + o, __float_as_int(fmaf(rq, av, 12582912.0f)) - 0x4B400000);
+                else
+                    atomicAdd(m.delta + e.x, r * av);
             }
         } else {
 #pragma unroll
@@ -370,21 +387,37 @@ __device__ void drop_item(const MemberDev& m, int b, int idx, int win_cap, doubl
     const int64_t r0 = __ldg(m.block_ptr + b) + (int64_t)idx * m.rows_per_item;
     const int64_t r1 = min(__ldg(m.block_ptr + b + 1), r0 + m.rows_per_item);
     const int w0 = win_cap > 0 ? __ldg(m.win_lo + __ldg(m.item0 + b) + idx) : -1;
+    // the window's quantum Q = |lambda| bound lmax / 2^30 from the block's statistics (lmax:
+    // the largest column sum of |a_ij| over the block's rows, so no slot passes 2^30 Q);
+    // rows above min(bound, 2^22 Q / (|lambda| amax)) go to global memory
+    float Q = 0.f, invQ = 0.f, bnd = 0.f;
+    unsigned* obs = m.wstat ? reinterpret_cast<unsigned*>(m.wstat + 2 * m.B + b) : nullptr;
+    if (w0 >= 0 && m.wstat) {
+        const float lmax = m.wstat[b], bound = m.wstat[m.B + b], amax = m.wstat[3 * m.B + b];
+        const float lam = fabsf(m.lambda);
+        Q = lam * bound * lmax * 0x1p-30f;
+        const float iq = 1.f / Q;
+        if (bound > 0.f && amax > 0.f && Q > 0.f && isfinite(Q) && isfinite(iq)) {
+            invQ = iq;
+            bnd = fminf(bound, 0x1p22f * Q / (lam * amax));
+        }
+    }
     if (w0 >= 0) {
-        for (int j = threadIdx.x; j < win_cap; j += blockDim.x) batch_win[j] = 0.f;
+        for (int j = threadIdx.x; j < win_cap; j += blockDim.x) batch_win[j] = 0.f;   // int 0 has the bits of 0.0f
         __syncthreads();
     }
     switch (m.lpr) {
-        case 8: drop_rows<8, 16>(m, r0, r1, w0, win_cap, m.resid + b, sh); break;
-        case 16: drop_rows<16, 10>(m, r0, r1, w0, win_cap, m.resid + b, sh); break;
-        default: drop_rows<32, 6>(m, r0, r1, w0, win_cap, m.resid + b, sh); break;
+        case 8: drop_rows<8, 16>(m, r0, r1, w0, win_cap, m.resid + b, sh, invQ, bnd, obs); break;
+        case 16: drop_rows<16, 10>(m, r0, r1, w0, win_cap, m.resid + b, sh, invQ, bnd, obs); break;
+        default: drop_rows<32, 6>(m, r0, r1, w0, win_cap, m.resid + b, sh, invQ, bnd, obs); break;
     }
     if (w0 >= 0) {
         __syncthreads();
         const int64_t n = min((int64_t)win_cap, m.vm.vint - (int64_t)w0);
+        const int* wint = reinterpret_cast<const int*>(batch_win);
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            const float v = batch_win[j];
-            if (v != 0.f) atomicAdd(m.delta + w0 + j, v);
+            const int v = wint[j];
+            if (v != 0) atomicAdd(m.delta + w0 + j, (float)v * Q);
         }
     }
 }
@@ -482,7 +515,11 @@ __device__ void finish_phase(const CycleArgs& a, int r, int phase, int items, un
             ph = PH_GRAD;
             n += 1;
             break;
-        case PH_DROP:
+        case PH_DROP:   // the block's next window bound: twice the largest |r / lambda| of this sweep
+            if (m.wstat) {
+                const float o = __uint_as_float(atomicExch(reinterpret_cast<unsigned*>(m.wstat + 2 * m.B + b), 0u));
+                if (o > 0.f) m.wstat[m.B + b] = 2.f * o;
+            }
             ph = PH_DAPPLY;
             break;
         case PH_DAPPLY:
@@ -722,6 +759,42 @@ __global__ void count_kernel(const int64_t* __restrict__ rp, const int32_t* __re
     const int64_t q0 = rp[r0], q1 = rp[r1];
     for (int64_t q = q0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < q1; q += (int64_t)gridDim.x * blockDim.x)
         if (val[q] != 0.f) atomicAdd(cnt + col[q], 1);
+}
+
+// The window statistics of one block (rows [r0, r1)), each a non-negative float kept as its
+// bits so that an unsigned atomic max orders them: colsum[j] += |a_ij| and *amax = max |a_ij|
+__global__ void colsum_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                              const float* __restrict__ val, int64_t r0, int64_t r1, float* __restrict__ colsum,
+                              unsigned* __restrict__ amax) {
+    const int64_t q0 = rp[r0], q1 = rp[r1];
+    unsigned mx = 0u;
+    for (int64_t q = q0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < q1; q += (int64_t)gridDim.x * blockDim.x) {
+        const float a = fabsf(val[q]);
+        if (a != 0.f) atomicAdd(colsum + col[q], a);
+        mx = max(mx, __float_as_uint(a));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(amax, mx);
+}
+
+// *out = max(*out, largest of v[0..n)) for non-negative v
+__global__ void max_bits_kernel(const float* __restrict__ v, int64_t n, unsigned* __restrict__ out) {
+    unsigned mx = 0u;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        mx = max(mx, __float_as_uint(v[j]));
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, mx);
+}
+
+// *out = max over rows [r0, r1) of |b_i| / ||a_i||^2: the residual bound at x = 0, the first
+// sweep's window bound
+__global__ void seed_bound_kernel(const float* __restrict__ b, const float* __restrict__ inn, int64_t r0, int64_t r1,
+                                  unsigned* __restrict__ out) {
+    unsigned mx = 0u;
+    for (int64_t i = r0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < r1; i += (int64_t)gridDim.x * blockDim.x)
+        mx = max(mx, __float_as_uint(fabsf(b[i]) * inn[i]));
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, mx);
 }
 
 __global__ void inv_count_kernel(const int32_t* __restrict__ cnt, float* __restrict__ inv_s, int64_t n) {
@@ -971,11 +1044,24 @@ int member_prep(ntvs_batch* bt, ntvs_batch::Member& mm, const void* x0, int x0_d
     if (M > 0) norm_kernel<<<grid_of(M * 32), 256, 0, s>>>(d.row_ptr, d.val, M, (float*)d.inv_norm2);
     int32_t* cnt = nullptr;
     BTRY(balloc(&cnt, sizeof(int32_t) * VI, "hit counts"));
+    BTRY(member_alloc(mm, (void**)&d.wstat, sizeof(float) * 4 * (size_t)B, "window statistics"));
+    cudaMemsetAsync(d.wstat, 0, sizeof(float) * 4 * (size_t)B, s);
     for (int t = 0; t < B; ++t) {
         cudaMemsetAsync(cnt, 0, sizeof(int32_t) * VI, s);
-        if (mm.block_ptr[t + 1] > mm.block_ptr[t])
+        if (mm.block_ptr[t + 1] > mm.block_ptr[t]) {
             count_kernel<<<grid_of(nnz), 256, 0, s>>>(d.row_ptr, d.col, d.val, mm.block_ptr[t], mm.block_ptr[t + 1], cnt);
-        inv_count_kernel<<<grid_of(VI), 256, 0, s>>>(cnt, (float*)d.inv_s + (size_t)t * VI, VI);
+            // the window statistics: column sums of |a| into the (reused) count buffer as floats
+            inv_count_kernel<<<grid_of(VI), 256, 0, s>>>(cnt, (float*)d.inv_s + (size_t)t * VI, VI);
+            cudaMemsetAsync(cnt, 0, sizeof(int32_t) * VI, s);
+            unsigned* w = reinterpret_cast<unsigned*>(d.wstat);
+            colsum_kernel<<<grid_of(nnz), 256, 0, s>>>(d.row_ptr, d.col, d.val, mm.block_ptr[t], mm.block_ptr[t + 1],
+                                                       reinterpret_cast<float*>(cnt), w + 3 * B + t);
+            max_bits_kernel<<<grid_of(VI), 256, 0, s>>>(reinterpret_cast<const float*>(cnt), VI, w + t);
+            seed_bound_kernel<<<grid_of(mm.block_ptr[t + 1] - mm.block_ptr[t]), 256, 0, s>>>(
+                d.b, d.inv_norm2, mm.block_ptr[t], mm.block_ptr[t + 1], w + B + t);
+        } else {
+            inv_count_kernel<<<grid_of(VI), 256, 0, s>>>(cnt, (float*)d.inv_s + (size_t)t * VI, VI);
+        }
     }
     // x0 on the device (copied when it is host memory)
     const size_t xb = (x0_dtype == NTVS_F64 ? sizeof(double) : sizeof(float)) * (size_t)V;
