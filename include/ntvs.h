@@ -479,7 +479,7 @@ int ntvs_batch_set_schedule(ntvs_batch* bt, int rows_per_item, int window_floats
  * of the cycles run after finalize.  Before finalize only.  The paper has no counterpart. */
 int ntvs_batch_set_fault_hook(ntvs_batch* bt, int64_t wait_ns, int flags);
 /* Lay out the work tables, pick the schedule (ntvs_batch_set_schedule, or by timing one
- * cycle of each candidate: rows per item {256, 512, 1024} x window {0, 8192, 16384} x
+ * cycle of each candidate: rows per item {256, 512, 1024} x window {0, 8192, 12288, 16384} x
  * {3, 4} CTAs per SM, then on the best of those the rows per warp: lanes per row 32, 16
  * or 8 for every member against each member's own; images restored afterwards) and
  * capture the cycle graph; max_cycles bounds the cycles that may be run (per-member phi

@@ -1540,7 +1540,7 @@ int ntvs_batch_finalize(ntvs_batch* bt, int max_cycles) {
     // schedule: fixed by the caller, else timed over kTrialCycles cycles per candidate
     // (images and schedule state saved before and restored after)
     std::vector<int> rows_c = bt->req_rows > 0 ? std::vector<int>{bt->req_rows} : std::vector<int>{256, 512, 1024};
-    std::vector<int> win_c = bt->req_win >= 0 ? std::vector<int>{bt->req_win} : std::vector<int>{0, 8192, 16384};
+    std::vector<int> win_c = bt->req_win >= 0 ? std::vector<int>{bt->req_win} : std::vector<int>{0, 8192, 12288, 16384};
     std::vector<int> minb_c = (bt->req_rows > 0 && bt->req_win >= 0) ? std::vector<int>{3} : std::vector<int>{3, 4};
     if (rows_c.size() * win_c.size() * minb_c.size() == 1) {
         bt->rows_per_item = rows_c[0];
