@@ -172,22 +172,23 @@ cudaError_t k_row_maxlen(const int64_t* row_ptr, int64_t r0, int64_t r1, unsigne
 
 // home slice of each row: the median of the z-slices of its first, middle and last
 // entries (-1 for an empty row); a path that bends out of its slice and back keeps the
-// slice it enters and leaves by
-__global__ void row_home_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int64_t M,
-                                int64_t slice, int32_t* __restrict__ home) {
+// slice it enters and leaves by.  Entry p's column is col[stride * p] (stride 2: the
+// packed pairs).
+__global__ void row_home_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int stride,
+                                int64_t M, int64_t slice, int32_t* __restrict__ home) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t p0 = row_ptr[i], p1 = row_ptr[i + 1];
         if (p1 <= p0) { home[i] = -1; continue; }
-        const int32_t a = (int32_t)(col[p0] / slice), m = (int32_t)(col[p0 + (p1 - p0) / 2] / slice),
-                      c = (int32_t)(col[p1 - 1] / slice);
+        const int32_t a = (int32_t)(col[stride * p0] / slice), m = (int32_t)(col[stride * (p0 + (p1 - p0) / 2)] / slice),
+                      c = (int32_t)(col[stride * (p1 - 1)] / slice);
         home[i] = max(min(a, m), min(max(a, m), c));
     }
 }
 
-cudaError_t k_row_home(const int64_t* row_ptr, const int32_t* col, int64_t M, int64_t slice, int32_t* home, int grid,
-                       cudaStream_t s) {
+cudaError_t k_row_home(const int64_t* row_ptr, const int32_t* col, int stride, int64_t M, int64_t slice, int32_t* home,
+                       int grid, cudaStream_t s) {
     if (M <= 0) return cudaSuccess;
-    row_home_kernel<<<grid, 256, 0, s>>>(row_ptr, col, M, slice, home);
+    row_home_kernel<<<grid, 256, 0, s>>>(row_ptr, col, stride, M, slice, home);
     return cudaGetLastError();
 }
 

@@ -80,7 +80,8 @@ namespace ntvs {
 template <typename V, typename T>
 __global__ void __launch_bounds__(256) prep_block_kernel(const int64_t* __restrict__ row_ptr,
                                                          const int32_t* __restrict__ col, const V* __restrict__ val,
-                                                         const T* __restrict__ b, int64_t r0, int64_t r1, int64_t nvox,
+                                                         int64_t e0, const T* __restrict__ b, int64_t r0, int64_t r1,
+                                                         int64_t nvox,
                                                          T* __restrict__ inv_norm2, int32_t* __restrict__ cnt,
                                                          int* flags, float* __restrict__ colsum, unsigned* rb) {
     const int lane = threadIdx.x & 31;
@@ -93,8 +94,8 @@ __global__ void __launch_bounds__(256) prep_block_kernel(const int64_t* __restri
         double sq = 0.0;
 #pragma unroll 4
         for (int64_t p = p0 + lane; p < p1; p += 32) {
-            const int32_t c = __ldcs(col + p);
-            const double a = as_f64(val[p]);
+            const int32_t c = __ldcs(col + (p - e0));
+            const double a = as_f64(val[p - e0]);
             if (!isfinite(a)) f |= 8;
             sq += a * a;
             if (c < 0 || (int64_t)c >= nvox) f |= 4;
@@ -142,36 +143,36 @@ cudaError_t k_colmax(const float* v, int64_t n, float* out, cudaStream_t s) {
 }
 
 template <typename V>
-static cudaError_t launch_prep(const int64_t* rp, const int32_t* col, const V* val, const void* b, int64_t r0,
-                               int64_t r1, int64_t nvox, void* inn, int cdt, int32_t* cnt, int* flags, float* colsum,
-                               float* rb, cudaStream_t s) {
+static cudaError_t launch_prep(const int64_t* rp, const int32_t* col, const V* val, int64_t e0, const void* b,
+                               int64_t r0, int64_t r1, int64_t nvox, void* inn, int cdt, int32_t* cnt, int* flags,
+                               float* colsum, float* rb, cudaStream_t s) {
     unsigned* rbu = reinterpret_cast<unsigned*>(rb);
     if (cdt == F64)
-        prep_block_kernel<V, double><<<prep_grid(), 256, 0, s>>>(rp, col, val, (const double*)b, r0, r1, nvox,
+        prep_block_kernel<V, double><<<prep_grid(), 256, 0, s>>>(rp, col, val, e0, (const double*)b, r0, r1, nvox,
                                                                  (double*)inn, cnt, flags, colsum, rbu);
     else
-        prep_block_kernel<V, float><<<prep_grid(), 256, 0, s>>>(rp, col, val, (const float*)b, r0, r1, nvox,
+        prep_block_kernel<V, float><<<prep_grid(), 256, 0, s>>>(rp, col, val, e0, (const float*)b, r0, r1, nvox,
                                                                 (float*)inn, cnt, flags, colsum, rbu);
     return cudaGetLastError();
 }
 
-cudaError_t k_prep_block(const int64_t* row_ptr, const int32_t* col, const void* val, int vdt, const void* b,
-                         int64_t r0, int64_t r1, int64_t nvox, void* inv_norm2, int cdt, int32_t* cnt, int* flags,
-                         float* colsum, float* rb, cudaStream_t s) {
+cudaError_t k_prep_block(const int64_t* row_ptr, const int32_t* col, const void* val, int64_t e0, int vdt,
+                         const void* b, int64_t r0, int64_t r1, int64_t nvox, void* inv_norm2, int cdt, int32_t* cnt,
+                         int* flags, float* colsum, float* rb, cudaStream_t s) {
     if (r1 <= r0) return cudaSuccess;
     switch (vdt) {
         case F64:
-            return launch_prep(row_ptr, col, (const double*)val, b, r0, r1, nvox, inv_norm2, cdt, cnt, flags, colsum,
-                               rb, s);
-        case F32:
-            return launch_prep(row_ptr, col, (const float*)val, b, r0, r1, nvox, inv_norm2, cdt, cnt, flags, colsum,
-                               rb, s);
-        case F16:
-            return launch_prep(row_ptr, col, (const __half*)val, b, r0, r1, nvox, inv_norm2, cdt, cnt, flags, colsum,
-                               rb, s);
-        case BF16:
-            return launch_prep(row_ptr, col, (const __nv_bfloat16*)val, b, r0, r1, nvox, inv_norm2, cdt, cnt, flags,
+            return launch_prep(row_ptr, col, (const double*)val, e0, b, r0, r1, nvox, inv_norm2, cdt, cnt, flags,
                                colsum, rb, s);
+        case F32:
+            return launch_prep(row_ptr, col, (const float*)val, e0, b, r0, r1, nvox, inv_norm2, cdt, cnt, flags,
+                               colsum, rb, s);
+        case F16:
+            return launch_prep(row_ptr, col, (const __half*)val, e0, b, r0, r1, nvox, inv_norm2, cdt, cnt, flags,
+                               colsum, rb, s);
+        case BF16:
+            return launch_prep(row_ptr, col, (const __nv_bfloat16*)val, e0, b, r0, r1, nvox, inv_norm2, cdt, cnt,
+                               flags, colsum, rb, s);
         default: return cudaErrorInvalidValue;
     }
 }

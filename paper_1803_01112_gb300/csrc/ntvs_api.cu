@@ -777,7 +777,8 @@ static int plan_schedule(ntvs_ctx* c, int requested) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(dch, chunk_ch.data(), chunk_ch.size(), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(dchanges, 0, sizeof(unsigned long long), c->stream);
-    if (e == cudaSuccess) e = k_row_home(c->row_ptr, c->col, c->M, slice, dhome, c->sms * 8, c->stream);
+    if (e == cudaSuccess)   // the columns of the packed pairs when there are any (col may be gone)
+        e = k_row_home(c->row_ptr, c->ent ? c->ent : c->col, c->ent ? 2 : 1, c->M, slice, dhome, c->sms * 8, c->stream);
     if (e == cudaSuccess) e = k_chunk_home(dhome, dstart, nch, dchunk, dchanges, c->sms * 8, c->stream);
     if (e == cudaSuccess) e = k_chunk_cost(c->row_ptr, dstart, dch, nch, dcost, c->sms * 8, c->stream);
     if (e == cudaSuccess && nch > 0)
@@ -1113,17 +1114,61 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
     // comes from the host row_ptr, clamped to [0, nnz); a row_ptr that is not
     // non-decreasing is rejected below before any block is prepared.
     const bool piped = s->mem_kind == NTVS_MEM_HOST && nnz > 0 && c->copy_stream && c->copy_stream2;
-    std::vector<cudaEvent_t> arrived;
+    // CSR32 storage with FP32 values from host arrays: the blocks pass through a ring of
+    // kLoadRing block-sized device slots on their way into the packed pairs, so that the
+    // separate column and value arrays are neither allocated nor freed (the copy of block
+    // t + kLoadRing waits until block t has been prepared and packed)
+    const bool ring = piped && c->storage == NTVS_CSR32 && c->vdt == F32;
+    constexpr int kLoadRing = 3;
+    std::vector<cudaEvent_t> arrived, freed;
     std::vector<int64_t> eb;   // [B+1] entry range of each block (piped)
     struct EventGuard {
         std::vector<cudaEvent_t>& v;
         ~EventGuard() { for (auto e : v) cudaEventDestroy(e); }
-    } guard{arrived};
+    } guard{arrived}, guard_freed{freed};
+    int32_t* slot_c = nullptr;
+    char* slot_v = nullptr;
+    int64_t slot_cap = 0;
+    int nslots = 0;
+    struct SlotGuard {   // released once no copy or kernel can still touch the slots
+        ntvs_ctx* c;
+        int32_t*& sc;
+        char*& sv;
+        ~SlotGuard() {
+            if (!sc && !sv) return;
+            for (cudaStream_t q : {c->copy_stream, c->copy_stream2, c->stream})
+                if (q) cudaStreamSynchronize(q);
+            dev_free(sc);
+            dev_free(sv);
+        }
+    } slot_guard{c, slot_c, slot_v};
+    // block t's columns and values on the device: its slot, or its part of the whole arrays
+    auto block_col = [&](int t) -> int32_t* {
+        return ring ? slot_c + (size_t)(t % nslots) * (size_t)slot_cap : c->col + eb[t];
+    };
+    auto block_val = [&](int t) -> char* {
+        return ring ? slot_v + (size_t)(t % nslots) * (size_t)slot_cap * vsz : (char*)c->val + vsz * (size_t)eb[t];
+    };
+    auto issue_copy = [&](int t) -> int {
+        const int64_t n = eb[t + 1] - eb[t];
+        if (ring && t >= nslots)
+            for (cudaStream_t cs : {c->copy_stream, c->copy_stream2})
+                CUDA_TRY(cudaStreamWaitEvent(cs, freed[(size_t)(t - nslots)], 0));
+        if (n > 0) {
+            CUDA_TRY(cudaMemcpyAsync(block_col(t), s->col + eb[t], sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice,
+                                     c->copy_stream));
+            CUDA_TRY(cudaMemcpyAsync(block_val(t), (const char*)s->val + vsz * (size_t)eb[t], vsz * (size_t)n,
+                                     cudaMemcpyHostToDevice, c->copy_stream2));
+        }
+        for (cudaStream_t cs : {c->copy_stream, c->copy_stream2}) {
+            cudaEvent_t ev;
+            CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+            arrived.push_back(ev);
+            CUDA_TRY(cudaEventRecord(ev, cs));
+        }
+        return NTVS_OK;
+    };
     if (piped) {
-        TRY(dev_alloc(&c->col, sizeof(int32_t) * (size_t)nnz, "col"));
-        c->own_col = true;
-        TRY(dev_alloc(&c->val, vsz * (size_t)nnz, "val"));
-        c->own_val = true;
         eb.resize((size_t)c->B + 1);
         for (int t = 0; t <= c->B; ++t) {
             int64_t e = s->row_ptr[bp[t]];
@@ -1131,20 +1176,19 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
             eb[t] = t > 0 && e < eb[t - 1] ? eb[t - 1] : e;
         }
         eb[c->B] = nnz;
-        for (int t = 0; t < c->B; ++t) {
-            const int64_t e0 = eb[t], n = eb[t + 1] - eb[t];
-            if (n > 0) {
-                CUDA_TRY(cudaMemcpyAsync(c->col + e0, s->col + e0, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice,
-                                         c->copy_stream));
-                CUDA_TRY(cudaMemcpyAsync((char*)c->val + vsz * (size_t)e0, (const char*)s->val + vsz * (size_t)e0,
-                                         vsz * (size_t)n, cudaMemcpyHostToDevice, c->copy_stream2));
-            }
-            for (cudaStream_t cs : {c->copy_stream, c->copy_stream2}) {
-                cudaEvent_t ev;
-                CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-                arrived.push_back(ev);
-                CUDA_TRY(cudaEventRecord(ev, cs));
-            }
+        if (ring) {
+            for (int t = 0; t < c->B; ++t) slot_cap = std::max<int64_t>(slot_cap, eb[t + 1] - eb[t]);
+            slot_cap = std::max<int64_t>(slot_cap, 1);
+            nslots = std::min(kLoadRing, c->B);
+            TRY(dev_alloc(&slot_c, sizeof(int32_t) * (size_t)slot_cap * (size_t)nslots, "column staging"));
+            TRY(dev_alloc(&slot_v, vsz * (size_t)slot_cap * (size_t)nslots, "value staging"));
+            for (int t = 0; t < nslots; ++t) TRY(issue_copy(t));
+        } else {
+            TRY(dev_alloc(&c->col, sizeof(int32_t) * (size_t)nnz, "col"));
+            c->own_col = true;
+            TRY(dev_alloc(&c->val, vsz * (size_t)nnz, "val"));
+            c->own_val = true;
+            for (int t = 0; t < c->B; ++t) TRY(issue_copy(t));
         }
     } else {
         TRY(copy_in((void**)&c->col, &c->own_col, s->col, sizeof(int32_t) * (size_t)nnz, s->mem_kind, st, "col"));
@@ -1193,20 +1237,34 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
     // pairs once they are validated and remapped (during the copy of the later blocks)
     if (c->storage == NTVS_CSR32 && c->vdt == F32)
         TRY(dev_alloc(&c->ent, sizeof(int32_t) * 2 * (size_t)std::max<int64_t>(nnz, 1), "packed entries"));
+    if (ring && !c->ent) return fail(NTVS_ERR_STATE, "staged load without packed entries");
     for (int t = 0; t < c->B; ++t) {
+        // block t's entries: from entry e0 on at bc / bv (the whole arrays when not piped)
+        int32_t* bc = c->col;
+        const void* bv = c->val;
+        int64_t e0 = 0;
         if (piped) {
-            CUDA_TRY(cudaStreamWaitEvent(st, arrived[2 * t], 0));
-            CUDA_TRY(cudaStreamWaitEvent(st, arrived[2 * t + 1], 0));
-            if (tiled) CUDA_TRY(k_remap_cols(c->col + eb[t], c->col + eb[t], eb[t + 1] - eb[t], c->vm, c->dflags, st));
+            CUDA_TRY(cudaStreamWaitEvent(st, arrived[2 * (size_t)t], 0));
+            CUDA_TRY(cudaStreamWaitEvent(st, arrived[2 * (size_t)t + 1], 0));
+            bc = block_col(t);
+            bv = block_val(t);
+            e0 = eb[t];
+            if (tiled) CUDA_TRY(k_remap_cols(bc, bc, eb[t + 1] - eb[t], c->vm, c->dflags, st));
         }
         if (colsum) CUDA_TRY(cudaMemsetAsync(colsum, 0, sizeof(float) * (size_t)VI, st));
-        CUDA_TRY(k_prep_block(c->row_ptr, c->col, c->val, c->vdt, c->b, bp[t], bp[t + 1], VI, c->inv_norm2, c->cdt,
+        CUDA_TRY(k_prep_block(c->row_ptr, bc, bv, e0, c->vdt, c->b, bp[t], bp[t + 1], VI, c->inv_norm2, c->cdt,
                               cnt + (size_t)t * VI, c->dflags, colsum, colsum ? c->wstat + 3 * c->B + 2 * t : nullptr,
                               st));
         if (colsum) CUDA_TRY(k_colmax(colsum, VI, c->wstat + t, st));
         if (c->ent && piped)
-            CUDA_TRY(k_pack_entries(c->col + eb[t], (const float*)c->val + eb[t], eb[t + 1] - eb[t], c->ent + 2 * eb[t],
-                                    st));
+            CUDA_TRY(k_pack_entries(bc, (const float*)bv, eb[t + 1] - eb[t], c->ent + 2 * eb[t], st));
+        if (ring) {   // the slot is free again: the block nslots on may be copied into it
+            cudaEvent_t ev;
+            CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+            freed.push_back(ev);
+            CUDA_TRY(cudaEventRecord(ev, st));
+            if (t + nslots < c->B) TRY(issue_copy(t + nslots));
+        }
     }
     if (c->ent && !piped) CUDA_TRY(k_pack_entries(c->col, (const float*)c->val, nnz, c->ent, st));
     {   // longest row of every block

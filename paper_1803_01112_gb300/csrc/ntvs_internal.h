@@ -76,10 +76,11 @@ cudaError_t k_validate_rows(const int64_t* row_ptr, int64_t M, int* flags, cudaS
 // fused pass over the rows [r0, r1) of one block: validation of columns, values and b
 // (flags 4 / 8 / 16), inv_norm2 of the rows and the block's hit counts cnt; with colsum
 // (nullable) also colsum[j] += |a_ij|, rb[0] = max(rb[0], max_i |b_i| / ||a_i||^2) and
-// rb[1] = max(rb[1], max |a_ij|)
-cudaError_t k_prep_block(const int64_t* row_ptr, const int32_t* col, const void* val, int vdt, const void* b,
-                         int64_t r0, int64_t r1, int64_t nvox, void* inv_norm2, int cdt, int32_t* cnt, int* flags,
-                         float* colsum, float* rb, cudaStream_t s);
+// rb[1] = max(rb[1], max |a_ij|).  col and val hold the entries from e0 on: entry p is
+// col[p - e0] (0 for whole arrays, the block's first entry for a staging slot).
+cudaError_t k_prep_block(const int64_t* row_ptr, const int32_t* col, const void* val, int64_t e0, int vdt,
+                         const void* b, int64_t r0, int64_t r1, int64_t nvox, void* inv_norm2, int cdt, int32_t* cnt,
+                         int* flags, float* colsum, float* rb, cudaStream_t s);
 // *out = max(*out, max_j v[j]) for n non-negative floats
 cudaError_t k_colmax(const float* v, int64_t n, float* out, cudaStream_t s);
 // col_out[p] = internal index of voxel col_in[p]; flags |= 4 for a column outside [0, V)
@@ -218,9 +219,10 @@ cudaError_t k_project(const DropArgs& a, int64_t M, const void* x, void* out, cu
 // *out = max(*out, longest row of rows [r0, r1)); *out zeroed by the caller
 cudaError_t k_row_maxlen(const int64_t* row_ptr, int64_t r0, int64_t r1, unsigned long long* out, int grid,
                          cudaStream_t s);
-// home[i] = median z-slice of the first, middle and last entries of row i (-1: empty row)
-cudaError_t k_row_home(const int64_t* row_ptr, const int32_t* col, int64_t M, int64_t slice, int32_t* home, int grid,
-                       cudaStream_t s);
+// home[i] = median z-slice of the first, middle and last entries of row i (-1: empty row);
+// entry p's column is col[stride * p] (2 for the packed pairs)
+cudaError_t k_row_home(const int64_t* row_ptr, const int32_t* col, int stride, int64_t M, int64_t slice, int32_t* home,
+                       int grid, cudaStream_t s);
 // chunk q = rows [chunk_start[q], chunk_start[q+1]) (at most 64 rows): out[q] = lower median
 // of the defined home slices (-1 if none); *changes += rows whose defined home differs from
 // the previous row's defined home (*changes must be zeroed by the caller)
