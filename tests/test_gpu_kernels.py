@@ -193,6 +193,44 @@ def test_drop_schedules_match_oracle(dtype, schedule):
     np.testing.assert_allclose(res, ss, rtol=1e-10 if dtype == np.float64 else 1e-4)
 
 
+@pytest.mark.parametrize("tile", [(4, 4), (1, 1)])
+@pytest.mark.parametrize("parts", ["1", "2", "3", "7", "empty_blocks"])
+def test_staged_load_matches_oracle(parts, tile):
+    """FP32 values from host arrays reach the device through a ring of three block-sized
+    slots, packed into {column, value} pairs block by block (the copy of block t + 3 waits
+    for block t).  Every ring depth (1, 2 or 3 slots in use, and more blocks than slots),
+    empty blocks (no copy into their slot), the tiled and the canonical voxel order: the
+    sweep is the oracle's, and the loaded rows project like the oracle's."""
+    ntvs = ntvs_module()
+    s = synth.generate(synth.spec_scaled_3d(nx=40, ny=40, nz=5, n_hist=30_000, n_angles=36, n_blocks=4, seed=8))
+    M = s.M
+    if parts == "empty_blocks":
+        bp = np.array([0, 0, M // 3, M // 3, M // 3 + 5, M, M], dtype=np.int64)
+    else:
+        nb = int(parts)
+        bp = np.array([(M * t) // nb for t in range(nb + 1)], dtype=np.int64)
+    val = s.val.astype(np.float32)
+    b = s.b.astype(np.float32)
+    x0 = s.xstar * 0.9 + 0.05
+    r = ntvs.Reconstructor(0).set_voxel_tile(*tile)
+    try:
+        r.load((40, 40, 5), s.row_ptr, s.col, val, b, block_ptr=bp)
+        r.set_params(lam=1.1, N=0, alpha=0.5)
+        proj = r.forward_project(x0)
+        r.set_image(x0)
+        r.drop_sweep()
+        got = r.get_image()
+        res = r.block_resid()
+    finally:
+        r.close()
+    val64, b64 = val.astype(np.float64), b.astype(np.float64)
+    want, ss = oracle.drop_sweep(s.row_ptr, s.col, val64, b64, bp, x0, 1.1)
+    assert rel_l2(got, want) < 1e-6
+    np.testing.assert_allclose(res, ss, rtol=1e-4, atol=1e-12)
+    ref = np.array([val64[s.row_ptr[i]:s.row_ptr[i + 1]] @ x0[s.col[s.row_ptr[i]:s.row_ptr[i + 1]]] for i in range(M)])
+    np.testing.assert_allclose(proj, ref, rtol=1e-5, atol=1e-6 * np.abs(ref).max())
+
+
 def test_pipeline_stages_stay_inside_exact_sized_arrays():
     """The pipelined schedule copies stages of whole rows with 16-byte aligned bulk copies;
     with BF16 values and int32 columns (8-entry alignment) and nnz not a multiple of 8, the
