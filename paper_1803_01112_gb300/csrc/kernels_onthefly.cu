@@ -212,10 +212,11 @@ __global__ void otf_rows_kernel(const float* __restrict__ paths, int64_t M, Grid
 // The dot-product pass keeps the first kOtfCache accepted pieces of each lane (voxel,
 // length) in shared memory, and the scatter pass replays them; a lane with more pieces
 // traces its segments again and scatters only the pieces past the cached ones.
+// Four CTAs per SM: 64 registers per thread (no spills) and 4 x 48 KB of piece caches.
 constexpr int kOtfThreads = 256;
 constexpr int kOtfCache = 24;
 
-__global__ void __launch_bounds__(kOtfThreads) otf_drop_kernel(const float* __restrict__ paths,
+__global__ void __launch_bounds__(kOtfThreads, 4) otf_drop_kernel(const float* __restrict__ paths,
                                                                 const float* __restrict__ b,
                                                                 const float* __restrict__ inv_norm2, int64_t r0,
                                                                 int64_t r1, Grid3 g, int n_seg, float min_len,
