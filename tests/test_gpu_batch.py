@@ -245,6 +245,38 @@ def test_batch_schedules_agree(rows, window):
         assert rel_l2(img, ref.x) <= 1e-5
 
 
+def test_batch_window_rows_above_the_bound_go_global():
+    """The shared window holds int32 multiples of a quantum scaled by a bound on |r_i/lambda|
+    (seeded with max_i |b_i| / ||a_i||^2, the residual at x = 0, then twice the previous
+    sweep's largest).  Starting from x0 = -5 xbar every residual of the first sweep is about
+    six times the seed, so those rows must scatter to global memory; later sweeps take the
+    bound from what they saw.  The images stay the oracle's."""
+    ntvs = ntvs_module()
+    K = 3
+    members = _members()[:3]
+    bt = ntvs.Batch(0)
+    x0s = []
+    try:
+        for s, prm in members:
+            x0 = -5.0 * s.xbar
+            x0s.append(x0)
+            bt.add((s.spec.nx, s.spec.ny, s.spec.nz), s.row_ptr, s.col, s.val.astype(np.float32),
+                   s.b.astype(np.float32), s.spec.n_blocks,
+                   ntvs.Params(lam=prm.lam, N=prm.N, alpha=prm.alpha, beta0=prm.beta0, seed=prm.seed,
+                               eps_tv=prm.eps_tv), x0)
+        bt.set_schedule(rows_per_item=128, window_floats=8192)
+        bt.finalize(max_cycles=K)
+        bt.run(K)
+        imgs = [bt.get_image(i) for i in range(len(members))]
+    finally:
+        bt.close()
+    for (s, prm), img, x0 in zip(members, imgs, x0s):
+        shape = (s.spec.nx, s.spec.ny, s.spec.nz)
+        v64, b64 = s.val.astype(np.float32).astype(np.float64), s.b.astype(np.float32).astype(np.float64)
+        ref = oracle.ntvs(s.row_ptr, s.col, v64, b64, s.block_ptr(), shape, prm, K, x0)
+        assert rel_l2(img, ref.x) <= 1e-5
+
+
 def test_batch_members_from_paths_match_oracle():
     """Members traced on the device from path records: their stored rows (read back) are
     valid intersection-length rows, and each member equals the oracle run on those rows."""
