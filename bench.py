@@ -508,6 +508,8 @@ def run_onthefly_variant(args, ntvs, local, stream, world, device):
     return {"name": "on-the-fly rows, 256x256x64, 720 angles, 40 blocks, N=4",
             "value": world * spec.n_hist * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
             "histories": spec.n_hist, "drop_launch_ms": avg,
+            "kernel_ms_per_step": {k: prof[k] for k in ("drop_block_ms", "drop_apply_ms", "tv_ms")},
+            "tv_share": prof["tv_ms"] / max(prof["drop_block_ms"] + prof["drop_apply_ms"] + prof["tv_ms"], 1e-12),
             "hbm_gb_s_per_drop_launch": hbm_bytes / (avg / 1e3) / 1e9,
             "bound": "alu + L2 atomics (path tracing; 60 B of HBM per history and launch)",
             "ncu_fractions": otf_profile_fractions(),
