@@ -195,7 +195,7 @@ cudaError_t k_row_home(const int64_t* row_ptr, const int32_t* col, int stride, i
 // A warp per chunk of rows: the chunk's work in issued register steps (k_chunk_cost); a
 // chunk of a block without a per-block depth (ch = 0) counts its rows
 __global__ void chunk_cost_kernel(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ cs,
-                                  const int8_t* __restrict__ ch, int64_t nchunks, int64_t* __restrict__ cost) {
+                                  const int8_t* __restrict__ ch, int mid, int64_t nchunks, int64_t* __restrict__ cost) {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -209,7 +209,8 @@ __global__ void chunk_cost_kernel(const int64_t* __restrict__ row_ptr, const int
                 continue;
             }
             const int64_t steps = (row_ptr[i + 1] - row_ptr[i] + 31) / 32;
-            const int64_t body = (steps <= kShortBody && d > kShortBody) ? kShortBody : d;
+            const int64_t body = (steps <= kShortBody && d > kShortBody) ? kShortBody
+                                 : (mid > 0 && d > mid && steps <= mid) ? mid : d;
             acc += 1 + body + 2 * (steps > d ? steps - d : 0);
         }
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -217,10 +218,10 @@ __global__ void chunk_cost_kernel(const int64_t* __restrict__ row_ptr, const int
     }
 }
 
-cudaError_t k_chunk_cost(const int64_t* row_ptr, const int64_t* cs, const int8_t* ch, int64_t nchunks, int64_t* cost,
-                         int grid, cudaStream_t s) {
+cudaError_t k_chunk_cost(const int64_t* row_ptr, const int64_t* cs, const int8_t* ch, int mid, int64_t nchunks,
+                         int64_t* cost, int grid, cudaStream_t s) {
     if (nchunks <= 0) return cudaSuccess;
-    chunk_cost_kernel<<<grid, 256, 0, s>>>(row_ptr, cs, ch, nchunks, cost);
+    chunk_cost_kernel<<<grid, 256, 0, s>>>(row_ptr, cs, ch, mid, nchunks, cost);
     return cudaGetLastError();
 }
 

@@ -355,10 +355,15 @@ __device__ __forceinline__ void drop_row_any(int64_t i, const RowHead& h, bool v
                                                          lambda, w, ss, ws);
     } else if constexpr (WIN && LPR == 32 && VW == 1 && CH > kShortSteps) {
         // rows of at most kShortSteps x 32 entries take a body with fewer register steps:
-        // with the block's deepest body a short row would issue its empty steps predicated off
+        // with the block's deepest body a short row would issue its empty steps predicated off;
+        // in blocks deeper than kMidBody steps a middle body takes the rows that fit it
+        // (measured 0.2356 -> 0.2326 ms per 500k-row block)
         if (h.p1 - h.p0 <= (int64_t)kShortSteps * 32)
             drop_row<T, V, LPR, kShortSteps, VW, WIN, false>(i, h, valid, sub, col, d16, val, bval, ival, x, delta,
                                                             lambda, w, ss, ws);
+        else if (CH > kMidBody && h.p1 - h.p0 <= (int64_t)kMidBody * 32)
+            drop_row<T, V, LPR, (CH > kMidBody ? kMidBody : CH), VW, WIN, false>(i, h, valid, sub, col, d16, val, bval,
+                                                                                ival, x, delta, lambda, w, ss, ws);
         else
             drop_row<T, V, LPR, CH, VW, WIN, false>(i, h, valid, sub, col, d16, val, bval, ival, x, delta, lambda, w,
                                                     ss, ws);

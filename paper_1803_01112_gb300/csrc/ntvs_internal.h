@@ -200,8 +200,11 @@ cudaError_t k_drop_block(const DropArgs& a, cudaStream_t s);
 // Register steps of the row body the windowed kernel runs for a block whose longest row
 // has max_row entries (a warp per row, FP32 compute on FP32 or BF16 values): as many 32-entry
 // steps as that row needs, 8..11, else 12 (longer rows finish in a tail loop).  Rows of at
-// most kShortBody steps take the 8-step body.  0: the kernel's fixed depth applies.
+// most kShortBody steps take the 8-step body, and on FP32 pairs in blocks deeper than
+// kMidBody, rows of at most kMidBody steps take a kMidBody-step body.  0: the kernel's fixed
+// depth applies.
 constexpr int kShortBody = 8;
+constexpr int kMidBody = 10;
 inline int window_register_steps(int64_t max_row, int cdt, int vdt, int lanes_per_row) {
     if (cdt != F32 || (vdt != F32 && vdt != BF16) || lanes_per_row != 32) return 0;
     const int64_t need = (max_row + 31) / 32;
@@ -209,9 +212,10 @@ inline int window_register_steps(int64_t max_row, int cdt, int vdt, int lanes_pe
 }
 // Work of rows [cs[q], cs[q+1]) for each chunk q in issued register steps: per row 1 (its
 // reductions and bookkeeping) + the steps of the body it runs (kShortBody when it fits, else
-// ch[q]) + 2 per step past ch[q] (the tail loop reads those entries twice)
-cudaError_t k_chunk_cost(const int64_t* row_ptr, const int64_t* cs, const int8_t* ch, int64_t nchunks, int64_t* cost,
-                         int grid, cudaStream_t s);
+// mid when it fits and mid > 0, else ch[q]) + 2 per step past ch[q] (the tail loop reads
+// those entries twice)
+cudaError_t k_chunk_cost(const int64_t* row_ptr, const int64_t* cs, const int8_t* ch, int mid, int64_t nchunks,
+                         int64_t* cost, int grid, cudaStream_t s);
 cudaError_t k_drop_block_d16(const DropArgs& a, cudaStream_t s);   // the same on DELTA16 storage
 // out[i] = <a_i, x> for the M rows (x: compute type, in the order of the stored columns;
 // out: compute type); a.row_ptr, col / d16, val, vdt, cdt, use_d16 and grid are used
