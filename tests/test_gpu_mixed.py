@@ -66,6 +66,39 @@ def test_delta16_with_many_escaped_jumps():
 
 
 @pytest.mark.parametrize("schedule", ["plain", "window", "pipeline"])
+@pytest.mark.parametrize("kind", ["fp16", "bf16"])
+def test_delta16_words_match_oracle_on_stored_system(schedule, kind):
+    """DELTA16 with 16-bit values keeps each entry as one 32-bit word (offset in the low
+    half, the value's bits in the high half).  Every schedule that reads the words, the TMA
+    pipeline's single-array ring included, gives the oracle's sweep on the quantized system,
+    and the projection of the stored rows equals the oracle's."""
+    ntvs = ntvs_module()
+    from paper_1803_01112_gb300._ffi import NTVS_DELTA16, NTVS_SCHED_PIPELINE, NTVS_SCHED_PLAIN, NTVS_SCHED_WINDOW
+    sched = {"plain": NTVS_SCHED_PLAIN, "window": NTVS_SCHED_WINDOW, "pipeline": NTVS_SCHED_PIPELINE}[schedule]
+    s = synth.generate(synth.spec_scaled_3d(nx=40, ny=40, nz=6, n_hist=30_000, n_angles=36, n_blocks=4, seed=12))
+    vq, v64 = quantize(s.val, kind)
+    b = s.b.astype(np.float32)
+    x0 = s.xstar * 0.9 + 0.05
+    r = ntvs.Reconstructor(0)
+    try:
+        r.load((40, 40, 6), s.row_ptr, s.col, vq, b, n_blocks=4, storage=NTVS_DELTA16, schedule=sched)
+        st = r.stats()
+        proj = r.forward_project(x0)
+        r.set_params(lam=1.2, N=0, alpha=0.5)
+        r.set_image(x0)
+        r.drop_sweep()
+        got = r.get_image()
+    finally:
+        r.close()
+    assert st["drop_schedule"] == sched
+    want, _ = oracle.drop_sweep(s.row_ptr, s.col, v64, b.astype(np.float64), s.block_ptr(), x0, 1.2)
+    assert rel_l2(got, want) < 1e-6
+    M = s.M
+    ref = np.array([v64[s.row_ptr[i]:s.row_ptr[i + 1]] @ x0[s.col[s.row_ptr[i]:s.row_ptr[i + 1]]] for i in range(M)])
+    np.testing.assert_allclose(proj, ref, rtol=1e-5, atol=1e-6 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("schedule", ["plain", "window", "pipeline"])
 def test_delta16_chunks_mix_packed_and_escaped(schedule):
     """Rows of slowly varying columns with rare far jumps: rows without a jump are narrow (one
     base), in the others most 32-entry chunks are stored as base + 16-bit offsets and the
