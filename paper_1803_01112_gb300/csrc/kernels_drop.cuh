@@ -344,6 +344,9 @@ __device__ __forceinline__ void drop_row_any(int64_t i, const RowHead& h, bool v
             if (CH > kShortSteps && h.p1 - h.p0 <= (int64_t)kShortSteps * 32)
                 drop_row<T, V, LPR, (CH > kShortSteps ? kShortSteps : CH), VW, WIN, true, false, true>(
                     i, h, valid, sub, col, d16, val, bval, ival, x, delta, lambda, w, ss, ws, rbase);
+            else if (CH > kMidBody && h.p1 - h.p0 <= (int64_t)kMidBody * 32)   // 0.2681 -> 0.2657 ms
+                drop_row<T, V, LPR, (CH > kMidBody ? kMidBody : CH), VW, WIN, true, false, true>(
+                    i, h, valid, sub, col, d16, val, bval, ival, x, delta, lambda, w, ss, ws, rbase);
             else
                 drop_row<T, V, LPR, CH, VW, WIN, true, false, true>(i, h, valid, sub, col, d16, val, bval, ival, x,
                                                                    delta, lambda, w, ss, ws, rbase);

@@ -200,8 +200,8 @@ cudaError_t k_drop_block(const DropArgs& a, cudaStream_t s);
 // Register steps of the row body the windowed kernel runs for a block whose longest row
 // has max_row entries (a warp per row, FP32 compute on FP32 or BF16 values): as many 32-entry
 // steps as that row needs, 8..11, else 12 (longer rows finish in a tail loop).  Rows of at
-// most kShortBody steps take the 8-step body, and on FP32 pairs in blocks deeper than
-// kMidBody, rows of at most kMidBody steps take a kMidBody-step body.  0: the kernel's fixed
+// most kShortBody steps take the 8-step body, and in blocks deeper than kMidBody rows of at
+// most kMidBody steps take a kMidBody-step body (CSR32 rows and narrow DELTA16 rows).  0: the kernel's fixed
 // depth applies.
 constexpr int kShortBody = 8;
 constexpr int kMidBody = 10;
