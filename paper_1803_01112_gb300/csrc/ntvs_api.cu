@@ -757,18 +757,27 @@ static int plan_schedule(ntvs_ctx* c, int requested) {
         const int8_t d = (int8_t)window_register_steps(mr, c->cdt, c->vdt, c->lpr);
         for (int64_t q = block_chunk[t]; q < block_chunk[t + 1]; ++q) chunk_ch[(size_t)q] = d;
     }
-    int32_t* dhome = nullptr;
-    int32_t* dchunk = nullptr;
-    int64_t* dstart = nullptr;
-    unsigned long long* dchanges = nullptr;
-    int8_t* dch = nullptr;
-    int64_t* dcost = nullptr;
-    TRY(dev_alloc(&dhome, sizeof(int32_t) * (size_t)c->M, "row home slices"));
-    TRY(dev_alloc(&dchunk, sizeof(int32_t) * (size_t)std::max<int64_t>(nch, 1), "chunk home slices"));
-    TRY(dev_alloc(&dstart, sizeof(int64_t) * cstart.size(), "chunk starts"));
-    TRY(dev_alloc(&dchanges, sizeof(unsigned long long), "home changes"));
-    TRY(dev_alloc(&dch, chunk_ch.size(), "chunk body depths"));
-    TRY(dev_alloc(&dcost, sizeof(int64_t) * (size_t)std::max<int64_t>(nch, 1), "chunk costs"));
+    // the planning's device temporaries in one allocation (each free synchronizes the device)
+    const size_t nchp = (size_t)std::max<int64_t>(nch, 1);
+    auto up256 = [](size_t n) { return (n + 255) & ~(size_t)255; };
+    const size_t o_home = 0, o_chunk = o_home + up256(sizeof(int32_t) * (size_t)c->M);
+    const size_t o_start = o_chunk + up256(sizeof(int32_t) * nchp);
+    const size_t o_changes = o_start + up256(sizeof(int64_t) * cstart.size());
+    const size_t o_ch = o_changes + up256(sizeof(unsigned long long));
+    const size_t o_cost = o_ch + up256(chunk_ch.size());
+    const size_t scratch_bytes = o_cost + up256(sizeof(int64_t) * nchp);
+    char* scratch = nullptr;
+    TRY(dev_alloc(&scratch, scratch_bytes, "schedule planning scratch"));
+    struct FreeScratch {
+        char*& p;
+        ~FreeScratch() { dev_free(p); }
+    } scratch_guard{scratch};
+    int32_t* dhome = reinterpret_cast<int32_t*>(scratch + o_home);
+    int32_t* dchunk = reinterpret_cast<int32_t*>(scratch + o_chunk);
+    int64_t* dstart = reinterpret_cast<int64_t*>(scratch + o_start);
+    unsigned long long* dchanges = reinterpret_cast<unsigned long long*>(scratch + o_changes);
+    int8_t* dch = reinterpret_cast<int8_t*>(scratch + o_ch);
+    int64_t* dcost = reinterpret_cast<int64_t*>(scratch + o_cost);
     std::vector<int32_t> chome((size_t)nch);
     std::vector<int64_t> ccost((size_t)nch);
     unsigned long long changes = 0;
@@ -790,12 +799,6 @@ static int plan_schedule(ntvs_ctx* c, int requested) {
         e = cudaMemcpyAsync(ccost.data(), dcost, sizeof(int64_t) * (size_t)nch, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&changes, dchanges, sizeof(changes), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    dev_free(dhome);
-    dev_free(dchunk);
-    dev_free(dstart);
-    dev_free(dchanges);
-    dev_free(dch);
-    dev_free(dcost);
     if (e != cudaSuccess) return fail(NTVS_ERR_CUDA, cuda_msg("row home slices", e));
     int32_t last = 0;
     for (auto& h : chome) {   // chunks of empty rows join their predecessor's run
