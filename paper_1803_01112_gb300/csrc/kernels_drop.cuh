@@ -44,11 +44,16 @@ __device__ __forceinline__ void load4(const __nv_bfloat16* p, float (&o)[4]) {
     o[0] = f0.x; o[1] = f0.y; o[2] = f1.x; o[3] = f1.y;
 }
 
-// The windowed kernel's dynamic shared memory: the stage of the current run of kRowStage
-// rows (row pointers, b, 1/||a||^2) at fixed offsets, then the slice window, voxels
-// [w0, w0 + W).  Fixed offsets keep the addresses out of the row loop's registers.
+// The windowed kernel's dynamic shared memory: the stage of the current run of
+// row_stage<D16>() rows (row pointers, b, 1/||a||^2) at fixed offsets, then the slice
+// window, voxels [w0, w0 + W).  Fixed offsets keep the addresses out of the row loop's
+// registers.  DELTA16 rows stage 5 more bytes each, so their stage is shorter: with the
+// 160 KB window of a 200x200 slice both fit the 196 KB shared-memory carve-out, and the
+// x gathers keep the L1 that a larger allocation would take (2048 DELTA16 rows measured
+// 0.2652 against 0.2588 ms with 1600; FP32 rows 0.2346 with 1600 against 0.2329 with 2048).
 extern __shared__ __align__(16) unsigned char drop_win_smem[];
-constexpr int kRowStage = 2048;   // rows staged at once by the windowed kernel
+template <bool D16>
+__host__ __device__ constexpr int row_stage() { return D16 ? 1600 : 2048; }   // rows staged at once
 constexpr int kPrefetchRows = 1;  // the windowed kernel asks L2 for the entries of the row this many ahead
 constexpr int kShortSteps = kShortBody;   // register steps of the windowed kernel's body for short rows
 
@@ -70,29 +75,29 @@ __device__ __forceinline__ void prefetch_lines_l2(const E* a, int64_t q0, int64_
     const int na = (int)((a1 - a0 + 127) >> 7);
     if (lane < na) asm volatile("prefetch.global.L2 [%0];" ::"l"(a0 + ((uintptr_t)lane << 7)));
 }
-template <typename T>
+template <typename T, bool D16>
 __host__ __device__ constexpr size_t stage_bytes() {
-    return ((sizeof(int64_t) * (kRowStage + 1) + 15) & ~(size_t)15) + 2 * sizeof(T) * kRowStage;
+    return ((sizeof(int64_t) * (row_stage<D16>() + 1) + 15) & ~(size_t)15) + 2 * sizeof(T) * row_stage<D16>();
 }
 // DELTA16 rows also stage their flags (1 byte) and their first chunk base (the base of a
 // narrow row), so that neither is a dependent global load at the start of a row
 template <typename T, bool D16>
 __host__ __device__ constexpr size_t stage_bytes_all() {
-    return stage_bytes<T>() + (D16 ? ((size_t)kRowStage + 4 * (size_t)kRowStage) : 0);
+    return stage_bytes<T, D16>() + (D16 ? ((size_t)row_stage<D16>() + 4 * (size_t)row_stage<D16>()) : 0);
 }
-template <typename T>
+template <typename T, bool D16>
 __device__ __forceinline__ int64_t* stage_rp() { return reinterpret_cast<int64_t*>(drop_win_smem); }
-template <typename T>
+template <typename T, bool D16>
 __device__ __forceinline__ T* stage_b() {
-    return reinterpret_cast<T*>(drop_win_smem + ((sizeof(int64_t) * (kRowStage + 1) + 15) & ~(size_t)15));
+    return reinterpret_cast<T*>(drop_win_smem + ((sizeof(int64_t) * (row_stage<D16>() + 1) + 15) & ~(size_t)15));
 }
-template <typename T>
-__device__ __forceinline__ T* stage_inv() { return stage_b<T>() + kRowStage; }
-template <typename T>
-__device__ __forceinline__ uint8_t* stage_fl() { return drop_win_smem + stage_bytes<T>(); }
-template <typename T>
+template <typename T, bool D16>
+__device__ __forceinline__ T* stage_inv() { return stage_b<T, D16>() + row_stage<D16>(); }
+template <typename T, bool D16>
+__device__ __forceinline__ uint8_t* stage_fl() { return drop_win_smem + stage_bytes<T, D16>(); }
+template <typename T, bool D16>
 __device__ __forceinline__ int32_t* stage_rb() {
-    return reinterpret_cast<int32_t*>(drop_win_smem + stage_bytes<T>() + kRowStage);
+    return reinterpret_cast<int32_t*>(drop_win_smem + stage_bytes<T, D16>() + row_stage<D16>());
 }
 template <typename T, bool D16>
 __device__ __forceinline__ unsigned char* window_base() { return drop_win_smem + stage_bytes_all<T, D16>(); }
@@ -499,21 +504,21 @@ drop_block_window_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __r
             w.w0 = (int)(cur * slice);
         }
         const int grp = lane / LPR;
-        // the segment's rows in runs of kRowStage: one coalesced load of their row
+        // the segment's rows in runs of row_stage<D16>(): one coalesced load of their row
         // pointers, b and 1/||a||^2 into shared memory, so that a row starts from its
         // entries' addresses instead of a round trip to HBM for its row pointer
-        for (int64_t c0 = sg.r0; c0 < sg.r1; c0 += kRowStage) {
-            const int n = (int)min((int64_t)kRowStage, sg.r1 - c0);
+        for (int64_t c0 = sg.r0; c0 < sg.r1; c0 += row_stage<D16>()) {
+            const int n = (int)min((int64_t)row_stage<D16>(), sg.r1 - c0);
             __syncthreads();   // the previous run's rows are done with the stage
             for (int j = threadIdx.x; j <= n; j += blockDim.x) {
                 const int64_t rp = __ldg(row_ptr + c0 + j);
-                stage_rp<T>()[j] = rp;
+                stage_rp<T, D16>()[j] = rp;
                 if (j < n) {
-                    stage_b<T>()[j] = __ldg(b + c0 + j);
-                    stage_inv<T>()[j] = __ldg(inv_norm2 + c0 + j);
+                    stage_b<T, D16>()[j] = __ldg(b + c0 + j);
+                    stage_inv<T, D16>()[j] = __ldg(inv_norm2 + c0 + j);
                     if constexpr (D16) {
-                        stage_fl<T>()[j] = __ldg(d16.rowesc + c0 + j);
-                        stage_rb<T>()[j] = __ldg(d16.cbase + (rp >> 5) + c0 + j);   // the row's first chunk base
+                        stage_fl<T, D16>()[j] = __ldg(d16.rowesc + c0 + j);
+                        stage_rb<T, D16>()[j] = __ldg(d16.cbase + (rp >> 5) + c0 + j);   // the row's first chunk base
                     }
                 }
             }
@@ -524,12 +529,12 @@ drop_block_window_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __r
                 if constexpr (kPrefetchRows > 0 && LPR == 32) {
                     const int kp = k + kPrefetchRows * nwarps;   // this warp's row that many iterations ahead
                     if (kp < n) {
-                        const int64_t q0 = stage_rp<T>()[kp], q1 = stage_rp<T>()[kp + 1];
+                        const int64_t q0 = stage_rp<T, D16>()[kp], q1 = stage_rp<T, D16>()[kp + 1];
                         if constexpr (D16) {
                             if constexpr (delta16_words<V, D16>()) prefetch_lines_l2(d16.word, q0, q1, lane);
                             else prefetch_row_l2(d16.off, val, q0, q1, lane);
                             // and the chunk bases of a row that is not narrow (one short run)
-                            if (lane == 31 && !(stage_fl<T>()[kp] & 2))
+                            if (lane == 31 && !(stage_fl<T, D16>()[kp] & 2))
                                 asm volatile("prefetch.global.L2 [%0];" ::"l"(d16.cbase + (q0 >> 5) + c0 + kp));
                         } else if constexpr (packed_entries<V, D16>()) {
                             prefetch_lines_l2(reinterpret_cast<const int2*>(col), q0, q1, lane);
@@ -538,11 +543,11 @@ drop_block_window_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __r
                         }
                     }
                 }
-                const RowHead h{valid ? stage_rp<T>()[k] : 0, valid ? stage_rp<T>()[k + 1] : 0};
+                const RowHead h{valid ? stage_rp<T, D16>()[k] : 0, valid ? stage_rp<T, D16>()[k + 1] : 0};
                 drop_row_any<T, V, LPR, CH, VW, true, D16>(
-                    c0 + k, h, valid, lane % LPR, col, d16, val, valid ? stage_b<T>()[k] : (T)0,
-                    valid ? stage_inv<T>()[k] : (T)0, x, delta, lambda, w, ss_grp[warp][grp], &ws,
-                    D16 ? (valid ? (int)stage_fl<T>()[k] : 0) : -1, (D16 && valid) ? stage_rb<T>()[k] : 0);
+                    c0 + k, h, valid, lane % LPR, col, d16, val, valid ? stage_b<T, D16>()[k] : (T)0,
+                    valid ? stage_inv<T, D16>()[k] : (T)0, x, delta, lambda, w, ss_grp[warp][grp], &ws,
+                    D16 ? (valid ? (int)stage_fl<T, D16>()[k] : 0) : -1, (D16 && valid) ? stage_rb<T, D16>()[k] : 0);
             }
         }
     }
