@@ -299,12 +299,15 @@ int ntvs_get_profile(ntvs_ctx* ctx, ntvs_profile* out);
  * of tx x ty voxels (each tile contiguous, slices contiguous), and the stored columns are
  * rewritten into that order on the device (into a buffer of the context's own when the
  * caller's columns are device memory: they are never modified).  Rows of a proton history
- * then touch fewer distinct cache lines per slice.  The results are those of the
- * canonical order up to the order of floating-point accumulation; images, gradients and
- * every other public array stay canonical.  tx, ty in {1, 2, 4, 8, 16}; 1 x 1 is the
- * canonical order; the default is 4 x 4.  It applies to ntvs_load_paths and
- * ntvs_load_histories too (the traced voxel indices are formed in that order); the FP64
- * path always uses the canonical order.  This layout has no counterpart in the paper.
+ * then touch fewer distinct cache lines per slice.  For stored systems the in-slice
+ * offsets are also permuted inside each aligned group of 32 (the shared-memory bank
+ * spread of the slice-windowed DROP kernels; a group stays on its 128-byte line).  The
+ * results are those of the canonical order up to the order of floating-point
+ * accumulation; images, gradients and every other public array stay canonical.  tx, ty
+ * in {1, 2, 4, 8, 16}; 1 x 1 leaves the in-plane order canonical; the default is 4 x 4.
+ * It applies to ntvs_load_paths and ntvs_load_histories too (the traced voxel indices are
+ * formed in the tiled order, without the in-group permutation); the FP64 path always uses
+ * the canonical order.  This layout has no counterpart in the paper.
  * NTVS_ERR_ARG on other sizes. */
 int ntvs_set_voxel_tile(ntvs_ctx* ctx, int tx, int ty);
 

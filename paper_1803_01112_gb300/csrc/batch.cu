@@ -714,8 +714,10 @@ __global__ void remap_kernel(int32_t* __restrict__ col, int64_t nnz, VoxMap vm) 
 
 // canonical index of internal slot p (the inverse of vox_internal on real voxels)
 __device__ __forceinline__ int64_t vox_canonical(const VoxMap& m, int64_t p) {
-    if (m.tx == 1 && m.ty == 1) return p;
-    const int64_t iz = p / m.slice_p, rem = p - iz * m.slice_p;
+    if (m.tx == 1 && m.ty == 1 && !m.sw) return p;
+    const int64_t iz = p / m.slice_p;
+    int64_t rem = p - iz * m.slice_p;
+    if (m.sw) rem ^= (rem >> 5) & 31;   // the swizzle is its own inverse
     const int64_t tile = rem >> (m.ltx + m.lty), in = rem & ((1 << (m.ltx + m.lty)) - 1);
     const int64_t ntx = m.nxp >> m.ltx;
     const int64_t ty = tile / ntx, tx = tile - ty * ntx;

@@ -35,14 +35,15 @@ __device__ __forceinline__ double step_scale(double beta, const double* gnorm2) 
 // internal index of canonical voxel j (see VoxMap); 32-bit arithmetic, as every index
 // of either order is below 2^31
 __device__ __forceinline__ int64_t vox_internal(const VoxMap& m, int64_t j) {
-    if (m.tx == 1 && m.ty == 1) return j;
+    if (m.tx == 1 && m.ty == 1 && !m.sw) return j;
     const uint32_t u = (uint32_t)j, nx = (uint32_t)m.nx, ny = (uint32_t)m.ny;
     const uint32_t t = u / nx, ix = u - t * nx;
     const uint32_t iz = t / ny, iy = t - iz * ny;
     const uint32_t ntx = (uint32_t)m.nxp >> m.ltx;
     const uint32_t tile = (iy >> m.lty) * ntx + (ix >> m.ltx);
-    return (int64_t)(iz * (uint32_t)m.slice_p + (tile << (m.ltx + m.lty)) +
-                     ((iy & (uint32_t)(m.ty - 1)) << m.ltx) + (ix & (uint32_t)(m.tx - 1)));
+    uint32_t p = (tile << (m.ltx + m.lty)) + ((iy & (uint32_t)(m.ty - 1)) << m.ltx) + (ix & (uint32_t)(m.tx - 1));
+    if (m.sw) p ^= (p >> 5) & 31u;
+    return (int64_t)(iz * (uint32_t)m.slice_p + p);
 }
 
 // the FP32 copies of master value v of canonical voxel j

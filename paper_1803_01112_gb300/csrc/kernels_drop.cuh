@@ -123,10 +123,18 @@ struct WinScale {
     unsigned obs;
 };
 
-// Shared-memory slot of window offset j: the low 5 bits are XORed with the next 5, a
-// bijection inside each group of 32 slots.  Paths along y step the offset by nx (200: 8
-// mod 32), which without the swizzle puts a warp's 32 updates into 4 banks.
+// Shared-memory slot of window offset j.  Paths along y step the offset by nx (200: 8
+// mod 32), which with slot = offset puts a warp's 32 updates into 4 banks; XORing the low
+// 5 bits with the next 5 (a bijection inside each group of 32 slots) spreads them.  The
+// FP32 path's internal voxel order already carries that swizzle inside each slice (the
+// window starts at a slice), so its slot is the offset itself; the FP64 path gathers the
+// canonical order and swizzles here.
 __device__ __forceinline__ int swz(int j) { return j ^ ((j >> 5) & 31); }
+template <typename T>
+__device__ __forceinline__ int win_slot(int j) {
+    if constexpr (sizeof(T) == 4) return j;
+    else return swz(j);
+}
 
 // delta_c += r * a.  In the window: FP32 compute adds round(rq * a) (rq = r / Q) to the
 // int32 fixed-point slot with a native shared-memory integer atomic when the row is
@@ -140,11 +148,11 @@ __device__ __forceinline__ void scatter(T* delta, const Window& w, int32_t c, T 
             if constexpr (sizeof(T) == 4) {
                 if (rowfix) {   // |rq a| < 2^22: adding 1.5 * 2^23 rounds it to the nearest integer
                     const int y = __float_as_int(fmaf(rq, (float)a, 12582912.0f)) - 0x4B400000;
-                    atomicAdd(reinterpret_cast<int*>(window_base<T, D16>()) + swz(rel), y);
+                    atomicAdd(reinterpret_cast<int*>(window_base<T, D16>()) + win_slot<T>(rel), y);
                     return;
                 }
             } else {
-                atomicAdd(reinterpret_cast<T*>(window_base<T, D16>()) + swz(rel), r * a);
+                atomicAdd(reinterpret_cast<T*>(window_base<T, D16>()) + win_slot<T>(rel), r * a);
                 return;
             }
         }
@@ -411,7 +419,7 @@ drop_block_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict
 }
 
 // Windowed variant: CTA b processes segments [seg_begin[b], seg_begin[b+1]) in order.
-// The window holds Wp = W rounded up to 32 slots (swizzled); slots past W stay 0.  FP32
+// The window holds Wp = W rounded up to 32 slots (win_slot); slots past W stay 0.  FP32
 // compute keeps int32 multiples of the quantum Q, FP64 compute doubles.
 // 4 consecutive floats added to global memory with one vector reduction (16-byte aligned)
 __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
@@ -422,27 +430,23 @@ template <typename T>
 __device__ __forceinline__ void flush_window(void* winp, int W, int Wp, T* delta, int w0, float Q) {
     if constexpr (sizeof(T) == 4) {
         int* win = reinterpret_cast<int*>(winp);
+        // slot j holds voxel w0 + j (win_slot<float> is the identity)
         if (((w0 | W) & 3) == 0 && ((uintptr_t)delta & 15) == 0) {
-            // Four voxel offsets j..j+3 (j a multiple of 4) lie in one group of 32 slots,
-            // and swz maps them to the aligned slots swz(j) & ~3 in the order
-            // e -> (swz(j) & 3) ^ e: one 16-byte shared load and one vector reduction each
+            // one 16-byte shared load and one vector reduction per four voxels
             for (int j = 4 * threadIdx.x; j < W; j += 4 * blockDim.x) {
-                const int sj = swz(j);
-                int4* slot = reinterpret_cast<int4*>(win + (sj & ~3));
+                int4* slot = reinterpret_cast<int4*>(win + j);
                 const int4 v4 = *slot;
                 if ((v4.x | v4.y | v4.z | v4.w) == 0) continue;
-                const int v[4] = {v4.x, v4.y, v4.z, v4.w};
-                const int k = sj & 3;
-                red_add_v4(reinterpret_cast<float*>(delta) + w0 + j, (float)v[k] * Q, (float)v[k ^ 1] * Q,
-                           (float)v[k ^ 2] * Q, (float)v[k ^ 3] * Q);
+                red_add_v4(reinterpret_cast<float*>(delta) + w0 + j, (float)v4.x * Q, (float)v4.y * Q,
+                           (float)v4.z * Q, (float)v4.w * Q);
                 *slot = make_int4(0, 0, 0, 0);
             }
             return;
         }
-        for (int jj = threadIdx.x; jj < Wp; jj += blockDim.x) {
+        for (int jj = threadIdx.x; jj < W; jj += blockDim.x) {
             const int v = win[jj];
             if (v != 0) {
-                atomicAdd(delta + w0 + swz(jj), (float)v * Q);
+                atomicAdd(delta + w0 + jj, (float)v * Q);
                 win[jj] = 0;
             }
         }

@@ -74,12 +74,19 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
-__device__ __forceinline__ int swz(int j) { return j ^ ((j >> 5) & 31); }
+// window slot of slice offset j: the FP32 path's internal voxel order carries the bank
+// swizzle inside each slice already; the FP64 path (canonical order) XORs the low 5 bits
+// with the next 5 here
+template <typename T>
+__device__ __forceinline__ int win_slot(int j) {
+    if constexpr (sizeof(T) == 4) return j;
+    else return j ^ ((j >> 5) & 31);
+}
 
 template <typename T>
 __device__ __forceinline__ void scatter_w(T* win, int W, int64_t w0, T* delta, int32_t c, T v) {
     const int64_t rel = (int64_t)c - w0;
-    if ((uint64_t)rel < (uint64_t)W) atomicAdd(win + swz((int)rel), v);
+    if ((uint64_t)rel < (uint64_t)W) atomicAdd(win + win_slot<T>((int)rel), v);
     else atomicAdd(delta + c, v);
 }
 
@@ -180,7 +187,7 @@ __device__ __forceinline__ void flush_w(T* win, int Wp, T* delta, int64_t w0, in
     for (int jj = tid; jj < Wp; jj += nthreads) {
         const T v = win[jj];
         if (v != (T)0) {
-            atomicAdd(delta + w0 + swz(jj), v);
+            atomicAdd(delta + w0 + win_slot<T>(jj), v);   // the slot map is its own inverse
             win[jj] = (T)0;
         }
     }

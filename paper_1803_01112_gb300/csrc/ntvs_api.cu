@@ -1076,11 +1076,16 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
     c->vdt = s->val_dtype;
     c->cdt = (s->val_dtype == NTVS_F64 || (s->val_dtype == NTVS_F32 && c->compute_req == F64)) ? F64 : F32;
     c->storage = s->storage;
-    // the FP64 path gathers the canonical master image: no internal order there
-    c->vm = (c->cdt == F32) ? make_voxmap(s->nx, s->ny, s->nz, c->tile_req_x, c->tile_req_y)
-                            : make_voxmap(s->nx, s->ny, s->nz, 1, 1);
+    // the FP64 path gathers the canonical master image: no internal order there; the FP32
+    // path's order carries the slice windows' slot swizzle
+    if (c->cdt == F32) {
+        c->vm = make_voxmap(s->nx, s->ny, s->nz, c->tile_req_x, c->tile_req_y, true);
+        if (c->vm.vint > 0x7fffffffLL) c->vm = make_voxmap(s->nx, s->ny, s->nz, 1, 1, true);
+    } else {
+        c->vm = make_voxmap(s->nx, s->ny, s->nz, 1, 1);
+    }
     if (c->vm.vint > 0x7fffffffLL) c->vm = make_voxmap(s->nx, s->ny, s->nz, 1, 1);
-    const bool tiled = c->vm.tx != 1 || c->vm.ty != 1;
+    const bool reordered = voxmap_reorders(c->vm);
     const int64_t VI = c->vm.vint;
     cudaStream_t st = c->stream;
 
@@ -1201,10 +1206,10 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
         TRY(copy_in(&c->val, &c->own_val, s->val, vsz * (size_t)nnz, s->mem_kind, st, "val"));
     }
 
-    // validation; columns of the tiled order are rewritten into a buffer of the context's
+    // validation; columns of the internal order are rewritten into a buffer of the context's
     // own (caller memory is never modified)
     CUDA_TRY(cudaMemsetAsync(c->dflags, 0, sizeof(int), st));
-    if (tiled && nnz > 0 && !piped) {
+    if (reordered && nnz > 0 && !piped) {
         if (!c->own_col) {
             int32_t* mine = nullptr;
             TRY(dev_alloc(&mine, sizeof(int32_t) * (size_t)nnz, "col (internal order)"));
@@ -1255,7 +1260,7 @@ int ntvs_load_system(ntvs_ctx* c, const ntvs_system* s) {
             bc = block_col(t);
             bv = block_val(t);
             e0 = eb[t];
-            if (tiled) CUDA_TRY(k_remap_cols(bc, bc, eb[t + 1] - eb[t], c->vm, c->dflags, st));
+            if (reordered) CUDA_TRY(k_remap_cols(bc, bc, eb[t + 1] - eb[t], c->vm, c->dflags, st));
         }
         if (colsum) CUDA_TRY(cudaMemsetAsync(colsum, 0, sizeof(float) * (size_t)VI, st));
         CUDA_TRY(k_prep_block(c->row_ptr, bc, bv, e0, c->vdt, c->b, bp[t], bp[t + 1], VI, c->inv_norm2, c->cdt,

@@ -16,20 +16,25 @@ inline size_t dt_size(int dt) { return dt == F64 ? 8 : dt == F32 ? 4 : 2; }
 
 // Internal voxel order of the FP32 gather copy, delta, hit counts and matrix columns:
 // in-plane tiles of tx x ty voxels, each tile contiguous, tiles row-major over a grid padded
-// to multiples of the tile, slices contiguous (slice_p voxels each).  tx = ty = 1 is the
-// canonical order (iz*ny + iy)*nx + ix.  Public images and the FP64 master stay canonical.
-// tx, ty are powers of two (ltx, lty their logarithms); V and vint stay below 2^31.
+// to multiples of the tile, slices contiguous (slice_p voxels each).  With sw set, the
+// in-slice offset p of that order is stored at p ^ ((p >> 5) & 31): a bijection inside
+// each aligned group of 32 offsets (slice_p is then a multiple of 32), which is the bank
+// spread of the DROP kernels' slice windows, so that their window slot is the voxel's
+// offset in its slice.  tx = ty = 1 without sw is the canonical order (iz*ny + iy)*nx + ix.
+// Public images and the FP64 master stay canonical.  tx, ty are powers of two (ltx, lty
+// their logarithms); V and vint stay below 2^31.
 struct VoxMap {
     int nx, ny, nz;
     int nxp, nyp;      // padded to multiples of tx, ty
     int tx, ty;
     int ltx, lty;
-    int64_t slice_p;   // nxp * nyp
+    int sw;            // 1: offsets swizzled inside each slice
+    int64_t slice_p;   // nxp * nyp, rounded up to a multiple of 32 with sw
     int64_t vint;      // nz * slice_p
 };
 
 // tx, ty powers of two
-inline VoxMap make_voxmap(int nx, int ny, int nz, int tx, int ty) {
+inline VoxMap make_voxmap(int nx, int ny, int nz, int tx, int ty, bool sw = false) {
     VoxMap m;
     m.nx = nx; m.ny = ny; m.nz = nz;
     m.tx = tx; m.ty = ty;
@@ -39,17 +44,24 @@ inline VoxMap make_voxmap(int nx, int ny, int nz, int tx, int ty) {
     while ((1 << m.lty) < ty) ++m.lty;
     m.nxp = (nx + tx - 1) / tx * tx;
     m.nyp = (ny + ty - 1) / ty * ty;
+    m.sw = sw ? 1 : 0;
     m.slice_p = (int64_t)m.nxp * m.nyp;
+    if (sw) m.slice_p = (m.slice_p + 31) / 32 * 32;
     m.vint = m.slice_p * nz;
     return m;
 }
 
+// true when the internal order is not the canonical one (columns are rewritten at load)
+inline bool voxmap_reorders(const VoxMap& m) { return m.tx != 1 || m.ty != 1 || m.sw; }
+
 // internal index of canonical voxel j on the host (the device has vox_internal)
 inline int64_t vox_internal_host(const VoxMap& m, int64_t j) {
-    if (m.tx == 1 && m.ty == 1) return j;
+    if (!voxmap_reorders(m)) return j;
     const int64_t ix = j % m.nx, t = j / m.nx, iy = t % m.ny, iz = t / m.ny;
     const int64_t ntx = m.nxp / m.tx;
-    return iz * m.slice_p + ((iy / m.ty) * ntx + ix / m.tx) * (int64_t)(m.tx * m.ty) + (iy % m.ty) * m.tx + ix % m.tx;
+    int64_t p = ((iy / m.ty) * ntx + ix / m.tx) * (int64_t)(m.tx * m.ty) + (iy % m.ty) * m.tx + ix % m.tx;
+    if (m.sw) p ^= (p >> 5) & 31;
+    return iz * m.slice_p + p;
 }
 
 // FP32 copies of the FP64 master image, written together with it: x32 in the internal
