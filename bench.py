@@ -191,14 +191,18 @@ def drop_kernel_hash():
     return h.hexdigest()
 
 
-def ncu_traffic_per_launch():
+def ncu_traffic_per_launch(config, dtype):
     """dram bytes per DROP launch from the committed ncu summary, if it was taken on the
-    current kernel source; else None."""
+    current kernel source and scaled to this line's workload and configuration; else None."""
     p = os.path.join(ROOT, "profiles", "drop_block_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
     if d.get("kernel_src_sha256") != drop_kernel_hash():
+        return None
+    want = d.get("applies_to") or {}
+    have = dict(config, dtype=dtype)
+    if not want or any(have.get(k) != v for k, v in want.items()):
         return None
     return d.get("dram_bytes_per_full_launch")
 
@@ -754,7 +758,12 @@ def run_ntvs(args):
     peak, peak_kind = measured_peaks()
     kname = {2: "drop_block_window_kernel", 3: "drop_pipe_kernel"}.get(st0["drop_schedule"], "drop_block_kernel")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": ncu_traffic_per_launch(), "kernel": kname,
+                "traffic": ncu_traffic_per_launch(
+                    {"workload": spec.name, "storage": "csr32",
+                     "drop_schedule": {1: "plain", 2: "window", 3: "pipeline"}.get(st0["drop_schedule"]),
+                     "voxel_tile": f"{st0['voxel_tile_x']}x{st0['voxel_tile_y']}"},
+                    "f32" if vdt == np.float32 else "f64"),
+                "kernel": kname,
                 "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": avg_bytes,
                 "avg_launch_ms": avg_ms,
                 "timing": f"CUDA events around every launch in a second timed pass of {args.steps} cycles "
