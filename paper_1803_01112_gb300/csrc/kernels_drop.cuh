@@ -130,6 +130,14 @@ struct WinScale {
 // window starts at a slice), so its slot is the offset itself; the FP64 path gathers the
 // canonical order and swizzles here.
 __device__ __forceinline__ int swz(int j) { return j ^ ((j >> 5) & 31); }
+// A DELTA16 word read without allocating in L1, which the x gathers then keep (0.2504 ->
+// 0.2481 ms per 500k-row BF16 block; the FP32 pairs measured slower this way, 0.2307 ->
+// 0.2325 ms, and keep the streaming load)
+__device__ __forceinline__ uint32_t ld_no_l1(const uint32_t* p) {
+    uint32_t v;
+    asm("ld.global.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
 template <typename T>
 __device__ __forceinline__ int win_slot(int j) {
     if constexpr (sizeof(T) == 4) return j;
@@ -278,7 +286,7 @@ __device__ __forceinline__ void drop_row(int64_t i, const RowHead& h, bool valid
                 }
             } else {
                 if constexpr (W16) {
-                    const uint32_t e = __ldcs(wr + q);
+                    const uint32_t e = ld_no_l1(wr + q);
                     if constexpr (NARROW) c[u][0] = rbase + (int)(e & 0xffffu);
                     else c[u][0] = d16_col_o<ESC>(d16, cbr, (int)(e & 0xffffu), q);
                     a[u][0] = (T)word_value<V>(e);
