@@ -4,7 +4,10 @@ copy, the DROP accumulator, the hit counts and the stored columns) against the F
 The order changes only which addresses the kernels touch, not what they sum: every bar
 here is the FP32 bar of the canonical order (relative L2 1e-6 for one DROP sweep, 1e-5
 for whole runs at eps 1e-4).  Grids are ragged (nx, ny not multiples of the tile) so the
-padded tiles of the last tile row and column are exercised.
+padded tiles of the last tile row and column are exercised.  The stored systems' order also
+permutes each slice's offsets inside aligned groups of 32 (the slice windows' bank
+swizzle); at 37 x 29 the 1x1, 2x2 and 8x2 tiles give slices of 1073, 1140 and 1200 voxels,
+so the padding of a slice to a multiple of 32 is exercised as well.
 """
 import numpy as np
 import pytest
