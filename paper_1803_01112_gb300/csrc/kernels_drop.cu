@@ -205,13 +205,14 @@ __global__ void chunk_cost_kernel(const int64_t* __restrict__ row_ptr, const int
         long long acc = 0;
         for (int64_t i = r0 + lane; i < r1; i += 32) {
             if (d <= 0) {
-                acc += 1;
+                acc += 4;
                 continue;
             }
             const int64_t steps = (row_ptr[i + 1] - row_ptr[i] + 31) / 32;
             const int64_t body = (steps <= kShortBody && d > kShortBody) ? kShortBody
                                  : (mid > 0 && d > mid && steps <= mid) ? mid : d;
-            acc += 1 + body + 2 * (steps > d ? steps - d : 0);
+            const int64_t live = steps < body ? steps : body;
+            acc += 4 + 4 * live + (body - live) + 8 * (steps > d ? steps - d : 0);
         }
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) cost[q] = acc;

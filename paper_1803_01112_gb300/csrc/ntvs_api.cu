@@ -720,7 +720,8 @@ static int pack_delta16(ntvs_ctx* c) {
 // the same home slice and adjacent rows merge into one segment.  A chunk's work is counted
 // in the register steps its rows issue (k_chunk_cost): a row costs the depth of the body
 // it runs, not its entry count, since every step of a body issues whether or not it holds
-// entries (measured: the busiest SM's excess over the mean follows this count).
+// entries (measured: the busiest SM's excess over the mean follows this count); a step
+// past the row's end issues predicated off and counts a quarter of a live one.
 constexpr int kChunkRows = 64;
 constexpr double kMinMeanRun = 8.0;
 
@@ -816,7 +817,7 @@ static int plan_schedule(ntvs_ctx* c, int requested) {
     std::vector<Chunk> ch;
     for (int t = 0; t < c->B; ++t) {
         ch.clear();
-        int64_t total = 0;   // the block's work (a chunk costs at least one unit per row)
+        int64_t total = 0;   // the block's work (at least one unit per row, as a guard)
         for (int64_t q = block_chunk[t]; q < block_chunk[t + 1]; ++q) {
             const int64_t w = std::max<int64_t>(ccost[(size_t)q], cstart[q + 1] - cstart[q]);
             ch.push_back({cstart[q], cstart[q + 1], chome[q], w});
